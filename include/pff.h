@@ -1,0 +1,178 @@
+/*
+ * pff.h -- C ABI of the B300 (sm_103a) matrix-free phase-field fracture step.
+ *
+ * The library computes the hot path of the explicit-dynamic phase-field
+ * method of arxiv 2606.23458: the P1 element kernel (strain, energy split,
+ * degraded stress, history), deterministic internal-force accumulation, the
+ * lumped-mass velocity-Verlet update, and the staggered damage solve (AT2 by
+ * Jacobi-preconditioned CG with post-clamp, AT1 by projected CG), plus the
+ * implicit-differentiation backward for dL/dGc.
+ *
+ * Conventions for every entry point:
+ *  - Units are SI (m, Pa, kg/m^3, J/m^2, s); energies are per unit thickness.
+ *  - Host pointers are marked "host"; all other buffers are device pointers
+ *    owned by the caller, contiguous, and typed by the mesh precision:
+ *      PFF_FP64       : u, v, a (N x 2, x/y interleaved), d (N) are double;
+ *      PFF_FP32_MIXED : u, v, a, d are float.
+ *    The history H (Ne) is always double.
+ *  - Calls are ordered on the given cudaStream_t and asynchronous, except
+ *    where a call returns host scalars (then it synchronises that stream).
+ *  - No call throws; every call returns a pff_status.  pff_last_error()
+ *    returns a thread-local message for the last failure.
+ *  - Deterministic: force and damage-operator accumulation use a
+ *    node-to-element gather in ascending element order (no float atomics);
+ *    reductions use fixed-order block partial sums.  Two runs on the same
+ *    device give bit-identical results.
+ */
+#ifndef PFF_H
+#define PFF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *pff_stream; /* same handle as cudaStream_t */
+
+typedef enum {
+  PFF_OK = 0,
+  PFF_ERR_ARG = 1,            /* invalid argument (null, size, enum) */
+  PFF_ERR_MESH = 2,           /* inverted/degenerate element or bad index */
+  PFF_ERR_CUDA = 3,           /* a CUDA runtime call failed */
+  PFF_ERR_OOM = 4,            /* device allocation failed */
+  PFF_ERR_NOT_CONVERGED = 5,  /* CG hit its iteration/restart cap; the last
+                                 iterate is still written */
+  PFF_ERR_TIMEOUT = 6,        /* a bounded device-side wait gave up */
+  PFF_ERR_NONFINITE = 7       /* NaN/Inf met in a reduction */
+} pff_status;
+
+enum { PFF_AT1 = 1, PFF_AT2 = 2 };
+enum { PFF_SPLIT_SPECTRAL = 0, PFF_SPLIT_AMOR = 1, PFF_SPLIT_ISO = 2 };
+enum { PFF_PLANE_STRAIN = 0 };
+enum { PFF_FP64 = 0, PFF_FP32_MIXED = 1 };
+enum { PFF_LOOP_GRAPH = 0, PFF_LOOP_HOST = 1 };
+
+typedef struct pff_mesh pff_mesh; /* opaque; owns geometry, CSR, workspaces */
+
+/* Material (Sec. 2.1 of the paper; Table 1 gives the benchmark values).
+ * model: PFF_AT1 | PFF_AT2 (crack density, Sec. 2.1);
+ * split: spectral (Eq. spectral_split), volumetric-deviatoric (Eq.
+ *        amor_split) or isotropic (psi+ = psi);
+ * plane: plane strain (lambda_PE); eta: residual stiffness in
+ *        g(d) = (1-d)^2 + eta. */
+typedef struct {
+  double E, nu, rho, Gc, l0, eta;
+  int32_t model, split, plane, reserved;
+} pff_material;
+
+/* Solver options.  Zero-initialise and set what you need; zero fields take
+ * the defaults given in brackets. */
+typedef struct {
+  double cg_tol;        /* ||r||_2 <= cg_tol * ||b_eff||_2 (Sec. 2.4) [1e-8] */
+  int32_t cg_max_it;    /* CG iterations per solve (all restarts) [10000] */
+  int32_t max_restarts; /* AT1 projected-CG restarts [50] */
+  double t_ramp;        /* traction ramp S(t), Eq. smooth_traction_ramp [5e-8 s] */
+  int32_t energy_every; /* pff_run: energies every k steps, 0 = off [0] */
+  int32_t ckpt_every;   /* pff_backward: checkpoint period [25] */
+  int32_t block;        /* threads per block, 0 = autotuned [0] */
+  int32_t loop_mode;    /* PFF_LOOP_GRAPH (device-side CG loop in a CUDA
+                           graph) or PFF_LOOP_HOST (host polls) [graph] */
+} pff_options;
+
+/* Device state of one plate (caller-owned). */
+typedef struct {
+  void *u, *v, *a; /* N x 2 displacement, velocity, acceleration */
+  void *d;         /* N damage */
+  double *H;       /* Ne history max of psi+ (per element) */
+} pff_state;
+
+/* Builds a mesh on the current device from host arrays (copied).
+ *  xy     host, N x 2 node coordinates (double);
+ *  tri    host, Ne x 3 counter-clockwise P1 connectivity (int32, 0-based);
+ *  notch  host, N flags (nullable): damage held at d = 1 there (Dirichlet);
+ *  tedges host, M x 2 loaded boundary edges; tvec host, M x 2 traction (Pa)
+ *         on each edge; the consistent P1 edge load gives half the edge
+ *         force to each end node;
+ *  precision: PFF_FP64 or PFF_FP32_MIXED.
+ * Geometry per Eq. (grad_phi) (Sec. 2.3): areas, shape gradients, the
+ * node-to-element incidence (for node i: (e << 2) | slot, ascending e) and
+ * the minimum incircle diameter are computed by device kernels.
+ * Errors: PFF_ERR_ARG (sizes, Ne >= 2^29), PFF_ERR_MESH (A_e <= 0 or an
+ * index outside [0, N); pff_last_error names the element), PFF_ERR_OOM. */
+pff_status pff_mesh_create(int64_t N, const double *xy, int64_t Ne,
+                           const int32_t *tri, const uint8_t *notch, int64_t M,
+                           const int32_t *tedges, const double *tvec,
+                           int32_t precision, pff_mesh **out);
+
+void pff_mesh_destroy(pff_mesh *mesh);
+
+/* Sets the material: plane-strain Lame constants (Sec. 2.1), lumped mass
+ * m_i = rho sum A_e / 3 and the stable step dt = cfl * h_min / c_p with
+ * c_p = sqrt((lambda + 2 mu) / rho) (velocity-Verlet paragraph, Sec. 2.3).
+ * dt_out (host, nullable) receives that step.  Synchronises internally. */
+pff_status pff_mesh_set_material(pff_mesh *mesh, const pff_material *mat,
+                                 double cfl, double *dt_out);
+
+/* Host copies for inspection (each output nullable):
+ *  N, Ne, h_min, precision; */
+pff_status pff_mesh_info(const pff_mesh *mesh, int64_t *N, int64_t *Ne,
+                         double *hmin, int32_t *precision);
+/*  ptr (N+1) and ent (3 Ne) incidence, int32; */
+pff_status pff_mesh_get_csr(const pff_mesh *mesh, int32_t *ptr, int32_t *ent);
+/*  area (Ne), grad (Ne x 3 x 2), fext (N x 2 full-scale load), minv (N)
+ *  converted to double (minv needs pff_mesh_set_material first). */
+pff_status pff_mesh_get_geometry(const pff_mesh *mesh, double *area,
+                                 double *grad, double *fext, double *minv);
+
+/* One explicit step n -> n+1 without the damage solve (Sec. 2.2, Eqs.
+ * vv_u, vv_a, vv_v): u += dt v + dt^2/2 a; f = internal force at the new u
+ * with the current d; H_e = max(H_e, psi+_e); a = (S(t_next) f_ext - f)/m;
+ * v += dt/2 (a_old + a_new).  In place on state.  Asynchronous. */
+pff_status pff_step_explicit(pff_mesh *mesh, const pff_state *state,
+                             double t_next, double dt, const pff_options *opt,
+                             pff_stream stream);
+
+/* Staggered damage solve with history H (Sec. 2.4):
+ *  AT2: Eq. (damage_pde_at2) with consistent mass, notch nodes eliminated
+ *       (x_D = 1), Jacobi-PCG from x0 = d_prev to cg_tol, then
+ *       d_out = min(1, max(x, d_prev)), d_out = 1 on the notch;
+ *  AT1: Eq. (damage_pde_at1) by projected CG on [d_prev, 1].
+ * d_out may alias d_prev.  iters/relres/restarts (host, nullable) receive
+ * the iteration count, ||r||/||b_eff|| and the AT1 restarts; this
+ * synchronises the stream.  PFF_ERR_NOT_CONVERGED still writes d_out. */
+pff_status pff_damage_solve(pff_mesh *mesh, const double *H, const void *d_prev,
+                            void *d_out, const pff_options *opt, int32_t *iters,
+                            double *relres, int32_t *restarts, pff_stream stream);
+
+/* nsteps staggered steps (predictor, force, history, corrector, damage
+ * solve) starting at step index step0 (t_n = n dt), in place on state.
+ * The step sequence runs as one CUDA graph per step with the CG loop on
+ * the device.  iters_log (device int32, nsteps x 2, nullable): per step
+ * (CG iterations, AT1 restarts).  energy_log (device double, nsteps x 4,
+ * nullable): E_el, E_kin, E_frac, W_ext after every opt->energy_every-th
+ * step (other rows untouched).  Asynchronous; pff_sync_status() returns the
+ * worst device status. */
+pff_status pff_run(pff_mesh *mesh, const pff_state *state, int64_t step0,
+                   int64_t nsteps, double dt, const pff_options *opt,
+                   int32_t *iters_log, double *energy_log, pff_stream stream);
+
+/* Synchronises the stream and returns (and clears) the worst status the
+ * device recorded since the last call (not converged, non-finite, timeout). */
+pff_status pff_sync_status(pff_mesh *mesh, pff_stream stream);
+
+/* Energies per unit thickness (Sec. 3.1): out[0] = E_el = sum A_e psi,
+ * out[1] = E_kin = 1/2 sum m |v|^2, out[2] = E_frac = Gc int gamma(d).
+ * out is host; synchronises the stream. */
+pff_status pff_energies(pff_mesh *mesh, const pff_state *state, double *out,
+                        pff_stream stream);
+
+/* Threads of the last failing call on this host thread. */
+const char *pff_last_error(void);
+const char *pff_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PFF_H */

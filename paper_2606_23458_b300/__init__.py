@@ -1,0 +1,243 @@
+"""Python binding of libpff (B300 / sm_103a phase-field fracture step).
+
+Argument marshalling only: every step of the method runs in the CUDA
+kernels of libpff.so, reached through its C ABI (include/pff.h).  PyTorch
+supplies device memory and streams.  Importing this package fails loudly if
+the library has not been built; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpff.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libpff.so is not built ({LIB_PATH}); run "
+                      "`python -m paper_2606_23458_b300.build` or __graft_entry__.build()")
+
+_lib = C.CDLL(LIB_PATH)
+
+PFF_OK, PFF_ERR_ARG, PFF_ERR_MESH, PFF_ERR_CUDA, PFF_ERR_OOM = 0, 1, 2, 3, 4
+PFF_ERR_NOT_CONVERGED, PFF_ERR_TIMEOUT, PFF_ERR_NONFINITE = 5, 6, 7
+PFF_AT1, PFF_AT2 = 1, 2
+PFF_SPLIT_SPECTRAL, PFF_SPLIT_AMOR, PFF_SPLIT_ISO = 0, 1, 2
+PFF_FP64, PFF_FP32_MIXED = 0, 1
+PFF_LOOP_GRAPH, PFF_LOOP_HOST = 0, 1
+
+MODELS = {"AT1": PFF_AT1, "AT2": PFF_AT2}
+SPLITS = {"spectral": PFF_SPLIT_SPECTRAL, "amor": PFF_SPLIT_AMOR, "iso": PFF_SPLIT_ISO}
+PRECISIONS = {"fp64": PFF_FP64, "fp32": PFF_FP32_MIXED}
+
+
+class PffError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"pff status {status}: {msg}")
+        self.status = status
+
+
+class pff_material(C.Structure):
+    _fields_ = [("E", C.c_double), ("nu", C.c_double), ("rho", C.c_double),
+                ("Gc", C.c_double), ("l0", C.c_double), ("eta", C.c_double),
+                ("model", C.c_int32), ("split", C.c_int32), ("plane", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+class pff_options(C.Structure):
+    _fields_ = [("cg_tol", C.c_double), ("cg_max_it", C.c_int32),
+                ("max_restarts", C.c_int32), ("t_ramp", C.c_double),
+                ("energy_every", C.c_int32), ("ckpt_every", C.c_int32),
+                ("block", C.c_int32), ("loop_mode", C.c_int32)]
+
+
+class pff_state(C.Structure):
+    _fields_ = [("u", C.c_void_p), ("v", C.c_void_p), ("a", C.c_void_p),
+                ("d", C.c_void_p), ("H", C.c_void_p)]
+
+
+_P = C.c_void_p
+_sig = {
+    "pff_mesh_create": [C.c_int64, _P, C.c_int64, _P, _P, C.c_int64, _P, _P, C.c_int32,
+                        C.POINTER(C.c_void_p)],
+    "pff_mesh_destroy": [_P],
+    "pff_mesh_set_material": [_P, C.POINTER(pff_material), C.c_double, C.POINTER(C.c_double)],
+    "pff_mesh_info": [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_double),
+                      C.POINTER(C.c_int32)],
+    "pff_mesh_get_csr": [_P, _P, _P],
+    "pff_mesh_get_geometry": [_P, _P, _P, _P, _P],
+    "pff_step_explicit": [_P, C.POINTER(pff_state), C.c_double, C.c_double,
+                          C.POINTER(pff_options), _P],
+    "pff_damage_solve": [_P, _P, _P, _P, C.POINTER(pff_options), C.POINTER(C.c_int32),
+                         C.POINTER(C.c_double), C.POINTER(C.c_int32), _P],
+    "pff_run": [_P, C.POINTER(pff_state), C.c_int64, C.c_int64, C.c_double,
+                C.POINTER(pff_options), _P, _P, _P],
+    "pff_sync_status": [_P, _P],
+    "pff_energies": [_P, C.POINTER(pff_state), _P, _P],
+}
+for _name, _args in _sig.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = None if _name == "pff_mesh_destroy" else C.c_int
+_lib.pff_last_error.restype = C.c_char_p
+_lib.pff_version.restype = C.c_char_p
+
+
+def _check(st):
+    if st != PFF_OK:
+        raise PffError(st, _lib.pff_last_error().decode())
+    return st
+
+
+def version():
+    return _lib.pff_version().decode()
+
+
+def _np(a, dtype):
+    return np.ascontiguousarray(np.asarray(a, dtype=dtype))
+
+
+def _hp(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def options(cg_tol=1e-8, cg_max_it=10000, max_restarts=50, t_ramp=0.05e-6, energy_every=0,
+            ckpt_every=25, block=0, loop_mode=PFF_LOOP_GRAPH):
+    return pff_options(cg_tol, cg_max_it, max_restarts, t_ramp, energy_every, ckpt_every,
+                       block, loop_mode)
+
+
+def material(mat):
+    return pff_material(float(mat["E"]), float(mat["nu"]), float(mat["rho"]), float(mat["Gc"]),
+                        float(mat["l0"]), float(mat.get("eta", 1e-7)),
+                        MODELS[mat.get("model", "AT2")], SPLITS[mat.get("split", "spectral")], 0, 0)
+
+
+def _dptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+class Mesh:
+    """A device mesh (pff_mesh handle) and its material."""
+
+    def __init__(self, xy, tri, notch=None, tedges=None, tvec=None, precision="fp32"):
+        xy = _np(xy, np.float64)
+        tri = _np(tri, np.int32)
+        self.N, self.Ne = xy.shape[0], tri.shape[0]
+        notch = None if notch is None else _np(notch, np.uint8)
+        if tedges is None:
+            tedges, tvec = np.zeros((0, 2), np.int32), np.zeros((0, 2))
+        tedges = _np(tedges, np.int32)
+        tvec = _np(tvec, np.float64)
+        self.precision = precision
+        h = C.c_void_p()
+        _check(_lib.pff_mesh_create(self.N, _hp(xy), self.Ne, _hp(tri), _hp(notch),
+                                    tedges.shape[0], _hp(tedges), _hp(tvec),
+                                    PRECISIONS[precision], C.byref(h)))
+        self._h = h
+        self.notch = np.zeros(self.N, np.uint8) if notch is None else notch
+        self.mat = None
+        self.dt = None
+
+    @classmethod
+    def from_plate(cls, p, precision="fp32"):
+        return cls(p["xy"], p["tri"], p["notch"], p["tedges"], p["tvec"], precision)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.pff_mesh_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def dtype(self):
+        import torch
+        return torch.float64 if self.precision == "fp64" else torch.float32
+
+    def set_material(self, mat, cfl=0.5):
+        m = material(mat)
+        dt = C.c_double()
+        _check(_lib.pff_mesh_set_material(self._h, C.byref(m), float(cfl), C.byref(dt)))
+        self.mat = dict(mat)
+        self.dt = dt.value
+        return dt.value
+
+    def info(self):
+        N = C.c_int64(); Ne = C.c_int64(); h = C.c_double(); p = C.c_int32()
+        _check(_lib.pff_mesh_info(self._h, C.byref(N), C.byref(Ne), C.byref(h), C.byref(p)))
+        return dict(N=N.value, Ne=Ne.value, hmin=h.value, precision=p.value)
+
+    def csr(self):
+        ptr = np.zeros(self.N + 1, np.int32)
+        ent = np.zeros(3 * self.Ne, np.int32)
+        _check(_lib.pff_mesh_get_csr(self._h, _hp(ptr), _hp(ent)))
+        return ptr, ent
+
+    def geometry(self):
+        area = np.zeros(self.Ne); grad = np.zeros((self.Ne, 3, 2))
+        fext = np.zeros((self.N, 2)); minv = np.zeros(self.N)
+        _check(_lib.pff_mesh_get_geometry(self._h, _hp(area), _hp(grad), _hp(fext),
+                                          _hp(minv) if self.mat is not None else None))
+        return area, grad, fext, minv
+
+    def new_state(self, device="cuda"):
+        import torch
+        dt = self.dtype
+        d = torch.as_tensor(self.notch, device=device).to(dt)
+        return dict(u=torch.zeros(self.N, 2, dtype=dt, device=device),
+                    v=torch.zeros(self.N, 2, dtype=dt, device=device),
+                    a=torch.zeros(self.N, 2, dtype=dt, device=device),
+                    d=d.contiguous(),
+                    H=torch.zeros(self.Ne, dtype=torch.float64, device=device))
+
+    def _state(self, st):
+        for k in ("u", "v", "a", "d"):
+            t = st[k]
+            assert t.is_cuda and t.is_contiguous() and t.dtype == self.dtype, k
+        assert st["H"].dtype.is_floating_point and st["H"].element_size() == 8
+        return pff_state(st["u"].data_ptr(), st["v"].data_ptr(), st["a"].data_ptr(),
+                         st["d"].data_ptr(), st["H"].data_ptr())
+
+    def step_explicit(self, st, t_next, dt=None, opts=None, stream=None):
+        s = self._state(st)
+        o = opts or options()
+        _check(_lib.pff_step_explicit(self._h, C.byref(s), float(t_next), float(dt or self.dt),
+                                      C.byref(o), _stream(stream)))
+
+    def damage_solve(self, H, dprev, dout, opts=None, stream=None, raise_on_error=True):
+        o = opts or options()
+        it = C.c_int32(); rel = C.c_double(); rs = C.c_int32()
+        st = _lib.pff_damage_solve(self._h, _dptr(H), _dptr(dprev), _dptr(dout), C.byref(o),
+                                   C.byref(it), C.byref(rel), C.byref(rs), _stream(stream))
+        if raise_on_error:
+            _check(st)
+        return dict(status=st, iters=it.value, relres=rel.value, restarts=rs.value)
+
+    def run(self, st, nsteps, step0=0, dt=None, opts=None, iters_log=None, energy_log=None,
+            stream=None):
+        s = self._state(st)
+        o = opts or options()
+        _check(_lib.pff_run(self._h, C.byref(s), int(step0), int(nsteps), float(dt or self.dt),
+                            C.byref(o), _dptr(iters_log), _dptr(energy_log), _stream(stream)))
+
+    def sync_status(self, stream=None):
+        return _lib.pff_sync_status(self._h, _stream(stream))
+
+    def energies(self, st, stream=None):
+        s = self._state(st)
+        out = np.zeros(3)
+        _check(_lib.pff_energies(self._h, C.byref(s), _hp(out), _stream(stream)))
+        return out

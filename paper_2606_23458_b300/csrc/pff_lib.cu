@@ -1,0 +1,887 @@
+// pff_lib.cu -- host runtime and C ABI of the phase-field fracture library.
+//
+// Owns the mesh (geometry, incidence, workspaces) on the device, builds the
+// CUDA graphs that run a damage solve or a whole staggered step with the CG
+// loop as a device-side conditional WHILE node, and exposes the C entry
+// points declared in include/pff.h.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+#include "pff.h"
+
+namespace pff {
+
+static thread_local std::string g_err;
+
+static pff_status fail(pff_status s, const std::string &msg) {
+  g_err = msg;
+  return s;
+}
+
+#define CUDA_TRY(call)                                                           \
+  do {                                                                           \
+    cudaError_t e_ = (call);                                                     \
+    if (e_ != cudaSuccess) {                                                     \
+      return fail(e_ == cudaErrorMemoryAllocation ? PFF_ERR_OOM : PFF_ERR_CUDA,  \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));           \
+    }                                                                            \
+  } while (0)
+
+#define PFF_TRY(call)              \
+  do {                             \
+    pff_status s_ = (call);        \
+    if (s_ != PFF_OK) return s_;   \
+  } while (0)
+
+template <typename T>
+static pff_status dalloc(T **p, size_t n) {
+  *p = nullptr;
+  if (n == 0) n = 1;
+  CUDA_TRY(cudaMalloc((void **)p, n * sizeof(T)));
+  return PFF_OK;
+}
+
+// --------------------------------------------------------- mesh kernels
+
+__global__ void k_check_tri(const int32_t *tri, int64_t Ne, int64_t N, unsigned long long *bad) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= Ne) return;
+  for (int a = 0; a < 3; ++a) {
+    const int32_t n = tri[3 * e + a];
+    if (n < 0 || n >= N) atomicMin(bad, (unsigned long long)e);
+  }
+}
+
+// P1 geometry, Eq. (grad_phi): A_e and the shape gradients; the incircle
+// diameter 4 A / P for the stable step; inverted elements are reported.
+template <typename R>
+__global__ void k_geometry(const double *xy, const int32_t *tri, int64_t Ne, int4 *tri4,
+                           typename V<R>::T4 *grad4, R *area, double *area_d,
+                           unsigned long long *bad, unsigned long long *hmin_bits) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= Ne) return;
+  const int32_t n1 = tri[3 * e], n2 = tri[3 * e + 1], n3 = tri[3 * e + 2];
+  const double x1 = xy[2 * n1], y1 = xy[2 * n1 + 1], x2 = xy[2 * n2], y2 = xy[2 * n2 + 1];
+  const double x3 = xy[2 * n3], y3 = xy[2 * n3 + 1];
+  const double A = 0.5 * ((x2 - x1) * (y3 - y1) - (x3 - x1) * (y2 - y1));
+  if (!(A > 0.0)) {
+    atomicMin(bad, (unsigned long long)e);
+    return;
+  }
+  const double s = 1.0 / (2.0 * A);
+  typename V<R>::T4 g;
+  g.x = (R)(s * (y2 - y3));
+  g.y = (R)(s * (x3 - x2));
+  g.z = (R)(s * (y3 - y1));
+  g.w = (R)(s * (x1 - x3));
+  grad4[e] = g;
+  area[e] = (R)A;
+  area_d[e] = A;
+  tri4[e] = make_int4(n1, n2, n3, 0);
+  const double P = hypot(x2 - x1, y2 - y1) + hypot(x3 - x2, y3 - y2) + hypot(x1 - x3, y1 - y3);
+  const double hin = 4.0 * A / P;
+  atomicMin(hmin_bits, (unsigned long long)__double_as_longlong(hin));  // positive doubles order as integers
+}
+
+__global__ void k_count(const int32_t *tri, int64_t Ne, int32_t *cnt) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= Ne) return;
+  for (int a = 0; a < 3; ++a) atomicAdd(&cnt[tri[3 * e + a]], 1);
+}
+
+// Exclusive scan of cnt[0..n) into out[0..n] (out[n] = total), three phases.
+__global__ void k_scan_blocks(const int32_t *in, int64_t n, int32_t *bsum) {
+  __shared__ int32_t sh[1024];
+  const int64_t i = blockIdx.x * 1024LL + threadIdx.x;
+  sh[threadIdx.x] = i < n ? in[i] : 0;
+  __syncthreads();
+  for (int o = 512; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) bsum[blockIdx.x] = sh[0];
+}
+
+__global__ void k_scan_sums(int32_t *bsum, int64_t nb) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    int32_t run = 0;
+    for (int64_t b = 0; b < nb; ++b) {
+      const int32_t v = bsum[b];
+      bsum[b] = run;
+      run += v;
+    }
+  }
+}
+
+__global__ void k_scan_final(const int32_t *in, int64_t n, const int32_t *bsum, int32_t *out) {
+  __shared__ int32_t sh[1024];
+  const int64_t i = blockIdx.x * 1024LL + threadIdx.x;
+  const int32_t v = i < n ? in[i] : 0;
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {  // Hillis-Steele inclusive scan
+    const int32_t t = threadIdx.x >= o ? sh[threadIdx.x - o] : 0;
+    __syncthreads();
+    sh[threadIdx.x] += t;
+    __syncthreads();
+  }
+  if (i < n) out[i] = bsum[blockIdx.x] + sh[threadIdx.x] - v;
+  if (i == n - 1) out[n] = bsum[blockIdx.x] + sh[threadIdx.x];
+}
+
+__global__ void k_fill(const int32_t *tri, int64_t Ne, const int32_t *ptr, int32_t *cursor, int32_t *ent) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= Ne) return;
+  for (int a = 0; a < 3; ++a) {
+    const int32_t n = tri[3 * e + a];
+    const int32_t pos = atomicAdd(&cursor[n], 1);
+    ent[ptr[n] + pos] = (int32_t)((e << 2) | a);
+  }
+}
+
+// Sort each node's incidence ascending (element id, then slot): fixes the
+// accumulation order independently of the fill's atomics.
+__global__ void k_sort_segments(const int32_t *ptr, int64_t N, int32_t *ent) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int32_t k0 = ptr[i], k1 = ptr[i + 1];
+  for (int32_t k = k0 + 1; k < k1; ++k) {
+    const int32_t v = ent[k];
+    int32_t j = k - 1;
+    while (j >= k0 && ent[j] > v) {
+      ent[j + 1] = ent[j];
+      --j;
+    }
+    ent[j + 1] = v;
+  }
+}
+
+// Consistent P1 traction load, edges in order (one thread: deterministic,
+// same order as a sequential assembly).
+__global__ void k_fext(const double *xy, const int32_t *ed, const double *tv, int64_t M, double *f) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int64_t k = 0; k < M; ++k) {
+    const int32_t i = ed[2 * k], j = ed[2 * k + 1];
+    const double L = hypot(xy[2 * j] - xy[2 * i], xy[2 * j + 1] - xy[2 * i + 1]);
+    for (int c = 0; c < 2; ++c) {
+      f[2 * i + c] += 0.5 * L * tv[2 * k + c];
+      f[2 * j + c] += 0.5 * L * tv[2 * k + c];
+    }
+  }
+}
+
+template <typename R>
+__global__ void k_node_init(const double *fd, const uint8_t *notch, int64_t N, typename V<R>::T2 *fext,
+                            uint8_t *flags) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  typename V<R>::T2 f;
+  f.x = (R)fd[2 * i];
+  f.y = (R)fd[2 * i + 1];
+  fext[i] = f;
+  uint8_t fl = 0;
+  if (notch && notch[i]) fl |= kNotch;
+  if (fd[2 * i] != 0.0 || fd[2 * i + 1] != 0.0) fl |= kLoaded;
+  flags[i] = fl;
+}
+
+// Lumped mass m_i = rho sum_{e ni i} A_e / 3 (ascending e), stored as 1/m.
+template <typename R>
+__global__ void k_lumped(const int32_t *ptr, const int32_t *ent, const double *area_d, int64_t N, double rho,
+                         R *minv) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  double m = 0.0;
+  for (int32_t k = ptr[i]; k < ptr[i + 1]; ++k) m += rho * area_d[ent[k] >> 2] / 3.0;
+  minv[i] = (R)(1.0 / m);
+}
+
+template <typename R>
+__global__ void k_geom_out(const typename V<R>::T4 *g4, const double *area_d, const typename V<R>::T2 *fext,
+                           const R *minv, int64_t N, int64_t Ne, double *area, double *grad, double *fo,
+                           double *mo) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < Ne) {
+    const typename V<R>::T4 g = g4[i];
+    if (area) area[i] = area_d[i];
+    if (grad) {
+      double *o = grad + 6 * i;
+      o[0] = g.x; o[1] = g.y; o[2] = g.z; o[3] = g.w;
+      o[4] = -((double)g.x + (double)g.z);
+      o[5] = -((double)g.y + (double)g.w);
+    }
+  }
+  if (i < N) {
+    if (fo) { fo[2 * i] = fext[i].x; fo[2 * i + 1] = fext[i].y; }
+    if (mo && minv) mo[i] = minv[i];
+  }
+}
+
+}  // namespace pff
+
+using namespace pff;
+
+struct GraphCache {
+  cudaGraphExec_t exec = nullptr;
+  std::vector<uint64_t> key;
+};
+
+struct pff_mesh {
+  int device = 0;
+  int32_t prec = PFF_FP64;
+  int64_t N = 0, Ne = 0;
+  size_t rs = 8;  // sizeof(R)
+  int32_t *ptr = nullptr, *ent = nullptr;
+  int4 *tri = nullptr;
+  void *grad = nullptr, *area = nullptr, *fext = nullptr, *minv = nullptr;
+  double *area_d = nullptr;
+  uint8_t *flags = nullptr;
+  double hmin = 0.0;
+  bool has_mat = false;
+  pff_material mat{};
+  double lam = 0, mu = 0, K = 0;
+  // workspace
+  double *x = nullptr, *r = nullptr, *b = nullptr, *part = nullptr, *energy = nullptr, *wext = nullptr;
+  void *z = nullptr, *p = nullptr, *q = nullptr, *dinv = nullptr, *mcoef = nullptr;
+  uint8_t *freef = nullptr;
+  unsigned int *ticket = nullptr;
+  SolveScalars *sc = nullptr;
+  int32_t *status_word = nullptr;
+  int64_t *step_ctr = nullptr;
+  GraphCache solve_g, step_g;
+  int block = 256;
+};
+
+namespace pff {
+
+static void free_graph(GraphCache &g) {
+  if (g.exec) cudaGraphExecDestroy(g.exec);
+  g.exec = nullptr;
+  g.key.clear();
+}
+
+static void mesh_free(pff_mesh *m) {
+  if (!m) return;
+  free_graph(m->solve_g);
+  free_graph(m->step_g);
+  void *ptrs[] = {m->ptr, m->ent, m->tri, m->grad, m->area, m->fext, m->minv, m->area_d, m->flags,
+                  m->x, m->r, m->b, m->part, m->energy, m->wext, m->z, m->p, m->q, m->dinv,
+                  m->mcoef, m->freef, m->ticket, m->sc, m->status_word, m->step_ctr};
+  for (void *q : ptrs)
+    if (q) cudaFree(q);
+  delete m;
+}
+
+static inline unsigned grid_for(int64_t n, int block) { return (unsigned)((n + block - 1) / block); }
+
+static pff_options defaults(const pff_options *o) {
+  pff_options d{};
+  if (o) d = *o;
+  if (!(d.cg_tol > 0)) d.cg_tol = 1e-8;
+  if (d.cg_max_it <= 0) d.cg_max_it = 10000;
+  if (d.max_restarts <= 0) d.max_restarts = 50;
+  if (!(d.t_ramp > 0)) d.t_ramp = 0.05e-6;
+  if (d.ckpt_every <= 0) d.ckpt_every = 25;
+  return d;
+}
+
+template <typename R>
+static Params<R> base_params(pff_mesh *m, const pff_options &o) {
+  Params<R> P;
+  std::memset(&P, 0, sizeof(P));
+  P.N = (int32_t)m->N;
+  P.Ne = (int32_t)m->Ne;
+  P.ptr = m->ptr;
+  P.ent = m->ent;
+  P.tri = m->tri;
+  P.grad = (const typename V<R>::T4 *)m->grad;
+  P.area = (const R *)m->area;
+  P.flags = m->flags;
+  P.fext = (const typename V<R>::T2 *)m->fext;
+  P.minv = (const R *)m->minv;
+  const pff_material &mt = m->mat;
+  P.lam = (R)m->lam;
+  P.mu = (R)m->mu;
+  P.K = (R)m->K;
+  P.eta = (R)mt.eta;
+  P.split = mt.split;
+  P.model = mt.model;
+  const bool at1 = mt.model == PFF_AT1;
+  P.kappa = (R)((at1 ? 0.75 : 1.0) * mt.Gc * mt.l0);
+  P.cbase = at1 ? 0.0 : mt.Gc / mt.l0;
+  P.wbase = at1 ? -3.0 * mt.Gc / (8.0 * mt.l0) : 0.0;
+  P.Gc = mt.Gc;
+  P.l0 = mt.l0;
+  P.t_ramp = o.t_ramp;
+  P.x = m->x;
+  P.r = m->r;
+  P.b = at1 ? m->b : nullptr;
+  P.z = (R *)m->z;
+  P.p = (R *)m->p;
+  P.q = (R *)m->q;
+  P.dinv = (R *)m->dinv;
+  P.mcoef = (R *)m->mcoef;
+  P.freef = at1 ? m->freef : nullptr;
+  P.part = m->part;
+  P.ticket = m->ticket;
+  P.sc = m->sc;
+  P.tol = o.cg_tol;
+  P.max_it = o.cg_max_it;
+  P.max_restarts = o.max_restarts;
+  P.status_word = m->status_word;
+  P.energy_out = m->energy;
+  P.wext = m->wext;
+  return P;
+}
+
+template <typename R>
+static pff_status add_kernel(cudaGraph_t g, const std::vector<cudaGraphNode_t> &deps, void (*fn)(Params<R>),
+                             unsigned grid, int block, Params<R> &P, cudaGraphNode_t *out) {
+  cudaKernelNodeParams kp;
+  std::memset(&kp, 0, sizeof(kp));
+  void *args[] = {(void *)&P};
+  kp.func = (void *)fn;
+  kp.gridDim = dim3(grid);
+  kp.blockDim = dim3(block);
+  kp.kernelParams = args;
+  CUDA_TRY(cudaGraphAddKernelNode(out, g, deps.data(), deps.size(), &kp));
+  return PFF_OK;
+}
+
+static pff_status add_while(cudaGraph_t g, const std::vector<cudaGraphNode_t> &deps,
+                            cudaGraphConditionalHandle h, cudaGraph_t *body, cudaGraphNode_t *out) {
+  cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  CUDA_TRY(cudaGraphAddNode(out, g, deps.data(), nullptr, deps.size(), &cp));
+  *body = cp.conditional.phGraph_out[0];
+  return PFF_OK;
+}
+
+// Appends the damage solve (rhs -> CG loop -> finish) to graph g after dep.
+// The handles must already be in P (created on the top-level graph).
+template <typename R>
+static pff_status append_solve(cudaGraph_t g, cudaGraphNode_t dep, Params<R> &P, int64_t N, int block,
+                               cudaGraphNode_t *last) {
+  const unsigned G = grid_for(N, block);
+  std::vector<cudaGraphNode_t> d;
+  if (dep) d.push_back(dep);
+  cudaGraphNode_t n_rhs, n_loop, n_fin;
+  PFF_TRY(add_kernel<R>(g, d, k_dmg_rhs<R>, G, block, P, &n_rhs));
+  if (P.model == kAT1) {
+    cudaGraph_t outer, inner;
+    PFF_TRY(add_while(g, {n_rhs}, P.cond_outer, &outer, &n_loop));
+    cudaGraphNode_t n_rs, n_in, n_mv, n_up;
+    PFF_TRY(add_kernel<R>(outer, {}, k_at1_restart<R>, G, block, P, &n_rs));
+    PFF_TRY(add_while(outer, {n_rs}, P.cond_inner, &inner, &n_in));
+    PFF_TRY(add_kernel<R>(inner, {}, k_cg_matvec<R>, G, block, P, &n_mv));
+    PFF_TRY(add_kernel<R>(inner, {n_mv}, k_cg_update<R>, G, block, P, &n_up));
+  } else {
+    cudaGraph_t body;
+    PFF_TRY(add_while(g, {n_rhs}, P.cond_inner, &body, &n_loop));
+    cudaGraphNode_t n_mv, n_up;
+    PFF_TRY(add_kernel<R>(body, {}, k_cg_matvec<R>, G, block, P, &n_mv));
+    PFF_TRY(add_kernel<R>(body, {n_mv}, k_cg_update<R>, G, block, P, &n_up));
+  }
+  PFF_TRY(add_kernel<R>(g, {n_loop}, k_dmg_finish<R>, G, block, P, &n_fin));
+  *last = n_fin;
+  return PFF_OK;
+}
+
+// Host-polled variant of the same solve (debugging / PFF_LOOP_HOST).
+template <typename R>
+static pff_status solve_host_loop(Params<R> P, int64_t N, int block, cudaStream_t s) {
+  const unsigned G = grid_for(N, block);
+  P.use_cond = 0;
+  SolveScalars hs;
+  k_dmg_rhs<R><<<G, block, 0, s>>>(P);
+  CUDA_TRY(cudaGetLastError());
+  if (P.model == kAT1) {
+    for (;;) {
+      k_at1_restart<R><<<G, block, 0, s>>>(P);
+      CUDA_TRY(cudaMemcpyAsync(&hs, P.sc, sizeof(hs), cudaMemcpyDeviceToHost, s));
+      CUDA_TRY(cudaStreamSynchronize(s));
+      if (hs.done) break;
+      for (;;) {
+        k_cg_matvec<R><<<G, block, 0, s>>>(P);
+        k_cg_update<R><<<G, block, 0, s>>>(P);
+        CUDA_TRY(cudaMemcpyAsync(&hs, P.sc, sizeof(hs), cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+        if (hs.inner_done) break;
+      }
+    }
+  } else {
+    for (;;) {
+      CUDA_TRY(cudaMemcpyAsync(&hs, P.sc, sizeof(hs), cudaMemcpyDeviceToHost, s));
+      CUDA_TRY(cudaStreamSynchronize(s));
+      if (hs.done) break;
+      k_cg_matvec<R><<<G, block, 0, s>>>(P);
+      k_cg_update<R><<<G, block, 0, s>>>(P);
+      CUDA_TRY(cudaGetLastError());
+    }
+  }
+  k_dmg_finish<R><<<G, block, 0, s>>>(P);
+  CUDA_TRY(cudaGetLastError());
+  return PFF_OK;
+}
+
+template <typename R>
+static pff_status damage_solve_t(pff_mesh *m, const double *H, const void *dprev, void *dout,
+                                 const pff_options &o, int32_t *iters, double *relres, int32_t *restarts,
+                                 cudaStream_t s) {
+  Params<R> P = base_params<R>(m, o);
+  P.H = const_cast<double *>(H);
+  P.dprev = (const R *)dprev;
+  P.dout = (R *)dout;
+  const int block = o.block > 0 ? o.block : m->block;
+  if (o.loop_mode == PFF_LOOP_HOST) {
+    PFF_TRY(solve_host_loop<R>(P, m->N, block, s));
+  } else {
+    std::vector<uint64_t> key = {(uint64_t)H, (uint64_t)dprev, (uint64_t)dout, (uint64_t)block,
+                                 (uint64_t)o.cg_max_it, (uint64_t)o.max_restarts};
+    uint64_t tb;
+    std::memcpy(&tb, &o.cg_tol, 8);
+    key.push_back(tb);
+    if (!m->solve_g.exec || m->solve_g.key != key) {
+      free_graph(m->solve_g);
+      cudaGraph_t g;
+      CUDA_TRY(cudaGraphCreate(&g, 0));
+      CUDA_TRY(cudaGraphConditionalHandleCreate(&P.cond_inner, g, 1, cudaGraphCondAssignDefault));
+      if (P.model == kAT1)  // an unused handle makes instantiation fail
+        CUDA_TRY(cudaGraphConditionalHandleCreate(&P.cond_outer, g, 1, cudaGraphCondAssignDefault));
+      P.use_cond = 1;
+      cudaGraphNode_t last;
+      pff_status st = append_solve<R>(g, nullptr, P, m->N, block, &last);
+      if (st != PFF_OK) {
+        cudaGraphDestroy(g);
+        return st;
+      }
+      cudaError_t e = cudaGraphInstantiate(&m->solve_g.exec, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) {
+        m->solve_g.exec = nullptr;
+        return fail(PFF_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+      }
+      m->solve_g.key = key;
+    }
+    CUDA_TRY(cudaGraphLaunch(m->solve_g.exec, s));
+  }
+  SolveScalars hs;
+  CUDA_TRY(cudaMemcpyAsync(&hs, m->sc, sizeof(hs), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if (iters) *iters = hs.iters;
+  if (restarts) *restarts = hs.restarts;
+  if (relres) *relres = hs.bn > 0 ? std::sqrt(hs.rr) / hs.bn : 0.0;
+  if (hs.status == kStNotConverged) return fail(PFF_ERR_NOT_CONVERGED, "damage CG did not converge");
+  if (hs.status == kStNonfinite) return fail(PFF_ERR_NONFINITE, "non-finite residual in damage CG");
+  return PFF_OK;
+}
+
+template <typename R>
+static pff_status step_explicit_t(pff_mesh *m, const pff_state *st, double t_next, double dt,
+                                  const pff_options &o, cudaStream_t s) {
+  Params<R> P = base_params<R>(m, o);
+  P.u = (typename V<R>::T2 *)st->u;
+  P.v = (typename V<R>::T2 *)st->v;
+  P.a = (typename V<R>::T2 *)st->a;
+  P.d = (R *)st->d;
+  P.H = st->H;
+  P.dt = dt;
+  P.t_next = t_next;
+  const int block = o.block > 0 ? o.block : m->block;
+  const unsigned G = grid_for(m->N, block);
+  k_predict<R><<<G, block, 0, s>>>(P);
+  k_force<R><<<G, block, 0, s>>>(P);
+  CUDA_TRY(cudaGetLastError());
+  return PFF_OK;
+}
+
+template <typename R>
+static pff_status run_t(pff_mesh *m, const pff_state *st, int64_t step0, int64_t nsteps, double dt,
+                        const pff_options &o, int32_t *iters_log, double *energy_log, cudaStream_t s) {
+  Params<R> P = base_params<R>(m, o);
+  P.u = (typename V<R>::T2 *)st->u;
+  P.v = (typename V<R>::T2 *)st->v;
+  P.a = (typename V<R>::T2 *)st->a;
+  P.d = (R *)st->d;
+  P.H = st->H;
+  P.dt = dt;
+  P.step_ctr = m->step_ctr;
+  P.step_inc = m->step_ctr;
+  P.dprev = (const R *)st->d;
+  P.dout = (R *)st->d;
+  P.iters_log = iters_log ? iters_log - 2 * step0 : nullptr;  // indexed by absolute step
+  P.track_work = o.energy_every > 0 ? 1 : 0;
+  const int block = o.block > 0 ? o.block : m->block;
+  const unsigned G = grid_for(m->N, block);
+  CUDA_TRY(cudaMemcpyAsync(m->step_ctr, &step0, sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  if (step0 == 0) CUDA_TRY(cudaMemsetAsync(m->wext, 0, sizeof(double), s));
+  if (o.loop_mode == PFF_LOOP_HOST) {
+    for (int64_t n = 0; n < nsteps; ++n) {
+      k_predict<R><<<G, block, 0, s>>>(P);
+      k_force<R><<<G, block, 0, s>>>(P);
+      PFF_TRY(solve_host_loop<R>(P, m->N, block, s));
+      if (energy_log && o.energy_every > 0 && (n + 1) % o.energy_every == 0) {
+        Params<R> E = P;
+        E.energy_out = energy_log + 4 * n;
+        k_energies<R><<<G, block, 0, s>>>(E);
+      }
+    }
+    CUDA_TRY(cudaGetLastError());
+    return PFF_OK;
+  }
+  std::vector<uint64_t> key = {(uint64_t)st->u, (uint64_t)st->v, (uint64_t)st->a, (uint64_t)st->d,
+                               (uint64_t)st->H, (uint64_t)block, (uint64_t)o.cg_max_it,
+                               (uint64_t)o.max_restarts, (uint64_t)P.iters_log, (uint64_t)P.track_work};
+  uint64_t b1, b2, b3;
+  std::memcpy(&b1, &o.cg_tol, 8);
+  std::memcpy(&b2, &dt, 8);
+  std::memcpy(&b3, &o.t_ramp, 8);
+  key.push_back(b1);
+  key.push_back(b2);
+  key.push_back(b3);
+  if (!m->step_g.exec || m->step_g.key != key) {
+    free_graph(m->step_g);
+    cudaGraph_t g;
+    CUDA_TRY(cudaGraphCreate(&g, 0));
+    CUDA_TRY(cudaGraphConditionalHandleCreate(&P.cond_inner, g, 1, cudaGraphCondAssignDefault));
+    if (P.model == kAT1)
+      CUDA_TRY(cudaGraphConditionalHandleCreate(&P.cond_outer, g, 1, cudaGraphCondAssignDefault));
+    P.use_cond = 1;
+    cudaGraphNode_t n_pr, n_f, last;
+    pff_status stt = add_kernel<R>(g, {}, k_predict<R>, G, block, P, &n_pr);
+    if (stt == PFF_OK) stt = add_kernel<R>(g, {n_pr}, k_force<R>, G, block, P, &n_f);
+    if (stt == PFF_OK) stt = append_solve<R>(g, n_f, P, m->N, block, &last);
+    if (stt != PFF_OK) {
+      cudaGraphDestroy(g);
+      return stt;
+    }
+    cudaError_t e = cudaGraphInstantiate(&m->step_g.exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      m->step_g.exec = nullptr;
+      return fail(PFF_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+    }
+    m->step_g.key = key;
+  }
+  for (int64_t n = 0; n < nsteps; ++n) {
+    CUDA_TRY(cudaGraphLaunch(m->step_g.exec, s));
+    if (energy_log && o.energy_every > 0 && (n + 1) % o.energy_every == 0) {
+      Params<R> E = P;
+      E.energy_out = energy_log + 4 * n;
+      k_energies<R><<<G, block, 0, s>>>(E);
+      CUDA_TRY(cudaGetLastError());
+    }
+  }
+  return PFF_OK;
+}
+
+template <typename R>
+static pff_status energies_t(pff_mesh *m, const pff_state *st, double *out, cudaStream_t s) {
+  pff_options o = defaults(nullptr);
+  Params<R> P = base_params<R>(m, o);
+  P.u = (typename V<R>::T2 *)st->u;
+  P.v = (typename V<R>::T2 *)st->v;
+  P.a = (typename V<R>::T2 *)st->a;
+  P.d = (R *)st->d;
+  P.H = st->H;
+  const int block = m->block;
+  k_energies<R><<<grid_for(m->N, block), block, 0, s>>>(P);
+  CUDA_TRY(cudaGetLastError());
+  double h[4];
+  CUDA_TRY(cudaMemcpyAsync(h, m->energy, sizeof(h), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  out[0] = h[0];
+  out[1] = h[1];
+  out[2] = h[2];
+  return PFF_OK;
+}
+
+template <typename R>
+static pff_status mesh_build_t(pff_mesh *m, const double *xy_d, const int32_t *tri_d, double *fd,
+                               const uint8_t *notch_d, unsigned long long *scratch) {
+  const int64_t N = m->N, Ne = m->Ne;
+  const int blk = 256;
+  PFF_TRY(dalloc((typename V<R>::T4 **)&m->grad, Ne));
+  PFF_TRY(dalloc((R **)&m->area, Ne));
+  PFF_TRY(dalloc((typename V<R>::T2 **)&m->fext, N));
+  PFF_TRY(dalloc((R **)&m->minv, N));
+  PFF_TRY(dalloc((R **)&m->z, N));
+  PFF_TRY(dalloc((R **)&m->p, N));
+  PFF_TRY(dalloc((R **)&m->q, N));
+  PFF_TRY(dalloc((R **)&m->dinv, N));
+  PFF_TRY(dalloc((R **)&m->mcoef, Ne));
+  k_geometry<R><<<grid_for(Ne, blk), blk>>>(xy_d, tri_d, Ne, m->tri, (typename V<R>::T4 *)m->grad,
+                                             (R *)m->area, m->area_d, scratch, scratch + 1);
+  k_node_init<R><<<grid_for(N, blk), blk>>>(fd, notch_d, N, (typename V<R>::T2 *)m->fext, m->flags);
+  CUDA_TRY(cudaGetLastError());
+  return PFF_OK;
+}
+
+}  // namespace pff
+
+// ================================================================== C ABI
+
+extern "C" {
+
+const char *pff_last_error(void) { return g_err.c_str(); }
+const char *pff_version(void) { return "pff 0.1 (sm_103a)"; }
+
+pff_status pff_mesh_create(int64_t N, const double *xy, int64_t Ne, const int32_t *tri, const uint8_t *notch,
+                           int64_t M, const int32_t *tedges, const double *tvec, int32_t precision,
+                           pff_mesh **out) {
+  if (!out) return fail(PFF_ERR_ARG, "out is null");
+  *out = nullptr;
+  if (N <= 0 || Ne <= 0 || !xy || !tri) return fail(PFF_ERR_ARG, "empty mesh");
+  if (N >= (1LL << 31) || Ne >= (1LL << 29)) return fail(PFF_ERR_ARG, "mesh too large (N < 2^31, Ne < 2^29)");
+  if (M < 0 || (M > 0 && (!tedges || !tvec))) return fail(PFF_ERR_ARG, "bad traction edges");
+  if (precision != PFF_FP64 && precision != PFF_FP32_MIXED) return fail(PFF_ERR_ARG, "bad precision");
+  for (int64_t k = 0; k < 2 * M; ++k)
+    if (tedges[k] < 0 || tedges[k] >= N) return fail(PFF_ERR_MESH, "traction edge index out of range");
+  pff_mesh *m = new pff_mesh();
+  m->N = N;
+  m->Ne = Ne;
+  m->prec = precision;
+  m->rs = precision == PFF_FP64 ? 8 : 4;
+  cudaGetDevice(&m->device);
+  double *xy_d = nullptr, *tv_d = nullptr, *fd = nullptr;
+  int32_t *tri_d = nullptr, *ed_d = nullptr, *cnt = nullptr, *bsum = nullptr;
+  uint8_t *notch_d = nullptr;
+  unsigned long long *scratch = nullptr;
+  pff_status st = PFF_OK;
+  auto cleanup = [&]() {
+    void *t[] = {xy_d, tv_d, fd, tri_d, ed_d, cnt, bsum, notch_d, scratch};
+    for (void *q : t)
+      if (q) cudaFree(q);
+  };
+#define STEP(x)          \
+  do {                   \
+    st = (x);            \
+    if (st != PFF_OK) {  \
+      cleanup();         \
+      mesh_free(m);      \
+      return st;         \
+    }                    \
+  } while (0)
+#define CSTEP(x)                                                                   \
+  do {                                                                             \
+    cudaError_t e_ = (x);                                                          \
+    if (e_ != cudaSuccess) {                                                       \
+      STEP(fail(e_ == cudaErrorMemoryAllocation ? PFF_ERR_OOM : PFF_ERR_CUDA,      \
+                std::string(#x) + ": " + cudaGetErrorString(e_)));                 \
+    }                                                                              \
+  } while (0)
+  const int blk = 256;
+  STEP(dalloc(&xy_d, 2 * N));
+  STEP(dalloc(&tri_d, 3 * Ne));
+  STEP(dalloc(&fd, 2 * N));
+  STEP(dalloc(&scratch, 2));
+  STEP(dalloc(&m->tri, Ne));
+  STEP(dalloc(&m->area_d, Ne));
+  STEP(dalloc(&m->flags, N));
+  STEP(dalloc(&m->ptr, N + 1));
+  STEP(dalloc(&m->ent, 3 * Ne));
+  STEP(dalloc(&cnt, N));
+  const int64_t nb = (N + 1023) / 1024;
+  STEP(dalloc(&bsum, nb));
+  CSTEP(cudaMemcpy(xy_d, xy, 2 * N * sizeof(double), cudaMemcpyHostToDevice));
+  CSTEP(cudaMemcpy(tri_d, tri, 3 * Ne * sizeof(int32_t), cudaMemcpyHostToDevice));
+  if (notch) {
+    STEP(dalloc(&notch_d, N));
+    CSTEP(cudaMemcpy(notch_d, notch, N, cudaMemcpyHostToDevice));
+  }
+  unsigned long long init[2] = {~0ULL, ~0ULL};
+  CSTEP(cudaMemcpy(scratch, init, sizeof(init), cudaMemcpyHostToDevice));
+  k_check_tri<<<grid_for(Ne, blk), blk>>>(tri_d, Ne, N, scratch);
+  unsigned long long bad = 0;
+  CSTEP(cudaMemcpy(&bad, scratch, 8, cudaMemcpyDeviceToHost));
+  if (bad != ~0ULL) STEP(fail(PFF_ERR_MESH, "element " + std::to_string(bad) + " has a node index out of range"));
+  CSTEP(cudaMemset(fd, 0, 2 * N * sizeof(double)));
+  if (M > 0) {
+    STEP(dalloc(&ed_d, 2 * M));
+    STEP(dalloc(&tv_d, 2 * M));
+    CSTEP(cudaMemcpy(ed_d, tedges, 2 * M * sizeof(int32_t), cudaMemcpyHostToDevice));
+    CSTEP(cudaMemcpy(tv_d, tvec, 2 * M * sizeof(double), cudaMemcpyHostToDevice));
+    k_fext<<<1, 1>>>(xy_d, ed_d, tv_d, M, fd);
+  }
+  if (precision == PFF_FP64)
+    STEP(mesh_build_t<double>(m, xy_d, tri_d, fd, notch_d, scratch));
+  else
+    STEP(mesh_build_t<float>(m, xy_d, tri_d, fd, notch_d, scratch));
+  unsigned long long res[2];
+  CSTEP(cudaMemcpy(res, scratch, sizeof(res), cudaMemcpyDeviceToHost));
+  if (res[0] != ~0ULL)
+    STEP(fail(PFF_ERR_MESH, "element " + std::to_string(res[0]) + " is inverted or degenerate (A_e <= 0)"));
+  std::memcpy(&m->hmin, &res[1], 8);
+  // incidence: counts, scan, fill, per-node sort
+  CSTEP(cudaMemset(cnt, 0, N * sizeof(int32_t)));
+  k_count<<<grid_for(Ne, blk), blk>>>(tri_d, Ne, cnt);
+  k_scan_blocks<<<(unsigned)nb, 1024>>>(cnt, N, bsum);
+  k_scan_sums<<<1, 1>>>(bsum, nb);
+  k_scan_final<<<(unsigned)nb, 1024>>>(cnt, N, bsum, m->ptr);
+  CSTEP(cudaMemset(cnt, 0, N * sizeof(int32_t)));
+  k_fill<<<grid_for(Ne, blk), blk>>>(tri_d, Ne, m->ptr, cnt, m->ent);
+  k_sort_segments<<<grid_for(N, blk), blk>>>(m->ptr, N, m->ent);
+  CSTEP(cudaGetLastError());
+  // workspaces
+  const int64_t maxblocks = (N + 31) / 32;
+  STEP(dalloc(&m->x, N));
+  STEP(dalloc(&m->r, N));
+  STEP(dalloc(&m->b, N));
+  STEP(dalloc(&m->freef, N));
+  STEP(dalloc(&m->part, 4 * maxblocks));
+  STEP(dalloc(&m->energy, 4));
+  STEP(dalloc(&m->wext, 1));
+  STEP(dalloc(&m->ticket, 8));
+  STEP(dalloc(&m->sc, 1));
+  STEP(dalloc(&m->status_word, 1));
+  STEP(dalloc(&m->step_ctr, 1));
+  CSTEP(cudaMemset(m->ticket, 0, 8 * sizeof(unsigned int)));
+  CSTEP(cudaMemset(m->sc, 0, sizeof(SolveScalars)));
+  CSTEP(cudaMemset(m->status_word, 0, sizeof(int32_t)));
+  CSTEP(cudaMemset(m->wext, 0, sizeof(double)));
+  CSTEP(cudaMemset(m->energy, 0, 4 * sizeof(double)));
+  CSTEP(cudaDeviceSynchronize());
+  cleanup();
+#undef STEP
+#undef CSTEP
+  *out = m;
+  return PFF_OK;
+}
+
+void pff_mesh_destroy(pff_mesh *mesh) { mesh_free(mesh); }
+
+pff_status pff_mesh_set_material(pff_mesh *m, const pff_material *mat, double cfl, double *dt_out) {
+  if (!m || !mat) return fail(PFF_ERR_ARG, "null argument");
+  if (!(mat->E > 0) || !(mat->rho > 0) || !(mat->Gc > 0) || !(mat->l0 > 0) || !(mat->nu > -1.0) ||
+      !(mat->nu < 0.5) || mat->eta < 0)
+    return fail(PFF_ERR_ARG, "invalid material constants");
+  if (mat->model != PFF_AT1 && mat->model != PFF_AT2) return fail(PFF_ERR_ARG, "model must be AT1 or AT2");
+  if (mat->split < 0 || mat->split > 2) return fail(PFF_ERR_ARG, "unknown split");
+  if (mat->plane != PFF_PLANE_STRAIN) return fail(PFF_ERR_ARG, "only plane strain is supported");
+  m->mat = *mat;
+  m->lam = mat->E * mat->nu / ((1.0 + mat->nu) * (1.0 - 2.0 * mat->nu));
+  m->mu = mat->E / (2.0 * (1.0 + mat->nu));
+  m->K = mat->E / (3.0 * (1.0 - 2.0 * mat->nu));
+  const int blk = 256;
+  if (m->prec == PFF_FP64)
+    k_lumped<double><<<grid_for(m->N, blk), blk>>>(m->ptr, m->ent, m->area_d, m->N, mat->rho, (double *)m->minv);
+  else
+    k_lumped<float><<<grid_for(m->N, blk), blk>>>(m->ptr, m->ent, m->area_d, m->N, mat->rho, (float *)m->minv);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaDeviceSynchronize());
+  free_graph(m->solve_g);
+  free_graph(m->step_g);
+  m->has_mat = true;
+  const double cp = std::sqrt((m->lam + 2.0 * m->mu) / mat->rho);
+  if (dt_out) *dt_out = cfl * m->hmin / cp;
+  return PFF_OK;
+}
+
+pff_status pff_mesh_info(const pff_mesh *m, int64_t *N, int64_t *Ne, double *hmin, int32_t *prec) {
+  if (!m) return fail(PFF_ERR_ARG, "null mesh");
+  if (N) *N = m->N;
+  if (Ne) *Ne = m->Ne;
+  if (hmin) *hmin = m->hmin;
+  if (prec) *prec = m->prec;
+  return PFF_OK;
+}
+
+pff_status pff_mesh_get_csr(const pff_mesh *m, int32_t *ptr, int32_t *ent) {
+  if (!m) return fail(PFF_ERR_ARG, "null mesh");
+  if (ptr) CUDA_TRY(cudaMemcpy(ptr, m->ptr, (m->N + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
+  if (ent) CUDA_TRY(cudaMemcpy(ent, m->ent, 3 * m->Ne * sizeof(int32_t), cudaMemcpyDeviceToHost));
+  return PFF_OK;
+}
+
+pff_status pff_mesh_get_geometry(const pff_mesh *m, double *area, double *grad, double *fext, double *minv) {
+  if (!m) return fail(PFF_ERR_ARG, "null mesh");
+  double *a = nullptr, *g = nullptr, *f = nullptr, *mi = nullptr;
+  const int64_t n = m->N > m->Ne ? m->N : m->Ne;
+  if (area) PFF_TRY(dalloc(&a, m->Ne));
+  if (grad) PFF_TRY(dalloc(&g, 6 * m->Ne));
+  if (fext) PFF_TRY(dalloc(&f, 2 * m->N));
+  if (minv) PFF_TRY(dalloc(&mi, m->N));
+  const int blk = 256;
+  if (m->prec == PFF_FP64)
+    k_geom_out<double><<<grid_for(n, blk), blk>>>((const dbl4 *)m->grad, m->area_d, (const double2 *)m->fext,
+                                                   m->has_mat ? (const double *)m->minv : nullptr, m->N, m->Ne,
+                                                   a, g, f, mi);
+  else
+    k_geom_out<float><<<grid_for(n, blk), blk>>>((const float4 *)m->grad, m->area_d, (const float2 *)m->fext,
+                                                  m->has_mat ? (const float *)m->minv : nullptr, m->N, m->Ne, a,
+                                                  g, f, mi);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess && area) e = cudaMemcpy(area, a, m->Ne * 8, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && grad) e = cudaMemcpy(grad, g, 6 * m->Ne * 8, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && fext) e = cudaMemcpy(fext, f, 2 * m->N * 8, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && minv) e = cudaMemcpy(minv, mi, m->N * 8, cudaMemcpyDeviceToHost);
+  if (a) cudaFree(a);
+  if (g) cudaFree(g);
+  if (f) cudaFree(f);
+  if (mi) cudaFree(mi);
+  if (e != cudaSuccess) return fail(PFF_ERR_CUDA, cudaGetErrorString(e));
+  return PFF_OK;
+}
+
+pff_status pff_step_explicit(pff_mesh *m, const pff_state *st, double t_next, double dt, const pff_options *opt,
+                             pff_stream stream) {
+  if (!m || !st || !st->u || !st->v || !st->a || !st->d || !st->H) return fail(PFF_ERR_ARG, "null argument");
+  if (!m->has_mat) return fail(PFF_ERR_ARG, "material not set");
+  if (!(dt > 0)) return fail(PFF_ERR_ARG, "dt must be positive");
+  const pff_options o = defaults(opt);
+  cudaStream_t s = (cudaStream_t)stream;
+  return m->prec == PFF_FP64 ? step_explicit_t<double>(m, st, t_next, dt, o, s)
+                             : step_explicit_t<float>(m, st, t_next, dt, o, s);
+}
+
+pff_status pff_damage_solve(pff_mesh *m, const double *H, const void *dprev, void *dout, const pff_options *opt,
+                            int32_t *iters, double *relres, int32_t *restarts, pff_stream stream) {
+  if (!m || !H || !dprev || !dout) return fail(PFF_ERR_ARG, "null argument");
+  if (!m->has_mat) return fail(PFF_ERR_ARG, "material not set");
+  const pff_options o = defaults(opt);
+  cudaStream_t s = (cudaStream_t)stream;
+  return m->prec == PFF_FP64 ? damage_solve_t<double>(m, H, dprev, dout, o, iters, relres, restarts, s)
+                             : damage_solve_t<float>(m, H, dprev, dout, o, iters, relres, restarts, s);
+}
+
+pff_status pff_run(pff_mesh *m, const pff_state *st, int64_t step0, int64_t nsteps, double dt,
+                   const pff_options *opt, int32_t *iters_log, double *energy_log, pff_stream stream) {
+  if (!m || !st || !st->u || !st->v || !st->a || !st->d || !st->H) return fail(PFF_ERR_ARG, "null argument");
+  if (!m->has_mat) return fail(PFF_ERR_ARG, "material not set");
+  if (!(dt > 0) || nsteps < 0 || step0 < 0) return fail(PFF_ERR_ARG, "bad dt / step range");
+  const pff_options o = defaults(opt);
+  cudaStream_t s = (cudaStream_t)stream;
+  return m->prec == PFF_FP64 ? run_t<double>(m, st, step0, nsteps, dt, o, iters_log, energy_log, s)
+                             : run_t<float>(m, st, step0, nsteps, dt, o, iters_log, energy_log, s);
+}
+
+pff_status pff_sync_status(pff_mesh *m, pff_stream stream) {
+  if (!m) return fail(PFF_ERR_ARG, "null mesh");
+  cudaStream_t s = (cudaStream_t)stream;
+  int32_t w = 0;
+  CUDA_TRY(cudaMemcpyAsync(&w, m->status_word, sizeof(w), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  CUDA_TRY(cudaMemsetAsync(m->status_word, 0, sizeof(int32_t), s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if (w == kStNotConverged) return fail(PFF_ERR_NOT_CONVERGED, "a damage solve did not converge");
+  if (w == kStNonfinite) return fail(PFF_ERR_NONFINITE, "non-finite value in a damage solve");
+  if (w == kStTimeout) return fail(PFF_ERR_TIMEOUT, "a device-side wait timed out");
+  return PFF_OK;
+}
+
+pff_status pff_energies(pff_mesh *m, const pff_state *st, double *out, pff_stream stream) {
+  if (!m || !st || !out || !st->u || !st->v || !st->d) return fail(PFF_ERR_ARG, "null argument");
+  if (!m->has_mat) return fail(PFF_ERR_ARG, "material not set");
+  cudaStream_t s = (cudaStream_t)stream;
+  return m->prec == PFF_FP64 ? energies_t<double>(m, st, out, s) : energies_t<float>(m, st, out, s);
+}
+
+}  // extern "C"

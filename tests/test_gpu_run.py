@@ -1,0 +1,117 @@
+"""Full staggered runs on the GPU vs the oracle on the 100 x 40 plate
+(4,141 nodes, 8,000 triangles, glass, AT2, 200 steps)."""
+import numpy as np
+import pytest
+
+import pff_synth as S
+from gpu_common import max_rel, rel_l2, state_to_torch, to_np
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pff():
+    import paper_2606_23458_b300 as pff
+    return pff
+
+
+def _setup(pff, orc, name="plate_100x40", split="spectral", model="AT2", prec="fp64"):
+    c = S.config(name, split=split, model=model)
+    om = orc.Mesh.from_plate(c["mesh"])
+    gm = pff.Mesh.from_plate(c["mesh"], precision=prec)
+    dt = gm.set_material(c["material"], c["cfl"])
+    return c, om, gm, dt
+
+
+@pytest.mark.parametrize("split", ["spectral", "amor"])
+def test_fp64_per_step_parity(orc, pff, split):
+    """FP64 fields agree with the oracle to 1e-10 relative after every step;
+    the oracle is forced to the GPU's CG iteration count, whose own stop
+    decision must be within one iteration."""
+    import torch
+    c, om, gm, dt = _setup(pff, orc, split=split)
+    mat = c["material"]
+    nsteps = 200
+    gst = gm.new_state()
+    ost = om.new_state()
+    log = torch.zeros(nsteps, 2, dtype=torch.int32, device="cuda")
+    worst = 0.0
+    for n in range(nsteps):
+        gm.run(gst, 1, step0=n, iters_log=log[n:n + 1])
+        torch.cuda.synchronize()
+        it = int(log[n, 0])
+        r = om.run(mat, ost, 1, dt, n0=n, forced=[it])
+        for k in ("u", "v", "a"):
+            worst = max(worst, rel_l2(to_np(gst[k]), ost[k]))
+        worst = max(worst, max_rel(to_np(gst["d"]), ost["d"], 1e-3))
+        worst = max(worst, rel_l2(to_np(gst["H"]), ost["H"]))
+        assert worst <= 1e-10, (n, worst)
+    assert gm.sync_status() == 0
+
+
+def test_fp64_natural_stop_matches(orc, pff):
+    import torch
+    c, om, gm, dt = _setup(pff, orc)
+    nsteps = 200
+    gst = gm.new_state()
+    log = torch.zeros(nsteps, 2, dtype=torch.int32, device="cuda")
+    gm.run(gst, nsteps, iters_log=log)
+    ost = om.new_state()
+    r = om.run(c["material"], ost, nsteps, dt)
+    gi = log[:, 0].cpu().numpy()
+    assert np.abs(gi - r["iters"][:, 0]).max() <= 1
+    assert rel_l2(to_np(gst["u"]), ost["u"]) <= 1e-8
+    assert np.abs(to_np(gst["d"]) - ost["d"]).max() <= 1e-7
+
+
+@pytest.mark.parametrize("split", ["spectral", "amor"])
+def test_fp32_error_vs_fp64_oracle(orc, pff, split):
+    """FP32 kernels with FP64 reductions over the 200-step window: relative
+    L2 error of u <= 1e-4 and max |d - d_oracle| <= 1e-3."""
+    import torch
+    c, om, gm, dt = _setup(pff, orc, split=split, prec="fp32")
+    nsteps = 200
+    gst = gm.new_state()
+    gm.run(gst, nsteps)
+    torch.cuda.synchronize()
+    ost = om.new_state()
+    om.run(c["material"], ost, nsteps, dt)
+    eu = rel_l2(to_np(gst["u"]), ost["u"])
+    ed = np.abs(to_np(gst["d"]) - ost["d"]).max()
+    print(f"fp32 {split}: u rel L2 {eu:.3e}, max|dd| {ed:.3e}")
+    assert eu <= 1e-4 and ed <= 1e-3
+
+
+def test_at1_run(orc, pff):
+    import torch
+    c, om, gm, dt = _setup(pff, orc, split="amor", model="AT1")
+    nsteps = 100
+    gst = gm.new_state()
+    gm.run(gst, nsteps)
+    torch.cuda.synchronize()
+    assert gm.sync_status() == 0
+    ost = om.new_state()
+    r = om.run(c["material"], ost, nsteps, dt)
+    assert r["status"] == 0
+    assert rel_l2(to_np(gst["u"]), ost["u"]) <= 1e-7
+    assert np.abs(to_np(gst["d"]) - ost["d"]).max() <= 1e-6
+
+
+def test_energy_log_and_determinism(orc, pff):
+    import torch
+    c, om, gm, dt = _setup(pff, orc)
+    nsteps = 60
+    runs = []
+    for rep in range(2):
+        gst = gm.new_state()
+        en = torch.full((nsteps, 4), float("nan"), dtype=torch.float64, device="cuda")
+        gm.run(gst, nsteps, opts=pff.options(energy_every=10), energy_log=en)
+        torch.cuda.synchronize()
+        runs.append((gst, en.cpu().numpy()))
+    for k in ("u", "v", "a", "d", "H"):
+        assert torch.equal(runs[0][0][k], runs[1][0][k]), k
+    ost = om.new_state()
+    r = om.run(c["material"], ost, nsteps, dt, energy_every=10)
+    rows = np.arange(9, nsteps, 10)
+    assert np.allclose(runs[0][1][rows], r["energies"][rows], rtol=1e-8)
+    assert np.all(np.isnan(runs[0][1][0]))
