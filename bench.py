@@ -1,0 +1,335 @@
+#!/usr/bin/env python
+"""Benchmark of the explicit phase-field fracture step on B300.
+
+Workload (default): the 1000 x 1000-cell glass plate, 100 x 40 mm,
+1,002,001 nodes / 2,000,000 P1 triangles with +-0.1h seeded interior
+jitter, AT2, spectral split, plane strain, traction 1 MPa with the smooth
+ramp, dt = 0.5 x CFL, FP32 kernels with FP64 reductions/history.  A step is
+one full staggered step: predictor, element force + history, corrector,
+damage right-hand side, the Jacobi-PCG loop to rel. tol 1e-8 and the clamp.
+
+`python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]`
+prints one JSON line.  Under torchrun each rank runs an independent replica
+of the plate (the method does not shard across GPUs here: "replicas only",
+weak scaling); value = all ranks' node-updates / max-over-ranks time.
+The reference arm times the FP64 CPU oracle on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import pff_synth as S  # noqa: E402
+
+METRIC = "explicit-step node-updates/s at 1M nodes; fwd+adjoint s/step; % HBM roofline"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--config", default="plate_1000x1000")
+    ap.add_argument("--prec", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--split", choices=["spectral", "amor"], default="spectral")
+    ap.add_argument("--model", choices=["AT2", "AT1"], default="AT2")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--loop", choices=["graph", "host"], default="graph",
+                    help="host: launch every kernel from the host (ncu cannot profile "
+                         "kernels inside graphs with conditional nodes)")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """Samples nvidia-smi SM clocks and throttle reasons while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"])
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return dict(sm_mhz=float(np.median(sm)) if sm else None, sm_max_mhz=smax,
+                    reasons=sorted(reasons), samples=len(sm))
+
+
+# ------------------------------------------------------------- utilities
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    lrank = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, lrank
+
+
+def algorithmic_bytes(N, Ne, prec):
+    """Bytes the method must move, by kernel (FP32_MIXED unless prec=fp64).
+    Element data: connectivity 12 B, geometry (4 independent shape
+    gradients + area) 5 words, history H 8 B (read + write in the force
+    kernel), reaction coefficient 1 word.  Node data per kernel below."""
+    w = 8 if prec == "fp64" else 4
+    geo = 5 * w
+    return {
+        # predictor: read u, v, a, write u
+        "predict": N * (8 * w),
+        # force: T, geometry, H r/w per element; u, d, v, a, 1/m, flags per node; write v, a
+        "force": Ne * (12 + geo + 16) + N * (2 * w + w + 4 * w + w + 1 + 4 * w),
+        # damage rhs: T, geometry, H per element; d_prev, flags; write x, r (f64), z, p, 1/diag, coef
+        "rhs": Ne * (12 + geo + 8 + w) + N * (w + 1 + 16 + 3 * w),
+        # CG matvec: T, geometry, coefficient per element; p (as z + beta p) read, q write
+        "matvec": Ne * (12 + geo + w) + N * (w + w + 1),
+        # CG update: x, r (f64) r/w, q, 1/diag, p read; z, p write
+        "update": N * (32 + 3 * w + 2 * w + 1),
+        # clamp: x (f64), d_prev read, d write
+        "finish": N * (8 + 2 * w + 1),
+    }
+
+
+# -------------------------------------------------------------- reference
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    c = S.config(args.config, split=args.split, model=args.model)
+    m = oracle.Mesh.from_plate(c["mesh"])
+    mat = c["material"]
+    dt = m.stable_dt(mat, c["cfl"])
+    st = m.new_state()
+    m.run(mat, st, args.warmup, dt, n0=0)
+    t0 = time.perf_counter()
+    r = m.run(mat, st, args.steps, dt, n0=args.warmup)
+    el = time.perf_counter() - t0
+    N = m.N
+    val = N * args.steps / el
+    line = dict(impl="reference", metric=METRIC, value=val, unit="node-updates/s", n_gpus=args.gpus,
+                steps=args.steps, warmup=args.warmup, ms_per_step=1e3 * el / args.steps,
+                higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
+                data="synthetic",
+                config=dict(workload=args.config, nodes=N, elements=m.Ne, split=args.split,
+                            model=args.model, precision="fp64", cg_tol=1e-8),
+                cpu_baseline=dict(value=val, unit="node-updates/s", cores=1, kind="oracle",
+                                  sample=f"full {args.config} plate, steps {args.warmup}.."
+                                         f"{args.warmup + args.steps - 1} after {args.warmup} untimed"),
+                e2e=dict(value=val, unit="node-updates/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0),
+                cg_iters_mean=float(r["iters"][:, 0].mean()))
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(args, budget_s=20.0):
+    """The oracle as it stands on one host core, on the same plate: warm-up
+    steps untimed, then as many of the bench's steps as fit the budget."""
+    import oracle
+    oracle.build()
+    c = S.config(args.config, split=args.split, model=args.model)
+    m = oracle.Mesh.from_plate(c["mesh"])
+    mat = c["material"]
+    dt = m.stable_dt(mat, c["cfl"])
+    st = m.new_state()
+    m.run(mat, st, args.warmup, dt, n0=0)
+    n, el = 0, 0.0
+    while n < args.steps and el < budget_s:
+        t0 = time.perf_counter()
+        m.run(mat, st, 1, dt, n0=args.warmup + n)
+        el += time.perf_counter() - t0
+        n += 1
+    return dict(value=m.N * n / el, unit="node-updates/s", cores=1, kind="oracle",
+                sample=f"{args.config} full plate, steps {args.warmup}..{args.warmup + n - 1} "
+                       f"({n} steps, {el:.1f} s, single thread, FP64)")
+
+
+# ------------------------------------------------------------------- ours
+
+def run_ours(args):
+    import torch
+    ws, rank, lrank = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(lrank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", lrank))
+    dev = torch.device("cuda", lrank)
+    torch.cuda.set_device(dev)
+    import paper_2606_23458_b300 as pff
+
+    c = S.config(args.config, split=args.split, model=args.model)
+    mesh = pff.Mesh.from_plate(c["mesh"], precision=args.prec)
+    dt = mesh.set_material(c["material"], c["cfl"])
+    N, Ne = mesh.N, mesh.Ne
+    opts = pff.options(cg_tol=c["cg_tol"], t_ramp=c["t_ramp"],
+                       loop_mode=pff.PFF_LOOP_HOST if args.loop == "host" else pff.PFF_LOOP_GRAPH)
+    st = mesh.new_state(device=dev)
+    total = args.warmup + args.steps
+    log = torch.zeros(total + args.e2e_steps, 2, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    # warm-up (also builds and instantiates the step graph)
+    mesh.run(st, args.warmup, step0=0, opts=opts, iters_log=log[:args.warmup])
+    torch.cuda.synchronize()
+
+    clk = ClockSampler(lrank)
+    clk.start()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    mesh.run(st, args.steps, step0=args.warmup, opts=opts, iters_log=log[args.warmup:total])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1)
+    status = mesh.sync_status()
+    iters = log[args.warmup:total, 0].cpu().numpy()
+    launches = int(4 * args.steps + 2 * iters.sum())
+
+    # end-to-end through the public API with host-resident state: every step
+    # copies the state in from pinned host memory, runs, and copies it back.
+    hs = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in st.items()}
+    for k in hs:
+        hs[k].copy_(st[k])
+    bytes_state = sum(v.numel() * v.element_size() for v in st.values())
+    torch.cuda.synchronize()
+    ee0 = torch.cuda.Event(enable_timing=True)
+    ee1 = torch.cuda.Event(enable_timing=True)
+    ee0.record(stream)
+    for n in range(args.e2e_steps):
+        for k in st:
+            st[k].copy_(hs[k], non_blocking=True)
+        mesh.run(st, 1, step0=total + n, opts=opts, iters_log=log[total + n:total + n + 1])
+        for k in st:
+            hs[k].copy_(st[k], non_blocking=True)
+    ee1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = ee0.elapsed_time(ee1)
+
+    # per-kernel device times on this data (overwrites the state)
+    prof = mesh.profile_kernels(st, reps=5, opts=opts)
+    names = list(prof.keys())
+    kms = np.array([prof[k] for k in names])
+
+    # aggregate over ranks
+    t_max = ms
+    if ws > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(t.item())
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
+    value = ws * N * args.steps / (t_max / 1e3)
+    ab = algorithmic_bytes(N, Ne, args.prec)
+    per_step = {"predict": kms[0], "force": kms[1], "rhs": kms[2], "finish": kms[5],
+                "matvec": kms[3] * iters.mean(), "update": kms[4] * iters.mean()}
+    dom = max(per_step, key=per_step.get)
+    kidx = names.index(dom)
+    peak, peak_kind = peaks()
+    achieved = ab[dom] / (kms[kidx] * 1e-3) / 1e9
+    roofline = dict(bound="hbm", kernel=dom, achieved=achieved, peak=peak, unit="GB/s",
+                    frac=achieved / peak, peak_kind=peak_kind, traffic=None,
+                    bytes_per_launch=ab[dom], ms_per_launch=kms[kidx])
+    step_bytes = sum(v for k, v in ab.items() if k not in ("matvec", "update")) + \
+        iters.mean() * (ab["matvec"] + ab["update"])
+    line = dict(
+        metric=METRIC, value=value, unit="node-updates/s", n_gpus=ws, steps=args.steps,
+        warmup=args.warmup, ms_per_step=t_max / args.steps, higher_is_better=True,
+        scaling="weak", vs_baseline=None, dtype="f32" if args.prec == "fp32" else "f64",
+        data="synthetic",
+        config=dict(workload=args.config, nodes=N, elements=Ne, split=args.split, model=args.model,
+                    precision="FP32 kernels, FP64 reductions/history" if args.prec == "fp32" else "FP64",
+                    cg_tol=c["cg_tol"], cg_tol_fp32_floor=2.0 ** -22 if args.prec == "fp32" else None,
+                    dt=dt, parallelism=f"replicas x{ws}", loop=args.loop,
+                    l2="inputs larger than L2 (working set > 126 MB), no flush"),
+        roofline=roofline,
+        step_roofline=dict(bytes=step_bytes, frac=step_bytes / (t_max / args.steps * 1e-3) / 1e9 / peak),
+        e2e=dict(value=ws * N * args.e2e_steps / (e2e_ms / 1e3), unit="node-updates/s",
+                 h2d_bytes_per_step=bytes_state, d2h_bytes_per_step=bytes_state),
+        gpu_launches=launches, clocks=clocks, status=int(status),
+        cg_iters=dict(mean=float(iters.mean()), max=int(iters.max()), min=int(iters.min())),
+        kernel_ms={k: float(v) for k, v in zip(names, kms)},
+    )
+    if not args.no_cpu_baseline and ws == 1:
+        line["cpu_baseline"] = cpu_baseline(args)
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

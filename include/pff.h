@@ -168,7 +168,18 @@ pff_status pff_sync_status(pff_mesh *mesh, pff_stream stream);
 pff_status pff_energies(pff_mesh *mesh, const pff_state *state, double *out,
                         pff_stream stream);
 
-/* Threads of the last failing call on this host thread. */
+/* Measurement helper: average device time (ms) of each kernel of the step
+ * on this mesh's data, ms_out[0..6] = predictor, force/corrector, damage
+ * right-hand side, CG matvec, CG update, clamp/finish, energies.  Every
+ * launch is preceded by a write larger than L2 and bracketed by CUDA events
+ * on `stream`; reps launches per kernel.  It OVERWRITES the state and the
+ * solve workspace (call it after the run whose numbers you need).
+ * Synchronises the stream. */
+pff_status pff_profile_kernels(pff_mesh *mesh, const pff_state *state, double dt,
+                               const pff_options *opt, int32_t reps, double *ms_out,
+                               pff_stream stream);
+
+/* Message of the last failing call on this host thread. */
 const char *pff_last_error(void);
 const char *pff_version(void);
 

@@ -76,6 +76,8 @@ _sig = {
                 C.POINTER(pff_options), _P, _P, _P],
     "pff_sync_status": [_P, _P],
     "pff_energies": [_P, C.POINTER(pff_state), _P, _P],
+    "pff_profile_kernels": [_P, C.POINTER(pff_state), C.c_double, C.POINTER(pff_options),
+                            C.c_int32, _P, _P],
 }
 for _name, _args in _sig.items():
     _f = getattr(_lib, _name)
@@ -235,6 +237,18 @@ class Mesh:
 
     def sync_status(self, stream=None):
         return _lib.pff_sync_status(self._h, _stream(stream))
+
+    KERNELS = ("predict", "force", "rhs", "matvec", "update", "finish", "energies")
+
+    def profile_kernels(self, st, reps=5, opts=None, dt=None, stream=None):
+        """Average device ms per launch of each kernel on this data (L2
+        flushed before every launch).  Overwrites the state."""
+        s = self._state(st)
+        o = opts or options()
+        out = np.zeros(len(self.KERNELS))
+        _check(_lib.pff_profile_kernels(self._h, C.byref(s), float(dt or self.dt), C.byref(o),
+                                        int(reps), _hp(out), _stream(stream)))
+        return dict(zip(self.KERNELS, out.tolist()))
 
     def energies(self, st, stream=None):
         s = self._state(st)

@@ -4,12 +4,19 @@
 // incident elements (the node-to-element incidence, ascending element id),
 // recomputing what it needs of each element.  Accumulation is therefore a
 // plain per-thread sum in a fixed order: no atomics, bit-identical reruns.
-// Per-element results that must be stored once (the history H, the damage
-// mass coefficient) are written by the element's slot-0 node ("owner").
+// Per-element results that must be stored once (the history H) are written
+// by the element's slot-0 node ("owner").
 //
-// Reductions (CG inner products, energies) are FP64: each block reduces with
-// warp shuffles, writes one partial per block, and the last block to finish
-// (ticket counter) sums the partials in block order.
+// Precision.  R = double: everything FP64 (the parity mode).  R = float
+// (FP32_MIXED): element and vector arithmetic in FP32; the history H stays
+// FP64 and its max is taken exactly; inner products and norms are
+// accumulated in double-word precision: each term is an exact FP32
+// product (TwoProd), warps sum (hi, lo) pairs with TwoSum, and warps and
+// blocks are summed in FP64.  B300 runs FP64 at ~1/57 of its FP32 rate, so
+// per-node FP64 instructions would otherwise dominate every kernel.
+//
+// Reductions: each block writes one partial per value, and the last block
+// to finish (ticket counter) sums the partials in block order.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -32,12 +39,14 @@ template <> struct V<double> {
   typedef dbl4 T4;
 };
 
-// Scalars of one damage solve, living in device memory.
+// Scalars of one damage solve, living in device memory.  Dot products are
+// of (rscale r), (rscale q) with z, p, so every ratio the solver uses is
+// unchanged by the power-of-two scale.
 struct SolveScalars {
-  double bn;      // ||b - A 1_D|| over free rows
+  double bn;      // ||b - A 1_D|| over free rows (scaled)
   double rho;     // r . z
   double alpha, beta;
-  double rr;      // ||r||^2 (free rows)
+  double rr;      // ||r||^2 (free rows, scaled)
   double pq;
   int32_t iters, restarts, status, done;
   int32_t projected, inner_done, pad0, pad1;
@@ -61,21 +70,24 @@ template <typename R> struct Params {
   R lam, mu, K, eta;
   int32_t split, model;
   R kappa;      // damage diffusion coefficient (Gc l0 or 3/4 Gc l0)
-  double cbase; // reaction: c_e = cbase + 2 H_e
-  double wbase; // load:     w_e = wbase + 2 H_e
+  R cbase;      // reaction: c_e = cbase + 2 H_e
+  R wbase;      // load:     w_e = wbase + 2 H_e
+  R rscale;     // power of two applied to residual-like vectors in the dots
   double Gc, l0;
   // state
   R2 *u, *v, *a;
   R *d;
-  double *H;
+  double *H;         // history (always FP64)
+  const R *Hr;       // history in the kernel precision (H itself, or Hf)
+  float *Hf;         // FP32 mirror of H kept by k_force (FP32 mode only)
   // time
   double dt, t_ramp, t_next; // t_next used when step_ctr == nullptr
   const int64_t *step_ctr;   // device step counter n (t_next = (n+1) dt)
   // damage solve
   const R *dprev;
   R *dout;
-  double *x, *r, *b;
-  R *z, *p, *q, *dinv, *mcoef;
+  R *x, *r, *b;
+  R *z, *p, *q, *dinv;
   uint8_t *freef;
   double *part;
   unsigned int *ticket;
@@ -93,47 +105,84 @@ template <typename R> struct Params {
   int32_t track_work;
 };
 
-// --------------------------------------------------------------- helpers
+// ------------------------------------------------------- accumulators
 
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  return v;
+// Unevaluated sum hi + lo of two floats (double-word arithmetic).
+struct DF {
+  float hi, lo;
+};
+
+// Exact product a*b = hi + lo (TwoProd with an FMA).
+__device__ __forceinline__ DF two_prod(float a, float b) {
+  const float p = a * b;
+  return DF{p, fmaf(a, b, -p)};
 }
 
-// Block-reduces NV doubles, publishes one partial per block and returns
-// true in every thread of the last block to arrive; that block then finds
-// the totals in `tot` (shared, valid after the call).  Fixed summation order.
-template <int NV>
-__device__ __forceinline__ bool reduce_last(const double (&v)[NV], double *part,
+// Double-word addition: TwoSum of the high parts, then the low parts.
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  const float s = a.hi + b.hi;
+  const float bb = s - a.hi;
+  float e = (a.hi - (s - bb)) + (b.hi - bb);
+  e += a.lo + b.lo;
+  const float hi = s + e;
+  return DF{hi, e - (hi - s)};
+}
+
+template <typename R> struct Acc;
+template <> struct Acc<double> {
+  typedef double T;
+  static __device__ __forceinline__ T zero() { return 0.0; }
+  static __device__ __forceinline__ T prod(double a, double b) { return a * b; }
+  static __device__ __forceinline__ T add(T a, T b) { return a + b; }
+  static __device__ __forceinline__ T shfl(T v, int o) { return __shfl_down_sync(0xffffffffu, v, o); }
+  static __device__ __forceinline__ double to_d(T v) { return v; }
+  static __device__ __forceinline__ T one() { return 1.0; }
+};
+template <> struct Acc<float> {
+  typedef DF T;
+  static __device__ __forceinline__ T zero() { return DF{0.f, 0.f}; }
+  static __device__ __forceinline__ T prod(float a, float b) { return two_prod(a, b); }
+  static __device__ __forceinline__ T add(T a, T b) { return df_add(a, b); }
+  static __device__ __forceinline__ T shfl(T v, int o) {
+    return DF{__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)};
+  }
+  static __device__ __forceinline__ double to_d(T v) { return (double)v.hi + (double)v.lo; }
+  static __device__ __forceinline__ T one() { return DF{1.f, 0.f}; }
+};
+
+// Block-reduces NV accumulators, publishes one FP64 partial per block and
+// returns true in every thread of the last block to arrive; that block
+// then finds the totals in `tot` (shared).  Fixed summation order.
+template <typename R, int NV>
+__device__ __forceinline__ bool reduce_last(typename Acc<R>::T (&v)[NV], double *part,
                                             unsigned int *ticket, double *tot) {
+  typedef Acc<R> A;
   __shared__ double sh[32][NV];
   __shared__ bool last;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int nw = (blockDim.x + 31) >> 5;
 #pragma unroll
   for (int k = 0; k < NV; ++k) {
-    double s = warp_sum(v[k]);
-    if (lane == 0) sh[wid][k] = s;
+    typename A::T s = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s = A::add(s, A::shfl(s, o));
+    if (lane == 0) sh[wid][k] = A::to_d(s);
   }
   __syncthreads();
-  if (wid == 0) {
-#pragma unroll
+  if (threadIdx.x == 0) {
     for (int k = 0; k < NV; ++k) {
-      double s = lane < nw ? sh[lane][k] : 0.0;
-      s = warp_sum(s);
-      if (lane == 0) part[(size_t)blockIdx.x * NV + k] = s;
+      double s = 0.0;
+      for (int w = 0; w < nw; ++w) s += sh[w][k];
+      part[(size_t)blockIdx.x * NV + k] = s;
     }
-    if (lane == 0) {
-      __threadfence();
-      unsigned int t = atomicAdd(ticket, 1u);
-      last = (t == gridDim.x - 1);
-    }
+    __threadfence();
+    const unsigned int t = atomicAdd(ticket, 1u);
+    last = (t == gridDim.x - 1);
   }
   __syncthreads();
   if (!last) return false;
   __threadfence();
-  // the last block: sum the partials in block order, strided by thread
+  // the last block sums the partials: thread j takes blocks j, j+B, ...
   double acc[NV];
 #pragma unroll
   for (int k = 0; k < NV; ++k) acc[k] = 0.0;
@@ -143,7 +192,9 @@ __device__ __forceinline__ bool reduce_last(const double (&v)[NV], double *part,
   __syncthreads();
 #pragma unroll
   for (int k = 0; k < NV; ++k) {
-    double s = warp_sum(acc[k]);
+    double s = acc[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
     if (lane == 0) sh[wid][k] = s;
   }
   __syncthreads();
@@ -172,6 +223,17 @@ __device__ __forceinline__ double ramp(double t, double tr) {
 template <typename R>
 __device__ __forceinline__ double step_time(const Params<R> &P) {
   return P.step_ctr ? (double)(*P.step_ctr + 1) * P.dt : P.t_next;
+}
+
+// IEEE-754 bit pattern of the double equal to a non-negative float (exact
+// conversion done with integer instructions; subnormal floats give 0).
+// Non-negative doubles order like their bit patterns, so the history max
+// max(H, psi+) is decided exactly without FP64 instructions.
+__device__ __forceinline__ long long f2d_bits(float f) {
+  const unsigned int b = __float_as_uint(f);
+  const unsigned int ex = (b >> 23) & 0xffu;
+  if (ex == 0u || (b >> 31)) return 0;
+  return ((long long)(ex - 127u + 1023u) << 52) | ((long long)(b & 0x7fffffu) << 29);
 }
 
 // Degraded stress and psi+ at one element (tensor strain components).
@@ -219,6 +281,11 @@ __device__ __forceinline__ void slot_grad(const R4 &G, int a, R &gx, R &gy) {
   gy = a == 0 ? G.y : (a == 1 ? G.w : -(G.y + G.w));
 }
 
+template <typename R>
+__device__ __forceinline__ bool is_fixed(const Params<R> &P, int i) {
+  return (P.flags[i] & kNotch) || (P.freef && !P.freef[i]);
+}
+
 // ------------------------------------------------------------ mechanics
 
 // Predictor, Eq. (vv_u): u += dt v + dt^2/2 a.  With track_work the
@@ -245,11 +312,13 @@ __global__ void k_predict(Params<R> P) {
   if (P.track_work) {
     double v1[1] = {w};
     __shared__ double tot[1];
-    if (reduce_last<1>(v1, P.part, P.ticket, tot) && threadIdx.x == 0) *P.wext += tot[0];
+    if (reduce_last<double, 1>(v1, P.part, P.ticket, tot) && threadIdx.x == 0) *P.wext += tot[0];
   }
 }
 
-// Internal force at u_{n+1} with d_n, history update, Eqs. (vv_a), (vv_v).
+// Internal force at u_{n+1} with d_n (gather, element contraction and
+// per-node sum, Sec. 2.3), history H = max(H, psi+) (Sec. 2.2), and the
+// acceleration and corrector, Eqs. (vv_a), (vv_v).
 template <typename R>
 __global__ void __launch_bounds__(256) k_force(Params<R> P) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -279,8 +348,17 @@ __global__ void __launch_bounds__(256) k_force(Params<R> P) {
     fx += A * (sxx * gx + sxy * gy);
     fy += A * (sxy * gx + syy * gy);
     if (a == 0) {
-      const double hp = (double)psip;
-      if (hp > P.H[e]) P.H[e] = hp;
+      if (sizeof(R) == 8) {
+        const double hp = (double)psip;
+        if (hp > P.H[e]) P.H[e] = hp;
+      } else {
+        const long long pb = f2d_bits((float)psip);
+        const long long hb = __double_as_longlong(P.H[e]);
+        if (pb > hb) {
+          P.H[e] = __longlong_as_double(pb);
+          P.Hf[e] = (float)psip;
+        }
+      }
     }
   }
   const uint8_t fl = P.flags[i];
@@ -304,75 +382,86 @@ __global__ void __launch_bounds__(256) k_force(Params<R> P) {
   P.a[i] = an;
 }
 
+// FP32 mirror of the history: Hf = (float) H.
+__global__ void k_h_mirror(const double *H, float *Hf, int n) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) Hf[e] = (float)H[e];
+}
+
 // --------------------------------------------------------------- damage
 
-// Right-hand side, Jacobi diagonal, lifted initial residual and mass
-// coefficients of the damage problem (AT2: Eq. damage_pde_at2; AT1: Eq.
-// damage_pde_at1), consistent mass M^e = A_e (1 + delta_ab)/12.
+// Element contribution to row `a` of A x for element coefficients kA =
+// kappa A_e, mA = c_e A_e / 12 (consistent mass, Sec. 2.4):
+//   kA grad(phi_a) . grad(x_e) + mA (x_a + x_0 + x_1 + x_2).
+template <typename R, typename R4>
+__device__ __forceinline__ R elem_row(const R4 &G, int a, R kA, R mA, R x0, R x1, R x2) {
+  const R dx = G.x * (x0 - x2) + G.z * (x1 - x2);
+  const R dy = G.y * (x0 - x2) + G.w * (x1 - x2);
+  R gx, gy;
+  slot_grad<R>(G, a, gx, gy);
+  const R xa = a == 0 ? x0 : (a == 1 ? x1 : x2);
+  return kA * (gx * dx + gy * dy) + mA * (xa + x0 + x1 + x2);
+}
+
+// Right-hand side, Jacobi diagonal and lifted initial residual of the
+// damage problem (AT2: Eq. damage_pde_at2; AT1: Eq. damage_pde_at1):
 //   x0 = d_prev (1 on the notch), r = b - A x0, b_eff = b - A 1_D.
 template <typename R>
 __global__ void __launch_bounds__(256) k_dmg_rhs(Params<R> P) {
   typedef typename Params<R>::R4 R4;
+  typedef Acc<R> AC;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  double vals[3] = {0.0, 0.0, 0.0};  // |b_eff|^2, |r|^2, r.z
+  typename AC::T vals[3] = {AC::zero(), AC::zero(), AC::zero()};  // |b_eff|^2, |r|^2, r.z
   if (i < P.N) {
     const bool notch = P.flags[i] & kNotch;
-    double bi = 0, dg = 0, ax = 0, a1 = 0;
-    const int k0 = P.ptr[i], k1 = P.ptr[i + 1];
-    for (int k = k0; k < k1; ++k) {
-      const int en = __ldg(&P.ent[k]);
-      const int e = en >> 2, a = en & 3;
-      const int4 t = __ldg(&P.tri[e]);
-      const R4 G = P.grad[e];
-      const double A = (double)__ldg(&P.area[e]);
-      const double h = P.H[e];
-      const double c = P.cbase + 2.0 * h, w = P.wbase + 2.0 * h;
-      if (a == 0) P.mcoef[e] = (R)(c * A / 12.0);
-      if (notch) continue;
-      const bool n0 = P.flags[t.x] & kNotch, n1 = P.flags[t.y] & kNotch, n2 = P.flags[t.z] & kNotch;
-      const double x0 = n0 ? 1.0 : (double)P.dprev[t.x];
-      const double x1 = n1 ? 1.0 : (double)P.dprev[t.y];
-      const double x2 = n2 ? 1.0 : (double)P.dprev[t.z];
-      const double o0 = n0 ? 1.0 : 0.0, o1 = n1 ? 1.0 : 0.0, o2 = n2 ? 1.0 : 0.0;
-      R gxr, gyr;
-      slot_grad<R>(G, a, gxr, gyr);
-      const double gx = gxr, gy = gyr;
-      const double G0x = G.x, G0y = G.y, G1x = G.z, G1y = G.w;
-      const double kA = (double)P.kappa * A, mA = c * A / 12.0;
-      bi += w * A / 3.0;
-      dg += kA * (gx * gx + gy * gy) + 2.0 * mA;
-      const double xa = a == 0 ? x0 : (a == 1 ? x1 : x2);
-      const double oa = a == 0 ? o0 : (a == 1 ? o1 : o2);
-      ax += kA * (gx * (G0x * (x0 - x2) + G1x * (x1 - x2)) + gy * (G0y * (x0 - x2) + G1y * (x1 - x2))) +
-            mA * (xa + x0 + x1 + x2);
-      a1 += kA * (gx * (G0x * (o0 - o2) + G1x * (o1 - o2)) + gy * (G0y * (o0 - o2) + G1y * (o1 - o2))) +
-            mA * (oa + o0 + o1 + o2);
-    }
     if (notch) {
-      P.x[i] = 1.0;
-      P.r[i] = 0.0;
+      P.x[i] = R(1);
+      P.r[i] = R(0);
       P.z[i] = R(0);
       P.p[i] = R(0);
       P.dinv[i] = R(0);
-      if (P.b) P.b[i] = 0.0;
+      if (P.b) P.b[i] = R(0);
     } else {
-      const double x0 = (double)P.dprev[i];
-      const double ri = bi - ax, be = bi - a1;
-      const double di = 1.0 / dg;
-      const R zi = (R)(ri * di);
-      P.x[i] = x0;
+      R bi = 0, dg = 0, ax = 0, a1 = 0;
+      const int k0 = P.ptr[i], k1 = P.ptr[i + 1];
+      for (int k = k0; k < k1; ++k) {
+        const int en = __ldg(&P.ent[k]);
+        const int e = en >> 2, a = en & 3;
+        const int4 t = __ldg(&P.tri[e]);
+        const R4 G = P.grad[e];
+        const R A = __ldg(&P.area[e]);
+        const R h = P.Hr[e];
+        const R c = P.cbase + R(2) * h, w = P.wbase + R(2) * h;
+        const bool n0 = P.flags[t.x] & kNotch, n1 = P.flags[t.y] & kNotch, n2 = P.flags[t.z] & kNotch;
+        const R x0 = n0 ? R(1) : P.dprev[t.x];
+        const R x1 = n1 ? R(1) : P.dprev[t.y];
+        const R x2 = n2 ? R(1) : P.dprev[t.z];
+        const R kA = P.kappa * A, mA = c * A * (R(1) / R(12));
+        R gx, gy;
+        slot_grad<R>(G, a, gx, gy);
+        bi += w * A * (R(1) / R(3));
+        dg += kA * (gx * gx + gy * gy) + R(2) * mA;
+        ax += elem_row<R>(G, a, kA, mA, x0, x1, x2);
+        if (n0 || n1 || n2)
+          a1 += elem_row<R>(G, a, kA, mA, n0 ? R(1) : R(0), n1 ? R(1) : R(0), n2 ? R(1) : R(0));
+      }
+      const R ri = bi - ax, be = bi - a1;
+      const R di = R(1) / dg;
+      const R zi = ri * di;
+      P.x[i] = P.dprev[i];
       P.r[i] = ri;
-      P.dinv[i] = (R)di;
+      P.dinv[i] = di;
       P.z[i] = zi;
       P.p[i] = R(0);
       if (P.b) P.b[i] = bi;
-      vals[0] = be * be;
-      vals[1] = ri * ri;
-      vals[2] = ri * (double)zi;
+      const R sr = P.rscale * ri, sb = P.rscale * be;
+      vals[0] = AC::prod(sb, sb);
+      vals[1] = AC::prod(sr, sr);
+      vals[2] = AC::prod(sr, zi);
     }
   }
   __shared__ double tot[3];
-  if (reduce_last<3>(vals, P.part, P.ticket, tot) && threadIdx.x == 0) {
+  if (reduce_last<R, 3>(vals, P.part, P.ticket, tot) && threadIdx.x == 0) {
     SolveScalars &S = *P.sc;
     S.bn = sqrt(tot[0]);
     S.rr = tot[1];
@@ -389,8 +478,9 @@ __global__ void __launch_bounds__(256) k_dmg_rhs(Params<R> P) {
   }
 }
 
-// Value of the next search direction at node j: p_new = z + beta p_old
-// (zero on the notch and, for AT1, outside the free set).
+// Next search direction at node j: p_new = z + beta p_old (zero on the
+// notch and, for AT1, outside the free set).  The same expression is
+// evaluated by the matvec (for neighbours) and the update (for the node).
 template <typename R>
 __device__ __forceinline__ R pnew(const Params<R> &P, int j, R beta) {
   return fma(beta, P.p[j], P.z[j]);
@@ -401,12 +491,12 @@ __device__ __forceinline__ R pnew(const Params<R> &P, int j, R beta) {
 template <typename R>
 __global__ void __launch_bounds__(256) k_cg_matvec(Params<R> P) {
   typedef typename Params<R>::R4 R4;
+  typedef Acc<R> AC;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  double vals[1] = {0.0};
+  typename AC::T vals[1] = {AC::zero()};
   const R beta = (R)P.sc->beta;
   if (i < P.N) {
-    const bool fixed = (P.flags[i] & kNotch) || (P.freef && !P.freef[i]);
-    if (!fixed) {
+    if (!is_fixed(P, i)) {
       R q = 0;
       const int k0 = P.ptr[i], k1 = P.ptr[i + 1];
       for (int k = k0; k < k1; ++k) {
@@ -414,24 +504,19 @@ __global__ void __launch_bounds__(256) k_cg_matvec(Params<R> P) {
         const int e = en >> 2, a = en & 3;
         const int4 t = __ldg(&P.tri[e]);
         const R4 G = P.grad[e];
-        const R kA = P.kappa * __ldg(&P.area[e]);
-        const R mc = P.mcoef[e];
-        const R p0 = pnew(P, t.x, beta), p1 = pnew(P, t.y, beta), p2 = pnew(P, t.z, beta);
-        const R dx = G.x * (p0 - p2) + G.z * (p1 - p2);
-        const R dy = G.y * (p0 - p2) + G.w * (p1 - p2);
-        R gx, gy;
-        slot_grad<R>(G, a, gx, gy);
-        const R pa = a == 0 ? p0 : (a == 1 ? p1 : p2);
-        q += kA * (gx * dx + gy * dy) + mc * (pa + p0 + p1 + p2);
+        const R A = __ldg(&P.area[e]);
+        const R kA = P.kappa * A;
+        const R mA = (P.cbase + R(2) * P.Hr[e]) * A * (R(1) / R(12));
+        q += elem_row<R>(G, a, kA, mA, pnew(P, t.x, beta), pnew(P, t.y, beta), pnew(P, t.z, beta));
       }
       P.q[i] = q;
-      vals[0] = (double)pnew(P, i, beta) * (double)q;
+      vals[0] = AC::prod(pnew(P, i, beta), P.rscale * q);
     } else {
       P.q[i] = R(0);
     }
   }
   __shared__ double tot[1];
-  if (reduce_last<1>(vals, P.part, P.ticket, tot) && threadIdx.x == 0) {
+  if (reduce_last<R, 1>(vals, P.part, P.ticket, tot) && threadIdx.x == 0) {
     SolveScalars &S = *P.sc;
     S.pq = tot[0];
     S.alpha = tot[0] != 0.0 ? S.rho / tot[0] : 0.0;
@@ -444,58 +529,62 @@ __global__ void __launch_bounds__(256) k_cg_matvec(Params<R> P) {
 // the box are projected and flag a restart.
 template <typename R>
 __global__ void __launch_bounds__(256) k_cg_update(Params<R> P) {
+  typedef Acc<R> AC;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  double vals[3] = {0.0, 0.0, 0.0};
+  typename AC::T vals[3] = {AC::zero(), AC::zero(), AC::zero()};
   const R beta = (R)P.sc->beta;
-  const double alpha = P.sc->alpha;
+  const R alpha = (R)P.sc->alpha;
   if (i < P.N) {
-    const bool fixed = (P.flags[i] & kNotch) || (P.freef && !P.freef[i]);
-    if (!fixed) {
+    if (!is_fixed(P, i)) {
       const R pn = pnew(P, i, beta);
-      double xi = P.x[i] + alpha * (double)pn;
-      const double ri = P.r[i] - alpha * (double)P.q[i];
+      R xi = fma(alpha, pn, P.x[i]);
+      const R ri = fma(-alpha, P.q[i], P.r[i]);
       if (P.model == kAT1) {
-        const double lo = (double)P.dprev[i];
-        if (xi < lo) { xi = lo; vals[2] = 1.0; }
-        if (xi > 1.0) { xi = 1.0; vals[2] = 1.0; }
+        const R lo = P.dprev[i];
+        if (xi < lo) { xi = lo; vals[2] = AC::one(); }
+        if (xi > R(1)) { xi = R(1); vals[2] = AC::one(); }
       }
-      const R zi = (R)(ri * (double)P.dinv[i]);
+      const R zi = ri * P.dinv[i];
       P.x[i] = xi;
       P.r[i] = ri;
       P.z[i] = zi;
       P.p[i] = pn;
-      vals[0] = ri * ri;
-      vals[1] = ri * (double)zi;
+      const R sr = P.rscale * ri;
+      vals[0] = AC::prod(sr, sr);
+      vals[1] = AC::prod(sr, zi);
     }
   }
   __shared__ double tot[3];
-  if (reduce_last<3>(vals, P.part, P.ticket, tot) && threadIdx.x == 0) {
+  if (reduce_last<R, 3>(vals, P.part, P.ticket, tot) && threadIdx.x == 0) {
     SolveScalars &S = *P.sc;
-    S.iters += 1;
-    S.rr = tot[0];
-    const double rz = tot[1];
     bool stop = false;
-    if (!(tot[0] == tot[0]) || isinf(tot[0])) {
-      S.status = kStNonfinite;
-      S.done = 1;
-      stop = true;
-    } else if (P.model == kAT1 && tot[2] > 0.0) {
-      S.projected = 1;
-      stop = true;  // restart
-    } else if (sqrt(tot[0]) <= P.tol * S.bn) {
+    if (S.pq == 0.0) {  // p = 0: nothing moved, the iterate is exact
       if (P.model == kAT2) S.done = 1;
       stop = true;
-    } else if (S.pq == 0.0) {
-      if (P.model == kAT2) S.done = 1;
-      stop = true;
+    } else {
+      S.iters += 1;
+      S.rr = tot[0];
+      if (!(tot[0] == tot[0]) || isinf(tot[0])) {
+        S.status = kStNonfinite;
+        S.done = 1;
+        stop = true;
+      } else if (P.model == kAT1 && tot[2] > 0.0) {
+        S.projected = 1;
+        stop = true;  // restart
+      } else if (sqrt(tot[0]) <= P.tol * S.bn) {
+        if (P.model == kAT2) S.done = 1;
+        stop = true;
+      }
+      if (!stop && S.iters >= P.max_it) {
+        stop = true;
+        if (P.model == kAT2) {
+          S.status = kStNotConverged;
+          S.done = 1;
+        }
+      }
+      S.beta = S.rho != 0.0 ? tot[1] / S.rho : 0.0;
+      S.rho = tot[1];
     }
-    if (!stop && S.iters >= P.max_it) {
-      S.status = kStNotConverged;
-      S.done = 1;
-      stop = true;
-    }
-    S.beta = S.rho != 0.0 ? rz / S.rho : 0.0;
-    S.rho = rz;
     S.inner_done = stop ? 1 : 0;
     if (P.use_cond) cudaGraphSetConditional(P.cond_inner, stop ? 0u : 1u);
   }
@@ -507,55 +596,50 @@ __global__ void __launch_bounds__(256) k_cg_update(Params<R> P) {
 template <typename R>
 __global__ void __launch_bounds__(256) k_at1_restart(Params<R> P) {
   typedef typename Params<R>::R4 R4;
+  typedef Acc<R> AC;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  double vals[2] = {0.0, 0.0};
+  typename AC::T vals[2] = {AC::zero(), AC::zero()};
   if (i < P.N) {
     const bool notch = P.flags[i] & kNotch;
     if (!notch) {
-      double ax = 0;
+      R ax = 0;
       const int k0 = P.ptr[i], k1 = P.ptr[i + 1];
       for (int k = k0; k < k1; ++k) {
         const int en = __ldg(&P.ent[k]);
         const int e = en >> 2, a = en & 3;
         const int4 t = __ldg(&P.tri[e]);
         const R4 G = P.grad[e];
-        const double A = (double)__ldg(&P.area[e]);
-        const double c = P.cbase + 2.0 * P.H[e];
-        const double x0 = __ldcg(&P.x[t.x]), x1 = __ldcg(&P.x[t.y]), x2 = __ldcg(&P.x[t.z]);
-        R gxr, gyr;
-        slot_grad<R>(G, a, gxr, gyr);
-        const double gx = gxr, gy = gyr;
-        const double kA = (double)P.kappa * A, mA = c * A / 12.0;
-        const double xa = a == 0 ? x0 : (a == 1 ? x1 : x2);
-        ax += kA * (gx * ((double)G.x * (x0 - x2) + (double)G.z * (x1 - x2)) +
-                    gy * ((double)G.y * (x0 - x2) + (double)G.w * (x1 - x2))) +
-              mA * (xa + x0 + x1 + x2);
+        const R A = __ldg(&P.area[e]);
+        const R kA = P.kappa * A;
+        const R mA = (P.cbase + R(2) * P.Hr[e]) * A * (R(1) / R(12));
+        ax += elem_row<R>(G, a, kA, mA, __ldcg(&P.x[t.x]), __ldcg(&P.x[t.y]), __ldcg(&P.x[t.z]));
       }
-      const double xi = P.x[i], ri = P.b[i] - ax, lo = (double)P.dprev[i];
-      const bool act = (xi <= lo && ri <= 0.0) || (xi >= 1.0 && ri >= 0.0);
+      const R xi = P.x[i], ri = P.b[i] - ax, lo = P.dprev[i];
+      const bool act = (xi <= lo && ri <= R(0)) || (xi >= R(1) && ri >= R(0));
       P.r[i] = ri;
       P.freef[i] = act ? 0 : 1;
       P.p[i] = R(0);
       if (act) {
         P.z[i] = R(0);
       } else {
-        const R zi = (R)(ri * (double)P.dinv[i]);
+        const R zi = ri * P.dinv[i];
         P.z[i] = zi;
-        vals[0] = ri * ri;
-        vals[1] = ri * (double)zi;
+        const R sr = P.rscale * ri;
+        vals[0] = AC::prod(sr, sr);
+        vals[1] = AC::prod(sr, zi);
       }
     } else {
       P.freef[i] = 0;
     }
   }
   __shared__ double tot[2];
-  if (reduce_last<2>(vals, P.part, P.ticket, tot) && threadIdx.x == 0) {
+  if (reduce_last<R, 2>(vals, P.part, P.ticket, tot) && threadIdx.x == 0) {
     SolveScalars &S = *P.sc;
     S.rr = tot[0];
     S.rho = tot[1];
     S.beta = 0.0;
     S.projected = 0;
-    bool conv = sqrt(tot[0]) <= P.tol * S.bn;
+    const bool conv = sqrt(tot[0]) <= P.tol * S.bn;
     bool stop = conv;
     if (!conv && (S.restarts >= P.max_restarts || S.iters >= P.max_it)) {
       S.status = kStNotConverged;
@@ -582,18 +666,18 @@ template <typename R>
 __global__ void k_dmg_finish(Params<R> P) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < P.N) {
-    double v;
+    R v;
     if (P.flags[i] & kNotch) {
-      v = 1.0;
+      v = R(1);
     } else {
       v = P.x[i];
       if (P.model == kAT2) {
-        const double lo = (double)P.dprev[i];
+        const R lo = P.dprev[i];
         v = v > lo ? v : lo;
-        v = v < 1.0 ? v : 1.0;
+        v = v < R(1) ? v : R(1);
       }
     }
-    P.dout[i] = (R)v;
+    P.dout[i] = v;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     const SolveScalars &S = *P.sc;
@@ -610,7 +694,7 @@ __global__ void k_dmg_finish(Params<R> P) {
 // ------------------------------------------------------------- energies
 
 // E_el = sum A_e (g psi+ + psi-), E_frac per model, E_kin = 1/2 sum m v^2.
-// Element terms are counted by the owner node (slot 0).
+// Element terms are counted by the owner node (slot 0).  FP64 (diagnostic).
 template <typename R>
 __global__ void __launch_bounds__(256) k_energies(Params<R> P) {
   typedef typename Params<R>::R2 R2;
@@ -636,8 +720,7 @@ __global__ void __launch_bounds__(256) k_energies(Params<R> P) {
       const double d0 = P.d[t.x], d1 = P.d[t.y], d2 = P.d[t.z];
       const double db = (d0 + d1 + d2) / 3.0;
       const double g = (1.0 - db) * (1.0 - db) + (double)P.eta;
-      // psi = g psi+ + psi-: evaluate the split at g and at g = 0 via the
-      // stress; psi- = psi_full - psi+ for all three splits.
+      // psi- = psi_full - psi+ for every split (psi_full = lambda/2 tr^2 + mu e:e)
       R sxx, syy, sxy, psip;
       stress(P, exx, eyy, exy, R(1), sxx, syy, sxy, psip);
       const double tr = (double)exx + eyy;
@@ -658,7 +741,7 @@ __global__ void __launch_bounds__(256) k_energies(Params<R> P) {
     }
   }
   __shared__ double tot[3];
-  if (reduce_last<3>(vals, P.part, P.ticket, tot) && threadIdx.x == 0) {
+  if (reduce_last<double, 3>(vals, P.part, P.ticket, tot) && threadIdx.x == 0) {
     P.energy_out[0] = tot[0];
     P.energy_out[1] = tot[1];
     P.energy_out[2] = tot[2];
