@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--model", choices=["AT2", "AT1"], default="AT2")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--variant", type=int, default=0,
+                    help="gather schedule (0 = autotuned; 1..5 fixed, see pff_options.variant)")
     ap.add_argument("--loop", choices=["graph", "host"], default="graph",
                     help="host: launch every kernel from the host (ncu cannot profile "
                          "kernels inside graphs with conditional nodes)")
@@ -221,7 +223,8 @@ def run_ours(args):
     dt = mesh.set_material(c["material"], c["cfl"])
     N, Ne = mesh.N, mesh.Ne
     opts = pff.options(cg_tol=c["cg_tol"], t_ramp=c["t_ramp"],
-                       loop_mode=pff.PFF_LOOP_HOST if args.loop == "host" else pff.PFF_LOOP_GRAPH)
+                       loop_mode=pff.PFF_LOOP_HOST if args.loop == "host" else pff.PFF_LOOP_GRAPH,
+                       variant=args.variant)
     st = mesh.new_state(device=dev)
     total = args.warmup + args.steps
     log = torch.zeros(total + args.e2e_steps, 2, dtype=torch.int32, device=dev)
@@ -271,6 +274,7 @@ def run_ours(args):
     e2e_ms = ee0.elapsed_time(ee1)
 
     # per-kernel device times on this data (overwrites the state)
+    sched_var, sched_ms = mesh.schedule()
     prof = mesh.profile_kernels(st, reps=5, opts=opts)
     names = list(prof.keys())
     kms = np.array([prof[k] for k in names])
@@ -315,6 +319,7 @@ def run_ours(args):
         gpu_launches=launches, clocks=clocks, status=int(status),
         cg_iters=dict(mean=float(iters.mean()), max=int(iters.max()), min=int(iters.min())),
         kernel_ms={k: float(v) for k, v in zip(names, kms)},
+        schedule=dict(variant=sched_var, tune_ms=sched_ms),
     )
     if not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline(args)

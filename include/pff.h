@@ -79,6 +79,11 @@ typedef struct {
   int32_t block;        /* threads per block, 0 = autotuned [0] */
   int32_t loop_mode;    /* PFF_LOOP_GRAPH (device-side CG loop in a CUDA
                            graph) or PFF_LOOP_HOST (host polls) [graph] */
+  int32_t variant;      /* gather schedule of the force / damage kernels:
+                           0 = autotuned on first use [0]; 1 = entry-parallel
+                           node blocks; 2..5 = node-centric with 1..4 gathers
+                           in flight.  All give bit-identical results. */
+  int32_t reserved;
 } pff_options;
 
 /* Device state of one plate (caller-owned). */
@@ -178,6 +183,11 @@ pff_status pff_energies(pff_mesh *mesh, const pff_state *state, double *out,
 pff_status pff_profile_kernels(pff_mesh *mesh, const pff_state *state, double dt,
                                const pff_options *opt, int32_t reps, double *ms_out,
                                pff_stream stream);
+
+/* Gather schedules in use for (force, damage right-hand side, CG matvec)
+ * as pff_options.variant codes (1..5), and the autotuner's timings in ms
+ * (3 x 5, 0 where not measured).  Host outputs, each nullable. */
+pff_status pff_mesh_schedule(const pff_mesh *mesh, int32_t *variant, float *tune_ms);
 
 /* Message of the last failing call on this host thread. */
 const char *pff_last_error(void);

@@ -50,7 +50,8 @@ class pff_options(C.Structure):
     _fields_ = [("cg_tol", C.c_double), ("cg_max_it", C.c_int32),
                 ("max_restarts", C.c_int32), ("t_ramp", C.c_double),
                 ("energy_every", C.c_int32), ("ckpt_every", C.c_int32),
-                ("block", C.c_int32), ("loop_mode", C.c_int32)]
+                ("block", C.c_int32), ("loop_mode", C.c_int32), ("variant", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class pff_state(C.Structure):
@@ -78,6 +79,7 @@ _sig = {
     "pff_energies": [_P, C.POINTER(pff_state), _P, _P],
     "pff_profile_kernels": [_P, C.POINTER(pff_state), C.c_double, C.POINTER(pff_options),
                             C.c_int32, _P, _P],
+    "pff_mesh_schedule": [_P, _P, _P],
 }
 for _name, _args in _sig.items():
     _f = getattr(_lib, _name)
@@ -112,9 +114,9 @@ def _stream(stream=None):
 
 
 def options(cg_tol=1e-8, cg_max_it=10000, max_restarts=50, t_ramp=0.05e-6, energy_every=0,
-            ckpt_every=25, block=0, loop_mode=PFF_LOOP_GRAPH):
+            ckpt_every=25, block=0, loop_mode=PFF_LOOP_GRAPH, variant=0):
     return pff_options(cg_tol, cg_max_it, max_restarts, t_ramp, energy_every, ckpt_every,
-                       block, loop_mode)
+                       block, loop_mode, variant, 0)
 
 
 def material(mat):
@@ -237,6 +239,15 @@ class Mesh:
 
     def sync_status(self, stream=None):
         return _lib.pff_sync_status(self._h, _stream(stream))
+
+    def schedule(self):
+        """(variant codes for force, rhs, matvec; autotuner ms per variant)."""
+        var = np.zeros(3, np.int32)
+        ms = np.zeros((3, 5), np.float32)
+        _check(_lib.pff_mesh_schedule(self._h, _hp(var), _hp(ms)))
+        names = ("force", "rhs", "matvec")
+        return ({n: int(v) for n, v in zip(names, var)},
+                {n: [round(float(x), 4) for x in row] for n, row in zip(names, ms)})
 
     KERNELS = ("predict", "force", "rhs", "matvec", "update", "finish", "energies")
 

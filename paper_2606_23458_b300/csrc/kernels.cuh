@@ -1,11 +1,17 @@
 // kernels.cuh -- device code of the phase-field fracture step for sm_103a.
 //
-// Every node-indexed kernel runs one thread per node and walks that node's
-// incident elements (the node-to-element incidence, ascending element id),
-// recomputing what it needs of each element.  Accumulation is therefore a
-// plain per-thread sum in a fixed order: no atomics, bit-identical reruns.
-// Per-element results that must be stored once (the history H) are written
-// by the element's slot-0 node ("owner").
+// Force and damage-operator accumulation is a gather: every node sums the
+// contributions of its incident elements (the node-to-element incidence,
+// ascending element id), recomputing what it needs of each element from a
+// packed 32-byte element record.  Accumulation is therefore a plain sum in a
+// fixed order: no atomics, bit-identical reruns, and every schedule variant
+// (entry-parallel node blocks or node-centric with U gathers in flight)
+// adds the same terms in the same order.  Per-element results that must be
+// stored once (the history H) are written by the element's slot-0 entry.
+//
+// The node-centric schedules read the incidence in ELL layout
+// (entry j of node i at ell[j N + i], padded with -1), so that a warp's
+// loads of one slot are coalesced.
 //
 // Precision.  R = double: everything FP64 (the parity mode).  R = float
 // (FP32_MIXED): element and vector arithmetic in FP32; the history H stays
@@ -39,6 +45,21 @@ template <> struct V<double> {
   typedef dbl4 T4;
 };
 
+// Packed element record: the three node ids, the area and the independent
+// shape gradients (dphi0/dx, dphi0/dy, dphi1/dx, dphi1/dy) of Eq. (grad_phi);
+// dphi2 = -(dphi0 + dphi1).  32 bytes (one sector) in FP32, 64 in FP64.
+template <typename R> struct ERec;
+template <> struct __align__(32) ERec<float> {
+  int n0, n1, n2;
+  float A;
+  float4 g;
+};
+template <> struct __align__(64) ERec<double> {
+  int n0, n1, n2, pad;
+  double A, pad2;
+  dbl4 g;
+};
+
 // Scalars of one damage solve, living in device memory.  Dot products are
 // of (rscale r), (rscale q) with z, p, so every ratio the solver uses is
 // unchanged by the power-of-two scale.
@@ -57,12 +78,13 @@ template <typename R> struct Params {
   typedef typename V<R>::T2 R2;
   typedef typename V<R>::T4 R4;
   int32_t N, Ne;
+  int32_t NB, nblk;  // nodes per node block, number of node blocks
+  int32_t D;         // ELL width (maximum incidence degree)
   // mesh
   const int32_t *__restrict__ ptr;
   const int32_t *__restrict__ ent;
-  const int4 *__restrict__ tri;
-  const R4 *__restrict__ grad;   // (dphi0/dx, dphi0/dy, dphi1/dx, dphi1/dy)
-  const R *__restrict__ area;
+  const int32_t *__restrict__ ell;
+  const ERec<R> *__restrict__ rec;
   const uint8_t *__restrict__ flags;
   const R2 *__restrict__ fext;
   const R *__restrict__ minv;
@@ -87,7 +109,8 @@ template <typename R> struct Params {
   const R *dprev;
   R *dout;
   R *x, *r, *b;
-  R *z, *p, *q, *dinv;
+  R2 *pz;      // (p, z) interleaved: search direction and preconditioned residual
+  R *q, *dinv;
   uint8_t *freef;
   double *part;
   unsigned int *ticket;
@@ -182,13 +205,23 @@ __device__ __forceinline__ bool reduce_last(typename Acc<R>::T (&v)[NV], double 
   __syncthreads();
   if (!last) return false;
   __threadfence();
-  // the last block sums the partials: thread j takes blocks j, j+B, ...
+  // the last block sums the partials: thread j takes blocks j, j+B, ...;
+  // eight loads are issued before they are added (one L2 round trip each)
   double acc[NV];
 #pragma unroll
-  for (int k = 0; k < NV; ++k) acc[k] = 0.0;
-  for (int j = threadIdx.x; j < (int)gridDim.x; j += blockDim.x)
+  for (int k = 0; k < NV; ++k) {
+    acc[k] = 0.0;
+    for (int j0 = threadIdx.x; j0 < (int)gridDim.x; j0 += 8 * blockDim.x) {
+      double buf[8];
 #pragma unroll
-    for (int k = 0; k < NV; ++k) acc[k] += __ldcg(&part[(size_t)j * NV + k]);
+      for (int u = 0; u < 8; ++u) {
+        const int j = j0 + u * blockDim.x;
+        buf[u] = j < (int)gridDim.x ? __ldcg(&part[(size_t)j * NV + k]) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) acc[k] += buf[u];
+    }
+  }
   __syncthreads();
 #pragma unroll
   for (int k = 0; k < NV; ++k) {
@@ -212,6 +245,11 @@ __device__ __forceinline__ bool reduce_last(typename Acc<R>::T (&v)[NV], double 
 
 template <typename R> __device__ __forceinline__ R rpos(R x) { return x > R(0) ? x : R(0); }
 template <typename R> __device__ __forceinline__ R rneg(R x) { return x < R(0) ? x : R(0); }
+
+// Accumulation a + b that the compiler may not contract into an FMA with
+// the producer of b: every schedule then rounds the same sums the same way.
+__device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double radd(double a, double b) { return __dadd_rn(a, b); }
 
 // Smooth traction ramp, Eq. (smooth_traction_ramp).
 __device__ __forceinline__ double ramp(double t, double tr) {
@@ -287,15 +325,67 @@ __device__ __forceinline__ bool is_fixed(const Params<R> &P, int i) {
 }
 
 // ------------------------------------------------------------ mechanics
+//
+// Node-block kernels: block b owns nodes [b NB, (b+1) NB) and walks all
+// their incidence entries [ptr[i0], ptr[i1]) with one thread per entry
+// (independent gathers, high memory-level parallelism); each entry's
+// contribution is staged in shared memory, then one thread per node sums
+// its own entries in ascending element order.
+
+template <typename R>
+__device__ __forceinline__ void block_nodes(const Params<R> &P, int b, int &i0, int &i1, int &k0, int &k1) {
+  i0 = b * P.NB;
+  i1 = min(i0 + P.NB, P.N);
+  k0 = __ldg(&P.ptr[i0]);
+  k1 = __ldg(&P.ptr[i1]);
+}
+
+// Loads element e's record: node ids, area and shape gradients.  The FP32
+// record is one 32-byte sector, read with a single 256-bit load.
+template <typename R>
+__device__ __forceinline__ void load_elem(const Params<R> &P, int e, int4 &t, R &A,
+                                          typename Params<R>::R4 &G) {
+  const ERec<R> *rp = P.rec + e;
+  if (sizeof(R) == 4) {
+    unsigned w0, w1, w2, w3, w4, w5, w6, w7;
+    asm("ld.global.nc.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=r"(w0), "=r"(w1), "=r"(w2), "=r"(w3), "=r"(w4), "=r"(w5), "=r"(w6), "=r"(w7)
+        : "l"(rp));
+    t = make_int4((int)w0, (int)w1, (int)w2, 0);
+    A = (R)__uint_as_float(w3);
+    G.x = (R)__uint_as_float(w4);
+    G.y = (R)__uint_as_float(w5);
+    G.z = (R)__uint_as_float(w6);
+    G.w = (R)__uint_as_float(w7);
+  } else {
+    t = __ldg(reinterpret_cast<const int4 *>(rp));
+    const double2 a = __ldg(reinterpret_cast<const double2 *>(rp) + 1);
+    const double2 g0 = __ldg(reinterpret_cast<const double2 *>(rp) + 2);
+    const double2 g1 = __ldg(reinterpret_cast<const double2 *>(rp) + 3);
+    A = (R)a.x;
+    G.x = (R)g0.x; G.y = (R)g0.y; G.z = (R)g1.x; G.w = (R)g1.y;
+  }
+}
+
+// Strain (tensor components) of element e from nodal u.
+template <typename R>
+__device__ __forceinline__ void elem_strain(const Params<R> &P, const typename Params<R>::R4 &G, const int4 &t,
+                                            R &exx, R &eyy, R &exy) {
+  typedef typename Params<R>::R2 R2;
+  const R2 u0 = P.u[t.x], u1 = P.u[t.y], u2 = P.u[t.z];
+  const R ax0 = u0.x - u2.x, ax1 = u1.x - u2.x, ay0 = u0.y - u2.y, ay1 = u1.y - u2.y;
+  exx = G.x * ax0 + G.z * ax1;
+  eyy = G.y * ay0 + G.w * ay1;
+  exy = R(0.5) * (G.y * ax0 + G.w * ax1 + G.x * ay0 + G.z * ay1);
+}
 
 // Predictor, Eq. (vv_u): u += dt v + dt^2/2 a.  With track_work the
 // trapezoid-rule external work increment 1/2 (S_n + S_n+1) f_ext . du is
 // reduced into *wext.
 template <typename R>
-__global__ void k_predict(Params<R> P) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(256) k_predict(Params<R> P) {
   double w = 0.0;
-  if (i < P.N) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.N; i += gridDim.x * blockDim.x) {
     typename Params<R>::R2 u = P.u[i], v = P.v[i], a = P.a[i];
     const R dt = (R)P.dt, h = R(0.5) * dt * dt;
     const R dux = dt * v.x + h * a.x, duy = dt * v.y + h * a.y;
@@ -303,7 +393,7 @@ __global__ void k_predict(Params<R> P) {
       const double t1 = step_time(P), t0 = t1 - P.dt;
       const double S = 0.5 * (ramp(t0, P.t_ramp) + ramp(t1, P.t_ramp));
       typename Params<R>::R2 f = P.fext[i];
-      w = S * ((double)f.x * dux + (double)f.y * duy);
+      w += S * ((double)f.x * dux + (double)f.y * duy);
     }
     u.x += dux;
     u.y += duy;
@@ -316,61 +406,63 @@ __global__ void k_predict(Params<R> P) {
   }
 }
 
-// Internal force at u_{n+1} with d_n (gather, element contraction and
-// per-node sum, Sec. 2.3), history H = max(H, psi+) (Sec. 2.2), and the
-// acceleration and corrector, Eqs. (vv_a), (vv_v).
+// Force contribution of one incidence entry (element e at local slot a):
+// f_a = A_e sigma_e . grad(phi_a) with sigma = g(dbar) sigma+ + sigma-
+// (Sec. 2.3 gather and element contraction); also returns psi+_e.
 template <typename R>
-__global__ void __launch_bounds__(256) k_force(Params<R> P) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= P.N) return;
-  typedef typename Params<R>::R2 R2;
+__device__ __forceinline__ void force_entry(const Params<R> &P, int en, R &fx, R &fy, R &psip) {
   typedef typename Params<R>::R4 R4;
-  R fx = 0, fy = 0;
-  const int k0 = P.ptr[i], k1 = P.ptr[i + 1];
-  for (int k = k0; k < k1; ++k) {
-    const int en = __ldg(&P.ent[k]);
-    const int e = en >> 2, a = en & 3;
-    const int4 t = __ldg(&P.tri[e]);
-    const R4 G = P.grad[e];
-    const R A = __ldg(&P.area[e]);
-    const R2 u0 = P.u[t.x], u1 = P.u[t.y], u2 = P.u[t.z];
-    const R d0 = P.d[t.x], d1 = P.d[t.y], d2 = P.d[t.z];
-    const R ax0 = u0.x - u2.x, ax1 = u1.x - u2.x, ay0 = u0.y - u2.y, ay1 = u1.y - u2.y;
-    const R exx = G.x * ax0 + G.z * ax1;
-    const R eyy = G.y * ay0 + G.w * ay1;
-    const R exy = R(0.5) * (G.y * ax0 + G.w * ax1 + G.x * ay0 + G.z * ay1);
-    const R db = (d0 + d1 + d2) * (R(1) / R(3));
-    const R g = (R(1) - db) * (R(1) - db) + P.eta;
-    R sxx, syy, sxy, psip;
-    stress(P, exx, eyy, exy, g, sxx, syy, sxy, psip);
-    R gx, gy;
-    slot_grad<R>(G, a, gx, gy);
-    fx += A * (sxx * gx + sxy * gy);
-    fy += A * (sxy * gx + syy * gy);
-    if (a == 0) {
-      if (sizeof(R) == 8) {
-        const double hp = (double)psip;
-        if (hp > P.H[e]) P.H[e] = hp;
-      } else {
-        const long long pb = f2d_bits((float)psip);
-        const long long hb = __double_as_longlong(P.H[e]);
-        if (pb > hb) {
-          P.H[e] = __longlong_as_double(pb);
-          P.Hf[e] = (float)psip;
-        }
-      }
+  const int e = en >> 2, a = en & 3;
+  int4 t;
+  R A;
+  R4 G;
+  load_elem(P, e, t, A, G);
+  R exx, eyy, exy;
+  elem_strain(P, G, t, exx, eyy, exy);
+  const R db = (P.d[t.x] + P.d[t.y] + P.d[t.z]) * (R(1) / R(3));
+  const R g = (R(1) - db) * (R(1) - db) + P.eta;
+  R sxx, syy, sxy;
+  stress(P, exx, eyy, exy, g, sxx, syy, sxy, psip);
+  R gx, gy;
+  slot_grad<R>(G, a, gx, gy);
+  fx = A * (sxx * gx + sxy * gy);
+  fy = A * (sxy * gx + syy * gy);
+}
+
+// History update H_e = max(H_e, psi+_e) by the element's owner entry
+// (slot 0), Sec. 2.2.  FP32 mode decides the FP64 max on bit patterns
+// (exact) and keeps the FP32 mirror equal to (float) H.
+template <typename R>
+__device__ __forceinline__ void history_update(const Params<R> &P, int en, R psip) {
+  if (en & 3) return;
+  const int e = en >> 2;
+  if (sizeof(R) == 8) {
+    const double hp = (double)psip;
+    if (hp > P.H[e]) P.H[e] = hp;
+  } else {
+    const long long pb = f2d_bits((float)psip);
+    const long long hb = __double_as_longlong(P.H[e]);
+    if (pb > hb) {
+      P.H[e] = __longlong_as_double(pb);
+      P.Hf[e] = (float)psip;
     }
   }
-  const uint8_t fl = P.flags[i];
-  R S = 0, fex = 0, fey = 0;
-  if (fl & kLoaded) {
-    S = (R)ramp(step_time(P), P.t_ramp);
+}
+
+// Acceleration and corrector at node i from its summed internal force,
+// Eqs. (vv_a), (vv_v).
+template <typename R>
+__device__ __forceinline__ void corrector(const Params<R> &P, int i, R fx, R fy, double S) {
+  typedef typename Params<R>::R2 R2;
+  R Sf = 0, fex = 0, fey = 0;
+  if (P.flags[i] & kLoaded) {
+    Sf = (R)S;
     const R2 fe = P.fext[i];
     fex = fe.x;
     fey = fe.y;
   }
   const R mi = P.minv[i];
-  const R anx = mi * (S * fex - fx), any = mi * (S * fey - fy);
+  const R anx = mi * (Sf * fex - fx), any = mi * (Sf * fey - fy);
   R2 v = P.v[i], ao = P.a[i];
   const R hd = R(0.5) * (R)P.dt;
   v.x += hd * (ao.x + anx);
@@ -382,10 +474,73 @@ __global__ void __launch_bounds__(256) k_force(Params<R> P) {
   P.a[i] = an;
 }
 
+// Internal force at u_{n+1} with d_n, history, acceleration and corrector.
+// Entry-parallel schedule (node blocks, contributions staged in shared
+// memory, per-node sums in ascending element order).
+template <typename R>
+__global__ void __launch_bounds__(256) k_force_ep(Params<R> P) {
+  typedef typename Params<R>::R2 R2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R2 *fc = reinterpret_cast<R2 *>(smem_raw);
+  const double S = ramp(step_time(P), P.t_ramp);
+  for (int b = blockIdx.x; b < P.nblk; b += gridDim.x) {
+    int i0, i1, k0, k1;
+    block_nodes(P, b, i0, i1, k0, k1);
+    for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+      const int en = __ldg(&P.ent[k]);
+      R2 f;
+      R psip;
+      force_entry(P, en, f.x, f.y, psip);
+      fc[k - k0] = f;
+      history_update(P, en, psip);
+    }
+    __syncthreads();
+    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+      const int j0 = __ldg(&P.ptr[i]) - k0, j1 = __ldg(&P.ptr[i + 1]) - k0;
+      R fx = 0, fy = 0;
+      for (int j = j0; j < j1; ++j) {
+        const R2 f = fc[j];
+        fx = radd(fx, f.x);
+        fy = radd(fy, f.y);
+      }
+      corrector(P, i, fx, fy, S);
+    }
+    __syncthreads();
+  }
+}
+
+// Same computation, node-centric schedule: one thread per node walks its
+// entries U at a time with all U gathers issued before use (independent
+// load chains); sums in the same ascending order, so the result is
+// bit-identical to the entry-parallel schedule.
+template <typename R, int U>
+__global__ void __launch_bounds__(256) k_force_nc(Params<R> P) {
+  const double S = ramp(step_time(P), P.t_ramp);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.N; i += gridDim.x * blockDim.x) {
+    R fx = 0, fy = 0;
+    for (int k = 0; k < P.D; k += U) {
+      int en[U];
+      R cx[U], cy[U], pp[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) en[u] = k + u < P.D ? __ldg(&P.ell[(size_t)(k + u) * P.N + i]) : -1;
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (en[u] >= 0) force_entry(P, en[u], cx[u], cy[u], pp[u]);
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (en[u] >= 0) {
+          fx = radd(fx, cx[u]);
+          fy = radd(fy, cy[u]);
+          history_update(P, en[u], pp[u]);
+        }
+    }
+    corrector(P, i, fx, fy, S);
+  }
+}
+
 // FP32 mirror of the history: Hf = (float) H.
 __global__ void k_h_mirror(const double *H, float *Hf, int n) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e < n) Hf[e] = (float)H[e];
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) Hf[e] = (float)H[e];
 }
 
 // --------------------------------------------------------------- damage
@@ -404,78 +559,155 @@ __device__ __forceinline__ R elem_row(const R4 &G, int a, R kA, R mA, R x0, R x1
 }
 
 // Right-hand side, Jacobi diagonal and lifted initial residual of the
-// damage problem (AT2: Eq. damage_pde_at2; AT1: Eq. damage_pde_at1):
-//   x0 = d_prev (1 on the notch), r = b - A x0, b_eff = b - A 1_D.
+// damage problem (AT2: Eq. damage_pde_at2; AT1: Eq. damage_pde_at1), one
+// incidence entry's share: (b, diag, (A x0)_a, (A 1_D)_a) with
+// x0 = d_prev (1 on the notch).
 template <typename R>
-__global__ void __launch_bounds__(256) k_dmg_rhs(Params<R> P) {
+__device__ __forceinline__ typename Params<R>::R4 rhs_entry(const Params<R> &P, int en) {
+  typedef typename Params<R>::R4 R4;
+  const int e = en >> 2, a = en & 3;
+  int4 t;
+  R A;
+  R4 G;
+  load_elem(P, e, t, A, G);
+  const R h = P.Hr[e];
+  const R c = P.cbase + R(2) * h, w = P.wbase + R(2) * h;
+  const bool n0 = P.flags[t.x] & kNotch, n1 = P.flags[t.y] & kNotch, n2 = P.flags[t.z] & kNotch;
+  const R x0 = n0 ? R(1) : P.dprev[t.x];
+  const R x1 = n1 ? R(1) : P.dprev[t.y];
+  const R x2 = n2 ? R(1) : P.dprev[t.z];
+  const R kA = P.kappa * A, mA = c * A * (R(1) / R(12));
+  R gx, gy;
+  slot_grad<R>(G, a, gx, gy);
+  R4 o;
+  o.x = w * A * (R(1) / R(3));
+  o.y = kA * (gx * gx + gy * gy) + R(2) * mA;
+  o.z = elem_row<R>(G, a, kA, mA, x0, x1, x2);
+  o.w = (n0 || n1 || n2) ? elem_row<R>(G, a, kA, mA, n0 ? R(1) : R(0), n1 ? R(1) : R(0), n2 ? R(1) : R(0))
+                         : R(0);
+  return o;
+}
+
+// Node i of the right-hand side: r = b - A x0, b_eff = b - A 1_D, the
+// Jacobi inverse diagonal and z = r / diag; accumulates |b_eff|^2, |r|^2
+// and r.z.
+template <typename R>
+__device__ __forceinline__ void rhs_node(const Params<R> &P, int i, R bi, R dg, R ax, R a1,
+                                         typename Acc<R>::T (&vals)[3]) {
+  typedef Acc<R> AC;
+  const R ri = bi - ax, be = bi - a1;
+  const R di = R(1) / dg;
+  const R zi = ri * di;
+  P.x[i] = P.dprev[i];
+  P.r[i] = ri;
+  P.dinv[i] = di;
+  typename Params<R>::R2 pz;
+  pz.x = R(0);
+  pz.y = zi;
+  P.pz[i] = pz;
+  if (P.b) P.b[i] = bi;
+  const R sr = P.rscale * ri, sb = P.rscale * be;
+  vals[0] = AC::add(vals[0], AC::prod(sb, sb));
+  vals[1] = AC::add(vals[1], AC::prod(sr, sr));
+  vals[2] = AC::add(vals[2], AC::prod(sr, zi));
+}
+
+template <typename R>
+__device__ __forceinline__ void rhs_notch_node(const Params<R> &P, int i) {
+  P.x[i] = R(1);
+  P.r[i] = R(0);
+  typename Params<R>::R2 pz;
+  pz.x = R(0);
+  pz.y = R(0);
+  P.pz[i] = pz;
+  P.dinv[i] = R(0);
+  if (P.b) P.b[i] = R(0);
+}
+
+// Last block of the right-hand side: solve scalars and the loop condition.
+template <typename R>
+__device__ __forceinline__ void rhs_finish(const Params<R> &P, const double *tot) {
+  SolveScalars &S = *P.sc;
+  S.bn = sqrt(tot[0]);
+  S.rr = tot[1];
+  S.rho = tot[2];
+  S.beta = 0.0;
+  S.alpha = 0.0;
+  S.iters = 0;
+  S.restarts = 0;
+  S.status = kStOk;
+  S.projected = 0;
+  const bool done = (P.model == kAT2) && (S.bn == 0.0 || sqrt(S.rr) <= P.tol * S.bn);
+  S.done = done ? 1 : 0;
+  if (P.use_cond) cudaGraphSetConditional(P.cond_inner, done ? 0u : 1u);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_dmg_rhs_ep(Params<R> P) {
   typedef typename Params<R>::R4 R4;
   typedef Acc<R> AC;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  typename AC::T vals[3] = {AC::zero(), AC::zero(), AC::zero()};  // |b_eff|^2, |r|^2, r.z
-  if (i < P.N) {
-    const bool notch = P.flags[i] & kNotch;
-    if (notch) {
-      P.x[i] = R(1);
-      P.r[i] = R(0);
-      P.z[i] = R(0);
-      P.p[i] = R(0);
-      P.dinv[i] = R(0);
-      if (P.b) P.b[i] = R(0);
-    } else {
-      R bi = 0, dg = 0, ax = 0, a1 = 0;
-      const int k0 = P.ptr[i], k1 = P.ptr[i + 1];
-      for (int k = k0; k < k1; ++k) {
-        const int en = __ldg(&P.ent[k]);
-        const int e = en >> 2, a = en & 3;
-        const int4 t = __ldg(&P.tri[e]);
-        const R4 G = P.grad[e];
-        const R A = __ldg(&P.area[e]);
-        const R h = P.Hr[e];
-        const R c = P.cbase + R(2) * h, w = P.wbase + R(2) * h;
-        const bool n0 = P.flags[t.x] & kNotch, n1 = P.flags[t.y] & kNotch, n2 = P.flags[t.z] & kNotch;
-        const R x0 = n0 ? R(1) : P.dprev[t.x];
-        const R x1 = n1 ? R(1) : P.dprev[t.y];
-        const R x2 = n2 ? R(1) : P.dprev[t.z];
-        const R kA = P.kappa * A, mA = c * A * (R(1) / R(12));
-        R gx, gy;
-        slot_grad<R>(G, a, gx, gy);
-        bi += w * A * (R(1) / R(3));
-        dg += kA * (gx * gx + gy * gy) + R(2) * mA;
-        ax += elem_row<R>(G, a, kA, mA, x0, x1, x2);
-        if (n0 || n1 || n2)
-          a1 += elem_row<R>(G, a, kA, mA, n0 ? R(1) : R(0), n1 ? R(1) : R(0), n2 ? R(1) : R(0));
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R4 *cc = reinterpret_cast<R4 *>(smem_raw);
+  typename AC::T vals[3] = {AC::zero(), AC::zero(), AC::zero()};
+  for (int b = blockIdx.x; b < P.nblk; b += gridDim.x) {
+    int i0, i1, k0, k1;
+    block_nodes(P, b, i0, i1, k0, k1);
+    for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) cc[k - k0] = rhs_entry(P, __ldg(&P.ent[k]));
+    __syncthreads();
+    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+      if (P.flags[i] & kNotch) {
+        rhs_notch_node(P, i);
+        continue;
       }
-      const R ri = bi - ax, be = bi - a1;
-      const R di = R(1) / dg;
-      const R zi = ri * di;
-      P.x[i] = P.dprev[i];
-      P.r[i] = ri;
-      P.dinv[i] = di;
-      P.z[i] = zi;
-      P.p[i] = R(0);
-      if (P.b) P.b[i] = bi;
-      const R sr = P.rscale * ri, sb = P.rscale * be;
-      vals[0] = AC::prod(sb, sb);
-      vals[1] = AC::prod(sr, sr);
-      vals[2] = AC::prod(sr, zi);
+      const int j0 = __ldg(&P.ptr[i]) - k0, j1 = __ldg(&P.ptr[i + 1]) - k0;
+      R bi = 0, dg = 0, ax = 0, a1 = 0;
+      for (int j = j0; j < j1; ++j) {
+        const R4 o = cc[j];
+        bi = radd(bi, o.x);
+        dg = radd(dg, o.y);
+        ax = radd(ax, o.z);
+        a1 = radd(a1, o.w);
+      }
+      rhs_node(P, i, bi, dg, ax, a1, vals);
     }
+    __syncthreads();
   }
   __shared__ double tot[3];
-  if (reduce_last<R, 3>(vals, P.part, P.ticket, tot) && threadIdx.x == 0) {
-    SolveScalars &S = *P.sc;
-    S.bn = sqrt(tot[0]);
-    S.rr = tot[1];
-    S.rho = tot[2];
-    S.beta = 0.0;
-    S.alpha = 0.0;
-    S.iters = 0;
-    S.restarts = 0;
-    S.status = kStOk;
-    S.projected = 0;
-    const bool done = (P.model == kAT2) && (S.bn == 0.0 || sqrt(S.rr) <= P.tol * S.bn);
-    S.done = done ? 1 : 0;
-    if (P.use_cond) cudaGraphSetConditional(P.cond_inner, done ? 0u : 1u);
+  if (reduce_last<R, 3>(vals, P.part, P.ticket, tot) && threadIdx.x == 0) rhs_finish(P, tot);
+}
+
+template <typename R, int U>
+__global__ void __launch_bounds__(256) k_dmg_rhs_nc(Params<R> P) {
+  typedef typename Params<R>::R4 R4;
+  typedef Acc<R> AC;
+  typename AC::T vals[3] = {AC::zero(), AC::zero(), AC::zero()};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.N; i += gridDim.x * blockDim.x) {
+    if (P.flags[i] & kNotch) {
+      rhs_notch_node(P, i);
+      continue;
+    }
+    R bi = 0, dg = 0, ax = 0, a1 = 0;
+    for (int k = 0; k < P.D; k += U) {
+      R4 o[U];
+      int en[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) en[u] = k + u < P.D ? __ldg(&P.ell[(size_t)(k + u) * P.N + i]) : -1;
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (en[u] >= 0) o[u] = rhs_entry(P, en[u]);
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (en[u] >= 0) {
+          bi = radd(bi, o[u].x);
+          dg = radd(dg, o[u].y);
+          ax = radd(ax, o[u].z);
+          a1 = radd(a1, o[u].w);
+        }
+    }
+    rhs_node(P, i, bi, dg, ax, a1, vals);
   }
+  __shared__ double tot[3];
+  if (reduce_last<R, 3>(vals, P.part, P.ticket, tot) && threadIdx.x == 0) rhs_finish(P, tot);
 }
 
 // Next search direction at node j: p_new = z + beta p_old (zero on the
@@ -483,111 +715,214 @@ __global__ void __launch_bounds__(256) k_dmg_rhs(Params<R> P) {
 // evaluated by the matvec (for neighbours) and the update (for the node).
 template <typename R>
 __device__ __forceinline__ R pnew(const Params<R> &P, int j, R beta) {
-  return fma(beta, P.p[j], P.z[j]);
+  const typename Params<R>::R2 v = P.pz[j];
+  return fma(beta, v.x, v.y);
 }
 
-// q = A p_new on free rows (matrix-free, Eq. matrix_free_fe_operator), and
-// the reduction p_new . q -> alpha = rho / (p.q).
+// One incidence entry's share of (A p_new)_a, matrix-free (Eq.
+// matrix_free_fe_operator): element coefficients are rebuilt from the
+// geometry and the history on every application.
 template <typename R>
-__global__ void __launch_bounds__(256) k_cg_matvec(Params<R> P) {
+__device__ __forceinline__ R mv_entry(const Params<R> &P, int en, R beta, R pc) {
   typedef typename Params<R>::R4 R4;
+  const int e = en >> 2, a = en & 3;
+  int4 t;
+  R A;
+  R4 G;
+  load_elem(P, e, t, A, G);
+  const R kA = P.kappa * A;
+  const R mA = (P.cbase + R(2) * P.Hr[e]) * A * (R(1) / R(12));
+  // the entry's own node (slot a) is the row's node: its value is pc
+  const R p0 = a == 0 ? pc : pnew(P, t.x, beta);
+  const R p1 = a == 1 ? pc : pnew(P, t.y, beta);
+  const R p2 = a == 2 ? pc : pnew(P, t.z, beta);
+  return elem_row<R>(G, a, kA, mA, p0, p1, p2);
+}
+
+template <typename R>
+__device__ __forceinline__ void matvec_finish(const Params<R> &P, const double *tot) {
+  SolveScalars &S = *P.sc;
+  S.pq = tot[0];
+  S.alpha = tot[0] != 0.0 ? S.rho / tot[0] : 0.0;
+}
+
+// q = A p_new on free rows and the reduction p_new . q -> alpha = rho/(p.q).
+// Entry-parallel schedule.
+template <typename R>
+__global__ void __launch_bounds__(256) k_cg_matvec_ep(Params<R> P) {
   typedef Acc<R> AC;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R *cq = reinterpret_cast<R *>(smem_raw);
   typename AC::T vals[1] = {AC::zero()};
   const R beta = (R)P.sc->beta;
-  if (i < P.N) {
-    if (!is_fixed(P, i)) {
+  for (int b = blockIdx.x; b < P.nblk; b += gridDim.x) {
+    int i0, i1, k0, k1;
+    block_nodes(P, b, i0, i1, k0, k1);
+    for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+      const int en = __ldg(&P.ent[k]);
+      const int e = en >> 2, a = en & 3;
+      const int4 t = make_int4(P.rec[e].n0, P.rec[e].n1, P.rec[e].n2, 0);
+      const int node = a == 0 ? t.x : (a == 1 ? t.y : t.z);
+      cq[k - k0] = mv_entry(P, en, beta, pnew(P, node, beta));
+    }
+    __syncthreads();
+    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
       R q = 0;
-      const int k0 = P.ptr[i], k1 = P.ptr[i + 1];
-      for (int k = k0; k < k1; ++k) {
-        const int en = __ldg(&P.ent[k]);
-        const int e = en >> 2, a = en & 3;
-        const int4 t = __ldg(&P.tri[e]);
-        const R4 G = P.grad[e];
-        const R A = __ldg(&P.area[e]);
-        const R kA = P.kappa * A;
-        const R mA = (P.cbase + R(2) * P.Hr[e]) * A * (R(1) / R(12));
-        q += elem_row<R>(G, a, kA, mA, pnew(P, t.x, beta), pnew(P, t.y, beta), pnew(P, t.z, beta));
+      if (!is_fixed(P, i)) {
+        const int j0 = __ldg(&P.ptr[i]) - k0, j1 = __ldg(&P.ptr[i + 1]) - k0;
+        for (int j = j0; j < j1; ++j) q = radd(q, cq[j]);
+        vals[0] = AC::add(vals[0], AC::prod(pnew(P, i, beta), P.rscale * q));
       }
       P.q[i] = q;
-      vals[0] = AC::prod(pnew(P, i, beta), P.rscale * q);
-    } else {
-      P.q[i] = R(0);
     }
+    __syncthreads();
   }
   __shared__ double tot[1];
-  if (reduce_last<R, 1>(vals, P.part, P.ticket, tot) && threadIdx.x == 0) {
-    SolveScalars &S = *P.sc;
-    S.pq = tot[0];
-    S.alpha = tot[0] != 0.0 ? S.rho / tot[0] : 0.0;
+  if (reduce_last<R, 1>(vals, P.part, P.ticket, tot) && threadIdx.x == 0) matvec_finish(P, tot);
+}
+
+// Node-centric schedule of the same matvec (U gathers in flight).
+template <typename R, int U>
+__global__ void __launch_bounds__(256) k_cg_matvec_nc(Params<R> P) {
+  typedef Acc<R> AC;
+  typename AC::T vals[1] = {AC::zero()};
+  const R beta = (R)P.sc->beta;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.N; i += gridDim.x * blockDim.x) {
+    R q = 0;
+    if (!is_fixed(P, i)) {
+      const R pc = pnew(P, i, beta);
+      for (int k = 0; k < P.D; k += U) {
+        R c[U];
+        int en[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) en[u] = k + u < P.D ? __ldg(&P.ell[(size_t)(k + u) * P.N + i]) : -1;
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (en[u] >= 0) c[u] = mv_entry(P, en[u], beta, pc);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (en[u] >= 0) q = radd(q, c[u]);
+      }
+      vals[0] = AC::add(vals[0], AC::prod(pnew(P, i, beta), P.rscale * q));
+    }
+    P.q[i] = q;
   }
+  __shared__ double tot[1];
+  if (reduce_last<R, 1>(vals, P.part, P.ticket, tot) && threadIdx.x == 0) matvec_finish(P, tot);
 }
 
 // x += alpha p, r -= alpha q, z = r / diag, p = p_new; reductions |r|^2 and
 // r.z; the last block takes the stop decision (Sec. 2.4; stop test on the
 // unpreconditioned residual).  AT1 (lo = d_prev, hi = 1): values leaving
-// the box are projected and flag a restart.
+// the box are projected and flag a restart.  FP32 handles two nodes per
+// thread with 8/16-byte vector accesses (workspace arrays are padded to an
+// even length; padding nodes are flagged fixed).
+template <typename R>
+__device__ __forceinline__ void update_node(const Params<R> &P, int i, R alpha, R beta, R &x, R &r,
+                                            typename Params<R>::R2 &pz, R q, R dinv,
+                                            typename Acc<R>::T (&vals)[3], bool &proj) {
+  typedef Acc<R> AC;
+  const R pn = fma(beta, pz.x, pz.y);
+  R xi = fma(alpha, pn, x);
+  const R ri = fma(-alpha, q, r);
+  if (P.model == kAT1) {
+    const R lo = P.dprev[i];
+    if (xi < lo) { xi = lo; proj = true; }
+    if (xi > R(1)) { xi = R(1); proj = true; }
+  }
+  const R zi = ri * dinv;
+  x = xi;
+  r = ri;
+  pz.x = pn;
+  pz.y = zi;
+  const R sr = P.rscale * ri;
+  vals[0] = AC::add(vals[0], AC::prod(sr, sr));
+  vals[1] = AC::add(vals[1], AC::prod(sr, zi));
+}
+
+template <typename R>
+__device__ __forceinline__ void update_finish(const Params<R> &P, const double *tot) {
+  SolveScalars &S = *P.sc;
+  bool stop = false;
+  if (S.pq == 0.0) {  // p = 0: nothing moved, the iterate is exact
+    if (P.model == kAT2) S.done = 1;
+    stop = true;
+  } else {
+    S.iters += 1;
+    S.rr = tot[0];
+    if (!(tot[0] == tot[0]) || isinf(tot[0])) {
+      S.status = kStNonfinite;
+      S.done = 1;
+      stop = true;
+    } else if (P.model == kAT1 && tot[2] > 0.0) {
+      S.projected = 1;
+      stop = true;  // restart
+    } else if (sqrt(tot[0]) <= P.tol * S.bn) {
+      if (P.model == kAT2) S.done = 1;
+      stop = true;
+    }
+    if (!stop && S.iters >= P.max_it) {
+      stop = true;
+      if (P.model == kAT2) {
+        S.status = kStNotConverged;
+        S.done = 1;
+      }
+    }
+    S.beta = S.rho != 0.0 ? tot[1] / S.rho : 0.0;
+    S.rho = tot[1];
+  }
+  S.inner_done = stop ? 1 : 0;
+  if (P.use_cond) cudaGraphSetConditional(P.cond_inner, stop ? 0u : 1u);
+}
+
 template <typename R>
 __global__ void __launch_bounds__(256) k_cg_update(Params<R> P) {
+  typedef typename Params<R>::R2 R2;
   typedef Acc<R> AC;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
   typename AC::T vals[3] = {AC::zero(), AC::zero(), AC::zero()};
   const R beta = (R)P.sc->beta;
   const R alpha = (R)P.sc->alpha;
-  if (i < P.N) {
-    if (!is_fixed(P, i)) {
-      const R pn = pnew(P, i, beta);
-      R xi = fma(alpha, pn, P.x[i]);
-      const R ri = fma(-alpha, P.q[i], P.r[i]);
-      if (P.model == kAT1) {
-        const R lo = P.dprev[i];
-        if (xi < lo) { xi = lo; vals[2] = AC::one(); }
-        if (xi > R(1)) { xi = R(1); vals[2] = AC::one(); }
-      }
-      const R zi = ri * P.dinv[i];
-      P.x[i] = xi;
-      P.r[i] = ri;
-      P.z[i] = zi;
-      P.p[i] = pn;
-      const R sr = P.rscale * ri;
-      vals[0] = AC::prod(sr, sr);
-      vals[1] = AC::prod(sr, zi);
+  bool proj = false;
+  const int stride = gridDim.x * blockDim.x;
+  if constexpr (sizeof(R) == 4) {
+    const int npair = (P.N + 1) >> 1;
+    const uchar2 *__restrict__ fl2 = reinterpret_cast<const uchar2 *>(P.flags);
+    float2 *__restrict__ x2 = reinterpret_cast<float2 *>(P.x);
+    float2 *__restrict__ r2 = reinterpret_cast<float2 *>(P.r);
+    float4 *__restrict__ pz4 = reinterpret_cast<float4 *>(P.pz);
+    const float2 *__restrict__ q2 = reinterpret_cast<const float2 *>(P.q);
+    const float2 *__restrict__ d2 = reinterpret_cast<const float2 *>(P.dinv);
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < npair; j += stride) {
+      const uchar2 f = fl2[j];
+      float2 xv = x2[j], rv = r2[j];
+      const float2 qv = q2[j], dv = d2[j];
+      const float4 pv = pz4[j];
+      const int i = 2 * j;
+      const bool fix0 = (f.x & kNotch) || (P.freef && !P.freef[i]);
+      const bool fix1 = (f.y & kNotch) || (P.freef && !P.freef[i + 1]);
+      R2 pz0, pz1;
+      pz0.x = pv.x; pz0.y = pv.y;
+      pz1.x = pv.z; pz1.y = pv.w;
+      if (!fix0) update_node(P, i, alpha, beta, xv.x, rv.x, pz0, qv.x, dv.x, vals, proj);
+      if (!fix1) update_node(P, i + 1, alpha, beta, xv.y, rv.y, pz1, qv.y, dv.y, vals, proj);
+      x2[j] = xv;
+      r2[j] = rv;
+      pz4[j] = make_float4(pz0.x, pz0.y, pz1.x, pz1.y);
+    }
+  } else {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.N; i += stride) {
+      if (is_fixed(P, i)) continue;
+      R2 pz = P.pz[i];
+      R x = P.x[i], r = P.r[i];
+      update_node(P, i, alpha, beta, x, r, pz, P.q[i], P.dinv[i], vals, proj);
+      P.x[i] = x;
+      P.r[i] = r;
+      P.pz[i] = pz;
     }
   }
+  if (proj) vals[2] = AC::one();
   __shared__ double tot[3];
-  if (reduce_last<R, 3>(vals, P.part, P.ticket, tot) && threadIdx.x == 0) {
-    SolveScalars &S = *P.sc;
-    bool stop = false;
-    if (S.pq == 0.0) {  // p = 0: nothing moved, the iterate is exact
-      if (P.model == kAT2) S.done = 1;
-      stop = true;
-    } else {
-      S.iters += 1;
-      S.rr = tot[0];
-      if (!(tot[0] == tot[0]) || isinf(tot[0])) {
-        S.status = kStNonfinite;
-        S.done = 1;
-        stop = true;
-      } else if (P.model == kAT1 && tot[2] > 0.0) {
-        S.projected = 1;
-        stop = true;  // restart
-      } else if (sqrt(tot[0]) <= P.tol * S.bn) {
-        if (P.model == kAT2) S.done = 1;
-        stop = true;
-      }
-      if (!stop && S.iters >= P.max_it) {
-        stop = true;
-        if (P.model == kAT2) {
-          S.status = kStNotConverged;
-          S.done = 1;
-        }
-      }
-      S.beta = S.rho != 0.0 ? tot[1] / S.rho : 0.0;
-      S.rho = tot[1];
-    }
-    S.inner_done = stop ? 1 : 0;
-    if (P.use_cond) cudaGraphSetConditional(P.cond_inner, stop ? 0u : 1u);
-  }
+  if (reduce_last<R, 3>(vals, P.part, P.ticket, tot) && threadIdx.x == 0) update_finish(P, tot);
 }
 
 // AT1 restart (projected CG, Sec. 2.4): r = b - A x, active set
@@ -597,40 +932,51 @@ template <typename R>
 __global__ void __launch_bounds__(256) k_at1_restart(Params<R> P) {
   typedef typename Params<R>::R4 R4;
   typedef Acc<R> AC;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R *cx = reinterpret_cast<R *>(smem_raw);
   typename AC::T vals[2] = {AC::zero(), AC::zero()};
-  if (i < P.N) {
-    const bool notch = P.flags[i] & kNotch;
-    if (!notch) {
-      R ax = 0;
-      const int k0 = P.ptr[i], k1 = P.ptr[i + 1];
-      for (int k = k0; k < k1; ++k) {
-        const int en = __ldg(&P.ent[k]);
-        const int e = en >> 2, a = en & 3;
-        const int4 t = __ldg(&P.tri[e]);
-        const R4 G = P.grad[e];
-        const R A = __ldg(&P.area[e]);
-        const R kA = P.kappa * A;
-        const R mA = (P.cbase + R(2) * P.Hr[e]) * A * (R(1) / R(12));
-        ax += elem_row<R>(G, a, kA, mA, __ldcg(&P.x[t.x]), __ldcg(&P.x[t.y]), __ldcg(&P.x[t.z]));
+  for (int b = blockIdx.x; b < P.nblk; b += gridDim.x) {
+    int i0, i1, k0, k1;
+    block_nodes(P, b, i0, i1, k0, k1);
+    for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+      const int en = __ldg(&P.ent[k]);
+      const int e = en >> 2, a = en & 3;
+      int4 t;
+      R A;
+      R4 G;
+      load_elem(P, e, t, A, G);
+      const R kA = P.kappa * A;
+      const R mA = (P.cbase + R(2) * P.Hr[e]) * A * (R(1) / R(12));
+      cx[k - k0] = elem_row<R>(G, a, kA, mA, P.x[t.x], P.x[t.y], P.x[t.z]);
+    }
+    __syncthreads();
+    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+      if (P.flags[i] & kNotch) {
+        P.freef[i] = 0;
+        continue;
       }
+      const int j0 = __ldg(&P.ptr[i]) - k0, j1 = __ldg(&P.ptr[i + 1]) - k0;
+      R ax = 0;
+      for (int j = j0; j < j1; ++j) ax += cx[j];
       const R xi = P.x[i], ri = P.b[i] - ax, lo = P.dprev[i];
       const bool act = (xi <= lo && ri <= R(0)) || (xi >= R(1) && ri >= R(0));
       P.r[i] = ri;
       P.freef[i] = act ? 0 : 1;
-      P.p[i] = R(0);
+      typename Params<R>::R2 w;
+      w.x = R(0);
+      w.y = R(0);
       if (act) {
-        P.z[i] = R(0);
+        P.pz[i] = w;
       } else {
         const R zi = ri * P.dinv[i];
-        P.z[i] = zi;
+        w.y = zi;
+        P.pz[i] = w;
         const R sr = P.rscale * ri;
-        vals[0] = AC::prod(sr, sr);
-        vals[1] = AC::prod(sr, zi);
+        vals[0] = AC::add(vals[0], AC::prod(sr, sr));
+        vals[1] = AC::add(vals[1], AC::prod(sr, zi));
       }
-    } else {
-      P.freef[i] = 0;
     }
+    __syncthreads();
   }
   __shared__ double tot[2];
   if (reduce_last<R, 2>(vals, P.part, P.ticket, tot) && threadIdx.x == 0) {
@@ -663,9 +1009,8 @@ __global__ void __launch_bounds__(256) k_at1_restart(Params<R> P) {
 // d = x; notch d = 1.  Logs the iteration count and status of the step and
 // advances the step counter.
 template <typename R>
-__global__ void k_dmg_finish(Params<R> P) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < P.N) {
+__global__ void __launch_bounds__(256) k_dmg_finish(Params<R> P) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.N; i += gridDim.x * blockDim.x) {
     R v;
     if (P.flags[i] & kNotch) {
       v = R(1);
@@ -693,55 +1038,52 @@ __global__ void k_dmg_finish(Params<R> P) {
 
 // ------------------------------------------------------------- energies
 
-// E_el = sum A_e (g psi+ + psi-), E_frac per model, E_kin = 1/2 sum m v^2.
-// Element terms are counted by the owner node (slot 0).  FP64 (diagnostic).
+// E_el = sum A_e (g psi+ + psi-), E_frac per model (element loop), and
+// E_kin = 1/2 sum m v^2 (node loop).  Terms in the kernel precision,
+// accumulated in FP64 (double-word in FP32 mode).
 template <typename R>
 __global__ void __launch_bounds__(256) k_energies(Params<R> P) {
   typedef typename Params<R>::R2 R2;
   typedef typename Params<R>::R4 R4;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  double vals[3] = {0.0, 0.0, 0.0};
-  if (i < P.N) {
-    const R2 vi = P.v[i];
-    vals[1] = 0.5 / (double)P.minv[i] * ((double)vi.x * vi.x + (double)vi.y * vi.y);
-    const int k0 = P.ptr[i], k1 = P.ptr[i + 1];
-    for (int k = k0; k < k1; ++k) {
-      const int en = __ldg(&P.ent[k]);
-      if (en & 3) continue;
-      const int e = en >> 2;
-      const int4 t = __ldg(&P.tri[e]);
-      const R4 G = P.grad[e];
-      const double A = (double)__ldg(&P.area[e]);
-      const R2 u0 = P.u[t.x], u1 = P.u[t.y], u2 = P.u[t.z];
-      const R ax0 = u0.x - u2.x, ax1 = u1.x - u2.x, ay0 = u0.y - u2.y, ay1 = u1.y - u2.y;
-      const R exx = G.x * ax0 + G.z * ax1;
-      const R eyy = G.y * ay0 + G.w * ay1;
-      const R exy = R(0.5) * (G.y * ax0 + G.w * ax1 + G.x * ay0 + G.z * ay1);
-      const double d0 = P.d[t.x], d1 = P.d[t.y], d2 = P.d[t.z];
-      const double db = (d0 + d1 + d2) / 3.0;
-      const double g = (1.0 - db) * (1.0 - db) + (double)P.eta;
-      // psi- = psi_full - psi+ for every split (psi_full = lambda/2 tr^2 + mu e:e)
-      R sxx, syy, sxy, psip;
-      stress(P, exx, eyy, exy, R(1), sxx, syy, sxy, psip);
-      const double tr = (double)exx + eyy;
-      const double full = 0.5 * (double)P.lam * tr * tr +
-                          (double)P.mu * ((double)exx * exx + (double)eyy * eyy + 2.0 * (double)exy * exy);
-      const double psim = P.split == kIso ? 0.0 : full - (double)psip;
-      vals[0] += A * (g * (double)psip + psim);
-      const double G0x = G.x, G0y = G.y, G1x = G.z, G1y = G.w;
-      const double gdx = G0x * (d0 - d2) + G1x * (d1 - d2);
-      const double gdy = G0y * (d0 - d2) + G1y * (d1 - d2);
-      const double g2 = gdx * gdx + gdy * gdy;
-      if (P.model == kAT1) {
-        vals[2] += P.Gc * 0.375 * (A / 3.0 * (d0 + d1 + d2) / P.l0 + P.l0 * A * g2);
-      } else {
-        const double dMd = A / 12.0 * (2.0 * (d0 * d0 + d1 * d1 + d2 * d2) + 2.0 * (d0 * d1 + d1 * d2 + d0 * d2));
-        vals[2] += P.Gc * (dMd / (2.0 * P.l0) + 0.5 * P.l0 * A * g2);
-      }
+  typedef Acc<R> AC;
+  typename AC::T vals[3] = {AC::zero(), AC::zero(), AC::zero()};
+  const int stride = gridDim.x * blockDim.x;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < P.Ne; e += stride) {
+    int4 t;
+    R A;
+    R4 G;
+    load_elem(P, e, t, A, G);
+    R exx, eyy, exy;
+    elem_strain(P, G, t, exx, eyy, exy);
+    const R d0 = P.d[t.x], d1 = P.d[t.y], d2 = P.d[t.z];
+    const R db = (d0 + d1 + d2) * (R(1) / R(3));
+    const R g = (R(1) - db) * (R(1) - db) + P.eta;
+    R sxx, syy, sxy, psip;
+    stress(P, exx, eyy, exy, R(1), sxx, syy, sxy, psip);
+    // psi- = psi_full - psi+ for every split (psi_full = lambda/2 tr^2 + mu e:e)
+    const R tr = exx + eyy;
+    const R full = R(0.5) * P.lam * tr * tr + P.mu * (exx * exx + eyy * eyy + R(2) * exy * exy);
+    const R psim = P.split == kIso ? R(0) : full - psip;
+    vals[0] = AC::add(vals[0], AC::prod(A, g * psip + psim));
+    const R gdx = G.x * (d0 - d2) + G.z * (d1 - d2);
+    const R gdy = G.y * (d0 - d2) + G.w * (d1 - d2);
+    const R g2 = gdx * gdx + gdy * gdy;
+    const R Gc = (R)P.Gc, l0 = (R)P.l0;
+    R dens;
+    if (P.model == kAT1) {
+      dens = Gc * R(0.375) * ((d0 + d1 + d2) * (R(1) / R(3)) / l0 + l0 * g2);
+    } else {
+      const R dMd = (R(2) * (d0 * d0 + d1 * d1 + d2 * d2) + R(2) * (d0 * d1 + d1 * d2 + d0 * d2)) * (R(1) / R(12));
+      dens = Gc * (dMd / (R(2) * l0) + R(0.5) * l0 * g2);
     }
+    vals[2] = AC::add(vals[2], AC::prod(A, dens));
+  }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.N; i += stride) {
+    const R2 vi = P.v[i];
+    vals[1] = AC::add(vals[1], AC::prod(R(0.5) / P.minv[i], vi.x * vi.x + vi.y * vi.y));
   }
   __shared__ double tot[3];
-  if (reduce_last<double, 3>(vals, P.part, P.ticket, tot) && threadIdx.x == 0) {
+  if (reduce_last<R, 3>(vals, P.part, P.ticket, tot) && threadIdx.x == 0) {
     P.energy_out[0] = tot[0];
     P.energy_out[1] = tot[1];
     P.energy_out[2] = tot[2];

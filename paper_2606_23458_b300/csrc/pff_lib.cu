@@ -64,8 +64,7 @@ __global__ void k_check_tri(const int32_t *tri, int64_t Ne, int64_t N, unsigned 
 // P1 geometry, Eq. (grad_phi): A_e and the shape gradients; the incircle
 // diameter 4 A / P for the stable step; inverted elements are reported.
 template <typename R>
-__global__ void k_geometry(const double *xy, const int32_t *tri, int64_t Ne, int4 *tri4,
-                           typename V<R>::T4 *grad4, R *area, double *area_d,
+__global__ void k_geometry(const double *xy, const int32_t *tri, int64_t Ne, ERec<R> *rec, double *area_d,
                            unsigned long long *bad, unsigned long long *hmin_bits) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= Ne) return;
@@ -78,15 +77,18 @@ __global__ void k_geometry(const double *xy, const int32_t *tri, int64_t Ne, int
     return;
   }
   const double s = 1.0 / (2.0 * A);
-  typename V<R>::T4 g;
-  g.x = (R)(s * (y2 - y3));
-  g.y = (R)(s * (x3 - x2));
-  g.z = (R)(s * (y3 - y1));
-  g.w = (R)(s * (x1 - x3));
-  grad4[e] = g;
-  area[e] = (R)A;
+  ERec<R> r;
+  std::memset(&r, 0, sizeof(r));
+  r.n0 = n1;
+  r.n1 = n2;
+  r.n2 = n3;
+  r.A = (R)A;
+  r.g.x = (R)(s * (y2 - y3));
+  r.g.y = (R)(s * (x3 - x2));
+  r.g.z = (R)(s * (y3 - y1));
+  r.g.w = (R)(s * (x1 - x3));
+  rec[e] = r;
   area_d[e] = A;
-  tri4[e] = make_int4(n1, n2, n3, 0);
   const double P = hypot(x2 - x1, y2 - y1) + hypot(x3 - x2, y3 - y2) + hypot(x1 - x3, y1 - y3);
   const double hin = 4.0 * A / P;
   atomicMin(hmin_bits, (unsigned long long)__double_as_longlong(hin));  // positive doubles order as integers
@@ -165,6 +167,14 @@ __global__ void k_sort_segments(const int32_t *ptr, int64_t N, int32_t *ent) {
   }
 }
 
+// ELL copy of the incidence: entry j of node i at ell[j N + i], -1 padded.
+__global__ void k_build_ell(const int32_t *ptr, const int32_t *ent, int64_t N, int D, int32_t *ell) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int32_t k0 = ptr[i], deg = ptr[i + 1] - k0;
+  for (int j = 0; j < D; ++j) ell[(size_t)j * N + i] = j < deg ? ent[k0 + j] : -1;
+}
+
 // Consistent P1 traction load, edges in order (one thread: deterministic,
 // same order as a sequential assembly).
 __global__ void k_fext(const double *xy, const int32_t *ed, const double *tv, int64_t M, double *f) {
@@ -206,12 +216,12 @@ __global__ void k_lumped(const int32_t *ptr, const int32_t *ent, const double *a
 }
 
 template <typename R>
-__global__ void k_geom_out(const typename V<R>::T4 *g4, const double *area_d, const typename V<R>::T2 *fext,
+__global__ void k_geom_out(const ERec<R> *rec, const double *area_d, const typename V<R>::T2 *fext,
                            const R *minv, int64_t N, int64_t Ne, double *area, double *grad, double *fo,
                            double *mo) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < Ne) {
-    const typename V<R>::T4 g = g4[i];
+    const auto g = rec[i].g;
     if (area) area[i] = area_d[i];
     if (grad) {
       double *o = grad + 6 * i;
@@ -240,9 +250,9 @@ struct pff_mesh {
   int32_t prec = PFF_FP64;
   int64_t N = 0, Ne = 0;
   size_t rs = 8;  // sizeof(R)
-  int32_t *ptr = nullptr, *ent = nullptr;
-  int4 *tri = nullptr;
-  void *grad = nullptr, *area = nullptr, *fext = nullptr, *minv = nullptr;
+  int32_t *ptr = nullptr, *ent = nullptr, *ell = nullptr;
+  int32_t D = 0;  // ELL width = maximum incidence degree
+  void *rec = nullptr, *fext = nullptr, *minv = nullptr;
   double *area_d = nullptr;
   uint8_t *flags = nullptr;
   double hmin = 0.0;
@@ -251,7 +261,7 @@ struct pff_mesh {
   double lam = 0, mu = 0, K = 0;
   // workspace
   double *x = nullptr, *r = nullptr, *b = nullptr, *part = nullptr, *energy = nullptr, *wext = nullptr;
-  void *z = nullptr, *p = nullptr, *q = nullptr, *dinv = nullptr;
+  void *pz = nullptr, *q = nullptr, *dinv = nullptr;
   float *Hf = nullptr;  // FP32 mirror of the history (FP32_MIXED)
   uint8_t *freef = nullptr;
   unsigned int *ticket = nullptr;
@@ -260,6 +270,14 @@ struct pff_mesh {
   int64_t *step_ctr = nullptr;
   GraphCache solve_g, step_g;
   int block = 256;
+  // launch configuration (kernel id -> grid, dynamic shared memory)
+  int32_t NB = 256, nblk = 0, maxE = 0;
+  unsigned grid[16][8] = {{0}};
+  size_t smem[16][8] = {{0}};
+  int32_t var[16] = {0};       // schedule variant in use per kernel
+  int32_t tuned_var[16] = {0}; // autotuner's choice
+  bool tuned[16] = {false};
+  float tune_ms[16][8] = {{0}};
 };
 
 namespace pff {
@@ -274,8 +292,8 @@ static void mesh_free(pff_mesh *m) {
   if (!m) return;
   free_graph(m->solve_g);
   free_graph(m->step_g);
-  void *ptrs[] = {m->ptr, m->ent, m->tri, m->grad, m->area, m->fext, m->minv, m->area_d, m->flags,
-                  m->x, m->r, m->b, m->part, m->energy, m->wext, m->z, m->p, m->q, m->dinv,
+  void *ptrs[] = {m->ptr, m->ent, m->ell, m->rec, m->fext, m->minv, m->area_d, m->flags,
+                  m->x, m->r, m->b, m->part, m->energy, m->wext, m->pz, m->q, m->dinv,
                   m->Hf, m->freef, m->ticket, m->sc, m->status_word, m->step_ctr};
   for (void *q : ptrs)
     if (q) cudaFree(q);
@@ -283,6 +301,117 @@ static void mesh_free(pff_mesh *m) {
 }
 
 static inline unsigned grid_for(int64_t n, int block) { return (unsigned)((n + block - 1) / block); }
+
+enum KernelId { KP_PREDICT = 0, KP_FORCE, KP_RHS, KP_MATVEC, KP_UPDATE, KP_FINISH, KP_RESTART, KP_ENERGIES,
+                KP_COUNT };
+constexpr int kThreads = 256;
+// Schedule variants of the gather kernels (force, rhs, matvec):
+// 0 = entry-parallel node blocks, 1..4 = node-centric with U = 1..4
+// gathers in flight.  All variants give bit-identical results.
+constexpr int kNumVariants = 5;
+static inline bool tunable(int id) { return id == KP_FORCE || id == KP_RHS || id == KP_MATVEC; }
+
+template <typename R>
+static const void *kfun(int id, int v) {
+  switch (id) {
+    case KP_PREDICT: return (const void *)k_predict<R>;
+    case KP_FORCE:
+      switch (v) {
+        case 1: return (const void *)k_force_nc<R, 1>;
+        case 2: return (const void *)k_force_nc<R, 2>;
+        case 3: return (const void *)k_force_nc<R, 3>;
+        case 4: return (const void *)k_force_nc<R, 4>;
+        default: return (const void *)k_force_ep<R>;
+      }
+    case KP_RHS:
+      switch (v) {
+        case 1: return (const void *)k_dmg_rhs_nc<R, 1>;
+        case 2: return (const void *)k_dmg_rhs_nc<R, 2>;
+        case 3: return (const void *)k_dmg_rhs_nc<R, 3>;
+        case 4: return (const void *)k_dmg_rhs_nc<R, 4>;
+        default: return (const void *)k_dmg_rhs_ep<R>;
+      }
+    case KP_MATVEC:
+      switch (v) {
+        case 1: return (const void *)k_cg_matvec_nc<R, 1>;
+        case 2: return (const void *)k_cg_matvec_nc<R, 2>;
+        case 3: return (const void *)k_cg_matvec_nc<R, 3>;
+        case 4: return (const void *)k_cg_matvec_nc<R, 4>;
+        default: return (const void *)k_cg_matvec_ep<R>;
+      }
+    case KP_UPDATE: return (const void *)k_cg_update<R>;
+    case KP_FINISH: return (const void *)k_dmg_finish<R>;
+    case KP_RESTART: return (const void *)k_at1_restart<R>;
+    default: return (const void *)k_energies<R>;
+  }
+}
+
+// Launch geometry.  Node-block kernels stage one value set per incidence
+// entry of a block of NB nodes in shared memory; NB is halved until the
+// largest block's entries fit in 40 KB.  Grids are the smaller of the
+// work and one full wave (SMs x resident blocks), with grid-stride loops.
+template <typename R>
+static pff_status configure(pff_mesh *m) {
+  std::vector<int32_t> ptr(m->N + 1);
+  CUDA_TRY(cudaMemcpy(ptr.data(), m->ptr, (m->N + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
+  const size_t per_entry = sizeof(typename V<R>::T4);  // the widest staged record (rhs)
+  int NB = 256, maxE = 0;
+  for (;;) {
+    maxE = 0;
+    for (int64_t i0 = 0; i0 < m->N; i0 += NB) {
+      const int64_t i1 = std::min<int64_t>(i0 + NB, m->N);
+      maxE = std::max<int>(maxE, ptr[i1] - ptr[i0]);
+    }
+    if ((size_t)maxE * per_entry <= 40 * 1024 || NB == 1) break;
+    NB /= 2;
+  }
+  if ((size_t)maxE * per_entry > 200 * 1024)
+    return fail(PFF_ERR_MESH, "a node has too many incident elements for the shared-memory staging");
+  m->NB = NB;
+  m->maxE = maxE;
+  int D = 0;
+  for (int64_t i = 0; i < m->N; ++i) D = std::max<int>(D, ptr[i + 1] - ptr[i]);
+  m->D = D;
+  if (!m->ell) {
+    PFF_TRY(dalloc(&m->ell, (size_t)D * m->N));
+    k_build_ell<<<grid_for(m->N, 256), 256>>>(m->ptr, m->ent, m->N, D, m->ell);
+    CUDA_TRY(cudaGetLastError());
+  }
+  m->nblk = (int32_t)((m->N + NB - 1) / NB);
+  const size_t sm_ep[KP_COUNT] = {0, maxE * sizeof(typename V<R>::T2), maxE * sizeof(typename V<R>::T4),
+                                  maxE * sizeof(R), 0, 0, maxE * sizeof(R), 0};
+  int dev = 0, nsm = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  for (int id = 0; id < KP_COUNT; ++id) {
+    const int nv = tunable(id) ? kNumVariants : 1;
+    for (int v = 0; v < nv; ++v) {
+      const void *f = kfun<R>(id, v);
+      const size_t sm = (v == 0) ? sm_ep[id] : 0;
+      if (sm > 0) CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+      int occ = 0;
+      CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f, kThreads, sm));
+      if (occ < 1) occ = 1;
+      const int64_t work = sm > 0 ? m->nblk
+                                  : (int64_t)grid_for(id == KP_ENERGIES ? std::max(m->N, m->Ne) : m->N, kThreads);
+      m->grid[id][v] = (unsigned)std::max<int64_t>(1, std::min<int64_t>(work, (int64_t)nsm * occ));
+      m->smem[id][v] = sm;
+    }
+  }
+  return PFF_OK;
+}
+
+template <typename R>
+static pff_status launch_v(const pff_mesh *m, int id, int v, Params<R> &P, cudaStream_t s) {
+  void *args[] = {(void *)&P};
+  CUDA_TRY(cudaLaunchKernel(kfun<R>(id, v), dim3(m->grid[id][v]), dim3(kThreads), args, m->smem[id][v], s));
+  return PFF_OK;
+}
+
+template <typename R>
+static pff_status launch(const pff_mesh *m, int id, Params<R> &P, cudaStream_t s) {
+  return launch_v<R>(m, id, m->var[id], P, s);
+}
 
 static pff_options defaults(const pff_options *o) {
   pff_options d{};
@@ -301,11 +430,13 @@ static Params<R> base_params(pff_mesh *m, const pff_options &o) {
   std::memset(&P, 0, sizeof(P));
   P.N = (int32_t)m->N;
   P.Ne = (int32_t)m->Ne;
+  P.NB = m->NB;
+  P.nblk = m->nblk;
   P.ptr = m->ptr;
   P.ent = m->ent;
-  P.tri = m->tri;
-  P.grad = (const typename V<R>::T4 *)m->grad;
-  P.area = (const R *)m->area;
+  P.ell = m->ell;
+  P.D = m->D;
+  P.rec = (const ERec<R> *)m->rec;
   P.flags = m->flags;
   P.fext = (const typename V<R>::T2 *)m->fext;
   P.minv = (const R *)m->minv;
@@ -328,8 +459,7 @@ static Params<R> base_params(pff_mesh *m, const pff_options &o) {
   P.x = (R *)m->x;
   P.r = (R *)m->r;
   P.b = at1 ? (R *)m->b : nullptr;
-  P.z = (R *)m->z;
-  P.p = (R *)m->p;
+  P.pz = (typename V<R>::T2 *)m->pz;
   P.q = (R *)m->q;
   P.dinv = (R *)m->dinv;
   P.Hf = m->Hf;
@@ -358,21 +488,23 @@ static pff_status bind_history(pff_mesh *m, Params<R> &P, const double *H, cudaS
     P.Hr = (const R *)H;
   } else {
     P.Hr = (const R *)m->Hf;
-    k_h_mirror<<<grid_for(m->Ne, 256), 256, 0, s>>>(H, m->Hf, (int)m->Ne);
+    k_h_mirror<<<std::min<unsigned>(grid_for(m->Ne, 256), 148 * 8), 256, 0, s>>>(H, m->Hf, (int)m->Ne);
     CUDA_TRY(cudaGetLastError());
   }
   return PFF_OK;
 }
 
 template <typename R>
-static pff_status add_kernel(cudaGraph_t g, const std::vector<cudaGraphNode_t> &deps, void (*fn)(Params<R>),
-                             unsigned grid, int block, Params<R> &P, cudaGraphNode_t *out) {
+static pff_status add_kernel(const pff_mesh *m, cudaGraph_t g, const std::vector<cudaGraphNode_t> &deps, int id,
+                             Params<R> &P, cudaGraphNode_t *out) {
   cudaKernelNodeParams kp;
   std::memset(&kp, 0, sizeof(kp));
   void *args[] = {(void *)&P};
-  kp.func = (void *)fn;
-  kp.gridDim = dim3(grid);
-  kp.blockDim = dim3(block);
+  const int v = m->var[id];
+  kp.func = const_cast<void *>(kfun<R>(id, v));
+  kp.gridDim = dim3(m->grid[id][v]);
+  kp.blockDim = dim3(kThreads);
+  kp.sharedMemBytes = (unsigned)m->smem[id][v];
   kp.kernelParams = args;
   CUDA_TRY(cudaGraphAddKernelNode(out, g, deps.data(), deps.size(), &kp));
   return PFF_OK;
@@ -392,50 +524,170 @@ static pff_status add_while(cudaGraph_t g, const std::vector<cudaGraphNode_t> &d
 // Appends the damage solve (rhs -> CG loop -> finish) to graph g after dep.
 // The handles must already be in P (created on the top-level graph).
 template <typename R>
-static pff_status append_solve(cudaGraph_t g, cudaGraphNode_t dep, Params<R> &P, int64_t N, int block,
+static pff_status append_solve(const pff_mesh *m, cudaGraph_t g, cudaGraphNode_t dep, Params<R> &P,
                                cudaGraphNode_t *last) {
-  const unsigned G = grid_for(N, block);
   std::vector<cudaGraphNode_t> d;
   if (dep) d.push_back(dep);
   cudaGraphNode_t n_rhs, n_loop, n_fin;
-  PFF_TRY(add_kernel<R>(g, d, k_dmg_rhs<R>, G, block, P, &n_rhs));
+  PFF_TRY(add_kernel<R>(m, g, d, KP_RHS, P, &n_rhs));
   if (P.model == kAT1) {
     cudaGraph_t outer, inner;
     PFF_TRY(add_while(g, {n_rhs}, P.cond_outer, &outer, &n_loop));
     cudaGraphNode_t n_rs, n_in, n_mv, n_up;
-    PFF_TRY(add_kernel<R>(outer, {}, k_at1_restart<R>, G, block, P, &n_rs));
+    PFF_TRY(add_kernel<R>(m, outer, {}, KP_RESTART, P, &n_rs));
     PFF_TRY(add_while(outer, {n_rs}, P.cond_inner, &inner, &n_in));
-    PFF_TRY(add_kernel<R>(inner, {}, k_cg_matvec<R>, G, block, P, &n_mv));
-    PFF_TRY(add_kernel<R>(inner, {n_mv}, k_cg_update<R>, G, block, P, &n_up));
+    PFF_TRY(add_kernel<R>(m, inner, {}, KP_MATVEC, P, &n_mv));
+    PFF_TRY(add_kernel<R>(m, inner, {n_mv}, KP_UPDATE, P, &n_up));
   } else {
     cudaGraph_t body;
     PFF_TRY(add_while(g, {n_rhs}, P.cond_inner, &body, &n_loop));
     cudaGraphNode_t n_mv, n_up;
-    PFF_TRY(add_kernel<R>(body, {}, k_cg_matvec<R>, G, block, P, &n_mv));
-    PFF_TRY(add_kernel<R>(body, {n_mv}, k_cg_update<R>, G, block, P, &n_up));
+    PFF_TRY(add_kernel<R>(m, body, {}, KP_MATVEC, P, &n_mv));
+    PFF_TRY(add_kernel<R>(m, body, {n_mv}, KP_UPDATE, P, &n_up));
   }
-  PFF_TRY(add_kernel<R>(g, {n_loop}, k_dmg_finish<R>, G, block, P, &n_fin));
+  PFF_TRY(add_kernel<R>(m, g, {n_loop}, KP_FINISH, P, &n_fin));
   *last = n_fin;
   return PFF_OK;
 }
 
+// Autotuner: times every schedule variant of the gather kernels (force,
+// damage right-hand side, CG matvec) on this mesh's own data, each launch
+// after a read of 256 MB (colder than L2) and bracketed by CUDA events, and
+// keeps the fastest.  The force kernel runs on scratch copies of the state
+// it writes.  opt->variant > 0 forces variant (variant - 1) instead.
+__global__ void k_read_flush(const float4 *buf, size_t n, float *sink) {
+  const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i < n) {
+    const float4 v = __ldcg(&buf[i]);
+    if (v.x == 12345.f) sink[0] = v.y;  // never true: buffer is zeroed
+  }
+}
+
+// with_force / with_damage say which kernels' inputs P carries: the force
+// kernel needs the state (u, v, a, d, H), the damage kernels need H and
+// d_prev.  Kernels without valid inputs are not launched.
+template <typename R>
+static pff_status autotune(pff_mesh *m, const pff_options &o, Params<R> P, bool with_force, bool with_damage,
+                           cudaStream_t s) {
+  const int ids[3] = {KP_FORCE, KP_RHS, KP_MATVEC};
+  if (o.variant > 0) {
+    for (int id : ids) m->var[id] = std::min(o.variant - 1, kNumVariants - 1);
+    return PFF_OK;
+  }
+  bool need = false;
+  for (int id : ids)
+    if (!m->tuned[id] && (id == KP_FORCE ? with_force : with_damage)) need = true;
+  if (!need) {
+    for (int id : ids)
+      if (m->tuned[id]) m->var[id] = m->tuned_var[id];
+    return PFF_OK;
+  }
+  typedef typename V<R>::T2 R2;
+  const size_t nflush = (size_t)16 << 20;  // 16 Mi float4 = 256 MB
+  float4 *fb = nullptr;
+  R2 *sv = nullptr, *sa = nullptr;
+  double *sH = nullptr;
+  float *sHf = nullptr;
+  cudaEvent_t e0, e1;
+  pff_status res = PFF_OK;
+  auto cleanup = [&]() {
+    if (fb) cudaFree(fb);
+    if (sv) cudaFree(sv);
+    if (sa) cudaFree(sa);
+    if (sH) cudaFree(sH);
+    if (sHf) cudaFree(sHf);
+  };
+#define TUNE_TRY(x)                                                  \
+  do {                                                               \
+    cudaError_t e_ = (x);                                            \
+    if (e_ != cudaSuccess) {                                         \
+      cleanup();                                                     \
+      return fail(PFF_ERR_CUDA, std::string("autotune: ") + #x + ": " + cudaGetErrorString(e_)); \
+    }                                                                \
+  } while (0)
+  TUNE_TRY(cudaMalloc(&fb, nflush * sizeof(float4) + 16));
+  TUNE_TRY(cudaMemsetAsync(fb, 0, nflush * sizeof(float4) + 16, s));
+  float *sink = (float *)(fb + nflush);
+  TUNE_TRY(cudaEventCreate(&e0));
+  TUNE_TRY(cudaEventCreate(&e1));
+  auto time_variants = [&](int id, Params<R> &Q) -> pff_status {
+    float best = 1e30f;
+    int bestv = 0;
+    for (int v = 0; v < kNumVariants; ++v) {
+      PFF_TRY(launch_v<R>(m, id, v, Q, s));  // warm-up (instruction cache, TLB)
+      float tmin = 1e30f;
+      for (int r = 0; r < 3; ++r) {
+        k_read_flush<<<(unsigned)((nflush + 255) / 256), 256, 0, s>>>(fb, nflush, sink);
+        cudaEventRecord(e0, s);
+        PFF_TRY(launch_v<R>(m, id, v, Q, s));
+        cudaEventRecord(e1, s);
+        CUDA_TRY(cudaEventSynchronize(e1));
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        tmin = std::min(tmin, t);
+      }
+      m->tune_ms[id][v] = tmin;
+      if (tmin < best) {
+        best = tmin;
+        bestv = v;
+      }
+    }
+    m->tuned_var[id] = bestv;
+    m->tuned[id] = true;
+    m->var[id] = bestv;
+    return PFF_OK;
+  };
+  P.use_cond = 0;
+  if (with_force && !m->tuned[KP_FORCE]) {
+    Params<R> Q = P;
+    TUNE_TRY(cudaMalloc(&sv, m->N * sizeof(R2)));
+    TUNE_TRY(cudaMalloc(&sa, m->N * sizeof(R2)));
+    TUNE_TRY(cudaMalloc(&sH, m->Ne * sizeof(double)));
+    TUNE_TRY(cudaMemcpyAsync(sv, P.v, m->N * sizeof(R2), cudaMemcpyDeviceToDevice, s));
+    TUNE_TRY(cudaMemcpyAsync(sa, P.a, m->N * sizeof(R2), cudaMemcpyDeviceToDevice, s));
+    TUNE_TRY(cudaMemcpyAsync(sH, P.H, m->Ne * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (sizeof(R) == 4) {
+      TUNE_TRY(cudaMalloc(&sHf, m->Ne * sizeof(float)));
+      TUNE_TRY(cudaMemcpyAsync(sHf, m->Hf, m->Ne * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    }
+    Q.v = sv;
+    Q.a = sa;
+    Q.H = sH;
+    Q.Hf = sHf;
+    Q.t_next = P.dt;
+    Q.step_ctr = nullptr;
+    res = time_variants(KP_FORCE, Q);
+  }
+  if (res == PFF_OK && with_damage && !m->tuned[KP_RHS]) res = time_variants(KP_RHS, P);
+  if (res == PFF_OK && with_damage && !m->tuned[KP_MATVEC]) {
+    res = launch<R>(m, KP_RHS, P, s);  // a fresh right-hand side sets up z, p and beta = 0
+    if (res == PFF_OK) res = time_variants(KP_MATVEC, P);
+  }
+  for (int id : ids)
+    if (m->tuned[id]) m->var[id] = m->tuned_var[id];
+  cudaStreamSynchronize(s);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cleanup();
+#undef TUNE_TRY
+  return res;
+}
+
 // Host-polled variant of the same solve (debugging / PFF_LOOP_HOST).
 template <typename R>
-static pff_status solve_host_loop(Params<R> P, int64_t N, int block, cudaStream_t s) {
-  const unsigned G = grid_for(N, block);
+static pff_status solve_host_loop(const pff_mesh *m, Params<R> P, cudaStream_t s) {
   P.use_cond = 0;
   SolveScalars hs;
-  k_dmg_rhs<R><<<G, block, 0, s>>>(P);
-  CUDA_TRY(cudaGetLastError());
+  PFF_TRY(launch<R>(m, KP_RHS, P, s));
   if (P.model == kAT1) {
     for (;;) {
-      k_at1_restart<R><<<G, block, 0, s>>>(P);
+      PFF_TRY(launch<R>(m, KP_RESTART, P, s));
       CUDA_TRY(cudaMemcpyAsync(&hs, P.sc, sizeof(hs), cudaMemcpyDeviceToHost, s));
       CUDA_TRY(cudaStreamSynchronize(s));
       if (hs.done) break;
       for (;;) {
-        k_cg_matvec<R><<<G, block, 0, s>>>(P);
-        k_cg_update<R><<<G, block, 0, s>>>(P);
+        PFF_TRY(launch<R>(m, KP_MATVEC, P, s));
+        PFF_TRY(launch<R>(m, KP_UPDATE, P, s));
         CUDA_TRY(cudaMemcpyAsync(&hs, P.sc, sizeof(hs), cudaMemcpyDeviceToHost, s));
         CUDA_TRY(cudaStreamSynchronize(s));
         if (hs.inner_done) break;
@@ -446,13 +698,11 @@ static pff_status solve_host_loop(Params<R> P, int64_t N, int block, cudaStream_
       CUDA_TRY(cudaMemcpyAsync(&hs, P.sc, sizeof(hs), cudaMemcpyDeviceToHost, s));
       CUDA_TRY(cudaStreamSynchronize(s));
       if (hs.done) break;
-      k_cg_matvec<R><<<G, block, 0, s>>>(P);
-      k_cg_update<R><<<G, block, 0, s>>>(P);
-      CUDA_TRY(cudaGetLastError());
+      PFF_TRY(launch<R>(m, KP_MATVEC, P, s));
+      PFF_TRY(launch<R>(m, KP_UPDATE, P, s));
     }
   }
-  k_dmg_finish<R><<<G, block, 0, s>>>(P);
-  CUDA_TRY(cudaGetLastError());
+  PFF_TRY(launch<R>(m, KP_FINISH, P, s));
   return PFF_OK;
 }
 
@@ -464,11 +714,12 @@ static pff_status damage_solve_t(pff_mesh *m, const double *H, const void *dprev
   PFF_TRY(bind_history<R>(m, P, H, s));
   P.dprev = (const R *)dprev;
   P.dout = (R *)dout;
-  const int block = o.block > 0 ? o.block : m->block;
+  PFF_TRY(autotune<R>(m, o, P, false, true, s));
   if (o.loop_mode == PFF_LOOP_HOST) {
-    PFF_TRY(solve_host_loop<R>(P, m->N, block, s));
+    PFF_TRY(solve_host_loop<R>(m, P, s));
   } else {
-    std::vector<uint64_t> key = {(uint64_t)H, (uint64_t)dprev, (uint64_t)dout, (uint64_t)block,
+    std::vector<uint64_t> key = {(uint64_t)H, (uint64_t)dprev, (uint64_t)dout, (uint64_t)m->var[KP_RHS],
+                                 (uint64_t)m->var[KP_MATVEC],
                                  (uint64_t)o.cg_max_it, (uint64_t)o.max_restarts};
     uint64_t tb;
     std::memcpy(&tb, &o.cg_tol, 8);
@@ -482,7 +733,7 @@ static pff_status damage_solve_t(pff_mesh *m, const double *H, const void *dprev
         CUDA_TRY(cudaGraphConditionalHandleCreate(&P.cond_outer, g, 1, cudaGraphCondAssignDefault));
       P.use_cond = 1;
       cudaGraphNode_t last;
-      pff_status st = append_solve<R>(g, nullptr, P, m->N, block, &last);
+      pff_status st = append_solve<R>(m, g, nullptr, P, &last);
       if (st != PFF_OK) {
         cudaGraphDestroy(g);
         return st;
@@ -520,11 +771,10 @@ static pff_status step_explicit_t(pff_mesh *m, const pff_state *st, double t_nex
   P.Hr = sizeof(R) == 8 ? (const R *)st->H : (const R *)m->Hf;
   P.dt = dt;
   P.t_next = t_next;
-  const int block = o.block > 0 ? o.block : m->block;
-  const unsigned G = grid_for(m->N, block);
-  k_predict<R><<<G, block, 0, s>>>(P);
-  k_force<R><<<G, block, 0, s>>>(P);
-  CUDA_TRY(cudaGetLastError());
+  if (sizeof(R) == 4 && !m->tuned[KP_FORCE] && o.variant <= 0) PFF_TRY(bind_history<R>(m, P, st->H, s));
+  PFF_TRY(autotune<R>(m, o, P, true, false, s));
+  PFF_TRY(launch<R>(m, KP_PREDICT, P, s));
+  PFF_TRY(launch<R>(m, KP_FORCE, P, s));
   return PFF_OK;
 }
 
@@ -544,26 +794,26 @@ static pff_status run_t(pff_mesh *m, const pff_state *st, int64_t step0, int64_t
   P.dout = (R *)st->d;
   P.iters_log = iters_log ? iters_log - 2 * step0 : nullptr;  // indexed by absolute step
   P.track_work = o.energy_every > 0 ? 1 : 0;
-  const int block = o.block > 0 ? o.block : m->block;
-  const unsigned G = grid_for(m->N, block);
+  PFF_TRY(autotune<R>(m, o, P, true, true, s));
   CUDA_TRY(cudaMemcpyAsync(m->step_ctr, &step0, sizeof(int64_t), cudaMemcpyHostToDevice, s));
   if (step0 == 0) CUDA_TRY(cudaMemsetAsync(m->wext, 0, sizeof(double), s));
   if (o.loop_mode == PFF_LOOP_HOST) {
     for (int64_t n = 0; n < nsteps; ++n) {
-      k_predict<R><<<G, block, 0, s>>>(P);
-      k_force<R><<<G, block, 0, s>>>(P);
-      PFF_TRY(solve_host_loop<R>(P, m->N, block, s));
+      PFF_TRY(launch<R>(m, KP_PREDICT, P, s));
+      PFF_TRY(launch<R>(m, KP_FORCE, P, s));
+      PFF_TRY(solve_host_loop<R>(m, P, s));
       if (energy_log && o.energy_every > 0 && (n + 1) % o.energy_every == 0) {
         Params<R> E = P;
         E.energy_out = energy_log + 4 * n;
-        k_energies<R><<<G, block, 0, s>>>(E);
+        PFF_TRY(launch<R>(m, KP_ENERGIES, E, s));
       }
     }
     CUDA_TRY(cudaGetLastError());
     return PFF_OK;
   }
   std::vector<uint64_t> key = {(uint64_t)st->u, (uint64_t)st->v, (uint64_t)st->a, (uint64_t)st->d,
-                               (uint64_t)st->H, (uint64_t)block, (uint64_t)o.cg_max_it,
+                               (uint64_t)st->H, (uint64_t)o.cg_max_it, (uint64_t)m->var[KP_FORCE],
+                               (uint64_t)m->var[KP_RHS], (uint64_t)m->var[KP_MATVEC],
                                (uint64_t)o.max_restarts, (uint64_t)P.iters_log, (uint64_t)P.track_work};
   uint64_t b1, b2, b3;
   std::memcpy(&b1, &o.cg_tol, 8);
@@ -581,9 +831,9 @@ static pff_status run_t(pff_mesh *m, const pff_state *st, int64_t step0, int64_t
       CUDA_TRY(cudaGraphConditionalHandleCreate(&P.cond_outer, g, 1, cudaGraphCondAssignDefault));
     P.use_cond = 1;
     cudaGraphNode_t n_pr, n_f, last;
-    pff_status stt = add_kernel<R>(g, {}, k_predict<R>, G, block, P, &n_pr);
-    if (stt == PFF_OK) stt = add_kernel<R>(g, {n_pr}, k_force<R>, G, block, P, &n_f);
-    if (stt == PFF_OK) stt = append_solve<R>(g, n_f, P, m->N, block, &last);
+    pff_status stt = add_kernel<R>(m, g, {}, KP_PREDICT, P, &n_pr);
+    if (stt == PFF_OK) stt = add_kernel<R>(m, g, {n_pr}, KP_FORCE, P, &n_f);
+    if (stt == PFF_OK) stt = append_solve<R>(m, g, n_f, P, &last);
     if (stt != PFF_OK) {
       cudaGraphDestroy(g);
       return stt;
@@ -601,8 +851,7 @@ static pff_status run_t(pff_mesh *m, const pff_state *st, int64_t step0, int64_t
     if (energy_log && o.energy_every > 0 && (n + 1) % o.energy_every == 0) {
       Params<R> E = P;
       E.energy_out = energy_log + 4 * n;
-      k_energies<R><<<G, block, 0, s>>>(E);
-      CUDA_TRY(cudaGetLastError());
+      PFF_TRY(launch<R>(m, KP_ENERGIES, E, s));
     }
   }
   return PFF_OK;
@@ -618,9 +867,7 @@ static pff_status energies_t(pff_mesh *m, const pff_state *st, double *out, cuda
   P.d = (R *)st->d;
   P.H = st->H;
   P.Hr = sizeof(R) == 8 ? (const R *)st->H : (const R *)m->Hf;
-  const int block = m->block;
-  k_energies<R><<<grid_for(m->N, block), block, 0, s>>>(P);
-  CUDA_TRY(cudaGetLastError());
+  PFF_TRY(launch<R>(m, KP_ENERGIES, P, s));
   double h[4];
   CUDA_TRY(cudaMemcpyAsync(h, m->energy, sizeof(h), cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaStreamSynchronize(s));
@@ -657,8 +904,7 @@ static pff_status profile_t(pff_mesh *m, const pff_state *st, double dt, const p
   P.dprev = (const R *)st->d;
   P.dout = (R *)st->d;
   P.use_cond = 0;
-  const int block = o.block > 0 ? o.block : m->block;
-  const unsigned G = grid_for(m->N, block);
+  PFF_TRY(autotune<R>(m, o, P, true, true, s));
   const size_t nflush = (size_t)64 << 20;  // 64 Mi float4 = 1 GiB
   float4 *fb = nullptr;
   CUDA_TRY(cudaMalloc(&fb, nflush * sizeof(float4) + 16));
@@ -666,24 +912,15 @@ static pff_status profile_t(pff_mesh *m, const pff_state *st, double dt, const p
   float *sink = (float *)(fb + nflush);
   std::vector<cudaEvent_t> ev(2 * reps);
   for (auto &e : ev) CUDA_TRY(cudaEventCreate(&e));
-  auto launch = [&](int k) {
-    switch (k) {
-      case 0: k_predict<R><<<G, block, 0, s>>>(P); break;
-      case 1: k_force<R><<<G, block, 0, s>>>(P); break;
-      case 2: k_dmg_rhs<R><<<G, block, 0, s>>>(P); break;
-      case 3: k_cg_matvec<R><<<G, block, 0, s>>>(P); break;
-      case 4: k_cg_update<R><<<G, block, 0, s>>>(P); break;
-      case 5: k_dmg_finish<R><<<G, block, 0, s>>>(P); break;
-      case 6: k_energies<R><<<G, block, 0, s>>>(P); break;
-    }
-  };
+  const int order[7] = {KP_PREDICT, KP_FORCE, KP_RHS, KP_MATVEC, KP_UPDATE, KP_FINISH, KP_ENERGIES};
+  auto run1 = [&](int k) { (void)launch<R>(m, order[k], P, s); };
   pff_status res = PFF_OK;
   for (int k = 0; k < 7 && res == PFF_OK; ++k) {
-    if (k == 3) launch(2);  // matvec/update need a prepared solve
+    if (k == 3) run1(2);  // matvec/update need a prepared solve
     for (int r = 0; r < reps; ++r) {
       k_flush<<<(unsigned)((nflush + 255) / 256), 256, 0, s>>>(fb, nflush, sink);
       cudaEventRecord(ev[2 * r], s);
-      launch(k);
+      run1(k);
       cudaEventRecord(ev[2 * r + 1], s);
     }
     cudaError_t e = cudaStreamSynchronize(s);
@@ -709,17 +946,17 @@ static pff_status mesh_build_t(pff_mesh *m, const double *xy_d, const int32_t *t
                                const uint8_t *notch_d, unsigned long long *scratch) {
   const int64_t N = m->N, Ne = m->Ne;
   const int blk = 256;
-  PFF_TRY(dalloc((typename V<R>::T4 **)&m->grad, Ne));
-  PFF_TRY(dalloc((R **)&m->area, Ne));
+  PFF_TRY(dalloc((ERec<R> **)&m->rec, Ne));
   PFF_TRY(dalloc((typename V<R>::T2 **)&m->fext, N));
   PFF_TRY(dalloc((R **)&m->minv, N));
-  PFF_TRY(dalloc((R **)&m->z, N));
-  PFF_TRY(dalloc((R **)&m->p, N));
-  PFF_TRY(dalloc((R **)&m->q, N));
-  PFF_TRY(dalloc((R **)&m->dinv, N));
+  PFF_TRY(dalloc((typename V<R>::T2 **)&m->pz, N + 2));
+  PFF_TRY(dalloc((R **)&m->q, N + 2));
+  PFF_TRY(dalloc((R **)&m->dinv, N + 2));
+  CUDA_TRY(cudaMemset(m->pz, 0, (N + 2) * sizeof(typename V<R>::T2)));
+  CUDA_TRY(cudaMemset(m->q, 0, (N + 2) * sizeof(R)));
+  CUDA_TRY(cudaMemset(m->dinv, 0, (N + 2) * sizeof(R)));
   if (sizeof(R) == 4) PFF_TRY(dalloc(&m->Hf, Ne));
-  k_geometry<R><<<grid_for(Ne, blk), blk>>>(xy_d, tri_d, Ne, m->tri, (typename V<R>::T4 *)m->grad,
-                                             (R *)m->area, m->area_d, scratch, scratch + 1);
+  k_geometry<R><<<grid_for(Ne, blk), blk>>>(xy_d, tri_d, Ne, (ERec<R> *)m->rec, m->area_d, scratch, scratch + 1);
   k_node_init<R><<<grid_for(N, blk), blk>>>(fd, notch_d, N, (typename V<R>::T2 *)m->fext, m->flags);
   CUDA_TRY(cudaGetLastError());
   return PFF_OK;
@@ -783,9 +1020,9 @@ pff_status pff_mesh_create(int64_t N, const double *xy, int64_t Ne, const int32_
   STEP(dalloc(&tri_d, 3 * Ne));
   STEP(dalloc(&fd, 2 * N));
   STEP(dalloc(&scratch, 2));
-  STEP(dalloc(&m->tri, Ne));
   STEP(dalloc(&m->area_d, Ne));
-  STEP(dalloc(&m->flags, N));
+  STEP(dalloc(&m->flags, N + 2));  // padded to an even length, padding nodes fixed
+  CSTEP(cudaMemset(m->flags + N, kNotch, 2));
   STEP(dalloc(&m->ptr, N + 1));
   STEP(dalloc(&m->ent, 3 * Ne));
   STEP(dalloc(&cnt, N));
@@ -830,12 +1067,20 @@ pff_status pff_mesh_create(int64_t N, const double *xy, int64_t Ne, const int32_
   k_fill<<<grid_for(Ne, blk), blk>>>(tri_d, Ne, m->ptr, cnt, m->ent);
   k_sort_segments<<<grid_for(N, blk), blk>>>(m->ptr, N, m->ent);
   CSTEP(cudaGetLastError());
+  CSTEP(cudaDeviceSynchronize());
+  if (precision == PFF_FP64)
+    STEP(configure<double>(m));
+  else
+    STEP(configure<float>(m));
   // workspaces
   const int64_t maxblocks = (N + 31) / 32;
-  STEP(dalloc(&m->x, N));
-  STEP(dalloc(&m->r, N));
-  STEP(dalloc(&m->b, N));
-  STEP(dalloc(&m->freef, N));
+  STEP(dalloc(&m->x, N + 2));
+  STEP(dalloc(&m->r, N + 2));
+  STEP(dalloc(&m->b, N + 2));
+  STEP(dalloc(&m->freef, N + 2));
+  CSTEP(cudaMemset(m->x, 0, (N + 2) * sizeof(double)));
+  CSTEP(cudaMemset(m->r, 0, (N + 2) * sizeof(double)));
+  CSTEP(cudaMemset(m->freef, 0, N + 2));
   STEP(dalloc(&m->part, 4 * maxblocks));
   STEP(dalloc(&m->energy, 4));
   STEP(dalloc(&m->wext, 1));
@@ -911,11 +1156,11 @@ pff_status pff_mesh_get_geometry(const pff_mesh *m, double *area, double *grad, 
   if (minv) PFF_TRY(dalloc(&mi, m->N));
   const int blk = 256;
   if (m->prec == PFF_FP64)
-    k_geom_out<double><<<grid_for(n, blk), blk>>>((const dbl4 *)m->grad, m->area_d, (const double2 *)m->fext,
+    k_geom_out<double><<<grid_for(n, blk), blk>>>((const ERec<double> *)m->rec, m->area_d, (const double2 *)m->fext,
                                                    m->has_mat ? (const double *)m->minv : nullptr, m->N, m->Ne,
                                                    a, g, f, mi);
   else
-    k_geom_out<float><<<grid_for(n, blk), blk>>>((const float4 *)m->grad, m->area_d, (const float2 *)m->fext,
+    k_geom_out<float><<<grid_for(n, blk), blk>>>((const ERec<float> *)m->rec, m->area_d, (const float2 *)m->fext,
                                                   m->has_mat ? (const float *)m->minv : nullptr, m->N, m->Ne, a,
                                                   g, f, mi);
   cudaError_t e = cudaDeviceSynchronize();
@@ -994,5 +1239,16 @@ pff_status pff_profile_kernels(pff_mesh *m, const pff_state *st, double dt, cons
                              : profile_t<float>(m, st, dt, o, reps, ms_out, s);
 }
 
+
+pff_status pff_mesh_schedule(const pff_mesh *m, int32_t *variant, float *tune_ms) {
+  if (!m) return fail(PFF_ERR_ARG, "null mesh");
+  const int ids[3] = {KP_FORCE, KP_RHS, KP_MATVEC};
+  for (int k = 0; k < 3; ++k) {
+    if (variant) variant[k] = m->var[ids[k]] + 1;
+    if (tune_ms)
+      for (int v = 0; v < kNumVariants; ++v) tune_ms[k * kNumVariants + v] = m->tune_ms[ids[k]][v];
+  }
+  return PFF_OK;
+}
 
 }  // extern "C"

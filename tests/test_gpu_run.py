@@ -115,3 +115,32 @@ def test_energy_log_and_determinism(orc, pff):
     rows = np.arange(9, nsteps, 10)
     assert np.allclose(runs[0][1][rows], r["energies"][rows], rtol=1e-8)
     assert np.all(np.isnan(runs[0][1][0]))
+
+
+def test_schedules_bit_identical(orc, pff):
+    """Every gather schedule (entry-parallel, node-centric with 1..4 gathers
+    in flight) sums in the same order: identical bits after 30 steps."""
+    import torch
+    outs = []
+    for var in range(1, 6):
+        for prec in ("fp32",):
+            c, om, gm, dt = _setup(pff, orc, prec=prec)
+            st = gm.new_state()
+            gm.run(st, 30, opts=pff.options(variant=var))
+            torch.cuda.synchronize()
+            outs.append(st)
+    for st in outs[1:]:
+        for k in ("u", "v", "a", "d", "H"):
+            assert torch.equal(st[k], outs[0][k]), k
+
+
+def test_autotuner_choice_reported(orc, pff):
+    import torch
+    c, om, gm, dt = _setup(pff, orc, prec="fp32")
+    st = gm.new_state()
+    gm.run(st, 2)
+    torch.cuda.synchronize()
+    var, ms = gm.schedule()
+    for k in ("force", "rhs", "matvec"):
+        assert 1 <= var[k] <= 5
+        assert ms[k][var[k] - 1] == min(ms[k]) > 0
