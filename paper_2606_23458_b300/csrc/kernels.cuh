@@ -70,7 +70,8 @@ struct SolveScalars {
   double rr;      // ||r||^2 (free rows, scaled)
   double pq;
   int32_t iters, restarts, status, done;
-  int32_t projected, inner_done, pad0, pad1;
+  int32_t projected, inner_done;
+  float alpha_f, beta_f;  // FP32 copies read by every thread in FP32 mode
 };
 
 // Everything a kernel needs, passed by value (graph-captured).
@@ -102,9 +103,14 @@ template <typename R> struct Params {
   double *H;         // history (always FP64)
   const R *Hr;       // history in the kernel precision (H itself, or Hf)
   float *Hf;         // FP32 mirror of H kept by k_force (FP32 mode only)
-  // time
-  double dt, t_ramp, t_next; // t_next used when step_ctr == nullptr
-  const int64_t *step_ctr;   // device step counter n (t_next = (n+1) dt)
+  // time and load: the traction scale S(t) of Eq. (smooth_traction_ramp)
+  // is evaluated on the host.  Single step: S_prev = S(t_n), S_next =
+  // S(t_n+1).  Graph-run steps: Stab[k] = S(t_{n0+k}) for the run's k-th
+  // step, k read from the device counter step_ctr.
+  double dt, t_ramp;
+  double S_prev, S_next;
+  const double *Stab;
+  const int64_t *step_ctr;
   // damage solve
   const R *dprev;
   R *dout;
@@ -160,6 +166,8 @@ template <> struct Acc<double> {
   static __device__ __forceinline__ T shfl(T v, int o) { return __shfl_down_sync(0xffffffffu, v, o); }
   static __device__ __forceinline__ double to_d(T v) { return v; }
   static __device__ __forceinline__ T one() { return 1.0; }
+  static __device__ __forceinline__ void store(double *p, T v) { *p = v; }
+  static __device__ __forceinline__ T load(const double *p) { return __ldcg(p); }
 };
 template <> struct Acc<float> {
   typedef DF T;
@@ -171,32 +179,43 @@ template <> struct Acc<float> {
   }
   static __device__ __forceinline__ double to_d(T v) { return (double)v.hi + (double)v.lo; }
   static __device__ __forceinline__ T one() { return DF{1.f, 0.f}; }
+  static __device__ __forceinline__ void store(double *p, T v) {
+    *reinterpret_cast<float2 *>(p) = make_float2(v.hi, v.lo);
+  }
+  static __device__ __forceinline__ T load(const double *p) {
+    const float2 f = __ldcg(reinterpret_cast<const float2 *>(p));
+    return DF{f.x, f.y};
+  }
 };
 
-// Block-reduces NV accumulators, publishes one FP64 partial per block and
-// returns true in every thread of the last block to arrive; that block
-// then finds the totals in `tot` (shared).  Fixed summation order.
+// Block-reduces NV accumulators, publishes one partial per block and
+// returns true in every thread of the last block to arrive; that block then
+// finds the totals (converted to FP64) in `tot` (shared).  The whole
+// reduction stays in the accumulator type (double-word FP32 in FP32 mode:
+// B300 issues an FP64 warp instruction in ~17 SM cycles), with one
+// conversion at the end.  Fixed summation order.
 template <typename R, int NV>
 __device__ __forceinline__ bool reduce_last(typename Acc<R>::T (&v)[NV], double *part,
                                             unsigned int *ticket, double *tot) {
   typedef Acc<R> A;
-  __shared__ double sh[32][NV];
+  typedef typename A::T T;
+  __shared__ T sh[32][NV];
   __shared__ bool last;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int nw = (blockDim.x + 31) >> 5;
 #pragma unroll
   for (int k = 0; k < NV; ++k) {
-    typename A::T s = v[k];
+    T s = v[k];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s = A::add(s, A::shfl(s, o));
-    if (lane == 0) sh[wid][k] = A::to_d(s);
+    if (lane == 0) sh[wid][k] = s;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     for (int k = 0; k < NV; ++k) {
-      double s = 0.0;
-      for (int w = 0; w < nw; ++w) s += sh[w][k];
-      part[(size_t)blockIdx.x * NV + k] = s;
+      T s = sh[0][k];
+      for (int w = 1; w < nw; ++w) s = A::add(s, sh[w][k]);
+      A::store(&part[(size_t)blockIdx.x * NV + k], s);
     }
     __threadfence();
     const unsigned int t = atomicAdd(ticket, 1u);
@@ -207,40 +226,49 @@ __device__ __forceinline__ bool reduce_last(typename Acc<R>::T (&v)[NV], double 
   __threadfence();
   // the last block sums the partials: thread j takes blocks j, j+B, ...;
   // eight loads are issued before they are added (one L2 round trip each)
-  double acc[NV];
+  T acc[NV];
 #pragma unroll
   for (int k = 0; k < NV; ++k) {
-    acc[k] = 0.0;
+    acc[k] = A::zero();
     for (int j0 = threadIdx.x; j0 < (int)gridDim.x; j0 += 8 * blockDim.x) {
-      double buf[8];
+      T buf[8];
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         const int j = j0 + u * blockDim.x;
-        buf[u] = j < (int)gridDim.x ? __ldcg(&part[(size_t)j * NV + k]) : 0.0;
+        buf[u] = j < (int)gridDim.x ? A::load(&part[(size_t)j * NV + k]) : A::zero();
       }
 #pragma unroll
-      for (int u = 0; u < 8; ++u) acc[k] += buf[u];
+      for (int u = 0; u < 8; ++u) acc[k] = A::add(acc[k], buf[u]);
     }
   }
   __syncthreads();
 #pragma unroll
   for (int k = 0; k < NV; ++k) {
-    double s = acc[k];
+    T s = acc[k];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    for (int o = 16; o > 0; o >>= 1) s = A::add(s, A::shfl(s, o));
     if (lane == 0) sh[wid][k] = s;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     for (int k = 0; k < NV; ++k) {
-      double s = 0.0;
-      for (int w = 0; w < nw; ++w) s += sh[w][k];
-      tot[k] = s;
+      T s = sh[0][k];
+      for (int w = 1; w < nw; ++w) s = A::add(s, sh[w][k]);
+      tot[k] = A::to_d(s);
     }
     *ticket = 0u;
   }
   __syncthreads();
   return true;
+}
+
+// CG coefficients in the kernel precision (FP32 copies in FP32 mode, so no
+// thread converts from FP64).
+template <typename R> __device__ __forceinline__ R sc_alpha(const SolveScalars *S) {
+  return sizeof(R) == 4 ? (R)S->alpha_f : (R)S->alpha;
+}
+template <typename R> __device__ __forceinline__ R sc_beta(const SolveScalars *S) {
+  return sizeof(R) == 4 ? (R)S->beta_f : (R)S->beta;
 }
 
 template <typename R> __device__ __forceinline__ R rpos(R x) { return x > R(0) ? x : R(0); }
@@ -251,16 +279,11 @@ template <typename R> __device__ __forceinline__ R rneg(R x) { return x < R(0) ?
 __device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ double radd(double a, double b) { return __dadd_rn(a, b); }
 
-// Smooth traction ramp, Eq. (smooth_traction_ramp).
-__device__ __forceinline__ double ramp(double t, double tr) {
-  if (t <= 0.0) return 0.0;
-  if (t >= tr) return 1.0;
-  return 0.5 * (1.0 - cos(3.14159265358979323846 * t / tr));
-}
-
+// Load scale at the end (which = 1) or start (which = 0) of the step.
 template <typename R>
-__device__ __forceinline__ double step_time(const Params<R> &P) {
-  return P.step_ctr ? (double)(*P.step_ctr + 1) * P.dt : P.t_next;
+__device__ __forceinline__ double load_scale(const Params<R> &P, int which) {
+  if (P.step_ctr) return P.Stab[*P.step_ctr + which];
+  return which ? P.S_next : P.S_prev;
 }
 
 // IEEE-754 bit pattern of the double equal to a non-negative float (exact
@@ -390,8 +413,7 @@ __global__ void __launch_bounds__(256) k_predict(Params<R> P) {
     const R dt = (R)P.dt, h = R(0.5) * dt * dt;
     const R dux = dt * v.x + h * a.x, duy = dt * v.y + h * a.y;
     if (P.track_work && (P.flags[i] & kLoaded)) {
-      const double t1 = step_time(P), t0 = t1 - P.dt;
-      const double S = 0.5 * (ramp(t0, P.t_ramp) + ramp(t1, P.t_ramp));
+      const double S = 0.5 * (load_scale(P, 0) + load_scale(P, 1));
       typename Params<R>::R2 f = P.fext[i];
       w += S * ((double)f.x * dux + (double)f.y * duy);
     }
@@ -482,7 +504,7 @@ __global__ void __launch_bounds__(256) k_force_ep(Params<R> P) {
   typedef typename Params<R>::R2 R2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R2 *fc = reinterpret_cast<R2 *>(smem_raw);
-  const double S = ramp(step_time(P), P.t_ramp);
+  const double S = load_scale(P, 1);
   for (int b = blockIdx.x; b < P.nblk; b += gridDim.x) {
     int i0, i1, k0, k1;
     block_nodes(P, b, i0, i1, k0, k1);
@@ -515,7 +537,7 @@ __global__ void __launch_bounds__(256) k_force_ep(Params<R> P) {
 // bit-identical to the entry-parallel schedule.
 template <typename R, int U>
 __global__ void __launch_bounds__(256) k_force_nc(Params<R> P) {
-  const double S = ramp(step_time(P), P.t_ramp);
+  const double S = load_scale(P, 1);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.N; i += gridDim.x * blockDim.x) {
     R fx = 0, fy = 0;
     for (int k = 0; k < P.D; k += U) {
@@ -633,6 +655,8 @@ __device__ __forceinline__ void rhs_finish(const Params<R> &P, const double *tot
   S.rho = tot[2];
   S.beta = 0.0;
   S.alpha = 0.0;
+  S.beta_f = 0.f;
+  S.alpha_f = 0.f;
   S.iters = 0;
   S.restarts = 0;
   S.status = kStOk;
@@ -744,6 +768,7 @@ __device__ __forceinline__ void matvec_finish(const Params<R> &P, const double *
   SolveScalars &S = *P.sc;
   S.pq = tot[0];
   S.alpha = tot[0] != 0.0 ? S.rho / tot[0] : 0.0;
+  S.alpha_f = (float)S.alpha;
 }
 
 // q = A p_new on free rows and the reduction p_new . q -> alpha = rho/(p.q).
@@ -754,7 +779,7 @@ __global__ void __launch_bounds__(256) k_cg_matvec_ep(Params<R> P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R *cq = reinterpret_cast<R *>(smem_raw);
   typename AC::T vals[1] = {AC::zero()};
-  const R beta = (R)P.sc->beta;
+  const R beta = sc_beta<R>(P.sc);
   for (int b = blockIdx.x; b < P.nblk; b += gridDim.x) {
     int i0, i1, k0, k1;
     block_nodes(P, b, i0, i1, k0, k1);
@@ -786,7 +811,7 @@ template <typename R, int U>
 __global__ void __launch_bounds__(256) k_cg_matvec_nc(Params<R> P) {
   typedef Acc<R> AC;
   typename AC::T vals[1] = {AC::zero()};
-  const R beta = (R)P.sc->beta;
+  const R beta = sc_beta<R>(P.sc);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.N; i += gridDim.x * blockDim.x) {
     R q = 0;
     if (!is_fixed(P, i)) {
@@ -869,6 +894,7 @@ __device__ __forceinline__ void update_finish(const Params<R> &P, const double *
       }
     }
     S.beta = S.rho != 0.0 ? tot[1] / S.rho : 0.0;
+    S.beta_f = (float)S.beta;
     S.rho = tot[1];
   }
   S.inner_done = stop ? 1 : 0;
@@ -880,8 +906,8 @@ __global__ void __launch_bounds__(256) k_cg_update(Params<R> P) {
   typedef typename Params<R>::R2 R2;
   typedef Acc<R> AC;
   typename AC::T vals[3] = {AC::zero(), AC::zero(), AC::zero()};
-  const R beta = (R)P.sc->beta;
-  const R alpha = (R)P.sc->alpha;
+  const R beta = sc_beta<R>(P.sc);
+  const R alpha = sc_alpha<R>(P.sc);
   bool proj = false;
   const int stride = gridDim.x * blockDim.x;
   if constexpr (sizeof(R) == 4) {
@@ -984,6 +1010,7 @@ __global__ void __launch_bounds__(256) k_at1_restart(Params<R> P) {
     S.rr = tot[0];
     S.rho = tot[1];
     S.beta = 0.0;
+    S.beta_f = 0.f;
     S.projected = 0;
     const bool conv = sqrt(tot[0]) <= P.tol * S.bn;
     bool stop = conv;

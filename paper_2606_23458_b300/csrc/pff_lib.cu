@@ -27,6 +27,13 @@ static pff_status fail(pff_status s, const std::string &msg) {
   return s;
 }
 
+// Smooth traction ramp S(t), Eq. (smooth_traction_ramp).
+static double ramp(double t, double tr) {
+  if (t <= 0.0) return 0.0;
+  if (t >= tr) return 1.0;
+  return 0.5 * (1.0 - std::cos(3.14159265358979323846 * t / tr));
+}
+
 #define CUDA_TRY(call)                                                           \
   do {                                                                           \
     cudaError_t e_ = (call);                                                     \
@@ -267,7 +274,9 @@ struct pff_mesh {
   unsigned int *ticket = nullptr;
   SolveScalars *sc = nullptr;
   int32_t *status_word = nullptr;
-  int64_t *step_ctr = nullptr;
+  int64_t *step_ctr = nullptr;   // step index k within the current run
+  double *stab = nullptr;        // S(t) per step of the current run
+  int64_t stab_cap = 0;
   GraphCache solve_g, step_g;
   int block = 256;
   // launch configuration (kernel id -> grid, dynamic shared memory)
@@ -294,7 +303,7 @@ static void mesh_free(pff_mesh *m) {
   free_graph(m->step_g);
   void *ptrs[] = {m->ptr, m->ent, m->ell, m->rec, m->fext, m->minv, m->area_d, m->flags,
                   m->x, m->r, m->b, m->part, m->energy, m->wext, m->pz, m->q, m->dinv,
-                  m->Hf, m->freef, m->ticket, m->sc, m->status_word, m->step_ctr};
+                  m->Hf, m->freef, m->ticket, m->sc, m->status_word, m->step_ctr, m->stab};
   for (void *q : ptrs)
     if (q) cudaFree(q);
   delete m;
@@ -654,7 +663,8 @@ static pff_status autotune(pff_mesh *m, const pff_options &o, Params<R> P, bool 
     Q.a = sa;
     Q.H = sH;
     Q.Hf = sHf;
-    Q.t_next = P.dt;
+    Q.S_prev = 0.0;
+    Q.S_next = 1.0;
     Q.step_ctr = nullptr;
     res = time_variants(KP_FORCE, Q);
   }
@@ -770,7 +780,8 @@ static pff_status step_explicit_t(pff_mesh *m, const pff_state *st, double t_nex
   P.H = st->H;
   P.Hr = sizeof(R) == 8 ? (const R *)st->H : (const R *)m->Hf;
   P.dt = dt;
-  P.t_next = t_next;
+  P.S_next = ramp(t_next, o.t_ramp);
+  P.S_prev = ramp(t_next - dt, o.t_ramp);
   if (sizeof(R) == 4 && !m->tuned[KP_FORCE] && o.variant <= 0) PFF_TRY(bind_history<R>(m, P, st->H, s));
   PFF_TRY(autotune<R>(m, o, P, true, false, s));
   PFF_TRY(launch<R>(m, KP_PREDICT, P, s));
@@ -790,12 +801,29 @@ static pff_status run_t(pff_mesh *m, const pff_state *st, int64_t step0, int64_t
   P.dt = dt;
   P.step_ctr = m->step_ctr;
   P.step_inc = m->step_ctr;
+  if (m->stab_cap < nsteps + 1) {
+    if (m->stab) cudaFree(m->stab);
+    m->stab = nullptr;
+    m->stab_cap = 0;
+    PFF_TRY(dalloc(&m->stab, nsteps + 1));
+    m->stab_cap = nsteps + 1;
+    free_graph(m->step_g);
+  }
+  {
+    std::vector<double> S(nsteps + 1);
+    for (int64_t k = 0; k <= nsteps; ++k) S[k] = ramp((double)(step0 + k) * dt, o.t_ramp);
+    CUDA_TRY(cudaMemcpyAsync(m->stab, S.data(), S.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaStreamSynchronize(s));  // S lives on this stack frame
+  }
+  P.Stab = m->stab;
   P.dprev = (const R *)st->d;
   P.dout = (R *)st->d;
-  P.iters_log = iters_log ? iters_log - 2 * step0 : nullptr;  // indexed by absolute step
+  P.iters_log = iters_log;  // indexed by the step within this run
   P.track_work = o.energy_every > 0 ? 1 : 0;
   PFF_TRY(autotune<R>(m, o, P, true, true, s));
-  CUDA_TRY(cudaMemcpyAsync(m->step_ctr, &step0, sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  const int64_t zero = 0;
+  CUDA_TRY(cudaMemcpyAsync(m->step_ctr, &zero, sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
   if (step0 == 0) CUDA_TRY(cudaMemsetAsync(m->wext, 0, sizeof(double), s));
   if (o.loop_mode == PFF_LOOP_HOST) {
     for (int64_t n = 0; n < nsteps; ++n) {
@@ -814,14 +842,13 @@ static pff_status run_t(pff_mesh *m, const pff_state *st, int64_t step0, int64_t
   std::vector<uint64_t> key = {(uint64_t)st->u, (uint64_t)st->v, (uint64_t)st->a, (uint64_t)st->d,
                                (uint64_t)st->H, (uint64_t)o.cg_max_it, (uint64_t)m->var[KP_FORCE],
                                (uint64_t)m->var[KP_RHS], (uint64_t)m->var[KP_MATVEC],
-                               (uint64_t)o.max_restarts, (uint64_t)P.iters_log, (uint64_t)P.track_work};
-  uint64_t b1, b2, b3;
+                               (uint64_t)o.max_restarts, (uint64_t)P.iters_log, (uint64_t)P.track_work,
+                               (uint64_t)m->stab};
+  uint64_t b1, b2;
   std::memcpy(&b1, &o.cg_tol, 8);
   std::memcpy(&b2, &dt, 8);
-  std::memcpy(&b3, &o.t_ramp, 8);
   key.push_back(b1);
   key.push_back(b2);
-  key.push_back(b3);
   if (!m->step_g.exec || m->step_g.key != key) {
     free_graph(m->step_g);
     cudaGraph_t g;
@@ -900,7 +927,8 @@ static pff_status profile_t(pff_mesh *m, const pff_state *st, double dt, const p
   P.d = (R *)st->d;
   PFF_TRY(bind_history<R>(m, P, st->H, s));
   P.dt = dt;
-  P.t_next = dt;
+  P.S_prev = 0.0;
+  P.S_next = ramp(dt, o.t_ramp);
   P.dprev = (const R *)st->d;
   P.dout = (R *)st->d;
   P.use_cond = 0;
