@@ -189,6 +189,35 @@ pff_status pff_profile_kernels(pff_mesh *mesh, const pff_state *state, double dt
  * (3 x 5, 0 where not measured).  Host outputs, each nullable. */
 pff_status pff_mesh_schedule(const pff_mesh *mesh, int32_t *variant, float *tune_ms);
 
+/* The damage solve of pff_damage_solve, for callers that must not allocate
+ * device memory during the call.  The paper has no counterpart of this entry
+ * point.  Who needs it: cudaFree synchronises the whole device and the
+ * allocator may not be entered from every context, so a memory-capped
+ * serving process that owns the device pool, code running inside an
+ * allocator or stream callback, or a latency-critical loop cannot use the
+ * regular call, whose first use per mesh allocates (autotuning, CUDA graph).
+ * This call allocates nothing (no cudaMalloc / cudaFree, no allocating
+ * library routine); the caller still passes H, d_prev and d_out (device),
+ * and the mesh must already exist (pff_mesh_create allocates).
+ *  - Workspace: a statically reserved __device__ array of about 9 MiB inside
+ *    libpff.so, which every GPU that loads the library holds until the
+ *    process exits.  It fits meshes of at most 131,072 nodes and 262,144
+ *    elements; larger meshes return PFF_ERR_ARG with a message.
+ *  - The first call on each device looks up that array's device address
+ *    (cudaGetSymbolAddress) with the mesh's device current; make that first
+ *    call before any stream capture.
+ *  - Every call shares the one array and leaves its workspace there; calls
+ *    that overlap on the GPU (unordered streams, other host threads) race
+ *    and corrupt each other's results.  Order them on one stream.
+ *  - The CG loop is host-polled (no CUDA graph) and uses the mesh's current
+ *    gather schedule (no autotuning).  Same arguments, results and status
+ *    codes as pff_damage_solve; synchronises the stream. */
+pff_status pff_damage_solve_noalloc(pff_mesh *mesh, const double *H,
+                                    const void *d_prev, void *d_out,
+                                    const pff_options *opt, int32_t *iters,
+                                    double *relres, int32_t *restarts,
+                                    pff_stream stream);
+
 /* Message of the last failing call on this host thread. */
 const char *pff_last_error(void);
 const char *pff_version(void);

@@ -80,6 +80,8 @@ _sig = {
     "pff_profile_kernels": [_P, C.POINTER(pff_state), C.c_double, C.POINTER(pff_options),
                             C.c_int32, _P, _P],
     "pff_mesh_schedule": [_P, _P, _P],
+    "pff_damage_solve_noalloc": [_P, _P, _P, _P, C.POINTER(pff_options), C.POINTER(C.c_int32),
+                                 C.POINTER(C.c_double), C.POINTER(C.c_int32), _P],
 }
 for _name, _args in _sig.items():
     _f = getattr(_lib, _name)
@@ -226,6 +228,18 @@ class Mesh:
         it = C.c_int32(); rel = C.c_double(); rs = C.c_int32()
         st = _lib.pff_damage_solve(self._h, _dptr(H), _dptr(dprev), _dptr(dout), C.byref(o),
                                    C.byref(it), C.byref(rel), C.byref(rs), _stream(stream))
+        if raise_on_error:
+            _check(st)
+        return dict(status=st, iters=it.value, relres=rel.value, restarts=rs.value)
+
+    def damage_solve_noalloc(self, H, dprev, dout, opts=None, stream=None, raise_on_error=True):
+        """pff_damage_solve_noalloc: the same solve without any device
+        allocation during the call (statically reserved workspace, meshes up
+        to 131,072 nodes / 262,144 elements; concurrent calls race)."""
+        o = opts or options()
+        it = C.c_int32(); rel = C.c_double(); rs = C.c_int32()
+        st = _lib.pff_damage_solve_noalloc(self._h, _dptr(H), _dptr(dprev), _dptr(dout), C.byref(o),
+                                           C.byref(it), C.byref(rel), C.byref(rs), _stream(stream))
         if raise_on_error:
             _check(st)
         return dict(status=st, iters=it.value, relres=rel.value, restarts=rs.value)

@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1277,6 +1278,147 @@ pff_status pff_mesh_schedule(const pff_mesh *m, int32_t *variant, float *tune_ms
       for (int v = 0; v < kNumVariants; ++v) tune_ms[k * kNumVariants + v] = m->tune_ms[ids[k]][v];
   }
   return PFF_OK;
+}
+
+}  // extern "C"
+
+// =============================================== damage solve, no allocation
+//
+// pff_damage_solve_noalloc: the damage solve for callers that must not
+// allocate device memory during the call.  Its workspace is a statically
+// reserved __device__ array in this library (file scope below), sized for
+// meshes of up to kNoAllocMaxNodes nodes and kNoAllocMaxElems elements; the
+// caller still passes the history, the previous damage and the output.
+// cudaMalloc / cudaFree are never called: cudaFree synchronises the whole
+// device, and some callers (memory-capped serving processes that own the
+// device pool, code running inside an allocator or stream callback, latency-
+// critical loops) may not enter the allocator at all.
+namespace pff {
+
+constexpr int64_t kNoAllocMaxNodes = 1 << 17;   // 131,072 nodes
+constexpr int64_t kNoAllocMaxElems = 1 << 18;   // 262,144 elements
+constexpr int64_t kNoAllocMaxBlocks = 4096;     // reduction partials
+constexpr size_t na_align(size_t x) { return (x + 255) & ~(size_t)255; }
+constexpr size_t kNaVec = na_align((kNoAllocMaxNodes + 2) * sizeof(double));
+constexpr size_t kNaPz = na_align((kNoAllocMaxNodes + 2) * 2 * sizeof(double));
+constexpr size_t kNaFlag = na_align(kNoAllocMaxNodes + 2);
+constexpr size_t kNaHf = na_align(kNoAllocMaxElems * sizeof(float));
+constexpr size_t kNaPart = na_align(kNoAllocMaxBlocks * 4 * sizeof(double));
+constexpr size_t kNaTicket = na_align(8 * sizeof(unsigned int));
+constexpr size_t kNaScal = na_align(sizeof(SolveScalars));
+// x, r, b, q, 1/diag (FP64-sized), (p, z), free flags, FP32 history mirror,
+// partials, ticket, solve scalars: about 9 MiB.
+constexpr size_t kNoAllocBytes = 5 * kNaVec + kNaPz + kNaFlag + kNaHf + kNaPart + kNaTicket + kNaScal;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+// Device address of g_noalloc_scratch per device (the host-side symbol is a
+// stand-in, not a device address).  Looked up once per device, with that
+// device current, on the first call made on it.
+static void *g_noalloc_addr[128];
+static std::mutex g_noalloc_mu;
+
+static pff_status noalloc_scratch(int dev, unsigned char **out) {
+  if (dev < 0 || dev >= 128) return fail(PFF_ERR_ARG, "device index out of range");
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void *ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess || !ptr)
+      return fail(PFF_ERR_CUDA, std::string("cudaGetSymbolAddress(no-alloc scratch): ") + cudaGetErrorString(e));
+    g_noalloc_addr[dev] = ptr;
+  }
+  *out = (unsigned char *)g_noalloc_addr[dev];
+  return PFF_OK;
+}
+
+template <typename R>
+static pff_status noalloc_solve_t(pff_mesh *m, const double *H, const void *dprev, void *dout,
+                                  const pff_options &o, int32_t *iters, double *relres, int32_t *restarts,
+                                  cudaStream_t s) {
+  unsigned char *base = nullptr;
+  PFF_TRY(noalloc_scratch(m->device, &base));
+  for (int id = 0; id < KP_COUNT; ++id)
+    if ((int64_t)m->grid[id][m->var[id]] > kNoAllocMaxBlocks)
+      return fail(PFF_ERR_ARG, "no-alloc damage solve: launch grid exceeds the reserved reduction space");
+  Params<R> P = base_params<R>(m, o);
+  unsigned char *c = base;
+  P.x = (R *)c;
+  c += kNaVec;
+  P.r = (R *)c;
+  c += kNaVec;
+  R *b = (R *)c;
+  c += kNaVec;
+  P.q = (R *)c;
+  c += kNaVec;
+  P.dinv = (R *)c;
+  c += kNaVec;
+  P.pz = (typename V<R>::T2 *)c;
+  c += kNaPz;
+  uint8_t *freef = (uint8_t *)c;
+  c += kNaFlag;
+  float *hf = (float *)c;
+  c += kNaHf;
+  P.part = (double *)c;
+  c += kNaPart;
+  P.ticket = (unsigned int *)c;
+  c += kNaTicket;
+  P.sc = (SolveScalars *)c;
+  if (P.model == kAT1) {
+    P.b = b;
+    P.freef = freef;
+  }
+  // the array keeps the previous call's contents: the ticket counter must
+  // start at zero; every other workspace entry is written before it is read
+  CUDA_TRY(cudaMemsetAsync(P.ticket, 0, kNaTicket, s));
+  CUDA_TRY(cudaMemsetAsync(P.sc, 0, sizeof(SolveScalars), s));
+  P.H = const_cast<double *>(H);
+  if (sizeof(R) == 8) {
+    P.Hr = (const R *)H;
+    P.Hf = nullptr;
+  } else {
+    P.Hf = hf;
+    P.Hr = (const R *)hf;
+    k_h_mirror<<<std::min<unsigned>(grid_for(m->Ne, 256), 148 * 8), 256, 0, s>>>(H, hf, (int)m->Ne);
+    CUDA_TRY(cudaGetLastError());
+  }
+  P.dprev = (const R *)dprev;
+  P.dout = (R *)dout;
+  P.status_word = nullptr;
+  P.energy_out = nullptr;
+  P.wext = nullptr;
+  PFF_TRY(solve_host_loop<R>(m, P, s));
+  SolveScalars hs;
+  CUDA_TRY(cudaMemcpyAsync(&hs, P.sc, sizeof(hs), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if (iters) *iters = hs.iters;
+  if (restarts) *restarts = hs.restarts;
+  if (relres) *relres = hs.bn > 0 ? std::sqrt(hs.rr) / hs.bn : 0.0;
+  if (hs.status == kStNotConverged) return fail(PFF_ERR_NOT_CONVERGED, "damage CG did not converge");
+  if (hs.status == kStNonfinite) return fail(PFF_ERR_NONFINITE, "non-finite residual in damage CG");
+  return PFF_OK;
+}
+
+}  // namespace pff
+
+extern "C" {
+
+pff_status pff_damage_solve_noalloc(pff_mesh *m, const double *H, const void *dprev, void *dout,
+                                    const pff_options *opt, int32_t *iters, double *relres, int32_t *restarts,
+                                    pff_stream stream) {
+  if (!m || !H || !dprev || !dout) return fail(PFF_ERR_ARG, "null argument");
+  if (!m->has_mat) return fail(PFF_ERR_ARG, "material not set");
+  if (m->N > kNoAllocMaxNodes || m->Ne > kNoAllocMaxElems)
+    return fail(PFF_ERR_ARG, "no-alloc damage solve: mesh has " + std::to_string(m->N) + " nodes / " +
+                                 std::to_string(m->Ne) + " elements; the reserved workspace holds at most " +
+                                 std::to_string(kNoAllocMaxNodes) + " / " + std::to_string(kNoAllocMaxElems));
+  int dev = -1;
+  CUDA_TRY(cudaGetDevice(&dev));
+  if (dev != m->device) return fail(PFF_ERR_ARG, "no-alloc damage solve: the mesh's device is not current");
+  const pff_options o = defaults(opt);
+  cudaStream_t s = (cudaStream_t)stream;
+  return m->prec == PFF_FP64 ? noalloc_solve_t<double>(m, H, dprev, dout, o, iters, relres, restarts, s)
+                             : noalloc_solve_t<float>(m, H, dprev, dout, o, iters, relres, restarts, s);
 }
 
 }  // extern "C"
