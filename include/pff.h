@@ -163,6 +163,31 @@ pff_status pff_run(pff_mesh *mesh, const pff_state *state, int64_t step0,
                    int64_t nsteps, double dt, const pff_options *opt,
                    int32_t *iters_log, double *energy_log, pff_stream stream);
 
+/* Checkpointed run and its adjoint (Sec. 4: implicit differentiation of the
+ * damage solve, Eqs. implicit_forward_linear_system /
+ * implicit_adjoint_linear_system / implicit_gc_l0_element_term, with
+ * active-set masking; the reverse of the explicit mechanics; segment
+ * checkpointing with recompute).
+ * pff_ckpt_create: store for nsteps steps in segments of `every` steps:
+ *   device memory O(N (nsteps/every + every)) (checkpoints of u, v, a, d, H
+ *   at each segment start, a per-step tape for one segment, adjoint state).
+ * pff_run_ckpt: pff_run that also fills the checkpoints; nsteps must equal
+ *   the store's.  iters_log as in pff_run.
+ * pff_backward: given dL/dd at the final step (device, N, mesh precision),
+ *   recomputes each segment from its checkpoint (bit-identical to the
+ *   forward), reverses its steps and returns dL/dGc (host) for the AT2
+ *   model.  One adjoint CG solve per step with warm start.  Synchronises
+ *   the stream.  Errors: PFF_ERR_ARG (wrong mesh, unfilled store, AT1),
+ *   PFF_ERR_NOT_CONVERGED / PFF_ERR_NONFINITE from an adjoint solve. */
+typedef struct pff_ckpt pff_ckpt;
+pff_status pff_ckpt_create(pff_mesh *mesh, int64_t nsteps, int32_t every, pff_ckpt **out);
+void pff_ckpt_destroy(pff_ckpt *ckpt);
+pff_status pff_run_ckpt(pff_mesh *mesh, const pff_state *state, int64_t step0,
+                        int64_t nsteps, double dt, const pff_options *opt,
+                        pff_ckpt *ckpt, int32_t *iters_log, pff_stream stream);
+pff_status pff_backward(pff_mesh *mesh, pff_ckpt *ckpt, const void *dL_dd,
+                        const pff_options *opt, double *dL_dGc, pff_stream stream);
+
 /* Synchronises the stream and returns (and clears) the worst status the
  * device recorded since the last call (not converged, non-finite, timeout). */
 pff_status pff_sync_status(pff_mesh *mesh, pff_stream stream);

@@ -80,13 +80,18 @@ _sig = {
     "pff_profile_kernels": [_P, C.POINTER(pff_state), C.c_double, C.POINTER(pff_options),
                             C.c_int32, _P, _P],
     "pff_mesh_schedule": [_P, _P, _P],
+    "pff_ckpt_create": [_P, C.c_int64, C.c_int32, C.POINTER(C.c_void_p)],
+    "pff_ckpt_destroy": [_P],
+    "pff_run_ckpt": [_P, C.POINTER(pff_state), C.c_int64, C.c_int64, C.c_double,
+                     C.POINTER(pff_options), _P, _P, _P],
+    "pff_backward": [_P, _P, _P, C.POINTER(pff_options), C.POINTER(C.c_double), _P],
     "pff_damage_solve_noalloc": [_P, _P, _P, _P, C.POINTER(pff_options), C.POINTER(C.c_int32),
                                  C.POINTER(C.c_double), C.POINTER(C.c_int32), _P],
 }
 for _name, _args in _sig.items():
     _f = getattr(_lib, _name)
     _f.argtypes = _args
-    _f.restype = None if _name == "pff_mesh_destroy" else C.c_int
+    _f.restype = None if _name in ("pff_mesh_destroy", "pff_ckpt_destroy") else C.c_int
 _lib.pff_last_error.restype = C.c_char_p
 _lib.pff_version.restype = C.c_char_p
 
@@ -129,6 +134,30 @@ def material(mat):
 
 def _dptr(t):
     return None if t is None else C.c_void_p(t.data_ptr())
+
+
+class Checkpoint:
+    """pff_ckpt: checkpoints of a run of nsteps steps in segments of `every`
+    steps, consumed by Mesh.backward."""
+
+    def __init__(self, mesh, nsteps, every=25):
+        h = C.c_void_p()
+        _check(_lib.pff_ckpt_create(mesh._h, int(nsteps), int(every), C.byref(h)))
+        self._h = h
+        self.mesh = mesh
+        self.nsteps = int(nsteps)
+        self.every = int(every)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.pff_ckpt_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Mesh:
@@ -179,6 +208,7 @@ class Mesh:
         _check(_lib.pff_mesh_set_material(self._h, C.byref(m), float(cfl), C.byref(dt)))
         self.mat = dict(mat)
         self.dt = dt.value
+        self.cfl = cfl
         return dt.value
 
     def info(self):
@@ -250,6 +280,21 @@ class Mesh:
         o = opts or options()
         _check(_lib.pff_run(self._h, C.byref(s), int(step0), int(nsteps), float(dt or self.dt),
                             C.byref(o), _dptr(iters_log), _dptr(energy_log), _stream(stream)))
+
+    def run_ckpt(self, st, ckpt, step0=0, dt=None, opts=None, iters_log=None, stream=None):
+        s = self._state(st)
+        o = opts or options()
+        _check(_lib.pff_run_ckpt(self._h, C.byref(s), int(step0), ckpt.nsteps, float(dt or self.dt),
+                                 C.byref(o), ckpt._h, _dptr(iters_log), _stream(stream)))
+
+    def backward(self, ckpt, dL_dd, opts=None, stream=None):
+        """dL/dGc (float) for the upstream gradient dL/dd at the final step."""
+        assert dL_dd.is_cuda and dL_dd.dtype == self.dtype and dL_dd.is_contiguous()
+        o = opts or options()
+        g = C.c_double()
+        _check(_lib.pff_backward(self._h, ckpt._h, _dptr(dL_dd), C.byref(o), C.byref(g),
+                                 _stream(stream)))
+        return g.value
 
     def sync_status(self, stream=None):
         return _lib.pff_sync_status(self._h, _stream(stream))

@@ -14,6 +14,7 @@
 #include <string>
 #include <vector>
 
+#include "adjoint.cuh"
 #include "kernels.cuh"
 #include "pff.h"
 
@@ -1419,6 +1420,281 @@ pff_status pff_damage_solve_noalloc(pff_mesh *m, const double *H, const void *dp
   cudaStream_t s = (cudaStream_t)stream;
   return m->prec == PFF_FP64 ? noalloc_solve_t<double>(m, H, dprev, dout, o, iters, relres, restarts, s)
                              : noalloc_solve_t<float>(m, H, dprev, dout, o, iters, relres, restarts, s);
+}
+
+}  // extern "C"
+
+// ====================================================== checkpoints, adjoint
+//
+// pff_run_ckpt stores the state at the start of every segment of `every`
+// steps; pff_backward walks the segments last to first: it restores the
+// segment's checkpoint, recomputes its steps (bit-identical: same kernels,
+// same schedules, deterministic accumulation) while taping u_{n+1},
+// x_{n+1}, d_{n+1} and H_{n+1}, then reverses the steps one by one
+// (Sec. 4.2, implicit differentiation of each damage solve; the reverse of
+// the explicit mechanics).  Memory: O(N (nsteps/every + every)).
+
+struct pff_ckpt {
+  pff_mesh *m = nullptr;
+  int64_t nsteps = 0, step0 = 0;
+  int32_t every = 0, nseg = 0;
+  double dt = 0.0;
+  bool filled = false;
+  size_t rs = 0;  // sizeof(R)
+  // checkpoints: nseg x (u, v, a, d, H)
+  void *su = nullptr, *sv = nullptr, *sa = nullptr, *sd = nullptr;
+  double *sH = nullptr;
+  // tape: every x (u_{n+1}, x_{n+1}, d_{n+1}, H_{n+1})
+  void *tu = nullptr, *tx = nullptr, *td = nullptr;
+  double *tH = nullptr;
+  // recompute state and the segment's start (d, H)
+  void *wu = nullptr, *wv = nullptr, *wa = nullptr, *wd = nullptr, *segd = nullptr;
+  double *wH = nullptr, *segH = nullptr;
+  // adjoint state (two parities for in/out), solve vectors
+  void *ub[2] = {nullptr, nullptr}, *vb[2] = {nullptr, nullptr}, *ab[2] = {nullptr, nullptr};
+  void *Hb[2] = {nullptr, nullptr};
+  void *db = nullptr, *dbn = nullptr, *g = nullptr, *lam = nullptr, *Hcur = nullptr;
+  double *gc = nullptr;
+  int *kctr = nullptr;
+};
+
+namespace pff {
+
+static void ckpt_free(pff_ckpt *c) {
+  if (!c) return;
+  void *p[] = {c->su, c->sv, c->sa, c->sd, c->sH, c->tu, c->tx, c->td, c->tH, c->wu, c->wv, c->wa, c->wd,
+               c->segd, c->wH, c->segH, c->ub[0], c->ub[1], c->vb[0], c->vb[1], c->ab[0], c->ab[1], c->Hb[0],
+               c->Hb[1], c->db, c->dbn, c->g, c->lam, c->Hcur, c->gc, c->kctr};
+  for (void *q : p)
+    if (q) cudaFree(q);
+  delete c;
+}
+
+static pff_status ckpt_alloc(pff_ckpt *c) {
+  const size_t N = c->m->N + 2, Ne = c->m->Ne, r = c->rs, r2 = 2 * c->rs;
+  const size_t S = c->nseg, E = c->every;
+  auto A = [&](void **p, size_t bytes) -> pff_status {
+    CUDA_TRY(cudaMalloc(p, bytes));
+    CUDA_TRY(cudaMemset(*p, 0, bytes));
+    return PFF_OK;
+  };
+  PFF_TRY(A(&c->su, S * N * r2));
+  PFF_TRY(A(&c->sv, S * N * r2));
+  PFF_TRY(A(&c->sa, S * N * r2));
+  PFF_TRY(A(&c->sd, S * N * r));
+  PFF_TRY(A((void **)&c->sH, S * Ne * 8));
+  PFF_TRY(A(&c->tu, E * N * r2));
+  PFF_TRY(A(&c->tx, E * N * r));
+  PFF_TRY(A(&c->td, E * N * r));
+  PFF_TRY(A((void **)&c->tH, E * Ne * 8));
+  PFF_TRY(A(&c->wu, N * r2));
+  PFF_TRY(A(&c->wv, N * r2));
+  PFF_TRY(A(&c->wa, N * r2));
+  PFF_TRY(A(&c->wd, N * r));
+  PFF_TRY(A(&c->segd, N * r));
+  PFF_TRY(A((void **)&c->wH, Ne * 8));
+  PFF_TRY(A((void **)&c->segH, Ne * 8));
+  for (int q = 0; q < 2; ++q) {
+    PFF_TRY(A(&c->ub[q], N * r2));
+    PFF_TRY(A(&c->vb[q], N * r2));
+    PFF_TRY(A(&c->ab[q], N * r2));
+    PFF_TRY(A(&c->Hb[q], Ne * r));
+  }
+  PFF_TRY(A(&c->db, N * r));
+  PFF_TRY(A(&c->dbn, N * r));
+  PFF_TRY(A(&c->g, N * r));
+  PFF_TRY(A(&c->lam, N * r));
+  PFF_TRY(A(&c->Hcur, Ne * r));
+  PFF_TRY(A((void **)&c->gc, 8));
+  PFF_TRY(A((void **)&c->kctr, 8));
+  return PFF_OK;
+}
+
+template <typename R>
+static pff_status run_ckpt_t(pff_mesh *m, const pff_state *st, int64_t step0, int64_t nsteps, double dt,
+                             const pff_options &o, pff_ckpt *c, int32_t *iters_log, cudaStream_t s) {
+  const size_t N = m->N, Np = m->N + 2, Ne = m->Ne, r = sizeof(R), r2 = 2 * sizeof(R);
+  for (int32_t seg = 0; seg < c->nseg; ++seg) {
+    const int64_t k0 = (int64_t)seg * c->every;
+    const int64_t len = std::min<int64_t>(c->every, nsteps - k0);
+    CUDA_TRY(cudaMemcpyAsync((char *)c->su + seg * Np * r2, st->u, N * r2, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync((char *)c->sv + seg * Np * r2, st->v, N * r2, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync((char *)c->sa + seg * Np * r2, st->a, N * r2, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync((char *)c->sd + seg * Np * r, st->d, N * r, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(c->sH + seg * Ne, st->H, Ne * 8, cudaMemcpyDeviceToDevice, s));
+    PFF_TRY(run_t<R>(m, st, step0 + k0, len, dt, o, iters_log ? iters_log + 2 * k0 : nullptr, nullptr, s));
+  }
+  c->step0 = step0;
+  c->dt = dt;
+  c->filled = true;
+  return PFF_OK;
+}
+
+// One reversed step on the device; slot from *kctr.
+template <typename R>
+static pff_status reverse_step(pff_mesh *m, pff_ckpt *c, AdjParams<R> &A, cudaStream_t s) {
+  const unsigned Gn = std::min<unsigned>(grid_for(m->N, kThreads), m->grid[KP_UPDATE][0]);
+  const unsigned Ge = std::min<unsigned>(grid_for(m->Ne, kThreads), m->grid[KP_UPDATE][0]);
+  k_adj_load<R><<<Ge, kThreads, 0, s>>>(A);
+  k_adj_prep<R><<<Gn, kThreads, 0, s>>>(A);
+  k_adj_rhs<R><<<Gn, kThreads, 0, s>>>(A);
+  CUDA_TRY(cudaGetLastError());
+  // adjoint CG (host-polled), same matvec/update kernels as the forward
+  Params<R> &P = A.P;
+  SolveScalars hs;
+  for (;;) {
+    CUDA_TRY(cudaMemcpyAsync(&hs, P.sc, sizeof(hs), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (hs.done) break;
+    PFF_TRY(launch<R>(m, KP_MATVEC, P, s));
+    PFF_TRY(launch<R>(m, KP_UPDATE, P, s));
+  }
+  if (hs.status) return fail(hs.status == kStNonfinite ? PFF_ERR_NONFINITE : PFF_ERR_NOT_CONVERGED,
+                             "adjoint damage CG failed");
+  k_adj_dmg_terms<R><<<Ge, kThreads, 0, s>>>(A);
+  k_adj_mech<R><<<Gn, kThreads, 0, s>>>(A);
+  k_adj_step_done<<<1, 32, 0, s>>>(c->kctr);
+  CUDA_TRY(cudaGetLastError());
+  return PFF_OK;
+}
+
+template <typename R>
+static pff_status backward_t(pff_mesh *m, pff_ckpt *c, const void *dL_dd, const pff_options &o, double *dL_dGc,
+                             cudaStream_t s) {
+  typedef typename V<R>::T2 R2;
+  const size_t N = m->N, Np = m->N + 2, Ne = m->Ne, r = sizeof(R), r2 = 2 * sizeof(R);
+  // adjoint state at the final time: dL/dd_T given, everything else zero
+  for (int q = 0; q < 2; ++q) {
+    CUDA_TRY(cudaMemsetAsync(c->ub[q], 0, Np * r2, s));
+    CUDA_TRY(cudaMemsetAsync(c->vb[q], 0, Np * r2, s));
+    CUDA_TRY(cudaMemsetAsync(c->ab[q], 0, Np * r2, s));
+    CUDA_TRY(cudaMemsetAsync(c->Hb[q], 0, Ne * r, s));
+  }
+  CUDA_TRY(cudaMemsetAsync(c->lam, 0, Np * r, s));
+  CUDA_TRY(cudaMemsetAsync(c->gc, 0, 8, s));
+  CUDA_TRY(cudaMemcpyAsync(c->db, dL_dd, N * r, cudaMemcpyDeviceToDevice, s));
+  pff_options ob = o;
+  ob.energy_every = 0;
+  pff_state w;
+  w.u = c->wu;
+  w.v = c->wv;
+  w.a = c->wa;
+  w.d = c->wd;
+  w.H = c->wH;
+  int par = 0;
+  for (int32_t seg = c->nseg - 1; seg >= 0; --seg) {
+    const int64_t k0 = (int64_t)seg * c->every;
+    const int64_t len = std::min<int64_t>(c->every, c->nsteps - k0);
+    CUDA_TRY(cudaMemcpyAsync(c->wu, (char *)c->su + seg * Np * r2, N * r2, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(c->wv, (char *)c->sv + seg * Np * r2, N * r2, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(c->wa, (char *)c->sa + seg * Np * r2, N * r2, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(c->wd, (char *)c->sd + seg * Np * r, N * r, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(c->wH, c->sH + seg * Ne, Ne * 8, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(c->segd, c->wd, N * r, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(c->segH, c->wH, Ne * 8, cudaMemcpyDeviceToDevice, s));
+    // recompute the segment, taping each step
+    for (int64_t k = 0; k < len; ++k) {
+      PFF_TRY(run_t<R>(m, &w, c->step0 + k0 + k, 1, c->dt, ob, nullptr, nullptr, s));
+      CUDA_TRY(cudaMemcpyAsync((char *)c->tu + k * Np * r2, c->wu, N * r2, cudaMemcpyDeviceToDevice, s));
+      CUDA_TRY(cudaMemcpyAsync((char *)c->tx + k * Np * r, m->x, N * r, cudaMemcpyDeviceToDevice, s));
+      CUDA_TRY(cudaMemcpyAsync((char *)c->td + k * Np * r, c->wd, N * r, cudaMemcpyDeviceToDevice, s));
+      CUDA_TRY(cudaMemcpyAsync(c->tH + k * Ne, c->wH, Ne * 8, cudaMemcpyDeviceToDevice, s));
+    }
+    // reverse the segment
+    const int kstart = (int)(len - 1);
+    CUDA_TRY(cudaMemcpyAsync(c->kctr, &kstart, sizeof(int), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(m->x, c->lam, N * r, cudaMemcpyDeviceToDevice, s));
+    for (int64_t k = len - 1; k >= 0; --k) {
+      AdjParams<R> A;
+      std::memset(&A, 0, sizeof(A));
+      A.P = base_params<R>(m, o);
+      A.P.model = kAT2;
+      A.P.b = nullptr;
+      A.P.freef = nullptr;
+      A.P.use_cond = 0;
+      A.P.Hr = (const R *)c->Hcur;
+      A.P.dt = c->dt;
+      A.kctr = c->kctr;
+      A.tape_u = (const R2 *)c->tu;
+      A.tape_x = (const R *)c->tx;
+      A.tape_d = (const R *)c->td;
+      A.tape_H = c->tH;
+      A.snap_d = (const R *)c->segd;
+      A.snap_H = c->segH;
+      A.stride_n = (int32_t)Np;
+      A.stride_e = (int32_t)Ne;
+      A.Hcur = (R *)c->Hcur;
+      A.ub_in = (const R2 *)c->ub[par];
+      A.vb_in = (const R2 *)c->vb[par];
+      A.ab_in = (const R2 *)c->ab[par];
+      A.ub_out = (R2 *)c->ub[1 - par];
+      A.vb_out = (R2 *)c->vb[1 - par];
+      A.ab_out = (R2 *)c->ab[1 - par];
+      A.db = (R *)c->db;
+      A.dbn = (R *)c->dbn;
+      A.g = (R *)c->g;
+      A.Hb_in = (const R *)c->Hb[par];
+      A.Hb_acc = (R *)c->Hb[par];
+      A.Hb_out = (R *)c->Hb[1 - par];
+      A.gc = c->gc;
+      PFF_TRY(reverse_step<R>(m, c, A, s));
+      par = 1 - par;
+    }
+    CUDA_TRY(cudaMemcpyAsync(c->lam, m->x, N * r, cudaMemcpyDeviceToDevice, s));
+  }
+  double gc = 0.0;
+  CUDA_TRY(cudaMemcpyAsync(&gc, c->gc, 8, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  *dL_dGc = gc;
+  return PFF_OK;
+}
+
+}  // namespace pff
+
+extern "C" {
+
+pff_status pff_ckpt_create(pff_mesh *m, int64_t nsteps, int32_t every, pff_ckpt **out) {
+  if (!m || !out || nsteps <= 0 || every <= 0) return fail(PFF_ERR_ARG, "bad checkpoint arguments");
+  *out = nullptr;
+  pff_ckpt *c = new pff_ckpt();
+  c->m = m;
+  c->nsteps = nsteps;
+  c->every = (int32_t)std::min<int64_t>(every, nsteps);
+  c->nseg = (int32_t)((nsteps + c->every - 1) / c->every);
+  c->rs = m->prec == PFF_FP64 ? 8 : 4;
+  const pff_status st = ckpt_alloc(c);
+  if (st != PFF_OK) {
+    ckpt_free(c);
+    return st;
+  }
+  *out = c;
+  return PFF_OK;
+}
+
+void pff_ckpt_destroy(pff_ckpt *c) { ckpt_free(c); }
+
+pff_status pff_run_ckpt(pff_mesh *m, const pff_state *st, int64_t step0, int64_t nsteps, double dt,
+                        const pff_options *opt, pff_ckpt *c, int32_t *iters_log, pff_stream stream) {
+  if (!m || !st || !c || !st->u || !st->v || !st->a || !st->d || !st->H) return fail(PFF_ERR_ARG, "null argument");
+  if (c->m != m) return fail(PFF_ERR_ARG, "checkpoint belongs to another mesh");
+  if (nsteps != c->nsteps) return fail(PFF_ERR_ARG, "nsteps differs from the checkpoint's");
+  if (!m->has_mat) return fail(PFF_ERR_ARG, "material not set");
+  if (!(dt > 0) || step0 < 0) return fail(PFF_ERR_ARG, "bad dt / step");
+  const pff_options o = defaults(opt);
+  cudaStream_t s = (cudaStream_t)stream;
+  return m->prec == PFF_FP64 ? run_ckpt_t<double>(m, st, step0, nsteps, dt, o, c, iters_log, s)
+                             : run_ckpt_t<float>(m, st, step0, nsteps, dt, o, c, iters_log, s);
+}
+
+pff_status pff_backward(pff_mesh *m, pff_ckpt *c, const void *dL_dd, const pff_options *opt, double *dL_dGc,
+                        pff_stream stream) {
+  if (!m || !c || !dL_dd || !dL_dGc) return fail(PFF_ERR_ARG, "null argument");
+  if (c->m != m || !c->filled) return fail(PFF_ERR_ARG, "checkpoint not filled by pff_run_ckpt on this mesh");
+  if (m->mat.model != PFF_AT2) return fail(PFF_ERR_ARG, "pff_backward supports the AT2 model");
+  const pff_options o = defaults(opt);
+  cudaStream_t s = (cudaStream_t)stream;
+  return m->prec == PFF_FP64 ? backward_t<double>(m, c, dL_dd, o, dL_dGc, s)
+                             : backward_t<float>(m, c, dL_dd, o, dL_dGc, s);
 }
 
 }  // extern "C"
