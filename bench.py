@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--model", choices=["AT2", "AT1"], default="AT2")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--no-adjoint", action="store_true",
+                    help="skip the forward+adjoint measurement on the 500x500 plate")
     ap.add_argument("--variant", type=int, default=0,
                     help="gather schedule (0 = autotuned; 1..5 fixed, see pff_options.variant)")
     ap.add_argument("--loop", choices=["graph", "host"], default="graph",
@@ -205,6 +207,47 @@ def cpu_baseline(args, budget_s=20.0):
                        f"({n} steps, {el:.1f} s, single thread, FP64)")
 
 
+def fwd_adjoint(pff, dev, steps=300, every=25):
+    """Forward + adjoint cost on the differentiation workload: the 500 x 500
+    plate (251,001 nodes), FP32 with FP64-class reductions, 300 steps,
+    checkpoints every 25 steps, loss = mean((d_T - d*)^2) with d* from
+    Gc* = 3 J/m^2, gradient dL/dGc at Gc = 2 (Sec. 4.1-4.2)."""
+    import torch
+    c = S.config("plate_500x500")
+    mesh = pff.Mesh.from_plate(c["mesh"], precision="fp32")
+    mat = c["material"]
+    opts = pff.options(cg_tol=c["cg_tol"], t_ramp=c["t_ramp"])
+    mesh.set_material(dict(mat, Gc=3.0), c["cfl"])
+    st = mesh.new_state(device=dev)
+    mesh.run(st, steps, opts=opts)
+    dstar = st["d"].clone()
+    mesh.set_material(dict(mat, Gc=2.0), c["cfl"])
+    ck = pff.Checkpoint(mesh, steps, every)
+    # warm-up of the graphs and autotuner on a short run
+    w = mesh.new_state(device=dev)
+    mesh.run(w, 3, opts=opts)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    st = mesh.new_state(device=dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e2 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    mesh.run_ckpt(st, ck, opts=opts)
+    e1.record(stream)
+    d = st["d"]
+    gup = (2.0 * (d.double() - dstar.double()) / mesh.N).float().contiguous()
+    g = mesh.backward(ck, gup, opts=opts)
+    e2.record(stream)
+    torch.cuda.synchronize()
+    tf = e0.elapsed_time(e1) / 1e3
+    tb = e1.elapsed_time(e2) / 1e3
+    loss = float(torch.mean((d.double() - dstar.double()) ** 2))
+    return dict(workload="plate_500x500", nodes=mesh.N, steps=steps, ckpt_every=every,
+                fwd_s_per_step=tf / steps, fwd_adj_s_per_step=(tf + tb) / steps,
+                ratio=(tf + tb) / tf, loss=loss, dL_dGc=g)
+
+
 # ------------------------------------------------------------------- ours
 
 def run_ours(args):
@@ -321,6 +364,8 @@ def run_ours(args):
         kernel_ms={k: float(v) for k, v in zip(names, kms)},
         schedule=dict(variant=sched_var, tune_ms=sched_ms),
     )
+    if not args.no_adjoint:
+        line["fwd_adjoint"] = fwd_adjoint(pff, dev)
     if not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline(args)
     print(json.dumps(line), flush=True)

@@ -42,6 +42,7 @@ template <typename R> struct AdjParams {
   R *Hb_acc;         // = Hb_in buffer, receives the damage terms
   R *Hb_out;         // dL/dH_n
   double *gc;        // running dL/dGc
+  int *astat;        // worst status of the adjoint solves (atomicMax)
 };
 
 template <typename R> struct Slot {
@@ -276,7 +277,10 @@ __global__ void __launch_bounds__(256) k_adj_dmg_terms(AdjParams<R> A) {
     A.Hb_acc[e] = A.Hb_acc[e] + R(2) * Ar * (R(1) / R(3)) * sl - R(2) * lMx;
   }
   __shared__ double tot[1];
-  if (reduce_last<R, 1>(vals, P.part, P.ticket, tot) && threadIdx.x == 0) *A.gc += tot[0];
+  if (reduce_last<R, 1>(vals, P.part, P.ticket, tot) && threadIdx.x == 0) {
+    *A.gc += tot[0];
+    if (P.sc->status && A.astat) atomicMax(A.astat, P.sc->status);
+  }
 }
 
 // fbar at node j: -(1/m_j) (abar_j + dt/2 vbar_j).

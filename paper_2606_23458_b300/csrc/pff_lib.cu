@@ -791,9 +791,36 @@ static pff_status step_explicit_t(pff_mesh *m, const pff_state *st, double t_nex
   return PFF_OK;
 }
 
+// Per-step tape of a recomputed segment (the adjoint's inputs): slot k
+// receives u_{n+1}, the unclamped damage solution x_{n+1}, d_{n+1} and
+// H_{n+1} of the segment's k-th step.
+struct Tape {
+  void *u, *x, *d;
+  double *H;
+  int64_t stride_n, stride_e;
+};
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_tape_store(Params<R> P, Tape T) {
+  typedef typename V<R>::T2 R2;
+  const int64_t k = *P.step_ctr - 1;  // the step just finished
+  R2 *tu = (R2 *)T.u + k * T.stride_n;
+  R *tx = (R *)T.x + k * T.stride_n, *td = (R *)T.d + k * T.stride_n;
+  double *tH = T.H + k * T.stride_e;
+  const int stride = gridDim.x * blockDim.x;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.N; i += stride) {
+    tu[i] = P.u[i];
+    tx[i] = P.x[i];
+    td[i] = P.d[i];
+  }
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < P.Ne; e += stride) tH[e] = P.H[e];
+}
+
 template <typename R>
 static pff_status run_t(pff_mesh *m, const pff_state *st, int64_t step0, int64_t nsteps, double dt,
-                        const pff_options &o, int32_t *iters_log, double *energy_log, cudaStream_t s) {
+                        const pff_options &o, int32_t *iters_log, double *energy_log, cudaStream_t s,
+                        GraphCache *gcache = nullptr, const Tape *tape = nullptr) {
+  GraphCache &gc = gcache ? *gcache : m->step_g;
   Params<R> P = base_params<R>(m, o);
   P.u = (typename V<R>::T2 *)st->u;
   P.v = (typename V<R>::T2 *)st->v;
@@ -810,6 +837,7 @@ static pff_status run_t(pff_mesh *m, const pff_state *st, int64_t step0, int64_t
     PFF_TRY(dalloc(&m->stab, nsteps + 1));
     m->stab_cap = nsteps + 1;
     free_graph(m->step_g);
+    if (gcache) free_graph(*gcache);
   }
   {
     std::vector<double> S(nsteps + 1);
@@ -827,11 +855,13 @@ static pff_status run_t(pff_mesh *m, const pff_state *st, int64_t step0, int64_t
   CUDA_TRY(cudaMemcpyAsync(m->step_ctr, &zero, sizeof(int64_t), cudaMemcpyHostToDevice, s));
   CUDA_TRY(cudaStreamSynchronize(s));
   if (step0 == 0) CUDA_TRY(cudaMemsetAsync(m->wext, 0, sizeof(double), s));
+  const unsigned Gtape = std::min<unsigned>(grid_for(std::max(m->N, m->Ne), kThreads), m->grid[KP_UPDATE][0]);
   if (o.loop_mode == PFF_LOOP_HOST) {
     for (int64_t n = 0; n < nsteps; ++n) {
       PFF_TRY(launch<R>(m, KP_PREDICT, P, s));
       PFF_TRY(launch<R>(m, KP_FORCE, P, s));
       PFF_TRY(solve_host_loop<R>(m, P, s));
+      if (tape) k_tape_store<R><<<Gtape, kThreads, 0, s>>>(P, *tape);
       if (energy_log && o.energy_every > 0 && (n + 1) % o.energy_every == 0) {
         Params<R> E = P;
         E.energy_out = energy_log + 4 * n;
@@ -845,14 +875,14 @@ static pff_status run_t(pff_mesh *m, const pff_state *st, int64_t step0, int64_t
                                (uint64_t)st->H, (uint64_t)o.cg_max_it, (uint64_t)m->var[KP_FORCE],
                                (uint64_t)m->var[KP_RHS], (uint64_t)m->var[KP_MATVEC],
                                (uint64_t)o.max_restarts, (uint64_t)P.iters_log, (uint64_t)P.track_work,
-                               (uint64_t)m->stab};
+                               (uint64_t)m->stab, (uint64_t)(tape ? tape->u : nullptr)};
   uint64_t b1, b2;
   std::memcpy(&b1, &o.cg_tol, 8);
   std::memcpy(&b2, &dt, 8);
   key.push_back(b1);
   key.push_back(b2);
-  if (!m->step_g.exec || m->step_g.key != key) {
-    free_graph(m->step_g);
+  if (!gc.exec || gc.key != key) {
+    free_graph(gc);
     cudaGraph_t g;
     CUDA_TRY(cudaGraphCreate(&g, 0));
     CUDA_TRY(cudaGraphConditionalHandleCreate(&P.cond_inner, g, 1, cudaGraphCondAssignDefault));
@@ -863,20 +893,32 @@ static pff_status run_t(pff_mesh *m, const pff_state *st, int64_t step0, int64_t
     pff_status stt = add_kernel<R>(m, g, {}, KP_PREDICT, P, &n_pr);
     if (stt == PFF_OK) stt = add_kernel<R>(m, g, {n_pr}, KP_FORCE, P, &n_f);
     if (stt == PFF_OK) stt = append_solve<R>(m, g, n_f, P, &last);
+    if (stt == PFF_OK && tape) {
+      cudaKernelNodeParams kp;
+      std::memset(&kp, 0, sizeof(kp));
+      Tape T = *tape;
+      void *args[] = {(void *)&P, (void *)&T};
+      kp.func = (void *)k_tape_store<R>;
+      kp.gridDim = dim3(Gtape);
+      kp.blockDim = dim3(kThreads);
+      kp.kernelParams = args;
+      cudaGraphNode_t n_t;
+      if (cudaGraphAddKernelNode(&n_t, g, &last, 1, &kp) != cudaSuccess) stt = fail(PFF_ERR_CUDA, "tape node");
+    }
     if (stt != PFF_OK) {
       cudaGraphDestroy(g);
       return stt;
     }
-    cudaError_t e = cudaGraphInstantiate(&m->step_g.exec, g, 0);
+    cudaError_t e = cudaGraphInstantiate(&gc.exec, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
-      m->step_g.exec = nullptr;
+      gc.exec = nullptr;
       return fail(PFF_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
     }
-    m->step_g.key = key;
+    gc.key = key;
   }
   for (int64_t n = 0; n < nsteps; ++n) {
-    CUDA_TRY(cudaGraphLaunch(m->step_g.exec, s));
+    CUDA_TRY(cudaGraphLaunch(gc.exec, s));
     if (energy_log && o.energy_every > 0 && (n + 1) % o.energy_every == 0) {
       Params<R> E = P;
       E.energy_out = energy_log + 4 * n;
@@ -1456,12 +1498,17 @@ struct pff_ckpt {
   void *db = nullptr, *dbn = nullptr, *g = nullptr, *lam = nullptr, *Hcur = nullptr;
   double *gc = nullptr;
   int *kctr = nullptr;
+  GraphCache rec_g;     // taping step graph of the recompute
+  GraphCache rev_g[2];  // reverse-step graphs (two in/out parities)
 };
 
 namespace pff {
 
 static void ckpt_free(pff_ckpt *c) {
   if (!c) return;
+  free_graph(c->rec_g);
+  free_graph(c->rev_g[0]);
+  free_graph(c->rev_g[1]);
   void *p[] = {c->su, c->sv, c->sa, c->sd, c->sH, c->tu, c->tx, c->td, c->tH, c->wu, c->wv, c->wa, c->wd,
                c->segd, c->wH, c->segH, c->ub[0], c->ub[1], c->vb[0], c->vb[1], c->ab[0], c->ab[1], c->Hb[0],
                c->Hb[1], c->db, c->dbn, c->g, c->lam, c->Hcur, c->gc, c->kctr};
@@ -1530,31 +1577,58 @@ static pff_status run_ckpt_t(pff_mesh *m, const pff_state *st, int64_t step0, in
   return PFF_OK;
 }
 
-// One reversed step on the device; slot from *kctr.
+// One reversed step as a CUDA graph: H load, clamp masks, adjoint solve set-
+// up, adjoint CG (device-side WHILE loop, same matvec/update kernels as the
+// forward), damage terms, mechanics reverse, slot advance.  The slot comes
+// from *kctr, so one graph per in/out parity serves every step.
+static pff_status add_generic(cudaGraph_t g, const std::vector<cudaGraphNode_t> &deps, const void *fn,
+                              unsigned grid, unsigned block, size_t smem, void **args, cudaGraphNode_t *out) {
+  cudaKernelNodeParams kp;
+  std::memset(&kp, 0, sizeof(kp));
+  kp.func = const_cast<void *>(fn);
+  kp.gridDim = dim3(grid);
+  kp.blockDim = dim3(block);
+  kp.sharedMemBytes = (unsigned)smem;
+  kp.kernelParams = args;
+  CUDA_TRY(cudaGraphAddKernelNode(out, g, deps.data(), deps.size(), &kp));
+  return PFF_OK;
+}
+
 template <typename R>
-static pff_status reverse_step(pff_mesh *m, pff_ckpt *c, AdjParams<R> &A, cudaStream_t s) {
+static pff_status build_reverse_graph(pff_mesh *m, pff_ckpt *c, AdjParams<R> A, GraphCache &gcache,
+                                      const std::vector<uint64_t> &key) {
   const unsigned Gn = std::min<unsigned>(grid_for(m->N, kThreads), m->grid[KP_UPDATE][0]);
   const unsigned Ge = std::min<unsigned>(grid_for(m->Ne, kThreads), m->grid[KP_UPDATE][0]);
-  k_adj_load<R><<<Ge, kThreads, 0, s>>>(A);
-  k_adj_prep<R><<<Gn, kThreads, 0, s>>>(A);
-  k_adj_rhs<R><<<Gn, kThreads, 0, s>>>(A);
-  CUDA_TRY(cudaGetLastError());
-  // adjoint CG (host-polled), same matvec/update kernels as the forward
-  Params<R> &P = A.P;
-  SolveScalars hs;
-  for (;;) {
-    CUDA_TRY(cudaMemcpyAsync(&hs, P.sc, sizeof(hs), cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(cudaStreamSynchronize(s));
-    if (hs.done) break;
-    PFF_TRY(launch<R>(m, KP_MATVEC, P, s));
-    PFF_TRY(launch<R>(m, KP_UPDATE, P, s));
+  free_graph(gcache);
+  cudaGraph_t g;
+  CUDA_TRY(cudaGraphCreate(&g, 0));
+  CUDA_TRY(cudaGraphConditionalHandleCreate(&A.P.cond_inner, g, 1, cudaGraphCondAssignDefault));
+  A.P.use_cond = 1;
+  void *aa[] = {(void *)&A};
+  void *ka[] = {(void *)&c->kctr};
+  cudaGraphNode_t n_load, n_prep, n_rhs, n_loop, n_mv, n_up, n_terms, n_mech, n_done;
+  cudaGraph_t body;
+  pff_status st = add_generic(g, {}, (const void *)k_adj_load<R>, Ge, kThreads, 0, aa, &n_load);
+  if (st == PFF_OK) st = add_generic(g, {n_load}, (const void *)k_adj_prep<R>, Gn, kThreads, 0, aa, &n_prep);
+  if (st == PFF_OK) st = add_generic(g, {n_prep}, (const void *)k_adj_rhs<R>, Gn, kThreads, 0, aa, &n_rhs);
+  if (st == PFF_OK) st = add_while(g, {n_rhs}, A.P.cond_inner, &body, &n_loop);
+  if (st == PFF_OK) st = add_kernel<R>(m, body, {}, KP_MATVEC, A.P, &n_mv);
+  if (st == PFF_OK) st = add_kernel<R>(m, body, {n_mv}, KP_UPDATE, A.P, &n_up);
+  if (st == PFF_OK)
+    st = add_generic(g, {n_loop}, (const void *)k_adj_dmg_terms<R>, Ge, kThreads, 0, aa, &n_terms);
+  if (st == PFF_OK) st = add_generic(g, {n_terms}, (const void *)k_adj_mech<R>, Gn, kThreads, 0, aa, &n_mech);
+  if (st == PFF_OK) st = add_generic(g, {n_mech}, (const void *)k_adj_step_done, 1, 32, 0, ka, &n_done);
+  if (st != PFF_OK) {
+    cudaGraphDestroy(g);
+    return st;
   }
-  if (hs.status) return fail(hs.status == kStNonfinite ? PFF_ERR_NONFINITE : PFF_ERR_NOT_CONVERGED,
-                             "adjoint damage CG failed");
-  k_adj_dmg_terms<R><<<Ge, kThreads, 0, s>>>(A);
-  k_adj_mech<R><<<Gn, kThreads, 0, s>>>(A);
-  k_adj_step_done<<<1, 32, 0, s>>>(c->kctr);
-  CUDA_TRY(cudaGetLastError());
+  const cudaError_t e = cudaGraphInstantiate(&gcache.exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    gcache.exec = nullptr;
+    return fail(PFF_ERR_CUDA, std::string("cudaGraphInstantiate (reverse step): ") + cudaGetErrorString(e));
+  }
+  gcache.key = key;
   return PFF_OK;
 }
 
@@ -1572,6 +1646,7 @@ static pff_status backward_t(pff_mesh *m, pff_ckpt *c, const void *dL_dd, const 
   }
   CUDA_TRY(cudaMemsetAsync(c->lam, 0, Np * r, s));
   CUDA_TRY(cudaMemsetAsync(c->gc, 0, 8, s));
+  CUDA_TRY(cudaMemsetAsync(c->kctr, 0, 2 * sizeof(int), s));
   CUDA_TRY(cudaMemcpyAsync(c->db, dL_dd, N * r, cudaMemcpyDeviceToDevice, s));
   pff_options ob = o;
   ob.energy_every = 0;
@@ -1592,26 +1667,27 @@ static pff_status backward_t(pff_mesh *m, pff_ckpt *c, const void *dL_dd, const 
     CUDA_TRY(cudaMemcpyAsync(c->wH, c->sH + seg * Ne, Ne * 8, cudaMemcpyDeviceToDevice, s));
     CUDA_TRY(cudaMemcpyAsync(c->segd, c->wd, N * r, cudaMemcpyDeviceToDevice, s));
     CUDA_TRY(cudaMemcpyAsync(c->segH, c->wH, Ne * 8, cudaMemcpyDeviceToDevice, s));
-    // recompute the segment, taping each step
-    for (int64_t k = 0; k < len; ++k) {
-      PFF_TRY(run_t<R>(m, &w, c->step0 + k0 + k, 1, c->dt, ob, nullptr, nullptr, s));
-      CUDA_TRY(cudaMemcpyAsync((char *)c->tu + k * Np * r2, c->wu, N * r2, cudaMemcpyDeviceToDevice, s));
-      CUDA_TRY(cudaMemcpyAsync((char *)c->tx + k * Np * r, m->x, N * r, cudaMemcpyDeviceToDevice, s));
-      CUDA_TRY(cudaMemcpyAsync((char *)c->td + k * Np * r, c->wd, N * r, cudaMemcpyDeviceToDevice, s));
-      CUDA_TRY(cudaMemcpyAsync(c->tH + k * Ne, c->wH, Ne * 8, cudaMemcpyDeviceToDevice, s));
-    }
+    // recompute the segment, taping each step (one graph per step)
+    Tape tape;
+    tape.u = c->tu;
+    tape.x = c->tx;
+    tape.d = c->td;
+    tape.H = c->tH;
+    tape.stride_n = (int64_t)Np;
+    tape.stride_e = (int64_t)Ne;
+    PFF_TRY(run_t<R>(m, &w, c->step0 + k0, len, c->dt, ob, nullptr, nullptr, s, &c->rec_g, &tape));
     // reverse the segment
     const int kstart = (int)(len - 1);
     CUDA_TRY(cudaMemcpyAsync(c->kctr, &kstart, sizeof(int), cudaMemcpyHostToDevice, s));
     CUDA_TRY(cudaMemcpyAsync(m->x, c->lam, N * r, cudaMemcpyDeviceToDevice, s));
-    for (int64_t k = len - 1; k >= 0; --k) {
+    for (int q = 0; q < 2; ++q) {
+      const int pin = q;
       AdjParams<R> A;
       std::memset(&A, 0, sizeof(A));
       A.P = base_params<R>(m, o);
       A.P.model = kAT2;
       A.P.b = nullptr;
       A.P.freef = nullptr;
-      A.P.use_cond = 0;
       A.P.Hr = (const R *)c->Hcur;
       A.P.dt = c->dt;
       A.kctr = c->kctr;
@@ -1624,28 +1700,42 @@ static pff_status backward_t(pff_mesh *m, pff_ckpt *c, const void *dL_dd, const 
       A.stride_n = (int32_t)Np;
       A.stride_e = (int32_t)Ne;
       A.Hcur = (R *)c->Hcur;
-      A.ub_in = (const R2 *)c->ub[par];
-      A.vb_in = (const R2 *)c->vb[par];
-      A.ab_in = (const R2 *)c->ab[par];
-      A.ub_out = (R2 *)c->ub[1 - par];
-      A.vb_out = (R2 *)c->vb[1 - par];
-      A.ab_out = (R2 *)c->ab[1 - par];
+      A.ub_in = (const R2 *)c->ub[pin];
+      A.vb_in = (const R2 *)c->vb[pin];
+      A.ab_in = (const R2 *)c->ab[pin];
+      A.ub_out = (R2 *)c->ub[1 - pin];
+      A.vb_out = (R2 *)c->vb[1 - pin];
+      A.ab_out = (R2 *)c->ab[1 - pin];
       A.db = (R *)c->db;
       A.dbn = (R *)c->dbn;
       A.g = (R *)c->g;
-      A.Hb_in = (const R *)c->Hb[par];
-      A.Hb_acc = (R *)c->Hb[par];
-      A.Hb_out = (R *)c->Hb[1 - par];
+      A.Hb_in = (const R *)c->Hb[pin];
+      A.Hb_acc = (R *)c->Hb[pin];
+      A.Hb_out = (R *)c->Hb[1 - pin];
       A.gc = c->gc;
-      PFF_TRY(reverse_step<R>(m, c, A, s));
+      A.astat = c->kctr + 1;
+      uint64_t tb, gb, lb;
+      std::memcpy(&tb, &o.cg_tol, 8);
+      std::memcpy(&gb, &m->mat.Gc, 8);
+      std::memcpy(&lb, &c->dt, 8);
+      std::vector<uint64_t> key = {tb, gb, lb, (uint64_t)m->var[KP_MATVEC], (uint64_t)o.cg_max_it,
+                                   (uint64_t)m->mat.split};
+      if (!c->rev_g[q].exec || c->rev_g[q].key != key) PFF_TRY(build_reverse_graph<R>(m, c, A, c->rev_g[q], key));
+    }
+    for (int64_t k = len - 1; k >= 0; --k) {
+      CUDA_TRY(cudaGraphLaunch(c->rev_g[par].exec, s));
       par = 1 - par;
     }
     CUDA_TRY(cudaMemcpyAsync(c->lam, m->x, N * r, cudaMemcpyDeviceToDevice, s));
   }
   double gc = 0.0;
+  int ks[2] = {0, 0};
   CUDA_TRY(cudaMemcpyAsync(&gc, c->gc, 8, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemcpyAsync(ks, c->kctr, sizeof(ks), cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaStreamSynchronize(s));
   *dL_dGc = gc;
+  if (ks[1] == kStNotConverged) return fail(PFF_ERR_NOT_CONVERGED, "an adjoint damage CG did not converge");
+  if (ks[1] == kStNonfinite) return fail(PFF_ERR_NONFINITE, "non-finite value in an adjoint damage CG");
   return PFF_OK;
 }
 
