@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--model", choices=["AT2", "AT1"], default="AT2")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the 64-plate batched measurement")
     ap.add_argument("--no-adjoint", action="store_true",
                     help="skip the forward+adjoint measurement on the 500x500 plate")
     ap.add_argument("--variant", type=int, default=0,
@@ -240,6 +242,37 @@ def cpu_baseline(args, budget_s=20.0):
                        f"({n} steps, {el:.1f} s, single thread, FP64)")
 
 
+def batched(pff, dev, steps=100, warmup=5):
+    """The batched workload: 64 independent plates drawn from SplitMix64
+    seed 1 (200..700 x 80..280 cells, Gc in [1, 5] J/m^2, traction in
+    [0.5, 2] MPa), FP32 with FP64-class reductions, all plates advanced by
+    one CUDA graph launch per step with per-plate CG convergence."""
+    import torch
+    plates = []
+    for dr in S.batch_draws(64, seed=1):
+        p = S.plate(dr["nx"], dr["ny"], jitter=0.1, seed=1, traction=dr["traction"])
+        plates.append((p, S.material(2 * p["h"], Gc=dr["Gc"])))
+    b = pff.Batch(plates, precision="fp32")
+    nodes = sum(inf["N"] for inf in b.info)
+    st = b.new_state(device=dev)
+    opts = pff.options()
+    b.run(st, warmup, opts=opts)
+    torch.cuda.synchronize()
+    log = torch.zeros(steps, b.nplates, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.run(st, steps, step0=warmup, opts=opts, iters_log=log)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    it = log.cpu().numpy()
+    return dict(workload="64 plates, seed 1", plates=b.nplates, nodes=nodes, steps=steps, warmup=warmup,
+                value=nodes * steps / (ms / 1e3), unit="node-updates/s", ms_per_step=ms / steps,
+                cg_iters_mean=float(it.mean()), cg_iters_max=int(it.max()))
+
+
 def fwd_adjoint(pff, dev, steps=300, every=25):
     """Forward + adjoint cost on the differentiation workload: the 500 x 500
     plate (251,001 nodes), FP32 with FP64-class reductions, 300 steps,
@@ -402,6 +435,8 @@ def run_ours(args):
     )
     if not args.no_adjoint:
         line["fwd_adjoint"] = fwd_adjoint(pff, dev)
+    if not args.no_batch:
+        line["batched"] = batched(pff, dev)
     if not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline(args)
     print(json.dumps(line), flush=True)

@@ -188,6 +188,39 @@ pff_status pff_run_ckpt(pff_mesh *mesh, const pff_state *state, int64_t step0,
 pff_status pff_backward(pff_mesh *mesh, pff_ckpt *ckpt, const void *dL_dd,
                         const pff_options *opt, double *dL_dGc, pff_stream stream);
 
+/* Batches: many independent plates (uneven sizes, Gc, l0, loads and time
+ * steps) advanced together, one CUDA graph launch per step for all plates,
+ * with per-plate CG reductions and convergence (a converged plate's blocks
+ * skip the remaining CG iterations).  Plates share E, nu, rho, eta, the split
+ * and the AT2 model.  The caller owns the concatenated state of
+ * pff_batch_size's N nodes / Ne elements: plate p's nodes start at node0
+ * (pff_batch_plate_info; a multiple of 256, padding nodes between plates
+ * carry no elements and stay at rest), its elements at elem0.  Each plate's
+ * dt = cfl * h_min / c_p of its own mesh.
+ * pff_batch_run: nsteps staggered steps of every plate (step index step0 +
+ * k of each plate's own clock); iters_log (device, nsteps x nplates,
+ * nullable) receives each plate's CG iterations.  Asynchronous. */
+typedef struct pff_batch pff_batch;
+typedef struct {
+  int64_t N;              /* nodes */
+  const double *xy;       /* host N x 2 */
+  int64_t Ne;             /* elements */
+  const int32_t *tri;     /* host Ne x 3, 0-based within the plate */
+  const uint8_t *notch;   /* host N, nullable */
+  int64_t M;              /* loaded edges */
+  const int32_t *tedges;  /* host M x 2 */
+  const double *tvec;     /* host M x 2 traction, Pa */
+  pff_material mat;
+} pff_plate;
+pff_status pff_batch_create(int32_t nplates, const pff_plate *plates, int32_t precision,
+                            double cfl, pff_batch **out);
+void pff_batch_destroy(pff_batch *batch);
+pff_status pff_batch_size(const pff_batch *batch, int64_t *N, int64_t *Ne);
+pff_status pff_batch_plate_info(const pff_batch *batch, int32_t plate, int64_t *node0,
+                                int64_t *N, int64_t *elem0, int64_t *Ne, double *dt);
+pff_status pff_batch_run(pff_batch *batch, const pff_state *state, int64_t step0, int64_t nsteps,
+                         const pff_options *opt, int32_t *iters_log, pff_stream stream);
+
 /* Synchronises the stream and returns (and clears) the worst status the
  * device recorded since the last call (not converged, non-finite, timeout). */
 pff_status pff_sync_status(pff_mesh *mesh, pff_stream stream);

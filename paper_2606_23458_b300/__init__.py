@@ -54,6 +54,12 @@ class pff_options(C.Structure):
                 ("reserved", C.c_int32)]
 
 
+class pff_plate(C.Structure):
+    _fields_ = [("N", C.c_int64), ("xy", C.c_void_p), ("Ne", C.c_int64), ("tri", C.c_void_p),
+                ("notch", C.c_void_p), ("M", C.c_int64), ("tedges", C.c_void_p),
+                ("tvec", C.c_void_p), ("mat", pff_material)]
+
+
 class pff_state(C.Structure):
     _fields_ = [("u", C.c_void_p), ("v", C.c_void_p), ("a", C.c_void_p),
                 ("d", C.c_void_p), ("H", C.c_void_p)]
@@ -85,13 +91,19 @@ _sig = {
     "pff_run_ckpt": [_P, C.POINTER(pff_state), C.c_int64, C.c_int64, C.c_double,
                      C.POINTER(pff_options), _P, _P, _P],
     "pff_backward": [_P, _P, _P, C.POINTER(pff_options), C.POINTER(C.c_double), _P],
+    "pff_batch_create": [C.c_int32, _P, C.c_int32, C.c_double, C.POINTER(C.c_void_p)],
+    "pff_batch_destroy": [_P],
+    "pff_batch_size": [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
+    "pff_batch_plate_info": [_P, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                             C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_double)],
+    "pff_batch_run": [_P, C.POINTER(pff_state), C.c_int64, C.c_int64, C.POINTER(pff_options), _P, _P],
     "pff_damage_solve_noalloc": [_P, _P, _P, _P, C.POINTER(pff_options), C.POINTER(C.c_int32),
                                  C.POINTER(C.c_double), C.POINTER(C.c_int32), _P],
 }
 for _name, _args in _sig.items():
     _f = getattr(_lib, _name)
     _f.argtypes = _args
-    _f.restype = None if _name in ("pff_mesh_destroy", "pff_ckpt_destroy") else C.c_int
+    _f.restype = None if _name in ("pff_mesh_destroy", "pff_ckpt_destroy", "pff_batch_destroy") else C.c_int
 _lib.pff_last_error.restype = C.c_char_p
 _lib.pff_version.restype = C.c_char_p
 
@@ -134,6 +146,82 @@ def material(mat):
 
 def _dptr(t):
     return None if t is None else C.c_void_p(t.data_ptr())
+
+
+class Batch:
+    """pff_batch: independent plates advanced together (one graph launch per
+    step for all plates, per-plate CG convergence).  `plates` is a list of
+    (plate dict from pff_synth.plate, material dict)."""
+
+    def __init__(self, plates, precision="fp32", cfl=0.5):
+        self._keep = []
+        arr = (pff_plate * len(plates))()
+        self.notch = []
+        for k, (p, mat) in enumerate(plates):
+            xy = _np(p["xy"], np.float64); tri = _np(p["tri"], np.int32)
+            notch = _np(p["notch"], np.uint8); ed = _np(p["tedges"], np.int32)
+            tv = _np(p["tvec"], np.float64)
+            self._keep += [xy, tri, notch, ed, tv]
+            self.notch.append(notch)
+            arr[k] = pff_plate(xy.shape[0], _hp(xy).value, tri.shape[0], _hp(tri).value, _hp(notch).value,
+                               ed.shape[0], _hp(ed).value, _hp(tv).value, material(mat))
+        h = C.c_void_p()
+        _check(_lib.pff_batch_create(len(plates), C.cast(arr, C.c_void_p), PRECISIONS[precision],
+                                     float(cfl), C.byref(h)))
+        self._h = h
+        self.precision = precision
+        self.nplates = len(plates)
+        N = C.c_int64(); Ne = C.c_int64()
+        _check(_lib.pff_batch_size(self._h, C.byref(N), C.byref(Ne)))
+        self.N, self.Ne = N.value, Ne.value
+        self.info = []
+        for k in range(self.nplates):
+            a = [C.c_int64() for _ in range(4)]; dt = C.c_double()
+            _check(_lib.pff_batch_plate_info(self._h, k, *[C.byref(x) for x in a], C.byref(dt)))
+            self.info.append(dict(node0=a[0].value, N=a[1].value, elem0=a[2].value, Ne=a[3].value,
+                                  dt=dt.value))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.pff_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def dtype(self):
+        import torch
+        return torch.float64 if self.precision == "fp64" else torch.float32
+
+    def new_state(self, device="cuda"):
+        import torch
+        dt = self.dtype
+        d = torch.zeros(self.N, dtype=dt, device=device)
+        for k, inf in enumerate(self.info):
+            d[inf["node0"]:inf["node0"] + inf["N"]] = torch.as_tensor(self.notch[k], device=device).to(dt)
+        return dict(u=torch.zeros(self.N, 2, dtype=dt, device=device),
+                    v=torch.zeros(self.N, 2, dtype=dt, device=device),
+                    a=torch.zeros(self.N, 2, dtype=dt, device=device), d=d,
+                    H=torch.zeros(self.Ne, dtype=torch.float64, device=device))
+
+    def plate(self, st, k):
+        """Views of plate k's part of a concatenated state."""
+        inf = self.info[k]
+        n0, n1 = inf["node0"], inf["node0"] + inf["N"]
+        e0, e1 = inf["elem0"], inf["elem0"] + inf["Ne"]
+        return dict(u=st["u"][n0:n1], v=st["v"][n0:n1], a=st["a"][n0:n1], d=st["d"][n0:n1],
+                    H=st["H"][e0:e1])
+
+    def run(self, st, nsteps, step0=0, opts=None, iters_log=None, stream=None):
+        s = pff_state(st["u"].data_ptr(), st["v"].data_ptr(), st["a"].data_ptr(), st["d"].data_ptr(),
+                      st["H"].data_ptr())
+        o = opts or options()
+        _check(_lib.pff_batch_run(self._h, C.byref(s), int(step0), int(nsteps), C.byref(o),
+                                  _dptr(iters_log), _stream(stream)))
 
 
 class Checkpoint:

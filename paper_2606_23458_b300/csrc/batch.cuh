@@ -1,0 +1,326 @@
+// batch.cuh -- many independent plates in one launch per kernel (sm_103a).
+//
+// The plates are concatenated into one mesh whose node ranges start on
+// multiples of 256 (padding nodes have no elements, no mass and are fixed),
+// so every 256-node block belongs to one plate.  Each plate keeps its own
+// time step, fracture toughness and regularisation length, traction-ramp
+// table, CG scalars and convergence: reductions are per plate (the plate's
+// last block sums its blocks' partials) and a converged plate's blocks skip
+// the CG kernels while the others iterate.  The step is the same staggered
+// step as for one plate (Sec. 2.2); the same entry functions are used.
+#pragma once
+#include "kernels.cuh"
+
+namespace pff {
+
+// Per-plate coefficients (device array, one per plate).
+struct PlateC {
+  double dt;        // the plate's stable step
+  double tol;       // relative CG tolerance
+  float kappa, cbase, wbase, rscale;  // damage coefficients (FP32 path)
+  double kappa_d, cbase_d, wbase_d, rscale_d;
+  int32_t blk0, nblk;  // first node block and number of node blocks
+  int32_t pad0, pad1;
+};
+
+struct Batch {
+  int32_t nplates;
+  int32_t nsteps1;            // stride of the S table (steps of the run + 1)
+  const int32_t *blk_plate;   // node block -> plate
+  const PlateC *pc;
+  const double *Stab;         // nplates x nsteps1 traction scales
+  SolveScalars *sc;           // nplates
+  unsigned int *tick;         // nplates block tickets (reductions)
+  unsigned int *gtick;        // plate ticket for the global loop decision
+  int32_t *nactive;           // plates still iterating
+  int32_t *iters_log;         // device, nsteps x nplates (nullable)
+};
+
+template <typename R>
+__device__ __forceinline__ void plate_apply(Params<R> &Q, const Batch &B, int p) {
+  const PlateC &c = B.pc[p];
+  Q.dt = c.dt;
+  Q.tol = c.tol;
+  if (sizeof(R) == 4) {
+    Q.kappa = (R)c.kappa;
+    Q.cbase = (R)c.cbase;
+    Q.wbase = (R)c.wbase;
+    Q.rscale = (R)c.rscale;
+  } else {
+    Q.kappa = (R)c.kappa_d;
+    Q.cbase = (R)c.cbase_d;
+    Q.wbase = (R)c.wbase_d;
+    Q.rscale = (R)c.rscale_d;
+  }
+  Q.sc = B.sc + p;
+  Q.Stab = B.Stab + (size_t)p * B.nsteps1;
+}
+
+// Per-plate version of reduce_last: the plate's blocks are
+// [blk0, blk0 + nblk); the last of them to finish gets the totals.
+template <typename R, int NV>
+__device__ __forceinline__ bool reduce_plate(typename Acc<R>::T (&v)[NV], double *part, unsigned int *ticket,
+                                             int blk0, int nblk, double *tot) {
+  typedef Acc<R> A;
+  typedef typename A::T T;
+  __shared__ T sh[32][NV];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    T s = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s = A::add(s, A::shfl(s, o));
+    if (lane == 0) sh[wid][k] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < NV; ++k) {
+      T s = sh[0][k];
+      for (int w = 1; w < nw; ++w) s = A::add(s, sh[w][k]);
+      A::store(&part[(size_t)blockIdx.x * NV + k], s);
+    }
+    __threadfence();
+    const unsigned int t = atomicAdd(ticket, 1u);
+    last = (t == (unsigned)nblk - 1);
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  T acc[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    acc[k] = A::zero();
+    for (int j0 = threadIdx.x; j0 < nblk; j0 += 8 * blockDim.x) {
+      T buf[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int j = j0 + u * blockDim.x;
+        buf[u] = j < nblk ? A::load(&part[(size_t)(blk0 + j) * NV + k]) : A::zero();
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) acc[k] = A::add(acc[k], buf[u]);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    T s = acc[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s = A::add(s, A::shfl(s, o));
+    if (lane == 0) sh[wid][k] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < NV; ++k) {
+      T s = sh[0][k];
+      for (int w = 1; w < nw; ++w) s = A::add(s, sh[w][k]);
+      tot[k] = A::to_d(s);
+    }
+    *ticket = 0u;
+  }
+  __syncthreads();
+  return true;
+}
+
+// The last plate to report sets the loop condition: continue while any
+// plate is still iterating.  Called by one thread of a plate's last block.
+template <typename R>
+__device__ __forceinline__ void plate_report(const Params<R> &P, const Batch &B, bool reset_active) {
+  __threadfence();
+  const int expected = reset_active ? B.nplates : *B.nactive;
+  const unsigned int t = atomicAdd(B.gtick, 1u);
+  if (t == (unsigned)expected - 1) {
+    __threadfence();
+    int act = 0;
+    for (int q = 0; q < B.nplates; ++q) act += __ldcg(&B.sc[q].inner_done) ? 0 : 1;
+    *B.nactive = act;
+    *B.gtick = 0u;
+    if (P.use_cond) cudaGraphSetConditional(P.cond_inner, act > 0 ? 1u : 0u);
+  }
+}
+
+// ---------------------------------------------------------------- kernels
+// Launched with exactly one block per 256-node block (no grid stride).
+
+template <typename R>
+__global__ void __launch_bounds__(256) kb_predict(Params<R> P, Batch B) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P.N) return;
+  const R dt = (R)B.pc[B.blk_plate[blockIdx.x]].dt, h = R(0.5) * dt * dt;
+  typename Params<R>::R2 u = P.u[i], v = P.v[i], a = P.a[i];
+  u.x += dt * v.x + h * a.x;
+  u.y += dt * v.y + h * a.y;
+  P.u[i] = u;
+}
+
+template <typename R, int U>
+__global__ void __launch_bounds__(256) kb_force(Params<R> P, Batch B) {
+  const int p = B.blk_plate[blockIdx.x];
+  Params<R> Q = P;
+  plate_apply(Q, B, p);
+  const double S = Q.Stab[*P.step_ctr + 1];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P.N) return;
+  R fx = 0, fy = 0;
+  for (int k = 0; k < P.D; k += U) {
+    int en[U];
+    R cx[U], cy[U], pp[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) en[u] = k + u < P.D ? __ldg(&P.ell[(size_t)(k + u) * P.N + i]) : -1;
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (en[u] >= 0) force_entry(Q, en[u], cx[u], cy[u], pp[u]);
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (en[u] >= 0) {
+        fx = radd(fx, cx[u]);
+        fy = radd(fy, cy[u]);
+        history_update(Q, en[u], pp[u]);
+      }
+  }
+  corrector(Q, i, fx, fy, S);
+}
+
+template <typename R, int U>
+__global__ void __launch_bounds__(256) kb_rhs(Params<R> P, Batch B) {
+  typedef typename Params<R>::R4 R4;
+  typedef Acc<R> AC;
+  const int p = B.blk_plate[blockIdx.x];
+  Params<R> Q = P;
+  plate_apply(Q, B, p);
+  typename AC::T vals[3] = {AC::zero(), AC::zero(), AC::zero()};
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < P.N) {
+    if (P.flags[i] & kNotch) {
+      rhs_notch_node(Q, i);
+    } else {
+      R bi = 0, dg = 0, ax = 0, a1 = 0;
+      for (int k = 0; k < P.D; k += U) {
+        R4 o[U];
+        int en[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) en[u] = k + u < P.D ? __ldg(&P.ell[(size_t)(k + u) * P.N + i]) : -1;
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (en[u] >= 0) o[u] = rhs_entry(Q, en[u]);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (en[u] >= 0) {
+            bi = radd(bi, o[u].x);
+            dg = radd(dg, o[u].y);
+            ax = radd(ax, o[u].z);
+            a1 = radd(a1, o[u].w);
+          }
+      }
+      rhs_node(Q, i, bi, dg, ax, a1, vals);
+    }
+  }
+  __shared__ double tot[3];
+  const PlateC &c = B.pc[p];
+  if (reduce_plate<R, 3>(vals, P.part, B.tick + p, c.blk0, c.nblk, tot) && threadIdx.x == 0) {
+    Params<R> F = Q;
+    F.use_cond = 0;  // the global decision is taken in plate_report
+    rhs_finish(F, tot);
+    Q.sc->inner_done = Q.sc->done;
+    plate_report(P, B, true);
+  }
+}
+
+template <typename R, int U>
+__global__ void __launch_bounds__(256) kb_matvec(Params<R> P, Batch B) {
+  typedef Acc<R> AC;
+  const int p = B.blk_plate[blockIdx.x];
+  if (B.sc[p].inner_done) return;  // converged plate
+  Params<R> Q = P;
+  plate_apply(Q, B, p);
+  typename AC::T vals[1] = {AC::zero()};
+  const R beta = sc_beta<R>(Q.sc);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < P.N) {
+    R q = 0;
+    if (!is_fixed(Q, i)) {
+      const R pc = pnew(Q, i, beta);
+      for (int k = 0; k < P.D; k += U) {
+        R c[U];
+        int en[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) en[u] = k + u < P.D ? __ldg(&P.ell[(size_t)(k + u) * P.N + i]) : -1;
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (en[u] >= 0) c[u] = mv_entry(Q, en[u], beta, pc);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (en[u] >= 0) q = radd(q, c[u]);
+      }
+      vals[0] = AC::add(vals[0], AC::prod(pc, Q.rscale * q));
+    }
+    P.q[i] = q;
+  }
+  __shared__ double tot[1];
+  const PlateC &c = B.pc[p];
+  if (reduce_plate<R, 1>(vals, P.part, B.tick + p, c.blk0, c.nblk, tot) && threadIdx.x == 0) matvec_finish(Q, tot);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) kb_update(Params<R> P, Batch B) {
+  typedef typename Params<R>::R2 R2;
+  typedef Acc<R> AC;
+  const int p = B.blk_plate[blockIdx.x];
+  if (B.sc[p].inner_done) return;
+  Params<R> Q = P;
+  plate_apply(Q, B, p);
+  typename AC::T vals[3] = {AC::zero(), AC::zero(), AC::zero()};
+  const R beta = sc_beta<R>(Q.sc), alpha = sc_alpha<R>(Q.sc);
+  bool proj = false;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < P.N && !is_fixed(Q, i)) {
+    R2 pz = P.pz[i];
+    R x = P.x[i], r = P.r[i];
+    update_node(Q, i, alpha, beta, x, r, pz, P.q[i], P.dinv[i], vals, proj);
+    P.x[i] = x;
+    P.r[i] = r;
+    P.pz[i] = pz;
+  }
+  __shared__ double tot[3];
+  const PlateC &c = B.pc[p];
+  if (reduce_plate<R, 3>(vals, P.part, B.tick + p, c.blk0, c.nblk, tot) && threadIdx.x == 0) {
+    Params<R> F = Q;
+    F.use_cond = 0;
+    update_finish(F, tot);
+    plate_report(P, B, false);
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) kb_finish(Params<R> P, Batch B) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < P.N) {
+    R v;
+    if (P.flags[i] & kNotch) {
+      v = R(1);
+    } else {
+      v = P.x[i];
+      const R lo = P.dprev[i];
+      v = v > lo ? v : lo;
+      v = v < R(1) ? v : R(1);
+    }
+    P.dout[i] = v;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const int64_t n = *P.step_ctr;
+    for (int q = 0; q < B.nplates; ++q) {
+      const SolveScalars &S = B.sc[q];
+      if (P.status_word && S.status) atomicMax(P.status_word, S.status);
+      if (B.iters_log) B.iters_log[n * B.nplates + q] = S.iters;
+    }
+  }
+}
+
+// Advances the step counter after all kernels of the step read it.
+__global__ void kb_step_done(int64_t *step_ctr) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *step_ctr += 1;
+}
+
+}  // namespace pff

@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "adjoint.cuh"
+#include "batch.cuh"
 #include "kernels.cuh"
 #include "pff.h"
 
@@ -221,7 +222,7 @@ __global__ void k_lumped(const int32_t *ptr, const int32_t *ent, const double *a
   if (i >= N) return;
   double m = 0.0;
   for (int32_t k = ptr[i]; k < ptr[i + 1]; ++k) m += rho * area_d[ent[k] >> 2] / 3.0;
-  minv[i] = (R)(1.0 / m);
+  minv[i] = m > 0.0 ? (R)(1.0 / m) : R(0);  // nodes without elements carry no mass
 }
 
 template <typename R>
@@ -1785,6 +1786,317 @@ pff_status pff_backward(pff_mesh *m, pff_ckpt *c, const void *dL_dd, const pff_o
   cudaStream_t s = (cudaStream_t)stream;
   return m->prec == PFF_FP64 ? backward_t<double>(m, c, dL_dd, o, dL_dGc, s)
                              : backward_t<float>(m, c, dL_dd, o, dL_dGc, s);
+}
+
+}  // extern "C"
+
+// ================================================================ batches
+//
+// pff_batch_*: many independent plates (each its own mesh, material, load
+// and time step) advanced together: one CUDA graph per step for all plates,
+// per-plate CG scalars and convergence (Sec. 2.2 step on every plate).
+
+struct pff_batch {
+  pff_mesh *m = nullptr;  // the concatenated mesh
+  int32_t np = 0;
+  std::vector<int64_t> node0, nnode, elem0, nelem;
+  std::vector<double> dt;
+  std::vector<pff_material> mats;
+  int32_t *blk_plate = nullptr;
+  PlateC *pc = nullptr;
+  double *stab = nullptr;
+  int64_t stab_cap = 0;
+  SolveScalars *sc = nullptr;
+  unsigned int *tick = nullptr, *gtick = nullptr;
+  int32_t *nactive = nullptr;
+  GraphCache g;
+  int32_t U = 3;
+};
+
+namespace pff {
+
+static void batch_free(pff_batch *b) {
+  if (!b) return;
+  free_graph(b->g);
+  void *p[] = {b->blk_plate, b->pc, b->stab, b->sc, b->tick, b->gtick, b->nactive};
+  for (void *q : p)
+    if (q) cudaFree(q);
+  if (b->m) mesh_free(b->m);
+  delete b;
+}
+
+template <typename R>
+static const void *kb_fun(int id, int U) {
+  switch (id) {
+    case KP_PREDICT: return (const void *)kb_predict<R>;
+    case KP_FORCE:
+      return U == 1 ? (const void *)kb_force<R, 1> : U == 2 ? (const void *)kb_force<R, 2>
+           : U == 3 ? (const void *)kb_force<R, 3> : (const void *)kb_force<R, 4>;
+    case KP_RHS:
+      return U == 1 ? (const void *)kb_rhs<R, 1> : U == 2 ? (const void *)kb_rhs<R, 2>
+           : U == 3 ? (const void *)kb_rhs<R, 3> : (const void *)kb_rhs<R, 4>;
+    case KP_MATVEC:
+      return U == 1 ? (const void *)kb_matvec<R, 1> : U == 2 ? (const void *)kb_matvec<R, 2>
+           : U == 3 ? (const void *)kb_matvec<R, 3> : (const void *)kb_matvec<R, 4>;
+    case KP_UPDATE: return (const void *)kb_update<R>;
+    default: return (const void *)kb_finish<R>;
+  }
+}
+
+template <typename R>
+static pff_status batch_run_t(pff_batch *b, const pff_state *st, int64_t step0, int64_t nsteps,
+                              const pff_options &o, int32_t *iters_log, cudaStream_t s) {
+  pff_mesh *m = b->m;
+  const int64_t nblk = (m->N + kThreads - 1) / kThreads;
+  // traction scale per plate and step
+  if (b->stab_cap < (nsteps + 1) * b->np) {
+    if (b->stab) cudaFree(b->stab);
+    b->stab = nullptr;
+    b->stab_cap = 0;
+    PFF_TRY(dalloc(&b->stab, (nsteps + 1) * b->np));
+    b->stab_cap = (nsteps + 1) * b->np;
+    free_graph(b->g);
+  }
+  {
+    std::vector<double> S((nsteps + 1) * b->np);
+    for (int32_t p = 0; p < b->np; ++p)
+      for (int64_t k = 0; k <= nsteps; ++k) S[p * (nsteps + 1) + k] = ramp((double)(step0 + k) * b->dt[p], o.t_ramp);
+    CUDA_TRY(cudaMemcpyAsync(b->stab, S.data(), S.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  Params<R> P = base_params<R>(m, o);
+  P.u = (typename V<R>::T2 *)st->u;
+  P.v = (typename V<R>::T2 *)st->v;
+  P.a = (typename V<R>::T2 *)st->a;
+  P.d = (R *)st->d;
+  PFF_TRY(bind_history<R>(m, P, st->H, s));
+  P.step_ctr = m->step_ctr;
+  P.dprev = (const R *)st->d;
+  P.dout = (R *)st->d;
+  P.model = kAT2;
+  P.b = nullptr;
+  P.freef = nullptr;
+  Batch B;
+  B.nplates = b->np;
+  B.nsteps1 = (int32_t)(nsteps + 1);
+  B.blk_plate = b->blk_plate;
+  B.pc = b->pc;
+  B.Stab = b->stab;
+  B.sc = b->sc;
+  B.tick = b->tick;
+  B.gtick = b->gtick;
+  B.nactive = b->nactive;
+  B.iters_log = iters_log;
+  const int64_t zero = 0;
+  CUDA_TRY(cudaMemcpyAsync(m->step_ctr, &zero, sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  std::vector<uint64_t> key = {(uint64_t)nsteps, (uint64_t)iters_log, (uint64_t)b->U, (uint64_t)o.cg_max_it,
+                               (uint64_t)b->stab, (uint64_t)st->u, (uint64_t)st->v, (uint64_t)st->a,
+                               (uint64_t)st->d, (uint64_t)st->H};
+  uint64_t tb;
+  std::memcpy(&tb, &o.cg_tol, 8);
+  key.push_back(tb);
+  if (!b->g.exec || b->g.key != key) {
+    free_graph(b->g);
+    cudaGraph_t g;
+    CUDA_TRY(cudaGraphCreate(&g, 0));
+    CUDA_TRY(cudaGraphConditionalHandleCreate(&P.cond_inner, g, 1, cudaGraphCondAssignDefault));
+    P.use_cond = 1;
+    void *args[] = {(void *)&P, (void *)&B};
+    void *sargs[] = {(void *)&m->step_ctr};
+    cudaGraphNode_t n_pr, n_f, n_rhs, n_loop, n_mv, n_up, n_fin, n_done;
+    cudaGraph_t body;
+    const unsigned G = (unsigned)nblk;
+    pff_status st = add_generic(g, {}, kb_fun<R>(KP_PREDICT, b->U), G, kThreads, 0, args, &n_pr);
+    if (st == PFF_OK) st = add_generic(g, {n_pr}, kb_fun<R>(KP_FORCE, b->U), G, kThreads, 0, args, &n_f);
+    if (st == PFF_OK) st = add_generic(g, {n_f}, kb_fun<R>(KP_RHS, b->U), G, kThreads, 0, args, &n_rhs);
+    if (st == PFF_OK) st = add_while(g, {n_rhs}, P.cond_inner, &body, &n_loop);
+    if (st == PFF_OK) st = add_generic(body, {}, kb_fun<R>(KP_MATVEC, b->U), G, kThreads, 0, args, &n_mv);
+    if (st == PFF_OK) st = add_generic(body, {n_mv}, kb_fun<R>(KP_UPDATE, b->U), G, kThreads, 0, args, &n_up);
+    if (st == PFF_OK) st = add_generic(g, {n_loop}, kb_fun<R>(KP_FINISH, b->U), G, kThreads, 0, args, &n_fin);
+    if (st == PFF_OK) st = add_generic(g, {n_fin}, (const void *)kb_step_done, 1, 32, 0, sargs, &n_done);
+    if (st != PFF_OK) {
+      cudaGraphDestroy(g);
+      return st;
+    }
+    const cudaError_t e = cudaGraphInstantiate(&b->g.exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      b->g.exec = nullptr;
+      return fail(PFF_ERR_CUDA, std::string("cudaGraphInstantiate (batch): ") + cudaGetErrorString(e));
+    }
+    b->g.key = key;
+  }
+  for (int64_t n = 0; n < nsteps; ++n) CUDA_TRY(cudaGraphLaunch(b->g.exec, s));
+  return PFF_OK;
+}
+
+}  // namespace pff
+
+extern "C" {
+
+pff_status pff_batch_create(int32_t nplates, const pff_plate *plates, int32_t precision, double cfl,
+                            pff_batch **out) {
+  if (!out || nplates <= 0 || !plates) return fail(PFF_ERR_ARG, "bad batch arguments");
+  *out = nullptr;
+  if (precision != PFF_FP64 && precision != PFF_FP32_MIXED) return fail(PFF_ERR_ARG, "bad precision");
+  pff_batch *b = new pff_batch();
+  b->np = nplates;
+  // concatenate: plate p's nodes start on a multiple of 256
+  std::vector<double> xy;
+  std::vector<int32_t> tri, ed;
+  std::vector<uint8_t> notch;
+  std::vector<double> tv;
+  int64_t N = 0, Ne = 0;
+  for (int32_t p = 0; p < nplates; ++p) {
+    const pff_plate &q = plates[p];
+    if (q.N <= 0 || q.Ne <= 0 || !q.xy || !q.tri) {
+      batch_free(b);
+      return fail(PFF_ERR_ARG, "empty plate " + std::to_string(p));
+    }
+    if (q.mat.model != PFF_AT2 || q.mat.split != plates[0].mat.split || q.mat.E != plates[0].mat.E ||
+        q.mat.nu != plates[0].mat.nu || q.mat.rho != plates[0].mat.rho || q.mat.eta != plates[0].mat.eta) {
+      batch_free(b);
+      return fail(PFF_ERR_ARG, "batched plates share E, nu, rho, eta, split and the AT2 model; Gc, l0 vary");
+    }
+    const int64_t n0 = (N + kThreads - 1) / kThreads * kThreads;
+    for (int64_t i = N; i < n0; ++i) {  // padding nodes: no elements, fixed
+      xy.push_back(0.0);
+      xy.push_back(0.0);
+      notch.push_back(1);
+    }
+    b->node0.push_back(n0);
+    b->nnode.push_back(q.N);
+    b->elem0.push_back(Ne);
+    b->nelem.push_back(q.Ne);
+    b->mats.push_back(q.mat);
+    for (int64_t i = 0; i < 2 * q.N; ++i) xy.push_back(q.xy[i]);
+    for (int64_t i = 0; i < q.N; ++i) notch.push_back(q.notch ? q.notch[i] : 0);
+    for (int64_t k = 0; k < 3 * q.Ne; ++k) {
+      if (q.tri[k] < 0 || q.tri[k] >= q.N) {
+        batch_free(b);
+        return fail(PFF_ERR_MESH, "plate " + std::to_string(p) + ": node index out of range");
+      }
+      tri.push_back((int32_t)(q.tri[k] + n0));
+    }
+    for (int64_t k = 0; k < 2 * q.M; ++k) ed.push_back((int32_t)(q.tedges[k] + n0));
+    for (int64_t k = 0; k < 2 * q.M; ++k) tv.push_back(q.tvec[k]);
+    N = n0 + q.N;
+    Ne += q.Ne;
+  }
+  pff_status st = pff_mesh_create(N, xy.data(), Ne, tri.data(), notch.data(), (int64_t)ed.size() / 2,
+                                  ed.empty() ? nullptr : ed.data(), tv.empty() ? nullptr : tv.data(), precision,
+                                  &b->m);
+  if (st != PFF_OK) {
+    batch_free(b);
+    return st;
+  }
+  pff_material base = plates[0].mat;
+  double dt_base = 0.0;
+  st = pff_mesh_set_material(b->m, &base, cfl, &dt_base);
+  if (st != PFF_OK) {
+    batch_free(b);
+    return st;
+  }
+  // per-plate minimum incircle diameter (host, from the plate's own arrays)
+  const double cp = std::sqrt((b->m->lam + 2.0 * b->m->mu) / base.rho);
+  std::vector<PlateC> pc(nplates);
+  const int64_t nblk = (N + kThreads - 1) / kThreads;
+  std::vector<int32_t> bp(nblk, 0);
+  for (int32_t p = 0; p < nplates; ++p) {
+    const pff_plate &q = plates[p];
+    double hmin = INFINITY;
+    for (int64_t e = 0; e < q.Ne; ++e) {
+      const int32_t n1 = q.tri[3 * e], n2 = q.tri[3 * e + 1], n3 = q.tri[3 * e + 2];
+      const double x1 = q.xy[2 * n1], y1 = q.xy[2 * n1 + 1], x2 = q.xy[2 * n2], y2 = q.xy[2 * n2 + 1];
+      const double x3 = q.xy[2 * n3], y3 = q.xy[2 * n3 + 1];
+      const double A = 0.5 * ((x2 - x1) * (y3 - y1) - (x3 - x1) * (y2 - y1));
+      const double P = std::hypot(x2 - x1, y2 - y1) + std::hypot(x3 - x2, y3 - y2) + std::hypot(x1 - x3, y1 - y3);
+      hmin = std::min(hmin, 4.0 * A / P);
+    }
+    const pff_material &mt = q.mat;
+    const double dt = cfl * hmin / cp;
+    b->dt.push_back(dt);
+    PlateC &c = pc[p];
+    std::memset(&c, 0, sizeof(c));
+    c.dt = dt;
+    c.kappa_d = mt.Gc * mt.l0;
+    c.cbase_d = mt.Gc / mt.l0;
+    c.wbase_d = 0.0;
+    c.rscale_d = std::ldexp(1.0, -std::ilogb(mt.Gc / mt.l0 * hmin * hmin));
+    c.kappa = (float)c.kappa_d;
+    c.cbase = (float)c.cbase_d;
+    c.wbase = 0.f;
+    c.rscale = (float)c.rscale_d;
+    c.tol = 0.0;  // set per run from the options
+    c.blk0 = (int32_t)(b->node0[p] / kThreads);
+    const int64_t last = b->node0[p] + q.N;  // exclusive
+    c.nblk = (int32_t)((last + kThreads - 1) / kThreads - c.blk0);
+    for (int32_t k = 0; k < c.nblk; ++k) bp[c.blk0 + k] = p;
+  }
+  auto A = [&](void **ptr, size_t bytes) -> pff_status {
+    CUDA_TRY(cudaMalloc(ptr, bytes));
+    CUDA_TRY(cudaMemset(*ptr, 0, bytes));
+    return PFF_OK;
+  };
+  st = A((void **)&b->blk_plate, nblk * sizeof(int32_t));
+  if (st == PFF_OK) st = A((void **)&b->pc, nplates * sizeof(PlateC));
+  if (st == PFF_OK) st = A((void **)&b->sc, nplates * sizeof(SolveScalars));
+  if (st == PFF_OK) st = A((void **)&b->tick, nplates * sizeof(unsigned int));
+  if (st == PFF_OK) st = A((void **)&b->gtick, 16);
+  if (st == PFF_OK) st = A((void **)&b->nactive, 16);
+  if (st != PFF_OK) {
+    batch_free(b);
+    return st;
+  }
+  cudaMemcpy(b->blk_plate, bp.data(), nblk * sizeof(int32_t), cudaMemcpyHostToDevice);
+  cudaMemcpy(b->pc, pc.data(), nplates * sizeof(PlateC), cudaMemcpyHostToDevice);
+  const cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    batch_free(b);
+    return fail(PFF_ERR_CUDA, cudaGetErrorString(e));
+  }
+  *out = b;
+  return PFF_OK;
+}
+
+void pff_batch_destroy(pff_batch *b) { batch_free(b); }
+
+pff_status pff_batch_size(const pff_batch *b, int64_t *N, int64_t *Ne) {
+  if (!b) return fail(PFF_ERR_ARG, "null batch");
+  if (N) *N = b->m->N;
+  if (Ne) *Ne = b->m->Ne;
+  return PFF_OK;
+}
+
+pff_status pff_batch_plate_info(const pff_batch *b, int32_t p, int64_t *node0, int64_t *N, int64_t *elem0,
+                                int64_t *Ne, double *dt) {
+  if (!b || p < 0 || p >= b->np) return fail(PFF_ERR_ARG, "bad plate index");
+  if (node0) *node0 = b->node0[p];
+  if (N) *N = b->nnode[p];
+  if (elem0) *elem0 = b->elem0[p];
+  if (Ne) *Ne = b->nelem[p];
+  if (dt) *dt = b->dt[p];
+  return PFF_OK;
+}
+
+pff_status pff_batch_run(pff_batch *b, const pff_state *st, int64_t step0, int64_t nsteps, const pff_options *opt,
+                         int32_t *iters_log, pff_stream stream) {
+  if (!b || !st || !st->u || !st->v || !st->a || !st->d || !st->H || nsteps < 0 || step0 < 0)
+    return fail(PFF_ERR_ARG, "bad arguments");
+  pff_options o = defaults(opt);
+  cudaStream_t s = (cudaStream_t)stream;
+  // per-plate tolerance (FP32 floor as for one plate)
+  {
+    std::vector<PlateC> pc(b->np);
+    CUDA_TRY(cudaMemcpy(pc.data(), b->pc, b->np * sizeof(PlateC), cudaMemcpyDeviceToHost));
+    const double tol = b->m->prec == PFF_FP32_MIXED ? std::max(o.cg_tol, kFp32TolFloor) : o.cg_tol;
+    for (auto &c : pc) c.tol = tol;
+    CUDA_TRY(cudaMemcpy(b->pc, pc.data(), b->np * sizeof(PlateC), cudaMemcpyHostToDevice));
+  }
+  if (o.variant >= 2) b->U = std::min(o.variant - 1, 4);
+  return b->m->prec == PFF_FP64 ? batch_run_t<double>(b, st, step0, nsteps, o, iters_log, s)
+                                : batch_run_t<float>(b, st, step0, nsteps, o, iters_log, s);
 }
 
 }  // extern "C"
