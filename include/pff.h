@@ -182,6 +182,8 @@ pff_status pff_run(pff_mesh *mesh, const pff_state *state, int64_t step0,
 typedef struct pff_ckpt pff_ckpt;
 pff_status pff_ckpt_create(pff_mesh *mesh, int64_t nsteps, int32_t every, pff_ckpt **out);
 void pff_ckpt_destroy(pff_ckpt *ckpt);
+/* Total adjoint CG iterations of the last pff_backward on this store. */
+pff_status pff_ckpt_stats(const pff_ckpt *ckpt, int64_t *adjoint_iters);
 pff_status pff_run_ckpt(pff_mesh *mesh, const pff_state *state, int64_t step0,
                         int64_t nsteps, double dt, const pff_options *opt,
                         pff_ckpt *ckpt, int32_t *iters_log, pff_stream stream);

@@ -88,6 +88,7 @@ _sig = {
     "pff_mesh_schedule": [_P, _P, _P],
     "pff_ckpt_create": [_P, C.c_int64, C.c_int32, C.POINTER(C.c_void_p)],
     "pff_ckpt_destroy": [_P],
+    "pff_ckpt_stats": [_P, C.POINTER(C.c_int64)],
     "pff_run_ckpt": [_P, C.POINTER(pff_state), C.c_int64, C.c_int64, C.c_double,
                      C.POINTER(pff_options), _P, _P, _P],
     "pff_backward": [_P, _P, _P, C.POINTER(pff_options), C.POINTER(C.c_double), _P],
@@ -235,6 +236,11 @@ class Checkpoint:
         self.mesh = mesh
         self.nsteps = int(nsteps)
         self.every = int(every)
+
+    def adjoint_iters(self):
+        n = C.c_int64()
+        _check(_lib.pff_ckpt_stats(self._h, C.byref(n)))
+        return n.value
 
     def close(self):
         if getattr(self, "_h", None):

@@ -279,7 +279,10 @@ __global__ void __launch_bounds__(256) k_adj_dmg_terms(AdjParams<R> A) {
   __shared__ double tot[1];
   if (reduce_last<R, 1>(vals, P.part, P.ticket, tot) && threadIdx.x == 0) {
     *A.gc += tot[0];
-    if (P.sc->status && A.astat) atomicMax(A.astat, P.sc->status);
+    if (A.astat) {
+      if (P.sc->status) atomicMax(A.astat, P.sc->status);
+      atomicAdd(A.astat + 1, P.sc->iters);  // adjoint CG iterations, summed
+    }
   }
 }
 

@@ -1499,6 +1499,7 @@ struct pff_ckpt {
   void *db = nullptr, *dbn = nullptr, *g = nullptr, *lam = nullptr, *Hcur = nullptr;
   double *gc = nullptr;
   int *kctr = nullptr;
+  int64_t adj_iters = 0;  // adjoint CG iterations of the last pff_backward
   GraphCache rec_g;     // taping step graph of the recompute
   GraphCache rev_g[2];  // reverse-step graphs (two in/out parities)
 };
@@ -1554,7 +1555,7 @@ static pff_status ckpt_alloc(pff_ckpt *c) {
   PFF_TRY(A(&c->lam, N * r));
   PFF_TRY(A(&c->Hcur, Ne * r));
   PFF_TRY(A((void **)&c->gc, 8));
-  PFF_TRY(A((void **)&c->kctr, 8));
+  PFF_TRY(A((void **)&c->kctr, 4 * sizeof(int)));
   return PFF_OK;
 }
 
@@ -1647,7 +1648,7 @@ static pff_status backward_t(pff_mesh *m, pff_ckpt *c, const void *dL_dd, const 
   }
   CUDA_TRY(cudaMemsetAsync(c->lam, 0, Np * r, s));
   CUDA_TRY(cudaMemsetAsync(c->gc, 0, 8, s));
-  CUDA_TRY(cudaMemsetAsync(c->kctr, 0, 2 * sizeof(int), s));
+  CUDA_TRY(cudaMemsetAsync(c->kctr, 0, 4 * sizeof(int), s));
   CUDA_TRY(cudaMemcpyAsync(c->db, dL_dd, N * r, cudaMemcpyDeviceToDevice, s));
   pff_options ob = o;
   ob.energy_every = 0;
@@ -1730,11 +1731,12 @@ static pff_status backward_t(pff_mesh *m, pff_ckpt *c, const void *dL_dd, const 
     CUDA_TRY(cudaMemcpyAsync(c->lam, m->x, N * r, cudaMemcpyDeviceToDevice, s));
   }
   double gc = 0.0;
-  int ks[2] = {0, 0};
+  int ks[3] = {0, 0, 0};
   CUDA_TRY(cudaMemcpyAsync(&gc, c->gc, 8, cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaMemcpyAsync(ks, c->kctr, sizeof(ks), cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaStreamSynchronize(s));
   *dL_dGc = gc;
+  c->adj_iters = ks[2];
   if (ks[1] == kStNotConverged) return fail(PFF_ERR_NOT_CONVERGED, "an adjoint damage CG did not converge");
   if (ks[1] == kStNonfinite) return fail(PFF_ERR_NONFINITE, "non-finite value in an adjoint damage CG");
   return PFF_OK;
@@ -1763,6 +1765,12 @@ pff_status pff_ckpt_create(pff_mesh *m, int64_t nsteps, int32_t every, pff_ckpt 
 }
 
 void pff_ckpt_destroy(pff_ckpt *c) { ckpt_free(c); }
+
+pff_status pff_ckpt_stats(const pff_ckpt *c, int64_t *adjoint_iters) {
+  if (!c) return fail(PFF_ERR_ARG, "null checkpoint");
+  if (adjoint_iters) *adjoint_iters = c->adj_iters;
+  return PFF_OK;
+}
 
 pff_status pff_run_ckpt(pff_mesh *m, const pff_state *st, int64_t step0, int64_t nsteps, double dt,
                         const pff_options *opt, pff_ckpt *c, int32_t *iters_log, pff_stream stream) {
