@@ -273,11 +273,14 @@ def batched(pff, dev, steps=100, warmup=5):
                 cg_iters_mean=float(it.mean()), cg_iters_max=int(it.max()))
 
 
-def fwd_adjoint(pff, dev, steps=300, every=25):
+def fwd_adjoint(pff, dev, steps=300, policies=(0, 25)):
     """Forward + adjoint cost on the differentiation workload: the 500 x 500
     plate (251,001 nodes), FP32 with FP64-class reductions, 300 steps,
-    checkpoints every 25 steps, loss = mean((d_T - d*)^2) with d* from
-    Gc* = 3 J/m^2, gradient dL/dGc at Gc = 2 (Sec. 4.1-4.2)."""
+    loss = mean((d_T - d*)^2) with d* from Gc* = 3 J/m^2, gradient dL/dGc at
+    Gc = 2 (Sec. 4.1-4.2).  Each tape policy is timed: every = 0 tapes the
+    whole run in the forward (Sec. 7, the activation tape kept on the GPU);
+    every = 25 keeps checkpoints and recomputes each segment.  The ratio
+    divides by a plain forward run (pff_run, no tape) of the same steps."""
     import torch
     c = S.config("plate_500x500")
     mesh = pff.Mesh.from_plate(c["mesh"], precision="fp32")
@@ -288,36 +291,55 @@ def fwd_adjoint(pff, dev, steps=300, every=25):
     mesh.run(st, steps, opts=opts)
     dstar = st["d"].clone()
     mesh.set_material(dict(mat, Gc=2.0), c["cfl"])
-    ck = pff.Checkpoint(mesh, steps, every)
-    # warm-up: graphs, autotuner, the backward's graphs and the torch ops of
-    # the loss gradient (their first use loads kernels)
-    w = mesh.new_state(device=dev)
-    ckw = pff.Checkpoint(mesh, 3, 3)
-    mesh.run_ckpt(w, ckw, opts=opts)
-    gw = (2.0 * (w["d"].double() - dstar.double()) / mesh.N).float().contiguous()
-    mesh.backward(ckw, gw, opts=opts)
-    ckw.close()
-    torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
+
+    def ev():
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(stream)
+        return e
+
+    # plain forward: the denominator
+    log = torch.zeros(steps, 2, dtype=torch.int32, device=dev)
+    w = mesh.new_state(device=dev)
+    mesh.run(w, 3, opts=opts)
     st = mesh.new_state(device=dev)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e2 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    mesh.run_ckpt(st, ck, opts=opts)
-    e1.record(stream)
-    d = st["d"]
-    gup = (2.0 * (d.double() - dstar.double()) / mesh.N).float().contiguous()
-    g = mesh.backward(ck, gup, opts=opts)
-    e2.record(stream)
     torch.cuda.synchronize()
-    tf = e0.elapsed_time(e1) / 1e3
-    tb = e1.elapsed_time(e2) / 1e3
-    loss = float(torch.mean((d.double() - dstar.double()) ** 2))
-    return dict(workload="plate_500x500", nodes=mesh.N, steps=steps, ckpt_every=every,
-                fwd_s_per_step=tf / steps, fwd_adj_s_per_step=(tf + tb) / steps,
-                ratio=(tf + tb) / tf, loss=loss, dL_dGc=g,
-                adjoint_cg_iters_mean=ck.adjoint_iters() / steps)
+    e0 = ev()
+    mesh.run(st, steps, opts=opts, iters_log=log)
+    e1 = ev()
+    torch.cuda.synchronize()
+    t_plain = e0.elapsed_time(e1) / 1e3
+    out = dict(workload="plate_500x500", nodes=mesh.N, steps=steps,
+               fwd_s_per_step=t_plain / steps, fwd_cg_iters_mean=float(log[:, 0].float().mean()))
+    for every in policies:
+        ck = pff.Checkpoint(mesh, steps, every)
+        # warm-up: graphs, autotuner, the backward's graphs and the torch ops
+        # of the loss gradient (their first use loads kernels)
+        w = mesh.new_state(device=dev)
+        ckw = pff.Checkpoint(mesh, 3, min(every, 3))
+        mesh.run_ckpt(w, ckw, opts=opts)
+        gw = (2.0 * (w["d"].double() - dstar.double()) / mesh.N).float().contiguous()
+        mesh.backward(ckw, gw, opts=opts)
+        ckw.close()
+        st = mesh.new_state(device=dev)
+        torch.cuda.synchronize()
+        e0 = ev()
+        mesh.run_ckpt(st, ck, opts=opts)
+        e1 = ev()
+        d = st["d"]
+        gup = (2.0 * (d.double() - dstar.double()) / mesh.N).float().contiguous()
+        g = mesh.backward(ck, gup, opts=opts)
+        e2 = ev()
+        torch.cuda.synchronize()
+        tf = e0.elapsed_time(e1) / 1e3
+        tb = e1.elapsed_time(e2) / 1e3
+        loss = float(torch.mean((d.double() - dstar.double()) ** 2))
+        out["full_tape" if every == 0 else f"ckpt_every_{every}"] = dict(
+            fwd_taped_s_per_step=tf / steps, bwd_s_per_step=tb / steps,
+            fwd_adj_s_per_step=(tf + tb) / steps, ratio=(tf + tb) / t_plain, loss=loss, dL_dGc=g,
+            adjoint_cg_iters_mean=ck.adjoint_iters() / steps)
+        ck.close()
+    return out
 
 
 # ------------------------------------------------------------------- ours

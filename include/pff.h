@@ -53,6 +53,7 @@ enum { PFF_SPLIT_SPECTRAL = 0, PFF_SPLIT_AMOR = 1, PFF_SPLIT_ISO = 2 };
 enum { PFF_PLANE_STRAIN = 0 };
 enum { PFF_FP64 = 0, PFF_FP32_MIXED = 1 };
 enum { PFF_LOOP_GRAPH = 0, PFF_LOOP_HOST = 1 };
+enum { PFF_CG_AUTO = 0, PFF_CG_PHASES = 1, PFF_CG_PERSISTENT = 2, PFF_CG_TEST_TIMEOUT = 3 };
 
 typedef struct pff_mesh pff_mesh; /* opaque; owns geometry, CSR, workspaces */
 
@@ -83,7 +84,20 @@ typedef struct {
                            0 = autotuned on first use [0]; 1 = entry-parallel
                            node blocks; 2..5 = node-centric with 1..4 gathers
                            in flight.  All give bit-identical results. */
-  int32_t reserved;
+  int32_t cg_kernel;    /* AT2 CG loop: PFF_CG_PHASES = a matvec and an
+                           update kernel per iteration; PFF_CG_PERSISTENT =
+                           the whole solve in one cooperative kernel (one
+                           CTA per SM, grid barriers with bounded waits,
+                           PFF_ERR_TIMEOUT if one gives up); PFF_CG_AUTO =
+                           the faster on this mesh, timed on first use [0].
+                           Same iteration arithmetic; the two group the
+                           partial sums of the dot products differently.
+                           AT1 always uses the kernel-per-phase loop.
+                           PFF_CG_TEST_TIMEOUT: the persistent loop awaits
+                           one arrival more than it launches, so its first
+                           barrier wait gives up after its 2 s limit and the
+                           call reports PFF_ERR_TIMEOUT (a test of the
+                           bounded wait; the result is not usable). */
 } pff_options;
 
 /* Device state of one plate (caller-owned). */
@@ -168,15 +182,20 @@ pff_status pff_run(pff_mesh *mesh, const pff_state *state, int64_t step0,
  * implicit_adjoint_linear_system / implicit_gc_l0_element_term, with
  * active-set masking; the reverse of the explicit mechanics; segment
  * checkpointing with recompute).
- * pff_ckpt_create: store for nsteps steps in segments of `every` steps:
- *   device memory O(N (nsteps/every + every)) (checkpoints of u, v, a, d, H
- *   at each segment start, a per-step tape for one segment, adjoint state).
- * pff_run_ckpt: pff_run that also fills the checkpoints; nsteps must equal
- *   the store's.  iters_log as in pff_run.
+ * pff_ckpt_create: store for nsteps steps.  every = 0: full tape (Sec. 7,
+ *   the whole activation tape in device memory): u, x, d (N each, mesh
+ *   precision) and H (Ne doubles) of every step, about
+ *   nsteps (4 sizeof(R) N + 8 Ne) bytes, and no recompute in the backward.
+ *   every > 0: segments of `every` steps, device memory
+ *   O(N (nsteps/every + every)) (checkpoints of u, v, a, d, H at each
+ *   segment start, a per-step tape for one segment, adjoint state) for one
+ *   extra forward pass in the backward.  PFF_ERR_OOM if it does not fit.
+ * pff_run_ckpt: pff_run that also fills the tape or the checkpoints; nsteps
+ *   must equal the store's.  iters_log as in pff_run.
  * pff_backward: given dL/dd at the final step (device, N, mesh precision),
  *   recomputes each segment from its checkpoint (bit-identical to the
- *   forward), reverses its steps and returns dL/dGc (host) for the AT2
- *   model.  One adjoint CG solve per step with warm start.  Synchronises
+ *   forward; skipped for a full tape), reverses the steps and returns
+ *   dL/dGc (host) for the AT2 model.  One adjoint CG solve per step with warm start.  Synchronises
  *   the stream.  Errors: PFF_ERR_ARG (wrong mesh, unfilled store, AT1),
  *   PFF_ERR_NOT_CONVERGED / PFF_ERR_NONFINITE from an adjoint solve. */
 typedef struct pff_ckpt pff_ckpt;
@@ -248,6 +267,14 @@ pff_status pff_profile_kernels(pff_mesh *mesh, const pff_state *state, double dt
  * as pff_options.variant codes (1..5), and the autotuner's timings in ms
  * (3 x 5, 0 where not measured).  Host outputs, each nullable. */
 pff_status pff_mesh_schedule(const pff_mesh *mesh, int32_t *variant, float *tune_ms);
+
+/* The AT2 CG loop the autotuner chose on this mesh: *cg_kernel =
+ * PFF_CG_PHASES or PFF_CG_PERSISTENT (PFF_CG_AUTO while not yet timed), the
+ * persistent kernel's gathers in flight (1..4), and the timings of 8
+ * iterations in ms of the kernel-per-phase loop and of the best persistent
+ * kernel (0 if not timed).  Host scalars; each pointer nullable. */
+pff_status pff_mesh_cg_choice(const pff_mesh *mesh, int32_t *cg_kernel, int32_t *gathers,
+                              float *ms_phases, float *ms_persistent);
 
 /* The damage solve of pff_damage_solve, for callers that must not allocate
  * device memory during the call.  The paper has no counterpart of this entry

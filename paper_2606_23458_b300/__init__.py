@@ -27,6 +27,7 @@ PFF_AT1, PFF_AT2 = 1, 2
 PFF_SPLIT_SPECTRAL, PFF_SPLIT_AMOR, PFF_SPLIT_ISO = 0, 1, 2
 PFF_FP64, PFF_FP32_MIXED = 0, 1
 PFF_LOOP_GRAPH, PFF_LOOP_HOST = 0, 1
+PFF_CG_AUTO, PFF_CG_PHASES, PFF_CG_PERSISTENT, PFF_CG_TEST_TIMEOUT = 0, 1, 2, 3
 
 MODELS = {"AT1": PFF_AT1, "AT2": PFF_AT2}
 SPLITS = {"spectral": PFF_SPLIT_SPECTRAL, "amor": PFF_SPLIT_AMOR, "iso": PFF_SPLIT_ISO}
@@ -51,7 +52,7 @@ class pff_options(C.Structure):
                 ("max_restarts", C.c_int32), ("t_ramp", C.c_double),
                 ("energy_every", C.c_int32), ("ckpt_every", C.c_int32),
                 ("block", C.c_int32), ("loop_mode", C.c_int32), ("variant", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("cg_kernel", C.c_int32)]
 
 
 class pff_plate(C.Structure):
@@ -86,6 +87,7 @@ _sig = {
     "pff_profile_kernels": [_P, C.POINTER(pff_state), C.c_double, C.POINTER(pff_options),
                             C.c_int32, _P, _P],
     "pff_mesh_schedule": [_P, _P, _P],
+    "pff_mesh_cg_choice": [_P, _P, _P, _P, _P],
     "pff_ckpt_create": [_P, C.c_int64, C.c_int32, C.POINTER(C.c_void_p)],
     "pff_ckpt_destroy": [_P],
     "pff_ckpt_stats": [_P, C.POINTER(C.c_int64)],
@@ -134,9 +136,9 @@ def _stream(stream=None):
 
 
 def options(cg_tol=1e-8, cg_max_it=10000, max_restarts=50, t_ramp=0.05e-6, energy_every=0,
-            ckpt_every=25, block=0, loop_mode=PFF_LOOP_GRAPH, variant=0):
+            ckpt_every=25, block=0, loop_mode=PFF_LOOP_GRAPH, variant=0, cg_kernel=PFF_CG_AUTO):
     return pff_options(cg_tol, cg_max_it, max_restarts, t_ramp, energy_every, ckpt_every,
-                       block, loop_mode, variant, 0)
+                       block, loop_mode, variant, cg_kernel)
 
 
 def material(mat):
@@ -226,8 +228,10 @@ class Batch:
 
 
 class Checkpoint:
-    """pff_ckpt: checkpoints of a run of nsteps steps in segments of `every`
-    steps, consumed by Mesh.backward."""
+    """pff_ckpt: the tape of a run of nsteps steps, consumed by Mesh.backward.
+    every = 0 tapes every step during the forward (no recompute); every > 0
+    keeps checkpoints at segment starts and recomputes each segment in the
+    backward."""
 
     def __init__(self, mesh, nsteps, every=25):
         h = C.c_void_p()
@@ -401,6 +405,18 @@ class Mesh:
         names = ("force", "rhs", "matvec")
         return ({n: int(v) for n, v in zip(names, var)},
                 {n: [round(float(x), 4) for x in row] for n, row in zip(names, ms)})
+
+    def cg_choice(self):
+        """(AT2 CG loop in use: "auto" (not timed yet) / "phases" /
+        "persistent", ms of 8 iterations kernel-per-phase, ms persistent,
+        gathers in flight of the persistent kernel)."""
+        k = C.c_int32()
+        u = C.c_int32()
+        a = C.c_float()
+        b = C.c_float()
+        _check(_lib.pff_mesh_cg_choice(self._h, C.byref(k), C.byref(u), C.byref(a), C.byref(b)))
+        return {PFF_CG_AUTO: "auto", PFF_CG_PHASES: "phases",
+                PFF_CG_PERSISTENT: "persistent"}[k.value], a.value, b.value, u.value
 
     KERNELS = ("predict", "force", "rhs", "matvec", "update", "finish", "energies")
 

@@ -235,6 +235,8 @@ __global__ void __launch_bounds__(256) k_adj_rhs(AdjParams<R> A) {
     S.restarts = 0;
     S.status = kStOk;
     S.projected = 0;
+    S.bar = 0u;
+    S.abort = 0;
     const bool done = S.bn == 0.0 || sqrt(S.rr) <= P.tol * S.bn;
     S.done = done ? 1 : 0;
     if (P.use_cond) cudaGraphSetConditional(P.cond_inner, done ? 0u : 1u);

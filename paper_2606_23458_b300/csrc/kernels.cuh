@@ -72,6 +72,8 @@ struct SolveScalars {
   int32_t iters, restarts, status, done;
   int32_t projected, inner_done;
   float alpha_f, beta_f;  // FP32 copies read by every thread in FP32 mode
+  uint32_t bar;           // persistent CG: grid-barrier arrivals of this solve
+  int32_t abort;          // persistent CG: a barrier wait gave up
 };
 
 // Everything a kernel needs, passed by value (graph-captured).
@@ -124,6 +126,7 @@ template <typename R> struct Params {
   double tol;
   int32_t max_it, max_restarts;
   int32_t use_cond;
+  int32_t bar_extra;  // persistent CG: arrivals awaited beyond the grid (0; 1 = test of the bounded wait)
   cudaGraphConditionalHandle cond_inner, cond_outer;
   // logs
   int32_t *iters_log;     // device, per step (iters, restarts)
@@ -661,6 +664,8 @@ __device__ __forceinline__ void rhs_finish(const Params<R> &P, const double *tot
   S.restarts = 0;
   S.status = kStOk;
   S.projected = 0;
+  S.bar = 0u;
+  S.abort = 0;
   const bool done = (P.model == kAT2) && (S.bn == 0.0 || sqrt(S.rr) <= P.tol * S.bn);
   S.done = done ? 1 : 0;
   if (P.use_cond) cudaGraphSetConditional(P.cond_inner, done ? 0u : 1u);
@@ -806,13 +811,13 @@ __global__ void __launch_bounds__(256) k_cg_matvec_ep(Params<R> P) {
   if (reduce_last<R, 1>(vals, P.part, P.ticket, tot) && threadIdx.x == 0) matvec_finish(P, tot);
 }
 
-// Node-centric schedule of the same matvec (U gathers in flight).
+// Node-centric rows i0, i0 + stride, ... of q = A p_new (U gathers in
+// flight) with their share of p_new . q added to acc.
 template <typename R, int U>
-__global__ void __launch_bounds__(256) k_cg_matvec_nc(Params<R> P) {
+__device__ __forceinline__ void matvec_rows(const Params<R> &P, R beta, int i0, int stride,
+                                            typename Acc<R>::T &acc) {
   typedef Acc<R> AC;
-  typename AC::T vals[1] = {AC::zero()};
-  const R beta = sc_beta<R>(P.sc);
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.N; i += gridDim.x * blockDim.x) {
+  for (int i = i0; i < P.N; i += stride) {
     R q = 0;
     if (!is_fixed(P, i)) {
       const R pc = pnew(P, i, beta);
@@ -828,10 +833,19 @@ __global__ void __launch_bounds__(256) k_cg_matvec_nc(Params<R> P) {
         for (int u = 0; u < U; ++u)
           if (en[u] >= 0) q = radd(q, c[u]);
       }
-      vals[0] = AC::add(vals[0], AC::prod(pnew(P, i, beta), P.rscale * q));
+      acc = AC::add(acc, AC::prod(pnew(P, i, beta), P.rscale * q));
     }
     P.q[i] = q;
   }
+}
+
+// Node-centric schedule of the same matvec (U gathers in flight).
+template <typename R, int U>
+__global__ void __launch_bounds__(256) k_cg_matvec_nc(Params<R> P) {
+  typedef Acc<R> AC;
+  typename AC::T vals[1] = {AC::zero()};
+  const R beta = sc_beta<R>(P.sc);
+  matvec_rows<R, U>(P, beta, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x, vals[0]);
   __shared__ double tot[1];
   if (reduce_last<R, 1>(vals, P.part, P.ticket, tot) && threadIdx.x == 0) matvec_finish(P, tot);
 }
@@ -901,15 +915,11 @@ __device__ __forceinline__ void update_finish(const Params<R> &P, const double *
   if (P.use_cond) cudaGraphSetConditional(P.cond_inner, stop ? 0u : 1u);
 }
 
+// The update of rows (pairs of rows in FP32) j0, j0 + stride, ...
 template <typename R>
-__global__ void __launch_bounds__(256) k_cg_update(Params<R> P) {
+__device__ __forceinline__ void update_rows(const Params<R> &P, R alpha, R beta, int j0, int stride,
+                                            typename Acc<R>::T (&vals)[3], bool &proj) {
   typedef typename Params<R>::R2 R2;
-  typedef Acc<R> AC;
-  typename AC::T vals[3] = {AC::zero(), AC::zero(), AC::zero()};
-  const R beta = sc_beta<R>(P.sc);
-  const R alpha = sc_alpha<R>(P.sc);
-  bool proj = false;
-  const int stride = gridDim.x * blockDim.x;
   if constexpr (sizeof(R) == 4) {
     const int npair = (P.N + 1) >> 1;
     const uchar2 *__restrict__ fl2 = reinterpret_cast<const uchar2 *>(P.flags);
@@ -918,7 +928,7 @@ __global__ void __launch_bounds__(256) k_cg_update(Params<R> P) {
     float4 *__restrict__ pz4 = reinterpret_cast<float4 *>(P.pz);
     const float2 *__restrict__ q2 = reinterpret_cast<const float2 *>(P.q);
     const float2 *__restrict__ d2 = reinterpret_cast<const float2 *>(P.dinv);
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < npair; j += stride) {
+    for (int j = j0; j < npair; j += stride) {
       const uchar2 f = fl2[j];
       float2 xv = x2[j], rv = r2[j];
       const float2 qv = q2[j], dv = d2[j];
@@ -936,7 +946,7 @@ __global__ void __launch_bounds__(256) k_cg_update(Params<R> P) {
       pz4[j] = make_float4(pz0.x, pz0.y, pz1.x, pz1.y);
     }
   } else {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.N; i += stride) {
+    for (int i = j0; i < P.N; i += stride) {
       if (is_fixed(P, i)) continue;
       R2 pz = P.pz[i];
       R x = P.x[i], r = P.r[i];
@@ -946,9 +956,237 @@ __global__ void __launch_bounds__(256) k_cg_update(Params<R> P) {
       P.pz[i] = pz;
     }
   }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_cg_update(Params<R> P) {
+  typedef Acc<R> AC;
+  typename AC::T vals[3] = {AC::zero(), AC::zero(), AC::zero()};
+  const R beta = sc_beta<R>(P.sc);
+  const R alpha = sc_alpha<R>(P.sc);
+  bool proj = false;
+  update_rows<R>(P, alpha, beta, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x, vals, proj);
   if (proj) vals[2] = AC::one();
   __shared__ double tot[3];
   if (reduce_last<R, 3>(vals, P.part, P.ticket, tot) && threadIdx.x == 0) update_finish(P, tot);
+}
+
+// ------------------------------------------------- persistent CG (AT2)
+//
+// The whole Jacobi-PCG loop of one AT2 solve in one cooperative launch
+// (kPersMinBlocks CTAs of kPersThreads per SM): per iteration the matvec
+// rows, a grid all-reduce of p.q, the update rows, a grid all-reduce of
+// (|r|^2, r.z).  Each all-reduce is a grid barrier: every CTA publishes its
+// partial, counts itself in on S.bar with a release reduction (monotonic
+// within the solve; the set-up kernel zeroes it), waits for the count with
+// acquire loads, and then sums all partials itself in CTA order, so every
+// CTA takes the same decisions from bit-identical totals and no second
+// round trip is needed to broadcast them.  The per-row arithmetic is that
+// of the kernel-per-phase loop (matvec_rows / update_rows); only the
+// grouping of the partial sums differs.  Waits are bounded: after
+// kSpinTimeoutNs a CTA raises S.abort, every CTA leaves, and the solve
+// reports kStTimeout.
+
+constexpr int kPersThreads = 768;
+constexpr int kPersMinBlocks = 2;  // 48 warps per SM; at most 42 registers
+constexpr unsigned long long kSpinTimeoutNs = 2000000000ull;  // 2 s
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int *p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void red_release_add_u32(unsigned int *p, unsigned int v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Sum of NV accumulators over the CTA in a fixed tree order; the result is
+// valid in thread 0.  sh: one slot per warp.
+template <typename R, int NV>
+__device__ __forceinline__ void cta_sum(typename Acc<R>::T (&v)[NV], typename Acc<R>::T (*sh)[NV]) {
+  typedef Acc<R> A;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] = A::add(v[k], A::shfl(v[k], o));
+    if (lane == 0) sh[wid][k] = v[k];
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      v[k] = lane < nw ? sh[lane][k] : A::zero();
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v[k] = A::add(v[k], A::shfl(v[k], o));
+    }
+  }
+  __syncthreads();  // sh is free again
+}
+
+// Grid all-reduce (see above).  part: this barrier's buffer of
+// gridDim.x * NV slots; target: arrivals that complete this barrier.
+// Returns false (in every thread) if the wait gave up; otherwise thread 0
+// holds the totals in tot.
+template <typename R, int NV>
+__device__ __forceinline__ bool grid_sum(typename Acc<R>::T (&v)[NV], double *part, SolveScalars *S,
+                                         unsigned int target, double *tot, typename Acc<R>::T (*sh)[NV],
+                                         int *ok_sh) {
+  typedef Acc<R> A;
+  cta_sum<R, NV>(v, sh);  // its barriers order every thread's row writes before thread 0's release
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) A::store(&part[(size_t)blockIdx.x * NV + k], v[k]);
+    red_release_add_u32(&S->bar, 1u);
+    int ok = 1;
+    const unsigned long long t0 = global_ns();
+    unsigned int spins = 0;
+    while (ld_acquire_u32(&S->bar) < target) {
+      if (*(volatile int32_t *)&S->abort) {
+        ok = 0;
+        break;
+      }
+      if ((++spins & 31u) == 0u && global_ns() - t0 > kSpinTimeoutNs) {
+        *(volatile int32_t *)&S->abort = 1;
+        ok = 0;
+        break;
+      }
+    }
+    *ok_sh = ok;
+  }
+  __syncthreads();
+  if (!*ok_sh) return false;
+  typename A::T w[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) w[k] = A::zero();
+  for (int j = threadIdx.x; j < (int)gridDim.x; j += blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) w[k] = A::add(w[k], A::load(&part[(size_t)j * NV + k]));
+  }
+  cta_sum<R, NV>(w, sh);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) tot[k] = A::to_d(w[k]);
+  }
+  return true;
+}
+
+// The solve's scalars, kept in shared memory by thread 0 of every CTA
+// (identical in all CTAs); coef holds alpha and beta in the kernel
+// precision for every thread.
+template <typename R> struct PersShared {
+  double rho, beta, alpha, rr, pq, bn;
+  double tot[2];
+  int iters, status, done, flag, ok;
+  R coef[2];
+};
+
+// Partials: P.part holds two buffers of 2 * gridDim.x slots, used by
+// alternate barriers (a CTA can only refill a buffer after every CTA has
+// passed the barrier that read it).
+template <typename R, int U>
+__global__ void __launch_bounds__(kPersThreads, kPersMinBlocks) k_cg_persistent(Params<R> P) {
+  typedef Acc<R> AC;
+  SolveScalars *S = P.sc;
+  __shared__ typename AC::T sh[kPersThreads / 32][2];
+  __shared__ PersShared<R> z;
+  if (S->done) return;  // set-up found b_eff = 0 or r_0 already small
+  if (threadIdx.x == 0) {
+    z.rho = S->rho;
+    z.beta = S->beta;
+    z.alpha = S->alpha;
+    z.rr = S->rr;
+    z.pq = S->pq;
+    z.bn = S->bn;
+    z.iters = S->iters;
+    z.status = kStOk;
+    z.done = 0;
+    z.coef[1] = sizeof(R) == 4 ? (R)S->beta_f : (R)S->beta;
+  }
+  __syncthreads();
+  const unsigned int nb = gridDim.x;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+  unsigned int nbar = 0;
+  for (;;) {
+    // q = A p_new, p_new . q
+    typename AC::T v1[1] = {AC::zero()};
+    matvec_rows<R, U>(P, z.coef[1], tid, stride, v1[0]);
+    ++nbar;
+    if (!grid_sum<R, 1>(v1, P.part + (nbar & 1u) * 2u * nb, S, nbar * nb + P.bar_extra, z.tot,
+                        (typename AC::T(*)[1])sh, &z.ok))
+      break;
+    if (threadIdx.x == 0) {
+      z.pq = z.tot[0];
+      if (z.pq == 0.0) {  // p = 0: nothing moved, the iterate is exact
+        z.done = 1;
+        z.flag = 1;
+      } else {
+        z.alpha = z.rho / z.pq;
+        z.coef[0] = sizeof(R) == 4 ? (R)(float)z.alpha : (R)z.alpha;
+        z.flag = 0;
+      }
+    }
+    __syncthreads();
+    if (z.flag) break;
+    // x += alpha p, r -= alpha q, z = r / diag; |r|^2 and r.z
+    typename AC::T v3[3] = {AC::zero(), AC::zero(), AC::zero()};
+    bool proj = false;
+    update_rows<R>(P, z.coef[0], z.coef[1], tid, stride, v3, proj);
+    typename AC::T v2[2] = {v3[0], v3[1]};
+    ++nbar;
+    if (!grid_sum<R, 2>(v2, P.part + (nbar & 1u) * 2u * nb, S, nbar * nb + P.bar_extra, z.tot, sh, &z.ok))
+      break;
+    if (threadIdx.x == 0) {
+      bool stop = false;
+      const double t0 = z.tot[0], t1 = z.tot[1];
+      z.iters += 1;
+      z.rr = t0;
+      if (!(t0 == t0) || isinf(t0)) {
+        z.status = kStNonfinite;
+        z.done = 1;
+        stop = true;
+      } else if (sqrt(t0) <= P.tol * z.bn) {
+        z.done = 1;
+        stop = true;
+      }
+      if (!stop && z.iters >= P.max_it) {
+        stop = true;
+        z.status = kStNotConverged;
+        z.done = 1;
+      }
+      z.beta = z.rho != 0.0 ? t1 / z.rho : 0.0;
+      z.rho = t1;
+      z.coef[1] = sizeof(R) == 4 ? (R)(float)z.beta : (R)z.beta;
+      z.flag = stop ? 1 : 0;
+    }
+    __syncthreads();
+    if (z.flag) break;
+  }
+  // CTA 0 leaves the scalars as the kernel-per-phase loop would
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (!z.ok) {
+      z.status = kStTimeout;
+      z.done = 1;
+    }
+    S->iters = z.iters;
+    S->rr = z.rr;
+    S->pq = z.pq;
+    S->alpha = z.alpha;
+    S->alpha_f = (float)z.alpha;
+    S->beta = z.beta;
+    S->beta_f = (float)z.beta;
+    S->rho = z.rho;
+    S->status = z.status;
+    S->done = z.done;
+    S->inner_done = 1;
+  }
 }
 
 // AT1 restart (projected CG, Sec. 2.4): r = b - A x, active set

@@ -290,6 +290,13 @@ struct pff_mesh {
   int32_t tuned_var[16] = {0}; // autotuner's choice
   bool tuned[16] = {false};
   float tune_ms[16][8] = {{0}};
+  // persistent AT2 CG (one cooperative launch per solve), per U = 1..4:
+  // grid (0 = cannot be co-resident); the autotuner's verdict against the
+  // kernel-per-phase loop and both timings (8 iterations, ms)
+  unsigned pgrid[5] = {0};
+  int pers_U = 0;  // gather width of the persistent kernel (0 = not tuned: the matvec's)
+  bool pers_tuned = false, pers_faster = false;
+  float pers_ms[2] = {0.f, 0.f};
 };
 
 namespace pff {
@@ -358,6 +365,16 @@ static const void *kfun(int id, int v) {
   }
 }
 
+template <typename R>
+static const void *pers_fun(int U) {
+  switch (U) {
+    case 1: return (const void *)k_cg_persistent<R, 1>;
+    case 3: return (const void *)k_cg_persistent<R, 3>;
+    case 4: return (const void *)k_cg_persistent<R, 4>;
+    default: return (const void *)k_cg_persistent<R, 2>;
+  }
+}
+
 // Launch geometry.  Node-block kernels stage one value set per incidence
 // entry of a block of NB nodes in shared memory; NB is halved until the
 // largest block's entries fit in 40 KB.  Grids are the smaller of the
@@ -410,6 +427,65 @@ static pff_status configure(pff_mesh *m) {
       m->smem[id][v] = sm;
     }
   }
+  // persistent CG: every CTA must be resident at once (cooperative launch)
+  int coop = 0;
+  CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  for (int U = 1; U <= 4; ++U) {
+    int occ = 0;
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pers_fun<R>(U), kPersThreads, 0));
+    // the fewest CTAs that give no thread more rows than a full wave would
+    const int64_t wave = (int64_t)nsm * occ;
+    const int64_t rows = std::max<int64_t>(1, (m->N + kPersThreads * wave - 1) / (kPersThreads * wave));
+    const int64_t ctas = std::max<int64_t>(1, (m->N + kPersThreads * rows - 1) / (kPersThreads * rows));
+    m->pgrid[U] = coop && occ > 0 ? (unsigned)std::min<int64_t>(ctas, wave) : 0u;
+  }
+  return PFF_OK;
+}
+
+// The persistent CG's gather width: its own tuned U, else the tuned matvec
+// schedule's (2 when the entry-parallel schedule won).
+static inline int pers_u(const pff_mesh *m) {
+  if (m->pers_U >= 1 && m->pers_U <= 4) return m->pers_U;
+  const int v = m->var[KP_MATVEC];
+  return v >= 1 && v <= 4 ? v : 2;
+}
+
+// Whether an AT2 solve runs as one persistent kernel: forced by
+// opt->cg_kernel (1 = kernel per phase, 2 = persistent), else the
+// autotuner's verdict.  The barrier count (2 per iteration per CTA) must
+// stay below 2^31.
+static bool use_persistent(const pff_mesh *m, const pff_options &o, int model) {
+  if (model != kAT2 || o.cg_kernel == PFF_CG_PHASES) return false;
+  const unsigned g = m->pgrid[pers_u(m)];
+  if (g == 0 || 2.0 * ((double)o.cg_max_it + 2.0) * g >= 2147483648.0) return false;
+  return o.cg_kernel == PFF_CG_PERSISTENT || o.cg_kernel == PFF_CG_TEST_TIMEOUT ||
+         (m->pers_tuned && m->pers_faster);
+}
+
+template <typename R>
+static pff_status launch_pers(const pff_mesh *m, Params<R> &P, cudaStream_t s) {
+  void *args[] = {(void *)&P};
+  const int U = pers_u(m);
+  CUDA_TRY(cudaLaunchCooperativeKernel(pers_fun<R>(U), dim3(m->pgrid[U]), dim3(kPersThreads), args, 0, s));
+  return PFF_OK;
+}
+
+template <typename R>
+static pff_status add_pers(const pff_mesh *m, cudaGraph_t g, const std::vector<cudaGraphNode_t> &deps,
+                           Params<R> &P, cudaGraphNode_t *out) {
+  cudaKernelNodeParams kp;
+  std::memset(&kp, 0, sizeof(kp));
+  void *args[] = {(void *)&P};
+  const int U = pers_u(m);
+  kp.func = const_cast<void *>(pers_fun<R>(U));
+  kp.gridDim = dim3(m->pgrid[U]);
+  kp.blockDim = dim3(kPersThreads);
+  kp.kernelParams = args;
+  CUDA_TRY(cudaGraphAddKernelNode(out, g, deps.data(), deps.size(), &kp));
+  cudaLaunchAttributeValue av;
+  std::memset(&av, 0, sizeof(av));
+  av.cooperative = 1;
+  CUDA_TRY(cudaGraphKernelNodeSetAttribute(*out, cudaLaunchAttributeCooperative, &av));
   return PFF_OK;
 }
 
@@ -485,6 +561,7 @@ static Params<R> base_params(pff_mesh *m, const pff_options &o) {
   P.tol = sizeof(R) == 4 ? std::max(o.cg_tol, kFp32TolFloor) : o.cg_tol;
   P.max_it = o.cg_max_it;
   P.max_restarts = o.max_restarts;
+  P.bar_extra = o.cg_kernel == PFF_CG_TEST_TIMEOUT ? 1 : 0;
   P.status_word = m->status_word;
   P.energy_out = m->energy;
   P.wext = m->wext;
@@ -534,15 +611,18 @@ static pff_status add_while(cudaGraph_t g, const std::vector<cudaGraphNode_t> &d
 }
 
 // Appends the damage solve (rhs -> CG loop -> finish) to graph g after dep.
-// The handles must already be in P (created on the top-level graph).
+// The handles must already be in P (created on the top-level graph), except
+// for a persistent solve (pers), which needs none.
 template <typename R>
 static pff_status append_solve(const pff_mesh *m, cudaGraph_t g, cudaGraphNode_t dep, Params<R> &P,
-                               cudaGraphNode_t *last) {
+                               bool pers, cudaGraphNode_t *last) {
   std::vector<cudaGraphNode_t> d;
   if (dep) d.push_back(dep);
   cudaGraphNode_t n_rhs, n_loop, n_fin;
   PFF_TRY(add_kernel<R>(m, g, d, KP_RHS, P, &n_rhs));
-  if (P.model == kAT1) {
+  if (pers) {
+    PFF_TRY(add_pers<R>(m, g, {n_rhs}, P, &n_loop));
+  } else if (P.model == kAT1) {
     cudaGraph_t outer, inner;
     PFF_TRY(add_while(g, {n_rhs}, P.cond_outer, &outer, &n_loop));
     cudaGraphNode_t n_rs, n_in, n_mv, n_up;
@@ -678,6 +758,104 @@ static pff_status autotune(pff_mesh *m, const pff_options &o, Params<R> P, bool 
   }
   for (int id : ids)
     if (m->tuned[id]) m->var[id] = m->tuned_var[id];
+  // AT2 CG loop: the solve graphs of a run (right-hand side, then the device
+  // WHILE loop of matvec/update kernels, or one persistent launch with
+  // U = 1..4 gathers in flight), each stopped after 8 iterations (tolerance
+  // 0), timed on this mesh's data with whatever the solve leaves in L2, as
+  // in a run
+  if (res == PFF_OK && with_damage && P.model == kAT2 && !m->pers_tuned &&
+      (o.cg_kernel == PFF_CG_AUTO || o.cg_kernel == PFF_CG_PERSISTENT)) {
+    constexpr int K = 8, NK = 5;  // kind 0: kernel per phase; kind U: persistent with U
+    Params<R> Q = P;
+    Q.use_cond = 0;
+    Q.tol = 0.0;
+    Q.max_it = K;
+    Q.iters_log = nullptr;
+    Q.status_word = nullptr;
+    Q.step_inc = nullptr;
+    Q.step_ctr = nullptr;
+    cudaGraph_t g[NK] = {nullptr};
+    cudaGraphExec_t ge[NK] = {nullptr};
+    pff_status st = launch<R>(m, KP_RHS, Q, s);
+    bool skip = false;  // b_eff = 0 here: nothing to time, decide on a later call
+    if (st == PFF_OK) {
+      SolveScalars hs;
+      if (cudaMemcpyAsync(&hs, m->sc, sizeof(hs), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+          cudaStreamSynchronize(s) != cudaSuccess)
+        st = fail(PFF_ERR_CUDA, "autotune: scalars");
+      else
+        skip = hs.done != 0;
+    }
+    const int keepU = m->pers_U;
+    for (int kind = 0; kind < NK && !skip && st == PFF_OK; ++kind) {
+      if (kind > 0 && m->pgrid[kind] == 0) continue;
+      Params<R> G = Q;
+      if (cudaGraphCreate(&g[kind], 0) != cudaSuccess) {
+        st = fail(PFF_ERR_CUDA, "autotune: graph");
+        break;
+      }
+      if (kind == 0) {
+        if (cudaGraphConditionalHandleCreate(&G.cond_inner, g[kind], 1, cudaGraphCondAssignDefault) != cudaSuccess) {
+          st = fail(PFF_ERR_CUDA, "autotune: conditional handle");
+          break;
+        }
+        G.use_cond = 1;
+      }
+      cudaGraphNode_t n_rhs, n_loop;
+      st = add_kernel<R>(m, g[kind], {}, KP_RHS, G, &n_rhs);
+      if (st == PFF_OK && kind == 0) {
+        cudaGraph_t body;
+        cudaGraphNode_t n_mv, n_up;
+        st = add_while(g[kind], {n_rhs}, G.cond_inner, &body, &n_loop);
+        if (st == PFF_OK) st = add_kernel<R>(m, body, {}, KP_MATVEC, G, &n_mv);
+        if (st == PFF_OK) st = add_kernel<R>(m, body, {n_mv}, KP_UPDATE, G, &n_up);
+      } else if (st == PFF_OK) {
+        m->pers_U = kind;
+        st = add_pers<R>(m, g[kind], {n_rhs}, G, &n_loop);
+        m->pers_U = keepU;
+      }
+      if (st == PFF_OK && cudaGraphInstantiate(&ge[kind], g[kind], 0) != cudaSuccess) {
+        ge[kind] = nullptr;
+        st = fail(PFF_ERR_CUDA, "autotune: instantiate");
+      }
+    }
+    float best[NK];
+    for (int kind = 0; kind < NK; ++kind) best[kind] = 1e30f;
+    for (int r = 0; r < 4 && !skip && st == PFF_OK; ++r) {  // first round: warm-up
+      for (int kind = 0; kind < NK && st == PFF_OK; ++kind) {
+        if (!ge[kind]) continue;
+        cudaEventRecord(e0, s);
+        if (cudaGraphLaunch(ge[kind], s) != cudaSuccess) st = fail(PFF_ERR_CUDA, "autotune: graph launch");
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) st = fail(PFF_ERR_CUDA, "autotune: CG loop timing");
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        if (r > 0) best[kind] = std::min(best[kind], t);
+        if (kind > 0 && st == PFF_OK) {
+          SolveScalars hs;
+          if (cudaMemcpy(&hs, m->sc, sizeof(hs), cudaMemcpyDeviceToHost) != cudaSuccess)
+            st = fail(PFF_ERR_CUDA, "autotune: scalars");
+          else if (hs.status == kStTimeout)
+            st = fail(PFF_ERR_TIMEOUT, "autotune: a grid-barrier wait of the persistent CG timed out");
+        }
+      }
+    }
+    if (!skip && st == PFF_OK) {
+      int bu = 0;
+      for (int kind = 1; kind < NK; ++kind)
+        if (ge[kind] && (bu == 0 || best[kind] < best[bu])) bu = kind;
+      m->pers_ms[0] = best[0];
+      m->pers_ms[1] = bu ? best[bu] : 0.f;
+      if (bu) m->pers_U = bu;
+      m->pers_faster = bu != 0 && best[bu] < best[0];
+    }
+    for (int kind = 0; kind < NK; ++kind) {
+      if (ge[kind]) cudaGraphExecDestroy(ge[kind]);
+      if (g[kind]) cudaGraphDestroy(g[kind]);
+    }
+    if (!skip) m->pers_tuned = true;
+    res = st;
+  }
   cudaStreamSynchronize(s);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -688,11 +866,13 @@ static pff_status autotune(pff_mesh *m, const pff_options &o, Params<R> P, bool 
 
 // Host-polled variant of the same solve (debugging / PFF_LOOP_HOST).
 template <typename R>
-static pff_status solve_host_loop(const pff_mesh *m, Params<R> P, cudaStream_t s) {
+static pff_status solve_host_loop(const pff_mesh *m, Params<R> P, bool pers, cudaStream_t s) {
   P.use_cond = 0;
   SolveScalars hs;
   PFF_TRY(launch<R>(m, KP_RHS, P, s));
-  if (P.model == kAT1) {
+  if (pers) {
+    PFF_TRY(launch_pers<R>(m, P, s));
+  } else if (P.model == kAT1) {
     for (;;) {
       PFF_TRY(launch<R>(m, KP_RESTART, P, s));
       CUDA_TRY(cudaMemcpyAsync(&hs, P.sc, sizeof(hs), cudaMemcpyDeviceToHost, s));
@@ -728,12 +908,13 @@ static pff_status damage_solve_t(pff_mesh *m, const double *H, const void *dprev
   P.dprev = (const R *)dprev;
   P.dout = (R *)dout;
   PFF_TRY(autotune<R>(m, o, P, false, true, s));
+  const bool pers = use_persistent(m, o, P.model);
   if (o.loop_mode == PFF_LOOP_HOST) {
-    PFF_TRY(solve_host_loop<R>(m, P, s));
+    PFF_TRY(solve_host_loop<R>(m, P, pers, s));
   } else {
     std::vector<uint64_t> key = {(uint64_t)H, (uint64_t)dprev, (uint64_t)dout, (uint64_t)m->var[KP_RHS],
                                  (uint64_t)m->var[KP_MATVEC],
-                                 (uint64_t)o.cg_max_it, (uint64_t)o.max_restarts};
+                                 (uint64_t)o.cg_max_it, (uint64_t)o.max_restarts, (uint64_t)pers};
     uint64_t tb;
     std::memcpy(&tb, &o.cg_tol, 8);
     key.push_back(tb);
@@ -741,12 +922,14 @@ static pff_status damage_solve_t(pff_mesh *m, const double *H, const void *dprev
       free_graph(m->solve_g);
       cudaGraph_t g;
       CUDA_TRY(cudaGraphCreate(&g, 0));
-      CUDA_TRY(cudaGraphConditionalHandleCreate(&P.cond_inner, g, 1, cudaGraphCondAssignDefault));
-      if (P.model == kAT1)  // an unused handle makes instantiation fail
-        CUDA_TRY(cudaGraphConditionalHandleCreate(&P.cond_outer, g, 1, cudaGraphCondAssignDefault));
-      P.use_cond = 1;
+      if (!pers) {  // an unused handle makes instantiation fail
+        CUDA_TRY(cudaGraphConditionalHandleCreate(&P.cond_inner, g, 1, cudaGraphCondAssignDefault));
+        if (P.model == kAT1)
+          CUDA_TRY(cudaGraphConditionalHandleCreate(&P.cond_outer, g, 1, cudaGraphCondAssignDefault));
+      }
+      P.use_cond = pers ? 0 : 1;
       cudaGraphNode_t last;
-      pff_status st = append_solve<R>(m, g, nullptr, P, &last);
+      pff_status st = append_solve<R>(m, g, nullptr, P, pers, &last);
       if (st != PFF_OK) {
         cudaGraphDestroy(g);
         return st;
@@ -769,6 +952,7 @@ static pff_status damage_solve_t(pff_mesh *m, const double *H, const void *dprev
   if (relres) *relres = hs.bn > 0 ? std::sqrt(hs.rr) / hs.bn : 0.0;
   if (hs.status == kStNotConverged) return fail(PFF_ERR_NOT_CONVERGED, "damage CG did not converge");
   if (hs.status == kStNonfinite) return fail(PFF_ERR_NONFINITE, "non-finite residual in damage CG");
+  if (hs.status == kStTimeout) return fail(PFF_ERR_TIMEOUT, "a grid-barrier wait of the CG timed out");
   return PFF_OK;
 }
 
@@ -852,6 +1036,7 @@ static pff_status run_t(pff_mesh *m, const pff_state *st, int64_t step0, int64_t
   P.iters_log = iters_log;  // indexed by the step within this run
   P.track_work = o.energy_every > 0 ? 1 : 0;
   PFF_TRY(autotune<R>(m, o, P, true, true, s));
+  const bool pers = use_persistent(m, o, P.model);
   const int64_t zero = 0;
   CUDA_TRY(cudaMemcpyAsync(m->step_ctr, &zero, sizeof(int64_t), cudaMemcpyHostToDevice, s));
   CUDA_TRY(cudaStreamSynchronize(s));
@@ -861,7 +1046,7 @@ static pff_status run_t(pff_mesh *m, const pff_state *st, int64_t step0, int64_t
     for (int64_t n = 0; n < nsteps; ++n) {
       PFF_TRY(launch<R>(m, KP_PREDICT, P, s));
       PFF_TRY(launch<R>(m, KP_FORCE, P, s));
-      PFF_TRY(solve_host_loop<R>(m, P, s));
+      PFF_TRY(solve_host_loop<R>(m, P, pers, s));
       if (tape) k_tape_store<R><<<Gtape, kThreads, 0, s>>>(P, *tape);
       if (energy_log && o.energy_every > 0 && (n + 1) % o.energy_every == 0) {
         Params<R> E = P;
@@ -876,7 +1061,7 @@ static pff_status run_t(pff_mesh *m, const pff_state *st, int64_t step0, int64_t
                                (uint64_t)st->H, (uint64_t)o.cg_max_it, (uint64_t)m->var[KP_FORCE],
                                (uint64_t)m->var[KP_RHS], (uint64_t)m->var[KP_MATVEC],
                                (uint64_t)o.max_restarts, (uint64_t)P.iters_log, (uint64_t)P.track_work,
-                               (uint64_t)m->stab, (uint64_t)(tape ? tape->u : nullptr)};
+                               (uint64_t)m->stab, (uint64_t)(tape ? tape->u : nullptr), (uint64_t)pers};
   uint64_t b1, b2;
   std::memcpy(&b1, &o.cg_tol, 8);
   std::memcpy(&b2, &dt, 8);
@@ -886,14 +1071,16 @@ static pff_status run_t(pff_mesh *m, const pff_state *st, int64_t step0, int64_t
     free_graph(gc);
     cudaGraph_t g;
     CUDA_TRY(cudaGraphCreate(&g, 0));
-    CUDA_TRY(cudaGraphConditionalHandleCreate(&P.cond_inner, g, 1, cudaGraphCondAssignDefault));
-    if (P.model == kAT1)
-      CUDA_TRY(cudaGraphConditionalHandleCreate(&P.cond_outer, g, 1, cudaGraphCondAssignDefault));
-    P.use_cond = 1;
+    if (!pers) {  // an unused handle makes instantiation fail
+      CUDA_TRY(cudaGraphConditionalHandleCreate(&P.cond_inner, g, 1, cudaGraphCondAssignDefault));
+      if (P.model == kAT1)
+        CUDA_TRY(cudaGraphConditionalHandleCreate(&P.cond_outer, g, 1, cudaGraphCondAssignDefault));
+    }
+    P.use_cond = pers ? 0 : 1;
     cudaGraphNode_t n_pr, n_f, last;
     pff_status stt = add_kernel<R>(m, g, {}, KP_PREDICT, P, &n_pr);
     if (stt == PFF_OK) stt = add_kernel<R>(m, g, {n_pr}, KP_FORCE, P, &n_f);
-    if (stt == PFF_OK) stt = append_solve<R>(m, g, n_f, P, &last);
+    if (stt == PFF_OK) stt = append_solve<R>(m, g, n_f, P, pers, &last);
     if (stt == PFF_OK && tape) {
       cudaKernelNodeParams kp;
       std::memset(&kp, 0, sizeof(kp));
@@ -1324,6 +1511,16 @@ pff_status pff_mesh_schedule(const pff_mesh *m, int32_t *variant, float *tune_ms
   return PFF_OK;
 }
 
+pff_status pff_mesh_cg_choice(const pff_mesh *m, int32_t *cg_kernel, int32_t *gathers, float *ms_phases,
+                              float *ms_persistent) {
+  if (!m) return fail(PFF_ERR_ARG, "null mesh");
+  if (cg_kernel) *cg_kernel = !m->pers_tuned ? PFF_CG_AUTO : (m->pers_faster ? PFF_CG_PERSISTENT : PFF_CG_PHASES);
+  if (gathers) *gathers = pers_u(m);
+  if (ms_phases) *ms_phases = m->pers_ms[0];
+  if (ms_persistent) *ms_persistent = m->pers_ms[1];
+  return PFF_OK;
+}
+
 }  // extern "C"
 
 // =============================================== damage solve, no allocation
@@ -1431,7 +1628,7 @@ static pff_status noalloc_solve_t(pff_mesh *m, const double *H, const void *dpre
   P.status_word = nullptr;
   P.energy_out = nullptr;
   P.wext = nullptr;
-  PFF_TRY(solve_host_loop<R>(m, P, s));
+  PFF_TRY(solve_host_loop<R>(m, P, false, s));
   SolveScalars hs;
   CUDA_TRY(cudaMemcpyAsync(&hs, P.sc, sizeof(hs), cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaStreamSynchronize(s));
@@ -1469,13 +1666,18 @@ pff_status pff_damage_solve_noalloc(pff_mesh *m, const double *H, const void *dp
 
 // ====================================================== checkpoints, adjoint
 //
-// pff_run_ckpt stores the state at the start of every segment of `every`
-// steps; pff_backward walks the segments last to first: it restores the
-// segment's checkpoint, recomputes its steps (bit-identical: same kernels,
-// same schedules, deterministic accumulation) while taping u_{n+1},
-// x_{n+1}, d_{n+1} and H_{n+1}, then reverses the steps one by one
-// (Sec. 4.2, implicit differentiation of each damage solve; the reverse of
-// the explicit mechanics).  Memory: O(N (nsteps/every + every)).
+// Two tape policies.  Full tape (every = 0): pff_run_ckpt tapes u_{n+1},
+// x_{n+1}, d_{n+1} and H_{n+1} of every step as it runs, so the backward
+// is the reverse sweep alone; memory O(N nsteps), which HBM holds for the
+// plates of this library (Sec. 7: the whole activation tape on the GPU).
+// Checkpointed (every > 0): pff_run_ckpt stores the state at the start of
+// every segment of `every` steps; pff_backward walks the segments last to
+// first: it restores the segment's checkpoint, recomputes its steps
+// (bit-identical: same kernels, same schedules, deterministic accumulation)
+// while taping, then reverses them; memory O(N (nsteps/every + every)) for
+// one more forward pass (Sec. 7, gradient checkpointing).  Either way each
+// step is reversed one by one (Sec. 4.2, implicit differentiation of each
+// damage solve; the reverse of the explicit mechanics).
 
 struct pff_ckpt {
   pff_mesh *m = nullptr;
@@ -1483,6 +1685,7 @@ struct pff_ckpt {
   int32_t every = 0, nseg = 0;
   double dt = 0.0;
   bool filled = false;
+  bool full = false;  // whole run taped in the forward, no recompute
   size_t rs = 0;  // sizeof(R)
   // checkpoints: nseg x (u, v, a, d, H)
   void *su = nullptr, *sv = nullptr, *sa = nullptr, *sd = nullptr;
@@ -1521,8 +1724,9 @@ static void ckpt_free(pff_ckpt *c) {
 
 static pff_status ckpt_alloc(pff_ckpt *c) {
   const size_t N = c->m->N + 2, Ne = c->m->Ne, r = c->rs, r2 = 2 * c->rs;
-  const size_t S = c->nseg, E = c->every;
+  const size_t S = c->full ? 0 : c->nseg, E = c->every, W = c->full ? 0 : 1;
   auto A = [&](void **p, size_t bytes) -> pff_status {
+    if (bytes == 0) return PFF_OK;
     CUDA_TRY(cudaMalloc(p, bytes));
     CUDA_TRY(cudaMemset(*p, 0, bytes));
     return PFF_OK;
@@ -1536,12 +1740,12 @@ static pff_status ckpt_alloc(pff_ckpt *c) {
   PFF_TRY(A(&c->tx, E * N * r));
   PFF_TRY(A(&c->td, E * N * r));
   PFF_TRY(A((void **)&c->tH, E * Ne * 8));
-  PFF_TRY(A(&c->wu, N * r2));
-  PFF_TRY(A(&c->wv, N * r2));
-  PFF_TRY(A(&c->wa, N * r2));
-  PFF_TRY(A(&c->wd, N * r));
+  PFF_TRY(A(&c->wu, W * N * r2));
+  PFF_TRY(A(&c->wv, W * N * r2));
+  PFF_TRY(A(&c->wa, W * N * r2));
+  PFF_TRY(A(&c->wd, W * N * r));
   PFF_TRY(A(&c->segd, N * r));
-  PFF_TRY(A((void **)&c->wH, Ne * 8));
+  PFF_TRY(A((void **)&c->wH, W * Ne * 8));
   PFF_TRY(A((void **)&c->segH, Ne * 8));
   for (int q = 0; q < 2; ++q) {
     PFF_TRY(A(&c->ub[q], N * r2));
@@ -1563,7 +1767,19 @@ template <typename R>
 static pff_status run_ckpt_t(pff_mesh *m, const pff_state *st, int64_t step0, int64_t nsteps, double dt,
                              const pff_options &o, pff_ckpt *c, int32_t *iters_log, cudaStream_t s) {
   const size_t N = m->N, Np = m->N + 2, Ne = m->Ne, r = sizeof(R), r2 = 2 * sizeof(R);
-  for (int32_t seg = 0; seg < c->nseg; ++seg) {
+  if (c->full) {
+    CUDA_TRY(cudaMemcpyAsync(c->segd, st->d, N * r, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(c->segH, st->H, Ne * 8, cudaMemcpyDeviceToDevice, s));
+    Tape tape;
+    tape.u = c->tu;
+    tape.x = c->tx;
+    tape.d = c->td;
+    tape.H = c->tH;
+    tape.stride_n = (int64_t)Np;
+    tape.stride_e = (int64_t)Ne;
+    PFF_TRY(run_t<R>(m, st, step0, nsteps, dt, o, iters_log, nullptr, s, &c->rec_g, &tape));
+  }
+  for (int32_t seg = 0; !c->full && seg < c->nseg; ++seg) {
     const int64_t k0 = (int64_t)seg * c->every;
     const int64_t len = std::min<int64_t>(c->every, nsteps - k0);
     CUDA_TRY(cudaMemcpyAsync((char *)c->su + seg * Np * r2, st->u, N * r2, cudaMemcpyDeviceToDevice, s));
@@ -1597,15 +1813,15 @@ static pff_status add_generic(cudaGraph_t g, const std::vector<cudaGraphNode_t> 
 }
 
 template <typename R>
-static pff_status build_reverse_graph(pff_mesh *m, pff_ckpt *c, AdjParams<R> A, GraphCache &gcache,
+static pff_status build_reverse_graph(pff_mesh *m, pff_ckpt *c, AdjParams<R> A, bool pers, GraphCache &gcache,
                                       const std::vector<uint64_t> &key) {
   const unsigned Gn = std::min<unsigned>(grid_for(m->N, kThreads), m->grid[KP_UPDATE][0]);
   const unsigned Ge = std::min<unsigned>(grid_for(m->Ne, kThreads), m->grid[KP_UPDATE][0]);
   free_graph(gcache);
   cudaGraph_t g;
   CUDA_TRY(cudaGraphCreate(&g, 0));
-  CUDA_TRY(cudaGraphConditionalHandleCreate(&A.P.cond_inner, g, 1, cudaGraphCondAssignDefault));
-  A.P.use_cond = 1;
+  if (!pers) CUDA_TRY(cudaGraphConditionalHandleCreate(&A.P.cond_inner, g, 1, cudaGraphCondAssignDefault));
+  A.P.use_cond = pers ? 0 : 1;
   void *aa[] = {(void *)&A};
   void *ka[] = {(void *)&c->kctr};
   cudaGraphNode_t n_load, n_prep, n_rhs, n_loop, n_mv, n_up, n_terms, n_mech, n_done;
@@ -1613,9 +1829,13 @@ static pff_status build_reverse_graph(pff_mesh *m, pff_ckpt *c, AdjParams<R> A, 
   pff_status st = add_generic(g, {}, (const void *)k_adj_load<R>, Ge, kThreads, 0, aa, &n_load);
   if (st == PFF_OK) st = add_generic(g, {n_load}, (const void *)k_adj_prep<R>, Gn, kThreads, 0, aa, &n_prep);
   if (st == PFF_OK) st = add_generic(g, {n_prep}, (const void *)k_adj_rhs<R>, Gn, kThreads, 0, aa, &n_rhs);
-  if (st == PFF_OK) st = add_while(g, {n_rhs}, A.P.cond_inner, &body, &n_loop);
-  if (st == PFF_OK) st = add_kernel<R>(m, body, {}, KP_MATVEC, A.P, &n_mv);
-  if (st == PFF_OK) st = add_kernel<R>(m, body, {n_mv}, KP_UPDATE, A.P, &n_up);
+  if (pers) {
+    if (st == PFF_OK) st = add_pers<R>(m, g, {n_rhs}, A.P, &n_loop);
+  } else {
+    if (st == PFF_OK) st = add_while(g, {n_rhs}, A.P.cond_inner, &body, &n_loop);
+    if (st == PFF_OK) st = add_kernel<R>(m, body, {}, KP_MATVEC, A.P, &n_mv);
+    if (st == PFF_OK) st = add_kernel<R>(m, body, {n_mv}, KP_UPDATE, A.P, &n_up);
+  }
   if (st == PFF_OK)
     st = add_generic(g, {n_loop}, (const void *)k_adj_dmg_terms<R>, Ge, kThreads, 0, aa, &n_terms);
   if (st == PFF_OK) st = add_generic(g, {n_terms}, (const void *)k_adj_mech<R>, Gn, kThreads, 0, aa, &n_mech);
@@ -1662,6 +1882,7 @@ static pff_status backward_t(pff_mesh *m, pff_ckpt *c, const void *dL_dd, const 
   for (int32_t seg = c->nseg - 1; seg >= 0; --seg) {
     const int64_t k0 = (int64_t)seg * c->every;
     const int64_t len = std::min<int64_t>(c->every, c->nsteps - k0);
+    if (!c->full) {
     CUDA_TRY(cudaMemcpyAsync(c->wu, (char *)c->su + seg * Np * r2, N * r2, cudaMemcpyDeviceToDevice, s));
     CUDA_TRY(cudaMemcpyAsync(c->wv, (char *)c->sv + seg * Np * r2, N * r2, cudaMemcpyDeviceToDevice, s));
     CUDA_TRY(cudaMemcpyAsync(c->wa, (char *)c->sa + seg * Np * r2, N * r2, cudaMemcpyDeviceToDevice, s));
@@ -1678,6 +1899,7 @@ static pff_status backward_t(pff_mesh *m, pff_ckpt *c, const void *dL_dd, const 
     tape.stride_n = (int64_t)Np;
     tape.stride_e = (int64_t)Ne;
     PFF_TRY(run_t<R>(m, &w, c->step0 + k0, len, c->dt, ob, nullptr, nullptr, s, &c->rec_g, &tape));
+    }
     // reverse the segment
     const int kstart = (int)(len - 1);
     CUDA_TRY(cudaMemcpyAsync(c->kctr, &kstart, sizeof(int), cudaMemcpyHostToDevice, s));
@@ -1720,9 +1942,11 @@ static pff_status backward_t(pff_mesh *m, pff_ckpt *c, const void *dL_dd, const 
       std::memcpy(&tb, &o.cg_tol, 8);
       std::memcpy(&gb, &m->mat.Gc, 8);
       std::memcpy(&lb, &c->dt, 8);
+      const bool pers = use_persistent(m, o, kAT2);
       std::vector<uint64_t> key = {tb, gb, lb, (uint64_t)m->var[KP_MATVEC], (uint64_t)o.cg_max_it,
-                                   (uint64_t)m->mat.split};
-      if (!c->rev_g[q].exec || c->rev_g[q].key != key) PFF_TRY(build_reverse_graph<R>(m, c, A, c->rev_g[q], key));
+                                   (uint64_t)m->mat.split, (uint64_t)pers};
+      if (!c->rev_g[q].exec || c->rev_g[q].key != key)
+        PFF_TRY(build_reverse_graph<R>(m, c, A, pers, c->rev_g[q], key));
     }
     for (int64_t k = len - 1; k >= 0; --k) {
       CUDA_TRY(cudaGraphLaunch(c->rev_g[par].exec, s));
@@ -1739,6 +1963,7 @@ static pff_status backward_t(pff_mesh *m, pff_ckpt *c, const void *dL_dd, const 
   c->adj_iters = ks[2];
   if (ks[1] == kStNotConverged) return fail(PFF_ERR_NOT_CONVERGED, "an adjoint damage CG did not converge");
   if (ks[1] == kStNonfinite) return fail(PFF_ERR_NONFINITE, "non-finite value in an adjoint damage CG");
+  if (ks[1] == kStTimeout) return fail(PFF_ERR_TIMEOUT, "a grid-barrier wait of an adjoint CG timed out");
   return PFF_OK;
 }
 
@@ -1747,12 +1972,14 @@ static pff_status backward_t(pff_mesh *m, pff_ckpt *c, const void *dL_dd, const 
 extern "C" {
 
 pff_status pff_ckpt_create(pff_mesh *m, int64_t nsteps, int32_t every, pff_ckpt **out) {
-  if (!m || !out || nsteps <= 0 || every <= 0) return fail(PFF_ERR_ARG, "bad checkpoint arguments");
+  if (!m || !out || nsteps <= 0 || every < 0) return fail(PFF_ERR_ARG, "bad checkpoint arguments");
+  if (every == 0 && nsteps > INT32_MAX) return fail(PFF_ERR_ARG, "full tape: too many steps");
   *out = nullptr;
   pff_ckpt *c = new pff_ckpt();
   c->m = m;
   c->nsteps = nsteps;
-  c->every = (int32_t)std::min<int64_t>(every, nsteps);
+  c->full = every == 0;
+  c->every = (int32_t)std::min<int64_t>(every == 0 ? nsteps : every, nsteps);
   c->nseg = (int32_t)((nsteps + c->every - 1) / c->every);
   c->rs = m->prec == PFF_FP64 ? 8 : 4;
   const pff_status st = ckpt_alloc(c);

@@ -43,25 +43,26 @@ def test_fp64_adjoint_matches_oracle(orc, pff):
     st = om.new_state()
     om.run(dict(mat, Gc=3.0), st, nsteps, dt, tol=1e-13)
     dstar = st["d"].copy()
-    for Gc in (2.0, 3.5):
+    for Gc, every in ((2.0, 10), (3.5, 0)):
         L, g, status = om.adjoint_gc(dict(mat, Gc=Gc), nsteps, dt, dstar, tol=1e-13)
-        gL, gg, _ = _gpu_grad(pff, p, mat, Gc, nsteps, dstar, "fp64", 10, 1e-13)
+        gL, gg, _ = _gpu_grad(pff, p, mat, Gc, nsteps, dstar, "fp64", every, 1e-13)
         assert abs(gL - L) <= 1e-10 * L
         assert abs(gg - g) <= 1e-7 * abs(g), (gg, g)
 
 
 def test_checkpoint_segmentation_is_exact(orc, pff):
     """Recompute is bit-identical, so the gradient does not depend on the
-    checkpoint spacing; the checkpointed run equals a plain run."""
+    checkpoint spacing, and a full tape (every = 0, no recompute) gives the
+    same gradient; the taped run equals a plain run."""
     import torch
     p, mat = _problem()
     nsteps = 30
     dstar = np.zeros(p["xy"].shape[0])
     grads = []
-    for every in (1, 7, 30):
+    for every in (1, 7, 30, 0):
         L, g, st = _gpu_grad(pff, p, mat, 2.5, nsteps, dstar, "fp32", every, 1e-8)
         grads.append(g)
-    assert grads[0] == grads[1] == grads[2]
+    assert grads[0] == grads[1] == grads[2] == grads[3]
     mesh = pff.Mesh.from_plate(p, precision="fp32")
     mesh.set_material(dict(mat, Gc=2.5), 0.5)
     s2 = mesh.new_state()

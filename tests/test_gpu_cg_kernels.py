@@ -1,0 +1,157 @@
+"""The two AT2 CG loops (a matvec and an update kernel per iteration, or the
+whole solve in one persistent cooperative kernel with grid barriers)
+against the oracle and against each other, on meshes from one CTA to a
+full wave; the bounded barrier wait; the autotuner's report."""
+import numpy as np
+import pytest
+
+import pff_synth as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pff():
+    import paper_2606_23458_b300 as pff
+    return pff
+
+
+def _inputs(p, seed):
+    rng = np.random.default_rng(seed)
+    Ne, N = p["tri"].shape[0], p["xy"].shape[0]
+    H = rng.uniform(0, 400, Ne) * (rng.uniform(size=Ne) < 0.4)
+    dprev = np.where(p["notch"] == 1, 1.0, rng.uniform(0, 0.3, N) * (rng.uniform(size=N) < 0.3))
+    return H, dprev
+
+
+def _solve(pff, mesh, H, dprev, cgk, tol=1e-8):
+    import torch
+    Ht = torch.tensor(H, device="cuda")
+    dp = torch.tensor(dprev, device="cuda", dtype=mesh.dtype)
+    out = torch.full_like(dp, float("nan"))
+    info = mesh.damage_solve(Ht, dp, out, opts=pff.options(cg_tol=tol, cg_kernel=cgk))
+    torch.cuda.synchronize()
+    return out.double().cpu().numpy(), info
+
+
+# 20 x 8: 189 nodes, one CTA; 300 x 120: 36,421 nodes, 36 CTAs;
+# 520 x 300 jittered: 156,821 nodes, one CTA per SM
+SIZES = [(20, 8, 0.0), (300, 120, 0.0), (520, 300, 0.1)]
+
+
+@pytest.mark.parametrize("nx,ny,jit", SIZES)
+def test_persistent_damage_solve_fp64_vs_oracle(orc, pff, nx, ny, jit):
+    """FP64: the persistent solve stops where the kernel-per-phase solve
+    stops, and both agree with the oracle forced to that iteration count."""
+    p = S.plate(nx, ny, jitter=jit, seed=5)
+    mat = S.material(2 * p["h"])
+    mesh = pff.Mesh.from_plate(p, precision="fp64")
+    mesh.set_material(mat, 0.5)
+    om = orc.Mesh.from_plate(p)
+    H, dprev = _inputs(p, 11)
+    d_pe, i_pe = _solve(pff, mesh, H, dprev, pff.PFF_CG_PERSISTENT)
+    d_ph, i_ph = _solve(pff, mesh, H, dprev, pff.PFF_CG_PHASES)
+    assert i_pe["iters"] == i_ph["iters"] > 0
+    d_or, info, rel, st, _ = om.damage_solve(mat, H, dprev, forced=i_pe["iters"])
+    scale = np.maximum(np.abs(d_or), 1e-3)
+    assert np.max(np.abs(d_pe - d_or) / scale) <= 1e-10
+    assert np.max(np.abs(d_ph - d_or) / scale) <= 1e-10
+    assert i_pe["relres"] <= 1e-8 * 1.0001
+
+
+@pytest.mark.parametrize("nx,ny,jit", SIZES)
+def test_persistent_damage_solve_fp32(pff, nx, ny, jit):
+    p = S.plate(nx, ny, jitter=jit, seed=5)
+    mesh = pff.Mesh.from_plate(p, precision="fp32")
+    mesh.set_material(S.material(2 * p["h"]), 0.5)
+    for seed in (1, 2):
+        H, dprev = _inputs(p, seed)
+        d_pe, i_pe = _solve(pff, mesh, H, dprev, pff.PFF_CG_PERSISTENT)
+        d_ph, i_ph = _solve(pff, mesh, H, dprev, pff.PFF_CG_PHASES)
+        assert abs(i_pe["iters"] - i_ph["iters"]) <= 1
+        assert np.max(np.abs(d_pe - d_ph) / np.maximum(np.abs(d_ph), 1e-3)) <= 1e-4
+        assert i_pe["relres"] <= 2.0 ** -22 * 1.0001
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_persistent_run_vs_phase_run(pff, prec):
+    """60 staggered steps of the 100 x 40 plate with each loop: the same
+    iteration counts (FP64; within one in FP32) and the same fields."""
+    import torch
+    c = S.config("plate_100x40")
+    res = {}
+    for cgk in (pff.PFF_CG_PHASES, pff.PFF_CG_PERSISTENT):
+        mesh = pff.Mesh.from_plate(c["mesh"], precision=prec)
+        mesh.set_material(c["material"], c["cfl"])
+        st = mesh.new_state()
+        log = torch.zeros(60, 2, dtype=torch.int32, device="cuda")
+        mesh.run(st, 60, opts=pff.options(cg_tol=c["cg_tol"], t_ramp=c["t_ramp"], cg_kernel=cgk),
+                 iters_log=log)
+        torch.cuda.synchronize()
+        assert mesh.sync_status() == 0
+        res[cgk] = ({k: v.double().cpu().numpy() for k, v in st.items()}, log[:, 0].cpu().numpy())
+    (a, ia), (b, ib) = res[pff.PFF_CG_PHASES], res[pff.PFF_CG_PERSISTENT]
+    if prec == "fp64":
+        assert np.array_equal(ia, ib)
+        tol = 1e-10
+    else:
+        assert np.max(np.abs(ia - ib)) <= 1
+        tol = 1e-4
+    for k in ("u", "d", "H"):
+        err = np.linalg.norm(a[k] - b[k]) / max(np.linalg.norm(a[k]), 1e-300)
+        assert err <= tol, (k, err)
+
+
+def test_persistent_backward_matches_phases(pff):
+    import torch
+    p = S.plate(40, 16)
+    mat = S.material(2 * p["h"])
+    grads = []
+    for cgk in (pff.PFF_CG_PHASES, pff.PFF_CG_PERSISTENT):
+        mesh = pff.Mesh.from_plate(p, precision="fp64")
+        mesh.set_material(dict(mat, Gc=2.5), 0.5)
+        opts = pff.options(cg_tol=1e-12, cg_kernel=cgk)
+        st = mesh.new_state()
+        ck = pff.Checkpoint(mesh, 30, 0)
+        mesh.run_ckpt(st, ck, opts=opts)
+        g = (2.0 * st["d"] / mesh.N).contiguous()
+        grads.append(mesh.backward(ck, g, opts=opts))
+        ck.close()
+    assert abs(grads[0] - grads[1]) <= 1e-9 * abs(grads[0]), grads
+
+
+def test_bounded_barrier_wait_reports_timeout(pff):
+    """A barrier that awaits one CTA more than the grid gives up after its
+    wait limit: the call returns PFF_ERR_TIMEOUT, the context stays usable
+    and the next solve is correct."""
+    import torch
+    p = S.plate(60, 24)
+    mesh = pff.Mesh.from_plate(p, precision="fp32")
+    mesh.set_material(S.material(2 * p["h"]), 0.5)
+    H, dprev = _inputs(p, 3)
+    Ht = torch.tensor(H, device="cuda")
+    dp = torch.tensor(dprev, device="cuda", dtype=mesh.dtype)
+    out = torch.empty_like(dp)
+    info = mesh.damage_solve(Ht, dp, out, opts=pff.options(cg_kernel=pff.PFF_CG_TEST_TIMEOUT),
+                             raise_on_error=False)
+    assert info["status"] == pff.PFF_ERR_TIMEOUT
+    assert "timed out" in pff._lib.pff_last_error().decode()
+    d_pe, i_pe = _solve(pff, mesh, H, dprev, pff.PFF_CG_PERSISTENT)
+    d_ph, i_ph = _solve(pff, mesh, H, dprev, pff.PFF_CG_PHASES)
+    assert i_pe["status"] == i_ph["status"] == 0
+    assert np.max(np.abs(d_pe - d_ph) / np.maximum(np.abs(d_ph), 1e-3)) <= 1e-4
+
+
+def test_autotuner_reports_cg_loop(pff):
+    import torch
+    c = S.config("plate_100x40")
+    mesh = pff.Mesh.from_plate(c["mesh"], precision="fp32")
+    mesh.set_material(c["material"], c["cfl"])
+    assert mesh.cg_choice()[0] == "auto"
+    st = mesh.new_state()
+    mesh.run(st, 5)
+    torch.cuda.synchronize()
+    kind, ms_ph, ms_pe, U = mesh.cg_choice()
+    assert kind in ("phases", "persistent")
+    assert ms_ph > 0 and ms_pe > 0 and 1 <= U <= 4
+    assert (kind == "persistent") == (ms_pe < ms_ph)
