@@ -53,7 +53,8 @@ enum { PFF_SPLIT_SPECTRAL = 0, PFF_SPLIT_AMOR = 1, PFF_SPLIT_ISO = 2 };
 enum { PFF_PLANE_STRAIN = 0 };
 enum { PFF_FP64 = 0, PFF_FP32_MIXED = 1 };
 enum { PFF_LOOP_GRAPH = 0, PFF_LOOP_HOST = 1 };
-enum { PFF_CG_AUTO = 0, PFF_CG_PHASES = 1, PFF_CG_PERSISTENT = 2, PFF_CG_TEST_TIMEOUT = 3 };
+enum { PFF_CG_AUTO = 0, PFF_CG_PHASES = 1, PFF_CG_PERSISTENT = 2, PFF_CG_TEST_TIMEOUT = 3,
+       PFF_CG_STAGED = 4, PFF_CG_FUSED = 5, PFF_CG_FUSED_STAGED = 6 };
 
 typedef struct pff_mesh pff_mesh; /* opaque; owns geometry, CSR, workspaces */
 
@@ -86,10 +87,22 @@ typedef struct {
                            in flight.  All give bit-identical results. */
   int32_t cg_kernel;    /* AT2 CG loop: PFF_CG_PHASES = a matvec and an
                            update kernel per iteration; PFF_CG_PERSISTENT =
-                           the whole solve in one cooperative kernel (one
-                           CTA per SM, grid barriers with bounded waits,
-                           PFF_ERR_TIMEOUT if one gives up); PFF_CG_AUTO =
-                           the faster on this mesh, timed on first use [0].
+                           the whole solve in one cooperative kernel (all
+                           CTAs resident, grid barriers with bounded waits,
+                           PFF_ERR_TIMEOUT if one gives up);
+                           PFF_CG_STAGED = the same kernel with each CTA's
+                           element records and history copied into shared
+                           memory once per solve (FP32 meshes whose CTA
+                           sets fit, else as PFF_CG_PERSISTENT);
+                           PFF_CG_FUSED = one cooperative kernel running the
+                           single-reduction (Chronopoulos-Gear) form of the
+                           same Jacobi PCG: one pass and one grid
+                           all-reduce per iteration (FP32; FP64 meshes use
+                           the kernel-per-phase loop);
+                           PFF_CG_FUSED_STAGED = that with the operator
+                           staged in shared memory;
+                           PFF_CG_AUTO = the fastest on this mesh, timed on
+                           first use [0].
                            Same iteration arithmetic; the two group the
                            partial sums of the dot products differently.
                            AT1 always uses the kernel-per-phase loop.
@@ -269,12 +282,12 @@ pff_status pff_profile_kernels(pff_mesh *mesh, const pff_state *state, double dt
 pff_status pff_mesh_schedule(const pff_mesh *mesh, int32_t *variant, float *tune_ms);
 
 /* The AT2 CG loop the autotuner chose on this mesh: *cg_kernel =
- * PFF_CG_PHASES or PFF_CG_PERSISTENT (PFF_CG_AUTO while not yet timed), the
- * persistent kernel's gathers in flight (1..4), and the timings of 8
- * iterations in ms of the kernel-per-phase loop and of the best persistent
- * kernel (0 if not timed).  Host scalars; each pointer nullable. */
-pff_status pff_mesh_cg_choice(const pff_mesh *mesh, int32_t *cg_kernel, int32_t *gathers,
-                              float *ms_phases, float *ms_persistent);
+ * PFF_CG_PHASES, _PERSISTENT, _STAGED, _FUSED or _FUSED_STAGED (PFF_CG_AUTO
+ * while not yet timed), the chosen persistent kernel's gathers in flight
+ * (1..4, 0 for phases), and ms[5]: 8 iterations of the kernel-per-phase
+ * loop and of the best variant of each persistent kernel in that order (0
+ * if not timed or not available).  Host outputs; each pointer nullable. */
+pff_status pff_mesh_cg_choice(const pff_mesh *mesh, int32_t *cg_kernel, int32_t *gathers, float *ms);
 
 /* The damage solve of pff_damage_solve, for callers that must not allocate
  * device memory during the call.  The paper has no counterpart of this entry

@@ -28,6 +28,9 @@ PFF_SPLIT_SPECTRAL, PFF_SPLIT_AMOR, PFF_SPLIT_ISO = 0, 1, 2
 PFF_FP64, PFF_FP32_MIXED = 0, 1
 PFF_LOOP_GRAPH, PFF_LOOP_HOST = 0, 1
 PFF_CG_AUTO, PFF_CG_PHASES, PFF_CG_PERSISTENT, PFF_CG_TEST_TIMEOUT = 0, 1, 2, 3
+PFF_CG_STAGED, PFF_CG_FUSED, PFF_CG_FUSED_STAGED = 4, 5, 6
+CG_KINDS = {PFF_CG_AUTO: "auto", PFF_CG_PHASES: "phases", PFF_CG_PERSISTENT: "persistent",
+            PFF_CG_STAGED: "staged", PFF_CG_FUSED: "fused", PFF_CG_FUSED_STAGED: "fused_staged"}
 
 MODELS = {"AT1": PFF_AT1, "AT2": PFF_AT2}
 SPLITS = {"spectral": PFF_SPLIT_SPECTRAL, "amor": PFF_SPLIT_AMOR, "iso": PFF_SPLIT_ISO}
@@ -87,7 +90,7 @@ _sig = {
     "pff_profile_kernels": [_P, C.POINTER(pff_state), C.c_double, C.POINTER(pff_options),
                             C.c_int32, _P, _P],
     "pff_mesh_schedule": [_P, _P, _P],
-    "pff_mesh_cg_choice": [_P, _P, _P, _P, _P],
+    "pff_mesh_cg_choice": [_P, _P, _P, _P],
     "pff_ckpt_create": [_P, C.c_int64, C.c_int32, C.POINTER(C.c_void_p)],
     "pff_ckpt_destroy": [_P],
     "pff_ckpt_stats": [_P, C.POINTER(C.c_int64)],
@@ -408,15 +411,14 @@ class Mesh:
 
     def cg_choice(self):
         """(AT2 CG loop in use: "auto" (not timed yet) / "phases" /
-        "persistent", ms of 8 iterations kernel-per-phase, ms persistent,
-        gathers in flight of the persistent kernel)."""
+        "persistent" / "staged" / "fused" / "fused_staged", its gathers in
+        flight, and {loop: ms of 8 iterations of its best variant})."""
         k = C.c_int32()
         u = C.c_int32()
-        a = C.c_float()
-        b = C.c_float()
-        _check(_lib.pff_mesh_cg_choice(self._h, C.byref(k), C.byref(u), C.byref(a), C.byref(b)))
-        return {PFF_CG_AUTO: "auto", PFF_CG_PHASES: "phases",
-                PFF_CG_PERSISTENT: "persistent"}[k.value], a.value, b.value, u.value
+        ms = np.zeros(5, np.float32)
+        _check(_lib.pff_mesh_cg_choice(self._h, C.byref(k), C.byref(u), _hp(ms)))
+        names = ("phases", "persistent", "staged", "fused", "fused_staged")
+        return CG_KINDS[k.value], u.value, {n: float(x) for n, x in zip(names, ms)}
 
     KERNELS = ("predict", "force", "rhs", "matvec", "update", "finish", "energies")
 

@@ -76,6 +76,14 @@ struct SolveScalars {
   int32_t abort;          // persistent CG: a barrier wait gave up
 };
 
+// One CTA's share of the shared-memory staging: rows [row0, row1); element
+// ranges [r0, r1) of the range table, nel elements in all, localized records
+// at lrec; node ranges [n0, n1), nn nodes in all, of which row row0 is at
+// position own.
+struct StageCta {
+  int32_t row0, row1, r0, r1, nel, lrec, n0, n1, nn, own;
+};
+
 // Everything a kernel needs, passed by value (graph-captured).
 template <typename R> struct Params {
   typedef typename V<R>::T2 R2;
@@ -91,6 +99,21 @@ template <typename R> struct Params {
   const uint8_t *__restrict__ flags;
   const R2 *__restrict__ fext;
   const R *__restrict__ minv;
+  // operator staged in shared memory by the persistent CG (FP32), per CTA
+  // (see StageCta): element ranges (first element, count), node ranges
+  // (first node, count), element records with node ids replaced by node
+  // positions in the CTA's staged node set, and the row entries: entry k of
+  // row i at st_slot[k * st_ns + i] = position << 2 | a (0xffff: none)
+  const StageCta *__restrict__ st_cta;
+  const int2 *__restrict__ st_rng;
+  const int2 *__restrict__ st_nrng;
+  const ERec<float> *__restrict__ st_lrec;
+  const uint16_t *__restrict__ st_slot;
+  int32_t st_ns;
+  // single-reduction CG (FP32): per node (r, w, s, 1/diag) in two buffers
+  // (read one, write the other each pass) and the search direction p
+  float4 *cgv0, *cgv1;
+  float *cgp;
   // material
   R lam, mu, K, eta;
   int32_t split, model;
@@ -752,6 +775,18 @@ __device__ __forceinline__ R pnew(const Params<R> &P, int j, R beta) {
 // matrix_free_fe_operator): element coefficients are rebuilt from the
 // geometry and the history on every application.
 template <typename R>
+__device__ __forceinline__ R mv_entry_vals(const Params<R> &P, const int4 &t, R A, const typename Params<R>::R4 &G,
+                                           R h, int a, R beta, R pc) {
+  const R kA = P.kappa * A;
+  const R mA = (P.cbase + R(2) * h) * A * (R(1) / R(12));
+  // the entry's own node (slot a) is the row's node: its value is pc
+  const R p0 = a == 0 ? pc : pnew(P, t.x, beta);
+  const R p1 = a == 1 ? pc : pnew(P, t.y, beta);
+  const R p2 = a == 2 ? pc : pnew(P, t.z, beta);
+  return elem_row<R>(G, a, kA, mA, p0, p1, p2);
+}
+
+template <typename R>
 __device__ __forceinline__ R mv_entry(const Params<R> &P, int en, R beta, R pc) {
   typedef typename Params<R>::R4 R4;
   const int e = en >> 2, a = en & 3;
@@ -759,13 +794,42 @@ __device__ __forceinline__ R mv_entry(const Params<R> &P, int en, R beta, R pc) 
   R A;
   R4 G;
   load_elem(P, e, t, A, G);
-  const R kA = P.kappa * A;
-  const R mA = (P.cbase + R(2) * P.Hr[e]) * A * (R(1) / R(12));
-  // the entry's own node (slot a) is the row's node: its value is pc
-  const R p0 = a == 0 ? pc : pnew(P, t.x, beta);
-  const R p1 = a == 1 ? pc : pnew(P, t.y, beta);
-  const R p2 = a == 2 ? pc : pnew(P, t.z, beta);
-  return elem_row<R>(G, a, kA, mA, p0, p1, p2);
+  return mv_entry_vals<R>(P, t, A, G, P.Hr[e], a, beta, pc);
+}
+
+// Rows n0 + threadIdx.x, ... < n1 of q = A p_new from the element records
+// and history staged in shared memory (srec: 32-byte records as float4
+// pairs, sh: H), U entries in flight; same per-entry arithmetic and
+// summation order as matvec_rows.
+template <int U>
+__device__ __forceinline__ void matvec_rows_staged(const Params<float> &P, float beta, int n0, int n1,
+                                                   const float4 *srec, const float *sh, DF &acc) {
+  typedef Acc<float> AC;
+  for (int i = n0 + (int)threadIdx.x; i < n1; i += blockDim.x) {
+    float q = 0.f;
+    if (!is_fixed(P, i)) {
+      const float pc = pnew(P, i, beta);
+      for (int k = 0; k < P.D; k += U) {
+        float c[U];
+        unsigned sl[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) sl[u] = k + u < P.D ? (unsigned)P.st_slot[(size_t)(k + u) * P.st_ns + i] : 0xffffu;
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (sl[u] != 0xffffu) {
+            const int sidx = (int)(sl[u] >> 2);
+            const float4 r0 = srec[2 * sidx], r1 = srec[2 * sidx + 1];
+            const int4 t = make_int4(__float_as_int(r0.x), __float_as_int(r0.y), __float_as_int(r0.z), 0);
+            c[u] = mv_entry_vals<float>(P, t, r0.w, r1, sh[sidx], (int)(sl[u] & 3u), beta, pc);
+          }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (sl[u] != 0xffffu) q = radd(q, c[u]);
+      }
+      acc = AC::add(acc, AC::prod(pnew(P, i, beta), P.rscale * q));
+    }
+    P.q[i] = q;
+  }
 }
 
 template <typename R>
@@ -1007,6 +1071,38 @@ __device__ __forceinline__ void red_release_add_u32(unsigned int *p, unsigned in
   asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// Bulk asynchronous copy global -> shared memory completing on an mbarrier
+// (the copy engine, no registers); 16-byte aligned addresses and sizes.
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0u;
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
 // Sum of NV accumulators over the CTA in a fixed tree order; the result is
 // valid in thread 0.  sh: one slot per warp.
 template <typename R, int NV>
@@ -1031,14 +1127,54 @@ __device__ __forceinline__ void cta_sum(typename Acc<R>::T (&v)[NV], typename Ac
   __syncthreads();  // sh is free again
 }
 
+// Warp 0 sums the gridDim.x partials of the barrier just passed in a fixed
+// order (lane l takes partials l, l + 32, ..., four loads in flight, then
+// a shuffle tree); thread 0 gets the totals in tot.
+template <typename R, int NV>
+__device__ __forceinline__ void grid_partials(const double *part, double *tot) {
+  typedef Acc<R> A;
+  if (threadIdx.x >= 32) return;
+  typename A::T w[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) w[k] = A::zero();
+  const int nb = (int)gridDim.x;
+  for (int j0 = (int)threadIdx.x; j0 < nb; j0 += 128) {
+    typename A::T buf[4][NV];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int j = j0 + 32 * u;
+#pragma unroll
+      for (int k = 0; k < NV; ++k) buf[u][k] = j < nb ? A::load(&part[(size_t)j * NV + k]) : A::zero();
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int k = 0; k < NV; ++k) w[k] = A::add(w[k], buf[u][k]);
+  }
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) w[k] = A::add(w[k], A::shfl(w[k], o));
+  }
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) tot[k] = A::to_d(w[k]);
+  }
+}
+
+struct NoHook {
+  __device__ void operator()() const {}
+};
+
 // Grid all-reduce (see above).  part: this barrier's buffer of
 // gridDim.x * NV slots; target: arrivals that complete this barrier.
 // Returns false (in every thread) if the wait gave up; otherwise thread 0
-// holds the totals in tot.
-template <typename R, int NV>
+// holds the totals in tot.  hook() runs in thread 0 as soon as the barrier
+// has completed, before the partials are summed.
+template <typename R, int NV, typename Hook = NoHook>
 __device__ __forceinline__ bool grid_sum(typename Acc<R>::T (&v)[NV], double *part, SolveScalars *S,
                                          unsigned int target, double *tot, typename Acc<R>::T (*sh)[NV],
-                                         int *ok_sh) {
+                                         int *ok_sh, const Hook &hook = Hook()) {
   typedef Acc<R> A;
   cta_sum<R, NV>(v, sh);  // its barriers order every thread's row writes before thread 0's release
   if (threadIdx.x == 0) {
@@ -1059,22 +1195,12 @@ __device__ __forceinline__ bool grid_sum(typename Acc<R>::T (&v)[NV], double *pa
         break;
       }
     }
+    if (ok) hook();
     *ok_sh = ok;
   }
   __syncthreads();
   if (!*ok_sh) return false;
-  typename A::T w[NV];
-#pragma unroll
-  for (int k = 0; k < NV; ++k) w[k] = A::zero();
-  for (int j = threadIdx.x; j < (int)gridDim.x; j += blockDim.x) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) w[k] = A::add(w[k], A::load(&part[(size_t)j * NV + k]));
-  }
-  cta_sum<R, NV>(w, sh);
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) tot[k] = A::to_d(w[k]);
-  }
+  grid_partials<R, NV>(part, tot);
   return true;
 }
 
@@ -1090,14 +1216,67 @@ template <typename R> struct PersShared {
 
 // Partials: P.part holds two buffers of 2 * gridDim.x slots, used by
 // alternate barriers (a CTA can only refill a buffer after every CTA has
-// passed the barrier that read it).
-template <typename R, int U>
+// passed the barrier that read it).  ST (FP32): the CTA first copies the
+// element records and history of its rows' elements into shared memory
+// (bulk asynchronous copies, one mbarrier, bounded wait) and every matvec
+// reads them there: the operator data cross the memory system once per
+// solve instead of once per iteration.
+template <typename R, int U, bool ST>
 __global__ void __launch_bounds__(kPersThreads, kPersMinBlocks) k_cg_persistent(Params<R> P) {
   typedef Acc<R> AC;
   SolveScalars *S = P.sc;
   __shared__ typename AC::T sh[kPersThreads / 32][2];
   __shared__ PersShared<R> z;
+  __shared__ __align__(8) unsigned long long stage_bar;
+  extern __shared__ __align__(128) unsigned char stage_smem[];
   if (S->done) return;  // set-up found b_eff = 0 or r_0 already small
+  int row0 = 0, row1 = 0;
+  const float4 *srec = nullptr;
+  const float *sH = nullptr;
+  if constexpr (ST) {
+    const StageCta sc = P.st_cta[blockIdx.x];
+    const int nel = sc.nel;
+    row0 = sc.row0;
+    row1 = sc.row1;
+    srec = reinterpret_cast<const float4 *>(stage_smem);
+    sH = reinterpret_cast<const float *>(stage_smem + (size_t)nel * sizeof(ERec<float>));
+    if (threadIdx.x == 0) {
+      mbar_init(&stage_bar, 1);
+      const int r0 = sc.r0, r1 = sc.r1;
+      mbar_arrive_expect_tx(&stage_bar, (unsigned)nel * (unsigned)(sizeof(ERec<float>) + sizeof(float)));
+      unsigned off = 0;
+      for (int r = r0; r < r1; ++r) {
+        const int2 g = P.st_rng[r];  // first element (a multiple of 4), count (a multiple of 4)
+        bulk_g2s(stage_smem + (size_t)off * sizeof(ERec<float>), P.rec + g.x, (unsigned)g.y * sizeof(ERec<float>),
+                 &stage_bar);
+        bulk_g2s((void *)(sH + off), P.Hr + g.x, (unsigned)g.y * sizeof(float), &stage_bar);
+        off += (unsigned)g.y;
+      }
+    }
+    __syncthreads();  // the barrier is initialised before anyone polls it
+    bool ok = true;
+    const unsigned long long t0 = global_ns();
+    unsigned spins = 0;
+    while (!mbar_try_wait(&stage_bar, 0u)) {
+      if ((++spins & 15u) == 0u && global_ns() - t0 > kSpinTimeoutNs) {
+        ok = false;
+        break;
+      }
+    }
+    if (!ok) *(volatile int32_t *)&S->abort = 1;
+    if (threadIdx.x == 0) z.ok = 1;
+    __syncthreads();
+    if (!ok) z.ok = 0;
+    __syncthreads();
+    if (!z.ok) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) {
+        S->status = kStTimeout;
+        S->done = 1;
+        S->inner_done = 1;
+      }
+      return;
+    }
+  }
   if (threadIdx.x == 0) {
     z.rho = S->rho;
     z.beta = S->beta;
@@ -1117,7 +1296,10 @@ __global__ void __launch_bounds__(kPersThreads, kPersMinBlocks) k_cg_persistent(
   for (;;) {
     // q = A p_new, p_new . q
     typename AC::T v1[1] = {AC::zero()};
-    matvec_rows<R, U>(P, z.coef[1], tid, stride, v1[0]);
+    if constexpr (ST)
+      matvec_rows_staged<U>(P, z.coef[1], row0, row1, srec, sH, v1[0]);
+    else
+      matvec_rows<R, U>(P, z.coef[1], tid, stride, v1[0]);
     ++nbar;
     if (!grid_sum<R, 1>(v1, P.part + (nbar & 1u) * 2u * nb, S, nbar * nb + P.bar_extra, z.tot,
                         (typename AC::T(*)[1])sh, &z.ok))
@@ -1183,6 +1365,355 @@ __global__ void __launch_bounds__(kPersThreads, kPersMinBlocks) k_cg_persistent(
     S->beta = z.beta;
     S->beta_f = (float)z.beta;
     S->rho = z.rho;
+    S->status = z.status;
+    S->done = z.done;
+    S->inner_done = 1;
+  }
+}
+
+// ------------------------------------ single-reduction persistent CG
+//
+// Jacobi PCG in the recurrences of Chronopoulos and Gear (1989): with
+// u = M^-1 r, w = A u and s = A p carried as vectors, both inner products
+// of an iteration, gamma = (r, u) and delta = (w, u), come from the same
+// pass, so each iteration is one pass over the rows and one grid
+// all-reduce instead of two of each:
+//   p = u + beta p,  s = w + beta s,  x += alpha p,  r -= alpha s,
+//   u = M^-1 r,  w = A u,  gamma' = (r, u),  delta' = (w, u),
+//   beta' = gamma' / gamma,  alpha' = gamma' / (delta' - beta' gamma' / alpha).
+// A row's matvec needs its neighbours' new u before they are stored: every
+// row rebuilds it from the neighbour's (r, w, s, 1/diag) of the previous
+// pass, which is why those four live in one 16-byte record, double
+// buffered.  In exact arithmetic the iterates are those of the Jacobi PCG
+// of the kernel-per-phase loop; the stop test is the same (||r|| <= tol
+// ||b_eff||, r carried by the recurrence).  Set-up: copy (r0, 0, 0, 1/diag)
+// from the right-hand side kernel's output, then one pass with
+// alpha = beta = 0 gives w0 = A u0 and delta0.  FP32 only.
+
+__device__ __forceinline__ float cg_unew(const float4 v, float al, float be) {
+  return v.w * fmaf(-al, fmaf(be, v.z, v.y), v.x);
+}
+
+// Rows i0, i0 + stride, ... < N of one single-reduction pass, operator and
+// neighbour vectors read from global memory (U entries in flight).
+template <int U>
+__device__ __forceinline__ void fused_rows(const Params<float> &P, float al, float be, const float4 *__restrict__ vin,
+                                           float4 *__restrict__ vout, int i0, int stride, DF (&acc)[3]) {
+  typedef Acc<float> AC;
+  for (int j = i0; j < P.N; j += stride) {
+    const float4 v = vin[j];
+    if (is_fixed(P, j)) {  // eliminated row: everything stays zero
+      vout[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+      continue;
+    }
+    const float p = fmaf(be, P.cgp[j], v.w * v.x);
+    const float sn = fmaf(be, v.z, v.y);
+    const float rn = fmaf(-al, sn, v.x);
+    const float un = v.w * rn;
+    P.x[j] = fmaf(al, p, P.x[j]);
+    P.cgp[j] = p;
+    float wq = 0.f;
+    for (int k = 0; k < P.D; k += U) {
+      float c[U];
+      int en[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) en[u] = k + u < P.D ? __ldg(&P.ell[(size_t)(k + u) * P.N + j]) : -1;
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (en[u] < 0) continue;
+        const int e = en[u] >> 2, a = en[u] & 3;
+        int4 t;
+        float A;
+        float4 G;
+        load_elem(P, e, t, A, G);
+        const float h = P.Hr[e];
+        const float kA = P.kappa * A;
+        const float mA = (P.cbase + 2.f * h) * A * (1.f / 12.f);
+        const float u0 = a == 0 ? un : cg_unew(vin[t.x], al, be);
+        const float u1 = a == 1 ? un : cg_unew(vin[t.y], al, be);
+        const float u2 = a == 2 ? un : cg_unew(vin[t.z], al, be);
+        c[u] = elem_row<float>(G, a, kA, mA, u0, u1, u2);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (en[u] >= 0) wq = radd(wq, c[u]);
+    }
+    vout[j] = make_float4(rn, wq, sn, v.w);
+    const float sr = P.rscale * rn;
+    acc[0] = AC::add(acc[0], AC::prod(sr, un));             // gamma
+    acc[1] = AC::add(acc[1], AC::prod(P.rscale * wq, un));  // delta
+    acc[2] = AC::add(acc[2], AC::prod(sr, sr));             // |r|^2
+  }
+}
+
+// The CTA's rows of one single-reduction pass with everything in shared
+// memory: localized element records (n0 | n1 << 16, n2 as positions in vs,
+// kappa A, (cbase + 2 H) A / 12, gradients), the rows' entries
+// (slot[k * mc + row - row0]) and the neighbourhood's (r, w, s, 1/diag) in
+// vs, own rows from position own.  Same arithmetic as fused_rows.
+template <int U>
+__device__ __forceinline__ void local_rows(const Params<float> &P, float al, float be, const float4 *vs, int own,
+                                           int row0, int row1, const uint16_t *slot, int mc, const float4 *srec,
+                                           float4 *__restrict__ vout, DF (&acc)[3]) {
+  typedef Acc<float> AC;
+  for (int jl = threadIdx.x; jl < row1 - row0; jl += blockDim.x) {
+    const int j = row0 + jl;
+    const float4 v = vs[own + jl];
+    if (is_fixed(P, j)) {
+      vout[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+      continue;
+    }
+    const float p = fmaf(be, P.cgp[j], v.w * v.x);
+    const float sn = fmaf(be, v.z, v.y);
+    const float rn = fmaf(-al, sn, v.x);
+    const float un = v.w * rn;
+    P.x[j] = fmaf(al, p, P.x[j]);
+    P.cgp[j] = p;
+    float wq = 0.f;
+    for (int k = 0; k < P.D; k += U) {
+      float c[U];
+      unsigned sl[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) sl[u] = k + u < P.D ? (unsigned)slot[(k + u) * mc + jl] : 0xffffu;
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (sl[u] == 0xffffu) continue;
+        const int sidx = (int)(sl[u] >> 2), a = (int)(sl[u] & 3u);
+        const float4 r0 = srec[2 * sidx], G = srec[2 * sidx + 1];
+        const unsigned n01 = __float_as_uint(r0.x);
+        const float u0 = a == 0 ? un : cg_unew(vs[n01 & 0xffffu], al, be);
+        const float u1 = a == 1 ? un : cg_unew(vs[n01 >> 16], al, be);
+        const float u2 = a == 2 ? un : cg_unew(vs[__float_as_int(r0.y)], al, be);
+        c[u] = elem_row<float>(G, a, r0.z, r0.w, u0, u1, u2);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (sl[u] != 0xffffu) wq = radd(wq, c[u]);
+    }
+    vout[j] = make_float4(rn, wq, sn, v.w);
+    const float sr = P.rscale * rn;
+    acc[0] = AC::add(acc[0], AC::prod(sr, un));
+    acc[1] = AC::add(acc[1], AC::prod(P.rscale * wq, un));
+    acc[2] = AC::add(acc[2], AC::prod(sr, sr));
+  }
+}
+
+// CTA shape: global operator, two CTAs of 512 per SM; shared-memory operator,
+// one CTA of 1024 per SM (the staged share of an SM is one CTA's); 32 warps
+// per SM and at most 64 registers either way.
+template <bool ST> struct FusedCfg {
+  static constexpr int threads = ST ? 1024 : 512;
+  static constexpr int minb = ST ? 1 : 2;
+};
+
+struct FusedShared {
+  double gamma, alpha, bn, rr;
+  double tot[3];
+  int iters, status, done, flag, ok;
+  float al, be;
+};
+
+// Shared-memory layout of the local (ST) kernel for one CTA: element
+// records (32 B), row entries (D rows of mc = row count rounded up to 8),
+// then a region that first receives the elements' history (4 B each) and,
+// once the records have absorbed it, the neighbourhood's vectors (16 B
+// each); byte offsets.
+struct LocalLayout {
+  unsigned slot, vec, total;
+  int mc;
+};
+
+__host__ __device__ __forceinline__ LocalLayout local_layout(int nel, int rows, int D, int nn) {
+  LocalLayout L;
+  L.mc = (rows + 7) / 8 * 8;
+  L.slot = (unsigned)nel * (unsigned)sizeof(ERec<float>);
+  L.vec = (L.slot + (unsigned)D * (unsigned)L.mc * 2u + 15u) / 16u * 16u;
+  const unsigned nv = (unsigned)nn * 16u, nh = (unsigned)nel * 4u;
+  L.total = L.vec + (nv > nh ? nv : nh);
+  return L;
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned parity) {
+  const unsigned long long t0 = global_ns();
+  unsigned spins = 0;
+  while (!mbar_try_wait(bar, parity))
+    if ((++spins & 15u) == 0u && global_ns() - t0 > kSpinTimeoutNs) return false;
+  return true;
+}
+
+// ST = false: rows read the operator and the neighbours' vectors from global
+// memory.  ST = true (local): once per solve the CTA copies its localized
+// element records, their history and its rows' entries into shared memory,
+// and before every pass the (r, w, s, 1/diag) of every node its elements
+// touch (bulk copies on two mbarriers, bounded waits); the pass itself then
+// reads shared memory only and writes its rows' results to global memory.
+template <int U, bool ST>
+__global__ void __launch_bounds__(FusedCfg<ST>::threads, FusedCfg<ST>::minb) k_cg_fused(Params<float> P) {
+  typedef Acc<float> AC;
+  SolveScalars *S = P.sc;
+  __shared__ DF sh[32][3];
+  __shared__ FusedShared z;
+  __shared__ __align__(8) unsigned long long bar_static, bar_vec;
+  extern __shared__ __align__(128) unsigned char stage_smem[];
+  if (S->done) return;  // set-up found b_eff = 0 or r_0 already small
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+  StageCta sc;
+  LocalLayout L;
+  if constexpr (ST) {
+    sc = P.st_cta[blockIdx.x];
+    L = local_layout(sc.nel, sc.row1 - sc.row0, P.D, sc.nn);
+    if (threadIdx.x == 0) {
+      mbar_init(&bar_static, 1);
+      mbar_init(&bar_vec, 1);
+      mbar_arrive_expect_tx(&bar_static, L.slot + (unsigned)sc.nel * 4u + (unsigned)P.D * (unsigned)L.mc * 2u);
+      bulk_g2s(stage_smem, P.st_lrec + sc.lrec, L.slot, &bar_static);
+      unsigned off = 0;
+      for (int r = sc.r0; r < sc.r1; ++r) {
+        const int2 g = P.st_rng[r];  // first element and count, multiples of 4
+        bulk_g2s(stage_smem + L.vec + off * 4u, P.Hr + g.x, (unsigned)g.y * 4u, &bar_static);
+        off += (unsigned)g.y;
+      }
+      for (int k = 0; k < P.D; ++k)
+        bulk_g2s(stage_smem + L.slot + (unsigned)k * (unsigned)L.mc * 2u,
+                 P.st_slot + (size_t)k * P.st_ns + sc.row0, (unsigned)L.mc * 2u, &bar_static);
+    }
+  }
+  // set-up: (r0, 0, 0, 1/diag) and p = 0
+  for (int j = tid; j < P.N; j += stride) {
+    P.cgv0[j] = make_float4(P.r[j], 0.f, 0.f, P.dinv[j]);
+    P.cgp[j] = 0.f;
+  }
+  if (threadIdx.x == 0) {
+    z.bn = S->bn;
+    z.gamma = S->rho;
+    z.rr = S->rr;
+    z.iters = S->iters;
+    z.status = kStOk;
+    z.done = 0;
+    z.al = 0.f;
+    z.be = 0.f;
+    z.alpha = 0.0;
+  }
+  if constexpr (ST) {
+    __syncthreads();  // the mbarriers are initialised before anyone polls them
+    if (!mbar_wait_bounded(&bar_static, 0u)) *(volatile int32_t *)&S->abort = 1;  // all leave at the next barrier
+    // records absorb the history: (n0 | n1 << 16, n2, kappa A, (cbase + 2 H) A / 12, grad)
+    float4 *srec = reinterpret_cast<float4 *>(stage_smem);
+    const float *hs = reinterpret_cast<const float *>(stage_smem + L.vec);
+    for (int e = threadIdx.x; e < sc.nel; e += blockDim.x) {
+      const float4 r0 = srec[2 * e];
+      const float A = r0.w, h = hs[e];
+      const float kA = P.kappa * A;
+      const float mA = (P.cbase + 2.f * h) * A * (1.f / 12.f);
+      const unsigned n01 = ((unsigned)__float_as_int(r0.x) & 0xffffu) | ((unsigned)__float_as_int(r0.y) << 16);
+      srec[2 * e] = make_float4(__uint_as_float(n01), r0.z, kA, mA);
+    }
+    // the history region becomes the vectors' (async copies) after the
+    // grid barrier below, which all threads reach after their reads
+  }
+  const unsigned int nb = gridDim.x;
+  unsigned int nbar = 1;
+  // ST: the copy of the neighbourhood's vectors for a pass is issued as
+  // soon as the barrier before it completes (the rows it reads are written),
+  // ahead of the partial sums.  The rows written in the last pass by other
+  // CTAs (generic proxy, ordered before this thread by the barrier) are read
+  // by the copy engine, which also overwrites shared memory this CTA last
+  // read generically: hence the proxy fences.
+  float4 *vs = ST ? reinterpret_cast<float4 *>(stage_smem + L.vec) : nullptr;
+  int copies = 0;  // vector copies issued (ST)
+  auto issue_vec = [&](const float4 *src) {
+    if constexpr (ST) {
+      asm volatile("fence.proxy.async.global;" ::: "memory");
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive_expect_tx(&bar_vec, (unsigned)sc.nn * 16u);
+      unsigned off = 0;
+      for (int r = sc.n0; r < sc.n1; ++r) {
+        const int2 g = P.st_nrng[r];  // first node, count
+        bulk_g2s(vs + off, src + g.x, (unsigned)g.y * 16u, &bar_vec);
+        off += (unsigned)g.y;
+      }
+    }
+  };
+  DF v3[3] = {AC::zero(), AC::zero(), AC::zero()};
+  bool fine = grid_sum<float, 3>(v3, P.part + 3u * nb, S, nb + P.bar_extra, z.tot, sh, &z.ok,
+                                 [&]() { issue_vec(P.cgv0); });
+  if (ST && fine) copies = 1;
+  int pass = 0;  // passes read cgv[pass & 1] and write the other buffer
+  while (fine) {
+    float4 *vin = (pass & 1) ? P.cgv1 : P.cgv0;
+    float4 *vout = (pass & 1) ? P.cgv0 : P.cgv1;
+    DF acc[3] = {AC::zero(), AC::zero(), AC::zero()};
+    if constexpr (ST) {
+      if (!mbar_wait_bounded(&bar_vec, (unsigned)pass & 1u)) *(volatile int32_t *)&S->abort = 1;
+      local_rows<U>(P, z.al, z.be, vs, sc.own, sc.row0, sc.row1,
+                    reinterpret_cast<const uint16_t *>(stage_smem + L.slot), L.mc,
+                    reinterpret_cast<const float4 *>(stage_smem), vout, acc);
+    } else {
+      fused_rows<U>(P, z.al, z.be, vin, vout, tid, stride, acc);
+    }
+    ++nbar;
+    ++pass;
+    if (ST) __syncthreads();  // every thread is done with vs before the next copy lands there
+    if (!grid_sum<float, 3>(acc, P.part + (nbar & 1u) * 3u * nb, S, nbar * nb + P.bar_extra, z.tot, sh, &z.ok,
+                            [&]() { issue_vec(vout); }))
+      break;
+    if (ST) copies = pass + 1;
+    if (threadIdx.x == 0) {
+      const double g1 = z.tot[0], d1 = z.tot[1], t0 = z.tot[2];
+      bool stop = false;
+      if (pass > 1) {  // pass 1 was the set-up pass (w0 = A u0): no iterate yet
+        z.iters += 1;
+        z.rr = t0;
+      }
+      if (!(t0 == t0) || isinf(t0) || !(d1 == d1) || isinf(d1)) {
+        z.status = kStNonfinite;
+        z.done = 1;
+        stop = true;
+      } else if (pass > 1 && sqrt(t0) <= P.tol * z.bn) {
+        z.done = 1;
+        stop = true;
+      } else if (g1 == 0.0) {  // u = 0: the iterate is exact
+        z.done = 1;
+        stop = true;
+      }
+      if (!stop && z.iters >= P.max_it) {
+        stop = true;
+        z.status = kStNotConverged;
+        z.done = 1;
+      }
+      if (!stop) {
+        const double beta = pass > 1 ? g1 / z.gamma : 0.0;
+        const double den = pass > 1 ? d1 - beta * g1 / z.alpha : d1;
+        if (den == 0.0 || !(den == den)) {  // breakdown: A is SPD, so only through rounding
+          z.status = kStNonfinite;
+          z.done = 1;
+          stop = true;
+        } else {
+          z.alpha = g1 / den;
+          z.gamma = g1;
+          z.al = (float)z.alpha;
+          z.be = (float)beta;
+        }
+      }
+      z.flag = stop ? 1 : 0;
+    }
+    __syncthreads();
+    if (z.flag) break;
+  }
+  if constexpr (ST) {
+    // a vector copy issued for a pass that did not run: let it land before
+    // the CTA (and its shared memory) goes away
+    if (copies > pass && !mbar_wait_bounded(&bar_vec, (unsigned)pass & 1u)) *(volatile int32_t *)&S->abort = 1;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (!z.ok) {
+      z.status = kStTimeout;
+      z.done = 1;
+    }
+    S->iters = z.iters;
+    S->rr = z.rr;
+    S->rho = z.gamma;
+    S->alpha = z.alpha;
     S->status = z.status;
     S->done = z.done;
     S->inner_done = 1;

@@ -294,9 +294,24 @@ struct pff_mesh {
   // grid (0 = cannot be co-resident); the autotuner's verdict against the
   // kernel-per-phase loop and both timings (8 iterations, ms)
   unsigned pgrid[5] = {0};
-  int pers_U = 0;  // gather width of the persistent kernel (0 = not tuned: the matvec's)
-  bool pers_tuned = false, pers_faster = false;
-  float pers_ms[2] = {0.f, 0.f};
+  unsigned fgrid[5] = {0};   // single-reduction CG grid per U (FP32)
+  bool st_fused = false;     // the staged tables also fit the single-reduction kernel
+  int fam_U[8] = {0};        // tuned gathers in flight per CG-loop family
+  int best_fam = 0;          // fastest family (kFamPhases when untuned)
+  // operator staged in shared memory by the persistent CG (FP32; see
+  // build_stage): CTAs, dynamic shared memory per CTA, device tables
+  unsigned st_grid = 0;
+  size_t st_smem = 0, st_smem_local = 0;
+  StageCta *st_cta = nullptr;
+  int2 *st_rng = nullptr, *st_nrng = nullptr;
+  ERec<float> *st_lrec = nullptr;
+  uint16_t *st_slot = nullptr;
+  int32_t st_ns = 0;
+  bool pers_tuned = false;
+  float fam_ms[8] = {0.f};   // 8 iterations of each family's best (0: not timed)
+  // single-reduction CG workspace (FP32): (r, w, s, 1/diag) x 2, p
+  void *cgv = nullptr;
+  float *cgp = nullptr;
 };
 
 namespace pff {
@@ -311,7 +326,8 @@ static void mesh_free(pff_mesh *m) {
   if (!m) return;
   free_graph(m->solve_g);
   free_graph(m->step_g);
-  void *ptrs[] = {m->ptr, m->ent, m->ell, m->rec, m->fext, m->minv, m->area_d, m->flags,
+  void *ptrs[] = {m->st_cta, m->st_rng, m->st_nrng, m->st_lrec, m->st_slot, m->cgv, m->cgp,
+                  m->ptr, m->ent, m->ell, m->rec, m->fext, m->minv, m->area_d, m->flags,
                   m->x, m->r, m->b, m->part, m->energy, m->wext, m->pz, m->q, m->dinv,
                   m->Hf, m->freef, m->ticket, m->sc, m->status_word, m->step_ctr, m->stab};
   for (void *q : ptrs)
@@ -366,13 +382,360 @@ static const void *kfun(int id, int v) {
 }
 
 template <typename R>
-static const void *pers_fun(int U) {
-  switch (U) {
-    case 1: return (const void *)k_cg_persistent<R, 1>;
-    case 3: return (const void *)k_cg_persistent<R, 3>;
-    case 4: return (const void *)k_cg_persistent<R, 4>;
-    default: return (const void *)k_cg_persistent<R, 2>;
+static const void *pers_fun(int U, bool st = false) {
+  if constexpr (sizeof(R) == 4) {
+    if (st) switch (U) {
+        case 1: return (const void *)k_cg_persistent<R, 1, true>;
+        case 3: return (const void *)k_cg_persistent<R, 3, true>;
+        case 4: return (const void *)k_cg_persistent<R, 4, true>;
+        default: return (const void *)k_cg_persistent<R, 2, true>;
+      }
   }
+  switch (U) {
+    case 1: return (const void *)k_cg_persistent<R, 1, false>;
+    case 3: return (const void *)k_cg_persistent<R, 3, false>;
+    case 4: return (const void *)k_cg_persistent<R, 4, false>;
+    default: return (const void *)k_cg_persistent<R, 2, false>;
+  }
+}
+
+// How an AT2 solve runs its CG loop (a family and, for the persistent
+// kernels, U gathers in flight):
+//   kFamPhases       matvec and update kernels in a device WHILE loop;
+//   kFamPersistent   one cooperative launch, two grid all-reduces per
+//                    iteration, operator read from global memory;
+//   kFamStaged       the same with each CTA's operator in shared memory;
+//   kFamFused        one cooperative launch of the single-reduction CG
+//                    (one pass and one all-reduce per iteration; FP32);
+//   kFamFusedStaged  the same with the operator in shared memory.
+// Forced by opt->cg_kernel, else the autotuner's fastest.  The barrier
+// count (at most 2 per iteration per CTA) must stay below 2^31; a plan that
+// cannot run falls back to the kernel-per-phase loop.
+enum { kFamPhases = 0, kFamPersistent, kFamStaged, kFamFused, kFamFusedStaged, kFamCount };
+
+struct CgPlan {
+  int fam = kFamPhases;
+  int U = 2;
+  unsigned grid = 0;
+  bool pers() const { return fam != kFamPhases; }
+  bool st() const { return fam == kFamStaged || fam == kFamFusedStaged; }
+  bool fused() const { return fam == kFamFused || fam == kFamFusedStaged; }
+};
+
+static inline int matvec_u(const pff_mesh *m) {
+  const int v = m->var[KP_MATVEC];
+  return v >= 1 && v <= 4 ? v : 2;
+}
+
+// Grid of a family with U (0 = not available on this mesh / precision).
+static inline unsigned fam_grid(const pff_mesh *m, int fam, int U, bool fp32) {
+  switch (fam) {
+    case kFamPersistent: return m->pgrid[U];
+    case kFamStaged: return fp32 ? m->st_grid : 0u;
+    case kFamFused: return fp32 ? m->fgrid[U] : 0u;
+    case kFamFusedStaged: return fp32 && m->st_fused ? m->st_grid : 0u;
+    default: return 0u;
+  }
+}
+
+static CgPlan cg_plan(const pff_mesh *m, const pff_options &o, int model, bool fp32) {
+  CgPlan p;
+  if (model != kAT2) return p;
+  switch (o.cg_kernel) {
+    case PFF_CG_PHASES: return p;
+    case PFF_CG_PERSISTENT:
+    case PFF_CG_TEST_TIMEOUT: p.fam = kFamPersistent; break;
+    case PFF_CG_STAGED: p.fam = kFamStaged; break;
+    case PFF_CG_FUSED: p.fam = kFamFused; break;
+    case PFF_CG_FUSED_STAGED: p.fam = kFamFusedStaged; break;
+    default:
+      if (!m->pers_tuned) return p;
+      p.fam = m->best_fam;
+  }
+  if (p.fam == kFamPhases) return p;
+  p.U = m->fam_U[p.fam] ? m->fam_U[p.fam] : matvec_u(m);
+  p.grid = fam_grid(m, p.fam, p.U, fp32);
+  if (p.grid == 0 && (p.fam == kFamStaged || p.fam == kFamFusedStaged)) {  // not stageable: unstaged
+    p.fam = p.fam == kFamStaged ? kFamPersistent : kFamFused;
+    p.U = m->fam_U[p.fam] ? m->fam_U[p.fam] : matvec_u(m);
+    p.grid = fam_grid(m, p.fam, p.U, fp32);
+  }
+  if (p.grid == 0 || 2.0 * ((double)o.cg_max_it + 3.0) * p.grid >= 2147483648.0) p = CgPlan();
+  return p;
+}
+
+template <typename R>
+static const void *plan_fun(const CgPlan &c) {
+  if constexpr (sizeof(R) == 4) {
+    if (c.fused()) {
+      const bool st = c.st();
+      switch (c.U) {
+        case 1: return st ? (const void *)k_cg_fused<1, true> : (const void *)k_cg_fused<1, false>;
+        case 3: return st ? (const void *)k_cg_fused<3, true> : (const void *)k_cg_fused<3, false>;
+        case 4: return st ? (const void *)k_cg_fused<4, true> : (const void *)k_cg_fused<4, false>;
+        default: return st ? (const void *)k_cg_fused<2, true> : (const void *)k_cg_fused<2, false>;
+      }
+    }
+  }
+  return pers_fun<R>(c.U, c.st());
+}
+
+static inline unsigned plan_threads(const CgPlan &c) {
+  return c.fam == kFamFusedStaged ? FusedCfg<true>::threads : (c.fam == kFamFused ? FusedCfg<false>::threads : kPersThreads);
+}
+
+static inline size_t plan_smem(const pff_mesh *m, const CgPlan &c) {
+  return c.fam == kFamStaged ? m->st_smem : (c.fam == kFamFusedStaged ? m->st_smem_local : 0);
+}
+
+template <typename R>
+static pff_status launch_pers(const pff_mesh *m, const CgPlan &c, Params<R> &P, cudaStream_t s) {
+  void *args[] = {(void *)&P};
+  CUDA_TRY(cudaLaunchCooperativeKernel(plan_fun<R>(c), dim3(c.grid), dim3(plan_threads(c)), args,
+                                       plan_smem(m, c), s));
+  return PFF_OK;
+}
+
+template <typename R>
+static pff_status add_pers(const pff_mesh *m, const CgPlan &c, cudaGraph_t g,
+                           const std::vector<cudaGraphNode_t> &deps, Params<R> &P, cudaGraphNode_t *out) {
+  cudaKernelNodeParams kp;
+  std::memset(&kp, 0, sizeof(kp));
+  void *args[] = {(void *)&P};
+  kp.func = const_cast<void *>(plan_fun<R>(c));
+  kp.gridDim = dim3(c.grid);
+  kp.blockDim = dim3(plan_threads(c));
+  kp.sharedMemBytes = (unsigned)plan_smem(m, c);
+  kp.kernelParams = args;
+  CUDA_TRY(cudaGraphAddKernelNode(out, g, deps.data(), deps.size(), &kp));
+  cudaLaunchAttributeValue av;
+  std::memset(&av, 0, sizeof(av));
+  av.cooperative = 1;
+  CUDA_TRY(cudaGraphKernelNodeSetAttribute(*out, cudaLaunchAttributeCooperative, &av));
+  return PFF_OK;
+}
+
+// Shared-memory staging of the damage operator for the persistent CG
+// (FP32).  CTA c owns a contiguous run of M rows (M a multiple of 64).  Its
+// elements are those incident to its rows; their sorted ids are cut into
+// ranges (gaps up to 8 elements bridged), each widened to whole groups of 4
+// elements so that every copy of the history starts and ends on a 16-byte
+// boundary (history arrays are padded to match).  Its nodes are those of
+// its elements, cut into ranges the same way (gaps up to 4 nodes bridged);
+// its own rows lie in one of them.  st_lrec holds, per CTA, the records of
+// its staged elements with node ids replaced by positions in its staged
+// node set.  Entry k of row i is found at slot[k * ns + i] = (position in
+// the CTA's staged elements) << 2 | a.  Tried with two CTAs per SM (half
+// the shared memory each), then one; left unavailable (st_grid = 0) when a
+// CTA's share does not fit.
+// Records why an optional fast path is off and carries on (PFF_OK).
+static pff_status fail_soft(const std::string &why) {
+  fprintf(stderr, "pff: %s\n", why.c_str());
+  return PFF_OK;
+}
+
+static pff_status build_stage(pff_mesh *m, const std::vector<int32_t> &ptr, int nsm) {
+  const int64_t N = m->N, Ne = m->Ne;
+  if (N < 64) return PFF_OK;
+  std::vector<int32_t> ent(ptr[N]);
+  CUDA_TRY(cudaMemcpy(ent.data(), m->ent, ent.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+  std::vector<ERec<float>> rec;  // fetched once a partition fits
+  const int D = m->D;
+  const int64_t ns = (N + 7) / 8 * 8;
+  int dev = 0, smem_optin = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  CUDA_TRY(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  auto cut = [](const std::vector<int32_t> &ids, int gap, int align, std::vector<int2> &out) {
+    out.clear();  // (lo, hi) inclusive
+    for (size_t k = 0; k < ids.size();) {
+      int lo = ids[k], hi = ids[k];
+      size_t j = k + 1;
+      while (j < ids.size() && ids[j] - hi <= gap) hi = ids[j++];
+      lo = lo / align * align;
+      hi = (hi / align + 1) * align - 1;
+      if (!out.empty() && lo <= out.back().y + 1)
+        out.back().y = std::max(out.back().y, hi);
+      else
+        out.push_back(make_int2(lo, hi));
+      k = j;
+    }
+  };
+  auto pos = [](const std::vector<int2> &rs, const std::vector<int64_t> &off, int v) -> int64_t {
+    const size_t r = (size_t)(std::upper_bound(rs.begin(), rs.end(), v,
+                                               [](int x, const int2 &g) { return x < g.x; }) - rs.begin()) - 1;
+    return off[r] + (v - rs[r].x);
+  };
+  // first choice: the partition whose local layout fits (two CTAs per SM,
+  // else one); otherwise the first whose element staging fits
+  for (int attempt = 0; attempt < 4; ++attempt) {
+    const bool need_local = attempt < 2;
+    const int minb = 2 - (attempt & 1);
+    // dynamic shared memory per CTA: the SM's share minus static use and
+    // the per-CTA reservation
+    const size_t budget = std::min<size_t>((size_t)smem_optin - 2048, (size_t)(228 * 1024) / minb - 4096);
+    const int64_t G0 = (int64_t)nsm * minb;
+    const int64_t M = std::max<int64_t>(64, ((N + G0 - 1) / G0 + 63) / 64 * 64);
+    const int64_t G = (N + M - 1) / M;
+    std::vector<StageCta> cta(G);
+    std::vector<int2> rng, nrng;
+    std::vector<std::vector<int32_t>> eids(G), nids(G);
+    std::vector<uint16_t> slot((size_t)D * ns, 0xffff);
+    bool fits = true;
+    size_t smax_el = 0, smax_loc = 0;
+    int64_t nlrec = 0;
+    std::vector<int2> cr, nr;
+    for (int64_t c = 0; c < G && fits; ++c) {
+      const int64_t i0 = c * M, i1 = std::min<int64_t>(N, i0 + M);
+      StageCta &t = cta[c];
+      t.row0 = (int32_t)i0;
+      t.row1 = (int32_t)i1;
+      std::vector<int32_t> &ids = eids[c];
+      ids.assign(ent.begin() + ptr[i0], ent.begin() + ptr[i1]);
+      for (auto &v : ids) v >>= 2;
+      std::sort(ids.begin(), ids.end());
+      ids.erase(std::unique(ids.begin(), ids.end()), ids.end());
+      cut(ids, 8, 4, cr);
+      std::vector<int64_t> off(cr.size());
+      int64_t cnt = 0;
+      t.r0 = (int32_t)rng.size();
+      for (size_t r = 0; r < cr.size(); ++r) {
+        off[r] = cnt;
+        cnt += cr[r].y - cr[r].x + 1;
+        rng.push_back(make_int2(cr[r].x, cr[r].y - cr[r].x + 1));
+      }
+      t.r1 = (int32_t)rng.size();
+      t.nel = (int32_t)cnt;
+      t.lrec = (int32_t)nlrec;
+      nlrec += cnt;
+      if (cnt > 16383) {
+        fits = false;
+        break;
+      }
+      for (int64_t i = i0; i < i1; ++i)
+        for (int32_t k = ptr[i]; k < ptr[i + 1]; ++k)
+          slot[(size_t)(k - ptr[i]) * ns + i] = (uint16_t)((pos(cr, off, ent[k] >> 2) << 2) | (ent[k] & 3));
+      smax_el = std::max(smax_el, (size_t)cnt * (sizeof(ERec<float>) + 4));
+      if (smax_el > budget) fits = false;
+    }
+    if (!fits) continue;
+    // nodes of each CTA's elements (needs the records' node ids)
+    if (rec.empty()) {
+      rec.resize(Ne);
+      CUDA_TRY(cudaMemcpy(rec.data(), m->rec, Ne * sizeof(ERec<float>), cudaMemcpyDeviceToHost));
+    }
+    std::vector<ERec<float>> lrec((size_t)nlrec);
+    std::memset(lrec.data(), 0, lrec.size() * sizeof(ERec<float>));
+    bool local_ok = true;
+    for (int64_t c = 0; c < G; ++c) {
+      StageCta &t = cta[c];
+      std::vector<int32_t> nodes;
+      nodes.reserve(eids[c].size() * 3 + (t.row1 - t.row0));
+      for (int32_t i = t.row0; i < t.row1; ++i) nodes.push_back(i);  // own rows stay one run
+      for (int e : eids[c]) {
+        nodes.push_back(rec[e].n0);
+        nodes.push_back(rec[e].n1);
+        nodes.push_back(rec[e].n2);
+      }
+      std::sort(nodes.begin(), nodes.end());
+      nodes.erase(std::unique(nodes.begin(), nodes.end()), nodes.end());
+      cut(nodes, 4, 1, nr);
+      std::vector<int64_t> noff(nr.size());
+      int64_t nn = 0;
+      t.n0 = (int32_t)nrng.size();
+      for (size_t r = 0; r < nr.size(); ++r) {
+        noff[r] = nn;
+        nn += nr[r].y - nr[r].x + 1;
+        nrng.push_back(make_int2(nr[r].x, nr[r].y - nr[r].x + 1));
+      }
+      t.n1 = (int32_t)nrng.size();
+      t.nn = (int32_t)nn;
+      t.own = (int32_t)pos(nr, noff, t.row0);
+      // localized records of the incident elements (staged padding stays 0)
+      std::vector<int2> er(rng.begin() + t.r0, rng.begin() + t.r1);
+      std::vector<int64_t> eoff(er.size());
+      int64_t acc = 0;
+      for (size_t r = 0; r < er.size(); ++r) {
+        eoff[r] = acc;
+        acc += er[r].y;
+        er[r].y = er[r].x + er[r].y - 1;  // (lo, hi)
+      }
+      for (int e : eids[c]) {
+        ERec<float> q = rec[e];
+        q.n0 = (int)pos(nr, noff, q.n0);
+        q.n1 = (int)pos(nr, noff, q.n1);
+        q.n2 = (int)pos(nr, noff, q.n2);
+        lrec[(size_t)t.lrec + pos(er, eoff, e)] = q;
+      }
+      const LocalLayout L = local_layout(t.nel, t.row1 - t.row0, D, t.nn);
+      smax_loc = std::max(smax_loc, (size_t)L.total);
+      if (L.total > budget) local_ok = false;
+    }
+    // the kernels index shared memory with these tables: check every
+    // position against its CTA's staged sizes and every copy against its array
+    bool sane = true;
+    for (int64_t c = 0; c < G && sane; ++c) {
+      const StageCta &t = cta[c];
+      const int64_t rows = t.row1 - t.row0;
+      if (t.own < 0 || t.own + rows > t.nn) sane = false;
+      for (int32_t r = t.r0; r < t.r1 && sane; ++r)
+        if (rng[r].x < 0 || rng[r].x % 4 || rng[r].y % 4 || rng[r].x + rng[r].y > (Ne + 3) / 4 * 4) sane = false;
+      for (int32_t r = t.n0; r < t.n1 && sane; ++r)
+        if (nrng[r].x < 0 || nrng[r].y <= 0 || nrng[r].x + nrng[r].y > N) sane = false;
+      for (int32_t k = 0; k < t.nel && sane; ++k) {
+        const ERec<float> &q = lrec[(size_t)t.lrec + k];
+        if (q.n0 < 0 || q.n0 >= t.nn || q.n1 < 0 || q.n1 >= t.nn || q.n2 < 0 || q.n2 >= t.nn) sane = false;
+      if (t.nn > 65535) sane = false;  // node positions travel as 16-bit fields
+      }
+      for (int64_t i = t.row0; i < t.row1 && sane; ++i)
+        for (int k = 0; k < D; ++k) {
+          const uint16_t v = slot[(size_t)k * ns + i];
+          if (v != 0xffff && ((v >> 2) >= t.nel || (v & 3) > 2)) sane = false;
+        }
+    }
+    if (!sane) return fail_soft("shared-memory staging tables failed their check; staging disabled");
+    // every CTA resident at once with this much shared memory?
+    auto coresident = [&](const void *f, int threads, size_t smem, bool &ok) -> pff_status {
+      cudaFuncAttributes fa;
+      CUDA_TRY(cudaFuncGetAttributes(&fa, f));
+      const int dyn_max = smem_optin - (int)fa.sharedSizeBytes;
+      if ((int64_t)smem > dyn_max) {
+        ok = false;
+        return PFF_OK;
+      }
+      CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max));
+      int occ = 0;
+      CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f, threads, smem));
+      ok = ok && (int64_t)occ * nsm >= G;
+      return PFF_OK;
+    };
+    bool ok = true;
+    for (int U = 1; U <= 4 && ok; ++U) PFF_TRY(coresident(pers_fun<float>(U, true), kPersThreads, smax_el, ok));
+    if (!ok) continue;
+    for (int U = 1; U <= 4 && local_ok; ++U) {
+      CgPlan pc;
+      pc.fam = kFamFusedStaged;
+      pc.U = U;
+      PFF_TRY(coresident(plan_fun<float>(pc), FusedCfg<true>::threads, smax_loc, local_ok));
+    }
+    if (need_local && !local_ok) continue;
+    m->st_fused = local_ok;
+    PFF_TRY(dalloc(&m->st_cta, G));
+    PFF_TRY(dalloc(&m->st_rng, rng.size()));
+    PFF_TRY(dalloc(&m->st_nrng, std::max<size_t>(1, nrng.size())));
+    PFF_TRY(dalloc(&m->st_lrec, std::max<size_t>(1, lrec.size())));
+    PFF_TRY(dalloc(&m->st_slot, slot.size()));
+    CUDA_TRY(cudaMemcpy(m->st_cta, cta.data(), G * sizeof(StageCta), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(m->st_rng, rng.data(), rng.size() * sizeof(int2), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(m->st_nrng, nrng.data(), nrng.size() * sizeof(int2), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(m->st_lrec, lrec.data(), lrec.size() * sizeof(ERec<float>), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(m->st_slot, slot.data(), slot.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
+    m->st_grid = (unsigned)G;
+    m->st_smem = smax_el;
+    m->st_smem_local = smax_loc;
+    m->st_ns = (int32_t)ns;
+    return PFF_OK;
+  }
+  return PFF_OK;
 }
 
 // Launch geometry.  Node-block kernels stage one value set per incidence
@@ -439,55 +802,31 @@ static pff_status configure(pff_mesh *m) {
     const int64_t ctas = std::max<int64_t>(1, (m->N + kPersThreads * rows - 1) / (kPersThreads * rows));
     m->pgrid[U] = coop && occ > 0 ? (unsigned)std::min<int64_t>(ctas, wave) : 0u;
   }
+  if constexpr (sizeof(R) == 4) {
+    // single-reduction CG: its grid per U and its workspace
+    for (int U = 1; U <= 4; ++U) {
+      CgPlan c;
+      c.fam = kFamFused;
+      c.U = U;
+      int occ = 0;
+      constexpr int T = FusedCfg<false>::threads;
+      CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, plan_fun<float>(c), T, 0));
+      const int64_t wave = (int64_t)nsm * occ;
+      const int64_t rows = std::max<int64_t>(1, (m->N + T * wave - 1) / (T * wave));
+      const int64_t ctas = std::max<int64_t>(1, (m->N + T * rows - 1) / (T * rows));
+      m->fgrid[U] = coop && occ > 0 ? (unsigned)std::min<int64_t>(ctas, wave) : 0u;
+    }
+    if (!m->cgv) {
+      PFF_TRY(dalloc((float4 **)&m->cgv, 2 * (size_t)(m->N + 2)));
+      PFF_TRY(dalloc(&m->cgp, (size_t)(m->N + 2)));
+      CUDA_TRY(cudaMemset(m->cgv, 0, 2 * (size_t)(m->N + 2) * sizeof(float4)));
+      CUDA_TRY(cudaMemset(m->cgp, 0, (size_t)(m->N + 2) * sizeof(float)));
+    }
+    if (coop) PFF_TRY(build_stage(m, ptr, nsm));
+  }
   return PFF_OK;
 }
 
-// The persistent CG's gather width: its own tuned U, else the tuned matvec
-// schedule's (2 when the entry-parallel schedule won).
-static inline int pers_u(const pff_mesh *m) {
-  if (m->pers_U >= 1 && m->pers_U <= 4) return m->pers_U;
-  const int v = m->var[KP_MATVEC];
-  return v >= 1 && v <= 4 ? v : 2;
-}
-
-// Whether an AT2 solve runs as one persistent kernel: forced by
-// opt->cg_kernel (1 = kernel per phase, 2 = persistent), else the
-// autotuner's verdict.  The barrier count (2 per iteration per CTA) must
-// stay below 2^31.
-static bool use_persistent(const pff_mesh *m, const pff_options &o, int model) {
-  if (model != kAT2 || o.cg_kernel == PFF_CG_PHASES) return false;
-  const unsigned g = m->pgrid[pers_u(m)];
-  if (g == 0 || 2.0 * ((double)o.cg_max_it + 2.0) * g >= 2147483648.0) return false;
-  return o.cg_kernel == PFF_CG_PERSISTENT || o.cg_kernel == PFF_CG_TEST_TIMEOUT ||
-         (m->pers_tuned && m->pers_faster);
-}
-
-template <typename R>
-static pff_status launch_pers(const pff_mesh *m, Params<R> &P, cudaStream_t s) {
-  void *args[] = {(void *)&P};
-  const int U = pers_u(m);
-  CUDA_TRY(cudaLaunchCooperativeKernel(pers_fun<R>(U), dim3(m->pgrid[U]), dim3(kPersThreads), args, 0, s));
-  return PFF_OK;
-}
-
-template <typename R>
-static pff_status add_pers(const pff_mesh *m, cudaGraph_t g, const std::vector<cudaGraphNode_t> &deps,
-                           Params<R> &P, cudaGraphNode_t *out) {
-  cudaKernelNodeParams kp;
-  std::memset(&kp, 0, sizeof(kp));
-  void *args[] = {(void *)&P};
-  const int U = pers_u(m);
-  kp.func = const_cast<void *>(pers_fun<R>(U));
-  kp.gridDim = dim3(m->pgrid[U]);
-  kp.blockDim = dim3(kPersThreads);
-  kp.kernelParams = args;
-  CUDA_TRY(cudaGraphAddKernelNode(out, g, deps.data(), deps.size(), &kp));
-  cudaLaunchAttributeValue av;
-  std::memset(&av, 0, sizeof(av));
-  av.cooperative = 1;
-  CUDA_TRY(cudaGraphKernelNodeSetAttribute(*out, cudaLaunchAttributeCooperative, &av));
-  return PFF_OK;
-}
 
 template <typename R>
 static pff_status launch_v(const pff_mesh *m, int id, int v, Params<R> &P, cudaStream_t s) {
@@ -526,6 +865,15 @@ static Params<R> base_params(pff_mesh *m, const pff_options &o) {
   P.D = m->D;
   P.rec = (const ERec<R> *)m->rec;
   P.flags = m->flags;
+  P.st_cta = m->st_cta;
+  P.st_rng = m->st_rng;
+  P.st_nrng = m->st_nrng;
+  P.st_lrec = m->st_lrec;
+  P.st_slot = m->st_slot;
+  P.st_ns = m->st_ns;
+  P.cgv0 = (float4 *)m->cgv;
+  P.cgv1 = m->cgv ? (float4 *)m->cgv + (m->N + 2) : nullptr;
+  P.cgp = m->cgp;
   P.fext = (const typename V<R>::T2 *)m->fext;
   P.minv = (const R *)m->minv;
   const pff_material &mt = m->mat;
@@ -612,16 +960,16 @@ static pff_status add_while(cudaGraph_t g, const std::vector<cudaGraphNode_t> &d
 
 // Appends the damage solve (rhs -> CG loop -> finish) to graph g after dep.
 // The handles must already be in P (created on the top-level graph), except
-// for a persistent solve (pers), which needs none.
+// for a persistent solve, which needs none.
 template <typename R>
 static pff_status append_solve(const pff_mesh *m, cudaGraph_t g, cudaGraphNode_t dep, Params<R> &P,
-                               bool pers, cudaGraphNode_t *last) {
+                               const CgPlan &plan, cudaGraphNode_t *last) {
   std::vector<cudaGraphNode_t> d;
   if (dep) d.push_back(dep);
   cudaGraphNode_t n_rhs, n_loop, n_fin;
   PFF_TRY(add_kernel<R>(m, g, d, KP_RHS, P, &n_rhs));
-  if (pers) {
-    PFF_TRY(add_pers<R>(m, g, {n_rhs}, P, &n_loop));
+  if (plan.pers()) {
+    PFF_TRY(add_pers<R>(m, plan, g, {n_rhs}, P, &n_loop));
   } else if (P.model == kAT1) {
     cudaGraph_t outer, inner;
     PFF_TRY(add_while(g, {n_rhs}, P.cond_outer, &outer, &n_loop));
@@ -758,14 +1106,13 @@ static pff_status autotune(pff_mesh *m, const pff_options &o, Params<R> P, bool 
   }
   for (int id : ids)
     if (m->tuned[id]) m->var[id] = m->tuned_var[id];
-  // AT2 CG loop: the solve graphs of a run (right-hand side, then the device
-  // WHILE loop of matvec/update kernels, or one persistent launch with
-  // U = 1..4 gathers in flight), each stopped after 8 iterations (tolerance
-  // 0), timed on this mesh's data with whatever the solve leaves in L2, as
-  // in a run
+  // AT2 CG loop: the solve graphs of a run (right-hand side, then the CG
+  // loop of each family with U = 1..4 gathers in flight), each stopped after
+  // 8 iterations (tolerance 0), timed on this mesh's data with whatever the
+  // solve leaves in L2, as in a run
   if (res == PFF_OK && with_damage && P.model == kAT2 && !m->pers_tuned &&
-      (o.cg_kernel == PFF_CG_AUTO || o.cg_kernel == PFF_CG_PERSISTENT)) {
-    constexpr int K = 8, NK = 5;  // kind 0: kernel per phase; kind U: persistent with U
+      o.cg_kernel != PFF_CG_PHASES && o.cg_kernel != PFF_CG_TEST_TIMEOUT) {
+    constexpr int K = 8, NK = 1 + 4 * (kFamCount - 1);  // kind 0: phases; 1 + 4 (fam - 1) + (U - 1)
     Params<R> Q = P;
     Q.use_cond = 0;
     Q.tol = 0.0;
@@ -786,9 +1133,17 @@ static pff_status autotune(pff_mesh *m, const pff_options &o, Params<R> P, bool 
       else
         skip = hs.done != 0;
     }
-    const int keepU = m->pers_U;
+    auto plan_of = [&](int kind) {
+      CgPlan c;
+      if (kind == 0) return c;
+      c.fam = 1 + (kind - 1) / 4;
+      c.U = 1 + (kind - 1) % 4;
+      c.grid = fam_grid(m, c.fam, c.U, sizeof(R) == 4);
+      return c;
+    };
     for (int kind = 0; kind < NK && !skip && st == PFF_OK; ++kind) {
-      if (kind > 0 && m->pgrid[kind] == 0) continue;
+      const CgPlan c = plan_of(kind);
+      if (kind > 0 && c.grid == 0) continue;
       Params<R> G = Q;
       if (cudaGraphCreate(&g[kind], 0) != cudaSuccess) {
         st = fail(PFF_ERR_CUDA, "autotune: graph");
@@ -810,9 +1165,7 @@ static pff_status autotune(pff_mesh *m, const pff_options &o, Params<R> P, bool 
         if (st == PFF_OK) st = add_kernel<R>(m, body, {}, KP_MATVEC, G, &n_mv);
         if (st == PFF_OK) st = add_kernel<R>(m, body, {n_mv}, KP_UPDATE, G, &n_up);
       } else if (st == PFF_OK) {
-        m->pers_U = kind;
-        st = add_pers<R>(m, g[kind], {n_rhs}, G, &n_loop);
-        m->pers_U = keepU;
+        st = add_pers<R>(m, c, g[kind], {n_rhs}, G, &n_loop);
       }
       if (st == PFF_OK && cudaGraphInstantiate(&ge[kind], g[kind], 0) != cudaSuccess) {
         ge[kind] = nullptr;
@@ -836,18 +1189,27 @@ static pff_status autotune(pff_mesh *m, const pff_options &o, Params<R> P, bool 
           if (cudaMemcpy(&hs, m->sc, sizeof(hs), cudaMemcpyDeviceToHost) != cudaSuccess)
             st = fail(PFF_ERR_CUDA, "autotune: scalars");
           else if (hs.status == kStTimeout)
-            st = fail(PFF_ERR_TIMEOUT, "autotune: a grid-barrier wait of the persistent CG timed out");
+            st = fail(PFF_ERR_TIMEOUT, "autotune: a grid-barrier wait of a persistent CG timed out");
         }
       }
     }
     if (!skip && st == PFF_OK) {
-      int bu = 0;
-      for (int kind = 1; kind < NK; ++kind)
-        if (ge[kind] && (bu == 0 || best[kind] < best[bu])) bu = kind;
-      m->pers_ms[0] = best[0];
-      m->pers_ms[1] = bu ? best[bu] : 0.f;
-      if (bu) m->pers_U = bu;
-      m->pers_faster = bu != 0 && best[bu] < best[0];
+      for (int f = 0; f < kFamCount; ++f) m->fam_ms[f] = 0.f;
+      m->fam_ms[kFamPhases] = best[0];
+      m->best_fam = kFamPhases;
+      float tb = best[0];
+      for (int kind = 1; kind < NK; ++kind) {
+        if (!ge[kind]) continue;
+        const CgPlan c = plan_of(kind);
+        if (m->fam_ms[c.fam] == 0.f || best[kind] < m->fam_ms[c.fam]) {
+          m->fam_ms[c.fam] = best[kind];
+          m->fam_U[c.fam] = c.U;
+        }
+        if (best[kind] < tb) {
+          tb = best[kind];
+          m->best_fam = c.fam;
+        }
+      }
     }
     for (int kind = 0; kind < NK; ++kind) {
       if (ge[kind]) cudaGraphExecDestroy(ge[kind]);
@@ -866,12 +1228,12 @@ static pff_status autotune(pff_mesh *m, const pff_options &o, Params<R> P, bool 
 
 // Host-polled variant of the same solve (debugging / PFF_LOOP_HOST).
 template <typename R>
-static pff_status solve_host_loop(const pff_mesh *m, Params<R> P, bool pers, cudaStream_t s) {
+static pff_status solve_host_loop(const pff_mesh *m, Params<R> P, const CgPlan &plan, cudaStream_t s) {
   P.use_cond = 0;
   SolveScalars hs;
   PFF_TRY(launch<R>(m, KP_RHS, P, s));
-  if (pers) {
-    PFF_TRY(launch_pers<R>(m, P, s));
+  if (plan.pers()) {
+    PFF_TRY(launch_pers<R>(m, plan, P, s));
   } else if (P.model == kAT1) {
     for (;;) {
       PFF_TRY(launch<R>(m, KP_RESTART, P, s));
@@ -908,13 +1270,15 @@ static pff_status damage_solve_t(pff_mesh *m, const double *H, const void *dprev
   P.dprev = (const R *)dprev;
   P.dout = (R *)dout;
   PFF_TRY(autotune<R>(m, o, P, false, true, s));
-  const bool pers = use_persistent(m, o, P.model);
+  const CgPlan plan = cg_plan(m, o, P.model, sizeof(R) == 4);
+  const bool pers = plan.pers();
   if (o.loop_mode == PFF_LOOP_HOST) {
-    PFF_TRY(solve_host_loop<R>(m, P, pers, s));
+    PFF_TRY(solve_host_loop<R>(m, P, plan, s));
   } else {
     std::vector<uint64_t> key = {(uint64_t)H, (uint64_t)dprev, (uint64_t)dout, (uint64_t)m->var[KP_RHS],
-                                 (uint64_t)m->var[KP_MATVEC],
-                                 (uint64_t)o.cg_max_it, (uint64_t)o.max_restarts, (uint64_t)pers};
+                                 (uint64_t)m->var[KP_MATVEC], (uint64_t)o.cg_max_it, (uint64_t)o.max_restarts,
+                                 (uint64_t)plan.fam, (uint64_t)plan.U,
+                                 (uint64_t)o.cg_kernel};
     uint64_t tb;
     std::memcpy(&tb, &o.cg_tol, 8);
     key.push_back(tb);
@@ -929,7 +1293,7 @@ static pff_status damage_solve_t(pff_mesh *m, const double *H, const void *dprev
       }
       P.use_cond = pers ? 0 : 1;
       cudaGraphNode_t last;
-      pff_status st = append_solve<R>(m, g, nullptr, P, pers, &last);
+      pff_status st = append_solve<R>(m, g, nullptr, P, plan, &last);
       if (st != PFF_OK) {
         cudaGraphDestroy(g);
         return st;
@@ -1036,7 +1400,8 @@ static pff_status run_t(pff_mesh *m, const pff_state *st, int64_t step0, int64_t
   P.iters_log = iters_log;  // indexed by the step within this run
   P.track_work = o.energy_every > 0 ? 1 : 0;
   PFF_TRY(autotune<R>(m, o, P, true, true, s));
-  const bool pers = use_persistent(m, o, P.model);
+  const CgPlan plan = cg_plan(m, o, P.model, sizeof(R) == 4);
+  const bool pers = plan.pers();
   const int64_t zero = 0;
   CUDA_TRY(cudaMemcpyAsync(m->step_ctr, &zero, sizeof(int64_t), cudaMemcpyHostToDevice, s));
   CUDA_TRY(cudaStreamSynchronize(s));
@@ -1046,7 +1411,7 @@ static pff_status run_t(pff_mesh *m, const pff_state *st, int64_t step0, int64_t
     for (int64_t n = 0; n < nsteps; ++n) {
       PFF_TRY(launch<R>(m, KP_PREDICT, P, s));
       PFF_TRY(launch<R>(m, KP_FORCE, P, s));
-      PFF_TRY(solve_host_loop<R>(m, P, pers, s));
+      PFF_TRY(solve_host_loop<R>(m, P, plan, s));
       if (tape) k_tape_store<R><<<Gtape, kThreads, 0, s>>>(P, *tape);
       if (energy_log && o.energy_every > 0 && (n + 1) % o.energy_every == 0) {
         Params<R> E = P;
@@ -1061,7 +1426,8 @@ static pff_status run_t(pff_mesh *m, const pff_state *st, int64_t step0, int64_t
                                (uint64_t)st->H, (uint64_t)o.cg_max_it, (uint64_t)m->var[KP_FORCE],
                                (uint64_t)m->var[KP_RHS], (uint64_t)m->var[KP_MATVEC],
                                (uint64_t)o.max_restarts, (uint64_t)P.iters_log, (uint64_t)P.track_work,
-                               (uint64_t)m->stab, (uint64_t)(tape ? tape->u : nullptr), (uint64_t)pers};
+                               (uint64_t)m->stab, (uint64_t)(tape ? tape->u : nullptr), (uint64_t)plan.fam,
+                               (uint64_t)plan.U, (uint64_t)o.cg_kernel};
   uint64_t b1, b2;
   std::memcpy(&b1, &o.cg_tol, 8);
   std::memcpy(&b2, &dt, 8);
@@ -1080,7 +1446,7 @@ static pff_status run_t(pff_mesh *m, const pff_state *st, int64_t step0, int64_t
     cudaGraphNode_t n_pr, n_f, last;
     pff_status stt = add_kernel<R>(m, g, {}, KP_PREDICT, P, &n_pr);
     if (stt == PFF_OK) stt = add_kernel<R>(m, g, {n_pr}, KP_FORCE, P, &n_f);
-    if (stt == PFF_OK) stt = append_solve<R>(m, g, n_f, P, pers, &last);
+    if (stt == PFF_OK) stt = append_solve<R>(m, g, n_f, P, plan, &last);
     if (stt == PFF_OK && tape) {
       cudaKernelNodeParams kp;
       std::memset(&kp, 0, sizeof(kp));
@@ -1206,7 +1572,11 @@ static pff_status mesh_build_t(pff_mesh *m, const double *xy_d, const int32_t *t
                                const uint8_t *notch_d, unsigned long long *scratch) {
   const int64_t N = m->N, Ne = m->Ne;
   const int blk = 256;
-  PFF_TRY(dalloc((ERec<R> **)&m->rec, Ne));
+  // records and FP32 history padded to whole groups of 4 elements (bulk
+  // copies of the shared-memory staging read whole groups)
+  const int64_t Ne4 = (Ne + 3) / 4 * 4;
+  PFF_TRY(dalloc((ERec<R> **)&m->rec, Ne4));
+  CUDA_TRY(cudaMemset(m->rec, 0, Ne4 * sizeof(ERec<R>)));
   PFF_TRY(dalloc((typename V<R>::T2 **)&m->fext, N));
   PFF_TRY(dalloc((R **)&m->minv, N));
   PFF_TRY(dalloc((typename V<R>::T2 **)&m->pz, N + 2));
@@ -1215,7 +1585,10 @@ static pff_status mesh_build_t(pff_mesh *m, const double *xy_d, const int32_t *t
   CUDA_TRY(cudaMemset(m->pz, 0, (N + 2) * sizeof(typename V<R>::T2)));
   CUDA_TRY(cudaMemset(m->q, 0, (N + 2) * sizeof(R)));
   CUDA_TRY(cudaMemset(m->dinv, 0, (N + 2) * sizeof(R)));
-  if (sizeof(R) == 4) PFF_TRY(dalloc(&m->Hf, Ne));
+  if (sizeof(R) == 4) {
+    PFF_TRY(dalloc(&m->Hf, Ne4));
+    CUDA_TRY(cudaMemset(m->Hf, 0, Ne4 * sizeof(float)));
+  }
   k_geometry<R><<<grid_for(Ne, blk), blk>>>(xy_d, tri_d, Ne, (ERec<R> *)m->rec, m->area_d, scratch, scratch + 1);
   k_node_init<R><<<grid_for(N, blk), blk>>>(fd, notch_d, N, (typename V<R>::T2 *)m->fext, m->flags);
   CUDA_TRY(cudaGetLastError());
@@ -1511,13 +1884,14 @@ pff_status pff_mesh_schedule(const pff_mesh *m, int32_t *variant, float *tune_ms
   return PFF_OK;
 }
 
-pff_status pff_mesh_cg_choice(const pff_mesh *m, int32_t *cg_kernel, int32_t *gathers, float *ms_phases,
-                              float *ms_persistent) {
+pff_status pff_mesh_cg_choice(const pff_mesh *m, int32_t *cg_kernel, int32_t *gathers, float *ms) {
   if (!m) return fail(PFF_ERR_ARG, "null mesh");
-  if (cg_kernel) *cg_kernel = !m->pers_tuned ? PFF_CG_AUTO : (m->pers_faster ? PFF_CG_PERSISTENT : PFF_CG_PHASES);
-  if (gathers) *gathers = pers_u(m);
-  if (ms_phases) *ms_phases = m->pers_ms[0];
-  if (ms_persistent) *ms_persistent = m->pers_ms[1];
+  static const int32_t kinds[kFamCount] = {PFF_CG_PHASES, PFF_CG_PERSISTENT, PFF_CG_STAGED, PFF_CG_FUSED,
+                                           PFF_CG_FUSED_STAGED};
+  if (cg_kernel) *cg_kernel = !m->pers_tuned ? PFF_CG_AUTO : kinds[m->best_fam];
+  if (gathers) *gathers = m->best_fam == kFamPhases ? 0 : m->fam_U[m->best_fam];
+  if (ms)
+    for (int k = 0; k < kFamCount; ++k) ms[k] = m->fam_ms[k];
   return PFF_OK;
 }
 
@@ -1628,7 +2002,7 @@ static pff_status noalloc_solve_t(pff_mesh *m, const double *H, const void *dpre
   P.status_word = nullptr;
   P.energy_out = nullptr;
   P.wext = nullptr;
-  PFF_TRY(solve_host_loop<R>(m, P, false, s));
+  PFF_TRY(solve_host_loop<R>(m, P, CgPlan(), s));
   SolveScalars hs;
   CUDA_TRY(cudaMemcpyAsync(&hs, P.sc, sizeof(hs), cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaStreamSynchronize(s));
@@ -1757,7 +2131,7 @@ static pff_status ckpt_alloc(pff_ckpt *c) {
   PFF_TRY(A(&c->dbn, N * r));
   PFF_TRY(A(&c->g, N * r));
   PFF_TRY(A(&c->lam, N * r));
-  PFF_TRY(A(&c->Hcur, Ne * r));
+  PFF_TRY(A(&c->Hcur, (Ne + 3) / 4 * 4 * r));  // whole groups of 4: see build_stage
   PFF_TRY(A((void **)&c->gc, 8));
   PFF_TRY(A((void **)&c->kctr, 4 * sizeof(int)));
   return PFF_OK;
@@ -1813,8 +2187,9 @@ static pff_status add_generic(cudaGraph_t g, const std::vector<cudaGraphNode_t> 
 }
 
 template <typename R>
-static pff_status build_reverse_graph(pff_mesh *m, pff_ckpt *c, AdjParams<R> A, bool pers, GraphCache &gcache,
-                                      const std::vector<uint64_t> &key) {
+static pff_status build_reverse_graph(pff_mesh *m, pff_ckpt *c, AdjParams<R> A, const CgPlan &plan,
+                                      GraphCache &gcache, const std::vector<uint64_t> &key) {
+  const bool pers = plan.pers();
   const unsigned Gn = std::min<unsigned>(grid_for(m->N, kThreads), m->grid[KP_UPDATE][0]);
   const unsigned Ge = std::min<unsigned>(grid_for(m->Ne, kThreads), m->grid[KP_UPDATE][0]);
   free_graph(gcache);
@@ -1830,7 +2205,7 @@ static pff_status build_reverse_graph(pff_mesh *m, pff_ckpt *c, AdjParams<R> A, 
   if (st == PFF_OK) st = add_generic(g, {n_load}, (const void *)k_adj_prep<R>, Gn, kThreads, 0, aa, &n_prep);
   if (st == PFF_OK) st = add_generic(g, {n_prep}, (const void *)k_adj_rhs<R>, Gn, kThreads, 0, aa, &n_rhs);
   if (pers) {
-    if (st == PFF_OK) st = add_pers<R>(m, g, {n_rhs}, A.P, &n_loop);
+    if (st == PFF_OK) st = add_pers<R>(m, plan, g, {n_rhs}, A.P, &n_loop);
   } else {
     if (st == PFF_OK) st = add_while(g, {n_rhs}, A.P.cond_inner, &body, &n_loop);
     if (st == PFF_OK) st = add_kernel<R>(m, body, {}, KP_MATVEC, A.P, &n_mv);
@@ -1942,11 +2317,12 @@ static pff_status backward_t(pff_mesh *m, pff_ckpt *c, const void *dL_dd, const 
       std::memcpy(&tb, &o.cg_tol, 8);
       std::memcpy(&gb, &m->mat.Gc, 8);
       std::memcpy(&lb, &c->dt, 8);
-      const bool pers = use_persistent(m, o, kAT2);
+      const CgPlan plan = cg_plan(m, o, kAT2, sizeof(R) == 4);
       std::vector<uint64_t> key = {tb, gb, lb, (uint64_t)m->var[KP_MATVEC], (uint64_t)o.cg_max_it,
-                                   (uint64_t)m->mat.split, (uint64_t)pers};
+                                   (uint64_t)m->mat.split, (uint64_t)plan.fam, (uint64_t)plan.U,
+                                   (uint64_t)o.cg_kernel};
       if (!c->rev_g[q].exec || c->rev_g[q].key != key)
-        PFF_TRY(build_reverse_graph<R>(m, c, A, pers, c->rev_g[q], key));
+        PFF_TRY(build_reverse_graph<R>(m, c, A, plan, c->rev_g[q], key));
     }
     for (int64_t k = len - 1; k >= 0; --k) {
       CUDA_TRY(cudaGraphLaunch(c->rev_g[par].exec, s));
