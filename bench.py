@@ -52,6 +52,8 @@ def parse():
                     help="skip the forward+adjoint measurement on the 500x500 plate")
     ap.add_argument("--variant", type=int, default=0,
                     help="gather schedule (0 = autotuned; 1..5 fixed, see pff_options.variant)")
+    ap.add_argument("--cg-kernel", choices=["auto", "phases", "persistent", "staged", "fused", "fused_staged"],
+                    default="auto", help="AT2 CG loop (pff_options.cg_kernel; auto = autotuned)")
     ap.add_argument("--loop", choices=["graph", "host"], default="graph",
                     help="host: launch every kernel from the host (ncu cannot profile "
                          "kernels inside graphs with conditional nodes)")
@@ -124,12 +126,13 @@ def peaks():
     return 6400.0, "fallback"
 
 
-def ncu_traffic(kernel_prefix):
-    """DRAM bytes (read + write) per launch of the named kernel from the
-    committed ncu summary, or None when the kernel source changed since the
-    capture (the summary records the source hash)."""
+def ncu_traffic(kernel_prefix, summary="ncu_full_gather_cg_plate_1000x1000_fp32.md"):
+    """DRAM bytes (read + write) from the committed ncu summary: the column of
+    the first table whose header names the kernel (per launch, or per CG
+    iteration for the CG loop summary), or None when the kernel source
+    changed since the capture (the summary records the source hash)."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "ncu_full_gather_cg_plate_1000x1000_fp32.md")
+    path = os.path.join(ROOT, "profiles", summary)
     src = os.path.join(ROOT, "paper_2606_23458_b300", "csrc", "kernels.cuh")
     try:
         text = open(path).read()
@@ -138,23 +141,28 @@ def ncu_traffic(kernel_prefix):
         return None
     if f"`{h}`" not in text:
         return None
-    rows = [ln for ln in text.splitlines() if ln.startswith("|")]
-    head = [c.strip(" `") for c in rows[0].strip("|").split("|")]
-    col = next((i for i, c in enumerate(head) if kernel_prefix in c), None)
-    if col is None:
-        return None
-    val = {}
-    for ln in rows[2:]:
-        cells = [c.strip() for c in ln.strip("|").split("|")]
-        if cells[0].startswith("dram__bytes_read.sum") or cells[0].startswith("dram__bytes_write.sum"):
-            unit = cells[0].split("(")[-1].rstrip(")")
-            scale = {"Mbyte": 1e6, "Kbyte": 1e3, "Gbyte": 1e9, "byte": 1.0}.get(unit, None)
-            if scale is None:
-                return None
-            val[cells[0].split(" ")[0]] = float(cells[col]) * scale
-    if len(val) != 2:
-        return None
-    return sum(val.values())
+    lines = text.splitlines()
+    for n, ln in enumerate(lines):
+        if not ln.startswith("|"):
+            continue
+        head = [c.strip(" `") for c in ln.strip("|").split("|")]
+        col = next((i for i, c in enumerate(head) if kernel_prefix in c), None)
+        if col is None:
+            continue
+        val = {}
+        for row in lines[n + 2:]:
+            if not row.startswith("|"):
+                break
+            cells = [c.strip() for c in row.strip("|").split("|")]
+            name = cells[0].split(" ")[0]
+            if name in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+                unit = cells[0].split("(")[-1].rstrip(")")
+                scale = {"Mbyte": 1e6, "Kbyte": 1e3, "Gbyte": 1e9, "byte": 1.0}.get(unit)
+                if scale is None:
+                    return None
+                val[name] = float(cells[col]) * scale
+        return sum(val.values()) if len(val) == 2 else None
+    return None
 
 
 def dist_env():
@@ -184,6 +192,10 @@ def algorithmic_bytes(N, Ne, prec):
         "update": N * (32 + 3 * w + 2 * w + 1),
         # clamp: x (f64), d_prev read, d write
         "finish": N * (8 + 2 * w + 1),
+        # one CG iteration as the method states it: element pass (connectivity
+        # 12 B, geometry 20 B, H 8 B), p read and q write, fused vector update
+        # (x, r in FP64, p, z, diag) -- multiplied by the iterations of a launch
+        "cg_iteration": Ne * (12 + 20 + 8) + N * (8 + 48),
     }
 
 
@@ -361,7 +373,8 @@ def run_ours(args):
     N, Ne = mesh.N, mesh.Ne
     opts = pff.options(cg_tol=c["cg_tol"], t_ramp=c["t_ramp"],
                        loop_mode=pff.PFF_LOOP_HOST if args.loop == "host" else pff.PFF_LOOP_GRAPH,
-                       variant=args.variant)
+                       variant=args.variant,
+                       cg_kernel={v: k for k, v in pff.CG_KINDS.items()}[args.cg_kernel])
     st = mesh.new_state(device=dev)
     total = args.warmup + args.steps
     log = torch.zeros(total + args.e2e_steps, 2, dtype=torch.int32, device=dev)
@@ -388,7 +401,12 @@ def run_ours(args):
     ms = e0.elapsed_time(e1)
     status = mesh.sync_status()
     iters = log[args.warmup:total, 0].cpu().numpy()
-    launches = int(4 * args.steps + 2 * iters.sum())
+    # our kernels in the timed region: the history mirror once per run call,
+    # then per step predictor, force, right-hand side, finish and the CG loop
+    # (one persistent launch, or a matvec and an update per iteration)
+    cg_kind_run = mesh.cg_choice()[0]
+    per_solve = 1 if cg_kind_run not in ("phases", "auto") else None
+    launches = int(1 + 4 * args.steps + (args.steps * per_solve if per_solve else 2 * iters.sum()))
 
     # end-to-end through the public API with host-resident state: every step
     # copies the state in from pinned host memory, runs, and copies it back.
@@ -412,9 +430,8 @@ def run_ours(args):
 
     # per-kernel device times on this data (overwrites the state)
     sched_var, sched_ms = mesh.schedule()
+    cg_kind, cg_U, cg_ms = mesh.cg_choice()
     prof = mesh.profile_kernels(st, reps=5, opts=opts)
-    names = list(prof.keys())
-    kms = np.array([prof[k] for k in names])
 
     # aggregate over ranks
     t_max = ms
@@ -428,20 +445,35 @@ def run_ours(args):
         return
     value = ws * N * args.steps / (t_max / 1e3)
     ab = algorithmic_bytes(N, Ne, args.prec)
-    per_step = {"predict": kms[0], "force": kms[1], "rhs": kms[2], "finish": kms[5],
-                "matvec": kms[3] * iters.mean(), "update": kms[4] * iters.mean()}
+    per_step = {k: prof[k] for k in ("predict", "force", "rhs", "finish")}
+    ms_launch = {k: prof[k] for k in per_step}
+    bytes_launch = {k: ab[k] for k in per_step}
+    if prof["cg_loop"] > 0:  # the solve's CG loop is one persistent launch
+        per_step["cg_loop"] = prof["cg_loop"] * iters.mean() / max(prof["cg_loop_iters"], 1)
+        ms_launch["cg_loop"] = prof["cg_loop"]
+        bytes_launch["cg_loop"] = ab["cg_iteration"] * prof["cg_loop_iters"]
+    else:
+        for k in ("matvec", "update"):
+            per_step[k] = prof[k] * iters.mean()
+            ms_launch[k] = prof[k]
+            bytes_launch[k] = ab[k]
     dom = max(per_step, key=per_step.get)
-    kidx = names.index(dom)
     peak, peak_kind = peaks()
-    achieved = ab[dom] / (kms[kidx] * 1e-3) / 1e9
+    achieved = bytes_launch[dom] / (ms_launch[dom] * 1e-3) / 1e9
     kname = {"matvec": "k_cg_matvec_nc", "update": "k_cg_update", "force": "k_force_nc",
-             "rhs": "k_dmg_rhs_nc"}.get(dom, dom)
-    roofline = dict(bound="hbm", kernel=dom, achieved=achieved, peak=peak, unit="GB/s",
-                    frac=achieved / peak, peak_kind=peak_kind,
-                    traffic=ncu_traffic(kname) if args.prec == "fp32" else None,
-                    bytes_per_launch=ab[dom], ms_per_launch=kms[kidx])
-    step_bytes = sum(v for k, v in ab.items() if k not in ("matvec", "update")) + \
-        iters.mean() * (ab["matvec"] + ab["update"])
+             "rhs": "k_dmg_rhs_nc", "cg_loop": "k_cg_"}.get(dom, dom)
+    traffic = None
+    if args.prec == "fp32":
+        if dom == "cg_loop":
+            per_iter = ncu_traffic(kname, "ncu_full_cg_loop_plate_1000x1000_fp32.md")
+            traffic = per_iter * prof["cg_loop_iters"] if per_iter else None
+        else:
+            traffic = ncu_traffic(kname)
+    roofline = dict(bound="hbm", kernel=dom if dom != "cg_loop" else f"cg_loop ({prof['cg_loop_family']})",
+                    achieved=achieved, peak=peak, unit="GB/s", frac=achieved / peak, peak_kind=peak_kind,
+                    traffic=traffic, bytes_per_launch=bytes_launch[dom], ms_per_launch=ms_launch[dom],
+                    cg_iterations_per_launch=prof["cg_loop_iters"] if dom == "cg_loop" else None)
+    step_bytes = sum(ab[k] for k in ("predict", "force", "rhs", "finish")) + iters.mean() * ab["cg_iteration"]
     line = dict(
         metric=METRIC, value=value, unit="node-updates/s", n_gpus=ws, steps=args.steps,
         warmup=args.warmup, ms_per_step=t_max / args.steps, higher_is_better=True,
@@ -457,9 +489,11 @@ def run_ours(args):
         e2e=dict(value=ws * N * args.e2e_steps / (e2e_ms / 1e3), unit="node-updates/s",
                  h2d_bytes_per_step=bytes_state, d2h_bytes_per_step=bytes_state),
         gpu_launches=launches, clocks=clocks, status=int(status),
-        cg_iters=dict(mean=float(iters.mean()), max=int(iters.max()), min=int(iters.min())),
-        kernel_ms={k: float(v) for k, v in zip(names, kms)},
-        schedule=dict(variant=sched_var, tune_ms=sched_ms),
+        cg_iters=dict(mean=float(iters.mean()), max=int(iters.max()), min=int(iters.min()),
+                      per_step=[int(v) for v in iters] if args.steps <= 64 else None),
+        kernel_ms=prof,
+        schedule=dict(variant=sched_var, tune_ms=sched_ms,
+                      cg_loop=dict(kind=cg_kind, gathers=cg_U, ms_8_iterations=cg_ms)),
     )
     if not args.no_adjoint:
         line["fwd_adjoint"] = fwd_adjoint(pff, dev)

@@ -267,11 +267,15 @@ pff_status pff_energies(pff_mesh *mesh, const pff_state *state, double *out,
 
 /* Measurement helper: average device time (ms) of each kernel of the step
  * on this mesh's data, ms_out[0..6] = predictor, force/corrector, damage
- * right-hand side, CG matvec, CG update, clamp/finish, energies.  Every
+ * right-hand side, CG matvec, CG update, clamp/finish, energies; when the
+ * AT2 solve runs as one persistent launch (pff_mesh_cg_choice),
+ * ms_out[7] = that launch after one mechanics step, ms_out[8] = its CG
+ * iterations, ms_out[9] = its family (0 phases, 1 persistent, 2 staged,
+ * 3 fused, 4 fused staged; ms_out[7..8] = 0 for phases).  Every timed
  * launch is preceded by a write larger than L2 and bracketed by CUDA events
  * on `stream`; reps launches per kernel.  It OVERWRITES the state and the
  * solve workspace (call it after the run whose numbers you need).
- * Synchronises the stream. */
+ * Synchronises the stream.  ms_out holds 10 doubles. */
 pff_status pff_profile_kernels(pff_mesh *mesh, const pff_state *state, double dt,
                                const pff_options *opt, int32_t reps, double *ms_out,
                                pff_stream stream);

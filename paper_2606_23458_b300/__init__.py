@@ -427,10 +427,14 @@ class Mesh:
         flushed before every launch).  Overwrites the state."""
         s = self._state(st)
         o = opts or options()
-        out = np.zeros(len(self.KERNELS))
+        out = np.zeros(10)
         _check(_lib.pff_profile_kernels(self._h, C.byref(s), float(dt or self.dt), C.byref(o),
                                         int(reps), _hp(out), _stream(stream)))
-        return dict(zip(self.KERNELS, out.tolist()))
+        d = dict(zip(self.KERNELS, out[:7].tolist()))
+        d["cg_loop"] = float(out[7])          # one persistent CG launch (0: kernel per phase)
+        d["cg_loop_iters"] = int(out[8])
+        d["cg_loop_family"] = ("phases", "persistent", "staged", "fused", "fused_staged")[int(out[9])]
+        return d
 
     def energies(self, st, stream=None):
         s = self._state(st)
