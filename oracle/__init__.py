@@ -46,7 +46,7 @@ class _Mat(C.Structure):
 class _RunOpts(C.Structure):
     _fields_ = [("dt", C.c_double), ("t_ramp", C.c_double), ("tol", C.c_double),
                 ("max_it", C.c_int32), ("max_restarts", C.c_int32),
-                ("damage_on", C.c_int32), ("energy_every", C.c_int32)]
+                ("damage_on", C.c_int32), ("energy_every", C.c_int32), ("n_sub", C.c_int32)]
 
 
 _lib = None
@@ -104,6 +104,16 @@ def material(mat):
                 float(mat["Gc"]), float(mat["l0"]), float(mat.get("eta", 1e-7)),
                 MODELS[mat.get("model", "AT2")], SPLITS[mat.get("split", "spectral")],
                 PLANES[mat.get("plane", "strain")], 0)
+
+
+def subcycling_limit(mat):
+    """(c_p / (0.6 c_R), N_max = floor of it): the pre-simulation check of the
+    damage subcycling factor (Sec. 2.4, sec:subcycling)."""
+    m = material(mat)
+    r = C.c_double()
+    n = C.c_int32()
+    _L().or_subcycling_limit(C.byref(m), C.byref(r), C.byref(n))
+    return r.value, n.value
 
 
 def ramp(t, t_ramp):
@@ -241,12 +251,14 @@ class Mesh:
 
     def run(self, mat, state, nsteps, dt, n0=0, t_ramp=0.05e-6, tol=1e-8,
             max_it=10000, max_restarts=50, damage_on=True, energy_every=0,
-            forced=None, W=0.0):
+            forced=None, W=0.0, n_sub=1):
         """Runs nsteps staggered steps on `state` (modified in place).
+        n_sub > 1: damage solved only after steps n with (n+1) % n_sub == 0
+        (subcycling, Sec. 2.4).
         Returns dict(status, iters (nsteps,2), relres, energies (nsteps,4), W)."""
         m = material(mat)
         o = _RunOpts(float(dt), float(t_ramp), float(tol), int(max_it), int(max_restarts),
-                     1 if damage_on else 0, int(energy_every))
+                     1 if damage_on else 0, int(energy_every), int(n_sub))
         for k in ("u", "v", "a"):
             state[k] = _f64(state[k], (self.N, 2))
         state["d"] = _f64(state["d"], (self.N,))
@@ -265,7 +277,7 @@ class Mesh:
                    tol=1e-8, max_it=10000):
         """(loss, dL/dGc, status) for L = mean((d_T - dstar)^2)."""
         m = material(mat)
-        o = _RunOpts(float(dt), float(t_ramp), float(tol), int(max_it), 50, 1, 0)
+        o = _RunOpts(float(dt), float(t_ramp), float(tol), int(max_it), 50, 1, 0, 1)
         s = state0 if state0 is not None else self.new_state()
         u0 = _f64(s["u"], (self.N, 2)); v0 = _f64(s["v"], (self.N, 2))
         a0 = _f64(s["a"], (self.N, 2)); d0 = _f64(s["d"], (self.N,))

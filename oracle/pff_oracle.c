@@ -677,6 +677,33 @@ void or_energies(const or_mesh *m, const or_material *mt, const double *mass,
   out[0] = Eel; out[1] = Ekin; out[2] = Efr;
 }
 
+/* --------------------------------------------- subcycling limit (check) */
+
+/* Pre-simulation check of the damage subcycling factor (Sec. 2.4,
+ * sec:subcycling): the damage front moves at most at about 0.6 c_R while
+ * the explicit step is set by the dilatational speed c_p, so
+ * N_max = floor(c_p / (0.6 c_R)).  c_p = sqrt((lambda + 2 mu) / rho) with
+ * the plane-strain lambda (the speed of the CFL step), c_s = sqrt(mu / rho),
+ * c_R = xi c_s with xi in (0, 1) the root of the Rayleigh equation
+ * (2 - xi^2)^2 = 4 sqrt(1 - k^2 xi^2) sqrt(1 - xi^2), k = c_s / c_p, found by
+ * bisection (xi = 0 is a trivial root; the left side minus the right side
+ * is negative just above 0 and positive at 1). */
+void or_subcycling_limit(const or_material *mt, double *ratio, int32_t *nmax) {
+  const double mu = mt->E / (2.0 * (1.0 + mt->nu));
+  const double lam = mt->E * mt->nu / ((1.0 + mt->nu) * (1.0 - 2.0 * mt->nu));
+  const double cp = sqrt((lam + 2.0 * mu) / mt->rho), cs = sqrt(mu / mt->rho);
+  const double k = cs / cp;
+  double lo = 1e-6, hi = 1.0;
+  for (int it = 0; it < 200; ++it) {
+    const double xi = 0.5 * (lo + hi), x2 = xi * xi;
+    const double f = (2.0 - x2) * (2.0 - x2) - 4.0 * sqrt(1.0 - k * k * x2) * sqrt(1.0 - x2);
+    if (f < 0.0) lo = xi; else hi = xi;
+  }
+  const double cR = 0.5 * (lo + hi) * cs;
+  *ratio = cp / (0.6 * cR);
+  *nmax = (int32_t)floor(*ratio);
+}
+
 /* ---------------------------------------------------------- time stepping */
 
 typedef struct {
@@ -684,6 +711,9 @@ typedef struct {
   int32_t max_it, max_restarts;
   int32_t damage_on;     /* 0: skip the damage solve (d frozen) */
   int32_t energy_every;  /* 0: no energies */
+  int32_t n_sub;         /* damage subcycling (Sec. 2.4, sec:subcycling):
+                            the damage problem is solved only after steps
+                            n with (n + 1) % n_sub == 0; 0 or 1: every step */
 } or_run_opts;
 
 /* One staggered step n -> n+1 (Sec. 2.2): predictor (vv_u), internal force
@@ -714,7 +744,10 @@ static int step_once(const or_mesh *m, const or_material *mt, const double *minv
   int st = OR_OK;
   info[0] = info[1] = 0;
   *relres = 0.0;
-  if (o->damage_on) {
+  /* subcycling: H above is still updated every step; d stays d_n between
+     the solves */
+  const int solve_now = o->n_sub <= 1 || (n + 1) % o->n_sub == 0;
+  if (o->damage_on && solve_now) {
     st = or_damage_solve(m, mt, H, d, dnew, o->tol, o->max_it, o->max_restarts,
                          forced, info, relres, x_out);
     memcpy(d, dnew, N * sizeof(double));
