@@ -354,6 +354,33 @@ def fwd_adjoint(pff, dev, steps=300, policies=(0, 25)):
     return out
 
 
+def subcycled(pff, dev, config, steps=100, warmup=10):
+    """Damage subcycling (Sec. 2.4) on the benchmark plate: N_sub = the
+    material's limit floor(c_p / (0.6 c_R)) (at least 2), same step and
+    tolerance otherwise."""
+    import torch
+    c = S.config(config)
+    ratio, nmax = pff.subcycling_limit(c["material"])
+    n_sub = max(2, nmax)
+    mesh = pff.Mesh.from_plate(c["mesh"], precision="fp32")
+    mesh.set_material(c["material"], c["cfl"])
+    opts = pff.options(cg_tol=c["cg_tol"], t_ramp=c["t_ramp"], damage_every=n_sub)
+    st = mesh.new_state(device=dev)
+    mesh.run(st, warmup, opts=opts)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    mesh.run(st, steps, step0=warmup, opts=opts)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    return dict(workload=config, n_sub=n_sub, limit_ratio=ratio, limit_n_max=nmax, steps=steps,
+                value=mesh.N * steps / (ms / 1e3), unit="node-updates/s", ms_per_step=ms / steps,
+                status=int(mesh.sync_status()))
+
+
 # ------------------------------------------------------------------- ours
 
 def run_ours(args):
@@ -495,6 +522,8 @@ def run_ours(args):
         schedule=dict(variant=sched_var, tune_ms=sched_ms,
                       cg_loop=dict(kind=cg_kind, gathers=cg_U, ms_8_iterations=cg_ms)),
     )
+    if args.model == "AT2":
+        line["subcycled"] = subcycled(pff, dev, args.config)
     if not args.no_adjoint:
         line["fwd_adjoint"] = fwd_adjoint(pff, dev)
     if not args.no_batch:

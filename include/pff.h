@@ -111,6 +111,15 @@ typedef struct {
                            barrier wait gives up after its 2 s limit and the
                            call reports PFF_ERR_TIMEOUT (a test of the
                            bounded wait; the result is not usable). */
+  int32_t damage_every; /* pff_run: damage subcycling N_sub (Sec. 2.4): the
+                           damage problem is solved only after steps n with
+                           (n + 1) % N_sub == 0 (n counted from 0 at step 0,
+                           not from step0); the history H is still updated
+                           every step; d stays d_n in between and those
+                           steps log 0 iterations.  0 or 1: every step [0].
+                           See pff_subcycling_limit for the admissible value.
+                           Not supported by pff_run_ckpt / pff_batch_run
+                           (PFF_ERR_ARG). */
 } pff_options;
 
 /* Device state of one plate (caller-owned). */
@@ -323,6 +332,15 @@ pff_status pff_damage_solve_noalloc(pff_mesh *mesh, const double *H,
                                     pff_stream stream);
 
 /* Message of the last failing call on this host thread. */
+/* Pre-simulation check of the damage subcycling factor (Sec. 2.4): the
+ * damage front moves at most at about 0.6 c_R while the explicit step is set
+ * by the dilatational wave speed c_p, so N_max = floor(c_p / (0.6 c_R)).
+ * c_p = sqrt((lambda + 2 mu) / rho) with the plane-strain lambda (the speed
+ * of the CFL step), c_R the Rayleigh wave speed.  Host-only (no device
+ * work); ratio and n_max nullable.  PFF_ERR_ARG for a non-physical material
+ * (E <= 0, rho <= 0, nu outside (-1, 0.5)). */
+pff_status pff_subcycling_limit(const pff_material *mat, double *ratio, int32_t *n_max);
+
 const char *pff_last_error(void);
 const char *pff_version(void);
 

@@ -55,7 +55,7 @@ class pff_options(C.Structure):
                 ("max_restarts", C.c_int32), ("t_ramp", C.c_double),
                 ("energy_every", C.c_int32), ("ckpt_every", C.c_int32),
                 ("block", C.c_int32), ("loop_mode", C.c_int32), ("variant", C.c_int32),
-                ("cg_kernel", C.c_int32)]
+                ("cg_kernel", C.c_int32), ("damage_every", C.c_int32)]
 
 
 class pff_plate(C.Structure):
@@ -91,6 +91,7 @@ _sig = {
                             C.c_int32, _P, _P],
     "pff_mesh_schedule": [_P, _P, _P],
     "pff_mesh_cg_choice": [_P, _P, _P, _P],
+    "pff_subcycling_limit": [C.POINTER(pff_material), C.POINTER(C.c_double), C.POINTER(C.c_int32)],
     "pff_ckpt_create": [_P, C.c_int64, C.c_int32, C.POINTER(C.c_void_p)],
     "pff_ckpt_destroy": [_P],
     "pff_ckpt_stats": [_P, C.POINTER(C.c_int64)],
@@ -139,9 +140,19 @@ def _stream(stream=None):
 
 
 def options(cg_tol=1e-8, cg_max_it=10000, max_restarts=50, t_ramp=0.05e-6, energy_every=0,
-            ckpt_every=25, block=0, loop_mode=PFF_LOOP_GRAPH, variant=0, cg_kernel=PFF_CG_AUTO):
+            ckpt_every=25, block=0, loop_mode=PFF_LOOP_GRAPH, variant=0, cg_kernel=PFF_CG_AUTO,
+            damage_every=0):
     return pff_options(cg_tol, cg_max_it, max_restarts, t_ramp, energy_every, ckpt_every,
-                       block, loop_mode, variant, cg_kernel)
+                       block, loop_mode, variant, cg_kernel, damage_every)
+
+
+def subcycling_limit(mat):
+    """(c_p / (0.6 c_R), N_max) for a material dict: the admissible damage
+    subcycling factor (pff_subcycling_limit)."""
+    r = C.c_double()
+    n = C.c_int32()
+    _check(_lib.pff_subcycling_limit(C.byref(material(mat)), C.byref(r), C.byref(n)))
+    return r.value, n.value
 
 
 def material(mat):

@@ -1557,8 +1557,8 @@ __global__ void __launch_bounds__(FusedCfg<ST>::threads, FusedCfg<ST>::minb) k_c
   extern __shared__ __align__(128) unsigned char stage_smem[];
   if (S->done) return;  // set-up found b_eff = 0 or r_0 already small
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
-  StageCta sc;
-  LocalLayout L;
+  StageCta sc{};
+  LocalLayout L{};
   if constexpr (ST) {
     sc = P.st_cta[blockIdx.x];
     L = local_layout(sc.nel, sc.row1 - sc.row0, P.D, sc.nn);
@@ -1827,6 +1827,20 @@ __global__ void __launch_bounds__(256) k_dmg_finish(Params<R> P) {
       const int64_t n = *P.step_ctr;
       P.iters_log[2 * n] = S.iters;
       P.iters_log[2 * n + 1] = S.restarts;
+    }
+    if (P.step_inc) *P.step_inc += 1;
+  }
+}
+
+// End of a step without a damage solve (subcycling, Sec. 2.4): d stays d_n;
+// the iteration log gets zeros and the step counter advances.
+template <typename R>
+__global__ void k_step_skip(Params<R> P) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (P.iters_log && P.step_ctr) {
+      const int64_t n = *P.step_ctr;
+      P.iters_log[2 * n] = 0;
+      P.iters_log[2 * n + 1] = 0;
     }
     if (P.step_inc) *P.step_inc += 1;
   }

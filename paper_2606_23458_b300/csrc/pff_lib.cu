@@ -280,7 +280,7 @@ struct pff_mesh {
   int64_t *step_ctr = nullptr;   // step index k within the current run
   double *stab = nullptr;        // S(t) per step of the current run
   int64_t stab_cap = 0;
-  GraphCache solve_g, step_g;
+  GraphCache solve_g, step_g, mech_g;  // mech_g: a step without the damage solve
   int block = 256;
   // launch configuration (kernel id -> grid, dynamic shared memory)
   int32_t NB = 256, nblk = 0, maxE = 0;
@@ -326,6 +326,7 @@ static void mesh_free(pff_mesh *m) {
   if (!m) return;
   free_graph(m->solve_g);
   free_graph(m->step_g);
+  free_graph(m->mech_g);
   void *ptrs[] = {m->st_cta, m->st_rng, m->st_nrng, m->st_lrec, m->st_slot, m->cgv, m->cgp,
                   m->ptr, m->ent, m->ell, m->rec, m->fext, m->minv, m->area_d, m->flags,
                   m->x, m->r, m->b, m->part, m->energy, m->wext, m->pz, m->q, m->dinv,
@@ -947,6 +948,19 @@ static pff_status add_kernel(const pff_mesh *m, cudaGraph_t g, const std::vector
   return PFF_OK;
 }
 
+static pff_status add_generic(cudaGraph_t g, const std::vector<cudaGraphNode_t> &deps, const void *fn,
+                              unsigned grid, unsigned block, size_t smem, void **args, cudaGraphNode_t *out) {
+  cudaKernelNodeParams kp;
+  std::memset(&kp, 0, sizeof(kp));
+  kp.func = const_cast<void *>(fn);
+  kp.gridDim = dim3(grid);
+  kp.blockDim = dim3(block);
+  kp.sharedMemBytes = (unsigned)smem;
+  kp.kernelParams = args;
+  CUDA_TRY(cudaGraphAddKernelNode(out, g, deps.data(), deps.size(), &kp));
+  return PFF_OK;
+}
+
 static pff_status add_while(cudaGraph_t g, const std::vector<cudaGraphNode_t> &deps,
                             cudaGraphConditionalHandle h, cudaGraph_t *body, cudaGraphNode_t *out) {
   cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
@@ -1386,6 +1400,7 @@ static pff_status run_t(pff_mesh *m, const pff_state *st, int64_t step0, int64_t
     PFF_TRY(dalloc(&m->stab, nsteps + 1));
     m->stab_cap = nsteps + 1;
     free_graph(m->step_g);
+    free_graph(m->mech_g);
     if (gcache) free_graph(*gcache);
   }
   {
@@ -1407,11 +1422,18 @@ static pff_status run_t(pff_mesh *m, const pff_state *st, int64_t step0, int64_t
   CUDA_TRY(cudaStreamSynchronize(s));
   if (step0 == 0) CUDA_TRY(cudaMemsetAsync(m->wext, 0, sizeof(double), s));
   const unsigned Gtape = std::min<unsigned>(grid_for(std::max(m->N, m->Ne), kThreads), m->grid[KP_UPDATE][0]);
+  // damage subcycling (Sec. 2.4): the solve runs after global steps n with
+  // (n + 1) % n_sub == 0 only; H is updated every step by the force kernel
+  const int64_t n_sub = std::max<int32_t>(1, o.damage_every);
+  auto solves = [&](int64_t n) { return (step0 + n + 1) % n_sub == 0; };
   if (o.loop_mode == PFF_LOOP_HOST) {
     for (int64_t n = 0; n < nsteps; ++n) {
       PFF_TRY(launch<R>(m, KP_PREDICT, P, s));
       PFF_TRY(launch<R>(m, KP_FORCE, P, s));
-      PFF_TRY(solve_host_loop<R>(m, P, plan, s));
+      if (solves(n))
+        PFF_TRY(solve_host_loop<R>(m, P, plan, s));
+      else
+        k_step_skip<R><<<1, 32, 0, s>>>(P);
       if (tape) k_tape_store<R><<<Gtape, kThreads, 0, s>>>(P, *tape);
       if (energy_log && o.energy_every > 0 && (n + 1) % o.energy_every == 0) {
         Params<R> E = P;
@@ -1471,8 +1493,34 @@ static pff_status run_t(pff_mesh *m, const pff_state *st, int64_t step0, int64_t
     }
     gc.key = key;
   }
+  if (n_sub > 1 && (!m->mech_g.exec || m->mech_g.key != key)) {
+    // the step without the damage solve: predictor, force, step bookkeeping
+    free_graph(m->mech_g);
+    cudaGraph_t g;
+    CUDA_TRY(cudaGraphCreate(&g, 0));
+    Params<R> Q = P;
+    Q.use_cond = 0;
+    cudaGraphNode_t n_pr, n_f, n_sk;
+    pff_status stt = add_kernel<R>(m, g, {}, KP_PREDICT, Q, &n_pr);
+    if (stt == PFF_OK) stt = add_kernel<R>(m, g, {n_pr}, KP_FORCE, Q, &n_f);
+    if (stt == PFF_OK) {
+      void *args[] = {(void *)&Q};
+      stt = add_generic(g, {n_f}, (const void *)k_step_skip<R>, 1, 32, 0, args, &n_sk);
+    }
+    if (stt != PFF_OK) {
+      cudaGraphDestroy(g);
+      return stt;
+    }
+    cudaError_t e = cudaGraphInstantiate(&m->mech_g.exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      m->mech_g.exec = nullptr;
+      return fail(PFF_ERR_CUDA, std::string("cudaGraphInstantiate (mechanics step): ") + cudaGetErrorString(e));
+    }
+    m->mech_g.key = key;
+  }
   for (int64_t n = 0; n < nsteps; ++n) {
-    CUDA_TRY(cudaGraphLaunch(gc.exec, s));
+    CUDA_TRY(cudaGraphLaunch(solves(n) ? gc.exec : m->mech_g.exec, s));
     if (energy_log && o.energy_every > 0 && (n + 1) % o.energy_every == 0) {
       Params<R> E = P;
       E.energy_out = energy_log + 4 * n;
@@ -1636,6 +1684,34 @@ static pff_status mesh_build_t(pff_mesh *m, const double *xy_d, const int32_t *t
 extern "C" {
 
 const char *pff_last_error(void) { return g_err.c_str(); }
+
+// Pre-simulation check of the damage subcycling factor (Sec. 2.4): c_p from
+// the plane-strain Lame constants (the speed behind the CFL step), c_s, and
+// the Rayleigh speed c_R = c_s sqrt(eta) with eta the root in (0, 1) of the
+// Rayleigh cubic eta^3 - 8 eta^2 + (24 - 16 k^2) eta - 16 (1 - k^2) = 0,
+// k = c_s / c_p (the squared Rayleigh equation with the eta = 0 root
+// divided out; negative at 0, +1 at 1, one root between), by Newton's
+// method from eta = 1.
+pff_status pff_subcycling_limit(const pff_material *mat, double *ratio, int32_t *n_max) {
+  if (!mat || !(mat->E > 0) || !(mat->rho > 0) || !(mat->nu > -1.0 && mat->nu < 0.5))
+    return fail(PFF_ERR_ARG, "bad material");
+  const double E = mat->E, nu = mat->nu;
+  const double mu = E / (2.0 * (1.0 + nu)), lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+  const double cp = std::sqrt((lam + 2.0 * mu) / mat->rho), cs = std::sqrt(mu / mat->rho);
+  const double k2 = (cs / cp) * (cs / cp);
+  double eta = 1.0;
+  for (int it = 0; it < 60; ++it) {
+    const double f = ((eta - 8.0) * eta + (24.0 - 16.0 * k2)) * eta - 16.0 * (1.0 - k2);
+    const double df = (3.0 * eta - 16.0) * eta + (24.0 - 16.0 * k2);
+    const double step = f / df;
+    eta -= step;
+    if (std::fabs(step) <= 1e-16 * eta) break;
+  }
+  const double r = cp / (0.6 * cs * std::sqrt(eta));
+  if (ratio) *ratio = r;
+  if (n_max) *n_max = (int32_t)std::floor(r);
+  return PFF_OK;
+}
 const char *pff_version(void) { return "pff 0.1 (sm_103a)"; }
 
 pff_status pff_mesh_create(int64_t N, const double *xy, int64_t Ne, const int32_t *tri, const uint8_t *notch,
@@ -2207,18 +2283,6 @@ static pff_status run_ckpt_t(pff_mesh *m, const pff_state *st, int64_t step0, in
 // up, adjoint CG (device-side WHILE loop, same matvec/update kernels as the
 // forward), damage terms, mechanics reverse, slot advance.  The slot comes
 // from *kctr, so one graph per in/out parity serves every step.
-static pff_status add_generic(cudaGraph_t g, const std::vector<cudaGraphNode_t> &deps, const void *fn,
-                              unsigned grid, unsigned block, size_t smem, void **args, cudaGraphNode_t *out) {
-  cudaKernelNodeParams kp;
-  std::memset(&kp, 0, sizeof(kp));
-  kp.func = const_cast<void *>(fn);
-  kp.gridDim = dim3(grid);
-  kp.blockDim = dim3(block);
-  kp.sharedMemBytes = (unsigned)smem;
-  kp.kernelParams = args;
-  CUDA_TRY(cudaGraphAddKernelNode(out, g, deps.data(), deps.size(), &kp));
-  return PFF_OK;
-}
 
 template <typename R>
 static pff_status build_reverse_graph(pff_mesh *m, pff_ckpt *c, AdjParams<R> A, const CgPlan &plan,
@@ -2414,6 +2478,7 @@ pff_status pff_run_ckpt(pff_mesh *m, const pff_state *st, int64_t step0, int64_t
   if (!m || !st || !c || !st->u || !st->v || !st->a || !st->d || !st->H) return fail(PFF_ERR_ARG, "null argument");
   if (c->m != m) return fail(PFF_ERR_ARG, "checkpoint belongs to another mesh");
   if (nsteps != c->nsteps) return fail(PFF_ERR_ARG, "nsteps differs from the checkpoint's");
+  if (opt && opt->damage_every > 1) return fail(PFF_ERR_ARG, "damage subcycling is not supported with the adjoint tape");
   if (!m->has_mat) return fail(PFF_ERR_ARG, "material not set");
   if (!(dt > 0) || step0 < 0) return fail(PFF_ERR_ARG, "bad dt / step");
   const pff_options o = defaults(opt);
@@ -2729,6 +2794,7 @@ pff_status pff_batch_run(pff_batch *b, const pff_state *st, int64_t step0, int64
                          int32_t *iters_log, pff_stream stream) {
   if (!b || !st || !st->u || !st->v || !st->a || !st->d || !st->H || nsteps < 0 || step0 < 0)
     return fail(PFF_ERR_ARG, "bad arguments");
+  if (opt && opt->damage_every > 1) return fail(PFF_ERR_ARG, "damage subcycling is not supported for batches");
   pff_options o = defaults(opt);
   cudaStream_t s = (cudaStream_t)stream;
   // per-plate tolerance (FP32 floor as for one plate)

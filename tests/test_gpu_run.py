@@ -144,3 +144,60 @@ def test_autotuner_choice_reported(orc, pff):
     for k in ("force", "rhs", "matvec"):
         assert 1 <= var[k] <= 5
         assert ms[k][var[k] - 1] == min(ms[k]) > 0
+
+
+@pytest.mark.parametrize("n_sub", [2, 3])
+def test_subcycled_run_per_step_parity(orc, pff, n_sub):
+    """Damage subcycling (Sec. 2.4): FP64 fields within 1e-10 of the oracle
+    after every step of a 60-step window (oracle forced to the GPU's
+    iteration counts); skipped steps log zero iterations and keep d."""
+    import torch
+    c, om, gm, dt = _setup(pff, orc)
+    mat = c["material"]
+    nsteps = 60
+    opts = pff.options(damage_every=n_sub)
+    gst = gm.new_state()
+    ost = om.new_state()
+    log = torch.zeros(nsteps, 2, dtype=torch.int32, device="cuda")
+    worst = 0.0
+    for n in range(nsteps):
+        d_before = to_np(gst["d"]).copy()
+        gm.run(gst, 1, step0=n, opts=opts, iters_log=log[n:n + 1])
+        torch.cuda.synchronize()
+        it = int(log[n, 0])
+        om.run(mat, ost, 1, dt, n0=n, forced=[it], n_sub=n_sub)
+        if (n + 1) % n_sub:
+            assert it == 0 and np.array_equal(to_np(gst["d"]), d_before), n
+        for k in ("u", "v", "a"):
+            worst = max(worst, rel_l2(to_np(gst[k]), ost[k]))
+        worst = max(worst, max_rel(to_np(gst["d"]), ost["d"], 1e-3))
+        worst = max(worst, rel_l2(to_np(gst["H"]), ost["H"]))
+        assert worst <= 1e-10, (n, worst)
+    assert gm.sync_status() == 0
+
+
+def test_subcycled_fp32_run_in_one_call(orc, pff):
+    """FP32, one pff_run call of 120 steps at N_sub = N_max of the material
+    against the FP64 oracle; a whole-run call gives the same fields as the
+    same steps split over several calls."""
+    import torch
+    c, om, gm, dt = _setup(pff, orc, prec="fp32")
+    mat = c["material"]
+    n_sub = max(2, pff.subcycling_limit(mat)[1])
+    opts = pff.options(damage_every=n_sub)
+    a = gm.new_state()
+    la = torch.zeros(120, 2, dtype=torch.int32, device="cuda")
+    gm.run(a, 120, opts=opts, iters_log=la)
+    b = gm.new_state()
+    for k0 in range(0, 120, 7):
+        gm.run(b, min(7, 120 - k0), step0=k0, opts=opts)
+    torch.cuda.synchronize()
+    for k in ("u", "v", "a", "d", "H"):
+        assert torch.equal(a[k], b[k]), k
+    li = la[:, 0].cpu().numpy()
+    assert np.all(li[np.arange(120) % n_sub != n_sub - 1] == 0)
+    ost = om.new_state()
+    om.run(mat, ost, 120, dt, n_sub=n_sub)
+    eu = rel_l2(to_np(a["u"]), ost["u"])
+    ed = np.abs(to_np(a["d"]) - ost["d"]).max()
+    assert eu <= 1e-4 and ed <= 1e-3, (eu, ed)
