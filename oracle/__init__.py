@@ -24,7 +24,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 
 MODELS = {"AT1": 1, "AT2": 2}
 SPLITS = {"spectral": 0, "amor": 1, "iso": 2}
-PLANES = {"strain": 0}
+PLANES = {"strain": 0, "stress": 1}
 
 
 def build(force=False):

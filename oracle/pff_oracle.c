@@ -44,7 +44,7 @@
 
 enum { OR_AT1 = 1, OR_AT2 = 2 };
 enum { OR_SPECTRAL = 0, OR_AMOR = 1, OR_ISO = 2 };
-enum { OR_PLANE_STRAIN = 0 };
+enum { OR_PLANE_STRAIN = 0, OR_PLANE_STRESS = 1 };
 
 typedef struct {
   double E, nu, rho, Gc, l0, eta;
@@ -190,15 +190,22 @@ int or_colour(const or_mesh *m, uint8_t *colour) {
 
 /* ------------------------------------------------------------- material */
 
-typedef struct { double lam, mu, K; } or_lame;
+typedef struct { double lam, mu, K, cz; } or_lame;
 
-/* Plane strain: lambda_PE = E nu / ((1+nu)(1-2nu)), mu = E / (2(1+nu)),
- * 3-D bulk modulus K = E / (3(1-2nu)) (Sec. 2.1, "Plane assumptions"). */
+/* Sec. 2.1, "Plane assumptions": the first Lame parameter of the plane
+ * model, lambda_PE = E nu / ((1+nu)(1-2nu)) (plane strain) or
+ * lambda_PS = E nu / (1 - nu^2) (plane stress); mu = E / (2(1+nu)); the
+ * 3-D bulk modulus K = E / (3(1-2nu)) in both; cz = nu / (1 - nu) under
+ * plane stress (e_zz = -cz tr_2D enters the 3-D trace of the
+ * volumetric-deviatoric split), 0 under plane strain (e_zz = 0). */
 static or_lame lame_of(const or_material *mt) {
   or_lame L;
-  L.lam = mt->E * mt->nu / ((1.0 + mt->nu) * (1.0 - 2.0 * mt->nu));
+  const int ps = mt->plane == OR_PLANE_STRESS;
+  L.lam = ps ? mt->E * mt->nu / (1.0 - mt->nu * mt->nu)
+             : mt->E * mt->nu / ((1.0 + mt->nu) * (1.0 - 2.0 * mt->nu));
   L.mu = mt->E / (2.0 * (1.0 + mt->nu));
   L.K = mt->E / (3.0 * (1.0 - 2.0 * mt->nu));
+  L.cz = ps ? mt->nu / (1.0 - mt->nu) : 0.0;
   return L;
 }
 
@@ -245,17 +252,22 @@ static void split_point(const or_material *mt, const double e[3], double sp[3],
     *psip = 0.5 * L.lam * pos(tr) * pos(tr) + L.mu * (pos(e1) * pos(e1) + pos(e2) * pos(e2));
     *psim = 0.5 * L.lam * neg(tr) * neg(tr) + L.mu * (neg(e1) * neg(e1) + neg(e2) * neg(e2));
   } else if (mt->split == OR_AMOR) {
-    /* Eq. (amor_split): 3-D deviator of the plane-strain tensor (e_zz = 0):
-     * e_dev:e_dev = e:e - tr^2/3. */
-    double ee = e[0] * e[0] + e[1] * e[1] + 2.0 * e[2] * e[2];
-    sp[0] = L.K * pos(tr) + 2.0 * L.mu * (e[0] - tr / 3.0);
-    sp[1] = L.K * pos(tr) + 2.0 * L.mu * (e[1] - tr / 3.0);
+    /* Eq. (amor_split) on the 3-D strain (e_xx, e_yy, e_xy; e_zz) with
+     * e_zz = -cz tr (0 in plane strain): tr3 = tr + e_zz,
+     * e_dev:e_dev = e:e + e_zz^2 - tr3^2/3.  The in-plane stresses are the
+     * derivatives of psi+- with respect to the in-plane strain, e_zz
+     * following it (d e_zz / d e_xx = d e_zz / d e_yy = -cz). */
+    double ez = -L.cz * tr, tr3 = tr + ez, f = 1.0 - L.cz;
+    double ee = e[0] * e[0] + e[1] * e[1] + 2.0 * e[2] * e[2] + ez * ez;
+    double dz = L.cz * ez;  /* e_zz's share of d(e:e)/2 d e_xx, sign included */
+    sp[0] = L.K * pos(tr3) * f + 2.0 * L.mu * (e[0] - dz - f * tr3 / 3.0);
+    sp[1] = L.K * pos(tr3) * f + 2.0 * L.mu * (e[1] - dz - f * tr3 / 3.0);
     sp[2] = 2.0 * L.mu * e[2];
-    sm[0] = L.K * neg(tr);
-    sm[1] = L.K * neg(tr);
+    sm[0] = L.K * neg(tr3) * f;
+    sm[1] = L.K * neg(tr3) * f;
     sm[2] = 0.0;
-    *psip = 0.5 * L.K * pos(tr) * pos(tr) + L.mu * (ee - tr * tr / 3.0);
-    *psim = 0.5 * L.K * neg(tr) * neg(tr);
+    *psip = 0.5 * L.K * pos(tr3) * pos(tr3) + L.mu * (ee - tr3 * tr3 / 3.0);
+    *psim = 0.5 * L.K * neg(tr3) * neg(tr3);
   } else {
     /* isotropic: psi+ = psi, psi- = 0 (Sec. 2.1). */
     double ee = e[0] * e[0] + e[1] * e[1] + 2.0 * e[2] * e[2];
@@ -335,11 +347,15 @@ static void split_tangent(const or_material *mt, const double e[3],
     dsm[1] = L.lam * (1.0 - Htr) * dtr + 2.0 * L.mu * (de[1] - dep[1][1]);
     dsm[2] = 2.0 * L.mu * (de[2] - dep[0][1]);
   } else if (mt->split == OR_AMOR) {
-    dsp[0] = L.K * Htr * dtr + 2.0 * L.mu * (de[0] - dtr / 3.0);
-    dsp[1] = L.K * Htr * dtr + 2.0 * L.mu * (de[1] - dtr / 3.0);
+    /* derivative of the stresses above: tr3 = f tr, e_zz = -cz tr */
+    double f = 1.0 - L.cz;
+    double H3 = f * tr > 0.0 ? 1.0 : 0.0;
+    double dlin = (L.cz * L.cz - f * f / 3.0) * dtr;  /* -cz d e_zz - f d tr3 / 3 */
+    dsp[0] = L.K * H3 * f * f * dtr + 2.0 * L.mu * (de[0] + dlin);
+    dsp[1] = L.K * H3 * f * f * dtr + 2.0 * L.mu * (de[1] + dlin);
     dsp[2] = 2.0 * L.mu * de[2];
-    dsm[0] = L.K * (1.0 - Htr) * dtr;
-    dsm[1] = L.K * (1.0 - Htr) * dtr;
+    dsm[0] = L.K * (1.0 - H3) * f * f * dtr;
+    dsm[1] = L.K * (1.0 - H3) * f * f * dtr;
     dsm[2] = 0.0;
   } else {
     dsp[0] = L.lam * dtr + 2.0 * L.mu * de[0];
@@ -683,15 +699,14 @@ void or_energies(const or_mesh *m, const or_material *mt, const double *mass,
  * sec:subcycling): the damage front moves at most at about 0.6 c_R while
  * the explicit step is set by the dilatational speed c_p, so
  * N_max = floor(c_p / (0.6 c_R)).  c_p = sqrt((lambda + 2 mu) / rho) with
- * the plane-strain lambda (the speed of the CFL step), c_s = sqrt(mu / rho),
+ * the plane model's lambda (the speed of the CFL step), c_s = sqrt(mu / rho),
  * c_R = xi c_s with xi in (0, 1) the root of the Rayleigh equation
  * (2 - xi^2)^2 = 4 sqrt(1 - k^2 xi^2) sqrt(1 - xi^2), k = c_s / c_p, found by
  * bisection (xi = 0 is a trivial root; the left side minus the right side
  * is negative just above 0 and positive at 1). */
 void or_subcycling_limit(const or_material *mt, double *ratio, int32_t *nmax) {
-  const double mu = mt->E / (2.0 * (1.0 + mt->nu));
-  const double lam = mt->E * mt->nu / ((1.0 + mt->nu) * (1.0 - 2.0 * mt->nu));
-  const double cp = sqrt((lam + 2.0 * mu) / mt->rho), cs = sqrt(mu / mt->rho);
+  or_lame L = lame_of(mt);
+  const double cp = sqrt((L.lam + 2.0 * L.mu) / mt->rho), cs = sqrt(L.mu / mt->rho);
   const double k = cs / cp;
   double lo = 1e-6, hi = 1.0;
   for (int it = 0; it < 200; ++it) {
