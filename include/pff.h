@@ -50,7 +50,7 @@ typedef enum {
 
 enum { PFF_AT1 = 1, PFF_AT2 = 2 };
 enum { PFF_SPLIT_SPECTRAL = 0, PFF_SPLIT_AMOR = 1, PFF_SPLIT_ISO = 2 };
-enum { PFF_PLANE_STRAIN = 0 };
+enum { PFF_PLANE_STRAIN = 0, PFF_PLANE_STRESS = 1 };
 enum { PFF_FP64 = 0, PFF_FP32_MIXED = 1 };
 enum { PFF_LOOP_GRAPH = 0, PFF_LOOP_HOST = 1 };
 enum { PFF_CG_AUTO = 0, PFF_CG_PHASES = 1, PFF_CG_PERSISTENT = 2, PFF_CG_TEST_TIMEOUT = 3,
@@ -62,8 +62,11 @@ typedef struct pff_mesh pff_mesh; /* opaque; owns geometry, CSR, workspaces */
  * model: PFF_AT1 | PFF_AT2 (crack density, Sec. 2.1);
  * split: spectral (Eq. spectral_split), volumetric-deviatoric (Eq.
  *        amor_split) or isotropic (psi+ = psi);
- * plane: plane strain (lambda_PE); eta: residual stiffness in
- *        g(d) = (1-d)^2 + eta. */
+ * plane: PFF_PLANE_STRAIN (lambda_PE = E nu / ((1+nu)(1-2nu))) or
+ *        PFF_PLANE_STRESS (lambda_PS = E nu / (1-nu^2); the
+ *        volumetric-deviatoric split keeps the 3-D bulk modulus and adds
+ *        e_zz = -nu/(1-nu) tr to the 3-D trace, Sec. 2.1 plane assumptions);
+ * eta: residual stiffness in g(d) = (1-d)^2 + eta. */
 typedef struct {
   double E, nu, rho, Gc, l0, eta;
   int32_t model, split, plane, reserved;
@@ -149,7 +152,7 @@ pff_status pff_mesh_create(int64_t N, const double *xy, int64_t Ne,
 
 void pff_mesh_destroy(pff_mesh *mesh);
 
-/* Sets the material: plane-strain Lame constants (Sec. 2.1), lumped mass
+/* Sets the material: the plane model's Lame constants (Sec. 2.1), lumped mass
  * m_i = rho sum A_e / 3 and the stable step dt = cfl * h_min / c_p with
  * c_p = sqrt((lambda + 2 mu) / rho) (velocity-Verlet paragraph, Sec. 2.3).
  * dt_out (host, nullable) receives that step.  Synchronises internally. */
@@ -335,10 +338,11 @@ pff_status pff_damage_solve_noalloc(pff_mesh *mesh, const double *H,
 /* Pre-simulation check of the damage subcycling factor (Sec. 2.4): the
  * damage front moves at most at about 0.6 c_R while the explicit step is set
  * by the dilatational wave speed c_p, so N_max = floor(c_p / (0.6 c_R)).
- * c_p = sqrt((lambda + 2 mu) / rho) with the plane-strain lambda (the speed
- * of the CFL step), c_R the Rayleigh wave speed.  Host-only (no device
- * work); ratio and n_max nullable.  PFF_ERR_ARG for a non-physical material
- * (E <= 0, rho <= 0, nu outside (-1, 0.5)). */
+ * c_p = sqrt((lambda + 2 mu) / rho) with the plane model's lambda (the
+ * speed of the CFL step), c_R the Rayleigh wave speed of the same plane
+ * model.  Host-only (no device work); ratio and n_max nullable.
+ * PFF_ERR_ARG for a non-physical material (E <= 0, rho <= 0, nu outside
+ * (-1, 0.5), unknown plane). */
 pff_status pff_subcycling_limit(const pff_material *mat, double *ratio, int32_t *n_max);
 
 const char *pff_last_error(void);

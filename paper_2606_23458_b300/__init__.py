@@ -34,6 +34,8 @@ CG_KINDS = {PFF_CG_AUTO: "auto", PFF_CG_PHASES: "phases", PFF_CG_PERSISTENT: "pe
 
 MODELS = {"AT1": PFF_AT1, "AT2": PFF_AT2}
 SPLITS = {"spectral": PFF_SPLIT_SPECTRAL, "amor": PFF_SPLIT_AMOR, "iso": PFF_SPLIT_ISO}
+PFF_PLANE_STRAIN, PFF_PLANE_STRESS = 0, 1
+PLANES = {"strain": PFF_PLANE_STRAIN, "stress": PFF_PLANE_STRESS}
 PRECISIONS = {"fp64": PFF_FP64, "fp32": PFF_FP32_MIXED}
 
 
@@ -158,7 +160,8 @@ def subcycling_limit(mat):
 def material(mat):
     return pff_material(float(mat["E"]), float(mat["nu"]), float(mat["rho"]), float(mat["Gc"]),
                         float(mat["l0"]), float(mat.get("eta", 1e-7)),
-                        MODELS[mat.get("model", "AT2")], SPLITS[mat.get("split", "spectral")], 0, 0)
+                        MODELS[mat.get("model", "AT2")], SPLITS[mat.get("split", "spectral")],
+                        PLANES[mat.get("plane", "strain")], 0)
 
 
 def _dptr(t):

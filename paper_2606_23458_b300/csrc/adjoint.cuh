@@ -133,13 +133,24 @@ __device__ __forceinline__ void split_tangent(const Params<R> &P, R exx, R eyy, 
     dsm[0] = P.lam * (R(1) - Htr) * dtr + mu2 * (de[0] - dxx);
     dsm[1] = P.lam * (R(1) - Htr) * dtr + mu2 * (de[1] - dyy);
     dsm[2] = mu2 * (de[2] - dxy);
-  } else if (P.split == kAmor) {
+  } else if (P.split == kAmor && P.cz == R(0)) {
     const R mu2 = R(2) * P.mu, t3 = dtr * (R(1) / R(3));
     dsp[0] = P.K * Htr * dtr + mu2 * (de[0] - t3);
     dsp[1] = P.K * Htr * dtr + mu2 * (de[1] - t3);
     dsp[2] = mu2 * de[2];
     dsm[0] = P.K * (R(1) - Htr) * dtr;
     dsm[1] = P.K * (R(1) - Htr) * dtr;
+    dsm[2] = R(0);
+  } else if (P.split == kAmor) {
+    // plane stress (see stress()): tr3 = f tr, e_zz = -cz tr
+    const R f = R(1) - P.cz, mu2 = R(2) * P.mu;
+    const R H3 = f * tr > R(0) ? R(1) : R(0);
+    const R lin = (P.cz * P.cz - f * f * (R(1) / R(3))) * dtr;
+    dsp[0] = P.K * H3 * f * f * dtr + mu2 * (de[0] + lin);
+    dsp[1] = P.K * H3 * f * f * dtr + mu2 * (de[1] + lin);
+    dsp[2] = mu2 * de[2];
+    dsm[0] = P.K * (R(1) - H3) * f * f * dtr;
+    dsm[1] = P.K * (R(1) - H3) * f * f * dtr;
     dsm[2] = R(0);
   } else {
     const R mu2 = R(2) * P.mu;

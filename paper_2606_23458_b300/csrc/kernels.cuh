@@ -114,8 +114,9 @@ template <typename R> struct Params {
   // (read one, write the other each pass) and the search direction p
   float4 *cgv0, *cgv1;
   float *cgp;
-  // material
-  R lam, mu, K, eta;
+  // material (lam: the plane model's first Lame parameter; K: 3-D bulk
+  // modulus; cz = nu / (1 - nu) under plane stress, 0 under plane strain)
+  R lam, mu, K, eta, cz;
   int32_t split, model;
   R kappa;      // damage diffusion coefficient (Gc l0 or 3/4 Gc l0)
   R cbase;      // reaction: c_e = cbase + 2 H_e
@@ -327,7 +328,9 @@ __device__ __forceinline__ long long f2d_bits(float f) {
 // Spectral (Eq. spectral_split): with D = eps - tr/2 I and R = |D|, the
 // tensile part is eps+ = (<e1>+ + <e2>+)/2 I + (<e1>+ - <e2>+)/(2R) D.
 // Volumetric-deviatoric (Eq. amor_split) uses the 3-D deviator of the
-// plane-strain tensor.  sigma = g sigma+ + sigma-.
+// strain with e_zz = -cz tr (0 in plane strain; plane stress: the
+// out-of-plane strain of Sec. 2.1, whose dependence on the in-plane strain
+// enters the stress).  sigma = g sigma+ + sigma-.
 template <typename R>
 __device__ __forceinline__ void stress(const Params<R> &P, R exx, R eyy, R exy, R g,
                                        R &sxx, R &syy, R &sxy, R &psip) {
@@ -346,13 +349,24 @@ __device__ __forceinline__ void stress(const Params<R> &P, R exx, R eyy, R exy, 
     syy = g * (tp + mu2 * pyy) + tm + mu2 * (eyy - pyy);
     sxy = g * (mu2 * pxy) + mu2 * (exy - pxy);
     psip = R(0.5) * P.lam * trp * trp + P.mu * (e1p * e1p + e2p * e2p);
-  } else if (P.split == kAmor) {
+  } else if (P.split == kAmor && P.cz == R(0)) {
     const R t3 = tr * (R(1) / R(3)), mu2 = R(2) * P.mu;
     sxx = g * (P.K * trp + mu2 * (exx - t3)) + P.K * trm;
     syy = g * (P.K * trp + mu2 * (eyy - t3)) + P.K * trm;
     sxy = g * (mu2 * exy);
     psip = R(0.5) * P.K * trp * trp +
            P.mu * (exx * exx + eyy * eyy + R(2) * exy * exy - tr * t3);
+  } else if (P.split == kAmor) {
+    // plane stress: e_zz = -cz tr, tr3 = f tr with f = 1 - cz; the in-plane
+    // stresses carry d e_zz / d e_ii = -cz
+    const R f = R(1) - P.cz, ez = -P.cz * tr, tr3 = f * tr;
+    const R t3p = rpos(tr3), t3m = rneg(tr3), mu2 = R(2) * P.mu;
+    const R lin = P.cz * P.cz * tr - f * tr3 * (R(1) / R(3));
+    sxx = g * (P.K * f * t3p + mu2 * (exx + lin)) + P.K * f * t3m;
+    syy = g * (P.K * f * t3p + mu2 * (eyy + lin)) + P.K * f * t3m;
+    sxy = g * (mu2 * exy);
+    psip = R(0.5) * P.K * t3p * t3p +
+           P.mu * (exx * exx + eyy * eyy + R(2) * exy * exy + ez * ez - tr3 * tr3 * (R(1) / R(3)));
   } else {
     const R mu2 = R(2) * P.mu;
     sxx = g * (P.lam * tr + mu2 * exx);

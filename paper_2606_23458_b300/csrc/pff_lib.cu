@@ -268,7 +268,7 @@ struct pff_mesh {
   double hmin = 0.0;
   bool has_mat = false;
   pff_material mat{};
-  double lam = 0, mu = 0, K = 0;
+  double lam = 0, mu = 0, K = 0, cz = 0;
   // workspace
   double *x = nullptr, *r = nullptr, *b = nullptr, *part = nullptr, *energy = nullptr, *wext = nullptr;
   void *pz = nullptr, *q = nullptr, *dinv = nullptr;
@@ -879,6 +879,7 @@ static Params<R> base_params(pff_mesh *m, const pff_options &o) {
   P.minv = (const R *)m->minv;
   const pff_material &mt = m->mat;
   P.lam = (R)m->lam;
+  P.cz = (R)m->cz;
   P.mu = (R)m->mu;
   P.K = (R)m->K;
   P.eta = (R)mt.eta;
@@ -1686,17 +1687,20 @@ extern "C" {
 const char *pff_last_error(void) { return g_err.c_str(); }
 
 // Pre-simulation check of the damage subcycling factor (Sec. 2.4): c_p from
-// the plane-strain Lame constants (the speed behind the CFL step), c_s, and
+// the plane model's Lame constants (the speed behind the CFL step), c_s, and
 // the Rayleigh speed c_R = c_s sqrt(eta) with eta the root in (0, 1) of the
 // Rayleigh cubic eta^3 - 8 eta^2 + (24 - 16 k^2) eta - 16 (1 - k^2) = 0,
 // k = c_s / c_p (the squared Rayleigh equation with the eta = 0 root
 // divided out; negative at 0, +1 at 1, one root between), by Newton's
 // method from eta = 1.
 pff_status pff_subcycling_limit(const pff_material *mat, double *ratio, int32_t *n_max) {
-  if (!mat || !(mat->E > 0) || !(mat->rho > 0) || !(mat->nu > -1.0 && mat->nu < 0.5))
+  if (!mat || !(mat->E > 0) || !(mat->rho > 0) || !(mat->nu > -1.0 && mat->nu < 0.5) ||
+      (mat->plane != PFF_PLANE_STRAIN && mat->plane != PFF_PLANE_STRESS))
     return fail(PFF_ERR_ARG, "bad material");
   const double E = mat->E, nu = mat->nu;
-  const double mu = E / (2.0 * (1.0 + nu)), lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+  const double mu = E / (2.0 * (1.0 + nu));
+  const double lam = mat->plane == PFF_PLANE_STRESS ? E * nu / (1.0 - nu * nu)
+                                                    : E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
   const double cp = std::sqrt((lam + 2.0 * mu) / mat->rho), cs = std::sqrt(mu / mat->rho);
   const double k2 = (cs / cp) * (cs / cp);
   double eta = 1.0;
@@ -1853,11 +1857,17 @@ pff_status pff_mesh_set_material(pff_mesh *m, const pff_material *mat, double cf
     return fail(PFF_ERR_ARG, "invalid material constants");
   if (mat->model != PFF_AT1 && mat->model != PFF_AT2) return fail(PFF_ERR_ARG, "model must be AT1 or AT2");
   if (mat->split < 0 || mat->split > 2) return fail(PFF_ERR_ARG, "unknown split");
-  if (mat->plane != PFF_PLANE_STRAIN) return fail(PFF_ERR_ARG, "only plane strain is supported");
+  if (mat->plane != PFF_PLANE_STRAIN && mat->plane != PFF_PLANE_STRESS)
+    return fail(PFF_ERR_ARG, "plane must be PFF_PLANE_STRAIN or PFF_PLANE_STRESS");
   m->mat = *mat;
-  m->lam = mat->E * mat->nu / ((1.0 + mat->nu) * (1.0 - 2.0 * mat->nu));
+  // Sec. 2.1, plane assumptions: the plane model's first Lame parameter, the
+  // 3-D bulk modulus, and the out-of-plane strain factor of plane stress
+  const bool ps = mat->plane == PFF_PLANE_STRESS;
+  m->lam = ps ? mat->E * mat->nu / (1.0 - mat->nu * mat->nu)
+              : mat->E * mat->nu / ((1.0 + mat->nu) * (1.0 - 2.0 * mat->nu));
   m->mu = mat->E / (2.0 * (1.0 + mat->nu));
   m->K = mat->E / (3.0 * (1.0 - 2.0 * mat->nu));
+  m->cz = ps ? mat->nu / (1.0 - mat->nu) : 0.0;
   const int blk = 256;
   if (m->prec == PFF_FP64)
     k_lumped<double><<<grid_for(m->N, blk), blk>>>(m->ptr, m->ent, m->area_d, m->N, mat->rho, (double *)m->minv);

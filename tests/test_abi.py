@@ -65,11 +65,12 @@ def test_subcycling_limit_matches_oracle(orc):
     """pff_subcycling_limit (host-only) against the oracle's check."""
     import paper_2606_23458_b300 as pff
     import pff_synth as S
-    for nu in (0.1, 0.2, 0.25, 0.35, 0.45):
-        mat = S.material(1e-3, nu=nu)
-        r, n = pff.subcycling_limit(mat)
-        ro, no = orc.subcycling_limit(mat)
-        assert abs(r - ro) <= 1e-10 * ro and n == no, (nu, r, ro)
+    for plane in ("strain", "stress"):
+        for nu in (0.1, 0.2, 0.25, 0.35, 0.45):
+            mat = S.material(1e-3, nu=nu, plane=plane)
+            r, n = pff.subcycling_limit(mat)
+            ro, no = orc.subcycling_limit(mat)
+            assert abs(r - ro) <= 1e-10 * ro and n == no, (plane, nu, r, ro)
     bad = pff.pff_material(0.0, 0.2, 2450.0, 3.0, 1e-3, 1e-7, 2, 0, 0, 0)
     assert pff._lib.pff_subcycling_limit(C.byref(bad), None, None) == 1
 

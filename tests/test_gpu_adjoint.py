@@ -107,3 +107,22 @@ def test_autograd_function(pff):
     _, g, _ = _gpu_grad(pff, p, mat, 2.0, nsteps, dstar.cpu().numpy(), "fp64", 5, 1e-8)
     assert abs(gc.grad.item() - g) <= 1e-12 * abs(g)
     assert gc.grad.item() < 0  # Gc below the target: increasing it reduces the misfit
+
+
+def test_plane_stress_adjoint_matches_oracle(orc, pff):
+    """dL/dGc in plane stress with the volumetric-deviatoric split (its
+    tangent carries the out-of-plane strain) against the oracle's discrete
+    adjoint, FP64."""
+    p, mat = _problem()
+    mat = dict(mat, split="amor", plane="stress")
+    om = orc.Mesh.from_plate(p)
+    dt = om.stable_dt(mat, 0.5)
+    nsteps = 40
+    st = om.new_state()
+    om.run(dict(mat, Gc=3.0), st, nsteps, dt, tol=1e-13)
+    dstar = st["d"].copy()
+    L, g, status = om.adjoint_gc(dict(mat, Gc=2.0), nsteps, dt, dstar, tol=1e-13)
+    gL, gg, _ = _gpu_grad(pff, p, mat, 2.0, nsteps, dstar, "fp64", 0, 1e-13)
+    assert abs(gL - L) <= 1e-10 * L
+    assert abs(gg - g) <= 1e-7 * abs(g), (gg, g)
+

@@ -201,3 +201,54 @@ def test_subcycled_fp32_run_in_one_call(orc, pff):
     eu = rel_l2(to_np(a["u"]), ost["u"])
     ed = np.abs(to_np(a["d"]) - ost["d"]).max()
     assert eu <= 1e-4 and ed <= 1e-3, (eu, ed)
+
+
+@pytest.mark.parametrize("split", ["amor", "spectral", "iso"])
+def test_plane_stress_per_step_parity(orc, pff, split):
+    """Plane stress (Sec. 2.1 plane assumptions): FP64 fields within 1e-10
+    of the oracle after each of 60 steps (oracle forced to the GPU's
+    iteration counts)."""
+    import torch
+    c = S.config("plate_100x40", split=split)
+    mat = dict(c["material"], plane="stress")
+    om = orc.Mesh.from_plate(c["mesh"])
+    gm = pff.Mesh.from_plate(c["mesh"], precision="fp64")
+    dt = gm.set_material(mat, c["cfl"])
+    assert abs(dt - om.stable_dt(mat, c["cfl"])) <= 1e-15 * dt
+    nsteps = 60
+    gst = gm.new_state()
+    ost = om.new_state()
+    log = torch.zeros(nsteps, 2, dtype=torch.int32, device="cuda")
+    worst = 0.0
+    for n in range(nsteps):
+        gm.run(gst, 1, step0=n, iters_log=log[n:n + 1])
+        torch.cuda.synchronize()
+        om.run(mat, ost, 1, dt, n0=n, forced=[int(log[n, 0])])
+        for k in ("u", "v", "a"):
+            worst = max(worst, rel_l2(to_np(gst[k]), ost[k]))
+        worst = max(worst, max_rel(to_np(gst["d"]), ost["d"], 1e-3))
+        worst = max(worst, rel_l2(to_np(gst["H"]), ost["H"]))
+        assert worst <= 1e-10, (n, worst)
+    assert np.abs(to_np(gst["d"])).max() > 0  # the damage field moved
+    # the plane matters: a plane-strain run differs
+    om2 = orc.Mesh.from_plate(c["mesh"])
+    st2 = om2.new_state()
+    om2.run(c["material"], st2, nsteps, om2.stable_dt(c["material"], c["cfl"]))
+    assert rel_l2(ost["u"], st2["u"]) > 1e-3
+
+
+def test_plane_stress_fp32_vs_fp64_oracle(orc, pff):
+    import torch
+    c = S.config("plate_100x40", split="amor")
+    mat = dict(c["material"], plane="stress")
+    om = orc.Mesh.from_plate(c["mesh"])
+    gm = pff.Mesh.from_plate(c["mesh"], precision="fp32")
+    dt = gm.set_material(mat, c["cfl"])
+    gst = gm.new_state()
+    gm.run(gst, 200)
+    torch.cuda.synchronize()
+    ost = om.new_state()
+    om.run(mat, ost, 200, dt)
+    eu = rel_l2(to_np(gst["u"]), ost["u"])
+    ed = np.abs(to_np(gst["d"]) - ost["d"]).max()
+    assert eu <= 1e-4 and ed <= 1e-3, (eu, ed)
