@@ -79,10 +79,12 @@ def _L():
         _lib.or_energies.argtypes = [P, P, P, P, P, P, P]
         _lib.or_run.argtypes = [P, P, P, C.c_int64, C.c_int64, P, P, P, P, P, P, P, P, P, P]
         _lib.or_run.restype = C.c_int
-        _lib.or_adjoint_gc.argtypes = [P, P, P, C.c_int64, P, P, P, P, P, P, P, P]
+        _lib.or_adjoint_gc.argtypes = [P, P, P, C.c_int64, P, P, P, P, P, P, P, P, P]
         _lib.or_adjoint_gc.restype = C.c_int
         _lib.or_elem_adjoint.argtypes = [P, P, P, P, P, P, P, P]
-        _lib.or_damage_adjoint_terms.argtypes = [P, P, P, P, P, P]
+        _lib.or_damage_adjoint_terms.argtypes = [P, P, P, P, P, P, P]
+        _lib.or_mesh_set_gc_field.argtypes = [P, P]
+        _lib.or_mesh_set_gc_field.restype = None
     return _lib
 
 
@@ -273,9 +275,16 @@ class Mesh:
                          _p(state["H"]), _p(it), _p(rel), _p(en), _p(fz), C.byref(Wc))
         return dict(status=st, iters=it, relres=rel, energies=en, W=Wc.value)
 
+    def set_gc_field(self, gc):
+        """Per-element toughness Gc_e (Ne values), or None for the material's
+        uniform Gc."""
+        self._gcf = None if gc is None else _f64(gc, (self.Ne,))
+        _L().or_mesh_set_gc_field(self._h, None if gc is None else _p(self._gcf))
+
     def adjoint_gc(self, mat, nsteps, dt, dstar, state0=None, t_ramp=0.05e-6,
-                   tol=1e-8, max_it=10000):
-        """(loss, dL/dGc, status) for L = mean((d_T - dstar)^2)."""
+                   tol=1e-8, max_it=10000, field=False):
+        """(loss, dL/dGc, status) for L = mean((d_T - dstar)^2); with
+        field=True also dL/dGc_e per element (Ne) as a fourth value."""
         m = material(mat)
         o = _RunOpts(float(dt), float(t_ramp), float(tol), int(max_it), 50, 1, 0, 1)
         s = state0 if state0 is not None else self.new_state()
@@ -283,9 +292,11 @@ class Mesh:
         a0 = _f64(s["a"], (self.N, 2)); d0 = _f64(s["d"], (self.N,))
         H0 = _f64(s["H"], (self.Ne,)); ds = _f64(dstar, (self.N,))
         L = C.c_double(); g = C.c_double()
+        ge = np.zeros(self.Ne) if field else None
         st = _L().or_adjoint_gc(self._h, C.byref(m), C.byref(o), int(nsteps), _p(u0), _p(v0),
-                                _p(a0), _p(d0), _p(H0), _p(ds), C.byref(L), C.byref(g))
-        return L.value, g.value, st
+                                _p(a0), _p(d0), _p(H0), _p(ds), C.byref(L), C.byref(g),
+                                None if ge is None else _p(ge))
+        return (L.value, g.value, st, ge) if field else (L.value, g.value, st)
 
     def elem_adjoint(self, mat, u, d, fbar, psibar=None):
         m = material(mat)
@@ -299,5 +310,5 @@ class Mesh:
         m = material(mat)
         lam = _f64(lam, (self.N,)); xt = _f64(xt, (self.N,))
         gc = C.c_double(0.0); Hb = np.zeros(self.Ne)
-        _L().or_damage_adjoint_terms(self._h, C.byref(m), _p(lam), _p(xt), C.byref(gc), _p(Hb))
+        _L().or_damage_adjoint_terms(self._h, C.byref(m), _p(lam), _p(xt), C.byref(gc), _p(Hb), None)
         return gc.value, Hb

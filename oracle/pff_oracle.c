@@ -60,6 +60,8 @@ typedef struct {
   double *grad;         /* Ne x 3 x 2: (dphi_a/dx, dphi_a/dy) */
   double *fext;         /* N x 2 nodal traction load at full scale */
   double hmin;          /* min over elements of the incircle diameter 4A/P */
+  double *gcf;          /* Ne: per-element toughness Gc_e (Secs. 4.2, 7: the
+                           field-valued inverse), NULL: the material's Gc */
 } or_mesh;
 
 /* ------------------------------------------------------------------ mesh */
@@ -125,7 +127,22 @@ or_mesh *or_mesh_create(int64_t N, const double *xy, int64_t Ne,
 void or_mesh_free(or_mesh *m) {
   if (!m) return;
   free(m->x); free(m->y); free(m->t); free(m->notch); free(m->area);
-  free(m->grad); free(m->fext); free(m);
+  free(m->grad); free(m->fext); free(m->gcf); free(m);
+}
+
+/* Per-element toughness field (gc: Ne values, copied; NULL restores the
+ * material's uniform Gc). */
+void or_mesh_set_gc_field(or_mesh *m, const double *gc) {
+  free(m->gcf);
+  m->gcf = NULL;
+  if (!gc) return;
+  m->gcf = (double *)malloc(m->Ne * sizeof(double));
+  memcpy(m->gcf, gc, m->Ne * sizeof(double));
+}
+
+/* Toughness of element e. */
+static double elem_gc(const or_mesh *m, const or_material *mt, int64_t e) {
+  return m->gcf ? m->gcf[e] : mt->Gc;
 }
 
 void or_mesh_geometry(const or_mesh *m, double *area, double *grad,
@@ -420,19 +437,20 @@ double or_ramp(double t, double tr) {
 
 /* -------------------------------------------------------------- damage */
 
-/* Coefficients of the damage operator A = sum_e [kappa K^e + c_e M^e] and
- * right-hand side b = sum_e w_e A_e / 3 per node:
+/* Coefficients of the damage operator A = sum_e [kappa_e K^e + c_e M^e] and
+ * right-hand side b = sum_e w_e A_e / 3 per node, with the element's Gc:
  *   AT2, Eq. (damage_pde_at2): kappa = Gc l0, c_e = Gc/l0 + 2H_e, w_e = 2H_e;
  *   AT1, Eq. (damage_pde_at1): kappa = 3/4 Gc l0, c_e = 2H_e,
  *                              w_e = 2H_e - 3Gc/(8 l0). */
-static double dmg_kappa(const or_material *mt) {
-  return mt->model == OR_AT1 ? 0.75 * mt->Gc * mt->l0 : mt->Gc * mt->l0;
+static double dmg_kappa(const or_mesh *m, const or_material *mt, int64_t e) {
+  const double gc = elem_gc(m, mt, e);
+  return mt->model == OR_AT1 ? 0.75 * gc * mt->l0 : gc * mt->l0;
 }
-static double dmg_c(const or_material *mt, double H) {
-  return mt->model == OR_AT1 ? 2.0 * H : mt->Gc / mt->l0 + 2.0 * H;
+static double dmg_c(const or_mesh *m, const or_material *mt, int64_t e, double H) {
+  return mt->model == OR_AT1 ? 2.0 * H : elem_gc(m, mt, e) / mt->l0 + 2.0 * H;
 }
-static double dmg_w(const or_material *mt, double H) {
-  return mt->model == OR_AT1 ? 2.0 * H - 3.0 * mt->Gc / (8.0 * mt->l0) : 2.0 * H;
+static double dmg_w(const or_mesh *m, const or_material *mt, int64_t e, double H) {
+  return mt->model == OR_AT1 ? 2.0 * H - 3.0 * elem_gc(m, mt, e) / (8.0 * mt->l0) : 2.0 * H;
 }
 
 /* q = A p over all nodes (no Dirichlet handling), element order:
@@ -441,10 +459,10 @@ static double dmg_w(const or_material *mt, double H) {
 void or_damage_apply(const or_mesh *m, const or_material *mt, const double *H,
                      const double *p, double *q) {
   memset(q, 0, m->N * sizeof(double));
-  double kap = dmg_kappa(mt);
   for (int64_t e = 0; e < m->Ne; ++e) {
     const double *g = m->grad + 6 * e;
-    double A = m->area[e], c = dmg_c(mt, H[e]);
+    double kap = dmg_kappa(m, mt, e);
+    double A = m->area[e], c = dmg_c(m, mt, e, H[e]);
     for (int a = 0; a < 3; ++a) {
       double s = 0.0;
       for (int b = 0; b < 3; ++b) {
@@ -461,10 +479,10 @@ void or_damage_rhs(const or_mesh *m, const or_material *mt, const double *H,
                    double *b, double *diag) {
   memset(b, 0, m->N * sizeof(double));
   memset(diag, 0, m->N * sizeof(double));
-  double kap = dmg_kappa(mt);
   for (int64_t e = 0; e < m->Ne; ++e) {
     const double *g = m->grad + 6 * e;
-    double A = m->area[e], c = dmg_c(mt, H[e]), w = dmg_w(mt, H[e]);
+    double kap = dmg_kappa(m, mt, e);
+    double A = m->area[e], c = dmg_c(m, mt, e, H[e]), w = dmg_w(m, mt, e, H[e]);
     for (int a = 0; a < 3; ++a) {
       int32_t n = m->t[3 * e + a];
       b[n] += w * A / 3.0;
@@ -679,13 +697,14 @@ void or_energies(const or_mesh *m, const or_material *mt, const double *mass,
       gy += g[2 * a + 1] * de[a];
     }
     double grad2 = gx * gx + gy * gy;
+    const double gc = elem_gc(m, mt, e);
     if (mt->model == OR_AT1) {
-      Efr += mt->Gc * 0.375 * (A / 3.0 * (de[0] + de[1] + de[2]) / mt->l0 + mt->l0 * A * grad2);
+      Efr += gc * 0.375 * (A / 3.0 * (de[0] + de[1] + de[2]) / mt->l0 + mt->l0 * A * grad2);
     } else {
       double dMd = 0.0;
       for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b) dMd += de[a] * de[b] * A * (a == b ? 2.0 : 1.0) / 12.0;
-      Efr += mt->Gc * (dMd / (2.0 * mt->l0) + 0.5 * mt->l0 * A * grad2);
+      Efr += gc * (dMd / (2.0 * mt->l0) + 0.5 * mt->l0 * A * grad2);
     }
   }
   for (int64_t i = 0; i < m->N; ++i)
@@ -845,12 +864,14 @@ static void adjoint_solve(const or_mesh *m, const or_material *mt, const double 
 }
 
 /* Parameter and history terms of the implicit damage adjoint (AT2):
- *   dL/dGc  += -lam^T (l0 K + M / l0) xt          (Eq. implicit_gc_l0_element_term)
+ *   dL/dGc_e += -lam_e^T (l0 K^e + M^e / l0) xt_e (Eq. implicit_gc_l0_element_term,
+ *               per element; their sum is dL/dGc for a uniform Gc)
  *   Hbar_e  += (2 A_e / 3) sum_a lam_a - 2 lam_e^T M^e xt_e
- * with xt = the unclamped solution on free nodes and 1 on the notch. */
+ * with xt = the unclamped solution on free nodes and 1 on the notch.
+ * gce_bar (Ne, nullable) accumulates the per-element terms. */
 void or_damage_adjoint_terms(const or_mesh *m, const or_material *mt,
                              const double *lam, const double *xt,
-                             double *gc_bar, double *Hbar) {
+                             double *gc_bar, double *Hbar, double *gce_bar) {
   double acc = 0.0;
   for (int64_t e = 0; e < m->Ne; ++e) {
     const double *g = m->grad + 6 * e;
@@ -867,7 +888,9 @@ void or_damage_adjoint_terms(const or_mesh *m, const or_material *mt,
         sM += la * Mab * xb;
       }
     }
-    acc += -(mt->l0 * sK + sM / mt->l0);
+    const double te = -(mt->l0 * sK + sM / mt->l0);
+    acc += te;
+    if (gce_bar) gce_bar[e] += te;
     Hbar[e] += 2.0 * A / 3.0 * slam - 2.0 * sM;
   }
   *gc_bar += acc;
@@ -914,8 +937,10 @@ void or_elem_adjoint(const or_mesh *m, const or_material *mt, const double *u,
 int or_adjoint_gc(const or_mesh *m, const or_material *mt, const or_run_opts *o,
                   int64_t nsteps, const double *u0, const double *v0,
                   const double *a0, const double *d0, const double *H0,
-                  const double *dstar, double *loss, double *dL_dGc) {
+                  const double *dstar, double *loss, double *dL_dGc,
+                  double *dL_dGc_field) {
   int64_t N = m->N, Ne = m->Ne, T = nsteps;
+  if (dL_dGc_field) memset(dL_dGc_field, 0, Ne * sizeof(double));
   double *U = malloc((T + 1) * 2 * N * sizeof(double));
   double *D = malloc((T + 1) * N * sizeof(double));
   double *HS = malloc((T + 1) * Ne * sizeof(double));
@@ -972,7 +997,7 @@ int or_adjoint_gc(const or_mesh *m, const or_material *mt, const or_run_opts *o,
     }
     adjoint_solve(m, mt, H1, xbar, lam);
     for (int64_t i = 0; i < N; ++i) xt[i] = m->notch[i] ? 1.0 : x[i];
-    or_damage_adjoint_terms(m, mt, lam, xt, &gc, Hb);
+    or_damage_adjoint_terms(m, mt, lam, xt, &gc, Hb, dL_dGc_field);
     /* corrector and acceleration: fbar = -minv (abar + dt/2 vbar) */
     for (int64_t i = 0; i < 2 * N; ++i)
       fbar[i] = -minv[i / 2] * (ab[i] + 0.5 * o->dt * vb[i]);
