@@ -152,6 +152,15 @@ pff_status pff_mesh_create(int64_t N, const double *xy, int64_t Ne,
 
 void pff_mesh_destroy(pff_mesh *mesh);
 
+/* Toughness field (Secs. 4.2 and 7: the field-valued inverse): per-element
+ * Gc_e (host, Ne doubles, each > 0 and finite; NULL restores the material's
+ * uniform Gc) in place of Gc in the damage operator, its right-hand side and
+ * the fracture energy.  Call after pff_mesh_set_material; the field is kept
+ * as Gc_e / Gc and follows later material changes.  While a field is set
+ * the shared-memory staged CG loops are not used.  Copies synchronously.
+ * PFF_ERR_ARG: null mesh, no material yet, a non-positive value. */
+pff_status pff_mesh_set_gc_field(pff_mesh *mesh, const double *gc);
+
 /* Sets the material: the plane model's Lame constants (Sec. 2.1), lumped mass
  * m_i = rho sum A_e / 3 and the stable step dt = cfl * h_min / c_p with
  * c_p = sqrt((lambda + 2 mu) / rho) (velocity-Verlet paragraph, Sec. 2.3).
@@ -233,6 +242,14 @@ pff_status pff_run_ckpt(pff_mesh *mesh, const pff_state *state, int64_t step0,
                         pff_ckpt *ckpt, int32_t *iters_log, pff_stream stream);
 pff_status pff_backward(pff_mesh *mesh, pff_ckpt *ckpt, const void *dL_dd,
                         const pff_options *opt, double *dL_dGc, pff_stream stream);
+
+/* pff_backward that also returns dL/dGc_e per element (device, Ne doubles,
+ * overwritten): the per-element terms of Eq. implicit_gc_l0_element_term
+ * summed over the steps, the gradient of a toughness field (see
+ * pff_mesh_set_gc_field); their sum is *dL_dGc. */
+pff_status pff_backward_field(pff_mesh *mesh, pff_ckpt *ckpt, const void *dL_dd,
+                              const pff_options *opt, double *dL_dGc, double *dL_dGc_field,
+                              pff_stream stream);
 
 /* Batches: many independent plates (uneven sizes, Gc, l0, loads and time
  * steps) advanced together, one CUDA graph launch per step for all plates,

@@ -100,6 +100,8 @@ _sig = {
     "pff_run_ckpt": [_P, C.POINTER(pff_state), C.c_int64, C.c_int64, C.c_double,
                      C.POINTER(pff_options), _P, _P, _P],
     "pff_backward": [_P, _P, _P, C.POINTER(pff_options), C.POINTER(C.c_double), _P],
+    "pff_backward_field": [_P, _P, _P, C.POINTER(pff_options), C.POINTER(C.c_double), _P, _P],
+    "pff_mesh_set_gc_field": [_P, _P],
     "pff_batch_create": [C.c_int32, _P, C.c_int32, C.c_double, C.POINTER(C.c_void_p)],
     "pff_batch_destroy": [_P],
     "pff_batch_size": [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
@@ -410,6 +412,27 @@ class Mesh:
         _check(_lib.pff_backward(self._h, ckpt._h, _dptr(dL_dd), C.byref(o), C.byref(g),
                                  _stream(stream)))
         return g.value
+
+    def backward_field(self, ckpt, dL_dd, opts=None, stream=None):
+        """(dL/dGc, dL/dGc_e per element as a float64 device tensor)."""
+        import torch
+        assert dL_dd.is_cuda and dL_dd.dtype == self.dtype and dL_dd.is_contiguous()
+        o = opts or options()
+        g = C.c_double()
+        ge = torch.empty(self.Ne, dtype=torch.float64, device=dL_dd.device)
+        _check(_lib.pff_backward_field(self._h, ckpt._h, _dptr(dL_dd), C.byref(o), C.byref(g),
+                                       _dptr(ge), _stream(stream)))
+        return g.value, ge
+
+    def set_gc_field(self, gc):
+        """Per-element toughness Gc_e (array of Ne, host), or None for the
+        material's uniform Gc."""
+        if gc is None:
+            _check(_lib.pff_mesh_set_gc_field(self._h, None))
+            return
+        a = _np(gc, np.float64)
+        assert a.shape == (self.Ne,)
+        _check(_lib.pff_mesh_set_gc_field(self._h, _hp(a)))
 
     def sync_status(self, stream=None):
         return _lib.pff_sync_status(self._h, _stream(stream))

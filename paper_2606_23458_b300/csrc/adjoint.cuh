@@ -42,6 +42,7 @@ template <typename R> struct AdjParams {
   R *Hb_acc;         // = Hb_in buffer, receives the damage terms
   R *Hb_out;         // dL/dH_n
   double *gc;        // running dL/dGc
+  double *gce;       // running dL/dGc_e per element (nullable)
   int *astat;        // worst status of the adjoint solves (atomicMax)
 };
 
@@ -209,8 +210,9 @@ __global__ void __launch_bounds__(256) k_adj_rhs(AdjParams<R> A) {
       R Ar;
       R4 G;
       load_elem(P, e, t, Ar, G);
-      const R c = P.cbase + R(2) * P.Hr[e];
-      const R kA = P.kappa * Ar, mA = c * Ar * (R(1) / R(12));
+      const R sg = gc_scale(P, e);
+      const R c = P.cbase * sg + R(2) * P.Hr[e];
+      const R kA = (P.kappa * sg) * Ar, mA = c * Ar * (R(1) / R(12));
       R gx, gy;
       slot_grad<R>(G, a, gx, gy);
       dg = radd(dg, kA * (gx * gx + gy * gy) + R(2) * mA);
@@ -256,7 +258,8 @@ __global__ void __launch_bounds__(256) k_adj_rhs(AdjParams<R> A) {
 
 // Parameter and history terms of the damage adjoint, one element at a time
 // (AT2; Eq. implicit_gc_l0_element_term and the H-derivative of A and b):
-//   dL/dGc += -lam_e^T (l0 K^e + M^e / l0) xt_e,
+//   dL/dGc += -lam_e^T (l0 K^e + M^e / l0) xt_e (also per element into gce:
+//   the derivative with respect to Gc_e of a toughness field),
 //   Hbar_e += (2 A_e / 3) sum_a lam_a - 2 lam_e^T M^e xt_e,
 // with xt = x_{n+1} on free nodes and 1 on the notch, M^e = A_e (1+delta)/12.
 template <typename R>
@@ -287,6 +290,7 @@ __global__ void __launch_bounds__(256) k_adj_dmg_terms(AdjParams<R> A) {
     const R sl = la0 + la1 + la2, sx = x0 + x1 + x2;
     const R lMx = Ar * (R(1) / R(12)) * (la0 * x0 + la1 * x1 + la2 * x2 + sl * sx);
     vals[0] = AC::add(vals[0], AC::prod(R(-1), l0 * lKx + il0 * lMx));
+    if (A.gce) A.gce[e] -= (double)(l0 * lKx + il0 * lMx);
     A.Hb_acc[e] = A.Hb_acc[e] + R(2) * Ar * (R(1) / R(3)) * sl - R(2) * lMx;
   }
   __shared__ double tot[1];

@@ -119,6 +119,8 @@ template <typename R> struct Params {
   R lam, mu, K, eta, cz;
   int32_t split, model;
   R kappa;      // damage diffusion coefficient (Gc l0 or 3/4 Gc l0)
+  const R *gcs; // per-element toughness field as Gc_e / Gc (nullable: uniform);
+                // kappa, cbase and wbase are linear in Gc and scale with it
   R cbase;      // reaction: c_e = cbase + 2 H_e
   R wbase;      // load:     w_e = wbase + 2 H_e
   R rscale;     // power of two applied to residual-like vectors in the dots
@@ -299,6 +301,11 @@ template <typename R> __device__ __forceinline__ R sc_beta(const SolveScalars *S
 }
 
 template <typename R> __device__ __forceinline__ R rpos(R x) { return x > R(0) ? x : R(0); }
+
+// Element e's toughness relative to the material's (1 without a field).
+template <typename R> __device__ __forceinline__ R gc_scale(const Params<R> &P, int e) {
+  return P.gcs ? P.gcs[e] : R(1);
+}
 template <typename R> __device__ __forceinline__ R rneg(R x) { return x < R(0) ? x : R(0); }
 
 // Accumulation a + b that the compiler may not contract into an FMA with
@@ -633,12 +640,13 @@ __device__ __forceinline__ typename Params<R>::R4 rhs_entry(const Params<R> &P, 
   R4 G;
   load_elem(P, e, t, A, G);
   const R h = P.Hr[e];
-  const R c = P.cbase + R(2) * h, w = P.wbase + R(2) * h;
+  const R sg = gc_scale(P, e);
+  const R c = P.cbase * sg + R(2) * h, w = P.wbase * sg + R(2) * h;
   const bool n0 = P.flags[t.x] & kNotch, n1 = P.flags[t.y] & kNotch, n2 = P.flags[t.z] & kNotch;
   const R x0 = n0 ? R(1) : P.dprev[t.x];
   const R x1 = n1 ? R(1) : P.dprev[t.y];
   const R x2 = n2 ? R(1) : P.dprev[t.z];
-  const R kA = P.kappa * A, mA = c * A * (R(1) / R(12));
+  const R kA = (P.kappa * sg) * A, mA = c * A * (R(1) / R(12));
   R gx, gy;
   slot_grad<R>(G, a, gx, gy);
   R4 o;
@@ -790,9 +798,9 @@ __device__ __forceinline__ R pnew(const Params<R> &P, int j, R beta) {
 // geometry and the history on every application.
 template <typename R>
 __device__ __forceinline__ R mv_entry_vals(const Params<R> &P, const int4 &t, R A, const typename Params<R>::R4 &G,
-                                           R h, int a, R beta, R pc) {
-  const R kA = P.kappa * A;
-  const R mA = (P.cbase + R(2) * h) * A * (R(1) / R(12));
+                                           R h, R sg, int a, R beta, R pc) {
+  const R kA = (P.kappa * sg) * A;
+  const R mA = (P.cbase * sg + R(2) * h) * A * (R(1) / R(12));
   // the entry's own node (slot a) is the row's node: its value is pc
   const R p0 = a == 0 ? pc : pnew(P, t.x, beta);
   const R p1 = a == 1 ? pc : pnew(P, t.y, beta);
@@ -808,7 +816,7 @@ __device__ __forceinline__ R mv_entry(const Params<R> &P, int en, R beta, R pc) 
   R A;
   R4 G;
   load_elem(P, e, t, A, G);
-  return mv_entry_vals<R>(P, t, A, G, P.Hr[e], a, beta, pc);
+  return mv_entry_vals<R>(P, t, A, G, P.Hr[e], gc_scale(P, e), a, beta, pc);
 }
 
 // Rows n0 + threadIdx.x, ... < n1 of q = A p_new from the element records
@@ -834,7 +842,7 @@ __device__ __forceinline__ void matvec_rows_staged(const Params<float> &P, float
             const int sidx = (int)(sl[u] >> 2);
             const float4 r0 = srec[2 * sidx], r1 = srec[2 * sidx + 1];
             const int4 t = make_int4(__float_as_int(r0.x), __float_as_int(r0.y), __float_as_int(r0.z), 0);
-            c[u] = mv_entry_vals<float>(P, t, r0.w, r1, sh[sidx], (int)(sl[u] & 3u), beta, pc);
+            c[u] = mv_entry_vals<float>(P, t, r0.w, r1, sh[sidx], 1.f, (int)(sl[u] & 3u), beta, pc);
           }
 #pragma unroll
         for (int u = 0; u < U; ++u)
@@ -1440,9 +1448,9 @@ __device__ __forceinline__ void fused_rows(const Params<float> &P, float al, flo
         float A;
         float4 G;
         load_elem(P, e, t, A, G);
-        const float h = P.Hr[e];
-        const float kA = P.kappa * A;
-        const float mA = (P.cbase + 2.f * h) * A * (1.f / 12.f);
+        const float h = P.Hr[e], sg = gc_scale(P, e);
+        const float kA = (P.kappa * sg) * A;
+        const float mA = (P.cbase * sg + 2.f * h) * A * (1.f / 12.f);
         const float u0 = a == 0 ? un : cg_unew(vin[t.x], al, be);
         const float u1 = a == 1 ? un : cg_unew(vin[t.y], al, be);
         const float u2 = a == 2 ? un : cg_unew(vin[t.z], al, be);
@@ -1754,8 +1762,9 @@ __global__ void __launch_bounds__(256) k_at1_restart(Params<R> P) {
       R A;
       R4 G;
       load_elem(P, e, t, A, G);
-      const R kA = P.kappa * A;
-      const R mA = (P.cbase + R(2) * P.Hr[e]) * A * (R(1) / R(12));
+      const R sg = gc_scale(P, e);
+      const R kA = (P.kappa * sg) * A;
+      const R mA = (P.cbase * sg + R(2) * P.Hr[e]) * A * (R(1) / R(12));
       cx[k - k0] = elem_row<R>(G, a, kA, mA, P.x[t.x], P.x[t.y], P.x[t.z]);
     }
     __syncthreads();
@@ -1892,7 +1901,7 @@ __global__ void __launch_bounds__(256) k_energies(Params<R> P) {
     const R gdx = G.x * (d0 - d2) + G.z * (d1 - d2);
     const R gdy = G.y * (d0 - d2) + G.w * (d1 - d2);
     const R g2 = gdx * gdx + gdy * gdy;
-    const R Gc = (R)P.Gc, l0 = (R)P.l0;
+    const R Gc = (R)P.Gc * gc_scale(P, e), l0 = (R)P.l0;
     R dens;
     if (P.model == kAT1) {
       dens = Gc * R(0.375) * ((d0 + d1 + d2) * (R(1) / R(3)) / l0 + l0 * g2);

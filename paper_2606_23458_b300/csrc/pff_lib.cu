@@ -269,6 +269,9 @@ struct pff_mesh {
   bool has_mat = false;
   pff_material mat{};
   double lam = 0, mu = 0, K = 0, cz = 0;
+  // toughness field (Secs. 4.2, 7): Gc_e on the host, Gc_e / Gc on the device
+  std::vector<double> gc_field;
+  void *gcs = nullptr;
   // workspace
   double *x = nullptr, *r = nullptr, *b = nullptr, *part = nullptr, *energy = nullptr, *wext = nullptr;
   void *pz = nullptr, *q = nullptr, *dinv = nullptr;
@@ -327,7 +330,7 @@ static void mesh_free(pff_mesh *m) {
   free_graph(m->solve_g);
   free_graph(m->step_g);
   free_graph(m->mech_g);
-  void *ptrs[] = {m->st_cta, m->st_rng, m->st_nrng, m->st_lrec, m->st_slot, m->cgv, m->cgp,
+  void *ptrs[] = {m->gcs, m->st_cta, m->st_rng, m->st_nrng, m->st_lrec, m->st_slot, m->cgv, m->cgp,
                   m->ptr, m->ent, m->ell, m->rec, m->fext, m->minv, m->area_d, m->flags,
                   m->x, m->r, m->b, m->part, m->energy, m->wext, m->pz, m->q, m->dinv,
                   m->Hf, m->freef, m->ticket, m->sc, m->status_word, m->step_ctr, m->stab};
@@ -430,11 +433,12 @@ static inline int matvec_u(const pff_mesh *m) {
 
 // Grid of a family with U (0 = not available on this mesh / precision).
 static inline unsigned fam_grid(const pff_mesh *m, int fam, int U, bool fp32) {
+  const bool stage = fp32 && !m->gcs;  // the staged operator has no toughness field
   switch (fam) {
     case kFamPersistent: return m->pgrid[U];
-    case kFamStaged: return fp32 ? m->st_grid : 0u;
+    case kFamStaged: return stage ? m->st_grid : 0u;
     case kFamFused: return fp32 ? m->fgrid[U] : 0u;
-    case kFamFusedStaged: return fp32 && m->st_fused ? m->st_grid : 0u;
+    case kFamFusedStaged: return stage && m->st_fused ? m->st_grid : 0u;
     default: return 0u;
   }
 }
@@ -887,6 +891,7 @@ static Params<R> base_params(pff_mesh *m, const pff_options &o) {
   P.model = mt.model;
   const bool at1 = mt.model == PFF_AT1;
   P.kappa = (R)((at1 ? 0.75 : 1.0) * mt.Gc * mt.l0);
+  P.gcs = (const R *)m->gcs;
   P.cbase = (R)(at1 ? 0.0 : mt.Gc / mt.l0);
   P.wbase = (R)(at1 ? -3.0 * mt.Gc / (8.0 * mt.l0) : 0.0);
   // residual-like vectors scale like (Gc / l0) h^2; bring them near 1
@@ -1680,6 +1685,24 @@ static pff_status mesh_build_t(pff_mesh *m, const double *xy_d, const int32_t *t
 
 }  // namespace pff
 
+namespace pff {
+// Gc_e / Gc in the kernel precision (padded to whole groups of 4 elements).
+static pff_status upload_gc_field(pff_mesh *m) {
+  const int64_t Ne4 = (m->Ne + 3) / 4 * 4;
+  const size_t rs = m->prec == PFF_FP64 ? 8 : 4;
+  if (!m->gcs) CUDA_TRY(cudaMalloc(&m->gcs, Ne4 * rs));
+  std::vector<double> d(Ne4, 1.0);
+  for (int64_t e = 0; e < m->Ne; ++e) d[e] = m->gc_field[e] / m->mat.Gc;
+  if (rs == 8) {
+    CUDA_TRY(cudaMemcpy(m->gcs, d.data(), Ne4 * 8, cudaMemcpyHostToDevice));
+  } else {
+    std::vector<float> f(d.begin(), d.end());
+    CUDA_TRY(cudaMemcpy(m->gcs, f.data(), Ne4 * 4, cudaMemcpyHostToDevice));
+  }
+  return PFF_OK;
+}
+}  // namespace pff
+
 // ================================================================== C ABI
 
 extern "C" {
@@ -1878,6 +1901,7 @@ pff_status pff_mesh_set_material(pff_mesh *m, const pff_material *mat, double cf
   free_graph(m->solve_g);
   free_graph(m->step_g);
   m->has_mat = true;
+  if (!m->gc_field.empty()) PFF_TRY(upload_gc_field(m));  // relative to the new Gc
   const double cp = std::sqrt((m->lam + 2.0 * m->mu) / mat->rho);
   if (dt_out) *dt_out = cfl * m->hmin / cp;
   return PFF_OK;
@@ -2339,9 +2363,10 @@ static pff_status build_reverse_graph(pff_mesh *m, pff_ckpt *c, AdjParams<R> A, 
 
 template <typename R>
 static pff_status backward_t(pff_mesh *m, pff_ckpt *c, const void *dL_dd, const pff_options &o, double *dL_dGc,
-                             cudaStream_t s) {
+                             cudaStream_t s, double *dL_dGc_field = nullptr) {
   typedef typename V<R>::T2 R2;
   const size_t N = m->N, Np = m->N + 2, Ne = m->Ne, r = sizeof(R), r2 = 2 * sizeof(R);
+  if (dL_dGc_field) CUDA_TRY(cudaMemsetAsync(dL_dGc_field, 0, Ne * sizeof(double), s));
   // adjoint state at the final time: dL/dd_T given, everything else zero
   for (int q = 0; q < 2; ++q) {
     CUDA_TRY(cudaMemsetAsync(c->ub[q], 0, Np * r2, s));
@@ -2420,6 +2445,7 @@ static pff_status backward_t(pff_mesh *m, pff_ckpt *c, const void *dL_dd, const 
       A.Hb_acc = (R *)c->Hb[pin];
       A.Hb_out = (R *)c->Hb[1 - pin];
       A.gc = c->gc;
+      A.gce = dL_dGc_field;
       A.astat = c->kctr + 1;
       uint64_t tb, gb, lb;
       std::memcpy(&tb, &o.cg_tol, 8);
@@ -2428,7 +2454,8 @@ static pff_status backward_t(pff_mesh *m, pff_ckpt *c, const void *dL_dd, const 
       const CgPlan plan = cg_plan(m, o, kAT2, sizeof(R) == 4);
       std::vector<uint64_t> key = {tb, gb, lb, (uint64_t)m->var[KP_MATVEC], (uint64_t)o.cg_max_it,
                                    (uint64_t)m->mat.split, (uint64_t)plan.fam, (uint64_t)plan.U,
-                                   (uint64_t)o.cg_kernel};
+                                   (uint64_t)o.cg_kernel, (uint64_t)dL_dGc_field, (uint64_t)m->gcs,
+                                   (uint64_t)m->mat.plane};
       if (!c->rev_g[q].exec || c->rev_g[q].key != key)
         PFF_TRY(build_reverse_graph<R>(m, c, A, plan, c->rev_g[q], key));
     }
@@ -2506,6 +2533,36 @@ pff_status pff_backward(pff_mesh *m, pff_ckpt *c, const void *dL_dd, const pff_o
   cudaStream_t s = (cudaStream_t)stream;
   return m->prec == PFF_FP64 ? backward_t<double>(m, c, dL_dd, o, dL_dGc, s)
                              : backward_t<float>(m, c, dL_dd, o, dL_dGc, s);
+}
+
+pff_status pff_backward_field(pff_mesh *m, pff_ckpt *c, const void *dL_dd, const pff_options *opt,
+                              double *dL_dGc, double *dL_dGc_field, pff_stream stream) {
+  if (!m || !c || !dL_dd || !dL_dGc || !dL_dGc_field) return fail(PFF_ERR_ARG, "null argument");
+  if (c->m != m || !c->filled) return fail(PFF_ERR_ARG, "checkpoint not filled by pff_run_ckpt on this mesh");
+  if (m->mat.model != PFF_AT2) return fail(PFF_ERR_ARG, "pff_backward_field supports the AT2 model");
+  const pff_options o = defaults(opt);
+  cudaStream_t s = (cudaStream_t)stream;
+  return m->prec == PFF_FP64 ? backward_t<double>(m, c, dL_dd, o, dL_dGc, s, dL_dGc_field)
+                             : backward_t<float>(m, c, dL_dd, o, dL_dGc, s, dL_dGc_field);
+}
+
+pff_status pff_mesh_set_gc_field(pff_mesh *m, const double *gc) {
+  if (!m) return fail(PFF_ERR_ARG, "null mesh");
+  if (!m->has_mat) return fail(PFF_ERR_ARG, "set the material first");
+  if (!gc) {
+    if (m->gcs) cudaFree(m->gcs);
+    m->gcs = nullptr;
+    m->gc_field.clear();
+  } else {
+    for (int64_t e = 0; e < m->Ne; ++e)
+      if (!(gc[e] > 0.0) || !std::isfinite(gc[e])) return fail(PFF_ERR_ARG, "toughness must be positive and finite");
+    m->gc_field.assign(gc, gc + m->Ne);
+    PFF_TRY(upload_gc_field(m));
+  }
+  free_graph(m->solve_g);
+  free_graph(m->step_g);
+  free_graph(m->mech_g);
+  return PFF_OK;
 }
 
 }  // extern "C"
