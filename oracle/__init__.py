@@ -306,6 +306,67 @@ class Mesh:
         _L().or_elem_adjoint(self._h, C.byref(m), _p(u), _p(d), _p(fb), _p(pb), _p(ub), _p(db))
         return ub, db
 
+    def tangent_apply(self, mat, u, d, p):
+        """K_T(u) p: the directional derivative of the internal force at u
+        along p with d fixed (Eq. matrix_free_tangent_action); the Hessian of
+        sum A_e psi is symmetric, so the element adjoint applies it."""
+        return self.elem_adjoint(mat, u, d, p)[0]
+
+    def qs_run(self, mat, state, bc, nincr, du, tol=1e-8, newton_max=25, incr0=0):
+        """Quasi-static staggered loop (Sec. 3.5 and the matrix-free tangent
+        of Sec. 2.3): per load increment k, the prescribed displacement
+        U = (incr0 + k + 1) du is put on the loaded dofs, the mechanics
+        f_int(u; d) = 0 on the free dofs is solved by Newton with the
+        tangent K_T(u) (assembled here column by column from tangent_apply
+        and solved directly, a library step) until ||r_free|| <= tol
+        ||f_int||, then H = max(H, psi+(u)) and the damage solve as in a
+        dynamic step; the reaction is the sum of f_int,y over the loaded
+        nodes before the damage update.
+        bc: N flags, 1 = u_x fixed (0), 2 = u_y fixed (0), 4 = loaded node
+        (u_y = U; implies 2).  Returns dict(reaction (nincr,), newton
+        (nincr,), damage_iters (nincr,), status)."""
+        bc = np.asarray(bc, np.uint8)
+        fixed = np.zeros((self.N, 2), bool)
+        fixed[:, 0] = (bc & 1) != 0
+        fixed[:, 1] = (bc & 6) != 0
+        loaded = (bc & 4) != 0
+        free = np.flatnonzero(~fixed.ravel())
+        u = state["u"]; d = state["d"]; H = state["H"]
+        out = dict(reaction=np.zeros(nincr), newton=np.zeros(nincr, np.int32),
+                   damage_iters=np.zeros(nincr, np.int32), status=0)
+        for k in range(nincr):
+            U = (incr0 + k + 1) * du
+            u[fixed[:, 0], 0] = 0.0
+            u[fixed[:, 1], 1] = 0.0
+            u[loaded, 1] = U
+            for it in range(newton_max + 1):
+                f, psip = self.internal_force(mat, u, d)
+                r = -f.ravel()[free]
+                fn = np.linalg.norm(f)
+                if np.linalg.norm(r) <= tol * fn or fn == 0.0:
+                    break
+                if it == newton_max:
+                    out["status"] = 5
+                    break
+                Kt = np.zeros((free.size, free.size))
+                e = np.zeros(2 * self.N)
+                for j, dof in enumerate(free):
+                    e[dof] = 1.0
+                    Kt[:, j] = self.tangent_apply(mat, u, d, e.reshape(self.N, 2)).ravel()[free]
+                    e[dof] = 0.0
+                step = np.linalg.solve(Kt, r)
+                uf = u.ravel()
+                uf[free] += step
+                u[:] = uf.reshape(self.N, 2)
+            out["newton"][k] = it
+            out["reaction"][k] = f[loaded, 1].sum()
+            np.maximum(H, psip, out=H)
+            dn, info, rel, st, _ = self.damage_solve(mat, H, d, tol=tol)
+            d[:] = dn
+            out["damage_iters"][k] = info[0]
+            out["status"] = max(out["status"], st)
+        return out
+
     def damage_adjoint_terms(self, mat, lam, xt):
         m = material(mat)
         lam = _f64(lam, (self.N,)); xt = _f64(xt, (self.N,))
