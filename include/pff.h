@@ -152,6 +152,27 @@ pff_status pff_mesh_create(int64_t N, const double *xy, int64_t Ne,
 
 void pff_mesh_destroy(pff_mesh *mesh);
 
+/* Quasi-static staggered loop (Sec. 3.5, e.g. single-edge-notched
+ * tension), nincr load increments: increment k puts u_y = (incr0 + k + 1) du
+ * on the loaded nodes, then solves the mechanics f_int(u; d) = 0 on the free
+ * dofs by Newton iterations (at most newton_max; stop when
+ * |r_free| <= newton_tol |f_int|), each linear step K_T(u) du = -r by
+ * Jacobi-PCG to 0.1 newton_tol (FP32 floor 2^-22) with the matrix-free
+ * tangent action (Eq. matrix_free_tangent_action: the internal force's
+ * derivative along the trial vector through the split's tangent), then
+ * H = max(H, psi+(u)) and the damage solve of pff_damage_solve (opt's
+ * tolerance; d_prev = d).  state: u, d, H on the device, updated in place
+ * (v, a unused).  bc (host, N bytes): 1 = u_x fixed at 0, 2 = u_y fixed at
+ * 0, 4 = loaded (u_y = U).  reaction (host, nincr, nullable): sum of
+ * f_int,y over the loaded nodes at the converged u (per unit thickness).
+ * iters (host, nincr x 3, nullable): Newton steps, mechanics CG iterations,
+ * damage CG iterations.  Synchronises the stream.  PFF_ERR_NOT_CONVERGED if
+ * a Newton loop, mechanics CG or damage solve hit its cap (the increments
+ * still complete). */
+pff_status pff_qs_run(pff_mesh *mesh, const pff_state *state, const uint8_t *bc, int64_t incr0,
+                      int32_t nincr, double du, double newton_tol, int32_t newton_max,
+                      const pff_options *opt, double *reaction, int32_t *iters, pff_stream stream);
+
 /* Toughness field (Secs. 4.2 and 7: the field-valued inverse): per-element
  * Gc_e (host, Ne doubles, each > 0 and finite; NULL restores the material's
  * uniform Gc) in place of Gc in the damage operator, its right-hand side and

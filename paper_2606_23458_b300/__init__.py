@@ -102,6 +102,8 @@ _sig = {
     "pff_backward": [_P, _P, _P, C.POINTER(pff_options), C.POINTER(C.c_double), _P],
     "pff_backward_field": [_P, _P, _P, C.POINTER(pff_options), C.POINTER(C.c_double), _P, _P],
     "pff_mesh_set_gc_field": [_P, _P],
+    "pff_qs_run": [_P, C.POINTER(pff_state), _P, C.c_int64, C.c_int32, C.c_double, C.c_double,
+                   C.c_int32, C.POINTER(pff_options), _P, _P, _P],
     "pff_batch_create": [C.c_int32, _P, C.c_int32, C.c_double, C.POINTER(C.c_void_p)],
     "pff_batch_destroy": [_P],
     "pff_batch_size": [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
@@ -423,6 +425,23 @@ class Mesh:
         _check(_lib.pff_backward_field(self._h, ckpt._h, _dptr(dL_dd), C.byref(o), C.byref(g),
                                        _dptr(ge), _stream(stream)))
         return g.value, ge
+
+    def qs_run(self, st, bc, nincr, du, incr0=0, newton_tol=1e-8, newton_max=25, opts=None,
+               stream=None):
+        """Quasi-static staggered increments (pff_qs_run).  bc: N uint8
+        flags (1 fix u_x, 2 fix u_y, 4 loaded: u_y = U).  Returns
+        dict(reaction (nincr,), iters (nincr, 3): Newton, mechanics CG,
+        damage CG)."""
+        s = self._state(st)
+        o = opts or options()
+        b = _np(bc, np.uint8)
+        assert b.shape == (self.N,)
+        reac = np.zeros(nincr)
+        it = np.zeros((nincr, 3), np.int32)
+        _check(_lib.pff_qs_run(self._h, C.byref(s), _hp(b), int(incr0), int(nincr), float(du),
+                               float(newton_tol), int(newton_max), C.byref(o), _hp(reac), _hp(it),
+                               _stream(stream)))
+        return dict(reaction=reac, iters=it)
 
     def set_gc_field(self, gc):
         """Per-element toughness Gc_e (array of Ne, host), or None for the

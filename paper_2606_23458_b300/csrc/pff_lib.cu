@@ -16,6 +16,7 @@
 
 #include "adjoint.cuh"
 #include "batch.cuh"
+#include "qs.cuh"
 #include "kernels.cuh"
 #include "pff.h"
 
@@ -1686,6 +1687,132 @@ static pff_status mesh_build_t(pff_mesh *m, const double *xy_d, const int32_t *t
 }  // namespace pff
 
 namespace pff {
+// Quasi-static staggered loop (Sec. 3.5): per increment the Dirichlet
+// values, Newton on the mechanics (each step a Jacobi-PCG solve with the
+// matrix-free tangent, launched in batches of 32 iterations that become
+// no-ops once converged, the host checking between batches), the history
+// and the damage solve.  reaction[k] = sum f_int,y over the loaded nodes at
+// the converged u (with the damage of that mechanics solve).
+template <typename R>
+static pff_status qs_run_t(pff_mesh *m, const pff_state *st, const uint8_t *bc_host, int64_t incr0,
+                           int32_t nincr, double du, double newton_tol, int32_t newton_max,
+                           const pff_options &o, double *reaction, int32_t *iters, cudaStream_t s) {
+  typedef typename V<R>::T2 R2;
+  typedef typename V<R>::T4 R4;
+  const int64_t N = m->N;
+  uint8_t *bc = nullptr;
+  R4 *pz = nullptr;
+  R2 *r = nullptr, *q = nullptr, *x = nullptr, *dg = nullptr;
+  QsScalars *qs = nullptr;
+  pff_status res = PFF_OK;
+  auto cleanup = [&]() {
+    void *ptrs[] = {bc, pz, r, q, x, dg, qs};
+    for (void *p : ptrs)
+      if (p) cudaFree(p);
+  };
+#define QS_TRY(x)              \
+  do {                         \
+    res = (x);                 \
+    if (res != PFF_OK) {       \
+      cleanup();               \
+      return res;              \
+    }                          \
+  } while (0)
+  QS_TRY(dalloc(&bc, N));
+  QS_TRY(dalloc(&pz, N));
+  QS_TRY(dalloc(&r, N));
+  QS_TRY(dalloc(&q, N));
+  QS_TRY(dalloc(&x, N));
+  QS_TRY(dalloc(&dg, N));
+  QS_TRY(dalloc(&qs, 1));
+  if (cudaMemcpyAsync(bc, bc_host, N, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemsetAsync(qs, 0, sizeof(QsScalars), s) != cudaSuccess) {
+    cleanup();
+    return fail(PFF_ERR_CUDA, "quasi-static workspace");
+  }
+  QsParams<R> Q;
+  std::memset(&Q, 0, sizeof(Q));
+  Q.P = base_params<R>(m, o);
+  Q.P.u = (R2 *)st->u;
+  Q.P.d = (R *)st->d;
+  Q.P.rscale = R(1);
+  QS_TRY(bind_history<R>(m, Q.P, st->H, s));
+  Q.bc = bc;
+  Q.pz = pz;
+  Q.r = r;
+  Q.q = q;
+  Q.x = x;
+  Q.dg = dg;
+  Q.qs = qs;
+  Q.tol = sizeof(R) == 4 ? std::max(0.1 * newton_tol, kFp32TolFloor) : 0.1 * newton_tol;
+  Q.max_it = o.cg_max_it;
+  const unsigned Gn = std::min<unsigned>(grid_for(N, kThreads), m->grid[KP_UPDATE][0]);
+  const unsigned Ge = std::min<unsigned>(grid_for(m->Ne, kThreads), m->grid[KP_UPDATE][0]);
+  QsScalars hs;
+  auto read = [&]() -> pff_status {
+    CUDA_TRY(cudaMemcpyAsync(&hs, qs, sizeof(hs), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return PFF_OK;
+  };
+  pff_status worst = PFF_OK;
+  for (int32_t k = 0; k < nincr; ++k) {
+    Q.U = (double)(incr0 + k + 1) * du;
+    k_qs_bc<R><<<Gn, kThreads, 0, s>>>(Q);
+    int32_t newton = 0, cg = 0;
+    double reac = 0.0;
+    for (int32_t it = 0;; ++it) {
+      k_qs_residual<R><<<Gn, kThreads, 0, s>>>(Q);
+      QS_TRY(read());
+      reac = hs.reaction;
+      if (hs.fsq == 0.0 || std::sqrt(hs.rr) <= newton_tol * std::sqrt(hs.fsq)) break;
+      if (it == newton_max) {
+        worst = PFF_ERR_NOT_CONVERGED;
+        break;
+      }
+      k_qs_setup<R><<<Gn, kThreads, 0, s>>>(Q);
+      for (;;) {
+        for (int b = 0; b < 32; ++b) {
+          k_qs_matvec<R><<<Gn, kThreads, 0, s>>>(Q);
+          k_qs_update<R><<<Gn, kThreads, 0, s>>>(Q);
+        }
+        QS_TRY(read());
+        if (hs.done) break;
+      }
+      cg += hs.iters;
+      if (hs.status == kStNonfinite) {
+        cleanup();
+        return fail(PFF_ERR_NONFINITE, "non-finite value in a mechanics CG");
+      }
+      if (hs.status == kStNotConverged) worst = PFF_ERR_NOT_CONVERGED;
+      k_qs_apply<R><<<Gn, kThreads, 0, s>>>(Q);
+      newton = it + 1;
+    }
+    if (reaction) reaction[k] = reac;
+    k_qs_history<R><<<Ge, kThreads, 0, s>>>(Q);
+    if (cudaGetLastError() != cudaSuccess) {
+      cleanup();
+      return fail(PFF_ERR_CUDA, "quasi-static kernel launch");
+    }
+    int32_t dit = 0, drs = 0;
+    double rel = 0.0;
+    const pff_status ds = damage_solve_t<R>(m, st->H, st->d, st->d, o, &dit, &rel, &drs, s);
+    if (ds != PFF_OK && ds != PFF_ERR_NOT_CONVERGED) {
+      cleanup();
+      return ds;
+    }
+    if (ds == PFF_ERR_NOT_CONVERGED) worst = ds;
+    if (iters) {
+      iters[3 * k] = newton;
+      iters[3 * k + 1] = cg;
+      iters[3 * k + 2] = dit;
+    }
+  }
+#undef QS_TRY
+  cleanup();
+  if (worst != PFF_OK) return fail(worst, "a quasi-static Newton, mechanics CG or damage solve did not converge");
+  return PFF_OK;
+}
+
 // Gc_e / Gc in the kernel precision (padded to whole groups of 4 elements).
 static pff_status upload_gc_field(pff_mesh *m) {
   const int64_t Ne4 = (m->Ne + 3) / 4 * 4;
@@ -2544,6 +2671,21 @@ pff_status pff_backward_field(pff_mesh *m, pff_ckpt *c, const void *dL_dd, const
   cudaStream_t s = (cudaStream_t)stream;
   return m->prec == PFF_FP64 ? backward_t<double>(m, c, dL_dd, o, dL_dGc, s, dL_dGc_field)
                              : backward_t<float>(m, c, dL_dd, o, dL_dGc, s, dL_dGc_field);
+}
+
+pff_status pff_qs_run(pff_mesh *m, const pff_state *st, const uint8_t *bc, int64_t incr0, int32_t nincr,
+                      double du, double newton_tol, int32_t newton_max, const pff_options *opt, double *reaction,
+                      int32_t *iters, pff_stream stream) {
+  if (!m || !st || !st->u || !st->d || !st->H || !bc || nincr < 0 || incr0 < 0 || !(newton_tol > 0) ||
+      newton_max < 1)
+    return fail(PFF_ERR_ARG, "bad quasi-static arguments");
+  if (!m->has_mat) return fail(PFF_ERR_ARG, "material not set");
+  const pff_options o = defaults(opt);
+  cudaStream_t s = (cudaStream_t)stream;
+  return m->prec == PFF_FP64 ? qs_run_t<double>(m, st, bc, incr0, nincr, du, newton_tol, newton_max, o, reaction,
+                                                iters, s)
+                             : qs_run_t<float>(m, st, bc, incr0, nincr, du, newton_tol, newton_max, o, reaction,
+                                               iters, s);
 }
 
 pff_status pff_mesh_set_gc_field(pff_mesh *m, const double *gc) {

@@ -1,0 +1,71 @@
+"""Quasi-static staggered mode on the GPU (Sec. 3.5; the matrix-free
+tangent of Sec. 2.3) against the oracle: the uniaxial bar's closed-form
+reactions and a small single-edge-notched tension run increment by
+increment (reactions, damage)."""
+import numpy as np
+import pytest
+
+import pff_synth as S
+from gpu_common import to_np
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pff():
+    import paper_2606_23458_b300 as pff
+    return pff
+
+
+def _sent(nx, ny, notch=True, rollers=False):
+    p = S.plate(nx, ny, Lx=1e-3, Ly=1e-3 if notch else 2e-3, notch=notch)
+    N = p["xy"].shape[0]
+    j = np.arange(N) // (nx + 1)
+    bc = np.zeros(N, np.uint8)
+    if rollers:
+        bc[j == 0] = 2
+        bc[0] |= 1
+        bc[j == ny] = 4
+    else:
+        bc[j == 0] = 3       # bottom edge clamped
+        bc[j == ny] = 1 | 4  # top edge: u_x = 0, u_y = U
+    return p, bc
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_uniaxial_bar_reaction(pff, prec):
+    p, bc = _sent(6, 10, notch=False, rollers=True)
+    mat = dict(S.material(2 * p["h"], split="amor"), E=210e9, nu=0.3, Gc=1e15)
+    m = pff.Mesh.from_plate(p, precision=prec)
+    m.set_material(mat, 0.5)
+    st = m.new_state()
+    du = 1e-7
+    r = m.qs_run(st, bc, 3, du, newton_tol=1e-10 if prec == "fp64" else 1e-5)
+    eps = du * np.arange(1, 4) / 2e-3
+    want = (1 + mat["eta"]) * mat["E"] / (1 - mat["nu"] ** 2) * eps * 1e-3
+    tol = 1e-9 if prec == "fp64" else 1e-5
+    assert np.allclose(r["reaction"], want, rtol=tol), (r["reaction"], want)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-7), ("fp32", 2e-3)])
+def test_sent_increments_match_oracle(orc, pff, prec, tol):
+    p, bc = _sent(16, 16)
+    mat = dict(S.material(2 * p["h"], split="amor"), E=210e9, nu=0.3, Gc=2700.0)
+    om = orc.Mesh.from_plate(p)
+    ost = om.new_state()
+    nincr, du = 8, 5e-7
+    ro = om.qs_run(mat, ost, bc, nincr, du, tol=1e-10)
+    m = pff.Mesh.from_plate(p, precision=prec)
+    m.set_material(mat, 0.5)
+    st = m.new_state()
+    opts = pff.options(cg_tol=1e-12 if prec == "fp64" else 1e-8)
+    r = m.qs_run(st, bc, nincr, du, newton_tol=1e-10 if prec == "fp64" else 1e-5, opts=opts)
+    assert np.allclose(r["reaction"], ro["reaction"], rtol=tol), (r["reaction"], ro["reaction"])
+    d = to_np(st["d"])
+    assert np.abs(d - ost["d"]).max() <= 10 * tol
+    assert np.all(r["iters"][:, 0] >= 1) and np.all(r["iters"][:, 1] > 0)
+    # split over two calls: the same increments
+    st2 = m.new_state()
+    a = m.qs_run(st2, bc, 3, du, newton_tol=1e-10 if prec == "fp64" else 1e-5, opts=opts)
+    b = m.qs_run(st2, bc, nincr - 3, du, incr0=3, newton_tol=1e-10 if prec == "fp64" else 1e-5, opts=opts)
+    assert np.allclose(np.concatenate([a["reaction"], b["reaction"]]), r["reaction"], rtol=1e-12)
