@@ -1703,10 +1703,11 @@ static pff_status qs_run_t(pff_mesh *m, const pff_state *st, const uint8_t *bc_h
   uint8_t *bc = nullptr;
   R4 *pz = nullptr;
   R2 *r = nullptr, *q = nullptr, *x = nullptr, *dg = nullptr;
+  R *ke = nullptr;
   QsScalars *qs = nullptr;
   pff_status res = PFF_OK;
   auto cleanup = [&]() {
-    void *ptrs[] = {bc, pz, r, q, x, dg, qs};
+    void *ptrs[] = {bc, pz, r, q, x, dg, ke, qs};
     for (void *p : ptrs)
       if (p) cudaFree(p);
   };
@@ -1725,6 +1726,7 @@ static pff_status qs_run_t(pff_mesh *m, const pff_state *st, const uint8_t *bc_h
   QS_TRY(dalloc(&x, N));
   QS_TRY(dalloc(&dg, N));
   QS_TRY(dalloc(&qs, 1));
+  QS_TRY(dalloc(&ke, (size_t)m->Ne * 36));
   if (cudaMemcpyAsync(bc, bc_host, N, cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemsetAsync(qs, 0, sizeof(QsScalars), s) != cudaSuccess) {
     cleanup();
@@ -1744,6 +1746,7 @@ static pff_status qs_run_t(pff_mesh *m, const pff_state *st, const uint8_t *bc_h
   Q.x = x;
   Q.dg = dg;
   Q.qs = qs;
+  Q.ke = ke;
   Q.tol = sizeof(R) == 4 ? std::max(0.1 * newton_tol, kFp32TolFloor) : 0.1 * newton_tol;
   Q.max_it = o.cg_max_it;
   const unsigned Gn = std::min<unsigned>(grid_for(N, kThreads), m->grid[KP_UPDATE][0]);
@@ -1769,6 +1772,7 @@ static pff_status qs_run_t(pff_mesh *m, const pff_state *st, const uint8_t *bc_h
         worst = PFF_ERR_NOT_CONVERGED;
         break;
       }
+      k_qs_elem_tangent<R><<<Ge, kThreads, 0, s>>>(Q);
       k_qs_setup<R><<<Gn, kThreads, 0, s>>>(Q);
       for (;;) {
         for (int b = 0; b < 32; ++b) {

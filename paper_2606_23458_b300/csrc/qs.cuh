@@ -29,6 +29,8 @@ template <typename R> struct QsParams {
   double U;           // prescribed u_y of the loaded nodes
   R4 *pz;             // (p_x, z_x, p_y, z_y) per node
   R2 *r, *q, *x, *dg; // residual, K_T p, the Newton step, Jacobi diagonal
+  R *ke;              // per element the 6 x 6 tangent K_e = A B^T C_T B (row-major,
+                      // dofs (x0, y0, x1, y1, x2, y2)), rebuilt each Newton step
   QsScalars *qs;
   double tol;         // CG: |r| <= tol |r_0|
   int32_t max_it;
@@ -114,6 +116,41 @@ __device__ __forceinline__ typename Params<R>::R2 qs_pnew(const QsParams<R> &Q, 
   return o;
 }
 
+// Element tangents at the current u and d (constant during the CG of a
+// Newton step): column (b, c) of K_e is A B^T dsigma[B e_(b,c)] with
+// dsigma = g(dbar) dsigma+ + dsigma- (the split's tangent); the Hessian of
+// A psi, so K_e is symmetric.
+template <typename R>
+__global__ void __launch_bounds__(256) k_qs_elem_tangent(QsParams<R> Q) {
+  typedef typename Params<R>::R4 R4;
+  const Params<R> &P = Q.P;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < P.Ne; e += gridDim.x * blockDim.x) {
+    int4 t;
+    R A;
+    R4 G;
+    load_elem(P, e, t, A, G);
+    R exx, eyy, exy;
+    elem_strain(P, G, t, exx, eyy, exy);
+    const R db = (P.d[t.x] + P.d[t.y] + P.d[t.z]) * (R(1) / R(3));
+    const R g = (R(1) - db) * (R(1) - db) + P.eta;
+    R gxs[3], gys[3];
+    for (int b = 0; b < 3; ++b) slot_grad<R>(G, b, gxs[b], gys[b]);
+    R *K = Q.ke + (size_t)e * 36;
+    for (int b = 0; b < 3; ++b)
+      for (int c = 0; c < 2; ++c) {
+        const R gx = gxs[b], gy = gys[b];
+        const R de[3] = {c == 0 ? gx : R(0), c == 1 ? gy : R(0), R(0.5) * (c == 0 ? gy : gx)};
+        R ds[3];
+        qs_dsigma(P, exx, eyy, exy, g, de, ds);
+        const int col = 2 * b + c;
+        for (int a = 0; a < 3; ++a) {
+          K[(2 * a) * 6 + col] = A * (ds[0] * gxs[a] + ds[2] * gys[a]);
+          K[(2 * a + 1) * 6 + col] = A * (ds[2] * gxs[a] + ds[1] * gys[a]);
+        }
+      }
+  }
+}
+
 // Jacobi diagonal of K_T(u) (one unit displacement per dof through the
 // tangent), z = r / diag, p = z; rho = r.z and |r_0|.
 template <typename R>
@@ -128,22 +165,9 @@ __global__ void __launch_bounds__(256) k_qs_setup(QsParams<R> Q) {
       const int en = __ldg(&P.ell[(size_t)k * P.N + i]);
       if (en < 0) continue;
       const int e = en >> 2, a = en & 3;
-      int4 t;
-      R A;
-      R4 G;
-      load_elem(P, e, t, A, G);
-      R exx, eyy, exy;
-      elem_strain(P, G, t, exx, eyy, exy);
-      const R db = (P.d[t.x] + P.d[t.y] + P.d[t.z]) * (R(1) / R(3));
-      const R g = (R(1) - db) * (R(1) - db) + P.eta;
-      R gx, gy;
-      slot_grad<R>(G, a, gx, gy);
-      const R ux[3] = {gx, R(0), R(0.5) * gy}, uy[3] = {R(0), gy, R(0.5) * gx};
-      R sx[3], sy[3];
-      qs_dsigma(P, exx, eyy, exy, g, ux, sx);
-      qs_dsigma(P, exx, eyy, exy, g, uy, sy);
-      dx = radd(dx, A * (sx[0] * gx + sx[2] * gy));
-      dy = radd(dy, A * (sy[2] * gx + sy[1] * gy));
+      const R *K = Q.ke + (size_t)e * 36;
+      dx = radd(dx, K[(2 * a) * 6 + 2 * a]);
+      dy = radd(dy, K[(2 * a + 1) * 6 + 2 * a + 1]);
     }
     const typename Params<R>::R2 r = Q.r[i];
     typename Params<R>::R2 dg;
@@ -189,24 +213,11 @@ __global__ void __launch_bounds__(256) k_qs_matvec(QsParams<R> Q) {
       const int en = __ldg(&P.ell[(size_t)k * P.N + i]);
       if (en < 0) continue;
       const int e = en >> 2, a = en & 3;
-      int4 t;
-      R A;
-      R4 G;
-      load_elem(P, e, t, A, G);
-      R exx, eyy, exy;
-      elem_strain(P, G, t, exx, eyy, exy);
-      const R db = (P.d[t.x] + P.d[t.y] + P.d[t.z]) * (R(1) / R(3));
-      const R g = (R(1) - db) * (R(1) - db) + P.eta;
-      const R2 p0 = qs_pnew(Q, t.x, beta), p1 = qs_pnew(Q, t.y, beta), p2 = qs_pnew(Q, t.z, beta);
-      const R ax0 = p0.x - p2.x, ax1 = p1.x - p2.x, ay0 = p0.y - p2.y, ay1 = p1.y - p2.y;
-      const R de[3] = {G.x * ax0 + G.z * ax1, G.y * ay0 + G.w * ay1,
-                       R(0.5) * (G.y * ax0 + G.w * ax1 + G.x * ay0 + G.z * ay1)};
-      R ds[3];
-      qs_dsigma(P, exx, eyy, exy, g, de, ds);
-      R gx, gy;
-      slot_grad<R>(G, a, gx, gy);
-      qx = radd(qx, A * (ds[0] * gx + ds[2] * gy));
-      qy = radd(qy, A * (ds[2] * gx + ds[1] * gy));
+      const ERec<R> &rc = P.rec[e];
+      const R2 p0 = qs_pnew(Q, rc.n0, beta), p1 = qs_pnew(Q, rc.n1, beta), p2 = qs_pnew(Q, rc.n2, beta);
+      const R *K = Q.ke + (size_t)e * 36 + 12 * a;  // rows 2a, 2a+1
+      qx = radd(qx, K[0] * p0.x + K[1] * p0.y + K[2] * p1.x + K[3] * p1.y + K[4] * p2.x + K[5] * p2.y);
+      qy = radd(qy, K[6] * p0.x + K[7] * p0.y + K[8] * p1.x + K[9] * p1.y + K[10] * p2.x + K[11] * p2.y);
     }
     if (qs_fx(Q, i)) qx = R(0);
     if (qs_fy(Q, i)) qy = R(0);

@@ -164,6 +164,25 @@ def config(name, split="spectral", model="AT2"):
                 cfl=0.5, t_ramp=0.05e-6, cg_tol=1e-8)
 
 
+def sent(n=700, increments=100, u_max=7e-6):
+    """Single-edge-notched tension, quasi-static (Sec. 3.5): a 1 x 1 mm
+    square of n x n cells, notch on the left half of the mid-line, bottom
+    edge clamped, top edge u_x = 0 and u_y = U rising in equal increments to
+    u_max (7e-3 mm); E = 210 GPa, nu = 0.3, Gc = 2.7 N/mm (2700 J/m^2),
+    l0 = 2h, AT2 with the volumetric-deviatoric split, plane strain.
+    bc flags per node: 1 fix u_x, 2 fix u_y, 4 loaded."""
+    mesh = plate(n, n, Lx=1e-3, Ly=1e-3, notch=True, traction=0.0)
+    N = mesh["xy"].shape[0]
+    j = np.arange(N) // (n + 1)
+    bc = np.zeros(N, np.uint8)
+    bc[j == 0] = 3
+    bc[j == n] = 1 | 4
+    mat = material(2.0 * mesh["h"], split="amor")
+    mat.update(E=210e9, nu=0.3, Gc=2700.0)
+    return dict(name=f"sent_{n}", mesh=mesh, material=mat, bc=bc, increments=increments,
+                du=u_max / increments, newton_tol=1e-8, cg_tol=1e-8)
+
+
 def batch_draws(n_plates=64, seed=1):
     """Per-plate draws for the batched workload from one SplitMix64 counter
     stream starting at (seed << 32): nx = 200 + floor(501 u) cells
