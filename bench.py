@@ -54,6 +54,12 @@ def parse():
                     help="gather schedule (0 = autotuned; 1..5 fixed, see pff_options.variant)")
     ap.add_argument("--cg-kernel", choices=["auto", "phases", "persistent", "staged", "fused", "fused_staged"],
                     default="auto", help="AT2 CG loop (pff_options.cg_kernel; auto = autotuned)")
+    ap.add_argument("--no-qs", action="store_true",
+                    help="skip the quasi-static single-edge-notched tension measurement")
+    ap.add_argument("--qs-only", action="store_true",
+                    help="run only the quasi-static measurement and print its line")
+    ap.add_argument("--qs-increments", type=int, default=5,
+                    help="timed load increments of the quasi-static run")
     ap.add_argument("--loop", choices=["graph", "host"], default="graph",
                     help="host: launch every kernel from the host (ncu cannot profile "
                          "kernels inside graphs with conditional nodes)")
@@ -381,6 +387,51 @@ def subcycled(pff, dev, config, steps=100, warmup=10):
                 status=int(mesh.sync_status()))
 
 
+def quasistatic(pff, dev, increments=5, n=700, compare_increments=2):
+    """Quasi-static single-edge-notched tension (Sec. 3.5): the 700 x 700
+    unit square, the first `increments` of the 100 equal load increments to
+    7e-3 mm, each an inexact Newton solve (FP64 state and residual; tangent
+    CG in FP32 with double-word dots, i.e. FP32 matvecs and FP64-class inner
+    products) to |r| <= 1e-8 |f|, history and the damage solve (FP64, tol
+    1e-8).  The same increments with the tangent CG in FP64 are timed
+    beside it (compare_increments).  qs_run synchronises, so the events
+    bracket whole increments."""
+    import torch
+    c = S.sent(n)
+    out = dict(workload=c["name"], nodes=None, elements=None, increments_total=c["increments"],
+               du=c["du"], newton_tol=c["newton_tol"], damage_cg_tol=c["cg_tol"])
+    opts = pff.options(cg_tol=c["cg_tol"], cg_max_it=100000)
+    stream = torch.cuda.current_stream()
+    for label, krylov, k in (("fp32_krylov", "fp32", increments), ("fp64_krylov", "mesh", compare_increments)):
+        if k <= 0:
+            continue
+        mesh = pff.Mesh.from_plate(c["mesh"], precision="fp64")
+        mesh.set_material(c["material"], 0.5)
+        out["nodes"], out["elements"] = mesh.N, mesh.Ne
+        q = pff.qs_options(newton_tol=c["newton_tol"], krylov=krylov)
+        st = mesh.new_state(device=dev)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = mesh.qs_run(st, c["bc"], k, c["du"], qopts=q, opts=opts)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        it = r["iters"]
+        out[label] = dict(increments=k, s_per_increment=ms / 1e3 / k, newton=it[:, 0].tolist(),
+                          tangent_cg=it[:, 1].tolist(), damage_cg=it[:, 2].tolist(),
+                          us_per_tangent_cg_iteration=ms * 1e3 / max(int(it[:, 1].sum()), 1),
+                          reaction_N_per_m=r["reaction"].tolist(), d_max=float(st["d"].max()))
+        del mesh, st
+    if "fp32_krylov" in out and "fp64_krylov" in out:
+        k = min(len(out["fp32_krylov"]["reaction_N_per_m"]), len(out["fp64_krylov"]["reaction_N_per_m"]))
+        a = np.array(out["fp32_krylov"]["reaction_N_per_m"][:k])
+        b = np.array(out["fp64_krylov"]["reaction_N_per_m"][:k])
+        out["reaction_rel_diff_fp32_vs_fp64_krylov"] = float(np.max(np.abs(a - b) / np.abs(b)))
+    return out
+
+
 # ------------------------------------------------------------------- ours
 
 def run_ours(args):
@@ -394,6 +445,13 @@ def run_ours(args):
     torch.cuda.set_device(dev)
     import paper_2606_23458_b300 as pff
 
+    if args.qs_only:
+        if rank == 0:
+            print(json.dumps(dict(quasistatic=quasistatic(pff, dev, args.qs_increments, compare_increments=0))),
+                  flush=True)
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
     c = S.config(args.config, split=args.split, model=args.model)
     mesh = pff.Mesh.from_plate(c["mesh"], precision=args.prec)
     dt = mesh.set_material(c["material"], c["cfl"])
@@ -528,6 +586,8 @@ def run_ours(args):
         line["fwd_adjoint"] = fwd_adjoint(pff, dev)
     if not args.no_batch:
         line["batched"] = batched(pff, dev)
+    if not args.no_qs:
+        line["quasistatic"] = quasistatic(pff, dev, args.qs_increments)
     if not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline(args)
     print(json.dumps(line), flush=True)

@@ -152,26 +152,48 @@ pff_status pff_mesh_create(int64_t N, const double *xy, int64_t Ne,
 
 void pff_mesh_destroy(pff_mesh *mesh);
 
+/* Options of the quasi-static loop.  Defaults in brackets (also taken when
+ * the pointer is NULL). */
+enum { PFF_QS_KRYLOV_FP32 = 0, PFF_QS_KRYLOV_MESH = 1 };
+typedef struct {
+  double newton_tol;  /* Newton stop: |r_free| <= newton_tol |f_int| [1e-8] */
+  int32_t newton_max; /* Newton steps per increment [25] */
+  int32_t krylov;     /* precision of the tangent CG (its vectors and the
+                         stored element tangents): PFF_QS_KRYLOV_FP32, or
+                         PFF_QS_KRYLOV_MESH for the mesh's precision.  Under
+                         an FP64 mesh FP32 is mixed-precision refinement:
+                         the state and the Newton residual stay FP64. [FP32] */
+  double eta_min;     /* forcing term of the inexact Newton step: the CG of a */
+  double eta_max;     /* step stops at |r_cg| <= eta |r|, eta = clamp(0.1
+                         newton_tol |f_int| / |r|, eta_min, eta_max).  With
+                         FP32 CG vectors eta_min is the attainable reduction
+                         per step. [1e-4 with FP32 CG, else 0; 0.5] */
+  int32_t cg_max_it;  /* CG iterations per Newton step [100000] */
+  int32_t pad;
+} pff_qs_options;
+
 /* Quasi-static staggered loop (Sec. 3.5, e.g. single-edge-notched
  * tension), nincr load increments: increment k puts u_y = (incr0 + k + 1) du
  * on the loaded nodes, then solves the mechanics f_int(u; d) = 0 on the free
- * dofs by Newton iterations (at most newton_max; stop when
- * |r_free| <= newton_tol |f_int|), each linear step K_T(u) du = -r by
- * Jacobi-PCG to 0.1 newton_tol (FP32 floor 2^-22) with the matrix-free
- * tangent action (Eq. matrix_free_tangent_action: the internal force's
- * derivative along the trial vector through the split's tangent), then
- * H = max(H, psi+(u)) and the damage solve of pff_damage_solve (opt's
- * tolerance; d_prev = d).  state: u, d, H on the device, updated in place
- * (v, a unused).  bc (host, N bytes): 1 = u_x fixed at 0, 2 = u_y fixed at
- * 0, 4 = loaded (u_y = U).  reaction (host, nincr, nullable): sum of
- * f_int,y over the loaded nodes at the converged u (per unit thickness).
- * iters (host, nincr x 3, nullable): Newton steps, mechanics CG iterations,
- * damage CG iterations.  Synchronises the stream.  PFF_ERR_NOT_CONVERGED if
- * a Newton loop, mechanics CG or damage solve hit its cap (the increments
- * still complete). */
+ * dofs by inexact Newton iterations (qopt), each linear step
+ * K_T(u) du = -r by Jacobi-PCG with the tangent action of Eq.
+ * matrix_free_tangent_action (the internal force's derivative along the
+ * trial vector through the split's tangent; the element's A C_T is
+ * evaluated once per Newton step), then H = max(H, psi+(u)) and the damage
+ * solve of pff_damage_solve (opt's tolerance; d_prev = d).  state: u, d, H
+ * on the device, updated in place (v, a unused).  bc (host, N bytes): 1 =
+ * u_x fixed at 0, 2 = u_y fixed at 0, 4 = loaded (u_y = U).  reaction
+ * (host, nincr, nullable): sum of f_int,y over the loaded nodes at the
+ * converged u (per unit thickness).  iters (host, nincr x 3, nullable):
+ * Newton steps, mechanics CG iterations, damage CG iterations.  Allocates
+ * its workspace (N x 49 + Ne x 88 bytes with FP32 CG) and frees it before
+ * returning; synchronises the stream.  PFF_ERR_ARG for options out of
+ * range (eta_min < 0, eta_max < eta_min or >= 1, newton_tol <= 0);
+ * PFF_ERR_NOT_CONVERGED if a Newton loop, mechanics CG or damage solve hit
+ * its cap (the increments still complete). */
 pff_status pff_qs_run(pff_mesh *mesh, const pff_state *state, const uint8_t *bc, int64_t incr0,
-                      int32_t nincr, double du, double newton_tol, int32_t newton_max,
-                      const pff_options *opt, double *reaction, int32_t *iters, pff_stream stream);
+                      int32_t nincr, double du, const pff_qs_options *qopt, const pff_options *opt,
+                      double *reaction, int32_t *iters, pff_stream stream);
 
 /* Toughness field (Secs. 4.2 and 7: the field-valued inverse): per-element
  * Gc_e (host, Ne doubles, each > 0 and finite; NULL restores the material's

@@ -35,6 +35,7 @@ CG_KINDS = {PFF_CG_AUTO: "auto", PFF_CG_PHASES: "phases", PFF_CG_PERSISTENT: "pe
 MODELS = {"AT1": PFF_AT1, "AT2": PFF_AT2}
 SPLITS = {"spectral": PFF_SPLIT_SPECTRAL, "amor": PFF_SPLIT_AMOR, "iso": PFF_SPLIT_ISO}
 PFF_PLANE_STRAIN, PFF_PLANE_STRESS = 0, 1
+PFF_QS_KRYLOV_FP32, PFF_QS_KRYLOV_MESH = 0, 1
 PLANES = {"strain": PFF_PLANE_STRAIN, "stress": PFF_PLANE_STRESS}
 PRECISIONS = {"fp64": PFF_FP64, "fp32": PFF_FP32_MIXED}
 
@@ -58,6 +59,12 @@ class pff_options(C.Structure):
                 ("energy_every", C.c_int32), ("ckpt_every", C.c_int32),
                 ("block", C.c_int32), ("loop_mode", C.c_int32), ("variant", C.c_int32),
                 ("cg_kernel", C.c_int32), ("damage_every", C.c_int32)]
+
+
+class pff_qs_options(C.Structure):
+    _fields_ = [("newton_tol", C.c_double), ("newton_max", C.c_int32), ("krylov", C.c_int32),
+                ("eta_min", C.c_double), ("eta_max", C.c_double), ("cg_max_it", C.c_int32),
+                ("pad", C.c_int32)]
 
 
 class pff_plate(C.Structure):
@@ -102,8 +109,8 @@ _sig = {
     "pff_backward": [_P, _P, _P, C.POINTER(pff_options), C.POINTER(C.c_double), _P],
     "pff_backward_field": [_P, _P, _P, C.POINTER(pff_options), C.POINTER(C.c_double), _P, _P],
     "pff_mesh_set_gc_field": [_P, _P],
-    "pff_qs_run": [_P, C.POINTER(pff_state), _P, C.c_int64, C.c_int32, C.c_double, C.c_double,
-                   C.c_int32, C.POINTER(pff_options), _P, _P, _P],
+    "pff_qs_run": [_P, C.POINTER(pff_state), _P, C.c_int64, C.c_int32, C.c_double,
+                   C.POINTER(pff_qs_options), C.POINTER(pff_options), _P, _P, _P],
     "pff_batch_create": [C.c_int32, _P, C.c_int32, C.c_double, C.POINTER(C.c_void_p)],
     "pff_batch_destroy": [_P],
     "pff_batch_size": [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
@@ -150,6 +157,17 @@ def options(cg_tol=1e-8, cg_max_it=10000, max_restarts=50, t_ramp=0.05e-6, energ
             damage_every=0):
     return pff_options(cg_tol, cg_max_it, max_restarts, t_ramp, energy_every, ckpt_every,
                        block, loop_mode, variant, cg_kernel, damage_every)
+
+
+def qs_options(newton_tol=1e-8, newton_max=25, krylov="fp32", eta_min=None, eta_max=0.5,
+               cg_max_it=100000):
+    """Options of the quasi-static loop (pff_qs_options).  krylov: "fp32"
+    (tangent CG in FP32; mixed-precision refinement under an FP64 mesh) or
+    "mesh" (the mesh's precision).  eta_min None: 1e-4 with FP32 CG, else 0."""
+    k = {"fp32": PFF_QS_KRYLOV_FP32, "mesh": PFF_QS_KRYLOV_MESH}[krylov]
+    if eta_min is None:
+        eta_min = 1e-4 if k == PFF_QS_KRYLOV_FP32 else 0.0
+    return pff_qs_options(newton_tol, newton_max, k, eta_min, eta_max, cg_max_it, 0)
 
 
 def subcycling_limit(mat):
@@ -426,21 +444,20 @@ class Mesh:
                                        _dptr(ge), _stream(stream)))
         return g.value, ge
 
-    def qs_run(self, st, bc, nincr, du, incr0=0, newton_tol=1e-8, newton_max=25, opts=None,
-               stream=None):
+    def qs_run(self, st, bc, nincr, du, incr0=0, qopts=None, opts=None, stream=None, **kw):
         """Quasi-static staggered increments (pff_qs_run).  bc: N uint8
-        flags (1 fix u_x, 2 fix u_y, 4 loaded: u_y = U).  Returns
-        dict(reaction (nincr,), iters (nincr, 3): Newton, mechanics CG,
-        damage CG)."""
+        flags (1 fix u_x, 2 fix u_y, 4 loaded: u_y = U).  qopts: a
+        qs_options(...) (or its keywords in kw).  Returns dict(reaction
+        (nincr,), iters (nincr, 3): Newton, mechanics CG, damage CG)."""
         s = self._state(st)
+        q = qopts if qopts is not None else qs_options(**kw)
         o = opts or options()
         b = _np(bc, np.uint8)
         assert b.shape == (self.N,)
         reac = np.zeros(nincr)
         it = np.zeros((nincr, 3), np.int32)
         _check(_lib.pff_qs_run(self._h, C.byref(s), _hp(b), int(incr0), int(nincr), float(du),
-                               float(newton_tol), int(newton_max), C.byref(o), _hp(reac), _hp(it),
-                               _stream(stream)))
+                               C.byref(q), C.byref(o), _hp(reac), _hp(it), _stream(stream)))
         return dict(reaction=reac, iters=it)
 
     def set_gc_field(self, gc):

@@ -1693,21 +1693,22 @@ namespace pff {
 // no-ops once converged, the host checking between batches), the history
 // and the damage solve.  reaction[k] = sum f_int,y over the loaded nodes at
 // the converged u (with the damage of that mechanics solve).
-template <typename R>
+template <typename R, typename K>
 static pff_status qs_run_t(pff_mesh *m, const pff_state *st, const uint8_t *bc_host, int64_t incr0,
-                           int32_t nincr, double du, double newton_tol, int32_t newton_max,
-                           const pff_options &o, double *reaction, int32_t *iters, cudaStream_t s) {
-  typedef typename V<R>::T2 R2;
-  typedef typename V<R>::T4 R4;
+                           int32_t nincr, double du, const pff_qs_options &qo, const pff_options &o,
+                           double *reaction, int32_t *iters, cudaStream_t s) {
+  typedef typename V<K>::T2 K2;
+  typedef typename V<K>::T4 K4;
   const int64_t N = m->N;
   uint8_t *bc = nullptr;
-  R4 *pz = nullptr;
-  R2 *r = nullptr, *q = nullptr, *x = nullptr, *dg = nullptr;
-  R *ke = nullptr;
+  K4 *pz = nullptr;
+  K2 *r = nullptr, *q = nullptr, *x = nullptr, *dg = nullptr;
+  K2 *fe = nullptr;
+  QRec<K> *rec = nullptr;
   QsScalars *qs = nullptr;
   pff_status res = PFF_OK;
   auto cleanup = [&]() {
-    void *ptrs[] = {bc, pz, r, q, x, dg, ke, qs};
+    void *ptrs[] = {bc, pz, r, q, x, dg, fe, rec, qs};
     for (void *p : ptrs)
       if (p) cudaFree(p);
   };
@@ -1726,31 +1727,39 @@ static pff_status qs_run_t(pff_mesh *m, const pff_state *st, const uint8_t *bc_h
   QS_TRY(dalloc(&x, N));
   QS_TRY(dalloc(&dg, N));
   QS_TRY(dalloc(&qs, 1));
-  QS_TRY(dalloc(&ke, (size_t)m->Ne * 36));
+  QS_TRY(dalloc(&rec, m->Ne));
+  QS_TRY(dalloc(&fe, 3 * m->Ne));
   if (cudaMemcpyAsync(bc, bc_host, N, cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemsetAsync(qs, 0, sizeof(QsScalars), s) != cudaSuccess) {
     cleanup();
     return fail(PFF_ERR_CUDA, "quasi-static workspace");
   }
-  QsParams<R> Q;
+  QsParams<R, K> Q;
   std::memset(&Q, 0, sizeof(Q));
   Q.P = base_params<R>(m, o);
-  Q.P.u = (R2 *)st->u;
+  Q.P.u = (typename V<R>::T2 *)st->u;
   Q.P.d = (R *)st->d;
   Q.P.rscale = R(1);
   QS_TRY(bind_history<R>(m, Q.P, st->H, s));
-  Q.bc = bc;
-  Q.pz = pz;
-  Q.r = r;
-  Q.q = q;
-  Q.x = x;
-  Q.dg = dg;
-  Q.qs = qs;
-  Q.ke = ke;
-  Q.tol = sizeof(R) == 4 ? std::max(0.1 * newton_tol, kFp32TolFloor) : 0.1 * newton_tol;
-  Q.max_it = o.cg_max_it;
+  QkParams<K> &I = Q.I;
+  I.N = (int)N;
+  I.D = Q.P.D;
+  I.ell = Q.P.ell;
+  I.rec = rec;
+  I.bc = bc;
+  I.pz = pz;
+  I.r = r;
+  I.q = q;
+  I.x = x;
+  I.dg = dg;
+  I.fe = fe;
+  I.qs = qs;
+  I.part = Q.P.part;
+  I.ticket = Q.P.ticket;
+  I.max_it = qo.cg_max_it;
   const unsigned Gn = std::min<unsigned>(grid_for(N, kThreads), m->grid[KP_UPDATE][0]);
   const unsigned Ge = std::min<unsigned>(grid_for(m->Ne, kThreads), m->grid[KP_UPDATE][0]);
+  const unsigned Gf = grid_for(m->Ne, kThreads);  // element pass: one element per thread, no reduction
   QsScalars hs;
   auto read = [&]() -> pff_status {
     CUDA_TRY(cudaMemcpyAsync(&hs, qs, sizeof(hs), cudaMemcpyDeviceToHost, s));
@@ -1760,24 +1769,28 @@ static pff_status qs_run_t(pff_mesh *m, const pff_state *st, const uint8_t *bc_h
   pff_status worst = PFF_OK;
   for (int32_t k = 0; k < nincr; ++k) {
     Q.U = (double)(incr0 + k + 1) * du;
-    k_qs_bc<R><<<Gn, kThreads, 0, s>>>(Q);
+    k_qs_bc<R, K><<<Gn, kThreads, 0, s>>>(Q);
     int32_t newton = 0, cg = 0;
     double reac = 0.0;
     for (int32_t it = 0;; ++it) {
-      k_qs_residual<R><<<Gn, kThreads, 0, s>>>(Q);
+      k_qs_residual<R, K><<<Gn, kThreads, 0, s>>>(Q);
       QS_TRY(read());
       reac = hs.reaction;
-      if (hs.fsq == 0.0 || std::sqrt(hs.rr) <= newton_tol * std::sqrt(hs.fsq)) break;
-      if (it == newton_max) {
+      const double rn = std::sqrt(hs.rr), fn = std::sqrt(hs.fsq);
+      if (fn == 0.0 || rn <= qo.newton_tol * fn) break;
+      if (it == qo.newton_max) {
         worst = PFF_ERR_NOT_CONVERGED;
         break;
       }
-      k_qs_elem_tangent<R><<<Ge, kThreads, 0, s>>>(Q);
-      k_qs_setup<R><<<Gn, kThreads, 0, s>>>(Q);
+      // inexact Newton: solve to the forcing term eta relative to |r|
+      I.tol = std::min(qo.eta_max, std::max(qo.eta_min, 0.1 * qo.newton_tol * fn / rn));
+      k_qs_elem_tangent<R, K><<<Ge, kThreads, 0, s>>>(Q);
+      k_qs_setup<K><<<Gn, kThreads, 0, s>>>(I);
       for (;;) {
         for (int b = 0; b < 32; ++b) {
-          k_qs_matvec<R><<<Gn, kThreads, 0, s>>>(Q);
-          k_qs_update<R><<<Gn, kThreads, 0, s>>>(Q);
+          k_qs_elem_apply<K><<<Gf, kThreads, 0, s>>>(I, (int)m->Ne);
+          k_qs_matvec<K><<<Gn, kThreads, 0, s>>>(I);
+          k_qs_update<K><<<Gn, kThreads, 0, s>>>(I);
         }
         QS_TRY(read());
         if (hs.done) break;
@@ -1788,11 +1801,11 @@ static pff_status qs_run_t(pff_mesh *m, const pff_state *st, const uint8_t *bc_h
         return fail(PFF_ERR_NONFINITE, "non-finite value in a mechanics CG");
       }
       if (hs.status == kStNotConverged) worst = PFF_ERR_NOT_CONVERGED;
-      k_qs_apply<R><<<Gn, kThreads, 0, s>>>(Q);
+      k_qs_apply<R, K><<<Gn, kThreads, 0, s>>>(Q);
       newton = it + 1;
     }
     if (reaction) reaction[k] = reac;
-    k_qs_history<R><<<Ge, kThreads, 0, s>>>(Q);
+    k_qs_history<R><<<Ge, kThreads, 0, s>>>(Q.P);
     if (cudaGetLastError() != cudaSuccess) {
       cleanup();
       return fail(PFF_ERR_CUDA, "quasi-static kernel launch");
@@ -2678,18 +2691,28 @@ pff_status pff_backward_field(pff_mesh *m, pff_ckpt *c, const void *dL_dd, const
 }
 
 pff_status pff_qs_run(pff_mesh *m, const pff_state *st, const uint8_t *bc, int64_t incr0, int32_t nincr,
-                      double du, double newton_tol, int32_t newton_max, const pff_options *opt, double *reaction,
+                      double du, const pff_qs_options *qopt, const pff_options *opt, double *reaction,
                       int32_t *iters, pff_stream stream) {
-  if (!m || !st || !st->u || !st->d || !st->H || !bc || nincr < 0 || incr0 < 0 || !(newton_tol > 0) ||
-      newton_max < 1)
+  if (!m || !st || !st->u || !st->d || !st->H || !bc || nincr < 0 || incr0 < 0)
     return fail(PFF_ERR_ARG, "bad quasi-static arguments");
+  pff_qs_options qo;
+  if (qopt) {
+    qo = *qopt;
+  } else {
+    qo = pff_qs_options{1e-8, 25, PFF_QS_KRYLOV_FP32, 1e-4, 0.5, 100000, 0};
+  }
+  if (!(qo.newton_tol > 0) || qo.newton_max < 1 || qo.cg_max_it < 1 || !(qo.eta_min >= 0) ||
+      !(qo.eta_max >= qo.eta_min) || !(qo.eta_max < 1) ||
+      (qo.krylov != PFF_QS_KRYLOV_FP32 && qo.krylov != PFF_QS_KRYLOV_MESH))
+    return fail(PFF_ERR_ARG, "bad quasi-static options");
   if (!m->has_mat) return fail(PFF_ERR_ARG, "material not set");
   const pff_options o = defaults(opt);
   cudaStream_t s = (cudaStream_t)stream;
-  return m->prec == PFF_FP64 ? qs_run_t<double>(m, st, bc, incr0, nincr, du, newton_tol, newton_max, o, reaction,
-                                                iters, s)
-                             : qs_run_t<float>(m, st, bc, incr0, nincr, du, newton_tol, newton_max, o, reaction,
-                                               iters, s);
+  if (m->prec == PFF_FP64)
+    return qo.krylov == PFF_QS_KRYLOV_MESH
+               ? qs_run_t<double, double>(m, st, bc, incr0, nincr, du, qo, o, reaction, iters, s)
+               : qs_run_t<double, float>(m, st, bc, incr0, nincr, du, qo, o, reaction, iters, s);
+  return qs_run_t<float, float>(m, st, bc, incr0, nincr, du, qo, o, reaction, iters, s);
 }
 
 pff_status pff_mesh_set_gc_field(pff_mesh *m, const double *gc) {

@@ -6,6 +6,12 @@
 // the directional derivative of the internal force, element by element
 // through the split's tangent, gathered per node), then the history and
 // the damage solve follow as in a dynamic step.
+//
+// Two precisions: R, the mesh's (state u, d, H, the Newton residual, the
+// element tangents' evaluation, history and damage), and K, the Krylov
+// solve's (its vectors and the stored element tangents).  K = float under
+// an FP64 mesh is mixed-precision iterative refinement: each Newton step
+// solves in FP32 to a forcing tolerance and the FP64 residual corrects it.
 #pragma once
 #include "adjoint.cuh"
 
@@ -21,46 +27,68 @@ struct QsScalars {
   float alpha_f, beta_f;
 };
 
-template <typename R> struct QsParams {
-  typedef typename Params<R>::R2 R2;
-  typedef typename Params<R>::R4 R4;
-  Params<R> P;        // mesh, material, u, d (P.u is the displacement)
+// Per element, for the Krylov solve: node ids, the tangent T = A C_T
+// (row-major 3 x 3, tensor strain (e_xx, e_yy, e_xy) -> stress, times the
+// area) and the shape gradients (dphi0/dx, dphi0/dy, dphi1/dx, dphi1/dy).
+// 64 bytes in FP32, 128 in FP64.
+template <typename K> struct QRec;
+template <> struct __align__(64) QRec<float> {
+  int n0, n1, n2;
+  float t[9];
+  float g[4];
+};
+template <> struct __align__(128) QRec<double> {
+  int n0, n1, n2, pad;
+  double g[4];
+  double t[9];
+};
+
+template <typename K> struct QkParams {
+  typedef typename V<K>::T2 K2;
+  typedef typename V<K>::T4 K4;
+  int N, D;
+  const int *ell;     // incidence, ELL: entry k of node i at ell[k N + i] = (e << 2) | slot, or -1
+  QRec<K> *rec;       // Ne
   const uint8_t *bc;  // N flags
-  double U;           // prescribed u_y of the loaded nodes
-  R4 *pz;             // (p_x, z_x, p_y, z_y) per node
-  R2 *r, *q, *x, *dg; // residual, K_T p, the Newton step, Jacobi diagonal
-  R *ke;              // per element the 6 x 6 tangent K_e = A B^T C_T B (row-major,
-                      // dofs (x0, y0, x1, y1, x2, y2)), rebuilt each Newton step
+  K4 *pz;             // (p_x, z_x, p_y, z_y) per node
+  K2 *r, *q, *x, *dg; // residual, K_T p, the Newton step, Jacobi diagonal
+  K2 *fe;             // 3 Ne: per element and slot the force A B_a^T C_T B p_e
   QsScalars *qs;
+  double *part;       // per-block partial sums and the ticket of reduce_last
+  unsigned int *ticket;
   double tol;         // CG: |r| <= tol |r_0|
   int32_t max_it;
 };
 
-template <typename R> __device__ __forceinline__ bool qs_fx(const QsParams<R> &Q, int i) {
-  return Q.bc[i] & kQsFixX;
-}
-template <typename R> __device__ __forceinline__ bool qs_fy(const QsParams<R> &Q, int i) {
-  return Q.bc[i] & (kQsFixY | kQsLoaded);
-}
+template <typename R, typename K> struct QsParams {
+  Params<R> P;        // mesh, material, u, d (P.u is the displacement)
+  QkParams<K> I;      // the Krylov solve
+  double U;           // prescribed u_y of the loaded nodes
+};
+
+__device__ __forceinline__ bool qs_fx(const uint8_t *bc, int i) { return bc[i] & kQsFixX; }
+__device__ __forceinline__ bool qs_fy(const uint8_t *bc, int i) { return bc[i] & (kQsFixY | kQsLoaded); }
 
 // Dirichlet values: fixed components 0, loaded u_y = U.
-template <typename R>
-__global__ void __launch_bounds__(256) k_qs_bc(QsParams<R> Q) {
+template <typename R, typename K>
+__global__ void __launch_bounds__(256) k_qs_bc(QsParams<R, K> Q) {
+  const uint8_t *bc = Q.I.bc;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Q.P.N; i += gridDim.x * blockDim.x) {
     typename Params<R>::R2 u = Q.P.u[i];
-    if (qs_fx(Q, i)) u.x = R(0);
-    if (qs_fy(Q, i)) u.y = (Q.bc[i] & kQsLoaded) ? (R)Q.U : R(0);
+    if (qs_fx(bc, i)) u.x = R(0);
+    if (qs_fy(bc, i)) u.y = (bc[i] & kQsLoaded) ? (R)Q.U : R(0);
     Q.P.u[i] = u;
   }
 }
 
-// Residual r = -f_int(u; d) on the free dofs (0 on fixed ones), with
-// |r_free|^2, |f_int|^2 over all dofs and the reaction sum_loaded f_y;
-// zeroes the Newton step x.
-template <typename R>
-__global__ void __launch_bounds__(256) k_qs_residual(QsParams<R> Q) {
+// Residual r = -f_int(u; d) on the free dofs (0 on fixed ones), evaluated
+// in R and stored in K, with |r_free|^2, |f_int|^2 over all dofs and the
+// reaction sum_loaded f_y; zeroes the Newton step x.
+template <typename R, typename K>
+__global__ void __launch_bounds__(256) k_qs_residual(QsParams<R, K> Q) {
   typedef Acc<R> AC;
   const Params<R> &P = Q.P;
+  const uint8_t *bc = Q.I.bc;
   typename AC::T vals[3] = {AC::zero(), AC::zero(), AC::zero()};
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.N; i += gridDim.x * blockDim.x) {
     R fx = 0, fy = 0;
@@ -72,56 +100,32 @@ __global__ void __launch_bounds__(256) k_qs_residual(QsParams<R> Q) {
       fx = radd(fx, ex);
       fy = radd(fy, ey);
     }
-    typename Params<R>::R2 r;
-    r.x = qs_fx(Q, i) ? R(0) : -fx;
-    r.y = qs_fy(Q, i) ? R(0) : -fy;
-    Q.r[i] = r;
-    typename Params<R>::R2 z;
-    z.x = R(0);
-    z.y = R(0);
-    Q.x[i] = z;
-    const R s = P.rscale;
-    vals[0] = AC::add(vals[0], AC::add(AC::prod(s * r.x, s * r.x), AC::prod(s * r.y, s * r.y)));
-    vals[1] = AC::add(vals[1], AC::add(AC::prod(s * fx, s * fx), AC::prod(s * fy, s * fy)));
-    if (Q.bc[i] & kQsLoaded) vals[2] = AC::add(vals[2], AC::prod(fy, R(1)));
+    const R rx = qs_fx(bc, i) ? R(0) : -fx, ry = qs_fy(bc, i) ? R(0) : -fy;
+    typename V<K>::T2 r, z;
+    r.x = (K)rx;
+    r.y = (K)ry;
+    z.x = K(0);
+    z.y = K(0);
+    Q.I.r[i] = r;
+    Q.I.x[i] = z;
+    vals[0] = AC::add(vals[0], AC::add(AC::prod(rx, rx), AC::prod(ry, ry)));
+    vals[1] = AC::add(vals[1], AC::add(AC::prod(fx, fx), AC::prod(fy, fy)));
+    if (bc[i] & kQsLoaded) vals[2] = AC::add(vals[2], AC::prod(fy, R(1)));
   }
   __shared__ double tot[3];
   if (reduce_last<R, 3>(vals, P.part, P.ticket, tot) && threadIdx.x == 0) {
-    Q.qs->rr = tot[0];
-    Q.qs->fsq = tot[1];
-    Q.qs->reaction = tot[2];
+    Q.I.qs->rr = tot[0];
+    Q.I.qs->fsq = tot[1];
+    Q.I.qs->reaction = tot[2];
   }
 }
 
-// The element's tangent stress along a strain direction de:
-// dsigma = g(dbar) dsigma+[de] + dsigma-[de] at the element's strain.
-template <typename R>
-__device__ __forceinline__ void qs_dsigma(const Params<R> &P, R exx, R eyy, R exy, R g, const R (&de)[3],
-                                          R (&ds)[3]) {
-  R dsp[3], dsm[3];
-  split_tangent(P, exx, eyy, exy, de, dsp, dsm);
-  ds[0] = g * dsp[0] + dsm[0];
-  ds[1] = g * dsp[1] + dsm[1];
-  ds[2] = g * dsp[2] + dsm[2];
-}
-
-// Strain of the element at node values of a field (p_new of the CG: own
-// node pc, neighbours rebuilt from (p, z) with beta).
-template <typename R>
-__device__ __forceinline__ typename Params<R>::R2 qs_pnew(const QsParams<R> &Q, int j, R beta) {
-  const typename Params<R>::R4 v = Q.pz[j];
-  typename Params<R>::R2 o;
-  o.x = fma(beta, v.x, v.y);
-  o.y = fma(beta, v.z, v.w);
-  return o;
-}
-
 // Element tangents at the current u and d (constant during the CG of a
-// Newton step): column (b, c) of K_e is A B^T dsigma[B e_(b,c)] with
-// dsigma = g(dbar) dsigma+ + dsigma- (the split's tangent); the Hessian of
-// A psi, so K_e is symmetric.
-template <typename R>
-__global__ void __launch_bounds__(256) k_qs_elem_tangent(QsParams<R> Q) {
+// Newton step): column j of C_T is dsigma[e_j] = g(dbar) dsigma+[e_j] +
+// dsigma-[e_j] (the split's tangent, linear in the strain direction), for
+// the unit tensor strains e_j; stored as A C_T with the gradients.
+template <typename R, typename K>
+__global__ void __launch_bounds__(256) k_qs_elem_tangent(QsParams<R, K> Q) {
   typedef typename Params<R>::R4 R4;
   const Params<R> &P = Q.P;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < P.Ne; e += gridDim.x * blockDim.x) {
@@ -133,105 +137,190 @@ __global__ void __launch_bounds__(256) k_qs_elem_tangent(QsParams<R> Q) {
     elem_strain(P, G, t, exx, eyy, exy);
     const R db = (P.d[t.x] + P.d[t.y] + P.d[t.z]) * (R(1) / R(3));
     const R g = (R(1) - db) * (R(1) - db) + P.eta;
-    R gxs[3], gys[3];
-    for (int b = 0; b < 3; ++b) slot_grad<R>(G, b, gxs[b], gys[b]);
-    R *K = Q.ke + (size_t)e * 36;
-    for (int b = 0; b < 3; ++b)
-      for (int c = 0; c < 2; ++c) {
-        const R gx = gxs[b], gy = gys[b];
-        const R de[3] = {c == 0 ? gx : R(0), c == 1 ? gy : R(0), R(0.5) * (c == 0 ? gy : gx)};
-        R ds[3];
-        qs_dsigma(P, exx, eyy, exy, g, de, ds);
-        const int col = 2 * b + c;
-        for (int a = 0; a < 3; ++a) {
-          K[(2 * a) * 6 + col] = A * (ds[0] * gxs[a] + ds[2] * gys[a]);
-          K[(2 * a + 1) * 6 + col] = A * (ds[2] * gxs[a] + ds[1] * gys[a]);
-        }
-      }
+    QRec<K> o;
+    o.n0 = t.x;
+    o.n1 = t.y;
+    o.n2 = t.z;
+    o.g[0] = (K)G.x;
+    o.g[1] = (K)G.y;
+    o.g[2] = (K)G.z;
+    o.g[3] = (K)G.w;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const R de[3] = {j == 0 ? R(1) : R(0), j == 1 ? R(1) : R(0), j == 2 ? R(1) : R(0)};
+      R dsp[3], dsm[3];
+      split_tangent(P, exx, eyy, exy, de, dsp, dsm);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) o.t[3 * i + j] = (K)(A * (g * dsp[i] + dsm[i]));
+    }
+    Q.I.rec[e] = o;
   }
 }
 
-// Jacobi diagonal of K_T(u) (one unit displacement per dof through the
-// tangent), z = r / diag, p = z; rho = r.z and |r_0|.
-template <typename R>
-__global__ void __launch_bounds__(256) k_qs_setup(QsParams<R> Q) {
-  typedef Acc<R> AC;
-  typedef typename Params<R>::R4 R4;
-  const Params<R> &P = Q.P;
-  typename AC::T vals[1] = {AC::zero()};
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.N; i += gridDim.x * blockDim.x) {
-    R dx = 0, dy = 0;
-    for (int k = 0; k < P.D; ++k) {
-      const int en = __ldg(&P.ell[(size_t)k * P.N + i]);
-      if (en < 0) continue;
-      const int e = en >> 2, a = en & 3;
-      const R *K = Q.ke + (size_t)e * 36;
-      dx = radd(dx, K[(2 * a) * 6 + 2 * a]);
-      dy = radd(dy, K[(2 * a + 1) * 6 + 2 * a + 1]);
+template <typename K>
+__device__ __forceinline__ void qrec_load(const QRec<K> *rp, int &n0, int &n1, int &n2, K (&t)[9], K (&g)[4]) {
+  if (sizeof(K) == 4) {
+    const float4 *f = reinterpret_cast<const float4 *>(rp);
+    const float4 a = __ldg(f), b = __ldg(f + 1), c = __ldg(f + 2), d = __ldg(f + 3);
+    n0 = __float_as_int(a.x);
+    n1 = __float_as_int(a.y);
+    n2 = __float_as_int(a.z);
+    t[0] = a.w; t[1] = b.x; t[2] = b.y; t[3] = b.z; t[4] = b.w;
+    t[5] = c.x; t[6] = c.y; t[7] = c.z; t[8] = c.w;
+    g[0] = d.x; g[1] = d.y; g[2] = d.z; g[3] = d.w;
+  } else {
+    const int4 n = __ldg(reinterpret_cast<const int4 *>(rp));
+    n0 = n.x;
+    n1 = n.y;
+    n2 = n.z;
+    const double2 *f = reinterpret_cast<const double2 *>(rp) + 1;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const double2 v = __ldg(f + k);
+      g[2 * k] = (K)v.x;
+      g[2 * k + 1] = (K)v.y;
     }
-    const typename Params<R>::R2 r = Q.r[i];
-    typename Params<R>::R2 dg;
-    dg.x = (qs_fx(Q, i) || dx == R(0)) ? R(1) : dx;
-    dg.y = (qs_fy(Q, i) || dy == R(0)) ? R(1) : dy;
-    Q.dg[i] = dg;
-    R4 pz;
-    pz.x = R(0);
-    pz.y = r.x / dg.x;
-    pz.z = R(0);
-    pz.w = r.y / dg.y;
-    Q.pz[i] = pz;
-    const R s = P.rscale;
-    vals[0] = AC::add(vals[0], AC::add(AC::prod(s * r.x, pz.y), AC::prod(s * r.y, pz.w)));
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const double2 v = __ldg(f + 2 + k);
+      t[2 * k] = (K)v.x;
+      t[2 * k + 1] = (K)v.y;
+    }
+    t[8] = (K)__ldg(reinterpret_cast<const double *>(f + 6));
   }
-  __shared__ double tot[1];
-  if (reduce_last<R, 1>(vals, P.part, P.ticket, tot) && threadIdx.x == 0) {
-    QsScalars &S = *Q.qs;
+}
+
+// Node force of slot a from the element tangent applied to a strain:
+// A B_a^T C_T de.
+template <typename K>
+__device__ __forceinline__ void qs_slot_force(const K (&t)[9], const K (&g)[4], int a, const K (&de)[3], K &fx,
+                                              K &fy) {
+  const K s0 = t[0] * de[0] + t[1] * de[1] + t[2] * de[2];
+  const K s1 = t[3] * de[0] + t[4] * de[1] + t[5] * de[2];
+  const K s2 = t[6] * de[0] + t[7] * de[1] + t[8] * de[2];
+  const K gx = a == 0 ? g[0] : (a == 1 ? g[2] : -(g[0] + g[2]));
+  const K gy = a == 0 ? g[1] : (a == 1 ? g[3] : -(g[1] + g[3]));
+  fx = s0 * gx + s2 * gy;
+  fy = s2 * gx + s1 * gy;
+}
+
+// p_new = z + beta p of a node, rebuilt from the stored (p, z).
+template <typename K>
+__device__ __forceinline__ typename V<K>::T2 qs_pnew(const QkParams<K> &I, int j, K beta) {
+  const typename V<K>::T4 v = I.pz[j];
+  typename V<K>::T2 o;
+  o.x = fma(beta, v.x, v.y);
+  o.y = fma(beta, v.z, v.w);
+  return o;
+}
+
+// Jacobi diagonal of K_T (one unit displacement per dof through the stored
+// tangents), z = r / diag, p = 0 (so that p_new = z); rho = r.z and |r_0|.
+template <typename K>
+__global__ void __launch_bounds__(256) k_qs_setup(QkParams<K> I) {
+  typedef Acc<K> AC;
+  typename AC::T vals[2] = {AC::zero(), AC::zero()};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < I.N; i += gridDim.x * blockDim.x) {
+    K dx = 0, dy = 0;
+    for (int k = 0; k < I.D; ++k) {
+      const int en = __ldg(&I.ell[(size_t)k * I.N + i]);
+      if (en < 0) continue;
+      const int a = en & 3;
+      int n0, n1, n2;
+      K t[9], g[4];
+      qrec_load(I.rec + (en >> 2), n0, n1, n2, t, g);
+      const K gx = a == 0 ? g[0] : (a == 1 ? g[2] : -(g[0] + g[2]));
+      const K gy = a == 0 ? g[1] : (a == 1 ? g[3] : -(g[1] + g[3]));
+      const K ex[3] = {gx, K(0), K(0.5) * gy}, ey[3] = {K(0), gy, K(0.5) * gx};
+      K fx, fy, hx, hy;
+      qs_slot_force(t, g, a, ex, fx, fy);
+      qs_slot_force(t, g, a, ey, hx, hy);
+      dx = radd(dx, fx);
+      dy = radd(dy, hy);
+    }
+    const typename V<K>::T2 r = I.r[i];
+    typename V<K>::T2 dg;
+    dg.x = (qs_fx(I.bc, i) || !(dx > K(0))) ? K(1) : dx;
+    dg.y = (qs_fy(I.bc, i) || !(dy > K(0))) ? K(1) : dy;
+    I.dg[i] = dg;
+    typename V<K>::T4 pz;
+    pz.x = K(0);
+    pz.y = r.x / dg.x;
+    pz.z = K(0);
+    pz.w = r.y / dg.y;
+    I.pz[i] = pz;
+    vals[0] = AC::add(vals[0], AC::add(AC::prod(r.x, pz.y), AC::prod(r.y, pz.w)));
+    vals[1] = AC::add(vals[1], AC::add(AC::prod(r.x, r.x), AC::prod(r.y, r.y)));
+  }
+  __shared__ double tot[2];
+  if (reduce_last<K, 2>(vals, I.part, I.ticket, tot) && threadIdx.x == 0) {
+    QsScalars &S = *I.qs;
     S.rho = tot[0];
-    S.rr0 = S.rr;
+    S.rr0 = tot[1];
     S.beta = 0.0;
     S.beta_f = 0.f;
     S.iters = 0;
     S.status = 0;
-    S.done = (S.rr == 0.0) ? 1 : 0;
+    S.done = (tot[1] == 0.0) ? 1 : 0;
   }
 }
 
-// q = K_T(u) p_new on the free dofs (p_new = z + beta p, rebuilt for the
-// neighbours), p_new . q -> alpha.  A no-op once the solve is done.
-template <typename R>
-__global__ void __launch_bounds__(256) k_qs_matvec(QsParams<R> Q) {
-  typedef Acc<R> AC;
-  typedef typename Params<R>::R2 R2;
-  typedef typename Params<R>::R4 R4;
-  const Params<R> &P = Q.P;
-  if (Q.qs->done) return;
-  const R beta = sizeof(R) == 4 ? (R)Q.qs->beta_f : (R)Q.qs->beta;
-  typename AC::T vals[1] = {AC::zero()};
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.N; i += gridDim.x * blockDim.x) {
-    R qx = 0, qy = 0;
-    for (int k = 0; k < P.D; ++k) {
-      const int en = __ldg(&P.ell[(size_t)k * P.N + i]);
-      if (en < 0) continue;
-      const int e = en >> 2, a = en & 3;
-      const ERec<R> &rc = P.rec[e];
-      const R2 p0 = qs_pnew(Q, rc.n0, beta), p1 = qs_pnew(Q, rc.n1, beta), p2 = qs_pnew(Q, rc.n2, beta);
-      const R *K = Q.ke + (size_t)e * 36 + 12 * a;  // rows 2a, 2a+1
-      qx = radd(qx, K[0] * p0.x + K[1] * p0.y + K[2] * p1.x + K[3] * p1.y + K[4] * p2.x + K[5] * p2.y);
-      qy = radd(qy, K[6] * p0.x + K[7] * p0.y + K[8] * p1.x + K[9] * p1.y + K[10] * p2.x + K[11] * p2.y);
+// Element pass of q = K_T p_new: per element (threads over consecutive
+// records, so the record loads coalesce) the strain of p_new (rebuilt from
+// (p, z) with beta at the three nodes), the stress T de and the three slot
+// forces.  A no-op once the solve is done.
+template <typename K>
+__global__ void __launch_bounds__(256) k_qs_elem_apply(QkParams<K> I, int Ne) {
+  typedef typename V<K>::T2 K2;
+  if (I.qs->done) return;
+  const K beta = sizeof(K) == 4 ? (K)I.qs->beta_f : (K)I.qs->beta;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < Ne; e += gridDim.x * blockDim.x) {
+    int n0, n1, n2;
+    K t[9], g[4];
+    qrec_load(I.rec + e, n0, n1, n2, t, g);
+    const K2 p0 = qs_pnew(I, n0, beta), p1 = qs_pnew(I, n1, beta), p2 = qs_pnew(I, n2, beta);
+    const K ax0 = p0.x - p2.x, ax1 = p1.x - p2.x, ay0 = p0.y - p2.y, ay1 = p1.y - p2.y;
+    const K de[3] = {g[0] * ax0 + g[2] * ax1, g[1] * ay0 + g[3] * ay1,
+                     K(0.5) * (g[1] * ax0 + g[3] * ax1 + g[0] * ay0 + g[2] * ay1)};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      K2 f;
+      qs_slot_force(t, g, a, de, f.x, f.y);
+      I.fe[(size_t)3 * e + a] = f;
     }
-    if (qs_fx(Q, i)) qx = R(0);
-    if (qs_fy(Q, i)) qy = R(0);
-    R2 q;
+  }
+}
+
+// Node pass: q_i = sum of its slot forces in ascending element order, 0 on
+// the fixed dofs; p_new . q -> alpha.  A no-op once the solve is done.
+template <typename K>
+__global__ void __launch_bounds__(256) k_qs_matvec(QkParams<K> I) {
+  typedef Acc<K> AC;
+  typedef typename V<K>::T2 K2;
+  if (I.qs->done) return;
+  const K beta = sizeof(K) == 4 ? (K)I.qs->beta_f : (K)I.qs->beta;
+  typename AC::T vals[1] = {AC::zero()};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < I.N; i += gridDim.x * blockDim.x) {
+    K qx = 0, qy = 0;
+    for (int k = 0; k < I.D; ++k) {
+      const int en = __ldg(&I.ell[(size_t)k * I.N + i]);
+      if (en < 0) continue;
+      const K2 f = I.fe[(size_t)3 * (en >> 2) + (en & 3)];
+      qx = radd(qx, f.x);
+      qy = radd(qy, f.y);
+    }
+    if (qs_fx(I.bc, i)) qx = K(0);
+    if (qs_fy(I.bc, i)) qy = K(0);
+    K2 q;
     q.x = qx;
     q.y = qy;
-    Q.q[i] = q;
-    const R2 pn = qs_pnew(Q, i, beta);
-    const R s = P.rscale;
-    vals[0] = AC::add(vals[0], AC::add(AC::prod(pn.x, s * qx), AC::prod(pn.y, s * qy)));
+    I.q[i] = q;
+    const K2 pn = qs_pnew(I, i, beta);
+    vals[0] = AC::add(vals[0], AC::add(AC::prod(pn.x, qx), AC::prod(pn.y, qy)));
   }
   __shared__ double tot[1];
-  if (reduce_last<R, 1>(vals, P.part, P.ticket, tot) && threadIdx.x == 0) {
-    QsScalars &S = *Q.qs;
+  if (reduce_last<K, 1>(vals, I.part, I.ticket, tot) && threadIdx.x == 0) {
+    QsScalars &S = *I.qs;
     S.pq = tot[0];
     S.alpha = tot[0] != 0.0 ? S.rho / tot[0] : 0.0;
     S.alpha_f = (float)S.alpha;
@@ -240,48 +329,44 @@ __global__ void __launch_bounds__(256) k_qs_matvec(QsParams<R> Q) {
 
 // x += alpha p, r -= alpha q, z = r / diag, (p, z) stored; |r|^2, r.z ->
 // beta and the stop test |r| <= tol |r_0|.
-template <typename R>
-__global__ void __launch_bounds__(256) k_qs_update(QsParams<R> Q) {
-  typedef Acc<R> AC;
-  typedef typename Params<R>::R2 R2;
-  typedef typename Params<R>::R4 R4;
-  const Params<R> &P = Q.P;
-  if (Q.qs->done) return;
-  const R beta = sizeof(R) == 4 ? (R)Q.qs->beta_f : (R)Q.qs->beta;
-  const R alpha = sizeof(R) == 4 ? (R)Q.qs->alpha_f : (R)Q.qs->alpha;
+template <typename K>
+__global__ void __launch_bounds__(256) k_qs_update(QkParams<K> I) {
+  typedef Acc<K> AC;
+  typedef typename V<K>::T2 K2;
+  if (I.qs->done) return;
+  const K beta = sizeof(K) == 4 ? (K)I.qs->beta_f : (K)I.qs->beta;
+  const K alpha = sizeof(K) == 4 ? (K)I.qs->alpha_f : (K)I.qs->alpha;
   typename AC::T vals[2] = {AC::zero(), AC::zero()};
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.N; i += gridDim.x * blockDim.x) {
-    const R2 pn = qs_pnew(Q, i, beta), q = Q.q[i], dg = Q.dg[i];
-    R2 x = Q.x[i], r = Q.r[i];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < I.N; i += gridDim.x * blockDim.x) {
+    const K2 pn = qs_pnew(I, i, beta), q = I.q[i], dg = I.dg[i];
+    K2 x = I.x[i], r = I.r[i];
     x.x = fma(alpha, pn.x, x.x);
     x.y = fma(alpha, pn.y, x.y);
     r.x = fma(-alpha, q.x, r.x);
     r.y = fma(-alpha, q.y, r.y);
-    if (qs_fx(Q, i)) r.x = R(0);
-    if (qs_fy(Q, i)) r.y = R(0);
-    Q.x[i] = x;
-    Q.r[i] = r;
-    R4 pz;
+    if (qs_fx(I.bc, i)) r.x = K(0);
+    if (qs_fy(I.bc, i)) r.y = K(0);
+    I.x[i] = x;
+    I.r[i] = r;
+    typename V<K>::T4 pz;
     pz.x = pn.x;
     pz.y = r.x / dg.x;
     pz.z = pn.y;
     pz.w = r.y / dg.y;
-    Q.pz[i] = pz;
-    const R s = P.rscale;
-    vals[0] = AC::add(vals[0], AC::add(AC::prod(s * r.x, s * r.x), AC::prod(s * r.y, s * r.y)));
-    vals[1] = AC::add(vals[1], AC::add(AC::prod(s * r.x, pz.y), AC::prod(s * r.y, pz.w)));
+    I.pz[i] = pz;
+    vals[0] = AC::add(vals[0], AC::add(AC::prod(r.x, r.x), AC::prod(r.y, r.y)));
+    vals[1] = AC::add(vals[1], AC::add(AC::prod(r.x, pz.y), AC::prod(r.y, pz.w)));
   }
   __shared__ double tot[2];
-  if (reduce_last<R, 2>(vals, P.part, P.ticket, tot) && threadIdx.x == 0) {
-    QsScalars &S = *Q.qs;
+  if (reduce_last<K, 2>(vals, I.part, I.ticket, tot) && threadIdx.x == 0) {
+    QsScalars &S = *I.qs;
     S.iters += 1;
-    S.rr = tot[0];
     if (!(tot[0] == tot[0]) || isinf(tot[0])) {
       S.status = kStNonfinite;
       S.done = 1;
-    } else if (S.pq == 0.0 || sqrt(tot[0]) <= Q.tol * sqrt(S.rr0)) {
+    } else if (S.pq == 0.0 || sqrt(tot[0]) <= I.tol * sqrt(S.rr0)) {
       S.done = 1;
-    } else if (S.iters >= Q.max_it) {
+    } else if (S.iters >= I.max_it) {
       S.status = kStNotConverged;
       S.done = 1;
     }
@@ -292,13 +377,13 @@ __global__ void __launch_bounds__(256) k_qs_update(QsParams<R> Q) {
 }
 
 // u += x on the free dofs.
-template <typename R>
-__global__ void __launch_bounds__(256) k_qs_apply(QsParams<R> Q) {
+template <typename R, typename K>
+__global__ void __launch_bounds__(256) k_qs_apply(QsParams<R, K> Q) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Q.P.N; i += gridDim.x * blockDim.x) {
     typename Params<R>::R2 u = Q.P.u[i];
-    const typename Params<R>::R2 x = Q.x[i];
-    if (!qs_fx(Q, i)) u.x += x.x;
-    if (!qs_fy(Q, i)) u.y += x.y;
+    const typename V<K>::T2 x = Q.I.x[i];
+    if (!qs_fx(Q.I.bc, i)) u.x += (R)x.x;
+    if (!qs_fy(Q.I.bc, i)) u.y += (R)x.y;
     Q.P.u[i] = u;
   }
 }
@@ -306,9 +391,8 @@ __global__ void __launch_bounds__(256) k_qs_apply(QsParams<R> Q) {
 // History H = max(H, psi+(u)) per element (the owner-entry rule of the
 // dynamic step, element by element).
 template <typename R>
-__global__ void __launch_bounds__(256) k_qs_history(QsParams<R> Q) {
+__global__ void __launch_bounds__(256) k_qs_history(Params<R> P) {
   typedef typename Params<R>::R4 R4;
-  const Params<R> &P = Q.P;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < P.Ne; e += gridDim.x * blockDim.x) {
     int4 t;
     R A;

@@ -74,3 +74,35 @@ def test_subcycling_limit_matches_oracle(orc):
     bad = pff.pff_material(0.0, 0.2, 2450.0, 3.0, 1e-3, 1e-7, 2, 0, 0, 0)
     assert pff._lib.pff_subcycling_limit(C.byref(bad), None, None) == 1
 
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """Every struct the binding passes by pointer has the header's size and
+    field offsets (a C program compiled against include/pff.h prints them)."""
+    import shutil
+    import subprocess
+    import paper_2606_23458_b300 as pff
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"pff_material": pff.pff_material, "pff_options": pff.pff_options,
+               "pff_state": pff.pff_state, "pff_qs_options": pff.pff_qs_options,
+               "pff_plate": pff.pff_plate}
+    lines = ['#include <stdio.h>', '#include "pff.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} size %zu\\n", sizeof({name}));')
+        for f, _ in cls._fields_:
+            lines.append(f'printf("{name} {f} %zu\\n", offsetof({name}, {f}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for ln in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        s, f, v = ln.split()
+        got[(s, f)] = int(v)
+    for name, cls in structs.items():
+        assert got[(name, "size")] == C.sizeof(cls), name
+        for f, _ in cls._fields_:
+            assert got[(name, f)] == getattr(cls, f).offset, (name, f)

@@ -32,23 +32,23 @@ def _sent(nx, ny, notch=True, rollers=False):
     return p, bc
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_uniaxial_bar_reaction(pff, prec):
+@pytest.mark.parametrize("prec,krylov", [("fp64", "fp32"), ("fp64", "mesh"), ("fp32", "fp32")])
+def test_uniaxial_bar_reaction(pff, prec, krylov):
     p, bc = _sent(6, 10, notch=False, rollers=True)
     mat = dict(S.material(2 * p["h"], split="amor"), E=210e9, nu=0.3, Gc=1e15)
     m = pff.Mesh.from_plate(p, precision=prec)
     m.set_material(mat, 0.5)
     st = m.new_state()
     du = 1e-7
-    r = m.qs_run(st, bc, 3, du, newton_tol=1e-10 if prec == "fp64" else 1e-5)
+    r = m.qs_run(st, bc, 3, du, newton_tol=1e-10 if prec == "fp64" else 1e-5, krylov=krylov)
     eps = du * np.arange(1, 4) / 2e-3
     want = (1 + mat["eta"]) * mat["E"] / (1 - mat["nu"] ** 2) * eps * 1e-3
     tol = 1e-9 if prec == "fp64" else 1e-5
     assert np.allclose(r["reaction"], want, rtol=tol), (r["reaction"], want)
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-7), ("fp32", 2e-3)])
-def test_sent_increments_match_oracle(orc, pff, prec, tol):
+@pytest.mark.parametrize("prec,krylov,tol", [("fp64", "fp32", 1e-7), ("fp64", "mesh", 1e-7), ("fp32", "fp32", 2e-3)])
+def test_sent_increments_match_oracle(orc, pff, prec, krylov, tol):
     p, bc = _sent(16, 16)
     mat = dict(S.material(2 * p["h"], split="amor"), E=210e9, nu=0.3, Gc=2700.0)
     om = orc.Mesh.from_plate(p)
@@ -59,13 +59,24 @@ def test_sent_increments_match_oracle(orc, pff, prec, tol):
     m.set_material(mat, 0.5)
     st = m.new_state()
     opts = pff.options(cg_tol=1e-12 if prec == "fp64" else 1e-8)
-    r = m.qs_run(st, bc, nincr, du, newton_tol=1e-10 if prec == "fp64" else 1e-5, opts=opts)
+    q = pff.qs_options(newton_tol=1e-10 if prec == "fp64" else 1e-5, krylov=krylov)
+    r = m.qs_run(st, bc, nincr, du, qopts=q, opts=opts)
     assert np.allclose(r["reaction"], ro["reaction"], rtol=tol), (r["reaction"], ro["reaction"])
     d = to_np(st["d"])
     assert np.abs(d - ost["d"]).max() <= 10 * tol
     assert np.all(r["iters"][:, 0] >= 1) and np.all(r["iters"][:, 1] > 0)
     # split over two calls: the same increments
     st2 = m.new_state()
-    a = m.qs_run(st2, bc, 3, du, newton_tol=1e-10 if prec == "fp64" else 1e-5, opts=opts)
-    b = m.qs_run(st2, bc, nincr - 3, du, incr0=3, newton_tol=1e-10 if prec == "fp64" else 1e-5, opts=opts)
+    a = m.qs_run(st2, bc, 3, du, qopts=q, opts=opts)
+    b = m.qs_run(st2, bc, nincr - 3, du, incr0=3, qopts=q, opts=opts)
     assert np.allclose(np.concatenate([a["reaction"], b["reaction"]]), r["reaction"], rtol=1e-12)
+
+
+def test_options_are_checked(pff):
+    p, bc = _sent(4, 4)
+    m = pff.Mesh.from_plate(p, precision="fp64")
+    m.set_material(dict(S.material(2 * p["h"], split="amor"), E=210e9, nu=0.3, Gc=2700.0), 0.5)
+    st = m.new_state()
+    for kw in (dict(newton_tol=0.0), dict(eta_min=0.6), dict(eta_max=1.0), dict(newton_max=0)):
+        with pytest.raises(pff.PffError):
+            m.qs_run(st, bc, 1, 1e-7, **kw)
