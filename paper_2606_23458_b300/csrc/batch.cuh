@@ -195,6 +195,7 @@ __global__ void __launch_bounds__(256) kb_rhs(Params<R> P, Batch B) {
   if (i < P.N) {
     if (P.flags[i] & kNotch) {
       rhs_notch_node(Q, i);
+      drec_notch_node(Q, i);
     } else {
       R bi = 0, dg = 0, ax = 0, a1 = 0;
       for (int k = 0; k < P.D; k += U) {

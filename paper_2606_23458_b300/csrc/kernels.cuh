@@ -60,6 +60,24 @@ template <> struct __align__(64) ERec<double> {
   dbl4 g;
 };
 
+// Damage operator record of an element for one solve (the history is fixed
+// while the damage CG runs): node ids, the off-diagonal stiffness weights
+// w_ab = kappa_e A_e grad(phi_a) . grad(phi_b) and the mass coefficient
+// mA = c_e A_e / 12 (Eqs. damage_pde_at2 / damage_pde_at1, consistent mass).
+// Because the rows of the element stiffness sum to zero, row a of the
+// element operator applied to x is
+//   w_ab (x_b - x_a) + w_ac (x_c - x_a) + mA (2 x_a + x_b + x_c).
+// 32 bytes (one sector) in FP32, 64 in FP64.
+template <typename R> struct DRec;
+template <> struct __align__(32) DRec<float> {
+  int n0, n1, n2;
+  float w01, w02, w12, mA, pad;
+};
+template <> struct __align__(64) DRec<double> {
+  int n0, n1, n2, pad;
+  double w01, w02, w12, mA;
+};
+
 // Scalars of one damage solve, living in device memory.  Dot products are
 // of (rscale r), (rscale q) with z, p, so every ratio the solver uses is
 // unchanged by the power-of-two scale.
@@ -119,6 +137,9 @@ template <typename R> struct Params {
   R lam, mu, K, eta, cz;
   int32_t split, model;
   R kappa;      // damage diffusion coefficient (Gc l0 or 3/4 Gc l0)
+  DRec<R> *drec; // damage records of the current solve (nullable: the
+                 // operator is rebuilt from the geometry and H per entry);
+                 // written by the right-hand-side kernels, read by the matvec
   const R *gcs; // per-element toughness field as Gc_e / Gc (nullable: uniform);
                 // kappa, cbase and wbase are linear in Gc and scale with it
   R cbase;      // reaction: c_e = cbase + 2 H_e
@@ -627,6 +648,70 @@ __device__ __forceinline__ R elem_row(const R4 &G, int a, R kA, R mA, R x0, R x1
   return kA * (gx * dx + gy * dy) + mA * (xa + x0 + x1 + x2);
 }
 
+// The damage record of an element from its geometry and coefficients.
+template <typename R>
+__device__ __forceinline__ DRec<R> make_drec(const int4 &t, const typename Params<R>::R4 &G, R kA, R mA) {
+  const R g2x = -(G.x + G.z), g2y = -(G.y + G.w);
+  DRec<R> o;
+  o.n0 = t.x;
+  o.n1 = t.y;
+  o.n2 = t.z;
+  o.w01 = kA * (G.x * G.z + G.y * G.w);
+  o.w02 = kA * (G.x * g2x + G.y * g2y);
+  o.w12 = kA * (G.z * g2x + G.w * g2y);
+  o.mA = mA;
+  return o;
+}
+
+template <typename R>
+__device__ __forceinline__ void load_drec(const Params<R> &P, int e, int &n0, int &n1, int &n2, R &w01, R &w02,
+                                          R &w12, R &mA) {
+  const DRec<R> *rp = P.drec + e;
+  if constexpr (sizeof(R) == 4) {
+    unsigned v0, v1, v2, v3, v4, v5, v6, v7;
+    asm("ld.global.nc.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=r"(v0), "=r"(v1), "=r"(v2), "=r"(v3), "=r"(v4), "=r"(v5), "=r"(v6), "=r"(v7)
+        : "l"(rp));
+    (void)v7;
+    n0 = (int)v0;
+    n1 = (int)v1;
+    n2 = (int)v2;
+    w01 = __uint_as_float(v3);
+    w02 = __uint_as_float(v4);
+    w12 = __uint_as_float(v5);
+    mA = __uint_as_float(v6);
+  } else {
+    const int4 n = __ldg(reinterpret_cast<const int4 *>(rp));
+    const double2 a = __ldg(reinterpret_cast<const double2 *>(rp) + 1);
+    const double2 b = __ldg(reinterpret_cast<const double2 *>(rp) + 2);
+    n0 = n.x;
+    n1 = n.y;
+    n2 = n.z;
+    w01 = (R)a.x;
+    w02 = (R)a.y;
+    w12 = (R)b.x;
+    mA = (R)b.y;
+  }
+}
+
+// Damage records of every element from the geometry and the history P.Hr
+// (element-parallel; the forward's right-hand-side kernels write them as a
+// by-product instead).
+template <typename R>
+__global__ void __launch_bounds__(256) k_drec_build(Params<R> P) {
+  typedef typename Params<R>::R4 R4;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < P.Ne; e += gridDim.x * blockDim.x) {
+    int4 t;
+    R A;
+    R4 G;
+    load_elem(P, e, t, A, G);
+    const R sg = gc_scale(P, e);
+    const R kA = (P.kappa * sg) * A;
+    const R mA = (P.cbase * sg + R(2) * P.Hr[e]) * A * (R(1) / R(12));
+    P.drec[e] = make_drec<R>(t, G, kA, mA);
+  }
+}
+
 // Right-hand side, Jacobi diagonal and lifted initial residual of the
 // damage problem (AT2: Eq. damage_pde_at2; AT1: Eq. damage_pde_at1), one
 // incidence entry's share: (b, diag, (A x0)_a, (A 1_D)_a) with
@@ -649,6 +734,7 @@ __device__ __forceinline__ typename Params<R>::R4 rhs_entry(const Params<R> &P, 
   const R kA = (P.kappa * sg) * A, mA = c * A * (R(1) / R(12));
   R gx, gy;
   slot_grad<R>(G, a, gx, gy);
+  if (a == 0 && P.drec) P.drec[e] = make_drec<R>(t, G, kA, mA);
   R4 o;
   o.x = w * A * (R(1) / R(3));
   o.y = kA * (gx * gx + gy * gy) + R(2) * mA;
@@ -750,6 +836,17 @@ __global__ void __launch_bounds__(256) k_dmg_rhs_ep(Params<R> P) {
   if (reduce_last<R, 3>(vals, P.part, P.ticket, tot) && threadIdx.x == 0) rhs_finish(P, tot);
 }
 
+// A notch node has no row, but the elements it holds in slot 0 still need
+// their damage records (written by rhs_entry as a by-product).
+template <typename R>
+__device__ __forceinline__ void drec_notch_node(const Params<R> &P, int i) {
+  if (!P.drec) return;
+  for (int k = 0; k < P.D; ++k) {
+    const int en = __ldg(&P.ell[(size_t)k * P.N + i]);
+    if (en >= 0 && (en & 3) == 0) (void)rhs_entry(P, en);
+  }
+}
+
 template <typename R, int U>
 __global__ void __launch_bounds__(256) k_dmg_rhs_nc(Params<R> P) {
   typedef typename Params<R>::R4 R4;
@@ -758,6 +855,7 @@ __global__ void __launch_bounds__(256) k_dmg_rhs_nc(Params<R> P) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.N; i += gridDim.x * blockDim.x) {
     if (P.flags[i] & kNotch) {
       rhs_notch_node(P, i);
+      drec_notch_node(P, i);
       continue;
     }
     R bi = 0, dg = 0, ax = 0, a1 = 0;
@@ -812,6 +910,17 @@ template <typename R>
 __device__ __forceinline__ R mv_entry(const Params<R> &P, int en, R beta, R pc) {
   typedef typename Params<R>::R4 R4;
   const int e = en >> 2, a = en & 3;
+  if (P.drec) {
+    // row a of the element operator from the solve's record: the other two
+    // slots b, c and their weights w_ab, w_ac
+    int n0, n1, n2;
+    R w01, w02, w12, mA;
+    load_drec(P, e, n0, n1, n2, w01, w02, w12, mA);
+    const int nb = a == 0 ? n1 : n0, nc = a == 2 ? n1 : n2;
+    const R wb = a == 2 ? w02 : w01, wc = a == 0 ? w02 : w12;
+    const R pb = pnew(P, nb, beta), pcc = pnew(P, nc, beta);
+    return wb * (pb - pc) + wc * (pcc - pc) + mA * (R(2) * pc + pb + pcc);
+  }
   int4 t;
   R A;
   R4 G;

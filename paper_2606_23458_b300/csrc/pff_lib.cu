@@ -264,6 +264,7 @@ struct pff_mesh {
   int32_t *ptr = nullptr, *ent = nullptr, *ell = nullptr;
   int32_t D = 0;  // ELL width = maximum incidence degree
   void *rec = nullptr, *fext = nullptr, *minv = nullptr;
+  void *drec = nullptr;  // DRec<R> per element: the damage operator of the current solve
   double *area_d = nullptr;
   uint8_t *flags = nullptr;
   double hmin = 0.0;
@@ -332,7 +333,7 @@ static void mesh_free(pff_mesh *m) {
   free_graph(m->step_g);
   free_graph(m->mech_g);
   void *ptrs[] = {m->gcs, m->st_cta, m->st_rng, m->st_nrng, m->st_lrec, m->st_slot, m->cgv, m->cgp,
-                  m->ptr, m->ent, m->ell, m->rec, m->fext, m->minv, m->area_d, m->flags,
+                  m->ptr, m->ent, m->ell, m->rec, m->drec, m->fext, m->minv, m->area_d, m->flags,
                   m->x, m->r, m->b, m->part, m->energy, m->wext, m->pz, m->q, m->dinv,
                   m->Hf, m->freef, m->ticket, m->sc, m->status_word, m->step_ctr, m->stab};
   for (void *q : ptrs)
@@ -870,6 +871,7 @@ static Params<R> base_params(pff_mesh *m, const pff_options &o) {
   P.ell = m->ell;
   P.D = m->D;
   P.rec = (const ERec<R> *)m->rec;
+  P.drec = (DRec<R> *)m->drec;
   P.flags = m->flags;
   P.st_cta = m->st_cta;
   P.st_rng = m->st_rng;
@@ -1666,6 +1668,10 @@ static pff_status mesh_build_t(pff_mesh *m, const double *xy_d, const int32_t *t
   const int64_t Ne4 = (Ne + 3) / 4 * 4;
   PFF_TRY(dalloc((ERec<R> **)&m->rec, Ne4));
   CUDA_TRY(cudaMemset(m->rec, 0, Ne4 * sizeof(ERec<R>)));
+  PFF_TRY(dalloc((DRec<R> **)&m->drec, Ne4));
+  // valid (zero) node ids until the first solve writes the records: a
+  // matvec timed before any right-hand side reads in bounds
+  CUDA_TRY(cudaMemset(m->drec, 0, Ne4 * sizeof(DRec<R>)));
   PFF_TRY(dalloc((typename V<R>::T2 **)&m->fext, N));
   PFF_TRY(dalloc((R **)&m->minv, N));
   PFF_TRY(dalloc((typename V<R>::T2 **)&m->pz, N + 2));
@@ -2477,8 +2483,13 @@ static pff_status build_reverse_graph(pff_mesh *m, pff_ckpt *c, AdjParams<R> A, 
   void *ka[] = {(void *)&c->kctr};
   cudaGraphNode_t n_load, n_prep, n_rhs, n_loop, n_mv, n_up, n_terms, n_mech, n_done;
   cudaGraph_t body;
+  // the adjoint solve's operator is A(H_n+1): its damage records are built
+  // from the step's history once k_adj_load has loaded it
+  void *pa[] = {(void *)&A.P};
+  cudaGraphNode_t n_drec;
   pff_status st = add_generic(g, {}, (const void *)k_adj_load<R>, Ge, kThreads, 0, aa, &n_load);
-  if (st == PFF_OK) st = add_generic(g, {n_load}, (const void *)k_adj_prep<R>, Gn, kThreads, 0, aa, &n_prep);
+  if (st == PFF_OK) st = add_generic(g, {n_load}, (const void *)k_drec_build<R>, Ge, kThreads, 0, pa, &n_drec);
+  if (st == PFF_OK) st = add_generic(g, {n_drec}, (const void *)k_adj_prep<R>, Gn, kThreads, 0, aa, &n_prep);
   if (st == PFF_OK) st = add_generic(g, {n_prep}, (const void *)k_adj_rhs<R>, Gn, kThreads, 0, aa, &n_rhs);
   if (pers) {
     if (st == PFF_OK) st = add_pers<R>(m, plan, g, {n_rhs}, A.P, &n_loop);
