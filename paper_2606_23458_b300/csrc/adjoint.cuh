@@ -25,6 +25,7 @@ template <typename R> struct AdjParams {
   // H_{n+1} of step n = s0 + k; slot -1 is the segment's checkpoint (d, H).
   // The slot of the step being reversed is read from *kctr.
   const int *kctr;
+  int *kdec;    // = kctr: decremented by the last block of the reverse step
   const R2 *tape_u;
   const R *tape_x, *tape_d;
   const double *tape_H;
@@ -32,15 +33,17 @@ template <typename R> struct AdjParams {
   const double *snap_H;
   int32_t stride_n, stride_e;  // slot strides (elements of R2/R, doubles)
   R *Hcur;                     // H_{n+1} in the kernel precision (operator)
+  int32_t h_tape;              // 1: k_adj_rhs reads H_{n+1} from the tape (no Hcur)
   // adjoint state (in: step n+1, out: step n)
   const R2 *ub_in, *vb_in, *ab_in;
   R2 *ub_out, *vb_out, *ab_out;
   R *db;             // dL/dd: in d_{n+1}, out d_n
   R *dbn;            // clamp share of dL/dd_n
   R *g;              // right-hand side of the adjoint solve
-  const R *Hb_in;    // dL/dH_{n+1} (after the damage terms are added)
-  R *Hb_acc;         // = Hb_in buffer, receives the damage terms
+  const R *Hb_in;    // dL/dH_{n+1} from the later steps (before this step's damage terms)
   R *Hb_out;         // dL/dH_n
+  R2 *fe;            // 3 Ne: the element shares of ubar per slot (reverse mechanics)
+  R *fd;             // Ne: the element shares of dbar
   double *gc;        // running dL/dGc
   double *gce;       // running dL/dGc_e per element (nullable)
   int *astat;        // worst status of the adjoint solves (atomicMax)
@@ -65,17 +68,12 @@ __device__ __forceinline__ Slot<R> slot(const AdjParams<R> &A) {
 }
 
 // H_{n+1} of the current slot in the kernel precision (the adjoint
-// operator's history).
+// operator's history, for the solves that read it from P.Hr).
 template <typename R>
 __global__ void __launch_bounds__(256) k_adj_load(AdjParams<R> A) {
   const Slot<R> S = slot(A);
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < A.P.Ne; e += gridDim.x * blockDim.x)
     A.Hcur[e] = (R)S.H1[e];
-}
-
-// Moves to the previous slot after a reversed step.
-__global__ void k_adj_step_done(int *kctr) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) *kctr -= 1;
 }
 
 // Splits at one point: sigma+, sigma- and psi+ (same formulas as stress()).
@@ -162,13 +160,46 @@ __device__ __forceinline__ void split_tangent(const Params<R> &P, R exx, R eyy, 
   }
 }
 
-// Right-hand side of the adjoint solve and the clamp share of dL/dd_n:
-//   g = dL/dd_{n+1} where d_n < x_{n+1} < 1 (free nodes), else 0;
-//   dbn = dL/dd_{n+1} where x_{n+1} <= d_n (free nodes), else 0.
+// One incidence entry (slot k of node i) of the adjoint solve's set-up: its
+// share of the Jacobi diagonal and of A lam0 (the operator at H_{n+1},
+// Eqs. damage_pde_at2 / matrix_free_fe_operator), writing the solve's FP32
+// entry record.
 template <typename R>
-__global__ void __launch_bounds__(256) k_adj_prep(AdjParams<R> A) {
+__device__ __forceinline__ void adj_rhs_entry(const AdjParams<R> &A, const Slot<R> &S, int en, int k, int i,
+                                              R &dgc, R &axc) {
+  typedef typename Params<R>::R4 R4;
+  const Params<R> &P = A.P;
+  const int e = en >> 2, a = en & 3;
+  int4 t;
+  R Ar;
+  R4 G;
+  load_elem(P, e, t, Ar, G);
+  const R sg = gc_scale(P, e);
+  const R c = P.cbase * sg + R(2) * (A.h_tape ? (R)S.H1[e] : P.Hr[e]);
+  const R kA = (P.kappa * sg) * Ar, mA = c * Ar * (R(1) / R(12));
+  R gx, gy;
+  slot_grad<R>(G, a, gx, gy);
+  dgc = kA * (gx * gx + gy * gy) + R(2) * mA;
+  if (P.erec) P.erec[(size_t)k * P.N + i] = make_erec<R>(t, G, a, kA, mA);
+  const R l0 = (P.flags[t.x] & kNotch) ? R(0) : P.x[t.x];
+  const R l1 = (P.flags[t.y] & kNotch) ? R(0) : P.x[t.y];
+  const R l2 = (P.flags[t.z] & kNotch) ? R(0) : P.x[t.z];
+  axc = elem_row<R>(G, a, kA, mA, l0, l1, l2);
+}
+
+// Adjoint solve set-up (same operator as the forward damage solve at
+// H_{n+1}): per node the right-hand side and the clamp share of dL/dd_n,
+//   g = dL/dd_{n+1} where d_n < x_{n+1} < 1 (free nodes), else 0;
+//   dbn = dL/dd_{n+1} where x_{n+1} <= d_n (free nodes), else 0;
+// warm start lam0 = previous lambda (in P.x), r = g - A lam0, Jacobi
+// diagonal, z, p = 0; reductions |g|^2, |r|^2, r.z.
+template <typename R>
+__global__ void __launch_bounds__(256) k_adj_rhs(AdjParams<R> A) {
+  typedef typename Params<R>::R4 R4;
+  typedef Acc<R> AC;
   const Params<R> &P = A.P;
   const Slot<R> S = slot(A);
+  typename AC::T vals[3] = {AC::zero(), AC::zero(), AC::zero()};
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.N; i += gridDim.x * blockDim.x) {
     R gi = R(0), bi = R(0);
     if (!(P.flags[i] & kNotch)) {
@@ -178,19 +209,6 @@ __global__ void __launch_bounds__(256) k_adj_prep(AdjParams<R> A) {
     }
     A.g[i] = gi;
     A.dbn[i] = bi;
-  }
-}
-
-// Adjoint solve set-up (same operator as the forward damage solve at
-// H_{n+1}): warm start lam0 = previous lambda (in P.x), r = g - A lam0,
-// Jacobi diagonal, z, p = 0; reductions |g|^2, |r|^2, r.z.
-template <typename R>
-__global__ void __launch_bounds__(256) k_adj_rhs(AdjParams<R> A) {
-  typedef typename Params<R>::R4 R4;
-  typedef Acc<R> AC;
-  const Params<R> &P = A.P;
-  typename AC::T vals[3] = {AC::zero(), AC::zero(), AC::zero()};
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.N; i += gridDim.x * blockDim.x) {
     if (P.flags[i] & kNotch) {
       P.x[i] = R(0);
       P.r[i] = R(0);
@@ -202,27 +220,24 @@ __global__ void __launch_bounds__(256) k_adj_rhs(AdjParams<R> A) {
       continue;
     }
     R dg = 0, ax = 0;
-    for (int k = 0; k < P.D; ++k) {
-      const int en = __ldg(&P.ell[(size_t)k * P.N + i]);
-      if (en < 0) break;
-      const int e = en >> 2, a = en & 3;
-      int4 t;
-      R Ar;
-      R4 G;
-      load_elem(P, e, t, Ar, G);
-      const R sg = gc_scale(P, e);
-      const R c = P.cbase * sg + R(2) * P.Hr[e];
-      const R kA = (P.kappa * sg) * Ar, mA = c * Ar * (R(1) / R(12));
-      R gx, gy;
-      slot_grad<R>(G, a, gx, gy);
-      dg = radd(dg, kA * (gx * gx + gy * gy) + R(2) * mA);
-      const R l0 = (P.flags[t.x] & kNotch) ? R(0) : P.x[t.x];
-      const R l1 = (P.flags[t.y] & kNotch) ? R(0) : P.x[t.y];
-      const R l2 = (P.flags[t.z] & kNotch) ? R(0) : P.x[t.z];
-      ax = radd(ax, elem_row<R>(G, a, kA, mA, l0, l1, l2));
+    // two incidence entries in flight, summed in slot order
+    for (int k = 0; k < P.D; k += 2) {
+      int en[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) en[u] = k + u < P.D ? __ldg(&P.ell[(size_t)(k + u) * P.N + i]) : -1;
+      R cd[2], ca[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+        if (en[u] >= 0) adj_rhs_entry(A, S, en[u], k + u, i, cd[u], ca[u]);
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+        if (en[u] >= 0) {
+          dg = radd(dg, cd[u]);
+          ax = radd(ax, ca[u]);
+        }
     }
-    const R gi = A.g[i];
     const R ri = gi - ax, di = R(1) / dg, zi = ri * di;
+    if (P.diag) P.diag[i] = dg;
     P.r[i] = ri;
     P.dinv[i] = di;
     typename Params<R>::R2 w;
@@ -256,51 +271,32 @@ __global__ void __launch_bounds__(256) k_adj_rhs(AdjParams<R> A) {
   }
 }
 
-// Parameter and history terms of the damage adjoint, one element at a time
-// (AT2; Eq. implicit_gc_l0_element_term and the H-derivative of A and b):
-//   dL/dGc += -lam_e^T (l0 K^e + M^e / l0) xt_e (also per element into gce:
+// Parameter and history terms of the damage adjoint for element e (AT2;
+// Eq. implicit_gc_l0_element_term and the H-derivative of A and b):
+//   gterm = lam_e^T (l0 K^e + M^e / l0) xt_e  (dL/dGc -= gterm; per element
 //   the derivative with respect to Gc_e of a toughness field),
 //   Hbar_e += (2 A_e / 3) sum_a lam_a - 2 lam_e^T M^e xt_e,
-// with xt = x_{n+1} on free nodes and 1 on the notch, M^e = A_e (1+delta)/12.
+// with xt = x_{n+1} on free nodes and 1 on the notch, M^e = A_e (1+delta)/12;
+// lam = 0 when the solve's right-hand side was 0 (the CG stopped at once and
+// left the warm start).  Returns Hbar_e with this step's terms.
 template <typename R>
-__global__ void __launch_bounds__(256) k_adj_dmg_terms(AdjParams<R> A) {
-  typedef typename Params<R>::R4 R4;
-  typedef Acc<R> AC;
+__device__ __forceinline__ R adj_dmg_terms(const AdjParams<R> &A, const Slot<R> &S, const int4 &t, R Ar,
+                                           const typename Params<R>::R4 &G, bool zero_lam, R hb_in, R &gterm) {
   const Params<R> &P = A.P;
-  const Slot<R> S = slot(A);
-  typename AC::T vals[1] = {AC::zero()};
-  const R l0 = (R)P.l0, il0 = R(1) / (R)P.l0;
-  // g = 0 solves to lam = 0; the CG stopped at once and left the warm start
-  const bool zero_lam = P.sc->bn == 0.0;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < P.Ne; e += gridDim.x * blockDim.x) {
-    int4 t;
-    R Ar;
-    R4 G;
-    load_elem(P, e, t, Ar, G);
-    const bool n0 = P.flags[t.x] & kNotch, n1 = P.flags[t.y] & kNotch, n2 = P.flags[t.z] & kNotch;
-    const R la0 = (n0 || zero_lam) ? R(0) : P.x[t.x];
-    const R la1 = (n1 || zero_lam) ? R(0) : P.x[t.y];
-    const R la2 = (n2 || zero_lam) ? R(0) : P.x[t.z];
-    const R x0 = n0 ? R(1) : S.x1[t.x], x1 = n1 ? R(1) : S.x1[t.y], x2 = n2 ? R(1) : S.x1[t.z];
-    // lam^T K^e xt with K^e = A grad(phi) grad(phi)^T: A (grad lam).(grad xt)
-    const R glx = G.x * (la0 - la2) + G.z * (la1 - la2), gly = G.y * (la0 - la2) + G.w * (la1 - la2);
-    const R gxx = G.x * (x0 - x2) + G.z * (x1 - x2), gxy = G.y * (x0 - x2) + G.w * (x1 - x2);
-    const R lKx = Ar * (glx * gxx + gly * gxy);
-    // lam^T M^e xt = A/12 (sum lam_a x_a + sum lam . sum x)
-    const R sl = la0 + la1 + la2, sx = x0 + x1 + x2;
-    const R lMx = Ar * (R(1) / R(12)) * (la0 * x0 + la1 * x1 + la2 * x2 + sl * sx);
-    vals[0] = AC::add(vals[0], AC::prod(R(-1), l0 * lKx + il0 * lMx));
-    if (A.gce) A.gce[e] -= (double)(l0 * lKx + il0 * lMx);
-    A.Hb_acc[e] = A.Hb_acc[e] + R(2) * Ar * (R(1) / R(3)) * sl - R(2) * lMx;
-  }
-  __shared__ double tot[1];
-  if (reduce_last<R, 1>(vals, P.part, P.ticket, tot) && threadIdx.x == 0) {
-    *A.gc += tot[0];
-    if (A.astat) {
-      if (P.sc->status) atomicMax(A.astat, P.sc->status);
-      atomicAdd(A.astat + 1, P.sc->iters);  // adjoint CG iterations, summed
-    }
-  }
+  const bool n0 = P.flags[t.x] & kNotch, n1 = P.flags[t.y] & kNotch, n2 = P.flags[t.z] & kNotch;
+  const R la0 = (n0 || zero_lam) ? R(0) : P.x[t.x];
+  const R la1 = (n1 || zero_lam) ? R(0) : P.x[t.y];
+  const R la2 = (n2 || zero_lam) ? R(0) : P.x[t.z];
+  const R x0 = n0 ? R(1) : S.x1[t.x], x1 = n1 ? R(1) : S.x1[t.y], x2 = n2 ? R(1) : S.x1[t.z];
+  // lam^T K^e xt with K^e = A grad(phi) grad(phi)^T: A (grad lam).(grad xt)
+  const R glx = G.x * (la0 - la2) + G.z * (la1 - la2), gly = G.y * (la0 - la2) + G.w * (la1 - la2);
+  const R gxx = G.x * (x0 - x2) + G.z * (x1 - x2), gxy = G.y * (x0 - x2) + G.w * (x1 - x2);
+  const R lKx = Ar * (glx * gxx + gly * gxy);
+  // lam^T M^e xt = A/12 (sum lam_a x_a + sum lam . sum x)
+  const R sl = la0 + la1 + la2, sx = x0 + x1 + x2;
+  const R lMx = Ar * (R(1) / R(12)) * (la0 * x0 + la1 * x1 + la2 * x2 + sl * sx);
+  gterm = (R)P.l0 * lKx + (R(1) / (R)P.l0) * lMx;
+  return hb_in + R(2) * Ar * (R(1) / R(3)) * sl - R(2) * lMx;
 }
 
 // fbar at node j: -(1/m_j) (abar_j + dt/2 vbar_j).
@@ -314,63 +310,114 @@ __device__ __forceinline__ typename Params<R>::R2 fbar_at(const AdjParams<R> &A,
   return f;
 }
 
-// Reverse of the mechanics of step n -> n+1 at node i (node-centric gather
-// over the incidence, ascending element order):
-//   ubar' = ubar_{n+1} + sum_e [A_e dsigma[de_e] . grad(phi_a)
-//                               + psibar_e sigma+_e . grad(phi_a)],
-//   with de_e = sym grad(fbar) on element e, dsigma = g dsigma+ + dsigma-,
-//   psibar_e = Hbar_e where H_{n+1,e} > H_{n,e} (the max picked psi+);
-//   dbar_n  = dbn + sum_e g'(dbar_e) A_e (de_e : sigma+_e) / 3;
-//   vbar_n = vbar_{n+1} + dt ubar', abar_n = dt/2 vbar_{n+1} + dt^2/2 ubar',
-//   ubar_n = ubar'; the element's owner entry writes Hbar_n.
+// Reverse of the mechanics of step n -> n+1, element pass (one thread per
+// element): with de_e = sym grad(fbar) on element e, dsigma = g dsigma+ +
+// dsigma-, and psibar_e = Hbar_e where H_{n+1,e} > H_{n,e} (the max picked
+// psi+), the element's share of ubar at its slot a,
+//   A_e dsigma[de_e] . grad(phi_a) + psibar_e sigma+_e . grad(phi_a),
+// goes to fe[3e + a], and its share of dbar at each of its nodes,
+//   g'(dbar_e) A_e (de_e : sigma+_e) / 3, to fd[e].  Hbar_e comes with the
+// step's damage terms (adj_dmg_terms); Hbar_n and the element's Gc term (to
+// dL/dGc and the per-element gradient) are written here.  The last block
+// adds the summed Gc terms and records the solve's status and iterations.
 template <typename R>
-__global__ void __launch_bounds__(256) k_adj_mech(AdjParams<R> A) {
+__global__ void __launch_bounds__(256) k_adj_mech_elem(AdjParams<R> A) {
   typedef typename Params<R>::R2 R2;
   typedef typename Params<R>::R4 R4;
+  typedef Acc<R> AC;
   const Params<R> &P = A.P;
   const Slot<R> S = slot(A);
+  const R hdt = R(0.5) * (R)P.dt;
+  const bool zero_lam = P.sc->bn == 0.0;
+  typename AC::T vals[1] = {AC::zero()};
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < P.Ne; e += gridDim.x * blockDim.x) {
+    int4 t;
+    R Ar;
+    R4 G;
+    load_elem(P, e, t, Ar, G);
+    // strain of u_{n+1}
+    const R2 u0 = S.u1[t.x], u1 = S.u1[t.y], u2 = S.u1[t.z];
+    R ax0 = u0.x - u2.x, ax1 = u1.x - u2.x, ay0 = u0.y - u2.y, ay1 = u1.y - u2.y;
+    const R exx = G.x * ax0 + G.z * ax1, eyy = G.y * ay0 + G.w * ay1;
+    const R exy = R(0.5) * (G.y * ax0 + G.w * ax1 + G.x * ay0 + G.z * ay1);
+    // strain of fbar
+    const R2 f0 = fbar_at(A, t.x, hdt), f1 = fbar_at(A, t.y, hdt), f2 = fbar_at(A, t.z, hdt);
+    ax0 = f0.x - f2.x; ax1 = f1.x - f2.x; ay0 = f0.y - f2.y; ay1 = f1.y - f2.y;
+    R de[3];
+    de[0] = G.x * ax0 + G.z * ax1;
+    de[1] = G.y * ay0 + G.w * ay1;
+    de[2] = R(0.5) * (G.y * ax0 + G.w * ax1 + G.x * ay0 + G.z * ay1);
+    const R db = (S.d0[t.x] + S.d0[t.y] + S.d0[t.z]) * (R(1) / R(3));
+    const R g = (R(1) - db) * (R(1) - db) + P.eta, gp = R(-2) * (R(1) - db);
+    R sp[3], sm[3], dsp[3], dsm[3];
+    split_parts(P, exx, eyy, exy, sp, sm);
+    split_tangent(P, exx, eyy, exy, de, dsp, dsm);
+    // the forward's max picked psi+ exactly where H grew (non-negative
+    // doubles compare like their bit patterns)
+    const bool picked = __double_as_longlong(S.H1[e]) > __double_as_longlong(S.H0[e]);
+    R gterm;
+    const R hb = adj_dmg_terms(A, S, t, Ar, G, zero_lam, A.Hb_in[e], gterm);
+    const R pb = picked ? hb : R(0);
+    const R sx = Ar * (g * dsp[0] + dsm[0]) + pb * sp[0];
+    const R sy = Ar * (g * dsp[1] + dsm[1]) + pb * sp[1];
+    const R sxy = Ar * (g * dsp[2] + dsm[2]) + pb * sp[2];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      R gx, gy;
+      slot_grad<R>(G, a, gx, gy);
+      R2 f;
+      f.x = sx * gx + sxy * gy;
+      f.y = sxy * gx + sy * gy;
+      A.fe[(size_t)3 * e + a] = f;
+    }
+    A.fd[e] = gp * Ar * (de[0] * sp[0] + de[1] * sp[1] + R(2) * de[2] * sp[2]) * (R(1) / R(3));
+    A.Hb_out[e] = picked ? R(0) : hb;
+    vals[0] = AC::add(vals[0], AC::prod(R(-1), gterm));
+    if (A.gce) A.gce[e] -= (double)gterm;
+  }
+  __shared__ double tot[1];
+  if (reduce_last<R, 1>(vals, P.part, P.ticket, tot) && threadIdx.x == 0) {
+    *A.gc += tot[0];
+    if (A.astat) {
+      if (P.sc->status) atomicMax(A.astat, P.sc->status);
+      atomicAdd(A.astat + 1, P.sc->iters);  // adjoint CG iterations, summed
+    }
+  }
+}
+
+// Reverse of the mechanics, node pass: ubar' = ubar_{n+1} + the element
+// shares at node i (incidence order, ascending element),
+//   dbar_n = dbn + the element shares fd, vbar_n = vbar_{n+1} + dt ubar',
+//   abar_n = dt/2 vbar_{n+1} + dt^2/2 ubar', ubar_n = ubar'.  The last block
+// to finish moves the slot counter to the previous step (every block has
+// read the slot by then).
+template <typename R>
+__global__ void __launch_bounds__(256) k_adj_mech_node(AdjParams<R> A) {
+  typedef typename Params<R>::R2 R2;
+  const Params<R> &P = A.P;
   const R dt = (R)P.dt, hdt = R(0.5) * dt;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.N; i += gridDim.x * blockDim.x) {
     R ux = 0, uy = 0, dsum = 0;
-    for (int k = 0; k < P.D; ++k) {
-      const int en = __ldg(&P.ell[(size_t)k * P.N + i]);
-      if (en < 0) break;
-      const int e = en >> 2, a = en & 3;
-      int4 t;
-      R Ar;
-      R4 G;
-      load_elem(P, e, t, Ar, G);
-      // strain of u_{n+1}
-      const R2 u0 = S.u1[t.x], u1 = S.u1[t.y], u2 = S.u1[t.z];
-      R ax0 = u0.x - u2.x, ax1 = u1.x - u2.x, ay0 = u0.y - u2.y, ay1 = u1.y - u2.y;
-      const R exx = G.x * ax0 + G.z * ax1, eyy = G.y * ay0 + G.w * ay1;
-      const R exy = R(0.5) * (G.y * ax0 + G.w * ax1 + G.x * ay0 + G.z * ay1);
-      // strain of fbar
-      const R2 f0 = fbar_at(A, t.x, hdt), f1 = fbar_at(A, t.y, hdt), f2 = fbar_at(A, t.z, hdt);
-      ax0 = f0.x - f2.x; ax1 = f1.x - f2.x; ay0 = f0.y - f2.y; ay1 = f1.y - f2.y;
-      R de[3];
-      de[0] = G.x * ax0 + G.z * ax1;
-      de[1] = G.y * ay0 + G.w * ay1;
-      de[2] = R(0.5) * (G.y * ax0 + G.w * ax1 + G.x * ay0 + G.z * ay1);
-      const R db = (S.d0[t.x] + S.d0[t.y] + S.d0[t.z]) * (R(1) / R(3));
-      const R g = (R(1) - db) * (R(1) - db) + P.eta, gp = R(-2) * (R(1) - db);
-      R sp[3], sm[3], dsp[3], dsm[3];
-      split_parts(P, exx, eyy, exy, sp, sm);
-      split_tangent(P, exx, eyy, exy, de, dsp, dsm);
-      // the forward's max picked psi+ exactly where H grew (non-negative
-      // doubles compare like their bit patterns)
-      const bool picked = __double_as_longlong(S.H1[e]) > __double_as_longlong(S.H0[e]);
-      const R hb = A.Hb_in[e];
-      const R pb = picked ? hb : R(0);
-      const R sx = Ar * (g * dsp[0] + dsm[0]) + pb * sp[0];
-      const R sy = Ar * (g * dsp[1] + dsm[1]) + pb * sp[1];
-      const R sxy = Ar * (g * dsp[2] + dsm[2]) + pb * sp[2];
-      R gx, gy;
-      slot_grad<R>(G, a, gx, gy);
-      ux = radd(ux, sx * gx + sxy * gy);
-      uy = radd(uy, sxy * gx + sy * gy);
-      dsum = radd(dsum, gp * Ar * (de[0] * sp[0] + de[1] * sp[1] + R(2) * de[2] * sp[2]) * (R(1) / R(3)));
-      if (a == 0) A.Hb_out[e] = picked ? R(0) : hb;
+    // four incidence entries in flight, summed in slot order
+    for (int k = 0; k < P.D; k += 4) {
+      int en[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) en[u] = k + u < P.D ? __ldg(&P.ell[(size_t)(k + u) * P.N + i]) : -1;
+      R2 f[4];
+      R fdv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (en[u] >= 0) {
+          f[u] = A.fe[(size_t)3 * (en[u] >> 2) + (en[u] & 3)];
+          fdv[u] = A.fd[en[u] >> 2];
+        }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (en[u] >= 0) {
+          ux = radd(ux, f[u].x);
+          uy = radd(uy, f[u].y);
+          dsum = radd(dsum, fdv[u]);
+        }
     }
     const R2 ubi = A.ub_in[i], vbi = A.vb_in[i];
     R2 up, vo, ao;
@@ -384,6 +431,17 @@ __global__ void __launch_bounds__(256) k_adj_mech(AdjParams<R> A) {
     A.vb_out[i] = vo;
     A.ab_out[i] = ao;
     A.db[i] = (P.flags[i] & kNotch) ? R(0) : A.dbn[i] + dsum;
+  }
+  __shared__ bool last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(P.ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    *P.ticket = 0;
+    *A.kdec -= 1;
   }
 }
 

@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(256) kb_rhs(Params<R> P, Batch B) {
         for (int u = 0; u < U; ++u) en[u] = k + u < P.D ? __ldg(&P.ell[(size_t)(k + u) * P.N + i]) : -1;
 #pragma unroll
         for (int u = 0; u < U; ++u)
-          if (en[u] >= 0) o[u] = rhs_entry(Q, en[u]);
+          if (en[u] >= 0) o[u] = rhs_entry(Q, en[u], k + u, i);
 #pragma unroll
         for (int u = 0; u < U; ++u)
           if (en[u] >= 0) {
@@ -243,7 +243,15 @@ __global__ void __launch_bounds__(256) kb_matvec(Params<R> P, Batch B) {
     R q = 0;
     if (!is_fixed(Q, i)) {
       const R pc = pnew(Q, i, beta);
-      for (int k = 0; k < P.D; k += U) {
+      bool done = false;
+      if constexpr (sizeof(R) == 4) {
+        if (Q.erec) {
+          // FP32 entry records (see matvec_rows)
+          q = erec_row<U>(Q, i, beta, pc);
+          done = true;
+        }
+      }
+      for (int k = 0; k < P.D && !done; k += U) {
         R c[U];
         int en[U];
 #pragma unroll

@@ -140,6 +140,13 @@ template <typename R> struct Params {
   DRec<R> *drec; // damage records of the current solve (nullable: the
                  // operator is rebuilt from the geometry and H per entry);
                  // written by the right-hand-side kernels, read by the matvec
+  float4 *erec;  // FP32: damage entry records of the current solve in the
+                 // incidence layout (entry k of node i at k N + i): the other
+                 // two nodes b, c of the entry's element and their row
+                 // coefficients (w_ab + mA, w_ac + mA); b = -1 marks an empty
+                 // slot.  Nullable.
+  R *diag;       // with erec: the row's diagonal sum over entries of
+                 // (kappa_e A_e |grad phi_a|^2 + 2 mA)
   const R *gcs; // per-element toughness field as Gc_e / Gc (nullable: uniform);
                 // kappa, cbase and wbase are linear in Gc and scale with it
   R cbase;      // reaction: c_e = cbase + 2 H_e
@@ -648,6 +655,23 @@ __device__ __forceinline__ R elem_row(const R4 &G, int a, R kA, R mA, R x0, R x1
   return kA * (gx * dx + gy * dy) + mA * (xa + x0 + x1 + x2);
 }
 
+// Entry record of slot a of an element (FP32 entry records): the other two
+// nodes b, c and the coefficients of their values in row a,
+//   kA grad(phi_a) . grad(phi_b) + mA  and  kA grad(phi_a) . grad(phi_c) + mA,
+// the row's own coefficient kA |grad(phi_a)|^2 + 2 mA going to the diagonal
+// (the element stiffness rows sum to zero, so row a of the element operator
+// is exactly this split).
+template <typename R>
+__device__ __forceinline__ float4 make_erec(const int4 &t, const typename Params<R>::R4 &G, int a, R kA, R mA) {
+  R gx, gy, gbx, gby, gcx, gcy;
+  slot_grad<R>(G, a, gx, gy);
+  slot_grad<R>(G, a == 0 ? 1 : 0, gbx, gby);
+  slot_grad<R>(G, a == 2 ? 1 : 2, gcx, gcy);
+  const int nb = a == 0 ? t.y : t.x, nc = a == 2 ? t.y : t.z;
+  return make_float4(__int_as_float(nb), __int_as_float(nc), (float)(kA * (gx * gbx + gy * gby) + mA),
+                     (float)(kA * (gx * gcx + gy * gcy) + mA));
+}
+
 // The damage record of an element from its geometry and coefficients.
 template <typename R>
 __device__ __forceinline__ DRec<R> make_drec(const int4 &t, const typename Params<R>::R4 &G, R kA, R mA) {
@@ -717,7 +741,8 @@ __global__ void __launch_bounds__(256) k_drec_build(Params<R> P) {
 // incidence entry's share: (b, diag, (A x0)_a, (A 1_D)_a) with
 // x0 = d_prev (1 on the notch).
 template <typename R>
-__device__ __forceinline__ typename Params<R>::R4 rhs_entry(const Params<R> &P, int en) {
+__device__ __forceinline__ typename Params<R>::R4 rhs_entry(const Params<R> &P, int en, int slot = -1,
+                                                            int node = -1, int csr = -1) {
   typedef typename Params<R>::R4 R4;
   const int e = en >> 2, a = en & 3;
   int4 t;
@@ -735,6 +760,14 @@ __device__ __forceinline__ typename Params<R>::R4 rhs_entry(const Params<R> &P, 
   R gx, gy;
   slot_grad<R>(G, a, gx, gy);
   if (a == 0 && P.drec) P.drec[e] = make_drec<R>(t, G, kA, mA);
+  if (P.erec) {
+    // the entry's incidence slot: given, or from its CSR position
+    if (slot < 0 && csr >= 0) {
+      node = a == 0 ? t.x : (a == 1 ? t.y : t.z);
+      slot = csr - __ldg(&P.ptr[node]);
+    }
+    if (slot >= 0) P.erec[(size_t)slot * P.N + node] = make_erec<R>(t, G, a, kA, mA);
+  }
   R4 o;
   o.x = w * A * (R(1) / R(3));
   o.y = kA * (gx * gx + gy * gy) + R(2) * mA;
@@ -753,6 +786,7 @@ __device__ __forceinline__ void rhs_node(const Params<R> &P, int i, R bi, R dg, 
   typedef Acc<R> AC;
   const R ri = bi - ax, be = bi - a1;
   const R di = R(1) / dg;
+  if (P.diag) P.diag[i] = dg;
   const R zi = ri * di;
   P.x[i] = P.dprev[i];
   P.r[i] = ri;
@@ -812,7 +846,7 @@ __global__ void __launch_bounds__(256) k_dmg_rhs_ep(Params<R> P) {
   for (int b = blockIdx.x; b < P.nblk; b += gridDim.x) {
     int i0, i1, k0, k1;
     block_nodes(P, b, i0, i1, k0, k1);
-    for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) cc[k - k0] = rhs_entry(P, __ldg(&P.ent[k]));
+    for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) cc[k - k0] = rhs_entry(P, __ldg(&P.ent[k]), -1, -1, k);
     __syncthreads();
     for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
       if (P.flags[i] & kNotch) {
@@ -866,7 +900,7 @@ __global__ void __launch_bounds__(256) k_dmg_rhs_nc(Params<R> P) {
       for (int u = 0; u < U; ++u) en[u] = k + u < P.D ? __ldg(&P.ell[(size_t)(k + u) * P.N + i]) : -1;
 #pragma unroll
       for (int u = 0; u < U; ++u)
-        if (en[u] >= 0) o[u] = rhs_entry(P, en[u]);
+        if (en[u] >= 0) o[u] = rhs_entry(P, en[u], k + u, i);
 #pragma unroll
       for (int u = 0; u < U; ++u)
         if (en[u] >= 0) {
@@ -889,6 +923,30 @@ template <typename R>
 __device__ __forceinline__ R pnew(const Params<R> &P, int j, R beta) {
   const typename Params<R>::R2 v = P.pz[j];
   return fma(beta, v.x, v.y);
+}
+
+// Row i of q = A p_new from the FP32 entry records: diag_i p_i, then per
+// incidence slot in order (U records in flight) c_b p_b + c_c p_c, rounded
+// the same way in every schedule (explicit fma and non-contracted adds).
+template <int U>
+__device__ __forceinline__ float erec_row(const Params<float> &P, int i, float beta, float pc) {
+  float q = P.diag[i] * pc;
+  for (int k = 0; k < P.D; k += U) {
+    float4 er[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      er[u] = k + u < P.D ? __ldg(&P.erec[(size_t)(k + u) * P.N + i]) : make_float4(__int_as_float(-1), 0.f, 0.f, 0.f);
+    float c[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int nb = __float_as_int(er[u].x);
+      if (nb >= 0) c[u] = fmaf(er[u].z, pnew(P, nb, beta), __fmul_rn(er[u].w, pnew(P, __float_as_int(er[u].y), beta)));
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (__float_as_int(er[u].x) >= 0) q = __fadd_rn(q, c[u]);
+  }
+  return q;
 }
 
 // One incidence entry's share of (A p_new)_a, matrix-free (Eq.
@@ -980,6 +1038,27 @@ __global__ void __launch_bounds__(256) k_cg_matvec_ep(Params<R> P) {
   R *cq = reinterpret_cast<R *>(smem_raw);
   typename AC::T vals[1] = {AC::zero()};
   const R beta = sc_beta<R>(P.sc);
+  if constexpr (sizeof(R) == 4) {
+    if (P.erec) {
+      // FP32 entry records: rows of the block's nodes, the same per-row
+      // arithmetic as the node-centric schedules
+      for (int b = blockIdx.x; b < P.nblk; b += gridDim.x) {
+        const int i0 = b * P.NB, i1 = min(i0 + P.NB, P.N);
+        for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+          R q = 0;
+          if (!is_fixed(P, i)) {
+            const R pc = pnew(P, i, beta);
+            q = erec_row<1>(P, i, beta, pc);
+            vals[0] = AC::add(vals[0], AC::prod(pc, P.rscale * q));
+          }
+          P.q[i] = q;
+        }
+      }
+      __shared__ double tot1[1];
+      if (reduce_last<R, 1>(vals, P.part, P.ticket, tot1) && threadIdx.x == 0) matvec_finish(P, tot1);
+      return;
+    }
+  }
   for (int b = blockIdx.x; b < P.nblk; b += gridDim.x) {
     int i0, i1, k0, k1;
     block_nodes(P, b, i0, i1, k0, k1);
@@ -1012,6 +1091,23 @@ template <typename R, int U>
 __device__ __forceinline__ void matvec_rows(const Params<R> &P, R beta, int i0, int stride,
                                             typename Acc<R>::T &acc) {
   typedef Acc<R> AC;
+  if constexpr (sizeof(R) == 4) {
+    if (P.erec) {
+      // FP32 entry records: the row's diagonal times its own value, then per
+      // entry the two other nodes' values times their coefficients (the
+      // records stream in coalesced; only the p gathers are indirect)
+      for (int i = i0; i < P.N; i += stride) {
+        R q = 0;
+        if (!is_fixed(P, i)) {
+          const R pc = pnew(P, i, beta);
+          q = erec_row<U>(P, i, beta, pc);
+          acc = AC::add(acc, AC::prod(pc, P.rscale * q));
+        }
+        P.q[i] = q;
+      }
+      return;
+    }
+  }
   for (int i = i0; i < P.N; i += stride) {
     R q = 0;
     if (!is_fixed(P, i)) {

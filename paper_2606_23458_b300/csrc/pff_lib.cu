@@ -264,7 +264,9 @@ struct pff_mesh {
   int32_t *ptr = nullptr, *ent = nullptr, *ell = nullptr;
   int32_t D = 0;  // ELL width = maximum incidence degree
   void *rec = nullptr, *fext = nullptr, *minv = nullptr;
-  void *drec = nullptr;  // DRec<R> per element: the damage operator of the current solve
+  void *drec = nullptr;  // FP64: DRec<double> per element, the damage operator of the current solve
+  float4 *erec = nullptr;  // FP32: damage entry records of the current solve (D x N, incidence layout)
+  float *diagf = nullptr;  // FP32: the damage rows' diagonals (N)
   double *area_d = nullptr;
   uint8_t *flags = nullptr;
   double hmin = 0.0;
@@ -333,7 +335,8 @@ static void mesh_free(pff_mesh *m) {
   free_graph(m->step_g);
   free_graph(m->mech_g);
   void *ptrs[] = {m->gcs, m->st_cta, m->st_rng, m->st_nrng, m->st_lrec, m->st_slot, m->cgv, m->cgp,
-                  m->ptr, m->ent, m->ell, m->rec, m->drec, m->fext, m->minv, m->area_d, m->flags,
+                  m->ptr, m->ent, m->ell, m->rec, m->drec, m->erec, m->diagf, m->fext, m->minv, m->area_d,
+                  m->flags,
                   m->x, m->r, m->b, m->part, m->energy, m->wext, m->pz, m->q, m->dinv,
                   m->Hf, m->freef, m->ticket, m->sc, m->status_word, m->step_ctr, m->stab};
   for (void *q : ptrs)
@@ -776,6 +779,15 @@ static pff_status configure(pff_mesh *m) {
     k_build_ell<<<grid_for(m->N, 256), 256>>>(m->ptr, m->ent, m->N, D, m->ell);
     CUDA_TRY(cudaGetLastError());
   }
+  if (sizeof(R) == 4 && !m->erec) {
+    // every slot empty (node id -1) until a right-hand side writes it: empty
+    // padding slots stay so, and a matvec timed before any solve reads in
+    // bounds
+    PFF_TRY(dalloc(&m->erec, (size_t)D * m->N));
+    CUDA_TRY(cudaMemset(m->erec, 0xff, (size_t)D * m->N * sizeof(float4)));
+    PFF_TRY(dalloc(&m->diagf, (size_t)m->N));
+    CUDA_TRY(cudaMemset(m->diagf, 0, (size_t)m->N * sizeof(float)));
+  }
   m->nblk = (int32_t)((m->N + NB - 1) / NB);
   const size_t sm_ep[KP_COUNT] = {0, maxE * sizeof(typename V<R>::T2), maxE * sizeof(typename V<R>::T4),
                                   maxE * sizeof(R), 0, 0, maxE * sizeof(R), 0};
@@ -872,6 +884,8 @@ static Params<R> base_params(pff_mesh *m, const pff_options &o) {
   P.D = m->D;
   P.rec = (const ERec<R> *)m->rec;
   P.drec = (DRec<R> *)m->drec;
+  P.erec = m->erec;
+  P.diag = (R *)m->diagf;
   P.flags = m->flags;
   P.st_cta = m->st_cta;
   P.st_rng = m->st_rng;
@@ -990,7 +1004,14 @@ static pff_status append_solve(const pff_mesh *m, cudaGraph_t g, cudaGraphNode_t
   std::vector<cudaGraphNode_t> d;
   if (dep) d.push_back(dep);
   cudaGraphNode_t n_rhs, n_loop, n_fin;
-  PFF_TRY(add_kernel<R>(m, g, d, KP_RHS, P, &n_rhs));
+  // the fused and staged families keep their own operator data: their
+  // right-hand side skips the entry records
+  Params<R> Pr = P;
+  if (plan.fused() || plan.st()) {
+    Pr.erec = nullptr;
+    Pr.diag = nullptr;
+  }
+  PFF_TRY(add_kernel<R>(m, g, d, KP_RHS, Pr, &n_rhs));
   if (plan.pers()) {
     PFF_TRY(add_pers<R>(m, plan, g, {n_rhs}, P, &n_loop));
   } else if (P.model == kAT1) {
@@ -1668,10 +1689,12 @@ static pff_status mesh_build_t(pff_mesh *m, const double *xy_d, const int32_t *t
   const int64_t Ne4 = (Ne + 3) / 4 * 4;
   PFF_TRY(dalloc((ERec<R> **)&m->rec, Ne4));
   CUDA_TRY(cudaMemset(m->rec, 0, Ne4 * sizeof(ERec<R>)));
-  PFF_TRY(dalloc((DRec<R> **)&m->drec, Ne4));
-  // valid (zero) node ids until the first solve writes the records: a
-  // matvec timed before any right-hand side reads in bounds
-  CUDA_TRY(cudaMemset(m->drec, 0, Ne4 * sizeof(DRec<R>)));
+  if (sizeof(R) == 8) {
+    PFF_TRY(dalloc((DRec<R> **)&m->drec, Ne4));
+    // valid (zero) node ids until the first solve writes the records: a
+    // matvec timed before any right-hand side reads in bounds
+    CUDA_TRY(cudaMemset(m->drec, 0, Ne4 * sizeof(DRec<R>)));
+  }
   PFF_TRY(dalloc((typename V<R>::T2 **)&m->fext, N));
   PFF_TRY(dalloc((R **)&m->minv, N));
   PFF_TRY(dalloc((typename V<R>::T2 **)&m->pz, N + 2));
@@ -2368,6 +2391,7 @@ struct pff_ckpt {
   void *ub[2] = {nullptr, nullptr}, *vb[2] = {nullptr, nullptr}, *ab[2] = {nullptr, nullptr};
   void *Hb[2] = {nullptr, nullptr};
   void *db = nullptr, *dbn = nullptr, *g = nullptr, *lam = nullptr, *Hcur = nullptr;
+  void *fe = nullptr, *fd = nullptr;  // element shares of the reverse mechanics
   double *gc = nullptr;
   int *kctr = nullptr;
   int64_t adj_iters = 0;  // adjoint CG iterations of the last pff_backward
@@ -2384,7 +2408,7 @@ static void ckpt_free(pff_ckpt *c) {
   free_graph(c->rev_g[1]);
   void *p[] = {c->su, c->sv, c->sa, c->sd, c->sH, c->tu, c->tx, c->td, c->tH, c->wu, c->wv, c->wa, c->wd,
                c->segd, c->wH, c->segH, c->ub[0], c->ub[1], c->vb[0], c->vb[1], c->ab[0], c->ab[1], c->Hb[0],
-               c->Hb[1], c->db, c->dbn, c->g, c->lam, c->Hcur, c->gc, c->kctr};
+               c->Hb[1], c->db, c->dbn, c->g, c->lam, c->Hcur, c->fe, c->fd, c->gc, c->kctr};
   for (void *q : p)
     if (q) cudaFree(q);
   delete c;
@@ -2426,6 +2450,8 @@ static pff_status ckpt_alloc(pff_ckpt *c) {
   PFF_TRY(A(&c->g, N * r));
   PFF_TRY(A(&c->lam, N * r));
   PFF_TRY(A(&c->Hcur, (Ne + 3) / 4 * 4 * r));  // whole groups of 4: see build_stage
+  PFF_TRY(A(&c->fe, 3 * Ne * r2));
+  PFF_TRY(A(&c->fd, Ne * r));
   PFF_TRY(A((void **)&c->gc, 8));
   PFF_TRY(A((void **)&c->kctr, 4 * sizeof(int)));
   return PFF_OK;
@@ -2480,17 +2506,27 @@ static pff_status build_reverse_graph(pff_mesh *m, pff_ckpt *c, AdjParams<R> A, 
   if (!pers) CUDA_TRY(cudaGraphConditionalHandleCreate(&A.P.cond_inner, g, 1, cudaGraphCondAssignDefault));
   A.P.use_cond = pers ? 0 : 1;
   void *aa[] = {(void *)&A};
-  void *ka[] = {(void *)&c->kctr};
-  cudaGraphNode_t n_load, n_prep, n_rhs, n_loop, n_mv, n_up, n_terms, n_mech, n_done;
+  cudaGraphNode_t n_load, n_rhs, n_loop, n_mv, n_up, n_mech, n_node;
   cudaGraph_t body;
-  // the adjoint solve's operator is A(H_n+1): its damage records are built
-  // from the step's history once k_adj_load has loaded it
+  // the adjoint solve's operator is A(H_n+1).  FP32 solves on entry
+  // records: k_adj_rhs reads H_n+1 from the tape and writes the records.
+  // FP64 element records, and the staged and fused families, need H_n+1 in
+  // the kernel precision first (k_adj_load).
+  const bool need_h = sizeof(R) == 8 || plan.st() || plan.fused();
+  A.h_tape = need_h ? 0 : 1;
   void *pa[] = {(void *)&A.P};
-  cudaGraphNode_t n_drec;
-  pff_status st = add_generic(g, {}, (const void *)k_adj_load<R>, Ge, kThreads, 0, aa, &n_load);
-  if (st == PFF_OK) st = add_generic(g, {n_load}, (const void *)k_drec_build<R>, Ge, kThreads, 0, pa, &n_drec);
-  if (st == PFF_OK) st = add_generic(g, {n_drec}, (const void *)k_adj_prep<R>, Gn, kThreads, 0, aa, &n_prep);
-  if (st == PFF_OK) st = add_generic(g, {n_prep}, (const void *)k_adj_rhs<R>, Gn, kThreads, 0, aa, &n_rhs);
+  std::vector<cudaGraphNode_t> dep;
+  pff_status st = PFF_OK;
+  if (need_h) {
+    st = add_generic(g, {}, (const void *)k_adj_load<R>, Ge, kThreads, 0, aa, &n_load);
+    dep = {n_load};
+    if (st == PFF_OK && sizeof(R) == 8) {
+      cudaGraphNode_t n_drec;
+      st = add_generic(g, dep, (const void *)k_drec_build<R>, Ge, kThreads, 0, pa, &n_drec);
+      dep = {n_drec};
+    }
+  }
+  if (st == PFF_OK) st = add_generic(g, dep, (const void *)k_adj_rhs<R>, Gn, kThreads, 0, aa, &n_rhs);
   if (pers) {
     if (st == PFF_OK) st = add_pers<R>(m, plan, g, {n_rhs}, A.P, &n_loop);
   } else {
@@ -2498,10 +2534,8 @@ static pff_status build_reverse_graph(pff_mesh *m, pff_ckpt *c, AdjParams<R> A, 
     if (st == PFF_OK) st = add_kernel<R>(m, body, {}, KP_MATVEC, A.P, &n_mv);
     if (st == PFF_OK) st = add_kernel<R>(m, body, {n_mv}, KP_UPDATE, A.P, &n_up);
   }
-  if (st == PFF_OK)
-    st = add_generic(g, {n_loop}, (const void *)k_adj_dmg_terms<R>, Ge, kThreads, 0, aa, &n_terms);
-  if (st == PFF_OK) st = add_generic(g, {n_terms}, (const void *)k_adj_mech<R>, Gn, kThreads, 0, aa, &n_mech);
-  if (st == PFF_OK) st = add_generic(g, {n_mech}, (const void *)k_adj_step_done, 1, 32, 0, ka, &n_done);
+  if (st == PFF_OK) st = add_generic(g, {n_loop}, (const void *)k_adj_mech_elem<R>, Ge, kThreads, 0, aa, &n_mech);
+  if (st == PFF_OK) st = add_generic(g, {n_mech}, (const void *)k_adj_mech_node<R>, Gn, kThreads, 0, aa, &n_node);
   if (st != PFF_OK) {
     cudaGraphDestroy(g);
     return st;
@@ -2578,6 +2612,7 @@ static pff_status backward_t(pff_mesh *m, pff_ckpt *c, const void *dL_dd, const 
       A.P.Hr = (const R *)c->Hcur;
       A.P.dt = c->dt;
       A.kctr = c->kctr;
+      A.kdec = c->kctr;
       A.tape_u = (const R2 *)c->tu;
       A.tape_x = (const R *)c->tx;
       A.tape_d = (const R *)c->td;
@@ -2597,8 +2632,9 @@ static pff_status backward_t(pff_mesh *m, pff_ckpt *c, const void *dL_dd, const 
       A.dbn = (R *)c->dbn;
       A.g = (R *)c->g;
       A.Hb_in = (const R *)c->Hb[pin];
-      A.Hb_acc = (R *)c->Hb[pin];
       A.Hb_out = (R *)c->Hb[1 - pin];
+      A.fe = (R2 *)c->fe;
+      A.fd = (R *)c->fd;
       A.gc = c->gc;
       A.gce = dL_dGc_field;
       A.astat = c->kctr + 1;
