@@ -1354,39 +1354,53 @@ __device__ __forceinline__ void cta_sum(typename Acc<R>::T (&v)[NV], typename Ac
   __syncthreads();  // sh is free again
 }
 
-// Warp 0 sums the gridDim.x partials of the barrier just passed in a fixed
-// order (lane l takes partials l, l + 32, ..., four loads in flight, then
-// a shuffle tree); thread 0 gets the totals in tot.
+// The CTA sums the gridDim.x partials of the barrier just passed in a fixed
+// order: thread t of the first kPartWarps warps takes partials t, t + 256,
+// ... (all its loads in flight: one L2 round trip for up to 512 CTAs), each
+// warp folds its lanes by a shuffle tree, and thread 0 adds the warps' sums
+// in warp order into tot.  Every CTA runs the same order, so all hold
+// bit-identical totals.  Called by every thread of the CTA (blockDim.x >=
+// 32 kPartWarps); sh is a free [>= kPartWarps][NV] scratch, free again on
+// return.
+constexpr int kPartWarps = 8;
 template <typename R, int NV>
-__device__ __forceinline__ void grid_partials(const double *part, double *tot) {
+__device__ __forceinline__ void grid_partials(const double *part, double *tot, typename Acc<R>::T (*sh)[NV]) {
   typedef Acc<R> A;
-  if (threadIdx.x >= 32) return;
-  typename A::T w[NV];
-#pragma unroll
-  for (int k = 0; k < NV; ++k) w[k] = A::zero();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int nb = (int)gridDim.x;
-  for (int j0 = (int)threadIdx.x; j0 < nb; j0 += 128) {
-    typename A::T buf[4][NV];
+  constexpr int T = 32 * kPartWarps;
+  if (wid < kPartWarps) {
+    typename A::T w[NV];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int j = j0 + 32 * u;
+    for (int k = 0; k < NV; ++k) w[k] = A::zero();
+    for (int j0 = (int)threadIdx.x; j0 < nb; j0 += 2 * T) {
+      typename A::T b0[NV], b1[NV];
+      const int j1 = j0 + T;
 #pragma unroll
-      for (int k = 0; k < NV; ++k) buf[u][k] = j < nb ? A::load(&part[(size_t)j * NV + k]) : A::zero();
+      for (int k = 0; k < NV; ++k) {
+        b0[k] = A::load(&part[(size_t)j0 * NV + k]);
+        b1[k] = j1 < nb ? A::load(&part[(size_t)j1 * NV + k]) : A::zero();
+      }
+#pragma unroll
+      for (int k = 0; k < NV; ++k) w[k] = A::add(A::add(w[k], b0[k]), b1[k]);
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+    for (int k = 0; k < NV; ++k) {
 #pragma unroll
-      for (int k = 0; k < NV; ++k) w[k] = A::add(w[k], buf[u][k]);
+      for (int o = 16; o > 0; o >>= 1) w[k] = A::add(w[k], A::shfl(w[k], o));
+      if (lane == 0) sh[wid][k] = w[k];
+    }
   }
-#pragma unroll
-  for (int k = 0; k < NV; ++k) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) w[k] = A::add(w[k], A::shfl(w[k], o));
-  }
+  __syncthreads();
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int k = 0; k < NV; ++k) tot[k] = A::to_d(w[k]);
+    for (int k = 0; k < NV; ++k) {
+      typename A::T s = sh[0][k];
+      for (int q = 1; q < kPartWarps; ++q) s = A::add(s, sh[q][k]);
+      tot[k] = A::to_d(s);
+    }
   }
+  __syncthreads();  // sh is free again, tot is visible to every thread
 }
 
 struct NoHook {
@@ -1427,7 +1441,7 @@ __device__ __forceinline__ bool grid_sum(typename Acc<R>::T (&v)[NV], double *pa
   }
   __syncthreads();
   if (!*ok_sh) return false;
-  grid_partials<R, NV>(part, tot);
+  grid_partials<R, NV>(part, tot, sh);
   return true;
 }
 
