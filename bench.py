@@ -54,6 +54,8 @@ def parse():
                     help="gather schedule (0 = autotuned; 1..5 fixed, see pff_options.variant)")
     ap.add_argument("--cg-kernel", choices=["auto", "phases", "persistent", "staged", "fused", "fused_staged"],
                     default="auto", help="AT2 CG loop (pff_options.cg_kernel; auto = autotuned)")
+    ap.add_argument("--no-precision", action="store_true",
+                    help="skip the FP64 run and the FP32-vs-FP64 error of the benchmark plate")
     ap.add_argument("--no-qs", action="store_true",
                     help="skip the quasi-static single-edge-notched tension measurement")
     ap.add_argument("--qs-only", action="store_true",
@@ -387,6 +389,44 @@ def subcycled(pff, dev, config, steps=100, warmup=10):
                 status=int(mesh.sync_status()))
 
 
+def precision_check(pff, dev, config, steps=997, warmup=3):
+    """The precision policy on the benchmark plate: the same steps in FP64
+    (the parity mode, itself checked against the oracle by the tests) and in
+    FP32_MIXED from the same zero state; the FP64 run is timed (CUDA events
+    after `warmup` steps), and the FP32 fields are compared with it at the
+    end of the window: relative L2 error of u and max |d32 - d64| (stated
+    tolerances 1e-4 and 1e-3 over a pre-branching window)."""
+    import torch
+    c = S.config(config)
+    out = {}
+    for prec in ("fp64", "fp32"):
+        mesh = pff.Mesh.from_plate(c["mesh"], precision=prec)
+        dt = mesh.set_material(c["material"], c["cfl"])
+        opts = pff.options(cg_tol=c["cg_tol"], t_ramp=c["t_ramp"])
+        st = mesh.new_state(device=dev)
+        mesh.run(st, warmup, opts=opts)
+        torch.cuda.synchronize()
+        stream = torch.cuda.current_stream()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        mesh.run(st, steps, step0=warmup, opts=opts)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        out[prec] = dict(ms_per_step=ms, value=mesh.N / (ms / 1e3), status=int(mesh.sync_status()),
+                         u=st["u"].double(), d=st["d"].double())
+        del mesh
+    u64, u32 = out["fp64"].pop("u"), out["fp32"].pop("u")
+    d64, d32 = out["fp64"].pop("d"), out["fp32"].pop("d")
+    return dict(workload=config, steps=warmup + steps, window_us=dt * (warmup + steps) * 1e6,
+                fp64=out["fp64"], fp32=out["fp32"],
+                fp32_vs_fp64=dict(u_rel_l2=float(torch.linalg.norm(u32 - u64) / torch.linalg.norm(u64)),
+                                  d_max_abs=float((d32 - d64).abs().max()), d_max=float(d64.max()),
+                                  tolerances=dict(u_rel_l2=1e-4, d_max_abs=1e-3)),
+                speedup_fp32_over_fp64=out["fp64"]["ms_per_step"] / out["fp32"]["ms_per_step"])
+
+
 def quasistatic(pff, dev, increments=5, n=700, compare_increments=2):
     """Quasi-static single-edge-notched tension (Sec. 3.5): the 700 x 700
     unit square, the first `increments` of the 100 equal load increments to
@@ -588,6 +628,8 @@ def run_ours(args):
         line["batched"] = batched(pff, dev)
     if not args.no_qs:
         line["quasistatic"] = quasistatic(pff, dev, args.qs_increments)
+    if not args.no_precision:
+        line["precision"] = precision_check(pff, dev, args.config)
     if not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline(args)
     print(json.dumps(line), flush=True)
