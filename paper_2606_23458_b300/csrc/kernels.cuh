@@ -610,8 +610,10 @@ __global__ void __launch_bounds__(256) k_force_ep(Params<R> P) {
 // entries U at a time with all U gathers issued before use (independent
 // load chains); sums in the same ascending order, so the result is
 // bit-identical to the entry-parallel schedule.
+// FP32: at most 40 registers, so that six blocks share an SM (the gather is
+// latency-bound: more warps in flight hide more of it).
 template <typename R, int U>
-__global__ void __launch_bounds__(256) k_force_nc(Params<R> P) {
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 6 : 1) k_force_nc(Params<R> P) {
   const double S = load_scale(P, 1);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.N; i += gridDim.x * blockDim.x) {
     R fx = 0, fy = 0;
