@@ -1655,31 +1655,26 @@ __device__ __forceinline__ void fused_rows(const Params<float> &P, float al, flo
     const float un = v.w * rn;
     P.x[j] = fmaf(al, p, P.x[j]);
     P.cgp[j] = p;
-    float wq = 0.f;
+    // entry records (FP32 meshes always carry them; only the staged
+    // families, which use local_rows, run without): diag_j u_j, then per
+    // slot c_b u_b + c_c u_c with the neighbours' u rebuilt from their
+    // records
+    float wq = P.diag[j] * un;
     for (int k = 0; k < P.D; k += U) {
-      float c[U];
-      int en[U];
+      float4 er[U];
 #pragma unroll
-      for (int u = 0; u < U; ++u) en[u] = k + u < P.D ? __ldg(&P.ell[(size_t)(k + u) * P.N + j]) : -1;
+      for (int u = 0; u < U; ++u)
+        er[u] = k + u < P.D ? __ldg(&P.erec[(size_t)(k + u) * P.N + j]) : make_float4(__int_as_float(-1), 0.f, 0.f, 0.f);
+      float c[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        if (en[u] < 0) continue;
-        const int e = en[u] >> 2, a = en[u] & 3;
-        int4 t;
-        float A;
-        float4 G;
-        load_elem(P, e, t, A, G);
-        const float h = P.Hr[e], sg = gc_scale(P, e);
-        const float kA = (P.kappa * sg) * A;
-        const float mA = (P.cbase * sg + 2.f * h) * A * (1.f / 12.f);
-        const float u0 = a == 0 ? un : cg_unew(vin[t.x], al, be);
-        const float u1 = a == 1 ? un : cg_unew(vin[t.y], al, be);
-        const float u2 = a == 2 ? un : cg_unew(vin[t.z], al, be);
-        c[u] = elem_row<float>(G, a, kA, mA, u0, u1, u2);
+        const int nb = __float_as_int(er[u].x);
+        if (nb >= 0)
+          c[u] = fmaf(er[u].z, cg_unew(vin[nb], al, be), __fmul_rn(er[u].w, cg_unew(vin[__float_as_int(er[u].y)], al, be)));
       }
 #pragma unroll
       for (int u = 0; u < U; ++u)
-        if (en[u] >= 0) wq = radd(wq, c[u]);
+        if (__float_as_int(er[u].x) >= 0) wq = __fadd_rn(wq, c[u]);
     }
     vout[j] = make_float4(rn, wq, sn, v.w);
     const float sr = P.rscale * rn;
@@ -1693,7 +1688,8 @@ __device__ __forceinline__ void fused_rows(const Params<float> &P, float al, flo
 // memory: localized element records (n0 | n1 << 16, n2 as positions in vs,
 // kappa A, (cbase + 2 H) A / 12, gradients), the rows' entries
 // (slot[k * mc + row - row0]) and the neighbourhood's (r, w, s, 1/diag) in
-// vs, own rows from position own.  Same arithmetic as fused_rows.
+// vs, own rows from position own.  The recurrences of fused_rows, with the
+// operator rebuilt per entry from the localized records.
 template <int U>
 __device__ __forceinline__ void local_rows(const Params<float> &P, float al, float be, const float4 *vs, int own,
                                            int row0, int row1, const uint16_t *slot, int mc, const float4 *srec,

@@ -442,7 +442,7 @@ static inline unsigned fam_grid(const pff_mesh *m, int fam, int U, bool fp32) {
   switch (fam) {
     case kFamPersistent: return m->pgrid[U];
     case kFamStaged: return stage ? m->st_grid : 0u;
-    case kFamFused: return fp32 ? m->fgrid[U] : 0u;
+    case kFamFused: return fp32 && m->erec ? m->fgrid[U] : 0u;  // reads the entry records
     case kFamFusedStaged: return stage && m->st_fused ? m->st_grid : 0u;
     default: return 0u;
   }
@@ -1004,10 +1004,10 @@ static pff_status append_solve(const pff_mesh *m, cudaGraph_t g, cudaGraphNode_t
   std::vector<cudaGraphNode_t> d;
   if (dep) d.push_back(dep);
   cudaGraphNode_t n_rhs, n_loop, n_fin;
-  // the fused and staged families keep their own operator data: their
-  // right-hand side skips the entry records
+  // the staged families keep their own operator data in shared memory:
+  // their right-hand side skips the entry records
   Params<R> Pr = P;
-  if (plan.fused() || plan.st()) {
+  if (plan.st()) {
     Pr.erec = nullptr;
     Pr.diag = nullptr;
   }
@@ -2510,9 +2510,9 @@ static pff_status build_reverse_graph(pff_mesh *m, pff_ckpt *c, AdjParams<R> A, 
   cudaGraph_t body;
   // the adjoint solve's operator is A(H_n+1).  FP32 solves on entry
   // records: k_adj_rhs reads H_n+1 from the tape and writes the records.
-  // FP64 element records, and the staged and fused families, need H_n+1 in
-  // the kernel precision first (k_adj_load).
-  const bool need_h = sizeof(R) == 8 || plan.st() || plan.fused();
+  // FP64 element records, and the staged families, need H_n+1 in the kernel
+  // precision first (k_adj_load).
+  const bool need_h = sizeof(R) == 8 || plan.st();
   A.h_tape = need_h ? 0 : 1;
   void *pa[] = {(void *)&A.P};
   std::vector<cudaGraphNode_t> dep;
