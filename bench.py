@@ -180,6 +180,21 @@ def dist_env():
     return ws, rank, lrank
 
 
+def job_throughput(ms_local, units_per_rank, steps, device=None):
+    """Whole-job throughput of independent replicas: the slowest rank's
+    timed region (max over ranks when a process group is up) and the units
+    all ranks processed.  Returns (value per second, max ms)."""
+    import torch
+    ws = 1
+    t_max = float(ms_local)
+    if torch.distributed.is_available() and torch.distributed.is_initialized():
+        ws = torch.distributed.get_world_size()
+        t = torch.tensor([t_max], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(t.item())
+    return ws * units_per_rank * steps / (t_max / 1e3), t_max
+
+
 def algorithmic_bytes(N, Ne, prec):
     """Bytes the method must move, by kernel (FP32_MIXED unless prec=fp64).
     Element data: connectivity 12 B, geometry (4 independent shape
@@ -559,16 +574,11 @@ def run_ours(args):
     prof = mesh.profile_kernels(st, reps=5, opts=opts)
 
     # aggregate over ranks
-    t_max = ms
-    if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(t.item())
+    value, t_max = job_throughput(ms, N, args.steps, device=dev)
     if rank != 0:
         if ws > 1:
             torch.distributed.destroy_process_group()
         return
-    value = ws * N * args.steps / (t_max / 1e3)
     ab = algorithmic_bytes(N, Ne, args.prec)
     per_step = {k: prof[k] for k in ("predict", "force", "rhs", "finish")}
     ms_launch = {k: prof[k] for k in per_step}
