@@ -229,8 +229,9 @@ __global__ void __launch_bounds__(256) kb_rhs(Params<R> P, Batch B) {
   }
 }
 
+// FP32: at most 40 registers (six blocks per SM; the gather is latency-bound).
 template <typename R, int U>
-__global__ void __launch_bounds__(256) kb_matvec(Params<R> P, Batch B) {
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 6 : 1) kb_matvec(Params<R> P, Batch B) {
   typedef Acc<R> AC;
   const int p = B.blk_plate[blockIdx.x];
   if (B.sc[p].inner_done) return;  // converged plate
@@ -245,7 +246,7 @@ __global__ void __launch_bounds__(256) kb_matvec(Params<R> P, Batch B) {
       const R pc = pnew(Q, i, beta);
       bool done = false;
       if constexpr (sizeof(R) == 4) {
-        if (Q.erec) {
+        if (has_erec(Q)) {
           // FP32 entry records (see matvec_rows)
           q = erec_row<U>(Q, i, beta, pc);
           done = true;

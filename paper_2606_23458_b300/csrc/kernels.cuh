@@ -145,6 +145,11 @@ template <typename R> struct Params {
                  // two nodes b, c of the entry's element and their row
                  // coefficients (w_ab + mA, w_ac + mA); b = -1 marks an empty
                  // slot.  Nullable.
+  uint32_t *ecmp; // FP32, compact form of the same (meshes whose elements span
+  float2 *ecf;    // fewer than 2^15 node ids): ecmp packs the 16-bit offsets
+                  // b - i (low half) and c - i (high half), ecf the two
+                  // coefficients; an empty slot is offsets 0, coefficients 0.
+                  // Nullable; at most one of erec and ecmp is set.
   R *diag;       // with erec: the row's diagonal sum over entries of
                  // (kappa_e A_e |grad phi_a|^2 + 2 mA)
   const R *gcs; // per-element toughness field as Gc_e / Gc (nullable: uniform);
@@ -664,14 +669,27 @@ __device__ __forceinline__ R elem_row(const R4 &G, int a, R kA, R mA, R x0, R x1
 // (the element stiffness rows sum to zero, so row a of the element operator
 // is exactly this split).
 template <typename R>
-__device__ __forceinline__ float4 make_erec(const int4 &t, const typename Params<R>::R4 &G, int a, R kA, R mA) {
+__device__ __forceinline__ bool has_erec(const Params<R> &P) {
+  return P.erec != nullptr || P.ecmp != nullptr;
+}
+
+// Writes the entry record of slot a of an element at (slot k, node i).
+template <typename R>
+__device__ __forceinline__ void put_erec(const Params<R> &P, int k, int i, const int4 &t,
+                                         const typename Params<R>::R4 &G, int a, R kA, R mA) {
   R gx, gy, gbx, gby, gcx, gcy;
   slot_grad<R>(G, a, gx, gy);
   slot_grad<R>(G, a == 0 ? 1 : 0, gbx, gby);
   slot_grad<R>(G, a == 2 ? 1 : 2, gcx, gcy);
   const int nb = a == 0 ? t.y : t.x, nc = a == 2 ? t.y : t.z;
-  return make_float4(__int_as_float(nb), __int_as_float(nc), (float)(kA * (gx * gbx + gy * gby) + mA),
-                     (float)(kA * (gx * gcx + gy * gcy) + mA));
+  const float cb = (float)(kA * (gx * gbx + gy * gby) + mA), cc = (float)(kA * (gx * gcx + gy * gcy) + mA);
+  const size_t q = (size_t)k * P.N + i;
+  if (P.ecmp) {
+    P.ecmp[q] = (uint32_t)(uint16_t)(int16_t)(nb - i) | ((uint32_t)(uint16_t)(int16_t)(nc - i) << 16);
+    P.ecf[q] = make_float2(cb, cc);
+  } else {
+    P.erec[q] = make_float4(__int_as_float(nb), __int_as_float(nc), cb, cc);
+  }
 }
 
 // The damage record of an element from its geometry and coefficients.
@@ -762,13 +780,13 @@ __device__ __forceinline__ typename Params<R>::R4 rhs_entry(const Params<R> &P, 
   R gx, gy;
   slot_grad<R>(G, a, gx, gy);
   if (a == 0 && P.drec) P.drec[e] = make_drec<R>(t, G, kA, mA);
-  if (P.erec) {
+  if (has_erec(P)) {
     // the entry's incidence slot: given, or from its CSR position
     if (slot < 0 && csr >= 0) {
       node = a == 0 ? t.x : (a == 1 ? t.y : t.z);
       slot = csr - __ldg(&P.ptr[node]);
     }
-    if (slot >= 0) P.erec[(size_t)slot * P.N + node] = make_erec<R>(t, G, a, kA, mA);
+    if (slot >= 0) put_erec(P, slot, node, t, G, a, kA, mA);
   }
   R4 o;
   o.x = w * A * (R(1) / R(3));
@@ -930,9 +948,31 @@ __device__ __forceinline__ R pnew(const Params<R> &P, int j, R beta) {
 // Row i of q = A p_new from the FP32 entry records: diag_i p_i, then per
 // incidence slot in order (U records in flight) c_b p_b + c_c p_c, rounded
 // the same way in every schedule (explicit fma and non-contracted adds).
+// Compact records add an exact 0 for empty slots.
 template <int U>
 __device__ __forceinline__ float erec_row(const Params<float> &P, int i, float beta, float pc) {
   float q = P.diag[i] * pc;
+  if (P.ecmp) {
+    for (int k = 0; k < P.D; k += U) {
+      uint32_t w[U];
+      float2 cf[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const bool in = k + u < P.D;
+        w[u] = in ? __ldg(&P.ecmp[(size_t)(k + u) * P.N + i]) : 0u;
+        cf[u] = in ? __ldg(&P.ecf[(size_t)(k + u) * P.N + i]) : make_float2(0.f, 0.f);
+      }
+      float c[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int ob = (int)(int16_t)(w[u] & 0xffffu), oc = (int)w[u] >> 16;
+        c[u] = fmaf(cf[u].x, pnew(P, i + ob, beta), __fmul_rn(cf[u].y, pnew(P, i + oc, beta)));
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) q = __fadd_rn(q, c[u]);
+    }
+    return q;
+  }
   for (int k = 0; k < P.D; k += U) {
     float4 er[U];
 #pragma unroll
@@ -1041,7 +1081,7 @@ __global__ void __launch_bounds__(256) k_cg_matvec_ep(Params<R> P) {
   typename AC::T vals[1] = {AC::zero()};
   const R beta = sc_beta<R>(P.sc);
   if constexpr (sizeof(R) == 4) {
-    if (P.erec) {
+    if (has_erec(P)) {
       // FP32 entry records: rows of the block's nodes, the same per-row
       // arithmetic as the node-centric schedules
       for (int b = blockIdx.x; b < P.nblk; b += gridDim.x) {
@@ -1094,7 +1134,7 @@ __device__ __forceinline__ void matvec_rows(const Params<R> &P, R beta, int i0, 
                                             typename Acc<R>::T &acc) {
   typedef Acc<R> AC;
   if constexpr (sizeof(R) == 4) {
-    if (P.erec) {
+    if (has_erec(P)) {
       // FP32 entry records: the row's diagonal times its own value, then per
       // entry the two other nodes' values times their coefficients (the
       // records stream in coalesced; only the p gathers are indirect)
@@ -1660,21 +1700,42 @@ __device__ __forceinline__ void fused_rows(const Params<float> &P, float al, flo
     // slot c_b u_b + c_c u_c with the neighbours' u rebuilt from their
     // records
     float wq = P.diag[j] * un;
-    for (int k = 0; k < P.D; k += U) {
-      float4 er[U];
+    if (P.ecmp) {
+      for (int k = 0; k < P.D; k += U) {
+        uint32_t w[U];
+        float2 cf[U];
 #pragma unroll
-      for (int u = 0; u < U; ++u)
-        er[u] = k + u < P.D ? __ldg(&P.erec[(size_t)(k + u) * P.N + j]) : make_float4(__int_as_float(-1), 0.f, 0.f, 0.f);
-      float c[U];
+        for (int u = 0; u < U; ++u) {
+          const bool in = k + u < P.D;
+          w[u] = in ? __ldg(&P.ecmp[(size_t)(k + u) * P.N + j]) : 0u;
+          cf[u] = in ? __ldg(&P.ecf[(size_t)(k + u) * P.N + j]) : make_float2(0.f, 0.f);
+        }
+        float c[U];
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int nb = __float_as_int(er[u].x);
-        if (nb >= 0)
-          c[u] = fmaf(er[u].z, cg_unew(vin[nb], al, be), __fmul_rn(er[u].w, cg_unew(vin[__float_as_int(er[u].y)], al, be)));
+        for (int u = 0; u < U; ++u) {
+          const int ob = (int)(int16_t)(w[u] & 0xffffu), oc = (int)w[u] >> 16;
+          c[u] = fmaf(cf[u].x, cg_unew(vin[j + ob], al, be), __fmul_rn(cf[u].y, cg_unew(vin[j + oc], al, be)));
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) wq = __fadd_rn(wq, c[u]);
       }
+    } else {
+      for (int k = 0; k < P.D; k += U) {
+        float4 er[U];
 #pragma unroll
-      for (int u = 0; u < U; ++u)
-        if (__float_as_int(er[u].x) >= 0) wq = __fadd_rn(wq, c[u]);
+        for (int u = 0; u < U; ++u)
+          er[u] = k + u < P.D ? __ldg(&P.erec[(size_t)(k + u) * P.N + j]) : make_float4(__int_as_float(-1), 0.f, 0.f, 0.f);
+        float c[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int nb = __float_as_int(er[u].x);
+          if (nb >= 0)
+            c[u] = fmaf(er[u].z, cg_unew(vin[nb], al, be), __fmul_rn(er[u].w, cg_unew(vin[__float_as_int(er[u].y)], al, be)));
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (__float_as_int(er[u].x) >= 0) wq = __fadd_rn(wq, c[u]);
+      }
     }
     vout[j] = make_float4(rn, wq, sn, v.w);
     const float sr = P.rscale * rn;

@@ -266,6 +266,9 @@ struct pff_mesh {
   void *rec = nullptr, *fext = nullptr, *minv = nullptr;
   void *drec = nullptr;  // FP64: DRec<double> per element, the damage operator of the current solve
   float4 *erec = nullptr;  // FP32: damage entry records of the current solve (D x N, incidence layout)
+  uint32_t *ecmp = nullptr;  // FP32, compact entry records: packed 16-bit neighbour offsets (D x N)
+  float2 *ecf = nullptr;     // FP32, compact entry records: coefficients (D x N)
+  int64_t span = 0;          // largest node-id difference within an element
   float *diagf = nullptr;  // FP32: the damage rows' diagonals (N)
   double *area_d = nullptr;
   uint8_t *flags = nullptr;
@@ -335,7 +338,8 @@ static void mesh_free(pff_mesh *m) {
   free_graph(m->step_g);
   free_graph(m->mech_g);
   void *ptrs[] = {m->gcs, m->st_cta, m->st_rng, m->st_nrng, m->st_lrec, m->st_slot, m->cgv, m->cgp,
-                  m->ptr, m->ent, m->ell, m->rec, m->drec, m->erec, m->diagf, m->fext, m->minv, m->area_d,
+                  m->ptr, m->ent, m->ell, m->rec, m->drec, m->erec, m->ecmp, m->ecf, m->diagf, m->fext, m->minv,
+                  m->area_d,
                   m->flags,
                   m->x, m->r, m->b, m->part, m->energy, m->wext, m->pz, m->q, m->dinv,
                   m->Hf, m->freef, m->ticket, m->sc, m->status_word, m->step_ctr, m->stab};
@@ -442,7 +446,7 @@ static inline unsigned fam_grid(const pff_mesh *m, int fam, int U, bool fp32) {
   switch (fam) {
     case kFamPersistent: return m->pgrid[U];
     case kFamStaged: return stage ? m->st_grid : 0u;
-    case kFamFused: return fp32 && m->erec ? m->fgrid[U] : 0u;  // reads the entry records
+    case kFamFused: return fp32 && (m->erec || m->ecmp) ? m->fgrid[U] : 0u;  // reads the entry records
     case kFamFusedStaged: return stage && m->st_fused ? m->st_grid : 0u;
     default: return 0u;
   }
@@ -779,12 +783,19 @@ static pff_status configure(pff_mesh *m) {
     k_build_ell<<<grid_for(m->N, 256), 256>>>(m->ptr, m->ent, m->N, D, m->ell);
     CUDA_TRY(cudaGetLastError());
   }
-  if (sizeof(R) == 4 && !m->erec) {
-    // every slot empty (node id -1) until a right-hand side writes it: empty
-    // padding slots stay so, and a matvec timed before any solve reads in
-    // bounds
-    PFF_TRY(dalloc(&m->erec, (size_t)D * m->N));
-    CUDA_TRY(cudaMemset(m->erec, 0xff, (size_t)D * m->N * sizeof(float4)));
+  if (sizeof(R) == 4 && !m->erec && !m->ecmp) {
+    // every slot empty until a right-hand side writes it (node id -1, or
+    // offsets 0 with coefficients 0 in the compact form): empty padding
+    // slots stay so, and a matvec timed before any solve reads in bounds
+    if (m->span < 32768) {
+      PFF_TRY(dalloc(&m->ecmp, (size_t)D * m->N));
+      CUDA_TRY(cudaMemset(m->ecmp, 0, (size_t)D * m->N * sizeof(uint32_t)));
+      PFF_TRY(dalloc(&m->ecf, (size_t)D * m->N));
+      CUDA_TRY(cudaMemset(m->ecf, 0, (size_t)D * m->N * sizeof(float2)));
+    } else {
+      PFF_TRY(dalloc(&m->erec, (size_t)D * m->N));
+      CUDA_TRY(cudaMemset(m->erec, 0xff, (size_t)D * m->N * sizeof(float4)));
+    }
     PFF_TRY(dalloc(&m->diagf, (size_t)m->N));
     CUDA_TRY(cudaMemset(m->diagf, 0, (size_t)m->N * sizeof(float)));
   }
@@ -885,6 +896,8 @@ static Params<R> base_params(pff_mesh *m, const pff_options &o) {
   P.rec = (const ERec<R> *)m->rec;
   P.drec = (DRec<R> *)m->drec;
   P.erec = m->erec;
+  P.ecmp = m->ecmp;
+  P.ecf = m->ecf;
   P.diag = (R *)m->diagf;
   P.flags = m->flags;
   P.st_cta = m->st_cta;
@@ -1009,6 +1022,8 @@ static pff_status append_solve(const pff_mesh *m, cudaGraph_t g, cudaGraphNode_t
   Params<R> Pr = P;
   if (plan.st()) {
     Pr.erec = nullptr;
+    Pr.ecmp = nullptr;
+    Pr.ecf = nullptr;
     Pr.diag = nullptr;
   }
   PFF_TRY(add_kernel<R>(m, g, d, KP_RHS, Pr, &n_rhs));
@@ -1928,6 +1943,10 @@ pff_status pff_mesh_create(int64_t N, const double *xy, int64_t Ne, const int32_
   pff_mesh *m = new pff_mesh();
   m->N = N;
   m->Ne = Ne;
+  for (int64_t e = 0; e < Ne; ++e) {
+    const int32_t a = tri[3 * e], b = tri[3 * e + 1], c = tri[3 * e + 2];
+    m->span = std::max<int64_t>(m->span, (int64_t)std::max(a, std::max(b, c)) - std::min(a, std::min(b, c)));
+  }
   m->prec = precision;
   m->rs = precision == PFF_FP64 ? 8 : 4;
   cudaGetDevice(&m->device);
