@@ -953,6 +953,27 @@ template <int U>
 __device__ __forceinline__ float erec_row(const Params<float> &P, int i, float beta, float pc) {
   float q = P.diag[i] * pc;
   if (P.ecmp) {
+    if (U >= 3 && P.D <= 6) {
+      // the whole row at once: six slots' records, then their twelve
+      // neighbour gathers in flight together (slots past D add an exact 0)
+      uint32_t w[6];
+      float2 cf[6];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        const bool in = k < P.D;
+        w[k] = in ? __ldg(&P.ecmp[(size_t)k * P.N + i]) : 0u;
+        cf[k] = in ? __ldg(&P.ecf[(size_t)k * P.N + i]) : make_float2(0.f, 0.f);
+      }
+      float c[6];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        const int ob = (int)(int16_t)(w[k] & 0xffffu), oc = (int)w[k] >> 16;
+        c[k] = fmaf(cf[k].x, pnew(P, i + ob, beta), __fmul_rn(cf[k].y, pnew(P, i + oc, beta)));
+      }
+#pragma unroll
+      for (int k = 0; k < 6; ++k) q = __fadd_rn(q, c[k]);
+      return q;
+    }
     for (int k = 0; k < P.D; k += U) {
       uint32_t w[U];
       float2 cf[U];
