@@ -826,10 +826,10 @@ static pff_status configure(pff_mesh *m) {
   for (int U = 1; U <= 4; ++U) {
     int occ = 0;
     CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pers_fun<R>(U), kPersThreads, 0));
-    // the fewest CTAs that give no thread more rows than a full wave would
+    // a full wave (every SM the same number of CTAs, so no SM carries more
+    // rows than its share), or fewer CTAs on a mesh too small to fill it
     const int64_t wave = (int64_t)nsm * occ;
-    const int64_t rows = std::max<int64_t>(1, (m->N + kPersThreads * wave - 1) / (kPersThreads * wave));
-    const int64_t ctas = std::max<int64_t>(1, (m->N + kPersThreads * rows - 1) / (kPersThreads * rows));
+    const int64_t ctas = std::max<int64_t>(1, (m->N + kPersThreads - 1) / kPersThreads);
     m->pgrid[U] = coop && occ > 0 ? (unsigned)std::min<int64_t>(ctas, wave) : 0u;
   }
   if constexpr (sizeof(R) == 4) {
@@ -841,9 +841,8 @@ static pff_status configure(pff_mesh *m) {
       int occ = 0;
       constexpr int T = FusedCfg<false>::threads;
       CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, plan_fun<float>(c), T, 0));
-      const int64_t wave = (int64_t)nsm * occ;
-      const int64_t rows = std::max<int64_t>(1, (m->N + T * wave - 1) / (T * wave));
-      const int64_t ctas = std::max<int64_t>(1, (m->N + T * rows - 1) / (T * rows));
+      const int64_t wave = (int64_t)nsm * occ;  // a full wave, as for the persistent loop
+      const int64_t ctas = std::max<int64_t>(1, (m->N + T - 1) / T);
       m->fgrid[U] = coop && occ > 0 ? (unsigned)std::min<int64_t>(ctas, wave) : 0u;
     }
     if (!m->cgv) {
