@@ -180,7 +180,7 @@ __device__ __forceinline__ void adj_rhs_entry(const AdjParams<R> &A, const Slot<
   R gx, gy;
   slot_grad<R>(G, a, gx, gy);
   dgc = kA * (gx * gx + gy * gy) + R(2) * mA;
-  if (has_erec(P)) put_erec(P, k, i, t, G, a, kA, mA);
+  if (has_erec(P)) put_erec(P, k, i, G, a, kA, mA);
   const R l0 = (P.flags[t.x] & kNotch) ? R(0) : P.x[t.x];
   const R l1 = (P.flags[t.y] & kNotch) ? R(0) : P.x[t.y];
   const R l2 = (P.flags[t.z] & kNotch) ? R(0) : P.x[t.z];

@@ -673,22 +673,47 @@ __device__ __forceinline__ bool has_erec(const Params<R> &P) {
   return P.erec != nullptr || P.ecmp != nullptr;
 }
 
-// Writes the entry record of slot a of an element at (slot k, node i).
+// Writes the coefficients of the entry record of slot a of an element at
+// (slot k, node i); the neighbour ids or offsets depend on the mesh alone
+// and are written once (k_erec_ids).
 template <typename R>
-__device__ __forceinline__ void put_erec(const Params<R> &P, int k, int i, const int4 &t,
-                                         const typename Params<R>::R4 &G, int a, R kA, R mA) {
+__device__ __forceinline__ void put_erec(const Params<R> &P, int k, int i, const typename Params<R>::R4 &G, int a,
+                                         R kA, R mA) {
   R gx, gy, gbx, gby, gcx, gcy;
   slot_grad<R>(G, a, gx, gy);
   slot_grad<R>(G, a == 0 ? 1 : 0, gbx, gby);
   slot_grad<R>(G, a == 2 ? 1 : 2, gcx, gcy);
-  const int nb = a == 0 ? t.y : t.x, nc = a == 2 ? t.y : t.z;
-  const float cb = (float)(kA * (gx * gbx + gy * gby) + mA), cc = (float)(kA * (gx * gcx + gy * gcy) + mA);
+  const float2 c = make_float2((float)(kA * (gx * gbx + gy * gby) + mA), (float)(kA * (gx * gcx + gy * gcy) + mA));
   const size_t q = (size_t)k * P.N + i;
-  if (P.ecmp) {
-    P.ecmp[q] = (uint32_t)(uint16_t)(int16_t)(nb - i) | ((uint32_t)(uint16_t)(int16_t)(nc - i) << 16);
-    P.ecf[q] = make_float2(cb, cc);
-  } else {
-    P.erec[q] = make_float4(__int_as_float(nb), __int_as_float(nc), cb, cc);
+  if (P.ecmp)
+    P.ecf[q] = c;
+  else
+    reinterpret_cast<float2 *>(P.erec + q)[1] = c;
+}
+
+// The mesh-only half of the entry records, once per mesh: per incidence
+// slot the other two nodes of the entry's element (16-bit offsets from the
+// row packed in one word, or the ids in the 16-byte form); empty slots get
+// offsets 0 (or ids -1).  Coefficients start at 0.
+template <typename R>
+__global__ void __launch_bounds__(256) k_erec_ids(const ERec<R> *rec, const int *ell, int N, int D, uint32_t *ecmp,
+                                                  float4 *erec) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    for (int k = 0; k < D; ++k) {
+      const size_t q = (size_t)k * N + i;
+      const int en = __ldg(&ell[q]);
+      int nb = -1, nc = -1;
+      if (en >= 0) {
+        const ERec<R> &r = rec[en >> 2];
+        const int a = en & 3;
+        nb = a == 0 ? r.n1 : r.n0;
+        nc = a == 2 ? r.n1 : r.n2;
+      }
+      if (ecmp)
+        ecmp[q] = en < 0 ? 0u : ((uint32_t)(uint16_t)(int16_t)(nb - i) | ((uint32_t)(uint16_t)(int16_t)(nc - i) << 16));
+      else
+        erec[q] = make_float4(__int_as_float(nb), __int_as_float(nc), 0.f, 0.f);
+    }
   }
 }
 
@@ -786,7 +811,7 @@ __device__ __forceinline__ typename Params<R>::R4 rhs_entry(const Params<R> &P, 
       node = a == 0 ? t.x : (a == 1 ? t.y : t.z);
       slot = csr - __ldg(&P.ptr[node]);
     }
-    if (slot >= 0) put_erec(P, slot, node, t, G, a, kA, mA);
+    if (slot >= 0) put_erec(P, slot, node, G, a, kA, mA);
   }
   R4 o;
   o.x = w * A * (R(1) / R(3));

@@ -784,18 +784,20 @@ static pff_status configure(pff_mesh *m) {
     CUDA_TRY(cudaGetLastError());
   }
   if (sizeof(R) == 4 && !m->erec && !m->ecmp) {
-    // every slot empty until a right-hand side writes it (node id -1, or
-    // offsets 0 with coefficients 0 in the compact form): empty padding
-    // slots stay so, and a matvec timed before any solve reads in bounds
+    // the neighbour half of the records is the mesh's and is written here;
+    // every coefficient is 0 until a right-hand side writes it (empty
+    // padding slots stay so, and a matvec timed before any solve reads in
+    // bounds)
     if (m->span < 32768) {
       PFF_TRY(dalloc(&m->ecmp, (size_t)D * m->N));
-      CUDA_TRY(cudaMemset(m->ecmp, 0, (size_t)D * m->N * sizeof(uint32_t)));
       PFF_TRY(dalloc(&m->ecf, (size_t)D * m->N));
       CUDA_TRY(cudaMemset(m->ecf, 0, (size_t)D * m->N * sizeof(float2)));
     } else {
       PFF_TRY(dalloc(&m->erec, (size_t)D * m->N));
-      CUDA_TRY(cudaMemset(m->erec, 0xff, (size_t)D * m->N * sizeof(float4)));
     }
+    k_erec_ids<R><<<std::min<unsigned>(grid_for(m->N, 256), 148 * 8), 256>>>(
+        (const ERec<R> *)m->rec, m->ell, (int)m->N, D, m->ecmp, m->erec);
+    CUDA_TRY(cudaGetLastError());
     PFF_TRY(dalloc(&m->diagf, (size_t)m->N));
     CUDA_TRY(cudaMemset(m->diagf, 0, (size_t)m->N * sizeof(float)));
   }
