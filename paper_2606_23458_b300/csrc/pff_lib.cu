@@ -1751,9 +1751,10 @@ static pff_status qs_run_t(pff_mesh *m, const pff_state *st, const uint8_t *bc_h
   K2 *fe = nullptr;
   QRec<K> *rec = nullptr;
   QsScalars *qs = nullptr;
+  SolveScalars *bsc = nullptr;  // grid-barrier counter and abort flag of the persistent CG
   pff_status res = PFF_OK;
   auto cleanup = [&]() {
-    void *ptrs[] = {bc, pz, r, q, x, dg, fe, rec, qs};
+    void *ptrs[] = {bc, pz, r, q, x, dg, fe, rec, qs, bsc};
     for (void *p : ptrs)
       if (p) cudaFree(p);
   };
@@ -1774,6 +1775,7 @@ static pff_status qs_run_t(pff_mesh *m, const pff_state *st, const uint8_t *bc_h
   QS_TRY(dalloc(&qs, 1));
   QS_TRY(dalloc(&rec, m->Ne));
   QS_TRY(dalloc(&fe, 3 * m->Ne));
+  QS_TRY(dalloc(&bsc, 1));
   if (cudaMemcpyAsync(bc, bc_host, N, cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemsetAsync(qs, 0, sizeof(QsScalars), s) != cudaSuccess) {
     cleanup();
@@ -1805,6 +1807,18 @@ static pff_status qs_run_t(pff_mesh *m, const pff_state *st, const uint8_t *bc_h
   const unsigned Gn = std::min<unsigned>(grid_for(N, kThreads), m->grid[KP_UPDATE][0]);
   const unsigned Ge = std::min<unsigned>(grid_for(m->Ne, kThreads), m->grid[KP_UPDATE][0]);
   const unsigned Gf = grid_for(m->Ne, kThreads);  // element pass: one element per thread, no reduction
+  // the tangent CG as one cooperative launch per Newton step: a full wave
+  // of co-resident CTAs (0: not available, the kernel-per-phase loop runs)
+  unsigned Gp = 0;
+  {
+    int dev = 0, coop = 0, nsm = 0, occ = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_qs_cg_persistent<K>, kQsPersThreads, 0));
+    const int64_t work = std::max<int64_t>(1, (std::max(N, m->Ne) + kQsPersThreads - 1) / kQsPersThreads);
+    if (coop && occ > 0) Gp = (unsigned)std::min<int64_t>(work, (int64_t)nsm * occ);
+  }
   QsScalars hs;
   auto read = [&]() -> pff_status {
     CUDA_TRY(cudaMemcpyAsync(&hs, qs, sizeof(hs), cudaMemcpyDeviceToHost, s));
@@ -1831,14 +1845,33 @@ static pff_status qs_run_t(pff_mesh *m, const pff_state *st, const uint8_t *bc_h
       I.tol = std::min(qo.eta_max, std::max(qo.eta_min, 0.1 * qo.newton_tol * fn / rn));
       k_qs_elem_tangent<R, K><<<Ge, kThreads, 0, s>>>(Q);
       k_qs_setup<K><<<Gn, kThreads, 0, s>>>(I);
-      for (;;) {
-        for (int b = 0; b < 32; ++b) {
-          k_qs_elem_apply<K><<<Gf, kThreads, 0, s>>>(I, (int)m->Ne);
-          k_qs_matvec<K><<<Gn, kThreads, 0, s>>>(I);
-          k_qs_update<K><<<Gn, kThreads, 0, s>>>(I);
+      if (Gp) {
+        if (cudaMemsetAsync(bsc, 0, sizeof(SolveScalars), s) != cudaSuccess) {
+          cleanup();
+          return fail(PFF_ERR_CUDA, "quasi-static CG barrier reset");
+        }
+        int ne = (int)m->Ne;
+        void *args[] = {(void *)&I, (void *)&ne, (void *)&bsc};
+        if (cudaLaunchCooperativeKernel((const void *)k_qs_cg_persistent<K>, dim3(Gp), dim3(kQsPersThreads), args, 0,
+                                        s) != cudaSuccess) {
+          cleanup();
+          return fail(PFF_ERR_CUDA, "quasi-static CG launch");
         }
         QS_TRY(read());
-        if (hs.done) break;
+      } else {
+        for (;;) {
+          for (int b = 0; b < 32; ++b) {
+            k_qs_elem_apply<K><<<Gf, kThreads, 0, s>>>(I, (int)m->Ne);
+            k_qs_matvec<K><<<Gn, kThreads, 0, s>>>(I);
+            k_qs_update<K><<<Gn, kThreads, 0, s>>>(I);
+          }
+          QS_TRY(read());
+          if (hs.done) break;
+        }
+      }
+      if (hs.status == kStTimeout) {
+        cleanup();
+        return fail(PFF_ERR_TIMEOUT, "a grid-barrier wait of the quasi-static CG timed out");
       }
       cg += hs.iters;
       if (hs.status == kStNonfinite) {

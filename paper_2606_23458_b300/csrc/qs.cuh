@@ -376,6 +376,149 @@ __global__ void __launch_bounds__(256) k_qs_update(QkParams<K> I) {
   }
 }
 
+// The tangent CG of one Newton step in one cooperative launch (persistent
+// CTAs): per iteration the element pass, a grid barrier, the node pass with
+// a grid all-reduce of p.q, the update with a grid all-reduce of
+// (|r|^2, r.z) -- the per-row arithmetic of k_qs_elem_apply, k_qs_matvec and
+// k_qs_update, with every CTA taking the same decisions from bit-identical
+// totals.  B holds the barrier counter and abort flag (zeroed before the
+// launch); waits are bounded, and a CTA that gives up makes every CTA leave
+// and the solve report kStTimeout.
+constexpr int kQsPersThreads = 512;
+template <typename K>
+__global__ void __launch_bounds__(kQsPersThreads, 2) k_qs_cg_persistent(QkParams<K> I, int Ne, SolveScalars *B) {
+  typedef Acc<K> AC;
+  typedef typename V<K>::T2 K2;
+  __shared__ typename AC::T sh[kQsPersThreads / 32][2];
+  __shared__ double tot[2];
+  __shared__ int ok_sh, flag;
+  __shared__ double rho, rr, pq, alpha_d, beta_d;
+  __shared__ int iters, status;
+  QsScalars *S = I.qs;
+  if (S->done) return;  // the set-up found r_0 = 0
+  if (threadIdx.x == 0) {
+    rho = S->rho;
+    rr = 0.0;
+    pq = 0.0;
+    alpha_d = 0.0;
+    beta_d = 0.0;
+    iters = 0;
+    status = 0;
+  }
+  __syncthreads();
+  const unsigned int nb = gridDim.x;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+  unsigned int nbar = 0;
+  bool done = false;
+  for (;;) {
+    const K beta = (K)beta_d;
+    // element pass: the slot forces of K_T p_new
+    for (int e = tid; e < Ne; e += stride) {
+      int n0, n1, n2;
+      K t[9], g[4];
+      qrec_load(I.rec + e, n0, n1, n2, t, g);
+      const K2 p0 = qs_pnew(I, n0, beta), p1 = qs_pnew(I, n1, beta), p2 = qs_pnew(I, n2, beta);
+      const K ax0 = p0.x - p2.x, ax1 = p1.x - p2.x, ay0 = p0.y - p2.y, ay1 = p1.y - p2.y;
+      const K de[3] = {g[0] * ax0 + g[2] * ax1, g[1] * ay0 + g[3] * ay1,
+                       K(0.5) * (g[1] * ax0 + g[3] * ax1 + g[0] * ay0 + g[2] * ay1)};
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        K2 f;
+        qs_slot_force(t, g, a, de, f.x, f.y);
+        I.fe[(size_t)3 * e + a] = f;
+      }
+    }
+    typename AC::T v0[1] = {AC::zero()};
+    ++nbar;
+    if (!grid_sum<K, 1>(v0, I.part + (nbar & 1u) * 2u * nb, B, nbar * nb, tot, (typename AC::T(*)[1])sh, &ok_sh))
+      break;
+    // node pass: q = gathered slot forces, p_new . q
+    typename AC::T v1[1] = {AC::zero()};
+    for (int i = tid; i < I.N; i += stride) {
+      K qx = 0, qy = 0;
+      for (int k = 0; k < I.D; ++k) {
+        const int en = __ldg(&I.ell[(size_t)k * I.N + i]);
+        if (en < 0) continue;
+        const K2 f = I.fe[(size_t)3 * (en >> 2) + (en & 3)];
+        qx = radd(qx, f.x);
+        qy = radd(qy, f.y);
+      }
+      if (qs_fx(I.bc, i)) qx = K(0);
+      if (qs_fy(I.bc, i)) qy = K(0);
+      K2 q;
+      q.x = qx;
+      q.y = qy;
+      I.q[i] = q;
+      const K2 pn = qs_pnew(I, i, beta);
+      v1[0] = AC::add(v1[0], AC::add(AC::prod(pn.x, qx), AC::prod(pn.y, qy)));
+    }
+    ++nbar;
+    if (!grid_sum<K, 1>(v1, I.part + (nbar & 1u) * 2u * nb, B, nbar * nb, tot, (typename AC::T(*)[1])sh, &ok_sh))
+      break;
+    if (threadIdx.x == 0) {
+      pq = tot[0];
+      alpha_d = pq != 0.0 ? rho / pq : 0.0;
+    }
+    __syncthreads();
+    const K alpha = (K)alpha_d;
+    // update: x += alpha p_new, r -= alpha q, z = r / diag, (p, z) stored
+    typename AC::T v2[2] = {AC::zero(), AC::zero()};
+    for (int i = tid; i < I.N; i += stride) {
+      const K2 pn = qs_pnew(I, i, beta), q = I.q[i], dg = I.dg[i];
+      K2 x = I.x[i], r = I.r[i];
+      x.x = fma(alpha, pn.x, x.x);
+      x.y = fma(alpha, pn.y, x.y);
+      r.x = fma(-alpha, q.x, r.x);
+      r.y = fma(-alpha, q.y, r.y);
+      if (qs_fx(I.bc, i)) r.x = K(0);
+      if (qs_fy(I.bc, i)) r.y = K(0);
+      I.x[i] = x;
+      I.r[i] = r;
+      typename V<K>::T4 pz;
+      pz.x = pn.x;
+      pz.y = r.x / dg.x;
+      pz.z = pn.y;
+      pz.w = r.y / dg.y;
+      I.pz[i] = pz;
+      v2[0] = AC::add(v2[0], AC::add(AC::prod(r.x, r.x), AC::prod(r.y, r.y)));
+      v2[1] = AC::add(v2[1], AC::add(AC::prod(r.x, pz.y), AC::prod(r.y, pz.w)));
+    }
+    ++nbar;
+    if (!grid_sum<K, 2>(v2, I.part + (nbar & 1u) * 2u * nb, B, nbar * nb, tot, sh, &ok_sh)) break;
+    if (threadIdx.x == 0) {
+      iters += 1;
+      rr = tot[0];
+      flag = 0;
+      if (!(tot[0] == tot[0]) || isinf(tot[0])) {
+        status = kStNonfinite;
+        flag = 1;
+      } else if (pq == 0.0 || sqrt(tot[0]) <= I.tol * sqrt(S->rr0)) {
+        flag = 1;
+      } else if (iters >= I.max_it) {
+        status = kStNotConverged;
+        flag = 1;
+      }
+      beta_d = rho != 0.0 ? tot[1] / rho : 0.0;
+      rho = tot[1];
+    }
+    __syncthreads();
+    if (flag) {
+      done = true;
+      break;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    S->iters = iters;
+    S->rr = rr;
+    S->pq = pq;
+    S->rho = rho;
+    S->alpha = alpha_d;
+    S->beta = beta_d;
+    S->status = done ? status : kStTimeout;
+    S->done = 1;
+  }
+}
+
 // u += x on the free dofs.
 template <typename R, typename K>
 __global__ void __launch_bounds__(256) k_qs_apply(QsParams<R, K> Q) {
