@@ -1752,9 +1752,11 @@ static pff_status qs_run_t(pff_mesh *m, const pff_state *st, const uint8_t *bc_h
   QRec<K> *rec = nullptr;
   QsScalars *qs = nullptr;
   SolveScalars *bsc = nullptr;  // grid-barrier counter and abort flag of the persistent CG
+  uint32_t *ofs = nullptr;      // FP32 entry records of the tangent (row form)
+  float4 *kb = nullptr, *kc = nullptr;
   pff_status res = PFF_OK;
   auto cleanup = [&]() {
-    void *ptrs[] = {bc, pz, r, q, x, dg, fe, rec, qs, bsc};
+    void *ptrs[] = {bc, pz, r, q, x, dg, fe, rec, qs, bsc, ofs, kb, kc};
     for (void *p : ptrs)
       if (p) cudaFree(p);
   };
@@ -1776,6 +1778,15 @@ static pff_status qs_run_t(pff_mesh *m, const pff_state *st, const uint8_t *bc_h
   QS_TRY(dalloc(&rec, m->Ne));
   QS_TRY(dalloc(&fe, 3 * m->Ne));
   QS_TRY(dalloc(&bsc, 1));
+  // row form of the tangent CG: FP32 Krylov on a mesh whose elements span
+  // fewer than 2^15 node ids (16-bit neighbour offsets)
+  const bool rows = sizeof(K) == 4 && m->span < 32768;
+  if (rows) {
+    const size_t DN = (size_t)m->D * N;
+    QS_TRY(dalloc(&ofs, DN));
+    QS_TRY(dalloc(&kb, DN));
+    QS_TRY(dalloc(&kc, DN));
+  }
   if (cudaMemcpyAsync(bc, bc_host, N, cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemsetAsync(qs, 0, sizeof(QsScalars), s) != cudaSuccess) {
     cleanup();
@@ -1800,6 +1811,9 @@ static pff_status qs_run_t(pff_mesh *m, const pff_state *st, const uint8_t *bc_h
   I.x = x;
   I.dg = dg;
   I.fe = fe;
+  I.ofs = ofs;
+  I.kb = kb;
+  I.kc = kc;
   I.qs = qs;
   I.part = Q.P.part;
   I.ticket = Q.P.ticket;
@@ -1815,8 +1829,11 @@ static pff_status qs_run_t(pff_mesh *m, const pff_state *st, const uint8_t *bc_h
     CUDA_TRY(cudaGetDevice(&dev));
     CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
     CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_qs_cg_persistent<K>, kQsPersThreads, 0));
-    const int64_t work = std::max<int64_t>(1, (std::max(N, m->Ne) + kQsPersThreads - 1) / kQsPersThreads);
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &occ, rows ? (const void *)k_qs_cg_rows<kQsRowGathers> : (const void *)k_qs_cg_persistent<K>, kQsPersThreads,
+        0));
+    const int64_t work =
+        std::max<int64_t>(1, ((rows ? N : std::max(N, m->Ne)) + kQsPersThreads - 1) / kQsPersThreads);
     if (coop && occ > 0) Gp = (unsigned)std::min<int64_t>(work, (int64_t)nsm * occ);
   }
   QsScalars hs;
@@ -1851,9 +1868,24 @@ static pff_status qs_run_t(pff_mesh *m, const pff_state *st, const uint8_t *bc_h
           return fail(PFF_ERR_CUDA, "quasi-static CG barrier reset");
         }
         int ne = (int)m->Ne;
-        void *args[] = {(void *)&I, (void *)&ne, (void *)&bsc};
-        if (cudaLaunchCooperativeKernel((const void *)k_qs_cg_persistent<K>, dim3(Gp), dim3(kQsPersThreads), args, 0,
-                                        s) != cudaSuccess) {
+        cudaError_t le;
+        if constexpr (sizeof(K) == 4) {
+          if (rows) {
+            k_qs_entry_build<<<Gn, kThreads, 0, s>>>(I);
+            void *args[] = {(void *)&I, (void *)&bsc};
+            le = cudaLaunchCooperativeKernel((const void *)k_qs_cg_rows<kQsRowGathers>, dim3(Gp),
+                                             dim3(kQsPersThreads), args, 0, s);
+          } else {
+            void *args[] = {(void *)&I, (void *)&ne, (void *)&bsc};
+            le = cudaLaunchCooperativeKernel((const void *)k_qs_cg_persistent<K>, dim3(Gp), dim3(kQsPersThreads),
+                                             args, 0, s);
+          }
+        } else {
+          void *args[] = {(void *)&I, (void *)&ne, (void *)&bsc};
+          le = cudaLaunchCooperativeKernel((const void *)k_qs_cg_persistent<K>, dim3(Gp), dim3(kQsPersThreads), args,
+                                           0, s);
+        }
+        if (le != cudaSuccess) {
           cleanup();
           return fail(PFF_ERR_CUDA, "quasi-static CG launch");
         }

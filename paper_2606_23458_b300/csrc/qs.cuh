@@ -53,6 +53,15 @@ template <typename K> struct QkParams {
   K4 *pz;             // (p_x, z_x, p_y, z_y) per node
   K2 *r, *q, *x, *dg; // residual, K_T p, the Newton step, Jacobi diagonal
   K2 *fe;             // 3 Ne: per element and slot the force A B_a^T C_T B p_e
+  // FP32 entry records of the tangent (nullable; meshes whose elements span
+  // fewer than 2^15 node ids): per incidence slot k of node i (at k N + i)
+  // the 16-bit offsets of the entry's other two nodes b, c (packed) and the
+  // 2 x 2 blocks K_ab, K_ac of the element tangent (row-major xx, xy, yx,
+  // yy).  The element's rows annihilate translations (K_aa = -K_ab - K_ac),
+  // so row i is sum_k K_ab (p_b - p_i) + K_ac (p_c - p_i): a rigid
+  // translation gives exactly 0 in FP32 too, and no diagonal block is kept
+  uint32_t *ofs;
+  float4 *kb, *kc;
   QsScalars *qs;
   double *part;       // per-block partial sums and the ticket of reduce_last
   unsigned int *ticket;
@@ -385,6 +394,7 @@ __global__ void __launch_bounds__(256) k_qs_update(QkParams<K> I) {
 // launch); waits are bounded, and a CTA that gives up makes every CTA leave
 // and the solve report kStTimeout.
 constexpr int kQsPersThreads = 512;
+constexpr int kQsRowGathers = 2;  // incidence slots in flight per round in k_qs_cg_rows
 template <typename K>
 __global__ void __launch_bounds__(kQsPersThreads, 2) k_qs_cg_persistent(QkParams<K> I, int Ne, SolveScalars *B) {
   typedef Acc<K> AC;
@@ -485,6 +495,184 @@ __global__ void __launch_bounds__(kQsPersThreads, 2) k_qs_cg_persistent(QkParams
     }
     ++nbar;
     if (!grid_sum<K, 2>(v2, I.part + (nbar & 1u) * 2u * nb, B, nbar * nb, tot, sh, &ok_sh)) break;
+    if (threadIdx.x == 0) {
+      iters += 1;
+      rr = tot[0];
+      flag = 0;
+      if (!(tot[0] == tot[0]) || isinf(tot[0])) {
+        status = kStNonfinite;
+        flag = 1;
+      } else if (pq == 0.0 || sqrt(tot[0]) <= I.tol * sqrt(S->rr0)) {
+        flag = 1;
+      } else if (iters >= I.max_it) {
+        status = kStNotConverged;
+        flag = 1;
+      }
+      beta_d = rho != 0.0 ? tot[1] / rho : 0.0;
+      rho = tot[1];
+    }
+    __syncthreads();
+    if (flag) {
+      done = true;
+      break;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    S->iters = iters;
+    S->rr = rr;
+    S->pq = pq;
+    S->rho = rho;
+    S->alpha = alpha_d;
+    S->beta = beta_d;
+    S->status = done ? status : kStTimeout;
+    S->done = 1;
+  }
+}
+
+// The 2 x 2 block K_ab of the element tangent (the force on slot a per unit
+// displacement of slot b): columns are the unit x and y displacements.
+template <typename K>
+__device__ __forceinline__ float4 qs_block(const K (&t)[9], const K (&g)[4], int a, int b) {
+  const K gx = b == 0 ? g[0] : (b == 1 ? g[2] : -(g[0] + g[2]));
+  const K gy = b == 0 ? g[1] : (b == 1 ? g[3] : -(g[1] + g[3]));
+  const K ex[3] = {gx, K(0), K(0.5) * gy}, ey[3] = {K(0), gy, K(0.5) * gx};
+  K xx, yx, xy, yy;
+  qs_slot_force(t, g, a, ex, xx, yx);
+  qs_slot_force(t, g, a, ey, xy, yy);
+  return make_float4((float)xx, (float)xy, (float)yx, (float)yy);
+}
+
+// The pair block K_ab evaluated the same way from either end (the lower
+// slot's block, transposed for the higher), so that the stored operator is
+// exactly symmetric, as CG needs.
+template <typename K>
+__device__ __forceinline__ float4 qs_pair_block(const K (&t)[9], const K (&g)[4], int a, int b) {
+  if (a < b) return qs_block(t, g, a, b);
+  const float4 m = qs_block(t, g, b, a);
+  return make_float4(m.x, m.z, m.y, m.w);
+}
+
+// Entry records of the tangent, once per Newton step (node-parallel over
+// the incidence): per slot the neighbour offsets and blocks K_ab, K_ac;
+// empty slots get zero offsets and zero blocks (they add an exact 0).
+__global__ void __launch_bounds__(256) k_qs_entry_build(QkParams<float> I) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < I.N; i += gridDim.x * blockDim.x) {
+    for (int k = 0; k < I.D; ++k) {
+      const size_t q = (size_t)k * I.N + i;
+      const int en = __ldg(&I.ell[q]);
+      if (en < 0) {
+        I.ofs[q] = 0u;
+        I.kb[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        I.kc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        continue;
+      }
+      const int a = en & 3;
+      int n0, n1, n2;
+      float t[9], g[4];
+      qrec_load(I.rec + (en >> 2), n0, n1, n2, t, g);
+      const int b = a == 0 ? 1 : 0, c = a == 2 ? 1 : 2;
+      const int nb = b == 0 ? n0 : n1, nc = c == 1 ? n1 : n2;
+      I.ofs[q] = (uint32_t)(uint16_t)(int16_t)(nb - i) | ((uint32_t)(uint16_t)(int16_t)(nc - i) << 16);
+      I.kb[q] = qs_pair_block(t, g, a, b);
+      I.kc[q] = qs_pair_block(t, g, a, c);
+    }
+  }
+}
+
+// The tangent CG of one Newton step on the entry records, one cooperative
+// launch: per iteration the node rows q_i = sum_k (K_ab (p_b - p_i) +
+// K_ac (p_c - p_i)) with a grid all-reduce of p.q, then the update with a grid
+// all-reduce of (|r|^2, r.z) -- two grid barriers per iteration instead of
+// the element pass's three.  Decisions and bounded waits as in
+// k_qs_cg_persistent.
+template <int U>
+__global__ void __launch_bounds__(kQsPersThreads, 2) k_qs_cg_rows(QkParams<float> I, SolveScalars *B) {
+  typedef Acc<float> AC;
+  typedef float2 K2;
+  __shared__ typename AC::T sh[kQsPersThreads / 32][2];
+  __shared__ double tot[2];
+  __shared__ int ok_sh, flag;
+  __shared__ double rho, rr, pq, alpha_d, beta_d;
+  __shared__ int iters, status;
+  QsScalars *S = I.qs;
+  if (S->done) return;
+  if (threadIdx.x == 0) {
+    rho = S->rho;
+    rr = 0.0;
+    pq = 0.0;
+    alpha_d = 0.0;
+    beta_d = 0.0;
+    iters = 0;
+    status = 0;
+  }
+  __syncthreads();
+  const unsigned int nb = gridDim.x;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+  unsigned int nbar = 0;
+  bool done = false;
+  for (;;) {
+    const float beta = (float)beta_d;
+    // rows: q = K_T p_new on the free dofs, p_new . q
+    typename AC::T v1[1] = {AC::zero()};
+    for (int i = tid; i < I.N; i += stride) {
+      const K2 pc = qs_pnew(I, i, beta);
+      float qx = 0.f, qy = 0.f;
+      for (int k = 0; k < I.D; k += U) {
+        uint32_t w[U];
+        float4 bb[U], cc[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const bool in = k + u < I.D;
+          const size_t q = (size_t)(k + u) * I.N + i;
+          w[u] = in ? __ldg(&I.ofs[q]) : 0u;
+          bb[u] = in ? __ldg(&I.kb[q]) : make_float4(0.f, 0.f, 0.f, 0.f);
+          cc[u] = in ? __ldg(&I.kc[q]) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const K2 pb = qs_pnew(I, i + (int)(int16_t)(w[u] & 0xffffu), beta);
+          const K2 pcc = qs_pnew(I, i + ((int)w[u] >> 16), beta);
+          const float bx = pb.x - pc.x, by = pb.y - pc.y, cx = pcc.x - pc.x, cy = pcc.y - pc.y;
+          const float fx = fmaf(bb[u].x, bx, fmaf(bb[u].y, by, fmaf(cc[u].x, cx, __fmul_rn(cc[u].y, cy))));
+          const float fy = fmaf(bb[u].z, bx, fmaf(bb[u].w, by, fmaf(cc[u].z, cx, __fmul_rn(cc[u].w, cy))));
+          qx = __fadd_rn(qx, fx);
+          qy = __fadd_rn(qy, fy);
+        }
+      }
+      if (qs_fx(I.bc, i)) qx = 0.f;
+      if (qs_fy(I.bc, i)) qy = 0.f;
+      I.q[i] = make_float2(qx, qy);
+      v1[0] = AC::add(v1[0], AC::add(AC::prod(pc.x, qx), AC::prod(pc.y, qy)));
+    }
+    ++nbar;
+    if (!grid_sum<float, 1>(v1, I.part + (nbar & 1u) * 2u * nb, B, nbar * nb, tot, (typename AC::T(*)[1])sh,
+                            &ok_sh))
+      break;
+    if (threadIdx.x == 0) {
+      pq = tot[0];
+      alpha_d = pq != 0.0 ? rho / pq : 0.0;
+    }
+    __syncthreads();
+    const float alpha = (float)alpha_d;
+    typename AC::T v2[2] = {AC::zero(), AC::zero()};
+    for (int i = tid; i < I.N; i += stride) {
+      const K2 pn = qs_pnew(I, i, beta), q = I.q[i], dg = I.dg[i];
+      K2 x = I.x[i], r = I.r[i];
+      x.x = fmaf(alpha, pn.x, x.x);
+      x.y = fmaf(alpha, pn.y, x.y);
+      r.x = fmaf(-alpha, q.x, r.x);
+      r.y = fmaf(-alpha, q.y, r.y);
+      if (qs_fx(I.bc, i)) r.x = 0.f;
+      if (qs_fy(I.bc, i)) r.y = 0.f;
+      I.x[i] = x;
+      I.r[i] = r;
+      const float4 pz = make_float4(pn.x, r.x / dg.x, pn.y, r.y / dg.y);
+      I.pz[i] = pz;
+      v2[0] = AC::add(v2[0], AC::add(AC::prod(r.x, r.x), AC::prod(r.y, r.y)));
+      v2[1] = AC::add(v2[1], AC::add(AC::prod(r.x, pz.y), AC::prod(r.y, pz.w)));
+    }
+    ++nbar;
+    if (!grid_sum<float, 2>(v2, I.part + (nbar & 1u) * 2u * nb, B, nbar * nb, tot, sh, &ok_sh)) break;
     if (threadIdx.x == 0) {
       iters += 1;
       rr = tot[0];
