@@ -80,3 +80,32 @@ def test_options_are_checked(pff):
     for kw in (dict(newton_tol=0.0), dict(eta_min=0.6), dict(eta_max=1.0), dict(newton_max=0)):
         with pytest.raises(pff.PffError):
             m.qs_run(st, bc, 1, 1e-7, **kw)
+
+
+def test_row_and_element_forms_agree(pff):
+    """The FP32 tangent CG runs in row form (per-slot pair blocks) when the
+    mesh's elements span fewer than 2^15 node ids, else in element form;
+    the same SENT plate, once in its natural numbering and once renumbered
+    by a random permutation, gives the same reactions and damage."""
+    import torch
+    p, bc = _sent(200, 200)
+    rng = np.random.default_rng(3)
+    N = p["xy"].shape[0]
+    perm = rng.permutation(N)
+    inv = np.argsort(perm)
+    q = dict(p, xy=np.ascontiguousarray(p["xy"][inv]), tri=np.ascontiguousarray(perm[p["tri"]].astype(np.int32)),
+             notch=np.ascontiguousarray(p["notch"][inv]),
+             tedges=np.ascontiguousarray(perm[p["tedges"]].astype(np.int32)))
+    t = q["tri"].astype(np.int64)
+    assert int((t.max(axis=1) - t.min(axis=1)).max()) >= 2 ** 15
+    mat = dict(S.material(2 * p["h"], split="amor"), E=210e9, nu=0.3, Gc=2700.0)
+    out = []
+    for pl, b in ((p, bc), (q, bc[inv])):
+        m = pff.Mesh.from_plate(pl, precision="fp64")
+        m.set_material(mat, 0.5)
+        st = m.new_state()
+        r = m.qs_run(st, b, 3, 2e-7, newton_tol=1e-8, opts=pff.options(cg_tol=1e-10))
+        torch.cuda.synchronize()
+        out.append((r["reaction"], to_np(st["d"])))
+    assert np.allclose(out[1][0], out[0][0], rtol=1e-6), (out[0][0], out[1][0])
+    assert np.max(np.abs(out[1][1][perm] - out[0][1])) <= 1e-6
