@@ -10,6 +10,7 @@
 * The 700 x 700 SENT: one load increment with the tangent CG in FP32 against
   the same increment with it in FP64 (the oracle cannot run this size in a
   test's time; both GPU runs converge the FP64 Newton residual to 1e-8).
+* The 64-plate batch: plates against their single-plate runs.
 """
 import numpy as np
 import pytest
@@ -108,3 +109,32 @@ def test_sent_full_size_increment(pff):
         out.append((r["reaction"][0], to_np(st["d"])))
     assert abs(out[0][0] - out[1][0]) <= 1e-7 * abs(out[1][0]), (out[0][0], out[1][0])
     assert np.abs(out[0][1] - out[1][1]).max() <= 1e-6
+
+
+def test_batch_workload_matches_single_plates(pff):
+    """The bench's 64-plate batch (5.24M nodes): after a few steps the
+    first, smallest and largest plates agree with their single-plate runs."""
+    import torch
+    plates = []
+    for dr in S.batch_draws(64, seed=1):
+        p = S.plate(dr["nx"], dr["ny"], jitter=0.1, seed=1, traction=dr["traction"])
+        plates.append((p, S.material(2 * p["h"], Gc=dr["Gc"])))
+    nsteps = 6
+    b = pff.Batch(plates, precision="fp32")
+    st = b.new_state()
+    log = torch.zeros(nsteps, b.nplates, dtype=torch.int32, device="cuda")
+    b.run(st, nsteps, iters_log=log)
+    torch.cuda.synchronize()
+    sizes = [p["xy"].shape[0] for p, _ in plates]
+    for k in sorted({0, int(np.argmin(sizes)), int(np.argmax(sizes))}):
+        p, mat = plates[k]
+        m = pff.Mesh.from_plate(p, precision="fp32")
+        m.set_material(mat, 0.5)
+        s1 = m.new_state()
+        l1 = torch.zeros(nsteps, 2, dtype=torch.int32, device="cuda")
+        m.run(s1, nsteps, iters_log=l1)
+        torch.cuda.synchronize()
+        v = b.plate(st, k)
+        assert rel_l2(to_np(v["u"]), to_np(s1["u"])) <= 2e-5, k
+        assert np.abs(to_np(v["d"]) - to_np(s1["d"])).max() <= 1e-4, k
+        assert np.abs(log[:, k].cpu().numpy() - l1[:, 0].cpu().numpy()).max() <= 1, k
