@@ -3,7 +3,9 @@ nodes are numbered so that some element spans 2^15 or more node ids gets
 the 16-byte records (explicit neighbour ids), the same plate in its natural
 numbering the compact ones (16-bit offsets).  Renumbering nodes does not
 change the physics, so both runs must agree after mapping the nodes back,
-for every CG family that reads the records and for the adjoint."""
+for every CG family that reads the records and for the adjoint; and a mesh
+whose nodes meet up to eight triangles (wider than the six-slot fast path)
+against the oracle."""
 import numpy as np
 import pytest
 
@@ -86,3 +88,38 @@ def test_wide_records_adjoint(pff, plates):
         ck.close()
         torch.cuda.synchronize()
     assert abs(grads[1] - grads[0]) <= 2e-3 * abs(grads[0]), grads
+
+
+def _union_jack(nx, ny):
+    """A plate whose quads are split along alternating diagonals, so that
+    nodes meet up to eight triangles (incidence width 8)."""
+    p = S.plate(nx, ny)
+    tri = []
+    for j in range(ny):
+        for i in range(nx):
+            n00 = j * (nx + 1) + i
+            n10, n01, n11 = n00 + 1, n00 + nx + 1, n00 + nx + 2
+            if (i + j) % 2 == 0:
+                tri += [(n00, n10, n11), (n00, n11, n01)]
+            else:
+                tri += [(n00, n10, n01), (n10, n11, n01)]
+    q = dict(p)
+    q["tri"] = np.ascontiguousarray(np.array(tri, dtype=np.int32))
+    return q
+
+
+@pytest.mark.parametrize("kind", ["phases", "persistent", "fused"])
+def test_incidence_wider_than_six(orc, pff, kind):
+    import torch
+    p = _union_jack(60, 24)
+    counts = np.bincount(p["tri"].ravel())
+    assert counts.max() == 8
+    mat = S.material(2 * p["h"])
+    cgk = {"phases": pff.PFF_CG_PHASES, "persistent": pff.PFF_CG_PERSISTENT, "fused": pff.PFF_CG_FUSED}[kind]
+    b, _ = _run(pff, p, mat, cgk)
+    om = orc.Mesh.from_plate(p)
+    dt = om.stable_dt(mat, 0.5)
+    ost = om.new_state()
+    om.run(mat, ost, 40, dt)
+    assert rel_l2(b["u"], ost["u"]) <= 1e-4
+    assert np.abs(b["d"] - ost["d"]).max() <= 1e-3
