@@ -350,6 +350,16 @@ static void mesh_free(pff_mesh *m) {
 
 static inline unsigned grid_for(int64_t n, int block) { return (unsigned)((n + block - 1) / block); }
 
+// A cap for grid-stride element/node loops: eight 256-thread blocks per SM
+// of the current device.
+static unsigned stride_cap() {
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) !=
+                                                 cudaSuccess || nsm <= 0)
+    nsm = 1;
+  return 8u * (unsigned)nsm;
+}
+
 enum KernelId { KP_PREDICT = 0, KP_FORCE, KP_RHS, KP_MATVEC, KP_UPDATE, KP_FINISH, KP_RESTART, KP_ENERGIES,
                 KP_COUNT };
 constexpr int kThreads = 256;
@@ -795,7 +805,7 @@ static pff_status configure(pff_mesh *m) {
     } else {
       PFF_TRY(dalloc(&m->erec, (size_t)D * m->N));
     }
-    k_erec_ids<R><<<std::min<unsigned>(grid_for(m->N, 256), 148 * 8), 256>>>(
+    k_erec_ids<R><<<std::min<unsigned>(grid_for(m->N, 256), stride_cap()), 256>>>(
         (const ERec<R> *)m->rec, m->ell, (int)m->N, D, m->ecmp, m->erec);
     CUDA_TRY(cudaGetLastError());
     PFF_TRY(dalloc(&m->diagf, (size_t)m->N));
@@ -963,7 +973,7 @@ static pff_status bind_history(pff_mesh *m, Params<R> &P, const double *H, cudaS
     P.Hr = (const R *)H;
   } else {
     P.Hr = (const R *)m->Hf;
-    k_h_mirror<<<std::min<unsigned>(grid_for(m->Ne, 256), 148 * 8), 256, 0, s>>>(H, m->Hf, (int)m->Ne);
+    k_h_mirror<<<std::min<unsigned>(grid_for(m->Ne, 256), stride_cap()), 256, 0, s>>>(H, m->Hf, (int)m->Ne);
     CUDA_TRY(cudaGetLastError());
   }
   return PFF_OK;
@@ -2396,7 +2406,7 @@ static pff_status noalloc_solve_t(pff_mesh *m, const double *H, const void *dpre
   } else {
     P.Hf = hf;
     P.Hr = (const R *)hf;
-    k_h_mirror<<<std::min<unsigned>(grid_for(m->Ne, 256), 148 * 8), 256, 0, s>>>(H, hf, (int)m->Ne);
+    k_h_mirror<<<std::min<unsigned>(grid_for(m->Ne, 256), stride_cap()), 256, 0, s>>>(H, hf, (int)m->Ne);
     CUDA_TRY(cudaGetLastError());
   }
   P.dprev = (const R *)dprev;
