@@ -487,6 +487,32 @@ def quasistatic(pff, dev, increments=5, n=700, compare_increments=2):
     return out
 
 
+def mechanics_only(pff, dev, config, steps=200, warmup=10):
+    """The explicit step without the damage solve (SURVEY metric: node-updates
+    per second with and without it): the same plate and step graph with the
+    damage solve never due (damage_every beyond the run), so each step is
+    the predictor, the force kernel with the history update and the
+    corrector."""
+    import torch
+    c = S.config(config)
+    mesh = pff.Mesh.from_plate(c["mesh"], precision="fp32")
+    mesh.set_material(c["material"], c["cfl"])
+    opts = pff.options(cg_tol=c["cg_tol"], t_ramp=c["t_ramp"], damage_every=warmup + steps + 1)
+    st = mesh.new_state(device=dev)
+    mesh.run(st, warmup, opts=opts)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    mesh.run(st, steps, step0=warmup, opts=opts)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    return dict(workload=config, steps=steps, value=mesh.N * steps / (ms / 1e3), unit="node-updates/s",
+                ms_per_step=ms / steps, status=int(mesh.sync_status()))
+
+
 # ------------------------------------------------------------------- ours
 
 def run_ours(args):
@@ -632,6 +658,7 @@ def run_ours(args):
     )
     if args.model == "AT2":
         line["subcycled"] = subcycled(pff, dev, args.config)
+    line["mechanics_only"] = mechanics_only(pff, dev, args.config)
     if not args.no_adjoint:
         line["fwd_adjoint"] = fwd_adjoint(pff, dev)
     if not args.no_batch:
