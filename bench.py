@@ -222,6 +222,26 @@ def algorithmic_bytes(N, Ne, prec):
     }
 
 
+def merged_row_width(tri, N):
+    """Width of the damage operator's merged rows on a compact FP32 mesh: 6
+    when no node has more than six distinct neighbours, 8 up to eight, else
+    None (the per-entry records are used)."""
+    t = np.asarray(tri, dtype=np.int64)
+    e = np.concatenate([t[:, [0, 1]], t[:, [1, 2]], t[:, [0, 2]]])
+    e.sort(axis=1)
+    key = np.unique(e[:, 0] * N + e[:, 1])
+    deg = np.bincount(np.concatenate([key // N, key % N]), minlength=N).max()
+    return 6 if deg <= 6 else 8 if deg <= 8 else None
+
+
+def format_bytes_cg_iteration(N, Dn):
+    """Bytes one FP32 CG iteration moves in the merged-row format: matvec
+    (flags, diagonal, Dn/2 offset words, Dn coefficients, the row's own
+    (p, z) pair, q written) and the vector update (flags; x, r, (p, z) read
+    and written; q and 1/diag read).  Neighbour values are L2 hits."""
+    return N * ((1 + 4 + 2 * Dn + 4 * Dn + 8 + 4) + (1 + 8 + 8 + 16 + 4 + 4))
+
+
 # -------------------------------------------------------------- reference
 
 def run_reference(args):
@@ -634,6 +654,14 @@ def run_ours(args):
                     achieved=achieved, peak=peak, unit="GB/s", frac=achieved / peak, peak_kind=peak_kind,
                     traffic=traffic, bytes_per_launch=bytes_launch[dom], ms_per_launch=ms_launch[dom],
                     cg_iterations_per_launch=prof["cg_loop_iters"] if dom == "cg_loop" else None)
+    Dn = merged_row_width(c["mesh"]["tri"], N) if args.prec == "fp32" else None
+    if dom == "cg_loop" and Dn and prof["cg_loop_family"] in ("persistent", "phases"):
+        # the same launch against the bytes its stored operator format moves
+        # (merged rows: fewer than the matrix-free element pass above)
+        fb = format_bytes_cg_iteration(N, Dn) * prof["cg_loop_iters"]
+        roofline["format"] = dict(name=f"merged rows, width {Dn}", bytes_per_launch=fb,
+                                  achieved=fb / (ms_launch[dom] * 1e-3) / 1e9,
+                                  frac=fb / (ms_launch[dom] * 1e-3) / 1e9 / peak)
     step_bytes = sum(ab[k] for k in ("predict", "force", "rhs", "finish")) + iters.mean() * ab["cg_iteration"]
     line = dict(
         metric=METRIC, value=value, unit="node-updates/s", n_gpus=ws, steps=args.steps,

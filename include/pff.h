@@ -86,8 +86,13 @@ typedef struct {
                            graph) or PFF_LOOP_HOST (host polls) [graph] */
   int32_t variant;      /* gather schedule of the force / damage kernels:
                            0 = autotuned on first use [0]; 1 = entry-parallel
-                           node blocks; 2..5 = node-centric with 1..4 gathers
-                           in flight.  All give bit-identical results. */
+                           node blocks (force: an element pass, then a node
+                           gather); 2..5 = node-centric with 1..4 gathers
+                           in flight.  Every row sums in the same order:
+                           bit-identical results in FP32; in FP64 the
+                           mechanics are bit-identical and the damage
+                           solve's FP64 dot products may differ in the
+                           last bit with the summation order. */
   int32_t cg_kernel;    /* AT2 CG loop: PFF_CG_PHASES = a matvec and an
                            update kernel per iteration; PFF_CG_PERSISTENT =
                            the whole solve in one cooperative kernel (all

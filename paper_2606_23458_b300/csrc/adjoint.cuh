@@ -166,7 +166,7 @@ __device__ __forceinline__ void split_tangent(const Params<R> &P, R exx, R eyy, 
 // entry record.
 template <typename R>
 __device__ __forceinline__ void adj_rhs_entry(const AdjParams<R> &A, const Slot<R> &S, int en, int k, int i,
-                                              R &dgc, R &axc) {
+                                              R &dgc, R &axc, float2 *cf) {
   typedef typename Params<R>::R4 R4;
   const Params<R> &P = A.P;
   const int e = en >> 2, a = en & 3;
@@ -180,7 +180,10 @@ __device__ __forceinline__ void adj_rhs_entry(const AdjParams<R> &A, const Slot<
   R gx, gy;
   slot_grad<R>(G, a, gx, gy);
   dgc = kA * (gx * gx + gy * gy) + R(2) * mA;
-  if (has_erec(P)) put_erec(P, k, i, G, a, kA, mA);
+  if (cf)
+    *cf = erec_coef<R>(G, a, kA, mA);
+  else if (has_erec(P))
+    put_erec(P, k, i, G, a, kA, mA);
   const R l0 = (P.flags[t.x] & kNotch) ? R(0) : P.x[t.x];
   const R l1 = (P.flags[t.y] & kNotch) ? R(0) : P.x[t.y];
   const R l2 = (P.flags[t.z] & kNotch) ? R(0) : P.x[t.z];
@@ -220,24 +223,32 @@ __global__ void __launch_bounds__(256) k_adj_rhs(AdjParams<R> A) {
       continue;
     }
     R dg = 0, ax = 0;
+    const bool merge = nb_merging(P);
+    NbAcc nacc;
+    nacc.zero();
     // two incidence entries in flight, summed in slot order
     for (int k = 0; k < P.D; k += 2) {
       int en[2];
 #pragma unroll
       for (int u = 0; u < 2; ++u) en[u] = k + u < P.D ? __ldg(&P.ell[(size_t)(k + u) * P.N + i]) : -1;
       R cd[2], ca[2];
+      float2 cf[2];
 #pragma unroll
       for (int u = 0; u < 2; ++u)
-        if (en[u] >= 0) adj_rhs_entry(A, S, en[u], k + u, i, cd[u], ca[u]);
+        if (en[u] >= 0) adj_rhs_entry(A, S, en[u], k + u, i, cd[u], ca[u], merge ? &cf[u] : nullptr);
 #pragma unroll
       for (int u = 0; u < 2; ++u)
         if (en[u] >= 0) {
           dg = radd(dg, cd[u]);
           ax = radd(ax, ca[u]);
+          if constexpr (sizeof(R) == 4)
+            if (merge) nacc.add(P, k + u, i, cf[u]);
         }
     }
     const R ri = gi - ax, di = R(1) / dg, zi = ri * di;
     if (P.diag) P.diag[i] = dg;
+    if constexpr (sizeof(R) == 4)
+      if (merge) nacc.store(P, i);
     P.r[i] = ri;
     P.dinv[i] = di;
     typename Params<R>::R2 w;

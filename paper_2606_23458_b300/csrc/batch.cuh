@@ -198,14 +198,18 @@ __global__ void __launch_bounds__(256) kb_rhs(Params<R> P, Batch B) {
       drec_notch_node(Q, i);
     } else {
       R bi = 0, dg = 0, ax = 0, a1 = 0;
+      const bool merge = nb_merging(Q);
+      NbAcc nacc;
+      nacc.zero();
       for (int k = 0; k < P.D; k += U) {
         R4 o[U];
+        float2 cf[U];
         int en[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) en[u] = k + u < P.D ? __ldg(&P.ell[(size_t)(k + u) * P.N + i]) : -1;
 #pragma unroll
         for (int u = 0; u < U; ++u)
-          if (en[u] >= 0) o[u] = rhs_entry(Q, en[u], k + u, i);
+          if (en[u] >= 0) o[u] = rhs_entry(Q, en[u], k + u, i, -1, merge ? &cf[u] : nullptr);
 #pragma unroll
         for (int u = 0; u < U; ++u)
           if (en[u] >= 0) {
@@ -213,9 +217,13 @@ __global__ void __launch_bounds__(256) kb_rhs(Params<R> P, Batch B) {
             dg = radd(dg, o[u].y);
             ax = radd(ax, o[u].z);
             a1 = radd(a1, o[u].w);
+            if constexpr (sizeof(R) == 4)
+              if (merge) nacc.add(Q, k + u, i, cf[u]);
           }
       }
       rhs_node(Q, i, bi, dg, ax, a1, vals);
+      if constexpr (sizeof(R) == 4)
+        if (merge) nacc.store(Q, i);
     }
   }
   __shared__ double tot[3];

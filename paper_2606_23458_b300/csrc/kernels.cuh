@@ -117,6 +117,7 @@ template <typename R> struct Params {
   const uint8_t *__restrict__ flags;
   const R2 *__restrict__ fext;
   const R *__restrict__ minv;
+  R2 *fe;  // 3 Ne: slot forces of the element-pass force schedule
   // operator staged in shared memory by the persistent CG (FP32), per CTA
   // (see StageCta): element ranges (first element, count), node ranges
   // (first node, count), element records with node ids replaced by node
@@ -150,6 +151,19 @@ template <typename R> struct Params {
                   // b - i (low half) and c - i (high half), ecf the two
                   // coefficients; an empty slot is offsets 0, coefficients 0.
                   // Nullable; at most one of erec and ecmp is set.
+  // FP32, compact meshes whose rows have at most kNbMax distinct neighbours:
+  // the same rows with each neighbour's coefficients merged (rows sum the
+  // per-element coefficients of a neighbour shared by two elements once):
+  // nbo packs the row's ascending neighbour offsets j - i two per word
+  // (Dn / 2 words, incidence-style layout w N + i), nbc holds the merged
+  // coefficient of each (Dn x N); padding slots are offset 0, coefficient
+  // 0.  nmap (D x N bytes) gives, per incidence slot, the merged slots of
+  // the entry's two neighbours (low and high nibble; 0xff = empty).  The
+  // right-hand side fills nbc from ecf.  Nullable.
+  const uint32_t *__restrict__ nbo;
+  float *nbc;
+  const uint8_t *__restrict__ nmap;
+  int32_t Dn;
   R *diag;       // with erec: the row's diagonal sum over entries of
                  // (kappa_e A_e |grad phi_a|^2 + 2 mA)
   const R *gcs; // per-element toughness field as Gc_e / Gc (nullable: uniform);
@@ -345,6 +359,10 @@ template <typename R> __device__ __forceinline__ R rneg(R x) { return x < R(0) ?
 // the producer of b: every schedule then rounds the same sums the same way.
 __device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ double radd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float rfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double rfma(double a, double b, double c) { return __fma_rn(a, b, c); }
 
 // Load scale at the end (which = 1) or start (which = 0) of the step.
 template <typename R>
@@ -508,6 +526,15 @@ __global__ void __launch_bounds__(256) k_predict(Params<R> P) {
   }
 }
 
+// f_a = A (sigma . grad(phi_a)) with every rounding spelled out, so that a
+// slot known at compile time (element pass) and one selected at run time
+// (per-entry schedules) give the same bits.
+template <typename R>
+__device__ __forceinline__ void slot_force(R A, R sxx, R syy, R sxy, R gx, R gy, R &fx, R &fy) {
+  fx = rmul(A, rfma(sxx, gx, rmul(sxy, gy)));
+  fy = rmul(A, rfma(sxy, gx, rmul(syy, gy)));
+}
+
 // Force contribution of one incidence entry (element e at local slot a):
 // f_a = A_e sigma_e . grad(phi_a) with sigma = g(dbar) sigma+ + sigma-
 // (Sec. 2.3 gather and element contraction); also returns psi+_e.
@@ -527,8 +554,7 @@ __device__ __forceinline__ void force_entry(const Params<R> &P, int en, R &fx, R
   stress(P, exx, eyy, exy, g, sxx, syy, sxy, psip);
   R gx, gy;
   slot_grad<R>(G, a, gx, gy);
-  fx = A * (sxx * gx + sxy * gy);
-  fy = A * (sxy * gx + syy * gy);
+  slot_force(A, sxx, syy, sxy, gx, gy, fx, fy);
 }
 
 // History update H_e = max(H_e, psi+_e) by the element's owner entry
@@ -579,35 +605,61 @@ __device__ __forceinline__ void corrector(const Params<R> &P, int i, R fx, R fy,
 // Internal force at u_{n+1} with d_n, history, acceleration and corrector.
 // Entry-parallel schedule (node blocks, contributions staged in shared
 // memory, per-node sums in ascending element order).
+// Force schedule "element pass + gather": one thread per element computes
+// the strain, split and degraded stress once, updates the element's history
+// and writes the three slot forces (force_entry's arithmetic); then one
+// thread per node sums its slot forces in incidence order (the node-centric
+// schedules' order, so all schedules give the same bits) and applies the
+// corrector.
 template <typename R>
-__global__ void __launch_bounds__(256) k_force_ep(Params<R> P) {
+__global__ void __launch_bounds__(256) k_force_elem(Params<R> P) {
   typedef typename Params<R>::R2 R2;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  R2 *fc = reinterpret_cast<R2 *>(smem_raw);
-  const double S = load_scale(P, 1);
-  for (int b = blockIdx.x; b < P.nblk; b += gridDim.x) {
-    int i0, i1, k0, k1;
-    block_nodes(P, b, i0, i1, k0, k1);
-    for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
-      const int en = __ldg(&P.ent[k]);
+  typedef typename Params<R>::R4 R4;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < P.Ne; e += gridDim.x * blockDim.x) {
+    int4 t;
+    R A;
+    R4 G;
+    load_elem(P, e, t, A, G);
+    R exx, eyy, exy;
+    elem_strain(P, G, t, exx, eyy, exy);
+    const R db = (P.d[t.x] + P.d[t.y] + P.d[t.z]) * (R(1) / R(3));
+    const R g = (R(1) - db) * (R(1) - db) + P.eta;
+    R sxx, syy, sxy, psip;
+    stress(P, exx, eyy, exy, g, sxx, syy, sxy, psip);
+    history_update(P, e << 2, psip);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      R gx, gy;
+      slot_grad<R>(G, a, gx, gy);
       R2 f;
-      R psip;
-      force_entry(P, en, f.x, f.y, psip);
-      fc[k - k0] = f;
-      history_update(P, en, psip);
+      slot_force(A, sxx, syy, sxy, gx, gy, f.x, f.y);
+      P.fe[(size_t)3 * e + a] = f;
     }
-    __syncthreads();
-    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-      const int j0 = __ldg(&P.ptr[i]) - k0, j1 = __ldg(&P.ptr[i + 1]) - k0;
-      R fx = 0, fy = 0;
-      for (int j = j0; j < j1; ++j) {
-        const R2 f = fc[j];
-        fx = radd(fx, f.x);
-        fy = radd(fy, f.y);
-      }
-      corrector(P, i, fx, fy, S);
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_force_gather(Params<R> P) {
+  typedef typename Params<R>::R2 R2;
+  const double S = load_scale(P, 1);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.N; i += gridDim.x * blockDim.x) {
+    R fx = 0, fy = 0;
+    for (int k = 0; k < P.D; k += 4) {
+      int en[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) en[u] = k + u < P.D ? __ldg(&P.ell[(size_t)(k + u) * P.N + i]) : -1;
+      R2 f[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (en[u] >= 0) f[u] = P.fe[(size_t)3 * (en[u] >> 2) + (en[u] & 3)];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (en[u] >= 0) {
+          fx = radd(fx, f[u].x);
+          fy = radd(fy, f[u].y);
+        }
     }
-    __syncthreads();
+    corrector(P, i, fx, fy, S);
   }
 }
 
@@ -677,13 +729,18 @@ __device__ __forceinline__ bool has_erec(const Params<R> &P) {
 // (slot k, node i); the neighbour ids or offsets depend on the mesh alone
 // and are written once (k_erec_ids).
 template <typename R>
-__device__ __forceinline__ void put_erec(const Params<R> &P, int k, int i, const typename Params<R>::R4 &G, int a,
-                                         R kA, R mA) {
+__device__ __forceinline__ float2 erec_coef(const typename Params<R>::R4 &G, int a, R kA, R mA) {
   R gx, gy, gbx, gby, gcx, gcy;
   slot_grad<R>(G, a, gx, gy);
   slot_grad<R>(G, a == 0 ? 1 : 0, gbx, gby);
   slot_grad<R>(G, a == 2 ? 1 : 2, gcx, gcy);
-  const float2 c = make_float2((float)(kA * (gx * gbx + gy * gby) + mA), (float)(kA * (gx * gcx + gy * gcy) + mA));
+  return make_float2((float)(kA * (gx * gbx + gy * gby) + mA), (float)(kA * (gx * gcx + gy * gcy) + mA));
+}
+
+template <typename R>
+__device__ __forceinline__ void put_erec(const Params<R> &P, int k, int i, const typename Params<R>::R4 &G, int a,
+                                         R kA, R mA) {
+  const float2 c = erec_coef<R>(G, a, kA, mA);
   const size_t q = (size_t)k * P.N + i;
   if (P.ecmp)
     P.ecf[q] = c;
@@ -715,6 +772,129 @@ __global__ void __launch_bounds__(256) k_erec_ids(const ERec<R> *rec, const int 
         erec[q] = make_float4(__int_as_float(nb), __int_as_float(nc), 0.f, 0.f);
     }
   }
+}
+
+constexpr int kNbMax = 8;  // merged rows: most distinct neighbours of a row
+
+// The mesh-only half of the merged rows, once per mesh (compact records):
+// per node the distinct neighbour offsets of its incidence entries in
+// ascending order.  count_only: the largest count goes to *maxcnt (atomic
+// max); else the offsets (Dn slots, padded with 0) and each incidence
+// slot's merged slots are written.
+__global__ void __launch_bounds__(256) k_nb_build(const uint32_t *__restrict__ ecmp, int N, int D, int Dn,
+                                                  int *maxcnt, uint32_t *nbo, uint8_t *nmap) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    int o[2 * kNbMax];
+    int n = 0;
+    for (int k = 0; k < D && k < kNbMax; ++k) {
+      const uint32_t w = ecmp[(size_t)k * N + i];
+      if (w == 0u) continue;  // empty slot (a real neighbour is never at offset 0)
+      const int c2[2] = {(int)(int16_t)(w & 0xffffu), (int)w >> 16};
+      for (int h = 0; h < 2; ++h) {
+        int j = 0;
+        while (j < n && o[j] < c2[h]) ++j;
+        if (j < n && o[j] == c2[h]) continue;
+        for (int m = n; m > j; --m) o[m] = o[m - 1];
+        o[j] = c2[h];
+        ++n;
+      }
+    }
+    if (maxcnt) {
+      atomicMax(maxcnt, D > kNbMax ? 2 * kNbMax : n);
+      continue;
+    }
+    for (int w = 0; w < Dn / 2; ++w) {
+      const int lo = 2 * w < n ? o[2 * w] : 0, hi = 2 * w + 1 < n ? o[2 * w + 1] : 0;
+      nbo[(size_t)w * N + i] = (uint32_t)(uint16_t)(int16_t)lo | ((uint32_t)(uint16_t)(int16_t)hi << 16);
+    }
+    for (int k = 0; k < D; ++k) {
+      const uint32_t w = ecmp[(size_t)k * N + i];
+      uint8_t m = 0xffu;
+      if (w != 0u) {
+        const int ob = (int)(int16_t)(w & 0xffffu), oc = (int)w >> 16;
+        int jb = 0, jc = 0;
+        while (o[jb] != ob) ++jb;
+        while (o[jc] != oc) ++jc;
+        m = (uint8_t)(jb | (jc << 4));
+      }
+      nmap[(size_t)k * N + i] = m;
+    }
+  }
+}
+
+// A row's merged coefficients, accumulated entry by entry in incidence-slot
+// order (b before c within an entry), then stored: the same order whichever
+// schedule produced the entries.
+struct NbAcc {
+  float a[kNbMax];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int j = 0; j < kNbMax; ++j) a[j] = 0.f;
+  }
+  __device__ __forceinline__ void add(const Params<float> &P, int k, int i, float2 c) {
+    const unsigned m = __ldg(&P.nmap[(size_t)k * P.N + i]);
+    if (m == 0xffu) return;
+    const unsigned jb = m & 15u, jc = m >> 4;
+#pragma unroll
+    for (int j = 0; j < kNbMax; ++j) {
+      if (jb == (unsigned)j) a[j] = __fadd_rn(a[j], c.x);
+      if (jc == (unsigned)j) a[j] = __fadd_rn(a[j], c.y);
+    }
+  }
+  __device__ __forceinline__ void store(const Params<float> &P, int i) const {
+#pragma unroll
+    for (int j = 0; j < kNbMax; ++j)
+      if (j < P.Dn) P.nbc[(size_t)j * P.N + i] = a[j];
+  }
+};
+
+// Whether a right-hand-side pass merges rows (FP32 with merged rows; the
+// staged families' passes run without records).
+template <typename R>
+__device__ __forceinline__ bool nb_merging(const Params<R> &P) {
+  if constexpr (sizeof(R) == 4) return P.nbc != nullptr && P.ecf != nullptr;
+  return false;
+}
+
+// Row i's merged coefficients from its entry coefficients in ecf (written
+// by its block before a block barrier: the entry-parallel schedule).
+template <typename R>
+__device__ __forceinline__ void nb_merge_row(const Params<R> &P, int i) {
+  if constexpr (sizeof(R) == 4) {
+    if (!nb_merging(P)) return;
+    NbAcc acc;
+    acc.zero();
+    for (int k = 0; k < P.D; ++k) acc.add(P, k, i, P.ecf[(size_t)k * P.N + i]);
+    acc.store(P, i);
+  }
+}
+
+// Row i of the merged operator applied to the values val(j) of its
+// neighbours, added to q (diag_i times the row's own value): all DN
+// records, then all DN neighbour gathers in flight, then an explicit fma
+// chain in slot order (padding slots add an exact 0).
+template <int DN, typename F>
+__device__ __forceinline__ float nb_row(const Params<float> &P, int i, float q, F val) {
+  uint32_t w[DN / 2];
+  float c[DN], v[DN];
+#pragma unroll
+  for (int j = 0; j < DN / 2; ++j) w[j] = __ldg(&P.nbo[(size_t)j * P.N + i]);
+#pragma unroll
+  for (int j = 0; j < DN; ++j) c[j] = __ldg(&P.nbc[(size_t)j * P.N + i]);
+#pragma unroll
+  for (int j = 0; j < DN; ++j) {
+    const uint32_t x = w[j >> 1];
+    const int o = (j & 1) ? (int)x >> 16 : (int)(int16_t)(x & 0xffffu);
+    v[j] = val(i + o);
+  }
+#pragma unroll
+  for (int j = 0; j < DN; ++j) q = fmaf(c[j], v[j], q);
+  return q;
+}
+
+template <typename F>
+__device__ __forceinline__ float nb_row_any(const Params<float> &P, int i, float q, F val) {
+  return P.Dn <= 6 ? nb_row<6>(P, i, q, val) : nb_row<8>(P, i, q, val);
 }
 
 // The damage record of an element from its geometry and coefficients.
@@ -785,9 +965,11 @@ __global__ void __launch_bounds__(256) k_drec_build(Params<R> P) {
 // damage problem (AT2: Eq. damage_pde_at2; AT1: Eq. damage_pde_at1), one
 // incidence entry's share: (b, diag, (A x0)_a, (A 1_D)_a) with
 // x0 = d_prev (1 on the notch).
+// With cf, a merging pass's entry coefficients are returned there instead
+// of written to the entry records.
 template <typename R>
 __device__ __forceinline__ typename Params<R>::R4 rhs_entry(const Params<R> &P, int en, int slot = -1,
-                                                            int node = -1, int csr = -1) {
+                                                            int node = -1, int csr = -1, float2 *cf = nullptr) {
   typedef typename Params<R>::R4 R4;
   const int e = en >> 2, a = en & 3;
   int4 t;
@@ -805,7 +987,9 @@ __device__ __forceinline__ typename Params<R>::R4 rhs_entry(const Params<R> &P, 
   R gx, gy;
   slot_grad<R>(G, a, gx, gy);
   if (a == 0 && P.drec) P.drec[e] = make_drec<R>(t, G, kA, mA);
-  if (has_erec(P)) {
+  if (cf) {
+    *cf = erec_coef<R>(G, a, kA, mA);
+  } else if (has_erec(P)) {
     // the entry's incidence slot: given, or from its CSR position
     if (slot < 0 && csr >= 0) {
       node = a == 0 ? t.x : (a == 1 ? t.y : t.z);
@@ -908,6 +1092,7 @@ __global__ void __launch_bounds__(256) k_dmg_rhs_ep(Params<R> P) {
         a1 = radd(a1, o.w);
       }
       rhs_node(P, i, bi, dg, ax, a1, vals);
+      nb_merge_row(P, i);
     }
     __syncthreads();
   }
@@ -938,14 +1123,18 @@ __global__ void __launch_bounds__(256) k_dmg_rhs_nc(Params<R> P) {
       continue;
     }
     R bi = 0, dg = 0, ax = 0, a1 = 0;
+    const bool merge = nb_merging(P);
+    NbAcc nacc;
+    nacc.zero();
     for (int k = 0; k < P.D; k += U) {
       R4 o[U];
+      float2 cf[U];
       int en[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) en[u] = k + u < P.D ? __ldg(&P.ell[(size_t)(k + u) * P.N + i]) : -1;
 #pragma unroll
       for (int u = 0; u < U; ++u)
-        if (en[u] >= 0) o[u] = rhs_entry(P, en[u], k + u, i);
+        if (en[u] >= 0) o[u] = rhs_entry(P, en[u], k + u, i, -1, merge ? &cf[u] : nullptr);
 #pragma unroll
       for (int u = 0; u < U; ++u)
         if (en[u] >= 0) {
@@ -953,9 +1142,13 @@ __global__ void __launch_bounds__(256) k_dmg_rhs_nc(Params<R> P) {
           dg = radd(dg, o[u].y);
           ax = radd(ax, o[u].z);
           a1 = radd(a1, o[u].w);
+          if constexpr (sizeof(R) == 4)
+            if (merge) nacc.add(P, k + u, i, cf[u]);
         }
     }
     rhs_node(P, i, bi, dg, ax, a1, vals);
+    if constexpr (sizeof(R) == 4)
+      if (merge) nacc.store(P, i);
   }
   __shared__ double tot[3];
   if (reduce_last<R, 3>(vals, P.part, P.ticket, tot) && threadIdx.x == 0) rhs_finish(P, tot);
@@ -977,6 +1170,7 @@ __device__ __forceinline__ R pnew(const Params<R> &P, int j, R beta) {
 template <int U>
 __device__ __forceinline__ float erec_row(const Params<float> &P, int i, float beta, float pc) {
   float q = P.diag[i] * pc;
+  if (P.nbc) return nb_row_any(P, i, q, [&](int j) { return pnew(P, j, beta); });
   if (P.ecmp) {
     if (U >= 3 && P.D <= 6) {
       // the whole row at once: six slots' records, then their twelve
@@ -1746,7 +1940,9 @@ __device__ __forceinline__ void fused_rows(const Params<float> &P, float al, flo
     // slot c_b u_b + c_c u_c with the neighbours' u rebuilt from their
     // records
     float wq = P.diag[j] * un;
-    if (P.ecmp) {
+    if (P.nbc) {
+      wq = nb_row_any(P, j, wq, [&](int n) { return cg_unew(vin[n], al, be); });
+    } else if (P.ecmp) {
       for (int k = 0; k < P.D; k += U) {
         uint32_t w[U];
         float2 cf[U];

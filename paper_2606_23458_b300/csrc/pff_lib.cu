@@ -269,7 +269,13 @@ struct pff_mesh {
   uint32_t *ecmp = nullptr;  // FP32, compact entry records: packed 16-bit neighbour offsets (D x N)
   float2 *ecf = nullptr;     // FP32, compact entry records: coefficients (D x N)
   int64_t span = 0;          // largest node-id difference within an element
+  uint32_t *nbo = nullptr;   // FP32 merged rows: neighbour offsets (Dn / 2 x N)
+  float *nbc = nullptr;      // FP32 merged rows: coefficients (Dn x N)
+  uint8_t *nmap = nullptr;   // FP32 merged rows: incidence slot -> merged slots (D x N)
+  int32_t Dn = 0;            // merged row width (6 or 8; 0 = not used)
   float *diagf = nullptr;  // FP32: the damage rows' diagonals (N)
+  void *fe = nullptr;      // slot forces of the element-pass force schedule (3 Ne x R2)
+  unsigned fg_grid = 0;    // grid of that schedule's node gather
   double *area_d = nullptr;
   uint8_t *flags = nullptr;
   double hmin = 0.0;
@@ -338,7 +344,7 @@ static void mesh_free(pff_mesh *m) {
   free_graph(m->step_g);
   free_graph(m->mech_g);
   void *ptrs[] = {m->gcs, m->st_cta, m->st_rng, m->st_nrng, m->st_lrec, m->st_slot, m->cgv, m->cgp,
-                  m->ptr, m->ent, m->ell, m->rec, m->drec, m->erec, m->ecmp, m->ecf, m->diagf, m->fext, m->minv,
+                  m->ptr, m->ent, m->ell, m->rec, m->drec, m->erec, m->ecmp, m->ecf, m->nbo, m->nbc, m->nmap, m->diagf, m->fe, m->fext, m->minv,
                   m->area_d,
                   m->flags,
                   m->x, m->r, m->b, m->part, m->energy, m->wext, m->pz, m->q, m->dinv,
@@ -364,8 +370,9 @@ enum KernelId { KP_PREDICT = 0, KP_FORCE, KP_RHS, KP_MATVEC, KP_UPDATE, KP_FINIS
                 KP_COUNT };
 constexpr int kThreads = 256;
 // Schedule variants of the gather kernels (force, rhs, matvec):
-// 0 = entry-parallel node blocks, 1..4 = node-centric with U = 1..4
-// gathers in flight.  All variants give bit-identical results.
+// 0 = entry-parallel node blocks (force: an element pass, then a node
+// gather), 1..4 = node-centric with U = 1..4 gathers in flight.  All
+// variants sum each row in the same order (bit-identical in FP32).
 constexpr int kNumVariants = 5;
 static inline bool tunable(int id) { return id == KP_FORCE || id == KP_RHS || id == KP_MATVEC; }
 
@@ -379,7 +386,7 @@ static const void *kfun(int id, int v) {
         case 2: return (const void *)k_force_nc<R, 2>;
         case 3: return (const void *)k_force_nc<R, 3>;
         case 4: return (const void *)k_force_nc<R, 4>;
-        default: return (const void *)k_force_ep<R>;
+        default: return (const void *)k_force_elem<R>;  // + k_force_gather
       }
     case KP_RHS:
       switch (v) {
@@ -808,11 +815,34 @@ static pff_status configure(pff_mesh *m) {
     k_erec_ids<R><<<std::min<unsigned>(grid_for(m->N, 256), stride_cap()), 256>>>(
         (const ERec<R> *)m->rec, m->ell, (int)m->N, D, m->ecmp, m->erec);
     CUDA_TRY(cudaGetLastError());
+    if (m->ecmp && D <= kNbMax) {
+      // merged rows where every row has at most kNbMax distinct neighbours
+      const unsigned gb = std::min<unsigned>(grid_for(m->N, 256), stride_cap());
+      int *cnt = nullptr;
+      PFF_TRY(dalloc(&cnt, 1));
+      CUDA_TRY(cudaMemset(cnt, 0, sizeof(int)));
+      k_nb_build<<<gb, 256>>>(m->ecmp, (int)m->N, D, 0, cnt, nullptr, nullptr);
+      int mx = 0;
+      cudaError_t e = cudaGetLastError();
+      if (e == cudaSuccess) e = cudaMemcpy(&mx, cnt, sizeof(int), cudaMemcpyDeviceToHost);
+      cudaFree(cnt);
+      CUDA_TRY(e);
+      if (mx <= kNbMax) {
+        m->Dn = mx <= 6 ? 6 : kNbMax;
+        PFF_TRY(dalloc(&m->nbo, (size_t)(m->Dn / 2) * m->N));
+        PFF_TRY(dalloc(&m->nbc, (size_t)m->Dn * m->N));
+        PFF_TRY(dalloc(&m->nmap, (size_t)D * m->N));
+        CUDA_TRY(cudaMemset(m->nbc, 0, (size_t)m->Dn * m->N * sizeof(float)));
+        k_nb_build<<<gb, 256>>>(m->ecmp, (int)m->N, D, m->Dn, nullptr, m->nbo, m->nmap);
+        CUDA_TRY(cudaGetLastError());
+      }
+    }
     PFF_TRY(dalloc(&m->diagf, (size_t)m->N));
     CUDA_TRY(cudaMemset(m->diagf, 0, (size_t)m->N * sizeof(float)));
   }
   m->nblk = (int32_t)((m->N + NB - 1) / NB);
-  const size_t sm_ep[KP_COUNT] = {0, maxE * sizeof(typename V<R>::T2), maxE * sizeof(typename V<R>::T4),
+  if (!m->fe) PFF_TRY(dalloc((typename V<R>::T2 **)&m->fe, 3 * (size_t)m->Ne));
+  const size_t sm_ep[KP_COUNT] = {0, 0, maxE * sizeof(typename V<R>::T4),
                                   maxE * sizeof(R), 0, 0, maxE * sizeof(R), 0};
   int dev = 0, nsm = 0;
   CUDA_TRY(cudaGetDevice(&dev));
@@ -826,11 +856,17 @@ static pff_status configure(pff_mesh *m) {
       int occ = 0;
       CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f, kThreads, sm));
       if (occ < 1) occ = 1;
-      const int64_t work = sm > 0 ? m->nblk
-                                  : (int64_t)grid_for(id == KP_ENERGIES ? std::max(m->N, m->Ne) : m->N, kThreads);
+      const bool per_elem = id == KP_ENERGIES || (id == KP_FORCE && v == 0);
+      const int64_t work = sm > 0 ? m->nblk : (int64_t)grid_for(per_elem ? std::max(m->N, m->Ne) : m->N, kThreads);
       m->grid[id][v] = (unsigned)std::max<int64_t>(1, std::min<int64_t>(work, (int64_t)nsm * occ));
       m->smem[id][v] = sm;
     }
+  }
+  {
+    int occ = 0;
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_force_gather<R>, kThreads, 0));
+    m->fg_grid = (unsigned)std::max<int64_t>(
+        1, std::min<int64_t>(grid_for(m->N, kThreads), (int64_t)nsm * std::max(occ, 1)));
   }
   // persistent CG: every CTA must be resident at once (cooperative launch)
   int coop = 0;
@@ -873,6 +909,8 @@ template <typename R>
 static pff_status launch_v(const pff_mesh *m, int id, int v, Params<R> &P, cudaStream_t s) {
   void *args[] = {(void *)&P};
   CUDA_TRY(cudaLaunchKernel(kfun<R>(id, v), dim3(m->grid[id][v]), dim3(kThreads), args, m->smem[id][v], s));
+  if (id == KP_FORCE && v == 0)
+    CUDA_TRY(cudaLaunchKernel((const void *)k_force_gather<R>, dim3(m->fg_grid), dim3(kThreads), args, 0, s));
   return PFF_OK;
 }
 
@@ -909,6 +947,10 @@ static Params<R> base_params(pff_mesh *m, const pff_options &o) {
   P.erec = m->erec;
   P.ecmp = m->ecmp;
   P.ecf = m->ecf;
+  P.nbo = m->nbo;
+  P.nbc = m->nbc;
+  P.nmap = m->nmap;
+  P.Dn = m->Dn;
   P.diag = (R *)m->diagf;
   P.flags = m->flags;
   P.st_cta = m->st_cta;
@@ -922,6 +964,7 @@ static Params<R> base_params(pff_mesh *m, const pff_options &o) {
   P.cgp = m->cgp;
   P.fext = (const typename V<R>::T2 *)m->fext;
   P.minv = (const R *)m->minv;
+  P.fe = (typename V<R>::T2 *)m->fe;
   const pff_material &mt = m->mat;
   P.lam = (R)m->lam;
   P.cz = (R)m->cz;
@@ -992,6 +1035,13 @@ static pff_status add_kernel(const pff_mesh *m, cudaGraph_t g, const std::vector
   kp.sharedMemBytes = (unsigned)m->smem[id][v];
   kp.kernelParams = args;
   CUDA_TRY(cudaGraphAddKernelNode(out, g, deps.data(), deps.size(), &kp));
+  if (id == KP_FORCE && v == 0) {  // the element pass, then its node gather (returned)
+    const cudaGraphNode_t n_el = *out;
+    kp.func = (void *)k_force_gather<R>;
+    kp.gridDim = dim3(m->fg_grid);
+    kp.sharedMemBytes = 0;
+    CUDA_TRY(cudaGraphAddKernelNode(out, g, &n_el, 1, &kp));
+  }
   return PFF_OK;
 }
 
@@ -1035,6 +1085,7 @@ static pff_status append_solve(const pff_mesh *m, cudaGraph_t g, cudaGraphNode_t
     Pr.erec = nullptr;
     Pr.ecmp = nullptr;
     Pr.ecf = nullptr;
+    Pr.nbc = nullptr;
     Pr.diag = nullptr;
   }
   PFF_TRY(add_kernel<R>(m, g, d, KP_RHS, Pr, &n_rhs));
