@@ -1367,13 +1367,68 @@ __global__ void __launch_bounds__(256) k_cg_matvec_ep(Params<R> P) {
   if (reduce_last<R, 1>(vals, P.part, P.ticket, tot) && threadIdx.x == 0) matvec_finish(P, tot);
 }
 
+// One width-6 merged row's records: neighbour offsets (three words), merged
+// coefficients, diagonal and flags.
+struct NbRow6 {
+  uint32_t w[3];
+  float c[6];
+  float dg;
+  unsigned fl;
+};
+
+__device__ __forceinline__ void nb_load6(const Params<float> &P, int i, NbRow6 &r) {
+#pragma unroll
+  for (int j = 0; j < 3; ++j) r.w[j] = __ldg(&P.nbo[(size_t)j * P.N + i]);
+#pragma unroll
+  for (int j = 0; j < 6; ++j) r.c[j] = __ldg(&P.nbc[(size_t)j * P.N + i]);
+  r.dg = __ldg(&P.diag[i]);
+  r.fl = __ldg(&P.flags[i]);
+}
+
+// Width-6 merged rows i0, i0 + stride, ... of q = A p_new, software-
+// pipelined: the next row's records load while this row's neighbour values
+// are gathered; cur holds row i0's records.  Same arithmetic as erec_row.
+__device__ __forceinline__ void nb_rows6(const Params<float> &P, float beta, int i0, int stride, DF &acc,
+                                         NbRow6 cur) {
+  typedef Acc<float> AC;
+  for (int i = i0; i < P.N; i += stride) {
+    NbRow6 nxt;
+    const int in = i + stride;
+    if (in < P.N) nb_load6(P, in, nxt);
+    float q = 0.f;
+    if (!((cur.fl & kNotch) || (P.freef && !P.freef[i]))) {
+      const float pc = pnew(P, i, beta);
+      q = cur.dg * pc;
+      float v[6];
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        const uint32_t x = cur.w[j >> 1];
+        const int o = (j & 1) ? (int)x >> 16 : (int)(int16_t)(x & 0xffffu);
+        v[j] = pnew(P, i + o, beta);
+      }
+#pragma unroll
+      for (int j = 0; j < 6; ++j) q = fmaf(cur.c[j], v[j], q);
+      acc = AC::add(acc, AC::prod(pc, P.rscale * q));
+    }
+    P.q[i] = q;
+    cur = nxt;
+  }
+}
+
 // Node-centric rows i0, i0 + stride, ... of q = A p_new (U gathers in
-// flight) with their share of p_new . q added to acc.
+// flight; merged rows of width 6: U >= 2 pipelines rows) with their share of
+// p_new . q added to acc.
 template <typename R, int U>
 __device__ __forceinline__ void matvec_rows(const Params<R> &P, R beta, int i0, int stride,
                                             typename Acc<R>::T &acc) {
   typedef Acc<R> AC;
   if constexpr (sizeof(R) == 4) {
+    if (U >= 2 && P.nbc && P.Dn <= 6) {
+      NbRow6 first;
+      if (i0 < P.N) nb_load6(P, i0, first);
+      nb_rows6(P, beta, i0, stride, acc, first);
+      return;
+    }
     if (has_erec(P)) {
       // FP32 entry records: the row's diagonal times its own value, then per
       // entry the two other nodes' values times their coefficients (the
@@ -1547,7 +1602,7 @@ __global__ void __launch_bounds__(256) k_cg_update(Params<R> P) {
 // ------------------------------------------------- persistent CG (AT2)
 //
 // The whole Jacobi-PCG loop of one AT2 solve in one cooperative launch
-// (kPersMinBlocks CTAs of kPersThreads per SM): per iteration the matvec
+// (kPersMinBlocks CTAs of pers_threads(U, ST) per SM): per iteration the matvec
 // rows, a grid all-reduce of p.q, the update rows, a grid all-reduce of
 // (|r|^2, r.z).  Each all-reduce is a grid barrier: every CTA publishes its
 // partial, counts itself in on S.bar with a release reduction (monotonic
@@ -1560,8 +1615,12 @@ __global__ void __launch_bounds__(256) k_cg_update(Params<R> P) {
 // kSpinTimeoutNs a CTA raises S.abort, every CTA leaves, and the solve
 // reports kStTimeout.
 
-constexpr int kPersThreads = 768;
-constexpr int kPersMinBlocks = 2;  // 48 warps per SM; at most 42 registers
+// CTA shape: two CTAs per SM; 768 threads (at most 42 registers) for one
+// gather group in flight and for the staged kernels, 512 (at most 64) for
+// the global-operator kernels with U >= 2, whose merged-row matvec keeps the
+// next row's records in registers.
+constexpr int kPersMinBlocks = 2;
+__host__ __device__ constexpr int pers_threads(int U, bool st) { return (!st && U >= 2) ? 512 : 768; }
 constexpr unsigned long long kSpinTimeoutNs = 2000000000ull;  // 2 s
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -1745,10 +1804,10 @@ template <typename R> struct PersShared {
 // reads them there: the operator data cross the memory system once per
 // solve instead of once per iteration.
 template <typename R, int U, bool ST>
-__global__ void __launch_bounds__(kPersThreads, kPersMinBlocks) k_cg_persistent(Params<R> P) {
+__global__ void __launch_bounds__(pers_threads(U, ST), kPersMinBlocks) k_cg_persistent(Params<R> P) {
   typedef Acc<R> AC;
   SolveScalars *S = P.sc;
-  __shared__ typename AC::T sh[kPersThreads / 32][2];
+  __shared__ typename AC::T sh[pers_threads(U, ST) / 32][2];
   __shared__ PersShared<R> z;
   __shared__ __align__(8) unsigned long long stage_bar;
   extern __shared__ __align__(128) unsigned char stage_smem[];

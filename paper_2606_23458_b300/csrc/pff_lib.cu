@@ -512,7 +512,7 @@ static const void *plan_fun(const CgPlan &c) {
 }
 
 static inline unsigned plan_threads(const CgPlan &c) {
-  return c.fam == kFamFusedStaged ? FusedCfg<true>::threads : (c.fam == kFamFused ? FusedCfg<false>::threads : kPersThreads);
+  return c.fam == kFamFusedStaged ? FusedCfg<true>::threads : (c.fam == kFamFused ? FusedCfg<false>::threads : pers_threads(c.U, c.st()));
 }
 
 static inline size_t plan_smem(const pff_mesh *m, const CgPlan &c) {
@@ -740,7 +740,7 @@ static pff_status build_stage(pff_mesh *m, const std::vector<int32_t> &ptr, int 
       return PFF_OK;
     };
     bool ok = true;
-    for (int U = 1; U <= 4 && ok; ++U) PFF_TRY(coresident(pers_fun<float>(U, true), kPersThreads, smax_el, ok));
+    for (int U = 1; U <= 4 && ok; ++U) PFF_TRY(coresident(pers_fun<float>(U, true), pers_threads(U, true), smax_el, ok));
     if (!ok) continue;
     for (int U = 1; U <= 4 && local_ok; ++U) {
       CgPlan pc;
@@ -873,11 +873,12 @@ static pff_status configure(pff_mesh *m) {
   CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
   for (int U = 1; U <= 4; ++U) {
     int occ = 0;
-    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pers_fun<R>(U), kPersThreads, 0));
+    const int T = pers_threads(U, false);
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pers_fun<R>(U), T, 0));
     // a full wave (every SM the same number of CTAs, so no SM carries more
     // rows than its share), or fewer CTAs on a mesh too small to fill it
     const int64_t wave = (int64_t)nsm * occ;
-    const int64_t ctas = std::max<int64_t>(1, (m->N + kPersThreads - 1) / kPersThreads);
+    const int64_t ctas = std::max<int64_t>(1, (m->N + T - 1) / T);
     m->pgrid[U] = coop && occ > 0 ? (unsigned)std::min<int64_t>(ctas, wave) : 0u;
   }
   if constexpr (sizeof(R) == 4) {
