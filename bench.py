@@ -234,12 +234,18 @@ def merged_row_width(tri, N):
     return 6 if deg <= 6 else 8 if deg <= 8 else None
 
 
-def format_bytes_cg_iteration(N, Dn):
-    """Bytes one FP32 CG iteration moves in the merged-row format: matvec
-    (flags, diagonal, Dn/2 offset words, Dn coefficients, the row's own
-    (p, z) pair, q written) and the vector update (flags; x, r, (p, z) read
-    and written; q and 1/diag read).  Neighbour values are L2 hits."""
-    return N * ((1 + 4 + 2 * Dn + 4 * Dn + 8 + 4) + (1 + 8 + 8 + 16 + 4 + 4))
+def format_bytes_cg_iteration(N, Dn, family):
+    """Bytes one FP32 CG iteration moves in the merged-row format (flags,
+    diagonal, Dn/2 offset words and Dn coefficients per row, plus the
+    vectors; neighbour values are L2 hits).  Two-pass families (persistent,
+    phases): matvec (the row's own (p, z) pair read, q written) and vector
+    update (x, r, (p, z) read and written; q and 1/diag read, flags again).
+    Single-reduction family: one pass reading the row's (r, w, s, 1/diag)
+    record, p and x, writing the new record, p and x."""
+    rec = 1 + 4 + 2 * Dn + 4 * Dn
+    if family == "fused":
+        return N * (rec + 16 + 8 + 8 + 16)
+    return N * ((rec + 8 + 4) + (1 + 8 + 8 + 16 + 4 + 4))
 
 
 # -------------------------------------------------------------- reference
@@ -655,10 +661,10 @@ def run_ours(args):
                     traffic=traffic, bytes_per_launch=bytes_launch[dom], ms_per_launch=ms_launch[dom],
                     cg_iterations_per_launch=prof["cg_loop_iters"] if dom == "cg_loop" else None)
     Dn = merged_row_width(c["mesh"]["tri"], N) if args.prec == "fp32" else None
-    if dom == "cg_loop" and Dn and prof["cg_loop_family"] in ("persistent", "phases"):
+    if dom == "cg_loop" and Dn and prof["cg_loop_family"] in ("persistent", "phases", "fused"):
         # the same launch against the bytes its stored operator format moves
         # (merged rows: fewer than the matrix-free element pass above)
-        fb = format_bytes_cg_iteration(N, Dn) * prof["cg_loop_iters"]
+        fb = format_bytes_cg_iteration(N, Dn, prof["cg_loop_family"]) * prof["cg_loop_iters"]
         roofline["format"] = dict(name=f"merged rows, width {Dn}", bytes_per_launch=fb,
                                   achieved=fb / (ms_launch[dom] * 1e-3) / 1e9,
                                   frac=fb / (ms_launch[dom] * 1e-3) / 1e9 / peak)
@@ -682,7 +688,7 @@ def run_ours(args):
                       per_step=[int(v) for v in iters] if args.steps <= 64 else None),
         kernel_ms=prof,
         schedule=dict(variant=sched_var, tune_ms=sched_ms,
-                      cg_loop=dict(kind=cg_kind, gathers=cg_U, ms_8_iterations=cg_ms)),
+                      cg_loop=dict(kind=cg_kind, gathers=cg_U, ms_20_iterations=cg_ms)),
     )
     if args.model == "AT2":
         line["subcycled"] = subcycled(pff, dev, args.config)

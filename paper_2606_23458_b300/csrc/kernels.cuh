@@ -1976,12 +1976,61 @@ __device__ __forceinline__ float cg_unew(const float4 v, float al, float be) {
   return v.w * fmaf(-al, fmaf(be, v.z, v.y), v.x);
 }
 
+// Width-6 merged rows of one single-reduction pass, software-pipelined as
+// nb_rows6 (the next row's records load while this row's neighbours are
+// gathered); the arithmetic of fused_rows.
+__device__ __forceinline__ void fused_rows6(const Params<float> &P, float al, float be,
+                                            const float4 *__restrict__ vin, float4 *__restrict__ vout, int i0,
+                                            int stride, DF (&acc)[3]) {
+  typedef Acc<float> AC;
+  NbRow6 cur;
+  if (i0 < P.N) nb_load6(P, i0, cur);
+  for (int j = i0; j < P.N; j += stride) {
+    NbRow6 nxt;
+    const int jn = j + stride;
+    if (jn < P.N) nb_load6(P, jn, nxt);
+    const float4 v = vin[j];
+    if ((cur.fl & kNotch) || (P.freef && !P.freef[j])) {  // eliminated row: everything stays zero
+      vout[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+      cur = nxt;
+      continue;
+    }
+    const float p = fmaf(be, P.cgp[j], v.w * v.x);
+    const float sn = fmaf(be, v.z, v.y);
+    const float rn = fmaf(-al, sn, v.x);
+    const float un = v.w * rn;
+    P.x[j] = fmaf(al, p, P.x[j]);
+    P.cgp[j] = p;
+    float wq = cur.dg * un;
+    float u[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      const uint32_t x = cur.w[k >> 1];
+      const int o = (k & 1) ? (int)x >> 16 : (int)(int16_t)(x & 0xffffu);
+      u[k] = cg_unew(vin[j + o], al, be);
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) wq = fmaf(cur.c[k], u[k], wq);
+    vout[j] = make_float4(rn, wq, sn, v.w);
+    const float sr = P.rscale * rn;
+    acc[0] = AC::add(acc[0], AC::prod(sr, un));             // gamma
+    acc[1] = AC::add(acc[1], AC::prod(P.rscale * wq, un));  // delta
+    acc[2] = AC::add(acc[2], AC::prod(sr, sr));             // |r|^2
+    cur = nxt;
+  }
+}
+
 // Rows i0, i0 + stride, ... < N of one single-reduction pass, operator and
-// neighbour vectors read from global memory (U entries in flight).
+// neighbour vectors read from global memory (U entries in flight; merged
+// rows of width 6: U >= 2 pipelines rows).
 template <int U>
 __device__ __forceinline__ void fused_rows(const Params<float> &P, float al, float be, const float4 *__restrict__ vin,
                                            float4 *__restrict__ vout, int i0, int stride, DF (&acc)[3]) {
   typedef Acc<float> AC;
+  if (U >= 2 && P.nbc && P.Dn <= 6) {
+    fused_rows6(P, al, be, vin, vout, i0, stride, acc);
+    return;
+  }
   for (int j = i0; j < P.N; j += stride) {
     const float4 v = vin[j];
     if (is_fixed(P, j)) {  // eliminated row: everything stays zero

@@ -308,7 +308,7 @@ struct pff_mesh {
   float tune_ms[16][8] = {{0}};
   // persistent AT2 CG (one cooperative launch per solve), per U = 1..4:
   // grid (0 = cannot be co-resident); the autotuner's verdict against the
-  // kernel-per-phase loop and both timings (8 iterations, ms)
+  // kernel-per-phase loop and both timings (kTuneCgIters iterations, ms)
   unsigned pgrid[5] = {0};
   unsigned fgrid[5] = {0};   // single-reduction CG grid per U (FP32)
   bool st_fused = false;     // the staged tables also fit the single-reduction kernel
@@ -324,7 +324,7 @@ struct pff_mesh {
   uint16_t *st_slot = nullptr;
   int32_t st_ns = 0;
   bool pers_tuned = false;
-  float fam_ms[8] = {0.f};   // 8 iterations of each family's best (0: not timed)
+  float fam_ms[8] = {0.f};   // kTuneCgIters iterations of each family's best (0: not timed)
   // single-reduction CG workspace (FP32): (r, w, s, 1/diag) x 2, p
   void *cgv = nullptr;
   float *cgp = nullptr;
@@ -442,6 +442,7 @@ static const void *pers_fun(int U, bool st = false) {
 // count (at most 2 per iteration per CTA) must stay below 2^31; a plan that
 // cannot run falls back to the kernel-per-phase loop.
 enum { kFamPhases = 0, kFamPersistent, kFamStaged, kFamFused, kFamFusedStaged, kFamCount };
+constexpr int kTuneCgIters = 20;  // CG iterations per timed solve of the family autotuner
 
 struct CgPlan {
   int fam = kFamPhases;
@@ -1230,11 +1231,12 @@ static pff_status autotune(pff_mesh *m, const pff_options &o, Params<R> P, bool 
     if (m->tuned[id]) m->var[id] = m->tuned_var[id];
   // AT2 CG loop: the solve graphs of a run (right-hand side, then the CG
   // loop of each family with U = 1..4 gathers in flight), each stopped after
-  // 8 iterations (tolerance 0), timed on this mesh's data with whatever the
-  // solve leaves in L2, as in a run
+  // kTuneCgIters iterations (tolerance 0: about a typical solve's count, so
+  // that a family's set-up cost weighs as in a run), timed on this mesh's
+  // data with whatever the solve leaves in L2, as in a run
   if (res == PFF_OK && with_damage && P.model == kAT2 && !m->pers_tuned &&
       o.cg_kernel != PFF_CG_PHASES && o.cg_kernel != PFF_CG_TEST_TIMEOUT) {
-    constexpr int K = 8, NK = 1 + 4 * (kFamCount - 1);  // kind 0: phases; 1 + 4 (fam - 1) + (U - 1)
+    constexpr int K = kTuneCgIters, NK = 1 + 4 * (kFamCount - 1);  // kind 0: phases; 1 + 4 (fam - 1) + (U - 1)
     Params<R> Q = P;
     Q.use_cond = 0;
     Q.tol = 0.0;
