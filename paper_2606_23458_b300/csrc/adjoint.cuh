@@ -226,6 +226,8 @@ __global__ void __launch_bounds__(256) k_adj_rhs(AdjParams<R> A) {
     const bool merge = nb_merging(P);
     NbAcc nacc;
     nacc.zero();
+    if constexpr (sizeof(R) == 4)
+      if (merge) nacc.load_map(P, i);
     // two incidence entries in flight, summed in slot order
     for (int k = 0; k < P.D; k += 2) {
       int en[2];

@@ -201,6 +201,8 @@ __global__ void __launch_bounds__(256) kb_rhs(Params<R> P, Batch B) {
       const bool merge = nb_merging(Q);
       NbAcc nacc;
       nacc.zero();
+      if constexpr (sizeof(R) == 4)
+        if (merge) nacc.load_map(Q, i);
       for (int k = 0; k < P.D; k += U) {
         R4 o[U];
         float2 cf[U];

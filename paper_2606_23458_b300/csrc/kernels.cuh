@@ -157,12 +157,12 @@ template <typename R> struct Params {
   // nbo packs the row's ascending neighbour offsets j - i two per word
   // (Dn / 2 words, incidence-style layout w N + i), nbc holds the merged
   // coefficient of each (Dn x N); padding slots are offset 0, coefficient
-  // 0.  nmap (D x N bytes) gives, per incidence slot, the merged slots of
-  // the entry's two neighbours (low and high nibble; 0xff = empty).  The
-  // right-hand side fills nbc from ecf.  Nullable.
+  // 0.  nmap (one 8-byte word per row, byte k for incidence slot k) gives
+  // the merged slots of the entry's two neighbours (low and high nibble;
+  // 0xff = empty).  The right-hand side fills nbc.  Nullable.
   const uint32_t *__restrict__ nbo;
   float *nbc;
-  const uint8_t *__restrict__ nmap;
+  const uint2 *__restrict__ nmap;
   int32_t Dn;
   R *diag;       // with erec: the row's diagonal sum over entries of
                  // (kappa_e A_e |grad phi_a|^2 + 2 mA)
@@ -782,7 +782,7 @@ constexpr int kNbMax = 8;  // merged rows: most distinct neighbours of a row
 // max); else the offsets (Dn slots, padded with 0) and each incidence
 // slot's merged slots are written.
 __global__ void __launch_bounds__(256) k_nb_build(const uint32_t *__restrict__ ecmp, int N, int D, int Dn,
-                                                  int *maxcnt, uint32_t *nbo, uint8_t *nmap) {
+                                                  int *maxcnt, uint32_t *nbo, uint2 *nmap) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
     int o[2 * kNbMax];
     int n = 0;
@@ -807,18 +807,19 @@ __global__ void __launch_bounds__(256) k_nb_build(const uint32_t *__restrict__ e
       const int lo = 2 * w < n ? o[2 * w] : 0, hi = 2 * w + 1 < n ? o[2 * w + 1] : 0;
       nbo[(size_t)w * N + i] = (uint32_t)(uint16_t)(int16_t)lo | ((uint32_t)(uint16_t)(int16_t)hi << 16);
     }
+    uint32_t mw[2] = {0xffffffffu, 0xffffffffu};
     for (int k = 0; k < D; ++k) {
       const uint32_t w = ecmp[(size_t)k * N + i];
-      uint8_t m = 0xffu;
       if (w != 0u) {
         const int ob = (int)(int16_t)(w & 0xffffu), oc = (int)w >> 16;
         int jb = 0, jc = 0;
         while (o[jb] != ob) ++jb;
         while (o[jc] != oc) ++jc;
-        m = (uint8_t)(jb | (jc << 4));
+        const int sh = 8 * (k & 3);
+        mw[k >> 2] = (mw[k >> 2] & ~(0xffu << sh)) | ((uint32_t)(jb | (jc << 4)) << sh);
       }
-      nmap[(size_t)k * N + i] = m;
     }
+    nmap[i] = make_uint2(mw[0], mw[1]);
   }
 }
 
@@ -827,12 +828,15 @@ __global__ void __launch_bounds__(256) k_nb_build(const uint32_t *__restrict__ e
 // schedule produced the entries.
 struct NbAcc {
   float a[kNbMax];
+  uint2 map;  // the row's slot map
   __device__ __forceinline__ void zero() {
 #pragma unroll
     for (int j = 0; j < kNbMax; ++j) a[j] = 0.f;
+    map = make_uint2(0xffffffffu, 0xffffffffu);
   }
+  __device__ __forceinline__ void load_map(const Params<float> &P, int i) { map = __ldg(&P.nmap[i]); }
   __device__ __forceinline__ void add(const Params<float> &P, int k, int i, float2 c) {
-    const unsigned m = __ldg(&P.nmap[(size_t)k * P.N + i]);
+    const unsigned m = ((k < 4 ? map.x : map.y) >> (8 * (k & 3))) & 0xffu;
     if (m == 0xffu) return;
     const unsigned jb = m & 15u, jc = m >> 4;
 #pragma unroll
@@ -864,6 +868,7 @@ __device__ __forceinline__ void nb_merge_row(const Params<R> &P, int i) {
     if (!nb_merging(P)) return;
     NbAcc acc;
     acc.zero();
+    acc.load_map(P, i);
     for (int k = 0; k < P.D; ++k) acc.add(P, k, i, P.ecf[(size_t)k * P.N + i]);
     acc.store(P, i);
   }
@@ -1126,6 +1131,8 @@ __global__ void __launch_bounds__(256) k_dmg_rhs_nc(Params<R> P) {
     const bool merge = nb_merging(P);
     NbAcc nacc;
     nacc.zero();
+    if constexpr (sizeof(R) == 4)
+      if (merge) nacc.load_map(P, i);
     for (int k = 0; k < P.D; k += U) {
       R4 o[U];
       float2 cf[U];
@@ -1733,12 +1740,13 @@ __device__ __forceinline__ void grid_partials(const double *part, double *tot, t
     }
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (wid == 0) {  // the warps' sums folded by a shuffle tree in warp 0
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
-      typename A::T s = sh[0][k];
-      for (int q = 1; q < kPartWarps; ++q) s = A::add(s, sh[q][k]);
-      tot[k] = A::to_d(s);
+      typename A::T s = lane < kPartWarps ? sh[lane][k] : A::zero();
+#pragma unroll
+      for (int o = kPartWarps / 2; o > 0; o >>= 1) s = A::add(s, A::shfl(s, o));
+      if (lane == 0) tot[k] = A::to_d(s);
     }
   }
   __syncthreads();  // sh is free again, tot is visible to every thread

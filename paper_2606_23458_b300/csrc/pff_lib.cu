@@ -271,7 +271,7 @@ struct pff_mesh {
   int64_t span = 0;          // largest node-id difference within an element
   uint32_t *nbo = nullptr;   // FP32 merged rows: neighbour offsets (Dn / 2 x N)
   float *nbc = nullptr;      // FP32 merged rows: coefficients (Dn x N)
-  uint8_t *nmap = nullptr;   // FP32 merged rows: incidence slot -> merged slots (D x N)
+  uint2 *nmap = nullptr;     // FP32 merged rows: incidence slot -> merged slots (8 bytes per row)
   int32_t Dn = 0;            // merged row width (6 or 8; 0 = not used)
   float *diagf = nullptr;  // FP32: the damage rows' diagonals (N)
   void *fe = nullptr;      // slot forces of the element-pass force schedule (3 Ne x R2)
@@ -832,7 +832,7 @@ static pff_status configure(pff_mesh *m) {
         m->Dn = mx <= 6 ? 6 : kNbMax;
         PFF_TRY(dalloc(&m->nbo, (size_t)(m->Dn / 2) * m->N));
         PFF_TRY(dalloc(&m->nbc, (size_t)m->Dn * m->N));
-        PFF_TRY(dalloc(&m->nmap, (size_t)D * m->N));
+        PFF_TRY(dalloc(&m->nmap, (size_t)m->N));
         CUDA_TRY(cudaMemset(m->nbc, 0, (size_t)m->Dn * m->N * sizeof(float)));
         k_nb_build<<<gb, 256>>>(m->ecmp, (int)m->N, D, m->Dn, nullptr, m->nbo, m->nmap);
         CUDA_TRY(cudaGetLastError());
