@@ -1818,9 +1818,13 @@ static pff_status qs_run_t(pff_mesh *m, const pff_state *st, const uint8_t *bc_h
   SolveScalars *bsc = nullptr;  // grid-barrier counter and abort flag of the persistent CG
   uint32_t *ofs = nullptr;      // FP32 entry records of the tangent (row form)
   float4 *kb = nullptr, *kc = nullptr;
+  uint32_t *qnbo = nullptr;     // merged rows of the tangent (row form, width 6)
+  uint2 *qnmap = nullptr;
+  float4 *nbk = nullptr;
+  int *cnt = nullptr;
   pff_status res = PFF_OK;
   auto cleanup = [&]() {
-    void *ptrs[] = {bc, pz, r, q, x, dg, fe, rec, qs, bsc, ofs, kb, kc};
+    void *ptrs[] = {bc, pz, r, q, x, dg, fe, rec, qs, bsc, ofs, kb, kc, qnbo, qnmap, nbk, cnt};
     for (void *p : ptrs)
       if (p) cudaFree(p);
   };
@@ -1831,6 +1835,14 @@ static pff_status qs_run_t(pff_mesh *m, const pff_state *st, const uint8_t *bc_h
       cleanup();               \
       return res;              \
     }                          \
+  } while (0)
+#define QS_CUDA(x)                                                                    \
+  do {                                                                                \
+    const cudaError_t e_ = (x);                                                       \
+    if (e_ != cudaSuccess) {                                                          \
+      cleanup();                                                                      \
+      return fail(PFF_ERR_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_));    \
+    }                                                                                 \
   } while (0)
   QS_TRY(dalloc(&bc, N));
   QS_TRY(dalloc(&pz, N));
@@ -1848,8 +1860,31 @@ static pff_status qs_run_t(pff_mesh *m, const pff_state *st, const uint8_t *bc_h
   if (rows) {
     const size_t DN = (size_t)m->D * N;
     QS_TRY(dalloc(&ofs, DN));
-    QS_TRY(dalloc(&kb, DN));
-    QS_TRY(dalloc(&kc, DN));
+    // merged rows where every row has at most six distinct neighbours: the
+    // neighbour offsets of the incidence (the packing of the damage
+    // records), then the rows' distinct neighbours and slot maps
+    int mx = 1 << 30;
+    if (m->D <= kNbMax) {
+      const unsigned gb = std::min<unsigned>(grid_for(N, 256), stride_cap());
+      k_erec_ids<R><<<gb, 256, 0, s>>>((const ERec<R> *)m->rec, m->ell, (int)N, m->D, ofs, nullptr);
+      QS_TRY(dalloc(&cnt, 1));
+      QS_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int), s));
+      k_nb_build<<<gb, 256, 0, s>>>(ofs, (int)N, m->D, 0, cnt, nullptr, nullptr);
+      QS_CUDA(cudaGetLastError());
+      QS_CUDA(cudaMemcpyAsync(&mx, cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
+      QS_CUDA(cudaStreamSynchronize(s));
+      if (mx <= 6) {
+        QS_TRY(dalloc(&qnbo, 3 * (size_t)N));
+        QS_TRY(dalloc(&qnmap, (size_t)N));
+        QS_TRY(dalloc(&nbk, 6 * (size_t)N));
+        k_nb_build<<<gb, 256, 0, s>>>(ofs, (int)N, m->D, 6, nullptr, qnbo, qnmap);
+        QS_CUDA(cudaGetLastError());
+      }
+    }
+    if (!nbk) {
+      QS_TRY(dalloc(&kb, DN));
+      QS_TRY(dalloc(&kc, DN));
+    }
   }
   if (cudaMemcpyAsync(bc, bc_host, N, cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemsetAsync(qs, 0, sizeof(QsScalars), s) != cudaSuccess) {
@@ -1878,6 +1913,9 @@ static pff_status qs_run_t(pff_mesh *m, const pff_state *st, const uint8_t *bc_h
   I.ofs = ofs;
   I.kb = kb;
   I.kc = kc;
+  I.nbo = qnbo;
+  I.nmap = qnmap;
+  I.nbk = nbk;
   I.qs = qs;
   I.part = Q.P.part;
   I.ticket = Q.P.ticket;
@@ -1999,6 +2037,7 @@ static pff_status qs_run_t(pff_mesh *m, const pff_state *st, const uint8_t *bc_h
     }
   }
 #undef QS_TRY
+#undef QS_CUDA
   cleanup();
   if (worst != PFF_OK) return fail(worst, "a quasi-static Newton, mechanics CG or damage solve did not converge");
   return PFF_OK;

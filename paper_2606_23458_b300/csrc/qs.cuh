@@ -62,6 +62,17 @@ template <typename K> struct QkParams {
   // translation gives exactly 0 in FP32 too, and no diagonal block is kept
   uint32_t *ofs;
   float4 *kb, *kc;
+  // merged rows of width 6 (nullable nbk: rows with more than six distinct
+  // neighbours keep the entry records): the row's ascending neighbour
+  // offsets (three words, incidence-style layout w N + i), the slot map of
+  // its incidence entries (one 8-byte word per row) and per neighbour slot
+  // the sum of the entries' 2 x 2 blocks for that neighbour (at j N + i;
+  // padding slots offset 0, block 0).  Row i is then
+  // sum_j K_ij (p_j - p_i), K_ij the exact transpose of K_ji (two
+  // elements per edge: the sum does not depend on their order).
+  const uint32_t *nbo;
+  const uint2 *nmap;
+  float4 *nbk;
   QsScalars *qs;
   double *part;       // per-block partial sums and the ticket of reduce_last
   unsigned int *ticket;
@@ -557,13 +568,22 @@ __device__ __forceinline__ float4 qs_pair_block(const K (&t)[9], const K (&g)[4]
 // empty slots get zero offsets and zero blocks (they add an exact 0).
 __global__ void __launch_bounds__(256) k_qs_entry_build(QkParams<float> I) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < I.N; i += gridDim.x * blockDim.x) {
+    float4 acc[6];
+    uint2 map = make_uint2(0xffffffffu, 0xffffffffu);
+    if (I.nbk) {
+#pragma unroll
+      for (int j = 0; j < 6; ++j) acc[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+      map = __ldg(&I.nmap[i]);
+    }
     for (int k = 0; k < I.D; ++k) {
       const size_t q = (size_t)k * I.N + i;
       const int en = __ldg(&I.ell[q]);
       if (en < 0) {
-        I.ofs[q] = 0u;
-        I.kb[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-        I.kc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (!I.nbk) {
+          I.ofs[q] = 0u;
+          I.kb[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+          I.kc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
         continue;
       }
       const int a = en & 3;
@@ -571,10 +591,36 @@ __global__ void __launch_bounds__(256) k_qs_entry_build(QkParams<float> I) {
       float t[9], g[4];
       qrec_load(I.rec + (en >> 2), n0, n1, n2, t, g);
       const int b = a == 0 ? 1 : 0, c = a == 2 ? 1 : 2;
+      const float4 kb = qs_pair_block(t, g, a, b), kc = qs_pair_block(t, g, a, c);
+      if (I.nbk) {
+        // merged: each block into its neighbour's slot, in slot order
+        const unsigned m = ((k < 4 ? map.x : map.y) >> (8 * (k & 3))) & 0xffu;
+        const unsigned jb = m & 15u, jc = m >> 4;
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+          if (jb == (unsigned)j) {
+            acc[j].x = __fadd_rn(acc[j].x, kb.x);
+            acc[j].y = __fadd_rn(acc[j].y, kb.y);
+            acc[j].z = __fadd_rn(acc[j].z, kb.z);
+            acc[j].w = __fadd_rn(acc[j].w, kb.w);
+          }
+          if (jc == (unsigned)j) {
+            acc[j].x = __fadd_rn(acc[j].x, kc.x);
+            acc[j].y = __fadd_rn(acc[j].y, kc.y);
+            acc[j].z = __fadd_rn(acc[j].z, kc.z);
+            acc[j].w = __fadd_rn(acc[j].w, kc.w);
+          }
+        }
+        continue;
+      }
       const int nb = b == 0 ? n0 : n1, nc = c == 1 ? n1 : n2;
       I.ofs[q] = (uint32_t)(uint16_t)(int16_t)(nb - i) | ((uint32_t)(uint16_t)(int16_t)(nc - i) << 16);
-      I.kb[q] = qs_pair_block(t, g, a, b);
-      I.kc[q] = qs_pair_block(t, g, a, c);
+      I.kb[q] = kb;
+      I.kc[q] = kc;
+    }
+    if (I.nbk) {
+#pragma unroll
+      for (int j = 0; j < 6; ++j) I.nbk[(size_t)j * I.N + i] = acc[j];
     }
   }
 }
@@ -617,7 +663,30 @@ __global__ void __launch_bounds__(kQsPersThreads, 2) k_qs_cg_rows(QkParams<float
     for (int i = tid; i < I.N; i += stride) {
       const K2 pc = qs_pnew(I, i, beta);
       float qx = 0.f, qy = 0.f;
-      for (int k = 0; k < I.D; k += U) {
+      if (I.nbk) {
+        // merged row: all six records, then the six neighbour gathers in
+        // flight, then sum_j K_ij (p_j - p_i) in slot order (padding slots
+        // have offset 0 and add an exact 0)
+        uint32_t w[3];
+        float4 kk[6];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) w[j] = __ldg(&I.nbo[(size_t)j * I.N + i]);
+#pragma unroll
+        for (int j = 0; j < 6; ++j) kk[j] = __ldg(&I.nbk[(size_t)j * I.N + i]);
+        K2 pj[6];
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+          const uint32_t x = w[j >> 1];
+          pj[j] = qs_pnew(I, i + ((j & 1) ? (int)x >> 16 : (int)(int16_t)(x & 0xffffu)), beta);
+        }
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+          const float dx = pj[j].x - pc.x, dy = pj[j].y - pc.y;
+          qx = __fadd_rn(qx, fmaf(kk[j].x, dx, __fmul_rn(kk[j].y, dy)));
+          qy = __fadd_rn(qy, fmaf(kk[j].z, dx, __fmul_rn(kk[j].w, dy)));
+        }
+      }
+      for (int k = 0; k < I.D && !I.nbk; k += U) {
         uint32_t w[U];
         float4 bb[U], cc[U];
 #pragma unroll
