@@ -778,11 +778,12 @@ constexpr int kNbMax = 8;  // merged rows: most distinct neighbours of a row
 
 // The mesh-only half of the merged rows, once per mesh (compact records):
 // per node the distinct neighbour offsets of its incidence entries in
-// ascending order.  count_only: the largest count goes to *maxcnt (atomic
-// max); else the offsets (Dn slots, padded with 0) and each incidence
-// slot's merged slots are written.
+// ascending order.  With maxcnt the largest count goes there (one atomic
+// max per warp); else the offsets (Dn slots, padded with 0) and each
+// incidence slot's merged slots are written.
 __global__ void __launch_bounds__(256) k_nb_build(const uint32_t *__restrict__ ecmp, int N, int D, int Dn,
                                                   int *maxcnt, uint32_t *nbo, uint2 *nmap) {
+  int most = 0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
     int o[2 * kNbMax];
     int n = 0;
@@ -800,7 +801,7 @@ __global__ void __launch_bounds__(256) k_nb_build(const uint32_t *__restrict__ e
       }
     }
     if (maxcnt) {
-      atomicMax(maxcnt, D > kNbMax ? 2 * kNbMax : n);
+      most = max(most, D > kNbMax ? 2 * kNbMax : n);
       continue;
     }
     for (int w = 0; w < Dn / 2; ++w) {
@@ -820,6 +821,10 @@ __global__ void __launch_bounds__(256) k_nb_build(const uint32_t *__restrict__ e
       }
     }
     nmap[i] = make_uint2(mw[0], mw[1]);
+  }
+  if (maxcnt) {
+    most = __reduce_max_sync(0xffffffffu, most);
+    if ((threadIdx.x & 31) == 0) atomicMax(maxcnt, most);
   }
 }
 

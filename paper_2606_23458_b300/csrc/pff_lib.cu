@@ -344,7 +344,8 @@ static void mesh_free(pff_mesh *m) {
   free_graph(m->step_g);
   free_graph(m->mech_g);
   void *ptrs[] = {m->gcs, m->st_cta, m->st_rng, m->st_nrng, m->st_lrec, m->st_slot, m->cgv, m->cgp,
-                  m->ptr, m->ent, m->ell, m->rec, m->drec, m->erec, m->ecmp, m->ecf, m->nbo, m->nbc, m->nmap, m->diagf, m->fe, m->fext, m->minv,
+                  m->ptr, m->ent, m->ell, m->rec, m->drec, m->erec, m->ecmp, m->ecf, m->nbo, m->nbc, m->nmap,
+                  m->diagf, m->fe, m->fext, m->minv,
                   m->area_d,
                   m->flags,
                   m->x, m->r, m->b, m->part, m->energy, m->wext, m->pz, m->q, m->dinv,
