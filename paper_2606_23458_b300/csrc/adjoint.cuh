@@ -166,7 +166,7 @@ __device__ __forceinline__ void split_tangent(const Params<R> &P, R exx, R eyy, 
 // entry record.
 template <typename R>
 __device__ __forceinline__ void adj_rhs_entry(const AdjParams<R> &A, const Slot<R> &S, int en, int k, int i,
-                                              R &dgc, R &axc, float2 *cf) {
+                                              R &dgc, R &axc, typename Params<R>::R2 *cf) {
   typedef typename Params<R>::R4 R4;
   const Params<R> &P = A.P;
   const int e = en >> 2, a = en & 3;
@@ -224,17 +224,16 @@ __global__ void __launch_bounds__(256) k_adj_rhs(AdjParams<R> A) {
     }
     R dg = 0, ax = 0;
     const bool merge = nb_merging(P);
-    NbAcc nacc;
+    NbAcc<R> nacc;
     nacc.zero();
-    if constexpr (sizeof(R) == 4)
-      if (merge) nacc.load_map(P, i);
+    if (merge) nacc.load_map(P, i);
     // two incidence entries in flight, summed in slot order
     for (int k = 0; k < P.D; k += 2) {
       int en[2];
 #pragma unroll
       for (int u = 0; u < 2; ++u) en[u] = k + u < P.D ? __ldg(&P.ell[(size_t)(k + u) * P.N + i]) : -1;
       R cd[2], ca[2];
-      float2 cf[2];
+      typename Params<R>::R2 cf[2];
 #pragma unroll
       for (int u = 0; u < 2; ++u)
         if (en[u] >= 0) adj_rhs_entry(A, S, en[u], k + u, i, cd[u], ca[u], merge ? &cf[u] : nullptr);
@@ -243,14 +242,12 @@ __global__ void __launch_bounds__(256) k_adj_rhs(AdjParams<R> A) {
         if (en[u] >= 0) {
           dg = radd(dg, cd[u]);
           ax = radd(ax, ca[u]);
-          if constexpr (sizeof(R) == 4)
-            if (merge) nacc.add(P, k + u, i, cf[u]);
+          if (merge) nacc.add(k + u, cf[u]);
         }
     }
     const R ri = gi - ax, di = R(1) / dg, zi = ri * di;
     if (P.diag) P.diag[i] = dg;
-    if constexpr (sizeof(R) == 4)
-      if (merge) nacc.store(P, i);
+    if (merge) nacc.store(P, i);
     P.r[i] = ri;
     P.dinv[i] = di;
     typename Params<R>::R2 w;

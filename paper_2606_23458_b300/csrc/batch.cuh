@@ -199,13 +199,12 @@ __global__ void __launch_bounds__(256) kb_rhs(Params<R> P, Batch B) {
     } else {
       R bi = 0, dg = 0, ax = 0, a1 = 0;
       const bool merge = nb_merging(Q);
-      NbAcc nacc;
+      NbAcc<R> nacc;
       nacc.zero();
-      if constexpr (sizeof(R) == 4)
-        if (merge) nacc.load_map(Q, i);
+      if (merge) nacc.load_map(Q, i);
       for (int k = 0; k < P.D; k += U) {
         R4 o[U];
-        float2 cf[U];
+        typename Params<R>::R2 cf[U];
         int en[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) en[u] = k + u < P.D ? __ldg(&P.ell[(size_t)(k + u) * P.N + i]) : -1;
@@ -219,13 +218,11 @@ __global__ void __launch_bounds__(256) kb_rhs(Params<R> P, Batch B) {
             dg = radd(dg, o[u].y);
             ax = radd(ax, o[u].z);
             a1 = radd(a1, o[u].w);
-            if constexpr (sizeof(R) == 4)
-              if (merge) nacc.add(Q, k + u, i, cf[u]);
+            if (merge) nacc.add(k + u, cf[u]);
           }
       }
       rhs_node(Q, i, bi, dg, ax, a1, vals);
-      if constexpr (sizeof(R) == 4)
-        if (merge) nacc.store(Q, i);
+      if (merge) nacc.store(Q, i);
     }
   }
   __shared__ double tot[3];
@@ -257,10 +254,13 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 6 : 1) kb_matvec(Params<
       bool done = false;
       if constexpr (sizeof(R) == 4) {
         if (has_erec(Q)) {
-          // FP32 entry records (see matvec_rows)
+          // FP32 entry records or merged rows (see matvec_rows)
           q = erec_row<U>(Q, i, beta, pc);
           done = true;
         }
+      } else if (Q.nbc) {  // FP64 merged rows
+        q = nb_row_any(Q, i, Q.diag[i] * pc, [&](int j) { return pnew(Q, j, beta); });
+        done = true;
       }
       for (int k = 0; k < P.D && !done; k += U) {
         R c[U];

@@ -151,7 +151,8 @@ template <typename R> struct Params {
                   // b - i (low half) and c - i (high half), ecf the two
                   // coefficients; an empty slot is offsets 0, coefficients 0.
                   // Nullable; at most one of erec and ecmp is set.
-  // FP32, compact meshes whose rows have at most kNbMax distinct neighbours:
+  // Compact meshes (both precisions) whose rows have at most kNbMax distinct
+  // neighbours:
   // the same rows with each neighbour's coefficients merged (rows sum the
   // per-element coefficients of a neighbour shared by two elements once):
   // nbo packs the row's ascending neighbour offsets j - i two per word
@@ -161,7 +162,7 @@ template <typename R> struct Params {
   // the merged slots of the entry's two neighbours (low and high nibble;
   // 0xff = empty).  The right-hand side fills nbc.  Nullable.
   const uint32_t *__restrict__ nbo;
-  float *nbc;
+  R *nbc;
   const uint2 *__restrict__ nmap;
   int32_t Dn;
   R *diag;       // with erec: the row's diagonal sum over entries of
@@ -729,18 +730,22 @@ __device__ __forceinline__ bool has_erec(const Params<R> &P) {
 // (slot k, node i); the neighbour ids or offsets depend on the mesh alone
 // and are written once (k_erec_ids).
 template <typename R>
-__device__ __forceinline__ float2 erec_coef(const typename Params<R>::R4 &G, int a, R kA, R mA) {
+__device__ __forceinline__ typename Params<R>::R2 erec_coef(const typename Params<R>::R4 &G, int a, R kA, R mA) {
   R gx, gy, gbx, gby, gcx, gcy;
   slot_grad<R>(G, a, gx, gy);
   slot_grad<R>(G, a == 0 ? 1 : 0, gbx, gby);
   slot_grad<R>(G, a == 2 ? 1 : 2, gcx, gcy);
-  return make_float2((float)(kA * (gx * gbx + gy * gby) + mA), (float)(kA * (gx * gcx + gy * gcy) + mA));
+  typename Params<R>::R2 c;  // roundings spelled out: every schedule gets the same bits
+  c.x = rfma(kA, rfma(gx, gbx, rmul(gy, gby)), mA);
+  c.y = rfma(kA, rfma(gx, gcx, rmul(gy, gcy)), mA);
+  return c;
 }
 
 template <typename R>
 __device__ __forceinline__ void put_erec(const Params<R> &P, int k, int i, const typename Params<R>::R4 &G, int a,
                                          R kA, R mA) {
-  const float2 c = erec_coef<R>(G, a, kA, mA);
+  const typename Params<R>::R2 cr = erec_coef<R>(G, a, kA, mA);
+  const float2 c = make_float2((float)cr.x, (float)cr.y);
   const size_t q = (size_t)k * P.N + i;
   if (P.ecmp)
     P.ecf[q] = c;
@@ -831,62 +836,82 @@ __global__ void __launch_bounds__(256) k_nb_build(const uint32_t *__restrict__ e
 // A row's merged coefficients, accumulated entry by entry in incidence-slot
 // order (b before c within an entry), then stored: the same order whichever
 // schedule produced the entries.
-struct NbAcc {
-  float a[kNbMax];
+template <typename R> struct NbAcc {
+  R a[kNbMax];
   uint2 map;  // the row's slot map
   __device__ __forceinline__ void zero() {
 #pragma unroll
-    for (int j = 0; j < kNbMax; ++j) a[j] = 0.f;
+    for (int j = 0; j < kNbMax; ++j) a[j] = R(0);
     map = make_uint2(0xffffffffu, 0xffffffffu);
   }
-  __device__ __forceinline__ void load_map(const Params<float> &P, int i) { map = __ldg(&P.nmap[i]); }
-  __device__ __forceinline__ void add(const Params<float> &P, int k, int i, float2 c) {
+  __device__ __forceinline__ void load_map(const Params<R> &P, int i) { map = __ldg(&P.nmap[i]); }
+  __device__ __forceinline__ void add(int k, typename Params<R>::R2 c) {
     const unsigned m = ((k < 4 ? map.x : map.y) >> (8 * (k & 3))) & 0xffu;
     if (m == 0xffu) return;
     const unsigned jb = m & 15u, jc = m >> 4;
 #pragma unroll
     for (int j = 0; j < kNbMax; ++j) {
-      if (jb == (unsigned)j) a[j] = __fadd_rn(a[j], c.x);
-      if (jc == (unsigned)j) a[j] = __fadd_rn(a[j], c.y);
+      if (jb == (unsigned)j) a[j] = radd(a[j], c.x);
+      if (jc == (unsigned)j) a[j] = radd(a[j], c.y);
     }
   }
-  __device__ __forceinline__ void store(const Params<float> &P, int i) const {
+  __device__ __forceinline__ void store(const Params<R> &P, int i) const {
 #pragma unroll
     for (int j = 0; j < kNbMax; ++j)
       if (j < P.Dn) P.nbc[(size_t)j * P.N + i] = a[j];
   }
 };
 
-// Whether a right-hand-side pass merges rows (FP32 with merged rows; the
+// Whether a right-hand-side pass merges rows (merged rows present; the
 // staged families' passes run without records).
 template <typename R>
 __device__ __forceinline__ bool nb_merging(const Params<R> &P) {
-  if constexpr (sizeof(R) == 4) return P.nbc != nullptr && P.ecf != nullptr;
-  return false;
+  return P.nbc != nullptr;
 }
 
-// Row i's merged coefficients from its entry coefficients in ecf (written
-// by its block before a block barrier: the entry-parallel schedule).
+// Coefficients kappa_e A_e and mA = c_e A_e / 12 of element e's damage
+// operator (c_e = cbase + 2 H_e, both scaled by the toughness field), with
+// every rounding spelled out so that each caller gets the same bits.
+template <typename R>
+__device__ __forceinline__ void dmg_coefs(const Params<R> &P, int e, R A, R h, R sg, R &kA, R &mA) {
+  const R c = rfma(P.cbase, sg, R(2) * h);
+  kA = rmul(rmul(P.kappa, sg), A);
+  mA = rmul(rmul(c, A), R(1) / R(12));
+}
+
+// Row i's merged coefficients with its entries' coefficients evaluated
+// again here (the entry-parallel schedule, whose entries are evaluated by
+// other threads of the block): rhs_entry's arithmetic.
 template <typename R>
 __device__ __forceinline__ void nb_merge_row(const Params<R> &P, int i) {
-  if constexpr (sizeof(R) == 4) {
-    if (!nb_merging(P)) return;
-    NbAcc acc;
-    acc.zero();
-    acc.load_map(P, i);
-    for (int k = 0; k < P.D; ++k) acc.add(P, k, i, P.ecf[(size_t)k * P.N + i]);
-    acc.store(P, i);
+  if (!nb_merging(P)) return;
+  typedef typename Params<R>::R4 R4;
+  NbAcc<R> acc;
+  acc.zero();
+  acc.load_map(P, i);
+  for (int k = 0; k < P.D; ++k) {
+    const int en = __ldg(&P.ell[(size_t)k * P.N + i]);
+    if (en < 0) continue;
+    const int e = en >> 2;
+    int4 t;
+    R A;
+    R4 G;
+    load_elem(P, e, t, A, G);
+    R kA, mA;
+    dmg_coefs(P, e, A, P.Hr[e], gc_scale(P, e), kA, mA);
+    acc.add(k, erec_coef<R>(G, en & 3, kA, mA));
   }
+  acc.store(P, i);
 }
 
 // Row i of the merged operator applied to the values val(j) of its
 // neighbours, added to q (diag_i times the row's own value): all DN
 // records, then all DN neighbour gathers in flight, then an explicit fma
 // chain in slot order (padding slots add an exact 0).
-template <int DN, typename F>
-__device__ __forceinline__ float nb_row(const Params<float> &P, int i, float q, F val) {
+template <int DN, typename R, typename F>
+__device__ __forceinline__ R nb_row(const Params<R> &P, int i, R q, F val) {
   uint32_t w[DN / 2];
-  float c[DN], v[DN];
+  R c[DN], v[DN];
 #pragma unroll
   for (int j = 0; j < DN / 2; ++j) w[j] = __ldg(&P.nbo[(size_t)j * P.N + i]);
 #pragma unroll
@@ -898,12 +923,12 @@ __device__ __forceinline__ float nb_row(const Params<float> &P, int i, float q, 
     v[j] = val(i + o);
   }
 #pragma unroll
-  for (int j = 0; j < DN; ++j) q = fmaf(c[j], v[j], q);
+  for (int j = 0; j < DN; ++j) q = fma(c[j], v[j], q);
   return q;
 }
 
-template <typename F>
-__device__ __forceinline__ float nb_row_any(const Params<float> &P, int i, float q, F val) {
+template <typename R, typename F>
+__device__ __forceinline__ R nb_row_any(const Params<R> &P, int i, R q, F val) {
   return P.Dn <= 6 ? nb_row<6>(P, i, q, val) : nb_row<8>(P, i, q, val);
 }
 
@@ -979,7 +1004,8 @@ __global__ void __launch_bounds__(256) k_drec_build(Params<R> P) {
 // of written to the entry records.
 template <typename R>
 __device__ __forceinline__ typename Params<R>::R4 rhs_entry(const Params<R> &P, int en, int slot = -1,
-                                                            int node = -1, int csr = -1, float2 *cf = nullptr) {
+                                                            int node = -1, int csr = -1,
+                                                            typename Params<R>::R2 *cf = nullptr) {
   typedef typename Params<R>::R4 R4;
   const int e = en >> 2, a = en & 3;
   int4 t;
@@ -988,12 +1014,13 @@ __device__ __forceinline__ typename Params<R>::R4 rhs_entry(const Params<R> &P, 
   load_elem(P, e, t, A, G);
   const R h = P.Hr[e];
   const R sg = gc_scale(P, e);
-  const R c = P.cbase * sg + R(2) * h, w = P.wbase * sg + R(2) * h;
+  const R w = P.wbase * sg + R(2) * h;
   const bool n0 = P.flags[t.x] & kNotch, n1 = P.flags[t.y] & kNotch, n2 = P.flags[t.z] & kNotch;
   const R x0 = n0 ? R(1) : P.dprev[t.x];
   const R x1 = n1 ? R(1) : P.dprev[t.y];
   const R x2 = n2 ? R(1) : P.dprev[t.z];
-  const R kA = (P.kappa * sg) * A, mA = c * A * (R(1) / R(12));
+  R kA, mA;
+  dmg_coefs(P, e, A, h, sg, kA, mA);
   R gx, gy;
   slot_grad<R>(G, a, gx, gy);
   if (a == 0 && P.drec) P.drec[e] = make_drec<R>(t, G, kA, mA);
@@ -1134,13 +1161,12 @@ __global__ void __launch_bounds__(256) k_dmg_rhs_nc(Params<R> P) {
     }
     R bi = 0, dg = 0, ax = 0, a1 = 0;
     const bool merge = nb_merging(P);
-    NbAcc nacc;
+    NbAcc<R> nacc;
     nacc.zero();
-    if constexpr (sizeof(R) == 4)
-      if (merge) nacc.load_map(P, i);
+    if (merge) nacc.load_map(P, i);
     for (int k = 0; k < P.D; k += U) {
       R4 o[U];
-      float2 cf[U];
+      typename Params<R>::R2 cf[U];
       int en[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) en[u] = k + u < P.D ? __ldg(&P.ell[(size_t)(k + u) * P.N + i]) : -1;
@@ -1154,13 +1180,11 @@ __global__ void __launch_bounds__(256) k_dmg_rhs_nc(Params<R> P) {
           dg = radd(dg, o[u].y);
           ax = radd(ax, o[u].z);
           a1 = radd(a1, o[u].w);
-          if constexpr (sizeof(R) == 4)
-            if (merge) nacc.add(P, k + u, i, cf[u]);
+          if (merge) nacc.add(k + u, cf[u]);
         }
     }
     rhs_node(P, i, bi, dg, ax, a1, vals);
-    if constexpr (sizeof(R) == 4)
-      if (merge) nacc.store(P, i);
+    if (merge) nacc.store(P, i);
   }
   __shared__ double tot[3];
   if (reduce_last<R, 3>(vals, P.part, P.ticket, tot) && threadIdx.x == 0) rhs_finish(P, tot);
@@ -1332,17 +1356,20 @@ __global__ void __launch_bounds__(256) k_cg_matvec_ep(Params<R> P) {
   R *cq = reinterpret_cast<R *>(smem_raw);
   typename AC::T vals[1] = {AC::zero()};
   const R beta = sc_beta<R>(P.sc);
-  if constexpr (sizeof(R) == 4) {
-    if (has_erec(P)) {
-      // FP32 entry records: rows of the block's nodes, the same per-row
-      // arithmetic as the node-centric schedules
+  if (P.nbc || has_erec(P)) {
+    {
+      // merged rows or FP32 entry records: rows of the block's nodes, the
+      // same per-row arithmetic as the node-centric schedules
       for (int b = blockIdx.x; b < P.nblk; b += gridDim.x) {
         const int i0 = b * P.NB, i1 = min(i0 + P.NB, P.N);
         for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
           R q = 0;
           if (!is_fixed(P, i)) {
             const R pc = pnew(P, i, beta);
-            q = erec_row<1>(P, i, beta, pc);
+            if constexpr (sizeof(R) == 4)
+              q = erec_row<1>(P, i, beta, pc);
+            else
+              q = nb_row_any(P, i, P.diag[i] * pc, [&](int j) { return pnew(P, j, beta); });
             vals[0] = AC::add(vals[0], AC::prod(pc, P.rscale * q));
           }
           P.q[i] = q;
@@ -1434,6 +1461,20 @@ template <typename R, int U>
 __device__ __forceinline__ void matvec_rows(const Params<R> &P, R beta, int i0, int stride,
                                             typename Acc<R>::T &acc) {
   typedef Acc<R> AC;
+  if constexpr (sizeof(R) == 8) {
+    if (P.nbc) {  // FP64 merged rows
+      for (int i = i0; i < P.N; i += stride) {
+        R q = 0;
+        if (!is_fixed(P, i)) {
+          const R pc = pnew(P, i, beta);
+          q = nb_row_any(P, i, P.diag[i] * pc, [&](int j) { return pnew(P, j, beta); });
+          acc = AC::add(acc, AC::prod(pc, P.rscale * q));
+        }
+        P.q[i] = q;
+      }
+      return;
+    }
+  }
   if constexpr (sizeof(R) == 4) {
     if (U >= 2 && P.nbc && P.Dn <= 6) {
       NbRow6 first;

@@ -269,11 +269,12 @@ struct pff_mesh {
   uint32_t *ecmp = nullptr;  // FP32, compact entry records: packed 16-bit neighbour offsets (D x N)
   float2 *ecf = nullptr;     // FP32, compact entry records: coefficients (D x N)
   int64_t span = 0;          // largest node-id difference within an element
-  uint32_t *nbo = nullptr;   // FP32 merged rows: neighbour offsets (Dn / 2 x N)
-  float *nbc = nullptr;      // FP32 merged rows: coefficients (Dn x N)
-  uint2 *nmap = nullptr;     // FP32 merged rows: incidence slot -> merged slots (8 bytes per row)
+  uint32_t *nbo = nullptr;   // merged rows: neighbour offsets (Dn / 2 x N)
+  void *nbc = nullptr;       // merged rows: coefficients (Dn x N, kernel precision)
+  uint2 *nmap = nullptr;     // merged rows: incidence slot -> merged slots (8 bytes per row)
   int32_t Dn = 0;            // merged row width (6 or 8; 0 = not used)
   float *diagf = nullptr;  // FP32: the damage rows' diagonals (N)
+  double *diagd = nullptr; // FP64 with merged rows: the same
   void *fe = nullptr;      // slot forces of the element-pass force schedule (3 Ne x R2)
   unsigned fg_grid = 0;    // grid of that schedule's node gather
   double *area_d = nullptr;
@@ -345,7 +346,7 @@ static void mesh_free(pff_mesh *m) {
   free_graph(m->mech_g);
   void *ptrs[] = {m->gcs, m->st_cta, m->st_rng, m->st_nrng, m->st_lrec, m->st_slot, m->cgv, m->cgp,
                   m->ptr, m->ent, m->ell, m->rec, m->drec, m->erec, m->ecmp, m->ecf, m->nbo, m->nbc, m->nmap,
-                  m->diagf, m->fe, m->fext, m->minv,
+                  m->diagf, m->diagd, m->fe, m->fext, m->minv,
                   m->area_d,
                   m->flags,
                   m->x, m->r, m->b, m->part, m->energy, m->wext, m->pz, m->q, m->dinv,
@@ -771,6 +772,36 @@ static pff_status build_stage(pff_mesh *m, const std::vector<int32_t> &ptr, int 
   return PFF_OK;
 }
 
+// Merged rows where every row has at most kNbMax distinct neighbours, from
+// the incidence offsets ofs (D x N packed words): the neighbour offsets and
+// slot maps, and the coefficient array in the kernel precision (zero until
+// a right-hand side writes it).  Leaves m->nbc null on wider meshes.
+template <typename R>
+static pff_status build_merged(pff_mesh *m, const uint32_t *ofs) {
+  if (m->D > kNbMax) return PFF_OK;
+  const unsigned gb = std::min<unsigned>(grid_for(m->N, 256), stride_cap());
+  int *cnt = nullptr;
+  PFF_TRY(dalloc(&cnt, 1));
+  cudaError_t e = cudaMemset(cnt, 0, sizeof(int));
+  if (e == cudaSuccess) {
+    k_nb_build<<<gb, 256>>>(ofs, (int)m->N, m->D, 0, cnt, nullptr, nullptr);
+    e = cudaGetLastError();
+  }
+  int mx = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&mx, cnt, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(cnt);
+  CUDA_TRY(e);
+  if (mx > kNbMax) return PFF_OK;
+  m->Dn = mx <= 6 ? 6 : kNbMax;
+  PFF_TRY(dalloc(&m->nbo, (size_t)(m->Dn / 2) * m->N));
+  PFF_TRY(dalloc(&m->nmap, (size_t)m->N));
+  PFF_TRY(dalloc((R **)&m->nbc, (size_t)m->Dn * m->N));
+  CUDA_TRY(cudaMemset(m->nbc, 0, (size_t)m->Dn * m->N * sizeof(R)));
+  k_nb_build<<<gb, 256>>>(ofs, (int)m->N, m->D, m->Dn, nullptr, m->nbo, m->nmap);
+  CUDA_TRY(cudaGetLastError());
+  return PFF_OK;
+}
+
 // Launch geometry.  Node-block kernels stage one value set per incidence
 // entry of a block of NB nodes in shared memory; NB is halved until the
 // largest block's entries fit in 40 KB.  Grids are the smaller of the
@@ -817,30 +848,24 @@ static pff_status configure(pff_mesh *m) {
     k_erec_ids<R><<<std::min<unsigned>(grid_for(m->N, 256), stride_cap()), 256>>>(
         (const ERec<R> *)m->rec, m->ell, (int)m->N, D, m->ecmp, m->erec);
     CUDA_TRY(cudaGetLastError());
-    if (m->ecmp && D <= kNbMax) {
-      // merged rows where every row has at most kNbMax distinct neighbours
-      const unsigned gb = std::min<unsigned>(grid_for(m->N, 256), stride_cap());
-      int *cnt = nullptr;
-      PFF_TRY(dalloc(&cnt, 1));
-      CUDA_TRY(cudaMemset(cnt, 0, sizeof(int)));
-      k_nb_build<<<gb, 256>>>(m->ecmp, (int)m->N, D, 0, cnt, nullptr, nullptr);
-      int mx = 0;
-      cudaError_t e = cudaGetLastError();
-      if (e == cudaSuccess) e = cudaMemcpy(&mx, cnt, sizeof(int), cudaMemcpyDeviceToHost);
-      cudaFree(cnt);
-      CUDA_TRY(e);
-      if (mx <= kNbMax) {
-        m->Dn = mx <= 6 ? 6 : kNbMax;
-        PFF_TRY(dalloc(&m->nbo, (size_t)(m->Dn / 2) * m->N));
-        PFF_TRY(dalloc(&m->nbc, (size_t)m->Dn * m->N));
-        PFF_TRY(dalloc(&m->nmap, (size_t)m->N));
-        CUDA_TRY(cudaMemset(m->nbc, 0, (size_t)m->Dn * m->N * sizeof(float)));
-        k_nb_build<<<gb, 256>>>(m->ecmp, (int)m->N, D, m->Dn, nullptr, m->nbo, m->nmap);
-        CUDA_TRY(cudaGetLastError());
-      }
-    }
+    if (m->ecmp) PFF_TRY(build_merged<R>(m, m->ecmp));
     PFF_TRY(dalloc(&m->diagf, (size_t)m->N));
     CUDA_TRY(cudaMemset(m->diagf, 0, (size_t)m->N * sizeof(float)));
+  }
+  if (sizeof(R) == 8 && !m->nbc && m->span < 32768 && D <= kNbMax) {
+    // FP64 merged rows: the incidence offsets in a scratch array first
+    uint32_t *ofs = nullptr;
+    PFF_TRY(dalloc(&ofs, (size_t)D * m->N));
+    k_erec_ids<R><<<std::min<unsigned>(grid_for(m->N, 256), stride_cap()), 256>>>(
+        (const ERec<R> *)m->rec, m->ell, (int)m->N, D, ofs, nullptr);
+    pff_status st = cudaGetLastError() == cudaSuccess ? PFF_OK : fail(PFF_ERR_CUDA, "merged rows: offsets");
+    if (st == PFF_OK) st = build_merged<R>(m, ofs);
+    cudaFree(ofs);
+    if (st != PFF_OK) return st;
+    if (m->nbc) {
+      PFF_TRY(dalloc(&m->diagd, (size_t)m->N));
+      CUDA_TRY(cudaMemset(m->diagd, 0, (size_t)m->N * sizeof(double)));
+    }
   }
   m->nblk = (int32_t)((m->N + NB - 1) / NB);
   if (!m->fe) PFF_TRY(dalloc((typename V<R>::T2 **)&m->fe, 3 * (size_t)m->Ne));
@@ -951,10 +976,10 @@ static Params<R> base_params(pff_mesh *m, const pff_options &o) {
   P.ecmp = m->ecmp;
   P.ecf = m->ecf;
   P.nbo = m->nbo;
-  P.nbc = m->nbc;
+  P.nbc = (R *)m->nbc;
   P.nmap = m->nmap;
   P.Dn = m->Dn;
-  P.diag = (R *)m->diagf;
+  P.diag = sizeof(R) == 4 ? (R *)m->diagf : (R *)m->diagd;
   P.flags = m->flags;
   P.st_cta = m->st_cta;
   P.st_rng = m->st_rng;
