@@ -865,6 +865,9 @@ static pff_status configure(pff_mesh *m) {
     if (m->nbc) {
       PFF_TRY(dalloc(&m->diagd, (size_t)m->N));
       CUDA_TRY(cudaMemset(m->diagd, 0, (size_t)m->N * sizeof(double)));
+      // the per-element damage records are no longer read
+      if (m->drec) CUDA_TRY(cudaFree(m->drec));
+      m->drec = nullptr;
     }
   }
   m->nblk = (int32_t)((m->N + NB - 1) / NB);
@@ -2734,7 +2737,7 @@ static pff_status build_reverse_graph(pff_mesh *m, pff_ckpt *c, AdjParams<R> A, 
   if (need_h) {
     st = add_generic(g, {}, (const void *)k_adj_load<R>, Ge, kThreads, 0, aa, &n_load);
     dep = {n_load};
-    if (st == PFF_OK && sizeof(R) == 8) {
+    if (st == PFF_OK && sizeof(R) == 8 && A.P.drec) {
       cudaGraphNode_t n_drec;
       st = add_generic(g, dep, (const void *)k_drec_build<R>, Ge, kThreads, 0, pa, &n_drec);
       dep = {n_drec};
