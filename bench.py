@@ -691,7 +691,7 @@ def run_ours(args):
                       per_step=[int(v) for v in iters] if args.steps <= 64 else None),
         kernel_ms=prof,
         schedule=dict(variant=sched_var, tune_ms=sched_ms,
-                      cg_loop=dict(kind=cg_kind, gathers=cg_U, ms_20_iterations=cg_ms)),
+                      cg_loop=dict(kind=cg_kind, gathers=cg_U, ms_30_iterations=cg_ms)),
     )
     if args.model == "AT2":
         line["subcycled"] = subcycled(pff, dev, args.config)

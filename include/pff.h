@@ -365,7 +365,7 @@ pff_status pff_mesh_schedule(const pff_mesh *mesh, int32_t *variant, float *tune
 /* The AT2 CG loop the autotuner chose on this mesh: *cg_kernel =
  * PFF_CG_PHASES, _PERSISTENT, _STAGED, _FUSED or _FUSED_STAGED (PFF_CG_AUTO
  * while not yet timed), the chosen persistent kernel's gathers in flight
- * (1..4, 0 for phases), and ms[5]: 20 iterations of the kernel-per-phase
+ * (1..4, 0 for phases), and ms[5]: 30 iterations of the kernel-per-phase
  * loop and of the best variant of each persistent kernel in that order (0
  * if not timed or not available).  Host outputs; each pointer nullable. */
 pff_status pff_mesh_cg_choice(const pff_mesh *mesh, int32_t *cg_kernel, int32_t *gathers, float *ms);

@@ -485,7 +485,7 @@ class Mesh:
     def cg_choice(self):
         """(AT2 CG loop in use: "auto" (not timed yet) / "phases" /
         "persistent" / "staged" / "fused" / "fused_staged", its gathers in
-        flight, and {loop: ms of 20 iterations of its best variant})."""
+        flight, and {loop: ms of 30 iterations of its best variant})."""
         k = C.c_int32()
         u = C.c_int32()
         ms = np.zeros(5, np.float32)

@@ -444,7 +444,8 @@ static const void *pers_fun(int U, bool st = false) {
 // count (at most 2 per iteration per CTA) must stay below 2^31; a plan that
 // cannot run falls back to the kernel-per-phase loop.
 enum { kFamPhases = 0, kFamPersistent, kFamStaged, kFamFused, kFamFusedStaged, kFamCount };
-constexpr int kTuneCgIters = 20;  // CG iterations per timed solve of the family autotuner
+constexpr int kTuneCgIters = 30;  // CG iterations per timed solve of the family autotuner
+constexpr int kTuneCgRounds = 8;  // timed rounds (the first warms up; the best of the rest counts)
 
 struct CgPlan {
   int fam = kFamPhases;
@@ -1327,7 +1328,7 @@ static pff_status autotune(pff_mesh *m, const pff_options &o, Params<R> P, bool 
     }
     float best[NK];
     for (int kind = 0; kind < NK; ++kind) best[kind] = 1e30f;
-    for (int r = 0; r < 4 && !skip && st == PFF_OK; ++r) {  // first round: warm-up
+    for (int r = 0; r < kTuneCgRounds && !skip && st == PFF_OK; ++r) {  // first round: warm-up
       for (int kind = 0; kind < NK && st == PFF_OK; ++kind) {
         if (!ge[kind]) continue;
         cudaEventRecord(e0, s);
