@@ -283,6 +283,8 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 6 : 1) kb_matvec(Params<
   if (reduce_plate<R, 1>(vals, P.part, B.tick + p, c.blk0, c.nblk, tot) && threadIdx.x == 0) matvec_finish(Q, tot);
 }
 
+constexpr int kbUpdatePairThreads = 128;  // FP32 kb_update: 128 threads x 2 rows = one 256-row block
+
 template <typename R>
 __global__ void __launch_bounds__(256) kb_update(Params<R> P, Batch B) {
   typedef typename Params<R>::R2 R2;
@@ -294,14 +296,37 @@ __global__ void __launch_bounds__(256) kb_update(Params<R> P, Batch B) {
   typename AC::T vals[3] = {AC::zero(), AC::zero(), AC::zero()};
   const R beta = sc_beta<R>(Q.sc), alpha = sc_alpha<R>(Q.sc);
   bool proj = false;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < P.N && !is_fixed(Q, i)) {
-    R2 pz = P.pz[i];
-    R x = P.x[i], r = P.r[i];
-    update_node(Q, i, alpha, beta, x, r, pz, P.q[i], P.dinv[i], vals, proj);
-    P.x[i] = x;
-    P.r[i] = r;
-    P.pz[i] = pz;
+  if constexpr (sizeof(R) == 4) {
+    // FP32: a block of kbUpdatePairThreads threads updates its 256 rows in
+    // pairs with vector loads and stores (the padded batch length is a
+    // multiple of 256, so every pair lies inside one plate's block)
+    const int j = blockIdx.x * blockDim.x + threadIdx.x, i = 2 * j;
+    if (i < P.N) {
+      const uchar2 f = reinterpret_cast<const uchar2 *>(P.flags)[j];
+      float2 xv = reinterpret_cast<const float2 *>(P.x)[j], rv = reinterpret_cast<const float2 *>(P.r)[j];
+      const float2 qv = reinterpret_cast<const float2 *>(P.q)[j], dv = reinterpret_cast<const float2 *>(P.dinv)[j];
+      const float4 pv = reinterpret_cast<const float4 *>(P.pz)[j];
+      R2 pz0, pz1;
+      pz0.x = pv.x; pz0.y = pv.y;
+      pz1.x = pv.z; pz1.y = pv.w;
+      const bool fix0 = (f.x & kNotch) || (Q.freef && !Q.freef[i]);
+      const bool fix1 = (f.y & kNotch) || (Q.freef && !Q.freef[i + 1]);
+      if (!fix0) update_node(Q, i, alpha, beta, xv.x, rv.x, pz0, qv.x, dv.x, vals, proj);
+      if (!fix1) update_node(Q, i + 1, alpha, beta, xv.y, rv.y, pz1, qv.y, dv.y, vals, proj);
+      reinterpret_cast<float2 *>(P.x)[j] = xv;
+      reinterpret_cast<float2 *>(P.r)[j] = rv;
+      reinterpret_cast<float4 *>(P.pz)[j] = make_float4(pz0.x, pz0.y, pz1.x, pz1.y);
+    }
+  } else {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < P.N && !is_fixed(Q, i)) {
+      R2 pz = P.pz[i];
+      R x = P.x[i], r = P.r[i];
+      update_node(Q, i, alpha, beta, x, r, pz, P.q[i], P.dinv[i], vals, proj);
+      P.x[i] = x;
+      P.r[i] = r;
+      P.pz[i] = pz;
+    }
   }
   __shared__ double tot[3];
   const PlateC &c = B.pc[p];

@@ -3123,7 +3123,9 @@ static pff_status batch_run_t(pff_batch *b, const pff_state *st, int64_t step0, 
     if (st == PFF_OK) st = add_generic(g, {n_f}, kb_fun<R>(KP_RHS, b->U), G, kThreads, 0, args, &n_rhs);
     if (st == PFF_OK) st = add_while(g, {n_rhs}, P.cond_inner, &body, &n_loop);
     if (st == PFF_OK) st = add_generic(body, {}, kb_fun<R>(KP_MATVEC, b->U), G, kThreads, 0, args, &n_mv);
-    if (st == PFF_OK) st = add_generic(body, {n_mv}, kb_fun<R>(KP_UPDATE, b->U), G, kThreads, 0, args, &n_up);
+    if (st == PFF_OK)
+      st = add_generic(body, {n_mv}, kb_fun<R>(KP_UPDATE, b->U), G, sizeof(R) == 4 ? kbUpdatePairThreads : kThreads,
+                       0, args, &n_up);
     if (st == PFF_OK) st = add_generic(g, {n_loop}, kb_fun<R>(KP_FINISH, b->U), G, kThreads, 0, args, &n_fin);
     if (st == PFF_OK) st = add_generic(g, {n_fin}, (const void *)kb_step_done, 1, 32, 0, sargs, &n_done);
     if (st != PFF_OK) {
