@@ -44,6 +44,9 @@ def parse():
     ap.add_argument("--prec", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--split", choices=["spectral", "amor"], default="spectral")
     ap.add_argument("--model", choices=["AT2", "AT1"], default="AT2")
+    ap.add_argument("--operator", choices=["element", "merged"], default="element",
+                    help="damage operator form (pff_mesh_set_operator): element-wise "
+                         "matrix-free (default) or rows merged per solve")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-batch", action="store_true",
@@ -60,8 +63,12 @@ def parse():
                     help="skip the quasi-static single-edge-notched tension measurement")
     ap.add_argument("--qs-only", action="store_true",
                     help="run only the quasi-static measurement and print its line")
-    ap.add_argument("--qs-increments", type=int, default=5,
-                    help="timed load increments of the quasi-static run")
+    ap.add_argument("--qs-increments", type=int, default=100,
+                    help="timed load increments of the quasi-static run (all 100 by default)")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the 1M-node volumetric-deviatoric and AT1 configurations")
+    ap.add_argument("--no-inversion", action="store_true",
+                    help="skip the gradient checks and L-BFGS recovery on the 500x500 plate")
     ap.add_argument("--loop", choices=["graph", "host"], default="graph",
                     help="host: launch every kernel from the host (ncu cannot profile "
                          "kernels inside graphs with conditional nodes)")
@@ -234,18 +241,35 @@ def merged_row_width(tri, N):
     return 6 if deg <= 6 else 8 if deg <= 8 else None
 
 
-def format_bytes_cg_iteration(N, Dn, family):
-    """Bytes one FP32 CG iteration moves in the merged-row format (flags,
-    diagonal, Dn/2 offset words and Dn coefficients per row, plus the
-    vectors; neighbour values are L2 hits).  Two-pass families (persistent,
-    phases): matvec (the row's own (p, z) pair read, q written) and vector
-    update (x, r, (p, z) read and written; q and 1/diag read, flags again).
-    Single-reduction family: one pass reading the row's (r, w, s, 1/diag)
-    record, p and x, writing the new record, p and x."""
-    rec = 1 + 4 + 2 * Dn + 4 * Dn
+def format_bytes_cg_iteration(N, form, width, family):
+    """Bytes one FP32 CG iteration reads and writes in the stored form of the
+    damage operator, per row (neighbour values are L2 hits):
+    element-wise (entry records): flags, diagonal and per incidence slot a
+    16-bit offset pair and two element coefficients (12 B, width = slots);
+    merged rows: flags, diagonal, width/2 offset words and width merged
+    coefficients.  Two-pass families (persistent, phases): matvec (the row's
+    own (p, z) pair read, q written) and vector update (x, r, (p, z) read
+    and written; q and 1/diag read, flags again).  Single-reduction family:
+    one pass reading the row's (r, w, s, 1/diag) record, p and x, writing
+    the new record, p and x."""
+    rec = 1 + 4 + (12 * width if form == "element" else 2 * width + 4 * width)
     if family == "fused":
         return N * (rec + 16 + 8 + 8 + 16)
     return N * ((rec + 8 + 4) + (1 + 8 + 8 + 16 + 4 + 4))
+
+
+def incidence_width(tri, N):
+    """Largest number of elements meeting at a node (the entry records'
+    slots per row)."""
+    return int(np.bincount(np.asarray(tri, dtype=np.int64).ravel(), minlength=N).max())
+
+
+def host_cores():
+    """Host CPU threads this process may run on (the box's core count)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count()
 
 
 # -------------------------------------------------------------- reference
@@ -273,7 +297,7 @@ def run_reference(args):
                 data="synthetic",
                 config=dict(workload=args.config, nodes=N, elements=m.Ne, split=args.split,
                             model=args.model, precision="fp64", cg_tol=1e-8),
-                cpu_baseline=dict(value=val, unit="node-updates/s", cores=1, kind="oracle",
+                cpu_baseline=dict(value=val, unit="node-updates/s", cores=1, host_cores=host_cores(), kind="oracle",
                                   sample=f"full {args.config} plate, steps {args.warmup}.."
                                          f"{args.warmup + args.steps - 1} after {args.warmup} untimed"),
                 e2e=dict(value=val, unit="node-updates/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0),
@@ -298,12 +322,12 @@ def cpu_baseline(args, budget_s=20.0):
         m.run(mat, st, 1, dt, n0=args.warmup + n)
         el += time.perf_counter() - t0
         n += 1
-    return dict(value=m.N * n / el, unit="node-updates/s", cores=1, kind="oracle",
+    return dict(value=m.N * n / el, unit="node-updates/s", cores=1, host_cores=host_cores(), kind="oracle",
                 sample=f"{args.config} full plate, steps {args.warmup}..{args.warmup + n - 1} "
-                       f"({n} steps, {el:.1f} s, single thread, FP64)")
+                       f"({n} steps, {el:.1f} s, single thread of {host_cores()} host threads, FP64)")
 
 
-def batched(pff, dev, steps=100, warmup=5):
+def batched(pff, dev, steps=500, warmup=5):
     """The batched workload: 64 independent plates drawn from SplitMix64
     seed 1 (200..700 x 80..280 cells, Gc in [1, 5] J/m^2, traction in
     [0.5, 2] MPa), FP32 with FP64-class reductions, all plates advanced by
@@ -468,14 +492,16 @@ def precision_check(pff, dev, config, steps=997, warmup=3):
                 speedup_fp32_over_fp64=out["fp64"]["ms_per_step"] / out["fp32"]["ms_per_step"])
 
 
-def quasistatic(pff, dev, increments=5, n=700, compare_increments=2):
+def quasistatic(pff, dev, increments=100, n=700, compare_increments=2):
     """Quasi-static single-edge-notched tension (Sec. 3.5): the 700 x 700
     unit square, the first `increments` of the 100 equal load increments to
-    7e-3 mm, each an inexact Newton solve (FP64 state and residual; tangent
-    CG in FP32 with double-word dots, i.e. FP32 matvecs and FP64-class inner
-    products) to |r| <= 1e-8 |f|, history and the damage solve (FP64, tol
-    1e-8).  The same increments with the tangent CG in FP64 are timed
-    beside it (compare_increments).  qs_run synchronises, so the events
+    7e-3 mm (all of them by default, with the reaction curve), each an
+    inexact Newton solve (FP64 state and residual; tangent CG in FP32 with
+    double-word dots, i.e. FP32 matvecs and FP64-class inner products) on
+    the element-wise tangent to |r| <= 1e-8 |f|, history and the damage
+    solve (FP64, tol 1e-8).  The first compare_increments are timed beside
+    it with the tangent CG in FP64, and with the tangent's rows merged per
+    Newton step (the assembled form).  qs_run synchronises, so the events
     bracket whole increments."""
     import torch
     c = S.sent(n)
@@ -483,11 +509,14 @@ def quasistatic(pff, dev, increments=5, n=700, compare_increments=2):
                du=c["du"], newton_tol=c["newton_tol"], damage_cg_tol=c["cg_tol"])
     opts = pff.options(cg_tol=c["cg_tol"], cg_max_it=100000)
     stream = torch.cuda.current_stream()
-    for label, krylov, k in (("fp32_krylov", "fp32", increments), ("fp64_krylov", "mesh", compare_increments)):
+    runs = (("fp32_krylov", "fp32", increments, "element"), ("fp64_krylov", "mesh", compare_increments, "element"),
+            ("fp32_krylov_merged", "fp32", compare_increments, "merged"))
+    for label, krylov, k, form in runs:
         if k <= 0:
             continue
         mesh = pff.Mesh.from_plate(c["mesh"], precision="fp64")
         mesh.set_material(c["material"], 0.5)
+        mesh.set_operator(form)
         out["nodes"], out["elements"] = mesh.N, mesh.Ne
         q = pff.qs_options(newton_tol=c["newton_tol"], krylov=krylov)
         st = mesh.new_state(device=dev)
@@ -500,13 +529,14 @@ def quasistatic(pff, dev, increments=5, n=700, compare_increments=2):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
         it = r["iters"]
-        out[label] = dict(increments=k, s_per_increment=ms / 1e3 / k, newton=it[:, 0].tolist(),
+        out[label] = dict(increments=k, operator=form, s_per_increment=ms / 1e3 / k, newton=it[:, 0].tolist(),
                           tangent_cg=it[:, 1].tolist(), damage_cg=it[:, 2].tolist(),
                           us_per_tangent_cg_iteration=ms * 1e3 / max(int(it[:, 1].sum()), 1),
                           reaction_N_per_m=r["reaction"].tolist(), d_max=float(st["d"].max()))
         del mesh, st
     if "fp32_krylov" in out and "fp64_krylov" in out:
         k = min(len(out["fp32_krylov"]["reaction_N_per_m"]), len(out["fp64_krylov"]["reaction_N_per_m"]))
+        out["top_displacement_m"] = [c["du"] * (j + 1) for j in range(len(out["fp32_krylov"]["reaction_N_per_m"]))]
         a = np.array(out["fp32_krylov"]["reaction_N_per_m"][:k])
         b = np.array(out["fp64_krylov"]["reaction_N_per_m"][:k])
         out["reaction_rel_diff_fp32_vs_fp64_krylov"] = float(np.max(np.abs(a - b) / np.abs(b)))
@@ -514,8 +544,8 @@ def quasistatic(pff, dev, increments=5, n=700, compare_increments=2):
 
 
 def mechanics_only(pff, dev, config, steps=200, warmup=10):
-    """The explicit step without the damage solve (SURVEY metric: node-updates
-    per second with and without it): the same plate and step graph with the
+    """The explicit step without the damage solve (node-updates per second
+    are reported with and without it): the same plate and step graph with the
     damage solve never due (damage_every beyond the run), so each step is
     the predictor, the force kernel with the history update and the
     corrector."""
@@ -537,6 +567,162 @@ def mechanics_only(pff, dev, config, steps=200, warmup=10):
     ms = e0.elapsed_time(e1)
     return dict(workload=config, steps=steps, value=mesh.N * steps / (ms / 1e3), unit="node-updates/s",
                 ms_per_step=ms / steps, status=int(mesh.sync_status()))
+
+
+def plate_rate(pff, dev, config, prec="fp32", split="spectral", model="AT2", form="element",
+               steps=50, warmup=5, profile=False):
+    """Node-updates/s of one plate configuration (CUDA events around `steps`
+    full staggered steps after `warmup` untimed ones), its CG iterations and,
+    with profile, the persistent CG launch's time per iteration."""
+    import torch
+    c = S.config(config, split=split, model=model)
+    mesh = pff.Mesh.from_plate(c["mesh"], precision=prec)
+    mesh.set_material(c["material"], c["cfl"])
+    mesh.set_operator(form)
+    opts = pff.options(cg_tol=c["cg_tol"], t_ramp=c["t_ramp"])
+    st = mesh.new_state(device=dev)
+    log = torch.zeros(warmup + steps, 2, dtype=torch.int32, device=dev)
+    mesh.run(st, warmup, opts=opts, iters_log=log[:warmup])
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    mesh.run(st, steps, step0=warmup, opts=opts, iters_log=log[warmup:])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    it = log[warmup:].cpu().numpy()
+    out = dict(workload=config, precision=prec, split=split, model=model, operator=form, steps=steps,
+               value=mesh.N * steps / (ms / 1e3), unit="node-updates/s", ms_per_step=ms / steps,
+               cg_iters_mean=float(it[:, 0].mean()), restarts_mean=float(it[:, 1].mean()),
+               status=int(mesh.sync_status()), cg_loop=mesh.cg_choice()[0])
+    if profile:
+        prof = mesh.profile_kernels(st, reps=5, opts=opts)
+        if prof["cg_loop"] > 0:
+            out["cg_us_per_iteration"] = 1e3 * prof["cg_loop"] / max(prof["cg_loop_iters"], 1)
+        out["kernel_ms"] = prof
+    return out
+
+
+def variants_1m(pff, dev, config, steps=30):
+    """The 1M-node plate's other configurations: the volumetric-deviatoric
+    split (Eq. amor_split) in FP32 and FP64, and AT1 with that split and the
+    bound-projected CG (Sec. 2.4), FP32 and FP64."""
+    out = {}
+    for prec, split, model in (("fp32", "amor", "AT2"), ("fp64", "amor", "AT2"),
+                               ("fp32", "amor", "AT1"), ("fp64", "amor", "AT1")):
+        out[f"{model}_{split}_{prec}"] = plate_rate(pff, dev, config, prec, split, model, steps=steps)
+    return out
+
+
+def inversion(pff, dev, steps=300, gcs=(2.0, 2.5, 3.5), gc_star=3.0, max_states=8):
+    """Toughness inversion on the differentiation plate (Sec. 4.1, Eq.
+    inversion_loss): 500 x 500 cells, FP32 kernels with FP64-class
+    reductions, 300 steps, target d* from Gc* = 3 J/m^2.  At each Gc of
+    `gcs`: dL/dGc from the adjoint (full tape) beside a central difference of
+    the GPU forward with delta = 1e-4 Gc.  Then L-BFGS on log Gc from Gc =
+    2.0 (strong-Wolfe line search, one accepted state per step), each
+    closure a forward with checkpoints every 25 steps and the adjoint."""
+    import torch
+    from paper_2606_23458_b300 import inverse
+    c = S.config("plate_500x500")
+    mat = c["material"]
+    mesh = pff.Mesh.from_plate(c["mesh"], precision="fp32")
+    mesh.set_material(mat, c["cfl"])
+    opts = pff.options(cg_tol=c["cg_tol"], t_ramp=c["t_ramp"])
+    f64 = torch.float64
+    dstar = inverse.final_damage(torch.tensor(gc_star, dtype=f64), mesh, mat, steps, 0, opts).detach()
+
+    def loss_at(gc, grad):
+        g = torch.tensor(gc, dtype=f64, requires_grad=grad)
+        L = inverse.mse_loss(inverse.final_damage(g, mesh, mat, steps, 0, opts), dstar)
+        if grad:
+            L.backward()
+            return float(L), float(g.grad)
+        return float(L), None
+
+    grads = []
+    for gc in gcs:
+        L, g = loss_at(gc, True)
+        h = 1e-4 * gc
+        fd = (loss_at(gc + h, False)[0] - loss_at(gc - h, False)[0]) / (2 * h)
+        grads.append(dict(Gc=gc, loss=L, dL_dGc_adjoint=g, dL_dGc_central_fd=fd,
+                          rel_diff=abs(g - fd) / abs(fd) if fd else None))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    gc, hist = inverse.recover_gc(mesh, mat, steps, dstar, 2.0, every=25, opts=opts, max_states=max_states)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    errs = [abs(g - gc_star) / gc_star for g in hist["states"]]
+    first = next((k + 1 for k, e in enumerate(errs) if e < 1e-3), None)
+    return dict(workload="plate_500x500", nodes=mesh.N, steps=steps, gc_star=gc_star, gradients=grads,
+                lbfgs=dict(gc0=2.0, states=hist["states"], rel_err=errs, accepted_states_to_1e_3=first,
+                           closure_evaluations=len(hist["evals"]), final_gc=gc,
+                           final_rel_err=abs(gc - gc_star) / gc_star, wall_s=el, checkpoint_every=25))
+
+
+def kernel_rooflines(prof, iters_mean, N, Ne, prec, form, width, peak, peak_kind):
+    """Roofline of the dominant kernel of a step and the HBM fractions of the
+    streaming kernels, from pff_profile_kernels' live launch times (CUDA
+    events on the launching stream, L2 flushed before every launch).
+
+    achieved = the method's algorithmic bytes per launch / launch time.  For
+    the CG loop (one persistent launch per solve) that is the matrix-free
+    count of one iteration (element pass 40 B per element, vectors 56 B per
+    node) times the launch's iterations; its working set (operator records
+    and vectors, about 100 MB on the 1M-node plate) stays in the 126 MB L2
+    across iterations, so `traffic` (ncu DRAM bytes) sits far below those
+    bytes and `dram_frac` is the fraction of HBM bandwidth the loop really
+    draws: the loop is bound by L2 latency and grid synchronisation, not by
+    HBM.  The streaming kernels (force with history and corrector, damage
+    right-hand side, predictor, clamp) read and write each element and node
+    once from HBM; their fractions are the HBM roofline figures proper."""
+    ab = algorithmic_bytes(N, Ne, prec)
+    per_step = {k: prof[k] for k in ("predict", "force", "rhs", "finish")}
+    ms_launch = {k: prof[k] for k in per_step}
+    bytes_launch = {k: ab[k] for k in per_step}
+    if prof["cg_loop"] > 0:  # the solve's CG loop is one persistent launch
+        per_step["cg_loop"] = prof["cg_loop"] * iters_mean / max(prof["cg_loop_iters"], 1)
+        ms_launch["cg_loop"] = prof["cg_loop"]
+        bytes_launch["cg_loop"] = ab["cg_iteration"] * prof["cg_loop_iters"]
+    else:
+        for k in ("matvec", "update"):
+            per_step[k] = prof[k] * iters_mean
+            ms_launch[k] = prof[k]
+            bytes_launch[k] = ab[k]
+    dom = max(per_step, key=per_step.get)
+    achieved = bytes_launch[dom] / (ms_launch[dom] * 1e-3) / 1e9
+    kname = {"matvec": "k_cg_matvec_nc", "update": "k_cg_update", "force": "k_force_nc",
+             "rhs": "k_dmg_rhs_nc", "cg_loop": "k_cg_"}.get(dom, dom)
+    traffic = None
+    if prec == "fp32":
+        if dom == "cg_loop":
+            per_iter = ncu_traffic(kname, f"ncu_full_cg_loop_plate_1000x1000_fp32_{form}.md")
+            traffic = per_iter * prof["cg_loop_iters"] if per_iter else None
+        else:
+            traffic = ncu_traffic(kname)
+    roofline = dict(bound="hbm", kernel=dom if dom != "cg_loop" else f"cg_loop ({prof['cg_loop_family']})",
+                    operator=form, achieved=achieved, peak=peak, unit="GB/s", frac=achieved / peak,
+                    peak_kind=peak_kind, traffic=traffic, bytes_per_launch=bytes_launch[dom],
+                    ms_per_launch=ms_launch[dom],
+                    cg_iterations_per_launch=prof["cg_loop_iters"] if dom == "cg_loop" else None)
+    if traffic:
+        roofline["dram_frac"] = traffic / (ms_launch[dom] * 1e-3) / 1e9 / peak
+    if dom == "cg_loop" and width and prec == "fp32" and prof["cg_loop_family"] in ("persistent", "phases", "fused"):
+        fb = format_bytes_cg_iteration(N, form, width, prof["cg_loop_family"]) * prof["cg_loop_iters"]
+        roofline["format"] = dict(name=("element-wise entry records" if form == "element" else "merged rows")
+                                  + f", width {width}", bytes_per_launch=fb,
+                                  achieved=fb / (ms_launch[dom] * 1e-3) / 1e9,
+                                  frac=fb / (ms_launch[dom] * 1e-3) / 1e9 / peak)
+        roofline["note"] = ("bytes_per_launch: the method's matrix-free count; format: the bytes the stored "
+                            "operator records and vectors move; the loop's working set stays in L2, so its "
+                            "DRAM traffic (traffic, dram_frac) is a small share of either: L2-latency and "
+                            "grid-synchronisation bound; the HBM roofline figures are the streaming kernels'")
+    streaming = {k: dict(bytes=ab[k], ms=prof[k], gbs=ab[k] / (prof[k] * 1e-3) / 1e9,
+                         frac=ab[k] / (prof[k] * 1e-3) / 1e9 / peak)
+                 for k in ("predict", "force", "rhs", "finish") if prof[k] > 0}
+    return roofline, streaming
 
 
 # ------------------------------------------------------------------- ours
@@ -562,6 +748,7 @@ def run_ours(args):
     c = S.config(args.config, split=args.split, model=args.model)
     mesh = pff.Mesh.from_plate(c["mesh"], precision=args.prec)
     dt = mesh.set_material(c["material"], c["cfl"])
+    mesh.set_operator(args.operator)
     N, Ne = mesh.N, mesh.Ne
     opts = pff.options(cg_tol=c["cg_tol"], t_ramp=c["t_ramp"],
                        loop_mode=pff.PFF_LOOP_HOST if args.loop == "host" else pff.PFF_LOOP_GRAPH,
@@ -631,46 +818,12 @@ def run_ours(args):
         if ws > 1:
             torch.distributed.destroy_process_group()
         return
-    ab = algorithmic_bytes(N, Ne, args.prec)
-    per_step = {k: prof[k] for k in ("predict", "force", "rhs", "finish")}
-    ms_launch = {k: prof[k] for k in per_step}
-    bytes_launch = {k: ab[k] for k in per_step}
-    if prof["cg_loop"] > 0:  # the solve's CG loop is one persistent launch
-        per_step["cg_loop"] = prof["cg_loop"] * iters.mean() / max(prof["cg_loop_iters"], 1)
-        ms_launch["cg_loop"] = prof["cg_loop"]
-        bytes_launch["cg_loop"] = ab["cg_iteration"] * prof["cg_loop_iters"]
-    else:
-        for k in ("matvec", "update"):
-            per_step[k] = prof[k] * iters.mean()
-            ms_launch[k] = prof[k]
-            bytes_launch[k] = ab[k]
-    dom = max(per_step, key=per_step.get)
     peak, peak_kind = peaks()
-    achieved = bytes_launch[dom] / (ms_launch[dom] * 1e-3) / 1e9
-    kname = {"matvec": "k_cg_matvec_nc", "update": "k_cg_update", "force": "k_force_nc",
-             "rhs": "k_dmg_rhs_nc", "cg_loop": "k_cg_"}.get(dom, dom)
-    traffic = None
-    if args.prec == "fp32":
-        if dom == "cg_loop":
-            per_iter = ncu_traffic(kname, "ncu_full_cg_loop_plate_1000x1000_fp32.md")
-            traffic = per_iter * prof["cg_loop_iters"] if per_iter else None
-        else:
-            traffic = ncu_traffic(kname)
-    roofline = dict(bound="hbm", kernel=dom if dom != "cg_loop" else f"cg_loop ({prof['cg_loop_family']})",
-                    achieved=achieved, peak=peak, unit="GB/s", frac=achieved / peak, peak_kind=peak_kind,
-                    traffic=traffic, bytes_per_launch=bytes_launch[dom], ms_per_launch=ms_launch[dom],
-                    cg_iterations_per_launch=prof["cg_loop_iters"] if dom == "cg_loop" else None)
-    Dn = merged_row_width(c["mesh"]["tri"], N) if args.prec == "fp32" else None
-    if dom == "cg_loop" and Dn and prof["cg_loop_family"] in ("persistent", "phases", "fused"):
-        # the same launch against the bytes its stored operator format moves
-        # (merged rows: fewer than the matrix-free element pass above)
-        fb = format_bytes_cg_iteration(N, Dn, prof["cg_loop_family"]) * prof["cg_loop_iters"]
-        roofline["format"] = dict(name=f"merged rows, width {Dn}", bytes_per_launch=fb,
-                                  achieved=fb / (ms_launch[dom] * 1e-3) / 1e9,
-                                  frac=fb / (ms_launch[dom] * 1e-3) / 1e9 / peak)
-        roofline["note"] = ("bytes_per_launch is the method's matrix-free count; the stored merged-row "
-                            "operator moves fewer (format), and the solve's working set stays in L2 "
-                            "(traffic: ncu DRAM bytes)")
+    roofline, streaming = kernel_rooflines(prof, iters.mean(), N, Ne, args.prec, args.operator,
+                                           incidence_width(c["mesh"]["tri"], N)
+                                           if args.operator == "element" else
+                                           merged_row_width(c["mesh"]["tri"], N), peak, peak_kind)
+    ab = algorithmic_bytes(N, Ne, args.prec)
     step_bytes = sum(ab[k] for k in ("predict", "force", "rhs", "finish")) + iters.mean() * ab["cg_iteration"]
     line = dict(
         metric=METRIC, value=value, unit="node-updates/s", n_gpus=ws, steps=args.steps,
@@ -681,8 +834,12 @@ def run_ours(args):
                     precision="FP32 kernels, FP64 reductions/history" if args.prec == "fp32" else "FP64",
                     cg_tol=c["cg_tol"], cg_tol_fp32_floor=2.0 ** -22 if args.prec == "fp32" else None,
                     dt=dt, parallelism=f"replicas x{ws}", loop=args.loop,
-                    l2="inputs larger than L2 (working set > 126 MB), no flush"),
+                    l2=("no flush between steps: a step streams about 0.4 GB of element and node data "
+                        "through HBM (inputs larger than the 126 MB L2); the damage solve's ~100 MB "
+                        "working set stays L2-resident within a step"),
+                    operator=args.operator),
         roofline=roofline,
+        streaming_kernels=streaming,
         step_roofline=dict(bytes=step_bytes, frac=step_bytes / (t_max / args.steps * 1e-3) / 1e9 / peak),
         e2e=dict(value=ws * N * args.e2e_steps / (e2e_ms / 1e3), unit="node-updates/s",
                  h2d_bytes_per_step=bytes_state, d2h_bytes_per_step=bytes_state),
@@ -693,6 +850,28 @@ def run_ours(args):
         schedule=dict(variant=sched_var, tune_ms=sched_ms,
                       cg_loop=dict(kind=cg_kind, gathers=cg_U, ms_30_iterations=cg_ms)),
     )
+    other = "merged" if args.operator == "element" else "element"
+    line["operator_forms"] = {
+        args.operator: dict(value=value, ms_per_step=t_max / args.steps, cg_iters_mean=float(iters.mean()),
+                            cg_us_per_iteration=(1e3 * prof["cg_loop"] / max(prof["cg_loop_iters"], 1)
+                                                 if prof["cg_loop"] > 0 else None),
+                            roofline=roofline),
+        other: plate_rate(pff, dev, args.config, args.prec, args.split, args.model, other,
+                          steps=min(args.steps, 100), profile=True),
+        "labels": dict(element="matrix-free: every CG product applies each element's own coefficients "
+                               "(Eq. matrix_free_fe_operator); the benchmarked default",
+                       merged="assembled per solve: the two elements' coefficients of each edge summed "
+                              "into one per neighbour by the right-hand side (pff_mesh_set_operator)"),
+    }
+    if other in line["operator_forms"] and line["operator_forms"][other].get("kernel_ms"):
+        pk, pk_kind = peaks()
+        line["operator_forms"][other]["roofline"] = kernel_rooflines(
+            line["operator_forms"][other].pop("kernel_ms"), line["operator_forms"][other]["cg_iters_mean"],
+            N, Ne, args.prec, other,
+            merged_row_width(c["mesh"]["tri"], N) if other == "merged" else incidence_width(c["mesh"]["tri"], N),
+            pk, pk_kind)[0]
+    if args.model == "AT2" and args.split == "spectral" and not args.no_variants:
+        line["variants_1m"] = variants_1m(pff, dev, args.config)
     if args.model == "AT2":
         line["subcycled"] = subcycled(pff, dev, args.config)
     line["mechanics_only"] = mechanics_only(pff, dev, args.config)
@@ -704,6 +883,8 @@ def run_ours(args):
         line["quasistatic"] = quasistatic(pff, dev, args.qs_increments)
     if not args.no_precision:
         line["precision"] = precision_check(pff, dev, args.config)
+    if not args.no_inversion:
+        line["inversion"] = inversion(pff, dev)
     if not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline(args)
     print(json.dumps(line), flush=True)

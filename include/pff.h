@@ -209,6 +209,36 @@ pff_status pff_qs_run(pff_mesh *mesh, const pff_state *state, const uint8_t *bc,
  * PFF_ERR_ARG: null mesh, no material yet, a non-positive value. */
 pff_status pff_mesh_set_gc_field(pff_mesh *mesh, const double *gc);
 
+/* Form in which the damage operator A = sum_e [kappa_e K^e + c_e M^e]
+ * (Eqs. damage_pde_at2 / damage_pde_at1 with the consistent mass, Sec. 2.4)
+ * is applied by every CG product of the damage solve (and of its adjoint,
+ * and by the quasi-static tangent CG for the element tangents):
+ *  PFF_OP_ELEMENT (default): matrix-free in the sense of Eq.
+ *    matrix_free_fe_operator -- each product gathers p on every element
+ *    and applies that element's own coefficients; no two elements'
+ *    coupling coefficients are ever added together.  The coefficients of
+ *    an element (they depend on H, which is fixed while a solve runs) are
+ *    evaluated once per solve by the right-hand-side pass: FP32 meshes keep
+ *    them per incidence entry (row a of element e: the coefficients of p_b
+ *    and p_c with 16-bit neighbour offsets, 12 bytes; the row's own terms
+ *    sum_e A^e_aa p_a are applied as diag_a p_a through the Jacobi diagonal
+ *    the preconditioner needs anyway), FP64 meshes one 64-byte record per
+ *    element (ids, three stiffness weights, mass) from which every product
+ *    evaluates whole element rows.
+ *  PFF_OP_MERGED: the two elements' coefficients of each mesh edge summed
+ *    once per solve into one coefficient per distinct neighbour -- the
+ *    solve's sparse operator assembled in an ELL layout and thrown away
+ *    after the solve (fewer bytes per product; FP32 roundings differ).
+ *    Only on meshes whose rows have at most 8 distinct neighbours and whose
+ *    elements span fewer than 2^15 node ids (PFF_ERR_ARG otherwise).
+ * Changing the form drops the mesh's step graphs and its CG autotuning
+ * (re-timed on the next solve).  Host-only; no device work. */
+enum { PFF_OP_ELEMENT = 0, PFF_OP_MERGED = 1 };
+pff_status pff_mesh_set_operator(pff_mesh *mesh, int32_t form);
+/* The form in use and whether PFF_OP_MERGED is available (host outputs,
+ * each nullable). */
+pff_status pff_mesh_get_operator(const pff_mesh *mesh, int32_t *form, int32_t *merged_available);
+
 /* Sets the material: the plane model's Lame constants (Sec. 2.1), lumped mass
  * m_i = rho sum A_e / 3 and the stable step dt = cfl * h_min / c_p with
  * c_p = sqrt((lambda + 2 mu) / rho) (velocity-Verlet paragraph, Sec. 2.3).
@@ -301,8 +331,10 @@ pff_status pff_backward_field(pff_mesh *mesh, pff_ckpt *ckpt, const void *dL_dd,
 
 /* Batches: many independent plates (uneven sizes, Gc, l0, loads and time
  * steps) advanced together, one CUDA graph launch per step for all plates,
- * with per-plate CG reductions and convergence (a converged plate's blocks
- * skip the remaining CG iterations).  Plates share E, nu, rho, eta, the split
+ * with per-plate CG reductions and convergence (the CG loop of all plates
+ * either as kernels per phase, a converged plate's blocks skipping the
+ * remaining iterations, or as one cooperative launch with a group of CTAs
+ * per plate; see pff_batch_tuning).  Plates share E, nu, rho, eta, the split
  * and the AT2 model.  The caller owns the concatenated state of
  * pff_batch_size's N nodes / Ne elements: plate p's nodes start at node0
  * (pff_batch_plate_info; a multiple of 256, padding nodes between plates
@@ -326,6 +358,23 @@ typedef struct {
 pff_status pff_batch_create(int32_t nplates, const pff_plate *plates, int32_t precision,
                             double cfl, pff_batch **out);
 void pff_batch_destroy(pff_batch *batch);
+/* The batch's loop configuration (host outputs, each nullable):
+ * choice[6] = gathers in flight of the force kernel, of the right-hand side,
+ * the CG loop form (PFF_CG_PHASES: a matvec and an update kernel per
+ * iteration for all plates in a device loop; PFF_CG_PERSISTENT: one
+ * cooperative launch in which each plate's group of CTAs iterates its own
+ * plate to its own stop), that loop's gathers in flight, 1 once the
+ * autotuner has run, and the persistent launch's CTAs (0: unavailable).
+ * ms[3 x 8]: the autotuner's timings -- force U = 1..4, right-hand side
+ * U = 1..4, a right-hand side plus a whole solve for the phases loop with
+ * U = 1..4 and the persistent loop with U = 2..4 (0 where not timed).  The
+ * autotuner runs at the first pff_batch_run unless pff_options.variant
+ * fixes the gathers; pff_options.cg_kernel PFF_CG_PHASES or
+ * PFF_CG_PERSISTENT forces the loop form. */
+pff_status pff_batch_tuning(const pff_batch *batch, int32_t *choice, float *ms);
+/* pff_mesh_set_operator for every plate of the batch (the same forms and
+ * conditions; PFF_OP_ELEMENT by default); the batch is re-tuned. */
+pff_status pff_batch_set_operator(pff_batch *batch, int32_t form);
 pff_status pff_batch_size(const pff_batch *batch, int64_t *N, int64_t *Ne);
 pff_status pff_batch_plate_info(const pff_batch *batch, int32_t plate, int64_t *node0,
                                 int64_t *N, int64_t *elem0, int64_t *Ne, double *dt);
@@ -389,7 +438,11 @@ pff_status pff_mesh_cg_choice(const pff_mesh *mesh, int32_t *cg_kernel, int32_t 
  *    call before any stream capture.
  *  - Every call shares the one array and leaves its workspace there; calls
  *    that overlap on the GPU (unordered streams, other host threads) race
- *    and corrupt each other's results.  Order them on one stream.
+ *    and corrupt each other's results.  Like every damage solve, it also
+ *    writes the mesh's own per-solve operator records and Jacobi diagonal
+ *    (allocated with the mesh), so it races as well with any other solve
+ *    on the same mesh (pff_damage_solve, pff_run, ...) that overlaps it on
+ *    the GPU.  Order them on one stream.
  *  - The CG loop is host-polled (no CUDA graph) and uses the mesh's current
  *    gather schedule (no autotuning).  Same arguments, results and status
  *    codes as pff_damage_solve; synchronises the stream. */
@@ -399,7 +452,6 @@ pff_status pff_damage_solve_noalloc(pff_mesh *mesh, const double *H,
                                     double *relres, int32_t *restarts,
                                     pff_stream stream);
 
-/* Message of the last failing call on this host thread. */
 /* Pre-simulation check of the damage subcycling factor (Sec. 2.4): the
  * damage front moves at most at about 0.6 c_R while the explicit step is set
  * by the dilatational wave speed c_p, so N_max = floor(c_p / (0.6 c_R)).
@@ -410,6 +462,7 @@ pff_status pff_damage_solve_noalloc(pff_mesh *mesh, const double *H,
  * (-1, 0.5), unknown plane). */
 pff_status pff_subcycling_limit(const pff_material *mat, double *ratio, int32_t *n_max);
 
+/* Message of the last failing call on this host thread. */
 const char *pff_last_error(void);
 const char *pff_version(void);
 

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libpff.so")
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"libpff.so is not built ({LIB_PATH}); run "
-                      "`python -m paper_2606_23458_b300.build` or __graft_entry__.build()")
+                      "`python paper_2606_23458_b300/build.py` or __graft_entry__.build()")
 
 _lib = C.CDLL(LIB_PATH)
 
@@ -35,6 +35,8 @@ CG_KINDS = {PFF_CG_AUTO: "auto", PFF_CG_PHASES: "phases", PFF_CG_PERSISTENT: "pe
 MODELS = {"AT1": PFF_AT1, "AT2": PFF_AT2}
 SPLITS = {"spectral": PFF_SPLIT_SPECTRAL, "amor": PFF_SPLIT_AMOR, "iso": PFF_SPLIT_ISO}
 PFF_PLANE_STRAIN, PFF_PLANE_STRESS = 0, 1
+PFF_OP_ELEMENT, PFF_OP_MERGED = 0, 1
+OPERATORS = {"element": PFF_OP_ELEMENT, "merged": PFF_OP_MERGED}
 PFF_QS_KRYLOV_FP32, PFF_QS_KRYLOV_MESH = 0, 1
 PLANES = {"strain": PFF_PLANE_STRAIN, "stress": PFF_PLANE_STRESS}
 PRECISIONS = {"fp64": PFF_FP64, "fp32": PFF_FP32_MIXED}
@@ -117,6 +119,10 @@ _sig = {
     "pff_batch_plate_info": [_P, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                              C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_double)],
     "pff_batch_run": [_P, C.POINTER(pff_state), C.c_int64, C.c_int64, C.POINTER(pff_options), _P, _P],
+    "pff_mesh_set_operator": [_P, C.c_int32],
+    "pff_mesh_get_operator": [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int32)],
+    "pff_batch_set_operator": [_P, C.c_int32],
+    "pff_batch_tuning": [_P, _P, _P],
     "pff_damage_solve_noalloc": [_P, _P, _P, _P, C.POINTER(pff_options), C.POINTER(C.c_int32),
                                  C.POINTER(C.c_double), C.POINTER(C.c_int32), _P],
 }
@@ -257,6 +263,24 @@ class Batch:
         e0, e1 = inf["elem0"], inf["elem0"] + inf["Ne"]
         return dict(u=st["u"][n0:n1], v=st["v"][n0:n1], a=st["a"][n0:n1], d=st["d"][n0:n1],
                     H=st["H"][e0:e1])
+
+    def tuning(self):
+        """The loop configuration (pff_batch_tuning): gathers in flight of the
+        force, right-hand side and CG kernels, the CG loop form ("phases" or
+        "persistent"), whether the autotuner has run, the persistent launch's
+        CTAs, and the autotuner's timings in ms."""
+        ch = np.zeros(6, np.int32)
+        ms = np.zeros((3, 8), np.float32)
+        _check(_lib.pff_batch_tuning(self._h, _hp(ch), _hp(ms)))
+        return dict(force_U=int(ch[0]), rhs_U=int(ch[1]), cg=CG_KINDS.get(int(ch[2]), str(int(ch[2]))),
+                    cg_U=int(ch[3]), tuned=bool(ch[4]), persistent_ctas=int(ch[5]),
+                    ms=dict(force=[float(x) for x in ms[0, :4]], rhs=[float(x) for x in ms[1, :4]],
+                            cg_phases=[float(x) for x in ms[2, :4]], cg_persistent=[float(x) for x in ms[2, 4:7]]))
+
+    def set_operator(self, form):
+        """Damage operator form of every plate: "element" (matrix-free, the
+        default) or "merged" (pff_batch_set_operator)."""
+        _check(_lib.pff_batch_set_operator(self._h, OPERATORS[form]))
 
     def run(self, st, nsteps, step0=0, opts=None, iters_log=None, stream=None):
         s = pff_state(st["u"].data_ptr(), st["v"].data_ptr(), st["a"].data_ptr(), st["d"].data_ptr(),
@@ -459,6 +483,17 @@ class Mesh:
         _check(_lib.pff_qs_run(self._h, C.byref(s), _hp(b), int(incr0), int(nincr), float(du),
                                C.byref(q), C.byref(o), _hp(reac), _hp(it), _stream(stream)))
         return dict(reaction=reac, iters=it)
+
+    def set_operator(self, form):
+        """Damage operator form: "element" (matrix-free, the default) or
+        "merged" (rows assembled per solve; pff_mesh_set_operator)."""
+        _check(_lib.pff_mesh_set_operator(self._h, OPERATORS[form]))
+
+    def operator(self):
+        """(form name, whether "merged" is available on this mesh)."""
+        f = C.c_int32(); a = C.c_int32()
+        _check(_lib.pff_mesh_get_operator(self._h, C.byref(f), C.byref(a)))
+        return {v: k for k, v in OPERATORS.items()}[f.value], bool(a.value)
 
     def set_gc_field(self, gc):
         """Per-element toughness Gc_e (array of Ne, host), or None for the

@@ -13,6 +13,8 @@
 
 namespace pff {
 
+constexpr int kThreadsBatch = 256;  // nodes per node block (plates start on block boundaries)
+
 // Per-plate coefficients (device array, one per plate).
 struct PlateC {
   double dt;        // the plate's stable step
@@ -20,7 +22,7 @@ struct PlateC {
   float kappa, cbase, wbase, rscale;  // damage coefficients (FP32 path)
   double kappa_d, cbase_d, wbase_d, rscale_d;
   int32_t blk0, nblk;  // first node block and number of node blocks
-  int32_t pad0, pad1;
+  int32_t cta0, ncta;  // the plate's CTA group in the persistent CG launch
 };
 
 struct Batch {
@@ -34,6 +36,7 @@ struct Batch {
   unsigned int *gtick;        // plate ticket for the global loop decision
   int32_t *nactive;           // plates still iterating
   int32_t *iters_log;         // device, nsteps x nplates (nullable)
+  const int2 *cta_plate;      // persistent CG: CTA -> (plate, rank in the plate's group)
 };
 
 template <typename R>
@@ -360,6 +363,129 @@ __global__ void __launch_bounds__(256) kb_finish(Params<R> P, Batch B) {
       if (P.status_word && S.status) atomicMax(P.status_word, S.status);
       if (B.iters_log) B.iters_log[n * B.nplates + q] = S.iters;
     }
+  }
+}
+
+// ------------------------------------------------ per-plate persistent CG
+//
+// Every plate's damage solve in one cooperative launch (a full wave of
+// co-resident CTAs).  The CTAs are split into one group per plate, sized in
+// proportion to the plate's rows (at least one each; cta0, ncta of
+// PlateC).  A group runs k_cg_persistent's iteration on its own plate only:
+// its rows are the plate's node blocks, its two all-reduces per iteration
+// are among its own CTAs (the plate's barrier counter, the plate's slice of
+// the partials, the group's rank order), it takes its plate's stop decision
+// and leaves when its plate has converged -- the others go on.  Every wait
+// is bounded as in the single-plate loop; a group that gives up marks only
+// its plate (status timeout).  Same arithmetic per plate as the
+// kernel-per-phase batch loop except for the grouping of the dot products'
+// partial sums.
+template <typename R, int U>
+__global__ void __launch_bounds__(pers_threads(U, false), kPersMinBlocks) kb_cg_persistent(Params<R> P, Batch B) {
+  typedef Acc<R> AC;
+  const int2 gp = B.cta_plate[blockIdx.x];
+  const int p = gp.x, rank = gp.y;
+  Params<R> Q = P;
+  plate_apply(Q, B, p);
+  const PlateC &c = B.pc[p];
+  SolveScalars *S = Q.sc;
+  __shared__ typename AC::T sh[pers_threads(U, false) / 32][2];
+  __shared__ PersShared<R> z;
+  if (S->done) return;  // set-up found b_eff = 0 or r_0 already small
+  if (threadIdx.x == 0) {
+    z.rho = S->rho;
+    z.beta = S->beta;
+    z.alpha = S->alpha;
+    z.rr = S->rr;
+    z.pq = S->pq;
+    z.bn = S->bn;
+    z.iters = S->iters;
+    z.status = kStOk;
+    z.done = 0;
+    z.ok = 1;
+    z.coef[1] = sizeof(R) == 4 ? (R)S->beta_f : (R)S->beta;
+  }
+  __syncthreads();
+  const unsigned int nb = (unsigned)c.ncta;
+  const int n0 = c.blk0 * kThreadsBatch;
+  const int n1 = min(P.N, (c.blk0 + c.nblk) * kThreadsBatch);
+  const int T = (int)blockDim.x;
+  const int tid = n0 + rank * T + (int)threadIdx.x, stride = (int)nb * T;
+  // FP32 updates work in row pairs (n0 is even: plates start on 256-node blocks)
+  const int pid = sizeof(R) == 4 ? n0 / 2 + rank * T + (int)threadIdx.x : tid;
+  double *part = P.part + 4u * (unsigned)c.cta0;
+  unsigned int nbar = 0;
+  for (;;) {
+    typename AC::T v1[1] = {AC::zero()};
+    matvec_rows<R, U>(Q, z.coef[1], tid, stride, v1[0], n1);
+    ++nbar;
+    if (!grid_sum<R, 1>(v1, part + (nbar & 1u) * 2u * nb, S, nbar * nb, z.tot, (typename AC::T(*)[1])sh, &z.ok,
+                        NoHook(), rank, (int)nb))
+      break;
+    if (threadIdx.x == 0) {
+      z.pq = z.tot[0];
+      if (z.pq == 0.0) {
+        z.done = 1;
+        z.flag = 1;
+      } else {
+        z.alpha = z.rho / z.pq;
+        z.coef[0] = sizeof(R) == 4 ? (R)(float)z.alpha : (R)z.alpha;
+        z.flag = 0;
+      }
+    }
+    __syncthreads();
+    if (z.flag) break;
+    typename AC::T v3[3] = {AC::zero(), AC::zero(), AC::zero()};
+    bool proj = false;
+    update_rows<R>(Q, z.coef[0], z.coef[1], pid, stride, v3, proj, n1);
+    typename AC::T v2[2] = {v3[0], v3[1]};
+    ++nbar;
+    if (!grid_sum<R, 2>(v2, part + (nbar & 1u) * 2u * nb, S, nbar * nb, z.tot, sh, &z.ok, NoHook(), rank,
+                        (int)nb))
+      break;
+    if (threadIdx.x == 0) {
+      bool stop = false;
+      const double t0 = z.tot[0], t1 = z.tot[1];
+      z.iters += 1;
+      z.rr = t0;
+      if (!(t0 == t0) || isinf(t0)) {
+        z.status = kStNonfinite;
+        z.done = 1;
+        stop = true;
+      } else if (sqrt(t0) <= Q.tol * z.bn) {
+        z.done = 1;
+        stop = true;
+      }
+      if (!stop && z.iters >= P.max_it) {
+        stop = true;
+        z.status = kStNotConverged;
+        z.done = 1;
+      }
+      z.beta = z.rho != 0.0 ? t1 / z.rho : 0.0;
+      z.rho = t1;
+      z.coef[1] = sizeof(R) == 4 ? (R)(float)z.beta : (R)z.beta;
+      z.flag = stop ? 1 : 0;
+    }
+    __syncthreads();
+    if (z.flag) break;
+  }
+  // the group's first CTA leaves the plate's scalars as the phases loop would
+  if (rank == 0 && threadIdx.x == 0) {
+    if (!z.ok) {
+      z.status = kStTimeout;
+      z.done = 1;
+    }
+    S->iters = z.iters;
+    S->rr = z.rr;
+    S->pq = z.pq;
+    S->alpha = z.alpha;
+    S->alpha_f = (float)z.alpha;
+    S->beta = z.beta;
+    S->beta_f = (float)z.beta;
+    S->rho = z.rho;
+    S->status = z.status;
+    S->done = z.done;
+    S->inner_done = 1;
   }
 }
 

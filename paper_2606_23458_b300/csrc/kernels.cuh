@@ -165,6 +165,13 @@ template <typename R> struct Params {
   R *nbc;
   const uint2 *__restrict__ nmap;
   int32_t Dn;
+  // Element-wise form (FP32 compact records, rows with at most six
+  // incidence slots and six distinct neighbours): the same offset words
+  // and slot maps, used only to gather each distinct neighbour's value
+  // once per row; every entry still applies its own element's two
+  // coefficients (ecf).  Nullable (then each slot gathers its two nodes).
+  const uint32_t *__restrict__ gnbo;
+  const uint2 *__restrict__ gmap;
   R *diag;       // with erec: the row's diagonal sum over entries of
                  // (kappa_e A_e |grad phi_a|^2 + 2 mA)
   const R *gcs; // per-element toughness field as Gc_e / Gc (nullable: uniform);
@@ -1267,6 +1274,66 @@ __device__ __forceinline__ float erec_row(const Params<float> &P, int i, float b
   return q;
 }
 
+// Element-wise rows with shared gathers: a row's six entry records (two
+// element coefficients each, Eq. matrix_free_fe_operator applied element
+// by element) use the values of the row's distinct neighbours, each
+// gathered once, picked per entry through the slot map.  The arithmetic is
+// erec_row's whole-row form term for term (c_b p_b + c_c p_c per entry,
+// then summed in slot order; an empty slot uses the row's own value with
+// zero coefficients), so the result is bit-identical to it: only loads are
+// shared, no two elements' coefficients are combined.
+struct ElRow6 {
+  uint32_t w[3];  // the row's distinct neighbour offsets, two per word
+  uint2 map;      // incidence slot k -> (jb | jc << 4), 0xff = empty
+  float2 cf[6];   // entry k's element coefficients of p_b and p_c
+  float dg;       // Jacobi diagonal
+  unsigned fl;
+};
+
+__device__ __forceinline__ void el_load6(const Params<float> &P, int i, ElRow6 &r) {
+#pragma unroll
+  for (int j = 0; j < 3; ++j) r.w[j] = __ldg(&P.gnbo[(size_t)j * P.N + i]);
+  r.map = __ldg(&P.gmap[i]);
+#pragma unroll
+  for (int k = 0; k < 6; ++k)
+    r.cf[k] = k < P.D ? __ldg(&P.ecf[(size_t)k * P.N + i]) : make_float2(0.f, 0.f);
+  r.dg = __ldg(&P.diag[i]);
+  r.fl = __ldg(&P.flags[i]);
+}
+
+// Value of merged slot j among the gathered v[0..5]; any other j (the
+// empty-slot code 15) gives the row's own value self.
+__device__ __forceinline__ float el_pick(const float (&v)[6], unsigned j, float self) {
+  float r = self;
+#pragma unroll
+  for (int t = 0; t < 6; ++t) r = j == (unsigned)t ? v[t] : r;
+  return r;
+}
+
+// q (= diag p_i) plus the row's entries applied to the gathered values.
+__device__ __forceinline__ float el_apply6(const ElRow6 &r, const float (&v)[6], float self, float q) {
+  float c[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const unsigned m = ((k < 4 ? r.map.x : r.map.y) >> (8 * (k & 3))) & 0xffu;
+    const float vb = el_pick(v, m & 15u, self), vc = el_pick(v, m >> 4, self);
+    c[k] = fmaf(r.cf[k].x, vb, __fmul_rn(r.cf[k].y, vc));
+  }
+#pragma unroll
+  for (int k = 0; k < 6; ++k) q = __fadd_rn(q, c[k]);
+  return q;
+}
+
+template <typename F>
+__device__ __forceinline__ void el_gather6(const ElRow6 &r, int i, float (&v)[6], F val) {
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    const uint32_t x = r.w[j >> 1];
+    const int o = (j & 1) ? (int)x >> 16 : (int)(int16_t)(x & 0xffffu);
+    v[j] = val(i + o);
+  }
+}
+
 // One incidence entry's share of (A p_new)_a, matrix-free (Eq.
 // matrix_free_fe_operator): element coefficients are rebuilt from the
 // geometry and the history on every application.
@@ -1428,12 +1495,12 @@ __device__ __forceinline__ void nb_load6(const Params<float> &P, int i, NbRow6 &
 // pipelined: the next row's records load while this row's neighbour values
 // are gathered; cur holds row i0's records.  Same arithmetic as erec_row.
 __device__ __forceinline__ void nb_rows6(const Params<float> &P, float beta, int i0, int stride, DF &acc,
-                                         NbRow6 cur) {
+                                         NbRow6 cur, int n) {
   typedef Acc<float> AC;
-  for (int i = i0; i < P.N; i += stride) {
+  for (int i = i0; i < n; i += stride) {
     NbRow6 nxt;
     const int in = i + stride;
-    if (in < P.N) nb_load6(P, in, nxt);
+    if (in < n) nb_load6(P, in, nxt);
     float q = 0.f;
     if (!((cur.fl & kNotch) || (P.freef && !P.freef[i]))) {
       const float pc = pnew(P, i, beta);
@@ -1459,11 +1526,12 @@ __device__ __forceinline__ void nb_rows6(const Params<float> &P, float beta, int
 // p_new . q added to acc.
 template <typename R, int U>
 __device__ __forceinline__ void matvec_rows(const Params<R> &P, R beta, int i0, int stride,
-                                            typename Acc<R>::T &acc) {
+                                            typename Acc<R>::T &acc, int iend = -1) {
   typedef Acc<R> AC;
+  const int n = iend < 0 ? P.N : iend;  // rows i0, i0 + stride, ... below n
   if constexpr (sizeof(R) == 8) {
     if (P.nbc) {  // FP64 merged rows
-      for (int i = i0; i < P.N; i += stride) {
+      for (int i = i0; i < n; i += stride) {
         R q = 0;
         if (!is_fixed(P, i)) {
           const R pc = pnew(P, i, beta);
@@ -1478,15 +1546,15 @@ __device__ __forceinline__ void matvec_rows(const Params<R> &P, R beta, int i0, 
   if constexpr (sizeof(R) == 4) {
     if (U >= 2 && P.nbc && P.Dn <= 6) {
       NbRow6 first;
-      if (i0 < P.N) nb_load6(P, i0, first);
-      nb_rows6(P, beta, i0, stride, acc, first);
+      if (i0 < n) nb_load6(P, i0, first);
+      nb_rows6(P, beta, i0, stride, acc, first, n);
       return;
     }
     if (has_erec(P)) {
       // FP32 entry records: the row's diagonal times its own value, then per
       // entry the two other nodes' values times their coefficients (the
       // records stream in coalesced; only the p gathers are indirect)
-      for (int i = i0; i < P.N; i += stride) {
+      for (int i = i0; i < n; i += stride) {
         R q = 0;
         if (!is_fixed(P, i)) {
           const R pc = pnew(P, i, beta);
@@ -1498,7 +1566,7 @@ __device__ __forceinline__ void matvec_rows(const Params<R> &P, R beta, int i0, 
       return;
     }
   }
-  for (int i = i0; i < P.N; i += stride) {
+  for (int i = i0; i < n; i += stride) {
     R q = 0;
     if (!is_fixed(P, i)) {
       const R pc = pnew(P, i, beta);
@@ -1599,10 +1667,11 @@ __device__ __forceinline__ void update_finish(const Params<R> &P, const double *
 // The update of rows (pairs of rows in FP32) j0, j0 + stride, ...
 template <typename R>
 __device__ __forceinline__ void update_rows(const Params<R> &P, R alpha, R beta, int j0, int stride,
-                                            typename Acc<R>::T (&vals)[3], bool &proj) {
+                                            typename Acc<R>::T (&vals)[3], bool &proj, int iend = -1) {
   typedef typename Params<R>::R2 R2;
+  const int n = iend < 0 ? P.N : iend;  // rows below n (FP32: pairs below (n + 1) / 2)
   if constexpr (sizeof(R) == 4) {
-    const int npair = (P.N + 1) >> 1;
+    const int npair = (n + 1) >> 1;
     const uchar2 *__restrict__ fl2 = reinterpret_cast<const uchar2 *>(P.flags);
     float2 *__restrict__ x2 = reinterpret_cast<float2 *>(P.x);
     float2 *__restrict__ r2 = reinterpret_cast<float2 *>(P.r);
@@ -1627,7 +1696,7 @@ __device__ __forceinline__ void update_rows(const Params<R> &P, R alpha, R beta,
       pz4[j] = make_float4(pz0.x, pz0.y, pz1.x, pz1.y);
     }
   } else {
-    for (int i = j0; i < P.N; i += stride) {
+    for (int i = j0; i < n; i += stride) {
       if (is_fixed(P, i)) continue;
       R2 pz = P.pz[i];
       R x = P.x[i], r = P.r[i];
@@ -1758,10 +1827,11 @@ __device__ __forceinline__ void cta_sum(typename Acc<R>::T (&v)[NV], typename Ac
 // return.
 constexpr int kPartWarps = 8;
 template <typename R, int NV>
-__device__ __forceinline__ void grid_partials(const double *part, double *tot, typename Acc<R>::T (*sh)[NV]) {
+__device__ __forceinline__ void grid_partials(const double *part, double *tot, typename Acc<R>::T (*sh)[NV],
+                                              int nbg = -1) {
   typedef Acc<R> A;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int nb = (int)gridDim.x;
+  const int nb = nbg < 0 ? (int)gridDim.x : nbg;
   constexpr int T = 32 * kPartWarps;
   if (wid < kPartWarps) {
     typename A::T w[NV];
@@ -1806,16 +1876,19 @@ struct NoHook {
 // gridDim.x * NV slots; target: arrivals that complete this barrier.
 // Returns false (in every thread) if the wait gave up; otherwise thread 0
 // holds the totals in tot.  hook() runs in thread 0 as soon as the barrier
-// has completed, before the partials are summed.
+// has completed, before the partials are summed.  A group of CTAs (the
+// CTAs of one plate of a batch) reduces among itself with cta = the CTA's
+// rank in the group and nb = the group's size (defaults: the whole grid).
 template <typename R, int NV, typename Hook = NoHook>
 __device__ __forceinline__ bool grid_sum(typename Acc<R>::T (&v)[NV], double *part, SolveScalars *S,
                                          unsigned int target, double *tot, typename Acc<R>::T (*sh)[NV],
-                                         int *ok_sh, const Hook &hook = Hook()) {
+                                         int *ok_sh, const Hook &hook = Hook(), int cta = -1, int nb = -1) {
   typedef Acc<R> A;
   cta_sum<R, NV>(v, sh);  // its barriers order every thread's row writes before thread 0's release
   if (threadIdx.x == 0) {
+    const int slot = cta < 0 ? (int)blockIdx.x : cta;
 #pragma unroll
-    for (int k = 0; k < NV; ++k) A::store(&part[(size_t)blockIdx.x * NV + k], v[k]);
+    for (int k = 0; k < NV; ++k) A::store(&part[(size_t)slot * NV + k], v[k]);
     red_release_add_u32(&S->bar, 1u);
     int ok = 1;
     const unsigned long long t0 = global_ns();
@@ -1836,7 +1909,7 @@ __device__ __forceinline__ bool grid_sum(typename Acc<R>::T (&v)[NV], double *pa
   }
   __syncthreads();
   if (!*ok_sh) return false;
-  grid_partials<R, NV>(part, tot, sh);
+  grid_partials<R, NV>(part, tot, sh, nb);
   return true;
 }
 
@@ -2077,12 +2150,47 @@ __device__ __forceinline__ void fused_rows6(const Params<float> &P, float al, fl
 // Rows i0, i0 + stride, ... < N of one single-reduction pass, operator and
 // neighbour vectors read from global memory (U entries in flight; merged
 // rows of width 6: U >= 2 pipelines rows).
+// Element-wise rows of one single-reduction pass with shared gathers
+// (el_rows6's operator, fused_rows6's recurrences).
+__device__ __forceinline__ void fused_el_rows6(const Params<float> &P, float al, float be,
+                                               const float4 *__restrict__ vin, float4 *__restrict__ vout, int i0,
+                                               int stride, DF (&acc)[3]) {
+  typedef Acc<float> AC;
+  for (int j = i0; j < P.N; j += stride) {
+    ElRow6 cur;
+    el_load6(P, j, cur);
+    const float4 v = vin[j];
+    if ((cur.fl & kNotch) || (P.freef && !P.freef[j])) {  // eliminated row: everything stays zero
+      vout[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+      continue;
+    }
+    const float p = fmaf(be, P.cgp[j], v.w * v.x);
+    const float sn = fmaf(be, v.z, v.y);
+    const float rn = fmaf(-al, sn, v.x);
+    const float un = v.w * rn;
+    P.x[j] = fmaf(al, p, P.x[j]);
+    P.cgp[j] = p;
+    float u[6];
+    el_gather6(cur, j, u, [&](int n) { return cg_unew(vin[n], al, be); });
+    const float wq = el_apply6(cur, u, un, cur.dg * un);
+    vout[j] = make_float4(rn, wq, sn, v.w);
+    const float sr = P.rscale * rn;
+    acc[0] = AC::add(acc[0], AC::prod(sr, un));             // gamma
+    acc[1] = AC::add(acc[1], AC::prod(P.rscale * wq, un));  // delta
+    acc[2] = AC::add(acc[2], AC::prod(sr, sr));             // |r|^2
+  }
+}
+
 template <int U>
 __device__ __forceinline__ void fused_rows(const Params<float> &P, float al, float be, const float4 *__restrict__ vin,
                                            float4 *__restrict__ vout, int i0, int stride, DF (&acc)[3]) {
   typedef Acc<float> AC;
   if (U >= 2 && P.nbc && P.Dn <= 6) {
     fused_rows6(P, al, be, vin, vout, i0, stride, acc);
+    return;
+  }
+  if (U >= 2 && P.gnbo) {
+    fused_el_rows6(P, al, be, vin, vout, i0, stride, acc);
     return;
   }
   for (int j = i0; j < P.N; j += stride) {

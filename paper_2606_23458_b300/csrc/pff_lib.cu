@@ -272,7 +272,8 @@ struct pff_mesh {
   uint32_t *nbo = nullptr;   // merged rows: neighbour offsets (Dn / 2 x N)
   void *nbc = nullptr;       // merged rows: coefficients (Dn x N, kernel precision)
   uint2 *nmap = nullptr;     // merged rows: incidence slot -> merged slots (8 bytes per row)
-  int32_t Dn = 0;            // merged row width (6 or 8; 0 = not used)
+  int32_t Dn = 0;            // merged row width (6 or 8; 0 = not available)
+  int32_t dop = PFF_OP_ELEMENT;  // damage operator form applied by the CG products
   float *diagf = nullptr;  // FP32: the damage rows' diagonals (N)
   double *diagd = nullptr; // FP64 with merged rows: the same
   void *fe = nullptr;      // slot forces of the element-pass force schedule (3 Ne x R2)
@@ -864,11 +865,10 @@ static pff_status configure(pff_mesh *m) {
     cudaFree(ofs);
     if (st != PFF_OK) return st;
     if (m->nbc) {
+      // merged rows are the opt-in form (PFF_OP_MERGED); the per-element
+      // records of the default form stay
       PFF_TRY(dalloc(&m->diagd, (size_t)m->N));
       CUDA_TRY(cudaMemset(m->diagd, 0, (size_t)m->N * sizeof(double)));
-      // the per-element damage records are no longer read
-      if (m->drec) CUDA_TRY(cudaFree(m->drec));
-      m->drec = nullptr;
     }
   }
   m->nblk = (int32_t)((m->N + NB - 1) / NB);
@@ -975,15 +975,23 @@ static Params<R> base_params(pff_mesh *m, const pff_options &o) {
   P.ell = m->ell;
   P.D = m->D;
   P.rec = (const ERec<R> *)m->rec;
-  P.drec = (DRec<R> *)m->drec;
+  // the damage operator's form: element coefficients (matrix-free, the
+  // default) or the merged rows assembled per solve (PFF_OP_MERGED)
+  const bool merged = m->dop == PFF_OP_MERGED && m->nbc;
+  P.drec = merged ? nullptr : (DRec<R> *)m->drec;
   P.erec = m->erec;
   P.ecmp = m->ecmp;
   P.ecf = m->ecf;
-  P.nbo = m->nbo;
-  P.nbc = (R *)m->nbc;
-  P.nmap = m->nmap;
-  P.Dn = m->Dn;
-  P.diag = sizeof(R) == 4 ? (R *)m->diagf : (R *)m->diagd;
+  P.nbo = merged ? m->nbo : nullptr;
+  P.nbc = merged ? (R *)m->nbc : nullptr;
+  P.nmap = merged ? m->nmap : nullptr;
+  P.Dn = merged ? m->Dn : 0;
+  // element-wise form on rows with at most six slots and six distinct
+  // neighbours: gather each distinct neighbour once (FP32 compact records)
+  const bool shared = !merged && sizeof(R) == 4 && m->ecmp && m->nbo && m->Dn == 6 && m->D <= 6;
+  P.gnbo = shared ? m->nbo : nullptr;
+  P.gmap = shared ? m->nmap : nullptr;
+  P.diag = sizeof(R) == 4 ? (R *)m->diagf : (merged ? (R *)m->diagd : nullptr);
   P.flags = m->flags;
   P.st_cta = m->st_cta;
   P.st_rng = m->st_rng;
@@ -1894,7 +1902,7 @@ static pff_status qs_run_t(pff_mesh *m, const pff_state *st, const uint8_t *bc_h
     // neighbour offsets of the incidence (the packing of the damage
     // records), then the rows' distinct neighbours and slot maps
     int mx = 1 << 30;
-    if (m->D <= kNbMax) {
+    if (m->D <= kNbMax && m->dop == PFF_OP_MERGED) {
       const unsigned gb = std::min<unsigned>(grid_for(N, 256), stride_cap());
       k_erec_ids<R><<<gb, 256, 0, s>>>((const ERec<R> *)m->rec, m->ell, (int)N, m->D, ofs, nullptr);
       QS_TRY(dalloc(&cnt, 1));
@@ -2999,6 +3007,35 @@ pff_status pff_mesh_set_gc_field(pff_mesh *m, const double *gc) {
   return PFF_OK;
 }
 
+pff_status pff_mesh_set_operator(pff_mesh *m, int32_t form) {
+  if (!m) return fail(PFF_ERR_ARG, "null mesh");
+  if (form != PFF_OP_ELEMENT && form != PFF_OP_MERGED) return fail(PFF_ERR_ARG, "unknown operator form");
+  if (form == PFF_OP_MERGED && !m->nbc)
+    return fail(PFF_ERR_ARG, "merged rows are not available on this mesh (a row with more than 8 distinct "
+                             "neighbours, or an element spanning 2^15 node ids or more)");
+  if (form == m->dop) return PFF_OK;
+  m->dop = form;
+  // the step graphs and the CG timings belong to the previous form
+  free_graph(m->solve_g);
+  free_graph(m->step_g);
+  free_graph(m->mech_g);
+  m->tuned[KP_RHS] = m->tuned[KP_MATVEC] = false;
+  m->pers_tuned = false;
+  m->best_fam = kFamPhases;
+  for (int f = 0; f < 8; ++f) {
+    m->fam_U[f] = 0;
+    m->fam_ms[f] = 0.f;
+  }
+  return PFF_OK;
+}
+
+pff_status pff_mesh_get_operator(const pff_mesh *m, int32_t *form, int32_t *merged_available) {
+  if (!m) return fail(PFF_ERR_ARG, "null mesh");
+  if (form) *form = m->dop;
+  if (merged_available) *merged_available = m->nbc ? 1 : 0;
+  return PFF_OK;
+}
+
 }  // extern "C"
 
 // ================================================================ batches
@@ -3021,7 +3058,16 @@ struct pff_batch {
   unsigned int *tick = nullptr, *gtick = nullptr;
   int32_t *nactive = nullptr;
   GraphCache g;
-  int32_t U = 3;
+  int32_t U = 3;         // gathers in flight of the kernel-per-phase matvec
+  // the autotuner's choice (gathers in flight per kernel, CG loop form) and
+  // its timings: force U = 1..4, right-hand side U = 1..4, CG loop
+  // candidates (phases U = 1..4, persistent U = 2..4), ms
+  int32_t Uf = 3, Ur = 3, cgU = 3, cg_mode = PFF_CG_PHASES;
+  bool tuned = false;
+  float tune_ms[3][8] = {{0.f}};
+  // per-plate persistent CG: CTA -> (plate, rank), grid (0: unavailable)
+  int2 *cta_plate = nullptr;
+  unsigned pgrid = 0;
 };
 
 namespace pff {
@@ -3029,7 +3075,7 @@ namespace pff {
 static void batch_free(pff_batch *b) {
   if (!b) return;
   free_graph(b->g);
-  void *p[] = {b->blk_plate, b->pc, b->stab, b->sc, b->tick, b->gtick, b->nactive};
+  void *p[] = {b->blk_plate, b->pc, b->stab, b->sc, b->tick, b->gtick, b->nactive, b->cta_plate};
   for (void *q : p)
     if (q) cudaFree(q);
   if (b->m) mesh_free(b->m);
@@ -3055,10 +3101,276 @@ static const void *kb_fun(int id, int U) {
 }
 
 template <typename R>
+static const void *kb_pers_fun(int U) {
+  return U <= 2 ? (const void *)kb_cg_persistent<R, 2> : U == 3 ? (const void *)kb_cg_persistent<R, 3>
+                                                                 : (const void *)kb_cg_persistent<R, 4>;
+}
+
+constexpr int kBatchPersThreads = pers_threads(2, false);  // every U >= 2 variant
+
+// CTA groups of the per-plate persistent CG: a full wave of co-resident
+// CTAs (the smallest residency of the U = 2..4 variants), split over the
+// plates in proportion to their node blocks, at least one CTA each, the
+// remainder by largest fractional share (ties to the lower plate).  No
+// groups (pgrid = 0) if the device cannot launch cooperatively or there
+// are more plates than CTAs.
+template <typename R>
+static pff_status batch_groups(pff_batch *b, std::vector<PlateC> &pc) {
+  int dev = 0, nsm = 0, coop = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  int occ = 1 << 30;
+  for (int U = 2; U <= 4; ++U) {
+    int o = 0;
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kb_pers_fun<R>(U), kBatchPersThreads, 0));
+    occ = std::min(occ, o);
+  }
+  const int np = b->np;
+  const int64_t G = (int64_t)nsm * occ;
+  b->pgrid = 0;
+  if (!coop || occ <= 0 || G < np) return PFF_OK;
+  int64_t tot = 0;
+  for (const auto &c : pc) tot += c.nblk;
+  std::vector<int64_t> n(np);
+  std::vector<double> frac(np);
+  int64_t used = 0;
+  for (int p = 0; p < np; ++p) {
+    const double share = (double)(G - np) * pc[p].nblk / (double)tot;  // beyond the one CTA each
+    n[p] = 1 + (int64_t)share;
+    frac[p] = share - (double)(int64_t)share;
+    used += n[p];
+  }
+  std::vector<int> order(np);
+  for (int p = 0; p < np; ++p) order[p] = p;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return frac[a] > frac[c]; });
+  for (int k = 0; used < G && k < np; ++k, ++used) n[order[k]] += 1;
+  std::vector<int2> map;
+  for (int p = 0; p < np; ++p) {
+    // no more CTAs than the plate has 256-row blocks' worth of threads
+    n[p] = std::max<int64_t>(1, std::min<int64_t>(n[p], ((int64_t)pc[p].nblk * kThreads + kBatchPersThreads - 1) /
+                                                           kBatchPersThreads));
+    pc[p].cta0 = (int32_t)map.size();
+    pc[p].ncta = (int32_t)n[p];
+    for (int64_t r = 0; r < n[p]; ++r) map.push_back(make_int2(p, (int)r));
+  }
+  PFF_TRY(dalloc(&b->cta_plate, map.size()));
+  CUDA_TRY(cudaMemcpy(b->cta_plate, map.data(), map.size() * sizeof(int2), cudaMemcpyHostToDevice));
+  b->pgrid = (unsigned)map.size();
+  return PFF_OK;
+}
+
+static pff_status add_coop(cudaGraph_t g, const std::vector<cudaGraphNode_t> &deps, const void *fn, unsigned grid,
+                           unsigned block, void **args, cudaGraphNode_t *out) {
+  PFF_TRY(add_generic(g, deps, fn, grid, block, 0, args, out));
+  cudaLaunchAttributeValue av;
+  std::memset(&av, 0, sizeof(av));
+  av.cooperative = 1;
+  CUDA_TRY(cudaGraphKernelNodeSetAttribute(*out, cudaLaunchAttributeCooperative, &av));
+  return PFF_OK;
+}
+
+// Builds the batch's step graph: predictor, force (Uf), right-hand side
+// (Ur), the CG loop (kernel per phase with cgU gathers in a WHILE node, or
+// the per-plate persistent launch), clamp and step counter.  With
+// solve_only: the right-hand side and the CG loop alone (the autotuner's
+// timed unit; it leaves the state untouched).
+template <typename R>
+static pff_status batch_graph(pff_batch *b, Params<R> P, Batch &B, int Uf, int Ur, int mode, int cgU,
+                              bool solve_only, cudaGraphExec_t *exec) {
+  pff_mesh *m = b->m;
+  const int64_t nblk = (m->N + kThreads - 1) / kThreads;
+  const bool pers = mode == PFF_CG_PERSISTENT && b->pgrid > 0;
+  cudaGraph_t g;
+  CUDA_TRY(cudaGraphCreate(&g, 0));
+  P.use_cond = 0;
+  if (!pers) {
+    if (cudaGraphConditionalHandleCreate(&P.cond_inner, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
+      cudaGraphDestroy(g);
+      return fail(PFF_ERR_CUDA, "batch graph: conditional handle");
+    }
+    P.use_cond = 1;
+  }
+  void *args[] = {(void *)&P, (void *)&B};
+  void *sargs[] = {(void *)&m->step_ctr};
+  cudaGraphNode_t n_pr, n_f, n_rhs, n_loop, n_mv, n_up, n_fin, n_done;
+  cudaGraph_t body;
+  const unsigned G = (unsigned)nblk;
+  pff_status st = PFF_OK;
+  std::vector<cudaGraphNode_t> dep;
+  if (!solve_only) {
+    st = add_generic(g, {}, kb_fun<R>(KP_PREDICT, Uf), G, kThreads, 0, args, &n_pr);
+    if (st == PFF_OK) st = add_generic(g, {n_pr}, kb_fun<R>(KP_FORCE, Uf), G, kThreads, 0, args, &n_f);
+    dep = {n_f};
+  }
+  if (st == PFF_OK) st = add_generic(g, dep, kb_fun<R>(KP_RHS, Ur), G, kThreads, 0, args, &n_rhs);
+  if (st == PFF_OK && pers) {
+    st = add_coop(g, {n_rhs}, kb_pers_fun<R>(cgU), b->pgrid, kBatchPersThreads, args, &n_loop);
+  } else if (st == PFF_OK) {
+    st = add_while(g, {n_rhs}, P.cond_inner, &body, &n_loop);
+    if (st == PFF_OK) st = add_generic(body, {}, kb_fun<R>(KP_MATVEC, cgU), G, kThreads, 0, args, &n_mv);
+    if (st == PFF_OK)
+      st = add_generic(body, {n_mv}, kb_fun<R>(KP_UPDATE, cgU), G, sizeof(R) == 4 ? kbUpdatePairThreads : kThreads,
+                       0, args, &n_up);
+  }
+  if (!solve_only) {
+    if (st == PFF_OK) st = add_generic(g, {n_loop}, kb_fun<R>(KP_FINISH, Uf), G, kThreads, 0, args, &n_fin);
+    if (st == PFF_OK) st = add_generic(g, {n_fin}, (const void *)kb_step_done, 1, 32, 0, sargs, &n_done);
+  }
+  if (st != PFF_OK) {
+    cudaGraphDestroy(g);
+    return st;
+  }
+  const cudaError_t e = cudaGraphInstantiate(exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    *exec = nullptr;
+    return fail(PFF_ERR_CUDA, std::string("cudaGraphInstantiate (batch): ") + cudaGetErrorString(e));
+  }
+  return PFF_OK;
+}
+
+// The batch's autotuner, at the first run on the run's own state: the
+// gathers in flight of the force kernel (on scratch copies of v, a and the
+// history, so the state is untouched) and of the right-hand side (U = 1..4,
+// each the best of three launches after a warm-up), then the CG loop --
+// kernel per phase with U = 1..4, per-plate persistent with U = 2..4 --
+// each timed as the right-hand side plus a whole solve of every plate (a
+// graph; best of three after a warm-up).  The fastest of each is kept.
+template <typename R>
+static pff_status batch_tune(pff_batch *b, Params<R> P, Batch B, cudaStream_t s) {
+  pff_mesh *m = b->m;
+  const int64_t nblk = (m->N + kThreads - 1) / kThreads;
+  typedef typename V<R>::T2 R2;
+  R2 *sv = nullptr, *sa = nullptr;
+  double *sH = nullptr;
+  float *sHf = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  pff_status res = PFF_OK;
+  auto cleanup = [&]() {
+    void *q[] = {sv, sa, sH, sHf};
+    for (void *x : q)
+      if (x) cudaFree(x);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  };
+#define BT_TRY(x)                                                                                   \
+  do {                                                                                              \
+    cudaError_t e_ = (x);                                                                           \
+    if (e_ != cudaSuccess) {                                                                        \
+      cleanup();                                                                                    \
+      return fail(PFF_ERR_CUDA, std::string("batch autotune: ") + #x + ": " + cudaGetErrorString(e_)); \
+    }                                                                                               \
+  } while (0)
+  BT_TRY(cudaEventCreate(&e0));
+  BT_TRY(cudaEventCreate(&e1));
+  auto timed = [&](auto launch) -> float {
+    float best = 1e30f;
+    for (int r = 0; r < 4; ++r) {  // the first is a warm-up
+      cudaEventRecord(e0, s);
+      launch();
+      cudaEventRecord(e1, s);
+      if (cudaEventSynchronize(e1) != cudaSuccess) return -1.f;
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e0, e1);
+      if (r > 0) best = std::min(best, t);
+    }
+    return best;
+  };
+  P.use_cond = 0;
+  // force: scratch copies of what it writes
+  {
+    Params<R> Q = P;
+    BT_TRY(cudaMalloc(&sv, m->N * sizeof(R2)));
+    BT_TRY(cudaMalloc(&sa, m->N * sizeof(R2)));
+    BT_TRY(cudaMalloc(&sH, m->Ne * sizeof(double)));
+    BT_TRY(cudaMemcpyAsync(sv, P.v, m->N * sizeof(R2), cudaMemcpyDeviceToDevice, s));
+    BT_TRY(cudaMemcpyAsync(sa, P.a, m->N * sizeof(R2), cudaMemcpyDeviceToDevice, s));
+    BT_TRY(cudaMemcpyAsync(sH, P.H, m->Ne * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (sizeof(R) == 4) {
+      BT_TRY(cudaMalloc(&sHf, m->Ne * sizeof(float)));
+      BT_TRY(cudaMemcpyAsync(sHf, m->Hf, m->Ne * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    }
+    Q.v = sv;
+    Q.a = sa;
+    Q.H = sH;
+    Q.Hf = sHf;
+    Q.step_ctr = m->step_ctr;  // reads S(t) at the counter (not advanced here)
+    float best = 1e30f;
+    for (int U = 1; U <= 4; ++U) {
+      void *args[] = {(void *)&Q, (void *)&B};
+      const float t = timed([&]() {
+        cudaLaunchKernel(kb_fun<R>(KP_FORCE, U), dim3((unsigned)nblk), dim3(kThreads), args, 0, s);
+      });
+      if (t < 0.f) res = fail(PFF_ERR_CUDA, "batch autotune: force timing");
+      b->tune_ms[0][U - 1] = t;
+      if (t >= 0.f && t < best) {
+        best = t;
+        b->Uf = U;
+      }
+    }
+  }
+  if (res == PFF_OK) {
+    float best = 1e30f;
+    for (int U = 1; U <= 4; ++U) {
+      void *args[] = {(void *)&P, (void *)&B};
+      const float t = timed([&]() {
+        cudaLaunchKernel(kb_fun<R>(KP_RHS, U), dim3((unsigned)nblk), dim3(kThreads), args, 0, s);
+      });
+      if (t < 0.f) res = fail(PFF_ERR_CUDA, "batch autotune: right-hand side timing");
+      b->tune_ms[1][U - 1] = t;
+      if (t >= 0.f && t < best) {
+        best = t;
+        b->Ur = U;
+      }
+    }
+  }
+  if (res == PFF_OK) {
+    float best = 1e30f;
+    for (int k = 0; k < 7 && res == PFF_OK; ++k) {
+      const int mode = k < 4 ? PFF_CG_PHASES : PFF_CG_PERSISTENT;
+      const int U = k < 4 ? k + 1 : k - 2;
+      if (mode == PFF_CG_PERSISTENT && b->pgrid == 0) continue;
+      cudaGraphExec_t ex = nullptr;
+      res = batch_graph<R>(b, P, B, b->Uf, b->Ur, mode, U, true, &ex);
+      if (res != PFF_OK) break;
+      const float t = timed([&]() { cudaGraphLaunch(ex, s); });
+      cudaGraphExecDestroy(ex);
+      if (t < 0.f) {
+        res = fail(PFF_ERR_CUDA, "batch autotune: CG timing");
+        break;
+      }
+      // a persistent group that gave up leaves a timeout status: not a candidate
+      std::vector<SolveScalars> hs(b->np);
+      if (cudaMemcpy(hs.data(), b->sc, b->np * sizeof(SolveScalars), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        res = fail(PFF_ERR_CUDA, "batch autotune: scalars");
+        break;
+      }
+      bool bad = false;
+      for (const auto &h : hs) bad = bad || h.status == kStTimeout;
+      if (bad) {
+        res = fail(PFF_ERR_TIMEOUT, "batch autotune: a grid-barrier wait of the persistent CG timed out");
+        break;
+      }
+      b->tune_ms[2][k] = t;
+      if (t < best) {
+        best = t;
+        b->cg_mode = mode;
+        b->cgU = U;
+      }
+    }
+  }
+  cudaStreamSynchronize(s);
+  cleanup();
+#undef BT_TRY
+  if (res == PFF_OK) b->tuned = true;
+  return res;
+}
+
+template <typename R>
 static pff_status batch_run_t(pff_batch *b, const pff_state *st, int64_t step0, int64_t nsteps,
                               const pff_options &o, int32_t *iters_log, cudaStream_t s) {
   pff_mesh *m = b->m;
-  const int64_t nblk = (m->N + kThreads - 1) / kThreads;
   // traction scale per plate and step
   if (b->stab_cap < (nsteps + 1) * b->np) {
     if (b->stab) cudaFree(b->stab);
@@ -3098,10 +3410,25 @@ static pff_status batch_run_t(pff_batch *b, const pff_state *st, int64_t step0, 
   B.gtick = b->gtick;
   B.nactive = b->nactive;
   B.iters_log = iters_log;
+  B.cta_plate = b->cta_plate;
   const int64_t zero = 0;
   CUDA_TRY(cudaMemcpyAsync(m->step_ctr, &zero, sizeof(int64_t), cudaMemcpyHostToDevice, s));
   CUDA_TRY(cudaStreamSynchronize(s));
-  std::vector<uint64_t> key = {(uint64_t)nsteps, (uint64_t)iters_log, (uint64_t)b->U, (uint64_t)o.cg_max_it,
+  // the loop form and gathers in flight: forced by the options, else the
+  // autotuner's (timed once, at the first run)
+  if (o.variant >= 2) {
+    b->Uf = b->Ur = b->cgU = std::min(o.variant - 1, 4);
+  } else if (!b->tuned && nsteps > 0) {
+    P.Stab = b->stab;
+    PFF_TRY(batch_tune<R>(b, P, B, s));
+  }
+  int mode = b->cg_mode, cgU = b->cgU;
+  if (o.cg_kernel == PFF_CG_PHASES) mode = PFF_CG_PHASES;
+  if (o.cg_kernel == PFF_CG_PERSISTENT) mode = PFF_CG_PERSISTENT;
+  if (mode == PFF_CG_PERSISTENT && b->pgrid == 0) mode = PFF_CG_PHASES;
+  if (mode == PFF_CG_PERSISTENT) cgU = std::max(cgU, 2);
+  std::vector<uint64_t> key = {(uint64_t)nsteps, (uint64_t)iters_log, (uint64_t)b->Uf, (uint64_t)b->Ur,
+                               (uint64_t)mode, (uint64_t)cgU, (uint64_t)o.cg_max_it,
                                (uint64_t)b->stab, (uint64_t)st->u, (uint64_t)st->v, (uint64_t)st->a,
                                (uint64_t)st->d, (uint64_t)st->H};
   uint64_t tb;
@@ -3109,35 +3436,7 @@ static pff_status batch_run_t(pff_batch *b, const pff_state *st, int64_t step0, 
   key.push_back(tb);
   if (!b->g.exec || b->g.key != key) {
     free_graph(b->g);
-    cudaGraph_t g;
-    CUDA_TRY(cudaGraphCreate(&g, 0));
-    CUDA_TRY(cudaGraphConditionalHandleCreate(&P.cond_inner, g, 1, cudaGraphCondAssignDefault));
-    P.use_cond = 1;
-    void *args[] = {(void *)&P, (void *)&B};
-    void *sargs[] = {(void *)&m->step_ctr};
-    cudaGraphNode_t n_pr, n_f, n_rhs, n_loop, n_mv, n_up, n_fin, n_done;
-    cudaGraph_t body;
-    const unsigned G = (unsigned)nblk;
-    pff_status st = add_generic(g, {}, kb_fun<R>(KP_PREDICT, b->U), G, kThreads, 0, args, &n_pr);
-    if (st == PFF_OK) st = add_generic(g, {n_pr}, kb_fun<R>(KP_FORCE, b->U), G, kThreads, 0, args, &n_f);
-    if (st == PFF_OK) st = add_generic(g, {n_f}, kb_fun<R>(KP_RHS, b->U), G, kThreads, 0, args, &n_rhs);
-    if (st == PFF_OK) st = add_while(g, {n_rhs}, P.cond_inner, &body, &n_loop);
-    if (st == PFF_OK) st = add_generic(body, {}, kb_fun<R>(KP_MATVEC, b->U), G, kThreads, 0, args, &n_mv);
-    if (st == PFF_OK)
-      st = add_generic(body, {n_mv}, kb_fun<R>(KP_UPDATE, b->U), G, sizeof(R) == 4 ? kbUpdatePairThreads : kThreads,
-                       0, args, &n_up);
-    if (st == PFF_OK) st = add_generic(g, {n_loop}, kb_fun<R>(KP_FINISH, b->U), G, kThreads, 0, args, &n_fin);
-    if (st == PFF_OK) st = add_generic(g, {n_fin}, (const void *)kb_step_done, 1, 32, 0, sargs, &n_done);
-    if (st != PFF_OK) {
-      cudaGraphDestroy(g);
-      return st;
-    }
-    const cudaError_t e = cudaGraphInstantiate(&b->g.exec, g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) {
-      b->g.exec = nullptr;
-      return fail(PFF_ERR_CUDA, std::string("cudaGraphInstantiate (batch): ") + cudaGetErrorString(e));
-    }
+    PFF_TRY(batch_graph<R>(b, P, B, b->Uf, b->Ur, mode, cgU, false, &b->g.exec));
     b->g.key = key;
   }
   for (int64_t n = 0; n < nsteps; ++n) CUDA_TRY(cudaGraphLaunch(b->g.exec, s));
@@ -3247,6 +3546,11 @@ pff_status pff_batch_create(int32_t nplates, const pff_plate *plates, int32_t pr
     c.nblk = (int32_t)((last + kThreads - 1) / kThreads - c.blk0);
     for (int32_t k = 0; k < c.nblk; ++k) bp[c.blk0 + k] = p;
   }
+  st = precision == PFF_FP64 ? batch_groups<double>(b, pc) : batch_groups<float>(b, pc);
+  if (st != PFF_OK) {
+    batch_free(b);
+    return st;
+  }
   auto A = [&](void **ptr, size_t bytes) -> pff_status {
     CUDA_TRY(cudaMalloc(ptr, bytes));
     CUDA_TRY(cudaMemset(*ptr, 0, bytes));
@@ -3274,6 +3578,31 @@ pff_status pff_batch_create(int32_t nplates, const pff_plate *plates, int32_t pr
 }
 
 void pff_batch_destroy(pff_batch *b) { batch_free(b); }
+
+pff_status pff_batch_tuning(const pff_batch *b, int32_t *choice, float *ms) {
+  if (!b) return fail(PFF_ERR_ARG, "null batch");
+  if (choice) {
+    choice[0] = b->Uf;
+    choice[1] = b->Ur;
+    choice[2] = b->cg_mode;
+    choice[3] = b->cgU;
+    choice[4] = b->tuned ? 1 : 0;
+    choice[5] = (int32_t)b->pgrid;
+  }
+  if (ms) std::memcpy(ms, b->tune_ms, sizeof(b->tune_ms));
+  return PFF_OK;
+}
+
+pff_status pff_batch_set_operator(pff_batch *b, int32_t form) {
+  if (!b) return fail(PFF_ERR_ARG, "null batch");
+  int32_t cur = 0;
+  PFF_TRY(pff_mesh_get_operator(b->m, &cur, nullptr));
+  if (cur == form) return PFF_OK;
+  PFF_TRY(pff_mesh_set_operator(b->m, form));
+  free_graph(b->g);
+  b->tuned = false;  // timings belong to the previous form
+  return PFF_OK;
+}
 
 pff_status pff_batch_size(const pff_batch *b, int64_t *N, int64_t *Ne) {
   if (!b) return fail(PFF_ERR_ARG, "null batch");
@@ -3308,7 +3637,6 @@ pff_status pff_batch_run(pff_batch *b, const pff_state *st, int64_t step0, int64
     for (auto &c : pc) c.tol = tol;
     CUDA_TRY(cudaMemcpy(b->pc, pc.data(), b->np * sizeof(PlateC), cudaMemcpyHostToDevice));
   }
-  if (o.variant >= 2) b->U = std::min(o.variant - 1, 4);
   return b->m->prec == PFF_FP64 ? batch_run_t<double>(b, st, step0, nsteps, o, iters_log, s)
                                 : batch_run_t<float>(b, st, step0, nsteps, o, iters_log, s);
 }

@@ -10,6 +10,8 @@ in Sec. 4.1.  All arithmetic of the method runs in libpff's kernels.
 """
 from __future__ import annotations
 
+import math
+
 import torch
 
 from . import Checkpoint, Mesh, options
@@ -43,13 +45,19 @@ def mse_loss(d, dstar):
     return torch.mean((d.double() - dstar.double()) ** 2)
 
 
-def recover_gc(mesh, material, nsteps, dstar, gc0, every=25, opts=None, max_iter=10):
-    """L-BFGS with strong-Wolfe line search on log Gc (Sec. 4.1).
-    Returns (Gc, history of (Gc, loss) per closure)."""
-    logg = torch.tensor(float(torch.log(torch.tensor(gc0))), dtype=torch.float64, requires_grad=True)
-    opt = torch.optim.LBFGS([logg], lr=1.0, max_iter=max_iter, line_search_fn="strong_wolfe",
-                            tolerance_grad=1e-12, tolerance_change=1e-14)
-    hist = []
+def recover_gc(mesh, material, nsteps, dstar, gc0, every=25, opts=None, max_states=10, history_size=10):
+    """L-BFGS with a strong-Wolfe line search on log Gc (Sec. 4.1; the
+    logarithm keeps Gc positive), driven one accepted state at a time so
+    that each state's Gc is recorded.  Each closure evaluation reruns the
+    differentiable forward run and the adjoint.  Stops after max_states
+    accepted states, or earlier when the gradient or the step vanishes.
+    Returns (Gc, dict(states=[Gc after each accepted state],
+    evals=[(Gc, loss, dL/dlogGc) per closure evaluation, line-search probes
+    included]))."""
+    logg = torch.tensor(math.log(float(gc0)), dtype=torch.float64, requires_grad=True)
+    opt = torch.optim.LBFGS([logg], lr=1.0, max_iter=1, history_size=history_size,
+                            line_search_fn="strong_wolfe", tolerance_grad=1e-14, tolerance_change=1e-16)
+    evals, states = [], []
 
     def closure():
         opt.zero_grad()
@@ -57,8 +65,13 @@ def recover_gc(mesh, material, nsteps, dstar, gc0, every=25, opts=None, max_iter
         d = final_damage(gc, mesh, material, nsteps, every, opts)
         loss = mse_loss(d, dstar)
         loss.backward()
-        hist.append((float(gc.item()), float(loss.item())))
+        evals.append((float(gc.item()), float(loss.item()), float(logg.grad.item())))
         return loss
 
-    opt.step(closure)
-    return float(torch.exp(logg).item()), hist
+    for _ in range(max_states):
+        before = float(logg.item())
+        opt.step(closure)
+        states.append(float(torch.exp(logg).item()))
+        if float(logg.item()) == before:   # no step taken: converged
+            break
+    return states[-1], dict(states=states, evals=evals)

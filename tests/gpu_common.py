@@ -1,6 +1,29 @@
 """Shared helpers of the GPU parity tests (CUDA path vs the FP64 oracle)."""
 import numpy as np
 
+# Element-wise comparisons divide each entry's error by max(|o_i|, floor),
+# with floor = a fraction of the field's largest magnitude: an entry far
+# below the field's scale (the quiet far field, the few elements where H has
+# just become non-zero) is held to an absolute error of floor x tol instead
+# of to its own tiny magnitude, but a local error anywhere (the notch tip,
+# the loaded edge rows) cannot hide under the bulk of the field.
+#
+# The FP64 GPU path and the oracle are two correct FP64 orderings of the
+# same arithmetic (fused multiply-adds, the damage dot products' summation
+# order); they differ by an ulp here and there every step, and the explicit
+# dynamics carries those differences forward.  Over the 200-step window of
+# the 100 x 40 plate the largest absolute differences, relative to each
+# field's maximum, were u 5e-15, v 4e-14, a 9e-13, d 3e-14 and H 1e-13
+# (measured): the velocity is the time integral and the acceleration the
+# discrete Laplacian of the displacement, so their small entries carry the
+# displacement's accumulated rounding.  FIELD_FLOORS puts every field's
+# element-wise error at or below 1e-10 with a margin of three or more over
+# that window; FIELD_FLOOR (1e-6 on every field) is used for short windows
+# (the first 8 steps of the 1M-node plate, single steps and solves).
+FIELD_FLOOR = 1e-6
+FIELD_FLOORS = {"u": 1e-4, "v": 1e-3, "a": 1e-2, "d": 1e-6, "H": 1e-6}
+STATE_KEYS = ("u", "v", "a", "d", "H")
+
 
 def to_np(t):
     return t.detach().double().cpu().numpy()
@@ -16,6 +39,34 @@ def max_rel(a, b, floor):
     """max |a - b| / max(|b|, floor)"""
     a = np.asarray(a, float); b = np.asarray(b, float)
     return float(np.max(np.abs(a - b) / np.maximum(np.abs(b), floor)))
+
+
+def field_err(g, o, floor_frac=FIELD_FLOOR):
+    """Element-wise relative error of a field against the oracle's:
+    max_i |g_i - o_i| / max(|o_i|, floor_frac * max_j |o_j|).  An all-zero
+    oracle field demands exact zeros."""
+    g = np.asarray(g, float).ravel(); o = np.asarray(o, float).ravel()
+    scale = float(np.abs(o).max()) if o.size else 0.0
+    floor = floor_frac * scale if scale > 0 else np.finfo(float).tiny
+    return float(np.max(np.abs(g - o) / np.maximum(np.abs(o), floor))) if o.size else 0.0
+
+
+def state_errs(g, o, keys=STATE_KEYS, floors=FIELD_FLOORS):
+    """field_err of every state field (GPU tensors or arrays against the
+    oracle's arrays), as a dict; floors: one fraction for every field or a
+    dict per field."""
+    out = {}
+    for k in keys:
+        gk = g[k]
+        gk = to_np(gk) if hasattr(gk, "detach") else np.asarray(gk, float)
+        out[k] = field_err(gk, o[k], floors[k] if isinstance(floors, dict) else floors)
+    return out
+
+
+def merge_worst(worst, errs):
+    for k, v in errs.items():
+        worst[k] = max(worst.get(k, 0.0), v)
+    return worst
 
 
 def state_to_torch(st, dtype, device="cuda"):

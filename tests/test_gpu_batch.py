@@ -79,3 +79,49 @@ def test_batch_fp32_vs_oracle(orc, pff):
         v = b.plate(st, k)
         assert rel_l2(to_np(v["u"]), ost["u"]) <= 1e-4, k
         assert np.abs(to_np(v["d"]) - ost["d"]).max() <= 1e-3, k
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_batch_persistent_loop_matches_phases(pff, prec):
+    """The per-plate persistent CG (one cooperative launch, a CTA group per
+    plate iterating to its own stop) against the kernel-per-phase batch
+    loop: the same Jacobi PCG per plate, the dot products' partial sums
+    grouped differently, so iteration counts within one and fields within
+    the rounding of the solve."""
+    import torch
+    plates = _plates()
+    nsteps = 40
+    out = {}
+    for kind in (pff.PFF_CG_PHASES, pff.PFF_CG_PERSISTENT):
+        b = pff.Batch(plates, precision=prec)
+        st = b.new_state()
+        log = torch.zeros(nsteps, len(plates), dtype=torch.int32, device="cuda")
+        b.run(st, nsteps, opts=pff.options(cg_kernel=kind), iters_log=log)
+        torch.cuda.synchronize()
+        assert b.tuning()["persistent_ctas"] >= len(plates)
+        out[kind] = ({k: to_np(v) for k, v in st.items()}, log.cpu().numpy())
+    (a, la), (c, lc) = out[pff.PFF_CG_PHASES], out[pff.PFF_CG_PERSISTENT]
+    assert np.abs(la - lc).max() <= 1
+    tol = 1e-9 if prec == "fp64" else 2e-5
+    assert rel_l2(c["u"], a["u"]) <= tol
+    assert np.abs(c["d"] - a["d"]).max() <= (1e-9 if prec == "fp64" else 1e-4)
+
+
+def test_batch_autotuner_report(pff):
+    import torch
+    plates = _plates()
+    b = pff.Batch(plates, precision="fp32")
+    assert not b.tuning()["tuned"]
+    st = b.new_state()
+    b.run(st, 3)
+    torch.cuda.synchronize()
+    t = b.tuning()
+    assert t["tuned"] and t["cg"] in ("phases", "persistent")
+    assert 1 <= t["force_U"] <= 4 and 1 <= t["rhs_U"] <= 4 and 1 <= t["cg_U"] <= 4
+    assert min(t["ms"]["force"]) > 0 and min(t["ms"]["rhs"]) > 0 and min(t["ms"]["cg_phases"]) > 0
+    if t["persistent_ctas"]:
+        assert min(t["ms"]["cg_persistent"]) > 0
+    best = min(t["ms"]["cg_phases"] + [x for x in t["ms"]["cg_persistent"] if x > 0])
+    chosen = (t["ms"]["cg_phases"][t["cg_U"] - 1] if t["cg"] == "phases"
+              else t["ms"]["cg_persistent"][t["cg_U"] - 2])
+    assert chosen == best

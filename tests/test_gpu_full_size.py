@@ -1,10 +1,12 @@
 """Parity at the benchmark sizes, in the configurations the bench times.
 
-* The 1M-node plate (1000 x 1000 cells, jittered, spectral AT2): the first
-  steps in FP64 against the oracle with the oracle forced to the GPU's CG
-  iteration counts (1e-10 relative on every field), and in FP32_MIXED with
-  the bench's options (graph loop, autotuned CG family) against the same
-  oracle state (u relative L2 <= 1e-4, max |d - d_oracle| <= 1e-3).
+* The 1M-node plate (1000 x 1000 cells, jittered): the first 8 steps in FP64
+  against the oracle with the oracle forced to the GPU's CG iteration
+  counts, every entry of every field within 1e-10 (spectral and
+  volumetric-deviatoric AT2); 3 steps of AT1 with the volumetric-deviatoric
+  split and the projected CG at natural stops; FP32_MIXED with the bench's
+  options against the same oracle state (u relative L2 <= 1e-4, max |d -
+  d_oracle| <= 1e-3).
 * The differentiation plate (500 x 500 cells): dL/dGc of a short window in
   FP32 against the oracle's discrete adjoint.
 * The 700 x 700 SENT: one load increment with the tangent CG in FP32 against
@@ -16,7 +18,7 @@ import numpy as np
 import pytest
 
 import pff_synth as S
-from gpu_common import max_rel, rel_l2, to_np
+from gpu_common import FIELD_FLOOR, merge_worst, rel_l2, state_errs, to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -27,37 +29,86 @@ def pff():
     return pff
 
 
-@pytest.fixture(scope="module")
-def plate_1m(orc, pff):
-    """GPU FP64 and the forced-count oracle over the first steps of the
-    1M-node plate; returns the config, dt, oracle state and GPU states."""
+def _fp64_window(orc, pff, c, nsteps, forced_counts=True):
+    """GPU FP64 and the oracle over the first nsteps steps of a plate, step
+    by step: with forced_counts the oracle runs each step's CG for the GPU's
+    iteration count (AT2), else to its own stop.  Returns the worst
+    element-wise error per field over the window, the last states and the
+    GPU's iteration counts."""
     import torch
-    c = S.config("plate_1000x1000")
-    nsteps = 4
+    mat = c["material"]
     gm = pff.Mesh.from_plate(c["mesh"], precision="fp64")
-    dt = gm.set_material(c["material"], c["cfl"])
-    gst = gm.new_state()
-    log = torch.zeros(nsteps, 2, dtype=torch.int32, device="cuda")
+    dt = gm.set_material(mat, c["cfl"])
     opts = pff.options(cg_tol=c["cg_tol"], t_ramp=c["t_ramp"])
-    gm.run(gst, nsteps, opts=opts, iters_log=log)
-    torch.cuda.synchronize()
-    assert gm.sync_status() == 0
-    forced = [int(v) for v in log[:, 0].cpu().numpy()]
+    gst = gm.new_state()
     om = orc.Mesh.from_plate(c["mesh"])
     ost = om.new_state()
-    om.run(c["material"], ost, nsteps, dt, t_ramp=c["t_ramp"], forced=forced)
-    return dict(c=c, dt=dt, nsteps=nsteps, ost=ost, g64={k: to_np(v) for k, v in gst.items()}, forced=forced)
+    log = torch.zeros(nsteps, 2, dtype=torch.int32, device="cuda")
+    worst, oiters = {}, []
+    for n in range(nsteps):
+        gm.run(gst, 1, step0=n, opts=opts, iters_log=log[n:n + 1])
+        torch.cuda.synchronize()
+        forced = [int(log[n, 0])] if forced_counts else None
+        r = om.run(mat, ost, 1, dt, n0=n, t_ramp=c["t_ramp"], forced=forced)
+        oiters.append(int(r["iters"][0, 0]))
+        merge_worst(worst, state_errs(gst, ost, floors=FIELD_FLOOR))  # 1e-6 on every field
+    assert gm.sync_status() == 0
+    return dict(c=c, dt=dt, nsteps=nsteps, ost=ost, g64={k: to_np(v) for k, v in gst.items()},
+                worst=worst, iters=[int(v) for v in log[:, 0].cpu().numpy()], oracle_iters=oiters)
+
+
+@pytest.fixture(scope="module")
+def plate_1m(orc, pff):
+    """The bench plate (spectral AT2) over its first 8 steps in FP64."""
+    return _fp64_window(orc, pff, S.config("plate_1000x1000"), 8)
 
 
 def test_fp64_1m_plate_matches_oracle(plate_1m):
-    g, o = plate_1m["g64"], plate_1m["ost"]
+    """Every entry of u, v, a, d and H within 1e-10 of the oracle after each
+    of the first 8 steps (|g - o| / max(|o|, 1e-6 max|o|))."""
+    w = plate_1m["worst"]
+    print(f"1M plate, spectral FP64, 8 steps: element-wise worst {w}, CG iterations {plate_1m['iters']}")
+    assert max(w.values()) <= 1e-10, w
+    g = plate_1m["g64"]
+    assert np.abs(g["u"]).max() > 0 and max(plate_1m["iters"]) > 0  # the window moved and solved
+    assert np.abs(g["H"]).max() > 0
+
+
+def test_fp64_1m_plate_amor_matches_oracle(orc, pff):
+    """The volumetric-deviatoric split (Eq. amor_split) on the 1M-node plate:
+    8 steps in FP64, every entry within 1e-10 of the oracle per step."""
+    r = _fp64_window(orc, pff, S.config("plate_1000x1000", split="amor"), 8)
+    print(f"1M plate, Amor FP64, 8 steps: element-wise worst {r['worst']}, CG iterations {r['iters']}")
+    assert max(r["worst"].values()) <= 1e-10, r["worst"]
+    assert np.abs(r["g64"]["H"]).max() > 0
+
+
+def test_fp64_1m_plate_at1_amor_matches_oracle(orc, pff):
+    """AT1 with the volumetric-deviatoric split and the bound-projected CG
+    (Sec. 2.4) on the 1M-node plate: 3 steps in FP64, GPU and oracle each to
+    its own stop (projected CG restarts are decisions taken on the iterate,
+    so counts are not forced).  Tolerances of the AT1 runs: u within 1e-7
+    relative L2 and entry by entry 1e-7, d within 1e-6 absolute; the first
+    solve builds the damage band around the notch."""
+    r = _fp64_window(orc, pff, S.config("plate_1000x1000", split="amor", model="AT1"), 3,
+                     forced_counts=False)
+    g, o = r["g64"], r["ost"]
+    print(f"1M plate, AT1 + Amor FP64, 3 steps: element-wise worst {r['worst']}, "
+          f"GPU iterations {r['iters']}, oracle {r['oracle_iters']}")
+    assert rel_l2(g["u"], o["u"]) <= 1e-7
     for k in ("u", "v", "a", "H"):
-        assert rel_l2(g[k], o[k]) <= 1e-10, k
-    assert max_rel(g["d"], o["d"], 1e-3) <= 1e-10
-    assert np.abs(g["u"]).max() > 0 and max(plate_1m["forced"]) > 0  # the window moved and solved
+        assert r["worst"][k] <= 1e-7, (k, r["worst"])
+    assert np.abs(g["d"] - o["d"]).max() <= 1e-6
+    band = (o["d"] > 0) & (np.asarray(r["c"]["mesh"]["notch"]) == 0)
+    assert band.sum() > 0  # the projected CG built the band around the notch
+    assert np.all(g["d"] >= -1e-15) and np.all(g["d"] <= 1.0)
 
 
 def test_fp32_1m_plate_bench_configuration(pff, plate_1m):
+    """FP32 with the bench's options (graph loop, autotuned CG family, the
+    default element-wise damage operator) against the FP64 oracle state at
+    the end of the window: u relative L2 <= 1e-4, max |d - d_oracle| <=
+    1e-3."""
     import torch
     c = plate_1m["c"]
     gm = pff.Mesh.from_plate(c["mesh"], precision="fp32")
@@ -111,9 +162,9 @@ def test_sent_full_size_increment(pff):
     assert np.abs(out[0][1] - out[1][1]).max() <= 1e-6
 
 
-def test_batch_workload_matches_single_plates(pff):
-    """The bench's 64-plate batch (5.24M nodes): after a few steps the
-    first, smallest and largest plates agree with their single-plate runs."""
+@pytest.fixture(scope="module")
+def batch64(pff):
+    """The bench's 64-plate batch (5.24M nodes, FP32) after 6 steps."""
     import torch
     plates = []
     for dr in S.batch_draws(64, seed=1):
@@ -126,8 +177,17 @@ def test_batch_workload_matches_single_plates(pff):
     b.run(st, nsteps, iters_log=log)
     torch.cuda.synchronize()
     sizes = [p["xy"].shape[0] for p, _ in plates]
-    for k in sorted({0, int(np.argmin(sizes)), int(np.argmax(sizes))}):
-        p, mat = plates[k]
+    picks = sorted({0, int(np.argmin(sizes)), int(np.argmax(sizes))})
+    return dict(plates=plates, b=b, st=st, log=log.cpu().numpy(), nsteps=nsteps, picks=picks)
+
+
+def test_batch_workload_matches_single_plates(pff, batch64):
+    """The first, smallest and largest plates of the batch agree with their
+    single-plate runs."""
+    import torch
+    b, st, nsteps = batch64["b"], batch64["st"], batch64["nsteps"]
+    for k in batch64["picks"]:
+        p, mat = batch64["plates"][k]
         m = pff.Mesh.from_plate(p, precision="fp32")
         m.set_material(mat, 0.5)
         s1 = m.new_state()
@@ -137,4 +197,25 @@ def test_batch_workload_matches_single_plates(pff):
         v = b.plate(st, k)
         assert rel_l2(to_np(v["u"]), to_np(s1["u"])) <= 2e-5, k
         assert np.abs(to_np(v["d"]) - to_np(s1["d"])).max() <= 1e-4, k
-        assert np.abs(log[:, k].cpu().numpy() - l1[:, 0].cpu().numpy()).max() <= 1, k
+        assert np.abs(batch64["log"][:, k] - l1[:, 0].cpu().numpy()).max() <= 1, k
+
+
+def test_batch_workload_matches_oracle(orc, batch64):
+    """The first, smallest and largest plates of the batch (FP32 kernels,
+    FP64-class reductions) against the FP64 oracle run of the same plate,
+    its own Gc, traction and time step: u relative L2 <= 1e-4 and max |d -
+    d_oracle| <= 1e-3 (the FP32 tolerances)."""
+    b, st, nsteps = batch64["b"], batch64["st"], batch64["nsteps"]
+    for k in batch64["picks"]:
+        p, mat = batch64["plates"][k]
+        om = orc.Mesh.from_plate(p)
+        dt = om.stable_dt(mat, 0.5)
+        assert abs(dt - b.info[k]["dt"]) <= 1e-12 * dt, k
+        ost = om.new_state()
+        r = om.run(mat, ost, nsteps, dt)
+        v = b.plate(st, k)
+        eu = rel_l2(to_np(v["u"]), ost["u"])
+        ed = np.abs(to_np(v["d"]) - ost["d"]).max()
+        print(f"batch plate {k} ({om.N} nodes) vs oracle: u rel L2 {eu:.2e}, max|dd| {ed:.2e}")
+        assert eu <= 1e-4 and ed <= 1e-3, (k, eu, ed)
+        assert r["status"] == 0 and batch64["log"][-1, k] > 0, k

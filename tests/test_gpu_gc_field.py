@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 import pff_synth as S
-from gpu_common import max_rel, rel_l2, to_np
+from gpu_common import field_err, merge_worst, rel_l2, state_errs, to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -36,15 +36,13 @@ def test_field_per_step_parity(orc, pff):
     gst = gm.new_state()
     ost = om.new_state()
     log = torch.zeros(nsteps, 2, dtype=torch.int32, device="cuda")
-    worst = 0.0
+    worst = {}
     for n in range(nsteps):
         gm.run(gst, 1, step0=n, iters_log=log[n:n + 1])
         torch.cuda.synchronize()
         om.run(mat, ost, 1, dt, n0=n, forced=[int(log[n, 0])])
-        for k in ("u", "v", "a"):
-            worst = max(worst, rel_l2(to_np(gst[k]), ost[k]))
-        worst = max(worst, max_rel(to_np(gst["d"]), ost["d"], 1e-3))
-        assert worst <= 1e-10, (n, worst)
+        merge_worst(worst, state_errs(gst, ost))
+        assert max(worst.values()) <= 1e-10, (n, worst)
     assert gm.sync_status() == 0
 
 
@@ -93,5 +91,10 @@ def test_field_gradient_matches_oracle(orc, pff, prec, tol):
     gfield = gfield.cpu().numpy()
     ck.close()
     assert abs(gg - g) <= tol * abs(g), (gg, g)
-    assert rel_l2(gfield, ge) <= tol, rel_l2(gfield, ge)
+    # per element: each dL/dGc_e against the oracle's, its error over
+    # max(|o_e|, 1e-3 max|o|) (the adjoint solves stop at 1e-13, so entries
+    # far below the field's scale carry that absolute error)
+    assert field_err(gfield, ge, 1e-3) <= tol, field_err(gfield, ge, 1e-3)
+    print(f"{prec}: dL/dGc_e element-wise error (floor 1e-3 max) {field_err(gfield, ge, 1e-3):.2e}, "
+          f"(floor 1e-6 max) {field_err(gfield, ge):.2e}, rel L2 {rel_l2(gfield, ge):.2e}")
     assert abs(gfield.sum() - gg) <= 1e-9 * abs(gg) + 1e-6 * np.abs(gfield).sum() * (prec == "fp32")

@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 
 import pff_synth as S
-from gpu_common import max_rel, rel_l2, state_to_torch, to_np
+from gpu_common import merge_worst, rel_l2, state_errs, to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -25,7 +25,9 @@ def _setup(pff, orc, name="plate_100x40", split="spectral", model="AT2", prec="f
 
 @pytest.mark.parametrize("split", ["spectral", "amor"])
 def test_fp64_per_step_parity(orc, pff, split):
-    """FP64 fields agree with the oracle to 1e-10 relative after every step;
+    """FP64 fields agree with the oracle to 1e-10 after every step, entry by
+    entry (|g - o| / max(|o|, floor), floors per field from gpu_common:
+    1e-4, 1e-3, 1e-2 of the field's maximum for u, v, a, 1e-6 for d and H);
     the oracle is forced to the GPU's CG iteration count, whose own stop
     decision must be within one iteration."""
     import torch
@@ -35,17 +37,15 @@ def test_fp64_per_step_parity(orc, pff, split):
     gst = gm.new_state()
     ost = om.new_state()
     log = torch.zeros(nsteps, 2, dtype=torch.int32, device="cuda")
-    worst = 0.0
+    worst = {}
     for n in range(nsteps):
         gm.run(gst, 1, step0=n, iters_log=log[n:n + 1])
         torch.cuda.synchronize()
         it = int(log[n, 0])
         r = om.run(mat, ost, 1, dt, n0=n, forced=[it])
-        for k in ("u", "v", "a"):
-            worst = max(worst, rel_l2(to_np(gst[k]), ost[k]))
-        worst = max(worst, max_rel(to_np(gst["d"]), ost["d"], 1e-3))
-        worst = max(worst, rel_l2(to_np(gst["H"]), ost["H"]))
-        assert worst <= 1e-10, (n, worst)
+        merge_worst(worst, state_errs(gst, ost))
+        assert max(worst.values()) <= 1e-10, (n, worst)
+    print(f"fp64 {split} 200 steps, element-wise worst per field: {worst}")
     assert gm.sync_status() == 0
 
 
@@ -161,9 +161,10 @@ def test_autotuner_choice_reported(orc, pff):
 
 @pytest.mark.parametrize("n_sub", [2, 3])
 def test_subcycled_run_per_step_parity(orc, pff, n_sub):
-    """Damage subcycling (Sec. 2.4): FP64 fields within 1e-10 of the oracle
-    after every step of a 60-step window (oracle forced to the GPU's
-    iteration counts); skipped steps log zero iterations and keep d."""
+    """Damage subcycling (Sec. 2.4): FP64 fields within 1e-10 of the oracle,
+    entry by entry, after every step of a 60-step window (oracle forced to
+    the GPU's iteration counts); skipped steps log zero iterations and keep
+    d."""
     import torch
     c, om, gm, dt = _setup(pff, orc)
     mat = c["material"]
@@ -172,7 +173,7 @@ def test_subcycled_run_per_step_parity(orc, pff, n_sub):
     gst = gm.new_state()
     ost = om.new_state()
     log = torch.zeros(nsteps, 2, dtype=torch.int32, device="cuda")
-    worst = 0.0
+    worst = {}
     for n in range(nsteps):
         d_before = to_np(gst["d"]).copy()
         gm.run(gst, 1, step0=n, opts=opts, iters_log=log[n:n + 1])
@@ -181,11 +182,8 @@ def test_subcycled_run_per_step_parity(orc, pff, n_sub):
         om.run(mat, ost, 1, dt, n0=n, forced=[it], n_sub=n_sub)
         if (n + 1) % n_sub:
             assert it == 0 and np.array_equal(to_np(gst["d"]), d_before), n
-        for k in ("u", "v", "a"):
-            worst = max(worst, rel_l2(to_np(gst[k]), ost[k]))
-        worst = max(worst, max_rel(to_np(gst["d"]), ost["d"], 1e-3))
-        worst = max(worst, rel_l2(to_np(gst["H"]), ost["H"]))
-        assert worst <= 1e-10, (n, worst)
+        merge_worst(worst, state_errs(gst, ost))
+        assert max(worst.values()) <= 1e-10, (n, worst)
     assert gm.sync_status() == 0
 
 
@@ -219,8 +217,8 @@ def test_subcycled_fp32_run_in_one_call(orc, pff):
 @pytest.mark.parametrize("split", ["amor", "spectral", "iso"])
 def test_plane_stress_per_step_parity(orc, pff, split):
     """Plane stress (Sec. 2.1 plane assumptions): FP64 fields within 1e-10
-    of the oracle after each of 60 steps (oracle forced to the GPU's
-    iteration counts)."""
+    of the oracle, entry by entry, after each of 60 steps (oracle forced to
+    the GPU's iteration counts)."""
     import torch
     c = S.config("plate_100x40", split=split)
     mat = dict(c["material"], plane="stress")
@@ -232,16 +230,13 @@ def test_plane_stress_per_step_parity(orc, pff, split):
     gst = gm.new_state()
     ost = om.new_state()
     log = torch.zeros(nsteps, 2, dtype=torch.int32, device="cuda")
-    worst = 0.0
+    worst = {}
     for n in range(nsteps):
         gm.run(gst, 1, step0=n, iters_log=log[n:n + 1])
         torch.cuda.synchronize()
         om.run(mat, ost, 1, dt, n0=n, forced=[int(log[n, 0])])
-        for k in ("u", "v", "a"):
-            worst = max(worst, rel_l2(to_np(gst[k]), ost[k]))
-        worst = max(worst, max_rel(to_np(gst["d"]), ost["d"], 1e-3))
-        worst = max(worst, rel_l2(to_np(gst["H"]), ost["H"]))
-        assert worst <= 1e-10, (n, worst)
+        merge_worst(worst, state_errs(gst, ost))
+        assert max(worst.values()) <= 1e-10, (n, worst)
     assert np.abs(to_np(gst["d"])).max() > 0  # the damage field moved
     # the plane matters: a plane-strain run differs
     om2 = orc.Mesh.from_plate(c["mesh"])

@@ -1,11 +1,12 @@
 """GPU explicit step and damage solve vs the FP64 oracle (Secs. 2.2-2.4):
-FP64 fields to 1e-10 relative per step with matched CG iteration counts;
+FP64 fields to 1e-10 entry by entry (each error over max(|o|, 1e-6 max|o|))
+with matched CG iteration counts;
 FP32-with-FP64-reductions error stated against the FP64 oracle."""
 import numpy as np
 import pytest
 
 import pff_synth as S
-from gpu_common import max_rel, rel_l2, state_to_torch, to_np
+from gpu_common import field_err, max_rel, rel_l2, state_to_torch, to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -40,10 +41,14 @@ def test_step_explicit(orc, pff, split, prec):
     gm.step_explicit(gst, (n + 1) * dt, dt)
     torch.cuda.synchronize()
     r = om.run(mat, st, 1, dt, n0=n, damage_on=False)
-    tol = 1e-10 if prec == "fp64" else 2e-5
-    for k in ("u", "v", "a"):
-        assert rel_l2(to_np(gst[k]), st[k]) <= tol, k
-    assert max_rel(to_np(gst["H"]), st["H"], 1e-3 * st["H"].max()) <= tol * 10
+    if prec == "fp64":
+        # entry by entry (floor 1e-6 of each field's largest magnitude)
+        for k in ("u", "v", "a", "H"):
+            assert field_err(to_np(gst[k]), st[k]) <= 1e-10, (k, field_err(to_np(gst[k]), st[k]))
+    else:
+        for k in ("u", "v", "a"):
+            assert rel_l2(to_np(gst[k]), st[k]) <= 2e-5, k
+        assert max_rel(to_np(gst["H"]), st["H"], 1e-3 * st["H"].max()) <= 2e-4
 
 
 @pytest.mark.parametrize("model", ["AT2", "AT1"])
@@ -68,7 +73,7 @@ def test_damage_solve_fp64(orc, pff, model, loop):
     if model == "AT2":
         d, oinfo, rel, st, _ = om.damage_solve(mat, H, dprev, tol=1e-8, forced=info["iters"])
         assert abs(int(oinfo[1]) - info["iters"]) <= 1   # natural stop within one iteration
-        assert max_rel(to_np(dout), d, 1e-3) <= 1e-10
+        assert field_err(to_np(dout), d) <= 1e-10, field_err(to_np(dout), d)
     else:
         d, oinfo, rel, st, _ = om.damage_solve(mat, H, dprev, tol=1e-8)
         assert st == 0
@@ -109,7 +114,7 @@ def test_damage_solve_clamp_and_aliasing(orc, pff):
     dp = torch.tensor(dprev, device="cuda")
     info = gm.damage_solve(torch.tensor(H, device="cuda"), dp, dp)  # in place
     d, *_ = om.damage_solve(mat, H, dprev, tol=1e-8, forced=info["iters"])
-    assert max_rel(to_np(dp), d, 1e-3) <= 1e-10
+    assert field_err(to_np(dp), d) <= 1e-10
     assert np.all(to_np(dp) >= dprev)
 
 
