@@ -78,18 +78,39 @@ def parse():
 # ----------------------------------------------------------------- clocks
 
 class ClockSampler:
-    """Samples nvidia-smi SM clocks and throttle reasons while running."""
+    """Samples the SM clock and the clock-event (throttle) reasons while
+    running: through NVML every millisecond when the bindings load (the
+    timed region of a short run lasts tens of milliseconds), else through
+    nvidia-smi every 100 ms.  Read-only queries."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    # NVML clock-event reason bits
+    BITS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20,
+            "hw_thermal_slowdown": 0x40}
 
     def __init__(self, index):
         self.index = index
         self.proc = None
+        self.nvml = None
         self.lines = []
+        self.samples = []
+        self.stop_flag = False
 
     def start(self):
+        try:
+            import pynvml
+            pynvml.nvmlInit()
+            h = pynvml.nvmlDeviceGetHandleByIndex(self.index)
+            self.nvml = (pynvml, h)
+            self.smax = float(pynvml.nvmlDeviceGetMaxClockInfo(h, pynvml.NVML_CLOCK_SM))
+            self.t = threading.Thread(target=self._poll, daemon=True)
+            self.t.start()
+            return
+        except Exception as e:  # no NVML bindings or library: nvidia-smi
+            self.nvml = None
+            self.nvml_error = f"{type(e).__name__}: {e}"
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
@@ -100,11 +121,34 @@ class ClockSampler:
         except (OSError, ValueError):
             self.proc = None
 
+    def _poll(self):
+        pynvml, h = self.nvml
+        get_reasons = getattr(pynvml, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            pynvml.nvmlDeviceGetCurrentClocksThrottleReasons
+        while not self.stop_flag:
+            try:
+                self.samples.append((float(pynvml.nvmlDeviceGetClockInfo(h, pynvml.NVML_CLOCK_SM)),
+                                     int(get_reasons(h))))
+            except Exception:
+                break
+            time.sleep(0.001)
+
     def _read(self):
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
     def stop(self):
+        if self.nvml is not None:
+            self.stop_flag = True
+            self.t.join(timeout=5)
+            sm = [c for c, _ in self.samples]
+            reasons = sorted({nm for _, r in self.samples for nm, b in self.BITS.items() if r & b})
+            try:
+                self.nvml[0].nvmlShutdown()
+            except Exception:
+                pass
+            return dict(sm_mhz=float(np.median(sm)) if sm else None, sm_max_mhz=self.smax,
+                        reasons=reasons, samples=len(sm), source="nvml, 1 ms")
         if self.proc is None:
             return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"])
         self.proc.terminate()
@@ -127,7 +171,8 @@ class ClockSampler:
                 if v.lower() == "active":
                     reasons.add(nm)
         return dict(sm_mhz=float(np.median(sm)) if sm else None, sm_max_mhz=smax,
-                    reasons=sorted(reasons), samples=len(sm))
+                    reasons=sorted(reasons), samples=len(sm), source="nvidia-smi, 100 ms",
+                    nvml_error=getattr(self, "nvml_error", None))
 
 
 # ------------------------------------------------------------- utilities
@@ -358,14 +403,17 @@ def batched(pff, dev, steps=500, warmup=5):
                 cg_iters_mean=float(it.mean()), cg_iters_max=int(it.max()))
 
 
-def fwd_adjoint(pff, dev, steps=300, policies=(0, 25)):
+def fwd_adjoint(pff, dev, steps=300, policies=((0, "recompute"), (25, "recompute"), (25, "damage_tape"))):
     """Forward + adjoint cost on the differentiation workload: the 500 x 500
     plate (251,001 nodes), FP32 with FP64-class reductions, 300 steps,
     loss = mean((d_T - d*)^2) with d* from Gc* = 3 J/m^2, gradient dL/dGc at
     Gc = 2 (Sec. 4.1-4.2).  Each tape policy is timed: every = 0 tapes the
     whole run in the forward (Sec. 7, the activation tape kept on the GPU);
-    every = 25 keeps checkpoints and recomputes each segment.  The ratio
-    divides by a plain forward run (pff_run, no tape) of the same steps."""
+    every = 25 keeps checkpoints and recomputes each segment, in full
+    ("recompute", damage solves included) or its mechanics only
+    ("damage_tape": the forward also tapes each step's unclamped damage
+    solution, one value per node and step).  The ratio divides by a plain
+    forward run (pff_run, no tape) of the same steps."""
     import torch
     c = S.config("plate_500x500")
     mesh = pff.Mesh.from_plate(c["mesh"], precision="fp32")
@@ -396,12 +444,16 @@ def fwd_adjoint(pff, dev, steps=300, policies=(0, 25)):
     t_plain = e0.elapsed_time(e1) / 1e3
     out = dict(workload="plate_500x500", nodes=mesh.N, steps=steps,
                fwd_s_per_step=t_plain / steps, fwd_cg_iters_mean=float(log[:, 0].float().mean()))
-    for every in policies:
-        ck = pff.Checkpoint(mesh, steps, every)
+    for every, policy in policies:
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        ck = pff.Checkpoint(mesh, steps, every, policy)
+        torch.cuda.synchronize()
+        store_bytes = free0 - torch.cuda.mem_get_info()[0]
         # warm-up: graphs, autotuner, the backward's graphs and the torch ops
         # of the loss gradient (their first use loads kernels)
         w = mesh.new_state(device=dev)
-        ckw = pff.Checkpoint(mesh, 3, min(every, 3))
+        ckw = pff.Checkpoint(mesh, 3, min(every, 3), policy)
         mesh.run_ckpt(w, ckw, opts=opts)
         gw = (2.0 * (w["d"].double() - dstar.double()) / mesh.N).float().contiguous()
         mesh.backward(ckw, gw, opts=opts)
@@ -419,10 +471,12 @@ def fwd_adjoint(pff, dev, steps=300, policies=(0, 25)):
         tf = e0.elapsed_time(e1) / 1e3
         tb = e1.elapsed_time(e2) / 1e3
         loss = float(torch.mean((d.double() - dstar.double()) ** 2))
-        out["full_tape" if every == 0 else f"ckpt_every_{every}"] = dict(
+        name = "full_tape" if every == 0 else (f"ckpt_every_{every}" if policy == "recompute"
+                                                else f"ckpt_every_{every}_damage_tape")
+        out[name] = dict(
             fwd_taped_s_per_step=tf / steps, bwd_s_per_step=tb / steps,
             fwd_adj_s_per_step=(tf + tb) / steps, ratio=(tf + tb) / t_plain, loss=loss, dL_dGc=g,
-            adjoint_cg_iters_mean=ck.adjoint_iters() / steps)
+            adjoint_cg_iters_mean=ck.adjoint_iters() / steps, store_bytes=int(store_bytes))
         ck.close()
     return out
 
@@ -639,8 +693,8 @@ def inversion(pff, dev, steps=300, gcs=(2.0, 2.5, 3.5), gc_star=3.0, max_states=
         L = inverse.mse_loss(inverse.final_damage(g, mesh, mat, steps, 0, opts), dstar)
         if grad:
             L.backward()
-            return float(L), float(g.grad)
-        return float(L), None
+            return float(L.detach()), float(g.grad)
+        return float(L.detach()), None
 
     grads = []
     for gc in gcs:

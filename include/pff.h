@@ -128,6 +128,12 @@ typedef struct {
                            See pff_subcycling_limit for the admissible value.
                            Not supported by pff_run_ckpt / pff_batch_run
                            (PFF_ERR_ARG). */
+  int32_t fuse;         /* a step's internal force and damage right-hand
+                           side: 0 = one fused kernel if the autotuner timed
+                           it faster than the two, 1 = two kernels, 2 = the
+                           fused kernel (same results either way: each
+                           element's history max is taken the way the force
+                           kernel stores it) [0] */
 } pff_options;
 
 /* Device state of one plate (caller-owned). */
@@ -312,6 +318,19 @@ pff_status pff_run(pff_mesh *mesh, const pff_state *state, int64_t step0,
  *   PFF_ERR_NOT_CONVERGED / PFF_ERR_NONFINITE from an adjoint solve. */
 typedef struct pff_ckpt pff_ckpt;
 pff_status pff_ckpt_create(pff_mesh *mesh, int64_t nsteps, int32_t every, pff_ckpt **out);
+/* pff_ckpt_create with a choice of what a checkpointed store (every > 0)
+ * keeps between its segment checkpoints:
+ *  PFF_CKPT_RECOMPUTE: nothing; the backward recomputes each segment in
+ *    full, damage solves included (what pff_ckpt_create does);
+ *  PFF_CKPT_DAMAGE_TAPE: the unclamped damage solution x_{n+1} of every
+ *    step (nsteps x N values of the mesh precision, an eighth of the full
+ *    tape in FP32); the backward recomputes each segment's mechanics only
+ *    (predictor, force with history and corrector, then the clamp of the
+ *    taped x, bit-identical to the forward) and no damage solve.
+ * Ignored for every = 0 (the full tape).  PFF_ERR_ARG for another policy. */
+enum { PFF_CKPT_RECOMPUTE = 0, PFF_CKPT_DAMAGE_TAPE = 1 };
+pff_status pff_ckpt_create_policy(pff_mesh *mesh, int64_t nsteps, int32_t every, int32_t policy,
+                                  pff_ckpt **out);
 void pff_ckpt_destroy(pff_ckpt *ckpt);
 /* Total adjoint CG iterations of the last pff_backward on this store. */
 pff_status pff_ckpt_stats(const pff_ckpt *ckpt, int64_t *adjoint_iters);
@@ -397,11 +416,12 @@ pff_status pff_energies(pff_mesh *mesh, const pff_state *state, double *out,
  * AT2 solve runs as one persistent launch (pff_mesh_cg_choice),
  * ms_out[7] = that launch after one mechanics step, ms_out[8] = its CG
  * iterations, ms_out[9] = its family (0 phases, 1 persistent, 2 staged,
- * 3 fused, 4 fused staged; ms_out[7..8] = 0 for phases).  Every timed
- * launch is preceded by a write larger than L2 and bracketed by CUDA events
- * on `stream`; reps launches per kernel.  It OVERWRITES the state and the
- * solve workspace (call it after the run whose numbers you need).
- * Synchronises the stream.  ms_out holds 10 doubles. */
+ * 3 fused, 4 fused staged; ms_out[7..8] = 0 for phases); ms_out[10] = the
+ * fused force and right-hand-side kernel, ms_out[11] = 1 if steps use it.
+ * Every timed launch is preceded by a write larger than L2 and bracketed
+ * by CUDA events on `stream`; reps launches per kernel.  It OVERWRITES the
+ * state and the solve workspace (call it after the run whose numbers you
+ * need).  Synchronises the stream.  ms_out holds 12 doubles. */
 pff_status pff_profile_kernels(pff_mesh *mesh, const pff_state *state, double dt,
                                const pff_options *opt, int32_t reps, double *ms_out,
                                pff_stream stream);

@@ -60,7 +60,7 @@ class pff_options(C.Structure):
                 ("max_restarts", C.c_int32), ("t_ramp", C.c_double),
                 ("energy_every", C.c_int32), ("ckpt_every", C.c_int32),
                 ("block", C.c_int32), ("loop_mode", C.c_int32), ("variant", C.c_int32),
-                ("cg_kernel", C.c_int32), ("damage_every", C.c_int32)]
+                ("cg_kernel", C.c_int32), ("damage_every", C.c_int32), ("fuse", C.c_int32)]
 
 
 class pff_qs_options(C.Structure):
@@ -104,6 +104,7 @@ _sig = {
     "pff_mesh_cg_choice": [_P, _P, _P, _P],
     "pff_subcycling_limit": [C.POINTER(pff_material), C.POINTER(C.c_double), C.POINTER(C.c_int32)],
     "pff_ckpt_create": [_P, C.c_int64, C.c_int32, C.POINTER(C.c_void_p)],
+    "pff_ckpt_create_policy": [_P, C.c_int64, C.c_int32, C.c_int32, C.POINTER(C.c_void_p)],
     "pff_ckpt_destroy": [_P],
     "pff_ckpt_stats": [_P, C.POINTER(C.c_int64)],
     "pff_run_ckpt": [_P, C.POINTER(pff_state), C.c_int64, C.c_int64, C.c_double,
@@ -160,9 +161,11 @@ def _stream(stream=None):
 
 def options(cg_tol=1e-8, cg_max_it=10000, max_restarts=50, t_ramp=0.05e-6, energy_every=0,
             ckpt_every=25, block=0, loop_mode=PFF_LOOP_GRAPH, variant=0, cg_kernel=PFF_CG_AUTO,
-            damage_every=0):
+            damage_every=0, fuse=0):
+    """pff_options; fuse: 0 autotuned, 1 separate force and right-hand-side
+    kernels, 2 the fused kernel."""
     return pff_options(cg_tol, cg_max_it, max_restarts, t_ramp, energy_every, ckpt_every,
-                       block, loop_mode, variant, cg_kernel, damage_every)
+                       block, loop_mode, variant, cg_kernel, damage_every, fuse)
 
 
 def qs_options(newton_tol=1e-8, newton_max=25, krylov="fp32", eta_min=None, eta_max=0.5,
@@ -294,11 +297,16 @@ class Checkpoint:
     """pff_ckpt: the tape of a run of nsteps steps, consumed by Mesh.backward.
     every = 0 tapes every step during the forward (no recompute); every > 0
     keeps checkpoints at segment starts and recomputes each segment in the
-    backward."""
+    backward: in full ("recompute"), or only its mechanics, the forward
+    having taped each step's unclamped damage solution ("damage_tape")."""
 
-    def __init__(self, mesh, nsteps, every=25):
+    POLICIES = {"recompute": 0, "damage_tape": 1}
+
+    def __init__(self, mesh, nsteps, every=25, policy="recompute"):
         h = C.c_void_p()
-        _check(_lib.pff_ckpt_create(mesh._h, int(nsteps), int(every), C.byref(h)))
+        _check(_lib.pff_ckpt_create_policy(mesh._h, int(nsteps), int(every), self.POLICIES[policy],
+                                           C.byref(h)))
+        self.policy = policy
         self._h = h
         self.mesh = mesh
         self.nsteps = int(nsteps)
@@ -535,13 +543,15 @@ class Mesh:
         flushed before every launch).  Overwrites the state."""
         s = self._state(st)
         o = opts or options()
-        out = np.zeros(10)
+        out = np.zeros(12)
         _check(_lib.pff_profile_kernels(self._h, C.byref(s), float(dt or self.dt), C.byref(o),
                                         int(reps), _hp(out), _stream(stream)))
         d = dict(zip(self.KERNELS, out[:7].tolist()))
         d["cg_loop"] = float(out[7])          # one persistent CG launch (0: kernel per phase)
         d["cg_loop_iters"] = int(out[8])
         d["cg_loop_family"] = ("phases", "persistent", "staged", "fused", "fused_staged")[int(out[9])]
+        d["force_rhs"] = float(out[10])        # the fused force and right-hand-side kernel
+        d["force_rhs_used"] = bool(out[11])
         return d
 
     def energies(self, st, stream=None):

@@ -32,6 +32,8 @@ template <typename R> struct AdjParams {
   const R *snap_d;
   const double *snap_H;
   int32_t stride_n, stride_e;  // slot strides (elements of R2/R, doubles)
+  const int64_t *x_base;       // nullable: tape_x holds the whole run, slot k of
+                               // this segment at *x_base + k (damage-tape policy)
   R *Hcur;                     // H_{n+1} in the kernel precision (operator)
   int32_t h_tape;              // 1: k_adj_rhs reads H_{n+1} from the tape (no Hcur)
   // adjoint state (in: step n+1, out: step n)
@@ -60,7 +62,7 @@ __device__ __forceinline__ Slot<R> slot(const AdjParams<R> &A) {
   const int k = *A.kctr;
   Slot<R> s;
   s.u1 = A.tape_u + (size_t)k * A.stride_n;
-  s.x1 = A.tape_x + (size_t)k * A.stride_n;
+  s.x1 = A.tape_x + (size_t)((A.x_base ? *A.x_base : 0) + k) * A.stride_n;
   s.H1 = A.tape_H + (size_t)k * A.stride_e;
   s.d0 = k > 0 ? A.tape_d + (size_t)(k - 1) * A.stride_n : A.snap_d;
   s.H0 = k > 0 ? A.tape_H + (size_t)(k - 1) * A.stride_e : A.snap_H;

@@ -1009,18 +1009,15 @@ __global__ void __launch_bounds__(256) k_drec_build(Params<R> P) {
 // x0 = d_prev (1 on the notch).
 // With cf, a merging pass's entry coefficients are returned there instead
 // of written to the entry records.
+// rhs_entry's arithmetic on an element already loaded (t, A, G), its
+// history h in the kernel precision and toughness scale sg (the fused
+// force and right-hand-side kernel calls this directly).
 template <typename R>
-__device__ __forceinline__ typename Params<R>::R4 rhs_entry(const Params<R> &P, int en, int slot = -1,
-                                                            int node = -1, int csr = -1,
-                                                            typename Params<R>::R2 *cf = nullptr) {
+__device__ __forceinline__ typename Params<R>::R4 rhs_entry_core(const Params<R> &P, int e, int a, const int4 &t,
+                                                                 R A, const typename Params<R>::R4 &G, R h, R sg,
+                                                                 int slot, int node, int csr,
+                                                                 typename Params<R>::R2 *cf) {
   typedef typename Params<R>::R4 R4;
-  const int e = en >> 2, a = en & 3;
-  int4 t;
-  R A;
-  R4 G;
-  load_elem(P, e, t, A, G);
-  const R h = P.Hr[e];
-  const R sg = gc_scale(P, e);
   const R w = P.wbase * sg + R(2) * h;
   const bool n0 = P.flags[t.x] & kNotch, n1 = P.flags[t.y] & kNotch, n2 = P.flags[t.z] & kNotch;
   const R x0 = n0 ? R(1) : P.dprev[t.x];
@@ -1048,6 +1045,19 @@ __device__ __forceinline__ typename Params<R>::R4 rhs_entry(const Params<R> &P, 
   o.w = (n0 || n1 || n2) ? elem_row<R>(G, a, kA, mA, n0 ? R(1) : R(0), n1 ? R(1) : R(0), n2 ? R(1) : R(0))
                          : R(0);
   return o;
+}
+
+template <typename R>
+__device__ __forceinline__ typename Params<R>::R4 rhs_entry(const Params<R> &P, int en, int slot = -1,
+                                                            int node = -1, int csr = -1,
+                                                            typename Params<R>::R2 *cf = nullptr) {
+  typedef typename Params<R>::R4 R4;
+  const int e = en >> 2, a = en & 3;
+  int4 t;
+  R A;
+  R4 G;
+  load_elem(P, e, t, A, G);
+  return rhs_entry_core<R>(P, e, a, t, A, G, P.Hr[e], gc_scale(P, e), slot, node, csr, cf);
 }
 
 // Node i of the right-hand side: r = b - A x0, b_eff = b - A 1_D, the
@@ -1192,6 +1202,96 @@ __global__ void __launch_bounds__(256) k_dmg_rhs_nc(Params<R> P) {
     }
     rhs_node(P, i, bi, dg, ax, a1, vals);
     if (merge) nacc.store(P, i);
+  }
+  __shared__ double tot[3];
+  if (reduce_last<R, 3>(vals, P.part, P.ticket, tot) && threadIdx.x == 0) rhs_finish(P, tot);
+}
+
+// Force and damage right-hand side in one pass (node-centric, U entries in
+// flight): per incidence entry the element's strain, split, degraded stress
+// and psi+ (force_entry's arithmetic), the history H_{n+1} = max(H_n, psi+)
+// that the entry's element will hold after this pass, and the damage
+// right-hand side's terms from that history (rhs_entry's arithmetic on the
+// element already loaded); per node the corrector and the solve's set-up
+// (rhs_node), per block the reductions of the set-up.  Results are those
+// of the force kernel followed by the right-hand-side kernel: the history
+// each thread uses is max(H_n, psi+) taken the way history_update takes it,
+// whether or not the element's owner entry has already stored it (max is
+// idempotent), so no thread depends on another's write.
+template <typename R>
+__device__ __forceinline__ void force_rhs_entry(const Params<R> &P, int en, int slot, int node, R &fx, R &fy, R &psip,
+                                                typename Params<R>::R4 &o, typename Params<R>::R2 *cf) {
+  typedef typename Params<R>::R4 R4;
+  const int e = en >> 2, a = en & 3;
+  int4 t;
+  R A;
+  R4 G;
+  load_elem(P, e, t, A, G);
+  R exx, eyy, exy;
+  elem_strain(P, G, t, exx, eyy, exy);
+  const R db = (P.d[t.x] + P.d[t.y] + P.d[t.z]) * (R(1) / R(3));
+  const R g = (R(1) - db) * (R(1) - db) + P.eta;
+  R sxx, syy, sxy;
+  stress(P, exx, eyy, exy, g, sxx, syy, sxy, psip);
+  R gx, gy;
+  slot_grad<R>(G, a, gx, gy);
+  slot_force(A, sxx, syy, sxy, gx, gy, fx, fy);
+  R h;
+  if constexpr (sizeof(R) == 8) {
+    const double ho = P.H[e], hp = (double)psip;
+    h = hp > ho ? hp : ho;
+  } else {
+    const long long pb = f2d_bits((float)psip);
+    const long long hb = __double_as_longlong(P.H[e]);
+    h = pb > hb ? (float)psip : (float)__longlong_as_double(hb);
+  }
+  o = rhs_entry_core<R>(P, e, a, t, A, G, h, gc_scale(P, e), slot, node, -1, cf);
+}
+
+template <typename R, int U>
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 1) k_force_rhs_nc(Params<R> P) {
+  typedef typename Params<R>::R4 R4;
+  typedef Acc<R> AC;
+  typename AC::T vals[3] = {AC::zero(), AC::zero(), AC::zero()};
+  const double S = load_scale(P, 1);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.N; i += gridDim.x * blockDim.x) {
+    const bool notch = P.flags[i] & kNotch;
+    const bool merge = !notch && nb_merging(P);
+    R fx = 0, fy = 0, bi = 0, dg = 0, ax = 0, a1 = 0;
+    NbAcc<R> nacc;
+    nacc.zero();
+    if (merge) nacc.load_map(P, i);
+    for (int k = 0; k < P.D; k += U) {
+      int en[U];
+      R cx[U], cy[U], pp[U];
+      R4 o[U];
+      typename Params<R>::R2 cf[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) en[u] = k + u < P.D ? __ldg(&P.ell[(size_t)(k + u) * P.N + i]) : -1;
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (en[u] >= 0)  // a notch row has no damage row: only the element records are written
+          force_rhs_entry(P, en[u], notch ? -1 : k + u, i, cx[u], cy[u], pp[u], o[u], merge ? &cf[u] : nullptr);
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (en[u] >= 0) {
+          fx = radd(fx, cx[u]);
+          fy = radd(fy, cy[u]);
+          history_update(P, en[u], pp[u]);
+          bi = radd(bi, o[u].x);
+          dg = radd(dg, o[u].y);
+          ax = radd(ax, o[u].z);
+          a1 = radd(a1, o[u].w);
+          if (merge) nacc.add(k + u, cf[u]);
+        }
+    }
+    corrector(P, i, fx, fy, S);
+    if (notch) {
+      rhs_notch_node(P, i);
+    } else {
+      rhs_node(P, i, bi, dg, ax, a1, vals);
+      if (merge) nacc.store(P, i);
+    }
   }
   __shared__ double tot[3];
   if (reduce_last<R, 3>(vals, P.part, P.ticket, tot) && threadIdx.x == 0) rhs_finish(P, tot);

@@ -305,6 +305,7 @@ struct pff_mesh {
   unsigned grid[16][8] = {{0}};
   size_t smem[16][8] = {{0}};
   int32_t var[16] = {0};       // schedule variant in use per kernel
+  bool fuse_rhs = false;       // the autotuner's choice: force and right-hand side in one kernel
   int32_t tuned_var[16] = {0}; // autotuner's choice
   bool tuned[16] = {false};
   float tune_ms[16][8] = {{0}};
@@ -370,14 +371,14 @@ static unsigned stride_cap() {
 }
 
 enum KernelId { KP_PREDICT = 0, KP_FORCE, KP_RHS, KP_MATVEC, KP_UPDATE, KP_FINISH, KP_RESTART, KP_ENERGIES,
-                KP_COUNT };
+                KP_FRHS, KP_COUNT };
 constexpr int kThreads = 256;
 // Schedule variants of the gather kernels (force, rhs, matvec):
 // 0 = entry-parallel node blocks (force: an element pass, then a node
 // gather), 1..4 = node-centric with U = 1..4 gathers in flight.  All
 // variants sum each row in the same order (bit-identical in FP32).
 constexpr int kNumVariants = 5;
-static inline bool tunable(int id) { return id == KP_FORCE || id == KP_RHS || id == KP_MATVEC; }
+static inline bool tunable(int id) { return id == KP_FORCE || id == KP_RHS || id == KP_MATVEC || id == KP_FRHS; }
 
 template <typename R>
 static const void *kfun(int id, int v) {
@@ -410,6 +411,13 @@ static const void *kfun(int id, int v) {
     case KP_UPDATE: return (const void *)k_cg_update<R>;
     case KP_FINISH: return (const void *)k_dmg_finish<R>;
     case KP_RESTART: return (const void *)k_at1_restart<R>;
+    case KP_FRHS:  // force and damage right-hand side fused (node-centric only)
+      switch (v) {
+        case 1: return (const void *)k_force_rhs_nc<R, 1>;
+        case 3: return (const void *)k_force_rhs_nc<R, 3>;
+        case 4: return (const void *)k_force_rhs_nc<R, 4>;
+        default: return (const void *)k_force_rhs_nc<R, 2>;
+      }
     default: return (const void *)k_energies<R>;
   }
 }
@@ -498,6 +506,16 @@ static CgPlan cg_plan(const pff_mesh *m, const pff_options &o, int model, bool f
   }
   if (p.grid == 0 || 2.0 * ((double)o.cg_max_it + 3.0) * p.grid >= 2147483648.0) p = CgPlan();
   return p;
+}
+
+// Whether a step's force and damage right-hand side run as one kernel:
+// forced by opt->fuse (1 separate, 2 fused), else the autotuner's timing.
+// The staged CG families take a right-hand side without entry records and
+// keep the separate kernels.
+static inline bool use_fused(const pff_mesh *m, const pff_options &o, const CgPlan &plan) {
+  if (plan.st() || o.fuse == 1) return false;
+  if (o.fuse == 2) return true;
+  return m->fuse_rhs && m->tuned[KP_FRHS];
 }
 
 template <typename R>
@@ -874,7 +892,7 @@ static pff_status configure(pff_mesh *m) {
   m->nblk = (int32_t)((m->N + NB - 1) / NB);
   if (!m->fe) PFF_TRY(dalloc((typename V<R>::T2 **)&m->fe, 3 * (size_t)m->Ne));
   const size_t sm_ep[KP_COUNT] = {0, 0, maxE * sizeof(typename V<R>::T4),
-                                  maxE * sizeof(R), 0, 0, maxE * sizeof(R), 0};
+                                  maxE * sizeof(R), 0, 0, maxE * sizeof(R), 0, 0};
   int dev = 0, nsm = 0;
   CUDA_TRY(cudaGetDevice(&dev));
   CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -882,7 +900,7 @@ static pff_status configure(pff_mesh *m) {
     const int nv = tunable(id) ? kNumVariants : 1;
     for (int v = 0; v < nv; ++v) {
       const void *f = kfun<R>(id, v);
-      const size_t sm = (v == 0) ? sm_ep[id] : 0;
+      const size_t sm = (v == 0 && id != KP_FRHS) ? sm_ep[id] : 0;
       if (sm > 0) CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
       int occ = 0;
       CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f, kThreads, sm));
@@ -1114,7 +1132,7 @@ static pff_status add_while(cudaGraph_t g, const std::vector<cudaGraphNode_t> &d
 // for a persistent solve, which needs none.
 template <typename R>
 static pff_status append_solve(const pff_mesh *m, cudaGraph_t g, cudaGraphNode_t dep, Params<R> &P,
-                               const CgPlan &plan, cudaGraphNode_t *last) {
+                               const CgPlan &plan, cudaGraphNode_t *last, bool rhs_done = false) {
   std::vector<cudaGraphNode_t> d;
   if (dep) d.push_back(dep);
   cudaGraphNode_t n_rhs, n_loop, n_fin;
@@ -1128,7 +1146,10 @@ static pff_status append_solve(const pff_mesh *m, cudaGraph_t g, cudaGraphNode_t
     Pr.nbc = nullptr;
     Pr.diag = nullptr;
   }
-  PFF_TRY(add_kernel<R>(m, g, d, KP_RHS, Pr, &n_rhs));
+  if (rhs_done)  // the fused force kernel set the solve up
+    n_rhs = dep;
+  else
+    PFF_TRY(add_kernel<R>(m, g, d, KP_RHS, Pr, &n_rhs));
   if (plan.pers()) {
     PFF_TRY(add_pers<R>(m, plan, g, {n_rhs}, P, &n_loop));
   } else if (P.model == kAT1) {
@@ -1170,14 +1191,15 @@ __global__ void k_read_flush(const float4 *buf, size_t n, float *sink) {
 template <typename R>
 static pff_status autotune(pff_mesh *m, const pff_options &o, Params<R> P, bool with_force, bool with_damage,
                            cudaStream_t s) {
-  const int ids[3] = {KP_FORCE, KP_RHS, KP_MATVEC};
+  const int ids[4] = {KP_FORCE, KP_RHS, KP_MATVEC, KP_FRHS};
   if (o.variant > 0) {
     for (int id : ids) m->var[id] = std::min(o.variant - 1, kNumVariants - 1);
     return PFF_OK;
   }
   bool need = false;
   for (int id : ids)
-    if (!m->tuned[id] && (id == KP_FORCE ? with_force : with_damage)) need = true;
+    if (!m->tuned[id] && (id == KP_FORCE ? with_force : id == KP_FRHS ? with_force && with_damage : with_damage))
+      need = true;
   if (!need) {
     for (int id : ids)
       if (m->tuned[id]) m->var[id] = m->tuned_var[id];
@@ -1259,8 +1281,19 @@ static pff_status autotune(pff_mesh *m, const pff_options &o, Params<R> P, bool 
     Q.S_next = 1.0;
     Q.step_ctr = nullptr;
     res = time_variants(KP_FORCE, Q);
+    // the force and right-hand side in one kernel, on the same scratch state
+    if (res == PFF_OK && with_damage && !m->tuned[KP_FRHS]) res = time_variants(KP_FRHS, Q);
   }
   if (res == PFF_OK && with_damage && !m->tuned[KP_RHS]) res = time_variants(KP_RHS, P);
+  if (m->tuned[KP_FORCE] && m->tuned[KP_RHS] && m->tuned[KP_FRHS]) {
+    float bf = 1e30f, br = 1e30f, bfr = 1e30f;
+    for (int v = 0; v < kNumVariants; ++v) {
+      bf = std::min(bf, m->tune_ms[KP_FORCE][v]);
+      br = std::min(br, m->tune_ms[KP_RHS][v]);
+      bfr = std::min(bfr, m->tune_ms[KP_FRHS][v]);
+    }
+    m->fuse_rhs = bfr < bf + br;
+  }
   if (res == PFF_OK && with_damage && !m->tuned[KP_MATVEC]) {
     res = launch<R>(m, KP_RHS, P, s);  // a fresh right-hand side sets up z, p and beta = 0
     if (res == PFF_OK) res = time_variants(KP_MATVEC, P);
@@ -1390,10 +1423,11 @@ static pff_status autotune(pff_mesh *m, const pff_options &o, Params<R> P, bool 
 
 // Host-polled variant of the same solve (debugging / PFF_LOOP_HOST).
 template <typename R>
-static pff_status solve_host_loop(const pff_mesh *m, Params<R> P, const CgPlan &plan, cudaStream_t s) {
+static pff_status solve_host_loop(const pff_mesh *m, Params<R> P, const CgPlan &plan, cudaStream_t s,
+                                  bool rhs_done = false) {
   P.use_cond = 0;
   SolveScalars hs;
-  PFF_TRY(launch<R>(m, KP_RHS, P, s));
+  if (!rhs_done) PFF_TRY(launch<R>(m, KP_RHS, P, s));
   if (plan.pers()) {
     PFF_TRY(launch_pers<R>(m, plan, P, s));
   } else if (P.model == kAT1) {
@@ -1504,27 +1538,58 @@ static pff_status step_explicit_t(pff_mesh *m, const pff_state *st, double t_nex
 
 // Per-step tape of a recomputed segment (the adjoint's inputs): slot k
 // receives u_{n+1}, the unclamped damage solution x_{n+1}, d_{n+1} and
-// H_{n+1} of the segment's k-th step.
+// H_{n+1} of the segment's k-th step.  Null arrays are not taped; with
+// base, the slot is *base + k (a tape of the whole run, filled segment by
+// segment).
 struct Tape {
   void *u, *x, *d;
   double *H;
   int64_t stride_n, stride_e;
+  const int64_t *base;
 };
 
 template <typename R>
 __global__ void __launch_bounds__(256) k_tape_store(Params<R> P, Tape T) {
   typedef typename V<R>::T2 R2;
-  const int64_t k = *P.step_ctr - 1;  // the step just finished
-  R2 *tu = (R2 *)T.u + k * T.stride_n;
-  R *tx = (R *)T.x + k * T.stride_n, *td = (R *)T.d + k * T.stride_n;
-  double *tH = T.H + k * T.stride_e;
+  const int64_t k = *P.step_ctr - 1 + (T.base ? *T.base : 0);  // the step just finished
+  R2 *tu = T.u ? (R2 *)T.u + k * T.stride_n : nullptr;
+  R *tx = T.x ? (R *)T.x + k * T.stride_n : nullptr;
+  R *td = T.d ? (R *)T.d + k * T.stride_n : nullptr;
+  double *tH = T.H ? T.H + k * T.stride_e : nullptr;
   const int stride = gridDim.x * blockDim.x;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.N; i += stride) {
-    tu[i] = P.u[i];
-    tx[i] = P.x[i];
-    td[i] = P.d[i];
+    if (tu) tu[i] = P.u[i];
+    if (tx) tx[i] = P.x[i];
+    if (td) td[i] = P.d[i];
   }
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < P.Ne; e += stride) tH[e] = P.H[e];
+  if (tH)
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < P.Ne; e += stride) tH[e] = P.H[e];
+}
+
+// The clamp of Sec. 2.4 (k_dmg_finish's arithmetic, AT2) applied to the
+// unclamped solution taped by the forward run instead of a fresh solve:
+// the mechanics-only recompute of the damage-tape checkpoint policy.
+// Slot *base + step of the run's tape; advances the step counter.
+template <typename R>
+__global__ void __launch_bounds__(256) k_finish_tape(Params<R> P, const R *tx, int64_t stride, const int64_t *base) {
+  const R *x = tx + (*P.step_ctr + *base) * stride;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.N; i += gridDim.x * blockDim.x) {
+    R v;
+    if (P.flags[i] & kNotch) {
+      v = R(1);
+    } else {
+      v = x[i];
+      const R lo = P.dprev[i];
+      v = v > lo ? v : lo;
+      v = v < R(1) ? v : R(1);
+    }
+    P.dout[i] = v;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && P.step_inc) *P.step_inc += 1;
+}
+
+__global__ void k_set_i64(int64_t *p, int64_t v) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *p = v;
 }
 
 template <typename R>
@@ -1565,6 +1630,7 @@ static pff_status run_t(pff_mesh *m, const pff_state *st, int64_t step0, int64_t
   PFF_TRY(autotune<R>(m, o, P, true, true, s));
   const CgPlan plan = cg_plan(m, o, P.model, sizeof(R) == 4);
   const bool pers = plan.pers();
+  const bool fused = use_fused(m, o, plan);
   const int64_t zero = 0;
   CUDA_TRY(cudaMemcpyAsync(m->step_ctr, &zero, sizeof(int64_t), cudaMemcpyHostToDevice, s));
   CUDA_TRY(cudaStreamSynchronize(s));
@@ -1577,11 +1643,16 @@ static pff_status run_t(pff_mesh *m, const pff_state *st, int64_t step0, int64_t
   if (o.loop_mode == PFF_LOOP_HOST) {
     for (int64_t n = 0; n < nsteps; ++n) {
       PFF_TRY(launch<R>(m, KP_PREDICT, P, s));
-      PFF_TRY(launch<R>(m, KP_FORCE, P, s));
-      if (solves(n))
-        PFF_TRY(solve_host_loop<R>(m, P, plan, s));
-      else
-        k_step_skip<R><<<1, 32, 0, s>>>(P);
+      if (solves(n) && fused) {
+        PFF_TRY(launch<R>(m, KP_FRHS, P, s));
+        PFF_TRY(solve_host_loop<R>(m, P, plan, s, true));
+      } else {
+        PFF_TRY(launch<R>(m, KP_FORCE, P, s));
+        if (solves(n))
+          PFF_TRY(solve_host_loop<R>(m, P, plan, s));
+        else
+          k_step_skip<R><<<1, 32, 0, s>>>(P);
+      }
       if (tape) k_tape_store<R><<<Gtape, kThreads, 0, s>>>(P, *tape);
       if (energy_log && o.energy_every > 0 && (n + 1) % o.energy_every == 0) {
         Params<R> E = P;
@@ -1596,8 +1667,11 @@ static pff_status run_t(pff_mesh *m, const pff_state *st, int64_t step0, int64_t
                                (uint64_t)st->H, (uint64_t)o.cg_max_it, (uint64_t)m->var[KP_FORCE],
                                (uint64_t)m->var[KP_RHS], (uint64_t)m->var[KP_MATVEC],
                                (uint64_t)o.max_restarts, (uint64_t)P.iters_log, (uint64_t)P.track_work,
-                               (uint64_t)m->stab, (uint64_t)(tape ? tape->u : nullptr), (uint64_t)plan.fam,
-                               (uint64_t)plan.U, (uint64_t)o.cg_kernel};
+                               (uint64_t)m->stab, (uint64_t)(tape ? tape->u : nullptr),
+                               (uint64_t)(tape ? tape->x : nullptr), (uint64_t)(tape ? tape->base : nullptr),
+                               (uint64_t)plan.fam,
+                               (uint64_t)plan.U, (uint64_t)o.cg_kernel, (uint64_t)fused,
+                               (uint64_t)m->var[KP_FRHS]};
   uint64_t b1, b2;
   std::memcpy(&b1, &o.cg_tol, 8);
   std::memcpy(&b2, &dt, 8);
@@ -1615,8 +1689,8 @@ static pff_status run_t(pff_mesh *m, const pff_state *st, int64_t step0, int64_t
     P.use_cond = pers ? 0 : 1;
     cudaGraphNode_t n_pr, n_f, last;
     pff_status stt = add_kernel<R>(m, g, {}, KP_PREDICT, P, &n_pr);
-    if (stt == PFF_OK) stt = add_kernel<R>(m, g, {n_pr}, KP_FORCE, P, &n_f);
-    if (stt == PFF_OK) stt = append_solve<R>(m, g, n_f, P, plan, &last);
+    if (stt == PFF_OK) stt = add_kernel<R>(m, g, {n_pr}, fused ? KP_FRHS : KP_FORCE, P, &n_f);
+    if (stt == PFF_OK) stt = append_solve<R>(m, g, n_f, P, plan, &last, fused);
     if (stt == PFF_OK && tape) {
       cudaKernelNodeParams kp;
       std::memset(&kp, 0, sizeof(kp));
@@ -1766,6 +1840,28 @@ static pff_status profile_t(pff_mesh *m, const pff_state *st, double dt, const p
   ms[7] = 0.0;
   ms[8] = 0.0;
   ms[9] = (double)plan.fam;
+  ms[10] = 0.0;
+  ms[11] = use_fused(m, o, plan) ? 1.0 : 0.0;
+  if (res == PFF_OK && !plan.st()) {  // the fused force and right-hand side
+    for (int r = 0; r < reps; ++r) {
+      k_flush<<<(unsigned)((nflush + 255) / 256), 256, 0, s>>>(fb, nflush, sink);
+      cudaEventRecord(ev[2 * r], s);
+      (void)launch<R>(m, KP_FRHS, P, s);
+      cudaEventRecord(ev[2 * r + 1], s);
+    }
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      res = fail(PFF_ERR_CUDA, cudaGetErrorString(e));
+    } else {
+      double tot = 0.0;
+      for (int r = 0; r < reps; ++r) {
+        float t = 0.f;
+        cudaEventElapsedTime(&t, ev[2 * r], ev[2 * r + 1]);
+        tot += t;
+      }
+      ms[10] = tot / reps;
+    }
+  }
   if (res == PFF_OK && plan.pers()) {
     run1(0);
     run1(1);
@@ -2603,6 +2699,9 @@ struct pff_ckpt {
   double dt = 0.0;
   bool filled = false;
   bool full = false;  // whole run taped in the forward, no recompute
+  int32_t policy = PFF_CKPT_RECOMPUTE;  // segments: recompute the damage solves, or tape x
+  void *tX = nullptr;      // damage-tape policy: x_{n+1} of every step of the run
+  int64_t *xbase = nullptr;  // device: first run step of the current segment
   size_t rs = 0;  // sizeof(R)
   // checkpoints: nseg x (u, v, a, d, H)
   void *su = nullptr, *sv = nullptr, *sa = nullptr, *sd = nullptr;
@@ -2622,6 +2721,7 @@ struct pff_ckpt {
   int *kctr = nullptr;
   int64_t adj_iters = 0;  // adjoint CG iterations of the last pff_backward
   GraphCache rec_g;     // taping step graph of the recompute
+  GraphCache mech_rec_g;  // damage-tape policy: the mechanics-only recompute step
   GraphCache rev_g[2];  // reverse-step graphs (two in/out parities)
 };
 
@@ -2630,11 +2730,12 @@ namespace pff {
 static void ckpt_free(pff_ckpt *c) {
   if (!c) return;
   free_graph(c->rec_g);
+  free_graph(c->mech_rec_g);
   free_graph(c->rev_g[0]);
   free_graph(c->rev_g[1]);
   void *p[] = {c->su, c->sv, c->sa, c->sd, c->sH, c->tu, c->tx, c->td, c->tH, c->wu, c->wv, c->wa, c->wd,
                c->segd, c->wH, c->segH, c->ub[0], c->ub[1], c->vb[0], c->vb[1], c->ab[0], c->ab[1], c->Hb[0],
-               c->Hb[1], c->db, c->dbn, c->g, c->lam, c->Hcur, c->fe, c->fd, c->gc, c->kctr};
+               c->Hb[1], c->db, c->dbn, c->g, c->lam, c->Hcur, c->fe, c->fd, c->gc, c->kctr, c->tX, c->xbase};
   for (void *q : p)
     if (q) cudaFree(q);
   delete c;
@@ -2680,6 +2781,10 @@ static pff_status ckpt_alloc(pff_ckpt *c) {
   PFF_TRY(A(&c->fd, Ne * r));
   PFF_TRY(A((void **)&c->gc, 8));
   PFF_TRY(A((void **)&c->kctr, 4 * sizeof(int)));
+  if (c->policy == PFF_CKPT_DAMAGE_TAPE && !c->full) {
+    PFF_TRY(A(&c->tX, (size_t)c->nsteps * N * r));
+    PFF_TRY(A((void **)&c->xbase, sizeof(int64_t)));
+  }
   return PFF_OK;
 }
 
@@ -2697,6 +2802,7 @@ static pff_status run_ckpt_t(pff_mesh *m, const pff_state *st, int64_t step0, in
     tape.H = c->tH;
     tape.stride_n = (int64_t)Np;
     tape.stride_e = (int64_t)Ne;
+    tape.base = nullptr;
     PFF_TRY(run_t<R>(m, st, step0, nsteps, dt, o, iters_log, nullptr, s, &c->rec_g, &tape));
   }
   for (int32_t seg = 0; !c->full && seg < c->nseg; ++seg) {
@@ -2707,7 +2813,23 @@ static pff_status run_ckpt_t(pff_mesh *m, const pff_state *st, int64_t step0, in
     CUDA_TRY(cudaMemcpyAsync((char *)c->sa + seg * Np * r2, st->a, N * r2, cudaMemcpyDeviceToDevice, s));
     CUDA_TRY(cudaMemcpyAsync((char *)c->sd + seg * Np * r, st->d, N * r, cudaMemcpyDeviceToDevice, s));
     CUDA_TRY(cudaMemcpyAsync(c->sH + seg * Ne, st->H, Ne * 8, cudaMemcpyDeviceToDevice, s));
-    PFF_TRY(run_t<R>(m, st, step0 + k0, len, dt, o, iters_log ? iters_log + 2 * k0 : nullptr, nullptr, s));
+    if (c->policy == PFF_CKPT_DAMAGE_TAPE) {
+      // tape the unclamped solution of every step of the segment
+      k_set_i64<<<1, 32, 0, s>>>(c->xbase, k0);
+      CUDA_TRY(cudaGetLastError());
+      Tape tape;
+      tape.u = nullptr;
+      tape.x = c->tX;
+      tape.d = nullptr;
+      tape.H = nullptr;
+      tape.stride_n = (int64_t)Np;
+      tape.stride_e = (int64_t)Ne;
+      tape.base = c->xbase;
+      PFF_TRY(run_t<R>(m, st, step0 + k0, len, dt, o, iters_log ? iters_log + 2 * k0 : nullptr, nullptr, s,
+                       &c->rec_g, &tape));
+    } else {
+      PFF_TRY(run_t<R>(m, st, step0 + k0, len, dt, o, iters_log ? iters_log + 2 * k0 : nullptr, nullptr, s));
+    }
   }
   c->step0 = step0;
   c->dt = dt;
@@ -2776,6 +2898,94 @@ static pff_status build_reverse_graph(pff_mesh *m, pff_ckpt *c, AdjParams<R> A, 
   return PFF_OK;
 }
 
+// Damage-tape policy: the segment's steps again, mechanics only --
+// predictor, force with history and corrector, then the clamp of the
+// unclamped solution the forward taped (no damage solve) -- taping u, d and
+// H for the reverse sweep.  Bit-identical to the forward's steps: the same
+// kernels on the same inputs, and the clamp of the same x.
+template <typename R>
+static pff_status recompute_mech_t(pff_mesh *m, pff_ckpt *c, const pff_state *st, int64_t step0, int64_t nsteps,
+                                   double dt, const pff_options &o, cudaStream_t s) {
+  const size_t Np = m->N + 2, Ne = m->Ne;
+  Params<R> P = base_params<R>(m, o);
+  P.u = (typename V<R>::T2 *)st->u;
+  P.v = (typename V<R>::T2 *)st->v;
+  P.a = (typename V<R>::T2 *)st->a;
+  P.d = (R *)st->d;
+  PFF_TRY(bind_history<R>(m, P, st->H, s));
+  P.dt = dt;
+  P.step_ctr = m->step_ctr;
+  P.step_inc = m->step_ctr;
+  if (m->stab_cap < nsteps + 1) {
+    if (m->stab) cudaFree(m->stab);
+    m->stab = nullptr;
+    m->stab_cap = 0;
+    PFF_TRY(dalloc(&m->stab, nsteps + 1));
+    m->stab_cap = nsteps + 1;
+    free_graph(m->step_g);
+    free_graph(m->mech_g);
+  }
+  {
+    std::vector<double> S(nsteps + 1);
+    for (int64_t k = 0; k <= nsteps; ++k) S[k] = ramp((double)(step0 + k) * dt, o.t_ramp);
+    CUDA_TRY(cudaMemcpyAsync(m->stab, S.data(), S.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaStreamSynchronize(s));  // S lives on this stack frame
+  }
+  P.Stab = m->stab;
+  P.dprev = (const R *)st->d;
+  P.dout = (R *)st->d;
+  P.iters_log = nullptr;
+  P.track_work = 0;
+  P.use_cond = 0;
+  PFF_TRY(autotune<R>(m, o, P, true, false, s));
+  const int64_t zero = 0;
+  CUDA_TRY(cudaMemcpyAsync(m->step_ctr, &zero, sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  uint64_t b2;
+  std::memcpy(&b2, &dt, 8);
+  const std::vector<uint64_t> key = {(uint64_t)st->u, (uint64_t)st->v, (uint64_t)st->a, (uint64_t)st->d,
+                                     (uint64_t)st->H, (uint64_t)m->var[KP_FORCE], (uint64_t)m->stab,
+                                     (uint64_t)c->tX, b2};
+  GraphCache &gc = c->mech_rec_g;
+  if (!gc.exec || gc.key != key) {
+    free_graph(gc);
+    cudaGraph_t g;
+    CUDA_TRY(cudaGraphCreate(&g, 0));
+    Tape T;
+    T.u = c->tu;
+    T.x = nullptr;
+    T.d = c->td;
+    T.H = c->tH;
+    T.stride_n = (int64_t)Np;
+    T.stride_e = (int64_t)Ne;
+    T.base = nullptr;
+    const R *tx = (const R *)c->tX;
+    int64_t stride = (int64_t)Np;
+    const int64_t *base = c->xbase;
+    void *fargs[] = {(void *)&P, (void *)&tx, (void *)&stride, (void *)&base};
+    void *targs[] = {(void *)&P, (void *)&T};
+    const unsigned Gn = std::min<unsigned>(grid_for(m->N, kThreads), m->grid[KP_UPDATE][0]);
+    const unsigned Gt = std::min<unsigned>(grid_for(std::max(m->N, m->Ne), kThreads), m->grid[KP_UPDATE][0]);
+    cudaGraphNode_t n_pr, n_f, n_fin, n_t;
+    pff_status stt = add_kernel<R>(m, g, {}, KP_PREDICT, P, &n_pr);
+    if (stt == PFF_OK) stt = add_kernel<R>(m, g, {n_pr}, KP_FORCE, P, &n_f);
+    if (stt == PFF_OK) stt = add_generic(g, {n_f}, (const void *)k_finish_tape<R>, Gn, kThreads, 0, fargs, &n_fin);
+    if (stt == PFF_OK) stt = add_generic(g, {n_fin}, (const void *)k_tape_store<R>, Gt, kThreads, 0, targs, &n_t);
+    if (stt != PFF_OK) {
+      cudaGraphDestroy(g);
+      return stt;
+    }
+    const cudaError_t e = cudaGraphInstantiate(&gc.exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      gc.exec = nullptr;
+      return fail(PFF_ERR_CUDA, std::string("cudaGraphInstantiate (recompute): ") + cudaGetErrorString(e));
+    }
+    gc.key = key;
+  }
+  for (int64_t n = 0; n < nsteps; ++n) CUDA_TRY(cudaGraphLaunch(gc.exec, s));
+  return PFF_OK;
+}
+
 template <typename R>
 static pff_status backward_t(pff_mesh *m, pff_ckpt *c, const void *dL_dd, const pff_options &o, double *dL_dGc,
                              cudaStream_t s, double *dL_dGc_field = nullptr) {
@@ -2813,6 +3023,12 @@ static pff_status backward_t(pff_mesh *m, pff_ckpt *c, const void *dL_dd, const 
     CUDA_TRY(cudaMemcpyAsync(c->wH, c->sH + seg * Ne, Ne * 8, cudaMemcpyDeviceToDevice, s));
     CUDA_TRY(cudaMemcpyAsync(c->segd, c->wd, N * r, cudaMemcpyDeviceToDevice, s));
     CUDA_TRY(cudaMemcpyAsync(c->segH, c->wH, Ne * 8, cudaMemcpyDeviceToDevice, s));
+    if (c->policy == PFF_CKPT_DAMAGE_TAPE) {
+      // the mechanics alone, with the damage solutions the forward taped
+      k_set_i64<<<1, 32, 0, s>>>(c->xbase, k0);
+      CUDA_TRY(cudaGetLastError());
+      PFF_TRY(recompute_mech_t<R>(m, c, &w, c->step0 + k0, len, c->dt, ob, s));
+    } else {
     // recompute the segment, taping each step (one graph per step)
     Tape tape;
     tape.u = c->tu;
@@ -2821,7 +3037,9 @@ static pff_status backward_t(pff_mesh *m, pff_ckpt *c, const void *dL_dd, const 
     tape.H = c->tH;
     tape.stride_n = (int64_t)Np;
     tape.stride_e = (int64_t)Ne;
+    tape.base = nullptr;
     PFF_TRY(run_t<R>(m, &w, c->step0 + k0, len, c->dt, ob, nullptr, nullptr, s, &c->rec_g, &tape));
+    }
     }
     // reverse the segment
     const int kstart = (int)(len - 1);
@@ -2840,7 +3058,9 @@ static pff_status backward_t(pff_mesh *m, pff_ckpt *c, const void *dL_dd, const 
       A.kctr = c->kctr;
       A.kdec = c->kctr;
       A.tape_u = (const R2 *)c->tu;
-      A.tape_x = (const R *)c->tx;
+      const bool xt = c->policy == PFF_CKPT_DAMAGE_TAPE && !c->full;
+      A.tape_x = xt ? (const R *)c->tX : (const R *)c->tx;
+      A.x_base = xt ? c->xbase : nullptr;
       A.tape_d = (const R *)c->td;
       A.tape_H = c->tH;
       A.snap_d = (const R *)c->segd;
@@ -2899,12 +3119,15 @@ static pff_status backward_t(pff_mesh *m, pff_ckpt *c, const void *dL_dd, const 
 
 extern "C" {
 
-pff_status pff_ckpt_create(pff_mesh *m, int64_t nsteps, int32_t every, pff_ckpt **out) {
+pff_status pff_ckpt_create_policy(pff_mesh *m, int64_t nsteps, int32_t every, int32_t policy, pff_ckpt **out) {
   if (!m || !out || nsteps <= 0 || every < 0) return fail(PFF_ERR_ARG, "bad checkpoint arguments");
   if (every == 0 && nsteps > INT32_MAX) return fail(PFF_ERR_ARG, "full tape: too many steps");
+  if (policy != PFF_CKPT_RECOMPUTE && policy != PFF_CKPT_DAMAGE_TAPE)
+    return fail(PFF_ERR_ARG, "unknown checkpoint policy");
   *out = nullptr;
   pff_ckpt *c = new pff_ckpt();
   c->m = m;
+  c->policy = policy;
   c->nsteps = nsteps;
   c->full = every == 0;
   c->every = (int32_t)std::min<int64_t>(every == 0 ? nsteps : every, nsteps);
@@ -2917,6 +3140,10 @@ pff_status pff_ckpt_create(pff_mesh *m, int64_t nsteps, int32_t every, pff_ckpt 
   }
   *out = c;
   return PFF_OK;
+}
+
+pff_status pff_ckpt_create(pff_mesh *m, int64_t nsteps, int32_t every, pff_ckpt **out) {
+  return pff_ckpt_create_policy(m, nsteps, every, PFF_CKPT_RECOMPUTE, out);
 }
 
 void pff_ckpt_destroy(pff_ckpt *c) { ckpt_free(c); }

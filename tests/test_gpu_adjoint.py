@@ -20,13 +20,13 @@ def _problem(nx=20, ny=8):
     return p, mat
 
 
-def _gpu_grad(pff, p, mat, Gc, nsteps, dstar, prec, every, tol):
+def _gpu_grad(pff, p, mat, Gc, nsteps, dstar, prec, every, tol, policy="recompute"):
     import torch
     mesh = pff.Mesh.from_plate(p, precision=prec)
     mesh.set_material(dict(mat, Gc=Gc), 0.5)
     opts = pff.options(cg_tol=tol)
     st = mesh.new_state()
-    ck = pff.Checkpoint(mesh, nsteps, every)
+    ck = pff.Checkpoint(mesh, nsteps, every, policy)
     mesh.run_ckpt(st, ck, opts=opts)
     d = st["d"].double()
     ds = torch.tensor(dstar, device="cuda")
@@ -52,8 +52,10 @@ def test_fp64_adjoint_matches_oracle(orc, pff):
 
 def test_checkpoint_segmentation_is_exact(orc, pff):
     """Recompute is bit-identical, so the gradient does not depend on the
-    checkpoint spacing, and a full tape (every = 0, no recompute) gives the
-    same gradient; the taped run equals a plain run."""
+    checkpoint spacing or on the checkpoint policy (full recompute, or the
+    mechanics alone with the damage solutions taped), and a full tape
+    (every = 0, no recompute) gives the same gradient; the taped run equals
+    a plain run."""
     import torch
     p, mat = _problem()
     nsteps = 30
@@ -63,6 +65,11 @@ def test_checkpoint_segmentation_is_exact(orc, pff):
         L, g, st = _gpu_grad(pff, p, mat, 2.5, nsteps, dstar, "fp32", every, 1e-8)
         grads.append(g)
     assert grads[0] == grads[1] == grads[2] == grads[3]
+    # the damage-tape policy (each step's unclamped solution taped, the
+    # mechanics alone recomputed) reverses the same trajectory bit for bit
+    for every in (1, 7, 30):
+        grads.append(_gpu_grad(pff, p, mat, 2.5, nsteps, dstar, "fp32", every, 1e-8, "damage_tape")[1])
+    assert all(g == grads[0] for g in grads), grads
     mesh = pff.Mesh.from_plate(p, precision="fp32")
     mesh.set_material(dict(mat, Gc=2.5), 0.5)
     s2 = mesh.new_state()
@@ -126,3 +133,22 @@ def test_plane_stress_adjoint_matches_oracle(orc, pff):
     assert abs(gL - L) <= 1e-10 * L
     assert abs(gg - g) <= 1e-7 * abs(g), (gg, g)
 
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_damage_tape_policy_matches_oracle(orc, pff, prec):
+    """The damage-tape checkpoint policy against the oracle's discrete
+    adjoint (FP64 1e-7, FP32 2e-3), segments of 9 steps over 40 (a ragged
+    last segment)."""
+    p, mat = _problem()
+    om = orc.Mesh.from_plate(p)
+    dt = om.stable_dt(mat, 0.5)
+    nsteps = 40
+    st = om.new_state()
+    om.run(dict(mat, Gc=3.0), st, nsteps, dt, tol=1e-13)
+    dstar = st["d"].copy()
+    L, g, status = om.adjoint_gc(dict(mat, Gc=2.0), nsteps, dt, dstar, tol=1e-13)
+    gL, gg, _ = _gpu_grad(pff, p, mat, 2.0, nsteps, dstar, prec, 9, 1e-13 if prec == "fp64" else 1e-8,
+                          "damage_tape")
+    tol = 1e-7 if prec == "fp64" else 2e-3
+    assert abs(gg - g) <= tol * abs(g), (gg, g)

@@ -260,3 +260,50 @@ def test_plane_stress_fp32_vs_fp64_oracle(orc, pff):
     eu = rel_l2(to_np(gst["u"]), ost["u"])
     ed = np.abs(to_np(gst["d"]) - ost["d"]).max()
     assert eu <= 1e-4 and ed <= 1e-3, (eu, ed)
+
+
+@pytest.mark.parametrize("prec,model", [("fp32", "AT2"), ("fp64", "AT2"), ("fp32", "AT1"), ("fp64", "AT1")])
+def test_fused_force_rhs_matches_separate(orc, pff, prec, model):
+    """The step's internal force and damage right-hand side in one kernel
+    (pff_options.fuse = 2) against the two kernels (fuse = 1): FP32 fields
+    bit-identical after 30 steps (per-element arithmetic identical, the
+    set-up's double-word sums round alike); FP64 mechanics identical to the
+    last bits of the damage, whose dot products sum in the kernel's own
+    block order."""
+    import torch
+    c, om, gm, dt = _setup(pff, orc, prec=prec, split="amor" if model == "AT1" else "spectral", model=model)
+    out = []
+    for fuse in (1, 2):
+        st = gm.new_state()
+        log = torch.zeros(30, 2, dtype=torch.int32, device="cuda")
+        gm.run(st, 30, opts=pff.options(fuse=fuse), iters_log=log)
+        torch.cuda.synchronize()
+        assert gm.sync_status() == 0
+        out.append((st, log.cpu().numpy()))
+    (a, la), (b, lb) = out
+    if prec == "fp32":
+        for k in ("u", "v", "a", "d", "H"):
+            assert torch.equal(a[k], b[k]), k
+        assert np.array_equal(la, lb)
+    else:
+        assert np.abs(la - lb).max() <= 1
+        assert float((a["d"] - b["d"]).abs().max()) <= 1e-12
+        assert rel_l2(to_np(a["u"]), to_np(b["u"])) <= 1e-12
+
+
+def test_fused_force_rhs_fp64_per_step_parity(orc, pff):
+    """60 FP64 steps with the fused kernel forced, every entry of every
+    field against the oracle (per-field floors, 1e-10)."""
+    import torch
+    c, om, gm, dt = _setup(pff, orc)
+    mat = c["material"]
+    gst, ost = gm.new_state(), om.new_state()
+    log = torch.zeros(60, 2, dtype=torch.int32, device="cuda")
+    worst = {}
+    for n in range(60):
+        gm.run(gst, 1, step0=n, opts=pff.options(fuse=2), iters_log=log[n:n + 1])
+        torch.cuda.synchronize()
+        om.run(mat, ost, 1, dt, n0=n, forced=[int(log[n, 0])])
+        merge_worst(worst, state_errs(gst, ost))
+        assert max(worst.values()) <= 1e-10, (n, worst)
+    assert gm.sync_status() == 0
