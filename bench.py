@@ -69,6 +69,8 @@ def parse():
                     help="skip the 1M-node volumetric-deviatoric and AT1 configurations")
     ap.add_argument("--no-inversion", action="store_true",
                     help="skip the gradient checks and L-BFGS recovery on the 500x500 plate")
+    ap.add_argument("--nvtx-range", action="store_true",
+                    help="wrap the timed steps in the NVTX range 'timed' (for ncu --nvtx-include timed/)")
     ap.add_argument("--loop", choices=["graph", "host"], default="graph",
                     help="host: launch every kernel from the host (ncu cannot profile "
                          "kernels inside graphs with conditional nodes)")
@@ -77,11 +79,54 @@ def parse():
 
 # ----------------------------------------------------------------- clocks
 
+class _Nvml:
+    """Read-only NVML queries through the driver's libnvidia-ml (ctypes):
+    the SM clock, its maximum and the active clock-event reasons."""
+
+    CLOCK_SM = 1
+
+    def __init__(self, index):
+        import ctypes
+        self.C = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit_v2 failed")
+        self.h = ctypes.c_void_p()
+        if self.lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(index), ctypes.byref(self.h)) != 0:
+            raise RuntimeError(f"nvmlDeviceGetHandleByIndex_v2({index}) failed")
+        self.get_reasons = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+
+    def _clock(self, fn):
+        v = self.C.c_uint()
+        if fn(self.h, self.C.c_int(self.CLOCK_SM), self.C.byref(v)) != 0:
+            raise RuntimeError("NVML clock query failed")
+        return float(v.value)
+
+    def sm_mhz(self):
+        return self._clock(self.lib.nvmlDeviceGetClockInfo)
+
+    def max_sm_mhz(self):
+        return self._clock(self.lib.nvmlDeviceGetMaxClockInfo)
+
+    def reasons(self):
+        v = self.C.c_ulonglong()
+        if self.get_reasons(self.h, self.C.byref(v)) != 0:
+            raise RuntimeError("NVML reasons query failed")
+        return int(v.value)
+
+    def close(self):
+        try:
+            self.lib.nvmlShutdown()
+        except Exception:
+            pass
+
+
 class ClockSampler:
     """Samples the SM clock and the clock-event (throttle) reasons while
-    running: through NVML every millisecond when the bindings load (the
-    timed region of a short run lasts tens of milliseconds), else through
-    nvidia-smi every 100 ms.  Read-only queries."""
+    running: through NVML every millisecond when the driver's library loads
+    (the timed region of a short run lasts tens of milliseconds), else
+    through nvidia-smi every 100 ms.  Read-only queries."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -100,15 +145,12 @@ class ClockSampler:
 
     def start(self):
         try:
-            import pynvml
-            pynvml.nvmlInit()
-            h = pynvml.nvmlDeviceGetHandleByIndex(self.index)
-            self.nvml = (pynvml, h)
-            self.smax = float(pynvml.nvmlDeviceGetMaxClockInfo(h, pynvml.NVML_CLOCK_SM))
+            self.nvml = _Nvml(self.index)
+            self.smax = self.nvml.max_sm_mhz()
             self.t = threading.Thread(target=self._poll, daemon=True)
             self.t.start()
             return
-        except Exception as e:  # no NVML bindings or library: nvidia-smi
+        except Exception as e:  # no NVML library: nvidia-smi
             self.nvml = None
             self.nvml_error = f"{type(e).__name__}: {e}"
         try:
@@ -122,13 +164,9 @@ class ClockSampler:
             self.proc = None
 
     def _poll(self):
-        pynvml, h = self.nvml
-        get_reasons = getattr(pynvml, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
-            pynvml.nvmlDeviceGetCurrentClocksThrottleReasons
         while not self.stop_flag:
             try:
-                self.samples.append((float(pynvml.nvmlDeviceGetClockInfo(h, pynvml.NVML_CLOCK_SM)),
-                                     int(get_reasons(h))))
+                self.samples.append((self.nvml.sm_mhz(), self.nvml.reasons()))
             except Exception:
                 break
             time.sleep(0.001)
@@ -143,12 +181,9 @@ class ClockSampler:
             self.t.join(timeout=5)
             sm = [c for c, _ in self.samples]
             reasons = sorted({nm for _, r in self.samples for nm, b in self.BITS.items() if r & b})
-            try:
-                self.nvml[0].nvmlShutdown()
-            except Exception:
-                pass
+            self.nvml.close()
             return dict(sm_mhz=float(np.median(sm)) if sm else None, sm_max_mhz=self.smax,
-                        reasons=reasons, samples=len(sm), source="nvml, 1 ms")
+                        reasons=reasons, samples=len(sm), source="nvml (libnvidia-ml), 1 ms")
         if self.proc is None:
             return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"])
         self.proc.terminate()
@@ -824,10 +859,14 @@ def run_ours(args):
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    if args.nvtx_range:
+        torch.cuda.nvtx.range_push("timed")
     e0.record(stream)
     mesh.run(st, args.steps, step0=args.warmup, opts=opts, iters_log=log[args.warmup:total])
     e1.record(stream)
     torch.cuda.synchronize()
+    if args.nvtx_range:
+        torch.cuda.nvtx.range_pop()
     if ws > 1:
         torch.distributed.barrier()
     clocks = clk.stop()

@@ -264,6 +264,9 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 6 : 1) kb_matvec(Params<
       } else if (Q.nbc) {  // FP64 merged rows
         q = nb_row_any(Q, i, Q.diag[i] * pc, [&](int j) { return pnew(Q, j, beta); });
         done = true;
+      } else if (Q.ecfd) {  // FP64 entry records
+        q = erec_row_d<U>(Q, i, beta, pc);
+        done = true;
       }
       for (int k = 0; k < P.D && !done; k += U) {
         R c[U];

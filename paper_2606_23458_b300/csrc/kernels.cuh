@@ -146,11 +146,12 @@ template <typename R> struct Params {
                  // two nodes b, c of the entry's element and their row
                  // coefficients (w_ab + mA, w_ac + mA); b = -1 marks an empty
                  // slot.  Nullable.
-  uint32_t *ecmp; // FP32, compact form of the same (meshes whose elements span
+  uint32_t *ecmp; // compact form of the same (meshes whose elements span
   float2 *ecf;    // fewer than 2^15 node ids): ecmp packs the 16-bit offsets
                   // b - i (low half) and c - i (high half), ecf the two
                   // coefficients; an empty slot is offsets 0, coefficients 0.
                   // Nullable; at most one of erec and ecmp is set.
+  double2 *ecfd;  // FP64 meshes: the entry coefficients in FP64 (with ecmp)
   // Compact meshes (both precisions) whose rows have at most kNbMax distinct
   // neighbours:
   // the same rows with each neighbour's coefficients merged (rows sum the
@@ -513,19 +514,36 @@ __device__ __forceinline__ void elem_strain(const Params<R> &P, const typename P
 // reduced into *wext.
 template <typename R>
 __global__ void __launch_bounds__(256) k_predict(Params<R> P) {
+  typedef typename Params<R>::R2 R2;
+  constexpr int B = 4;  // nodes per thread and pass: every load issued before the first store
   double w = 0.0;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.N; i += gridDim.x * blockDim.x) {
-    typename Params<R>::R2 u = P.u[i], v = P.v[i], a = P.a[i];
-    const R dt = (R)P.dt, h = R(0.5) * dt * dt;
-    const R dux = dt * v.x + h * a.x, duy = dt * v.y + h * a.y;
-    if (P.track_work && (P.flags[i] & kLoaded)) {
-      const double S = 0.5 * (load_scale(P, 0) + load_scale(P, 1));
-      typename Params<R>::R2 f = P.fext[i];
-      w += S * ((double)f.x * dux + (double)f.y * duy);
+  const int stride = gridDim.x * blockDim.x;
+  const R dt = (R)P.dt, h = R(0.5) * dt * dt;
+  for (int i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < P.N; i0 += B * stride) {
+    R2 u[B], v[B], a[B];
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const int i = i0 + b * stride;
+      if (i < P.N) {
+        u[b] = P.u[i];
+        v[b] = P.v[i];
+        a[b] = P.a[i];
+      }
     }
-    u.x += dux;
-    u.y += duy;
-    P.u[i] = u;
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const int i = i0 + b * stride;
+      if (i >= P.N) break;
+      const R dux = dt * v[b].x + h * a[b].x, duy = dt * v[b].y + h * a[b].y;
+      if (P.track_work && (P.flags[i] & kLoaded)) {
+        const double S = 0.5 * (load_scale(P, 0) + load_scale(P, 1));
+        const R2 f = P.fext[i];
+        w += S * ((double)f.x * dux + (double)f.y * duy);
+      }
+      u[b].x += dux;
+      u[b].y += duy;
+      P.u[i] = u[b];
+    }
   }
   if (P.track_work) {
     double v1[1] = {w};
@@ -752,8 +770,12 @@ template <typename R>
 __device__ __forceinline__ void put_erec(const Params<R> &P, int k, int i, const typename Params<R>::R4 &G, int a,
                                          R kA, R mA) {
   const typename Params<R>::R2 cr = erec_coef<R>(G, a, kA, mA);
-  const float2 c = make_float2((float)cr.x, (float)cr.y);
   const size_t q = (size_t)k * P.N + i;
+  if constexpr (sizeof(R) == 8) {
+    if (P.ecfd) P.ecfd[q] = make_double2((double)cr.x, (double)cr.y);
+    return;
+  }
+  const float2 c = make_float2((float)cr.x, (float)cr.y);
   if (P.ecmp)
     P.ecf[q] = c;
   else
@@ -1434,6 +1456,33 @@ __device__ __forceinline__ void el_gather6(const ElRow6 &r, int i, float (&v)[6]
   }
 }
 
+// Row i of q = A p_new from the FP64 entry records: erec_row's arithmetic
+// in FP64 (diag_i p_i, then per incidence slot c_b p_b + c_c p_c, U slots
+// in flight, summed in slot order; empty slots add an exact 0).
+template <int U>
+__device__ __forceinline__ double erec_row_d(const Params<double> &P, int i, double beta, double pc) {
+  double q = P.diag[i] * pc;
+  for (int k = 0; k < P.D; k += U) {
+    uint32_t w[U];
+    double2 cf[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const bool in = k + u < P.D;
+      w[u] = in ? __ldg(&P.ecmp[(size_t)(k + u) * P.N + i]) : 0u;
+      cf[u] = in ? __ldg(&P.ecfd[(size_t)(k + u) * P.N + i]) : make_double2(0.0, 0.0);
+    }
+    double c[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int ob = (int)(int16_t)(w[u] & 0xffffu), oc = (int)w[u] >> 16;
+      c[u] = fma(cf[u].x, pnew(P, i + ob, beta), __dmul_rn(cf[u].y, pnew(P, i + oc, beta)));
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) q = __dadd_rn(q, c[u]);
+  }
+  return q;
+}
+
 // One incidence entry's share of (A p_new)_a, matrix-free (Eq.
 // matrix_free_fe_operator): element coefficients are rebuilt from the
 // geometry and the history on every application.
@@ -1535,8 +1584,10 @@ __global__ void __launch_bounds__(256) k_cg_matvec_ep(Params<R> P) {
             const R pc = pnew(P, i, beta);
             if constexpr (sizeof(R) == 4)
               q = erec_row<1>(P, i, beta, pc);
-            else
+            else if (P.nbc)
               q = nb_row_any(P, i, P.diag[i] * pc, [&](int j) { return pnew(P, j, beta); });
+            else
+              q = erec_row_d<1>(P, i, beta, pc);
             vals[0] = AC::add(vals[0], AC::prod(pc, P.rscale * q));
           }
           P.q[i] = q;
@@ -1626,16 +1677,21 @@ __device__ __forceinline__ void nb_rows6(const Params<float> &P, float beta, int
 // p_new . q added to acc.
 template <typename R, int U>
 __device__ __forceinline__ void matvec_rows(const Params<R> &P, R beta, int i0, int stride,
-                                            typename Acc<R>::T &acc, int iend = -1) {
+                                            typename Acc<R>::T &acc, int iend = -1, bool rev = false) {
   typedef Acc<R> AC;
   const int n = iend < 0 ? P.N : iend;  // rows i0, i0 + stride, ... below n
+  // rev: the same rows, last first (the element-wise rows of the persistent
+  // loop alternate directions between iterations, so that each pass starts
+  // on the records and vectors the previous one touched last)
+  const int ilast = i0 < n ? i0 + (n - 1 - i0) / stride * stride : i0 - stride;
   if constexpr (sizeof(R) == 8) {
-    if (P.nbc) {  // FP64 merged rows
+    if (P.nbc || P.ecfd) {  // FP64 merged rows or entry records
       for (int i = i0; i < n; i += stride) {
         R q = 0;
         if (!is_fixed(P, i)) {
           const R pc = pnew(P, i, beta);
-          q = nb_row_any(P, i, P.diag[i] * pc, [&](int j) { return pnew(P, j, beta); });
+          q = P.nbc ? nb_row_any(P, i, P.diag[i] * pc, [&](int j) { return pnew(P, j, beta); })
+                    : erec_row_d<U>(P, i, beta, pc);
           acc = AC::add(acc, AC::prod(pc, P.rscale * q));
         }
         P.q[i] = q;
@@ -1654,7 +1710,8 @@ __device__ __forceinline__ void matvec_rows(const Params<R> &P, R beta, int i0, 
       // FP32 entry records: the row's diagonal times its own value, then per
       // entry the two other nodes' values times their coefficients (the
       // records stream in coalesced; only the p gathers are indirect)
-      for (int i = i0; i < n; i += stride) {
+      const int istep = rev ? -stride : stride;
+      for (int i = rev ? ilast : i0; rev ? i >= i0 : i < n; i += istep) {
         R q = 0;
         if (!is_fixed(P, i)) {
           const R pc = pnew(P, i, beta);
@@ -1767,18 +1824,21 @@ __device__ __forceinline__ void update_finish(const Params<R> &P, const double *
 // The update of rows (pairs of rows in FP32) j0, j0 + stride, ...
 template <typename R>
 __device__ __forceinline__ void update_rows(const Params<R> &P, R alpha, R beta, int j0, int stride,
-                                            typename Acc<R>::T (&vals)[3], bool &proj, int iend = -1) {
+                                            typename Acc<R>::T (&vals)[3], bool &proj, int iend = -1,
+                                            bool rev = false) {
   typedef typename Params<R>::R2 R2;
   const int n = iend < 0 ? P.N : iend;  // rows below n (FP32: pairs below (n + 1) / 2)
   if constexpr (sizeof(R) == 4) {
     const int npair = (n + 1) >> 1;
+    const int jlast = j0 < npair ? j0 + (npair - 1 - j0) / stride * stride : j0 - stride;
+    const int jstep = rev ? -stride : stride;
     const uchar2 *__restrict__ fl2 = reinterpret_cast<const uchar2 *>(P.flags);
     float2 *__restrict__ x2 = reinterpret_cast<float2 *>(P.x);
     float2 *__restrict__ r2 = reinterpret_cast<float2 *>(P.r);
     float4 *__restrict__ pz4 = reinterpret_cast<float4 *>(P.pz);
     const float2 *__restrict__ q2 = reinterpret_cast<const float2 *>(P.q);
     const float2 *__restrict__ d2 = reinterpret_cast<const float2 *>(P.dinv);
-    for (int j = j0; j < npair; j += stride) {
+    for (int j = rev ? jlast : j0; rev ? j >= j0 : j < npair; j += jstep) {
       const uchar2 f = fl2[j];
       float2 xv = x2[j], rv = r2[j];
       const float2 qv = q2[j], dv = d2[j];
@@ -2108,7 +2168,7 @@ __global__ void __launch_bounds__(pers_threads(U, ST), kPersMinBlocks) k_cg_pers
     if constexpr (ST)
       matvec_rows_staged<U>(P, z.coef[1], row0, row1, srec, sH, v1[0]);
     else
-      matvec_rows<R, U>(P, z.coef[1], tid, stride, v1[0]);
+      matvec_rows<R, U>(P, z.coef[1], tid, stride, v1[0], -1, (z.iters & 1) != 0);
     ++nbar;
     if (!grid_sum<R, 1>(v1, P.part + (nbar & 1u) * 2u * nb, S, nbar * nb + P.bar_extra, z.tot,
                         (typename AC::T(*)[1])sh, &z.ok))
@@ -2129,7 +2189,7 @@ __global__ void __launch_bounds__(pers_threads(U, ST), kPersMinBlocks) k_cg_pers
     // x += alpha p, r -= alpha q, z = r / diag; |r|^2 and r.z
     typename AC::T v3[3] = {AC::zero(), AC::zero(), AC::zero()};
     bool proj = false;
-    update_rows<R>(P, z.coef[0], z.coef[1], tid, stride, v3, proj);
+    update_rows<R>(P, z.coef[0], z.coef[1], tid, stride, v3, proj, -1, (z.iters & 1) != 0);
     typename AC::T v2[2] = {v3[0], v3[1]};
     ++nbar;
     if (!grid_sum<R, 2>(v2, P.part + (nbar & 1u) * 2u * nb, S, nbar * nb + P.bar_extra, z.tot, sh, &z.ok))
@@ -2418,6 +2478,18 @@ template <bool ST> struct FusedCfg {
   static constexpr int minb = ST ? 1 : 2;
 };
 
+// CTA size and residency of the unstaged single-reduction kernel per
+// variant U: 512 threads (64 registers) for U <= 2, 384 for U = 3 and 256
+// (three per SM) for U = 4 -- up to 85 registers, for rows whose records
+// and neighbour values do not fit 64 (the element-wise rows).  The
+// autotuner times every variant.
+__host__ __device__ constexpr int fused_threads(int U, bool ST) {
+  return ST ? FusedCfg<true>::threads : (U == 3 ? 384 : U == 4 ? 256 : FusedCfg<false>::threads);
+}
+__host__ __device__ constexpr int fused_minb(int U, bool ST) {
+  return ST ? FusedCfg<true>::minb : (U == 4 ? 3 : 2);
+}
+
 struct FusedShared {
   double gamma, alpha, bn, rr;
   double tot[3];
@@ -2460,7 +2532,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsig
 // touch (bulk copies on two mbarriers, bounded waits); the pass itself then
 // reads shared memory only and writes its rows' results to global memory.
 template <int U, bool ST>
-__global__ void __launch_bounds__(FusedCfg<ST>::threads, FusedCfg<ST>::minb) k_cg_fused(Params<float> P) {
+__global__ void __launch_bounds__(fused_threads(U, ST), fused_minb(U, ST)) k_cg_fused(Params<float> P) {
   typedef Acc<float> AC;
   SolveScalars *S = P.sc;
   __shared__ DF sh[32][3];
@@ -2719,19 +2791,38 @@ __global__ void __launch_bounds__(256) k_at1_restart(Params<R> P) {
 // advances the step counter.
 template <typename R>
 __global__ void __launch_bounds__(256) k_dmg_finish(Params<R> P) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.N; i += gridDim.x * blockDim.x) {
-    R v;
-    if (P.flags[i] & kNotch) {
-      v = R(1);
-    } else {
-      v = P.x[i];
-      if (P.model == kAT2) {
-        const R lo = P.dprev[i];
-        v = v > lo ? v : lo;
-        v = v < R(1) ? v : R(1);
+  // four nodes per thread and pass, every load before the first store
+  // (d_out may alias d_prev: each node's store follows its own loads)
+  constexpr int B = 4;
+  const int stride = gridDim.x * blockDim.x;
+  for (int i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < P.N; i0 += B * stride) {
+    R x[B], lo[B];
+    uint8_t fl[B];
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const int i = i0 + b * stride;
+      if (i < P.N) {
+        fl[b] = P.flags[i];
+        x[b] = P.x[i];
+        lo[b] = P.dprev[i];
       }
     }
-    P.dout[i] = v;
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const int i = i0 + b * stride;
+      if (i >= P.N) break;
+      R v;
+      if (fl[b] & kNotch) {
+        v = R(1);
+      } else {
+        v = x[b];
+        if (P.model == kAT2) {
+          v = v > lo[b] ? v : lo[b];
+          v = v < R(1) ? v : R(1);
+        }
+      }
+      P.dout[i] = v;
+    }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     const SolveScalars &S = *P.sc;

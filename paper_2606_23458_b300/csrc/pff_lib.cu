@@ -268,6 +268,7 @@ struct pff_mesh {
   float4 *erec = nullptr;  // FP32: damage entry records of the current solve (D x N, incidence layout)
   uint32_t *ecmp = nullptr;  // FP32, compact entry records: packed 16-bit neighbour offsets (D x N)
   float2 *ecf = nullptr;     // FP32, compact entry records: coefficients (D x N)
+  double2 *ecfd = nullptr;   // FP64, compact entry records: coefficients (D x N)
   int64_t span = 0;          // largest node-id difference within an element
   uint32_t *nbo = nullptr;   // merged rows: neighbour offsets (Dn / 2 x N)
   void *nbc = nullptr;       // merged rows: coefficients (Dn x N, kernel precision)
@@ -347,7 +348,7 @@ static void mesh_free(pff_mesh *m) {
   free_graph(m->step_g);
   free_graph(m->mech_g);
   void *ptrs[] = {m->gcs, m->st_cta, m->st_rng, m->st_nrng, m->st_lrec, m->st_slot, m->cgv, m->cgp,
-                  m->ptr, m->ent, m->ell, m->rec, m->drec, m->erec, m->ecmp, m->ecf, m->nbo, m->nbc, m->nmap,
+                  m->ptr, m->ent, m->ell, m->rec, m->drec, m->erec, m->ecmp, m->ecf, m->ecfd, m->nbo, m->nbc, m->nmap,
                   m->diagf, m->diagd, m->fe, m->fext, m->minv,
                   m->area_d,
                   m->flags,
@@ -535,7 +536,7 @@ static const void *plan_fun(const CgPlan &c) {
 }
 
 static inline unsigned plan_threads(const CgPlan &c) {
-  return c.fam == kFamFusedStaged ? FusedCfg<true>::threads : (c.fam == kFamFused ? FusedCfg<false>::threads : pers_threads(c.U, c.st()));
+  return c.fam == kFamFusedStaged ? FusedCfg<true>::threads : (c.fam == kFamFused ? fused_threads(c.U, false) : pers_threads(c.U, c.st()));
 }
 
 static inline size_t plan_smem(const pff_mesh *m, const CgPlan &c) {
@@ -872,22 +873,22 @@ static pff_status configure(pff_mesh *m) {
     PFF_TRY(dalloc(&m->diagf, (size_t)m->N));
     CUDA_TRY(cudaMemset(m->diagf, 0, (size_t)m->N * sizeof(float)));
   }
-  if (sizeof(R) == 8 && !m->nbc && m->span < 32768 && D <= kNbMax) {
-    // FP64 merged rows: the incidence offsets in a scratch array first
-    uint32_t *ofs = nullptr;
-    PFF_TRY(dalloc(&ofs, (size_t)D * m->N));
+  if (sizeof(R) == 8 && !m->ecmp && m->span < 32768) {
+    // FP64 compact entry records (the default element-wise form reads them
+    // as the FP32 meshes do; the per-element records are then not needed)
+    // and, for rows with at most eight distinct neighbours, the opt-in
+    // merged rows
+    PFF_TRY(dalloc(&m->ecmp, (size_t)D * m->N));
+    PFF_TRY(dalloc(&m->ecfd, (size_t)D * m->N));
+    CUDA_TRY(cudaMemset(m->ecfd, 0, (size_t)D * m->N * sizeof(double2)));
     k_erec_ids<R><<<std::min<unsigned>(grid_for(m->N, 256), stride_cap()), 256>>>(
-        (const ERec<R> *)m->rec, m->ell, (int)m->N, D, ofs, nullptr);
-    pff_status st = cudaGetLastError() == cudaSuccess ? PFF_OK : fail(PFF_ERR_CUDA, "merged rows: offsets");
-    if (st == PFF_OK) st = build_merged<R>(m, ofs);
-    cudaFree(ofs);
-    if (st != PFF_OK) return st;
-    if (m->nbc) {
-      // merged rows are the opt-in form (PFF_OP_MERGED); the per-element
-      // records of the default form stay
-      PFF_TRY(dalloc(&m->diagd, (size_t)m->N));
-      CUDA_TRY(cudaMemset(m->diagd, 0, (size_t)m->N * sizeof(double)));
-    }
+        (const ERec<R> *)m->rec, m->ell, (int)m->N, D, m->ecmp, nullptr);
+    CUDA_TRY(cudaGetLastError());
+    PFF_TRY(build_merged<R>(m, m->ecmp));
+    PFF_TRY(dalloc(&m->diagd, (size_t)m->N));
+    CUDA_TRY(cudaMemset(m->diagd, 0, (size_t)m->N * sizeof(double)));
+    if (m->drec) CUDA_TRY(cudaFree(m->drec));
+    m->drec = nullptr;
   }
   m->nblk = (int32_t)((m->N + NB - 1) / NB);
   if (!m->fe) PFF_TRY(dalloc((typename V<R>::T2 **)&m->fe, 3 * (size_t)m->Ne));
@@ -937,7 +938,7 @@ static pff_status configure(pff_mesh *m) {
       c.fam = kFamFused;
       c.U = U;
       int occ = 0;
-      constexpr int T = FusedCfg<false>::threads;
+      const int T = fused_threads(U, false);
       CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, plan_fun<float>(c), T, 0));
       const int64_t wave = (int64_t)nsm * occ;  // a full wave, as for the persistent loop
       const int64_t ctas = std::max<int64_t>(1, (m->N + T - 1) / T);
@@ -1000,6 +1001,7 @@ static Params<R> base_params(pff_mesh *m, const pff_options &o) {
   P.erec = m->erec;
   P.ecmp = m->ecmp;
   P.ecf = m->ecf;
+  P.ecfd = sizeof(R) == 8 ? m->ecfd : nullptr;
   P.nbo = merged ? m->nbo : nullptr;
   P.nbc = merged ? (R *)m->nbc : nullptr;
   P.nmap = merged ? m->nmap : nullptr;
@@ -1009,7 +1011,7 @@ static Params<R> base_params(pff_mesh *m, const pff_options &o) {
   const bool shared = !merged && sizeof(R) == 4 && m->ecmp && m->nbo && m->Dn == 6 && m->D <= 6;
   P.gnbo = shared ? m->nbo : nullptr;
   P.gmap = shared ? m->nmap : nullptr;
-  P.diag = sizeof(R) == 4 ? (R *)m->diagf : (merged ? (R *)m->diagd : nullptr);
+  P.diag = sizeof(R) == 4 ? (R *)m->diagf : (R *)m->diagd;  // FP64: nullable (wide meshes)
   P.flags = m->flags;
   P.st_cta = m->st_cta;
   P.st_rng = m->st_rng;
