@@ -221,7 +221,7 @@ def peaks():
     return 6400.0, "fallback"
 
 
-def ncu_traffic(kernel_prefix, summary="ncu_full_gather_cg_plate_1000x1000_fp32.md"):
+def ncu_traffic(kernel_prefix, summary="ncu_streaming_plate_1000x1000_fp32.md"):
     """DRAM bytes (read + write) from the committed ncu summary: the column of
     the first table whose header names the kernel (per launch, or per CG
     iteration for the CG loop summary), or None when the kernel source
@@ -808,9 +808,14 @@ def kernel_rooflines(prof, iters_mean, N, Ne, prec, form, width, peak, peak_kind
                             "operator records and vectors move; the loop's working set stays in L2, so its "
                             "DRAM traffic (traffic, dram_frac) is a small share of either: L2-latency and "
                             "grid-synchronisation bound; the HBM roofline figures are the streaming kernels'")
-    streaming = {k: dict(bytes=ab[k], ms=prof[k], gbs=ab[k] / (prof[k] * 1e-3) / 1e9,
-                         frac=ab[k] / (prof[k] * 1e-3) / 1e9 / peak)
-                 for k in ("predict", "force", "rhs", "finish") if prof[k] > 0}
+    streaming = {}
+    for k, kn in (("predict", "k_predict"), ("force", "k_force_nc"), ("rhs", "k_dmg_rhs_nc"),
+                  ("finish", "k_dmg_finish")):
+        if prof[k] > 0:
+            t = ncu_traffic(kn) if prec == "fp32" else None
+            streaming[k] = dict(bytes=ab[k], ms=prof[k], gbs=ab[k] / (prof[k] * 1e-3) / 1e9,
+                                frac=ab[k] / (prof[k] * 1e-3) / 1e9 / peak, traffic=t,
+                                dram_frac=t / (prof[k] * 1e-3) / 1e9 / peak if t else None)
     return roofline, streaming
 
 

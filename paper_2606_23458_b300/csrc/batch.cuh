@@ -420,7 +420,7 @@ __global__ void __launch_bounds__(pers_threads(U, false), kPersMinBlocks) kb_cg_
   unsigned int nbar = 0;
   for (;;) {
     typename AC::T v1[1] = {AC::zero()};
-    matvec_rows<R, U>(Q, z.coef[1], tid, stride, v1[0], n1);
+    matvec_rows<R, U>(Q, z.coef[1], tid, stride, v1[0], n1, (z.iters & 1) != 0);
     ++nbar;
     if (!grid_sum<R, 1>(v1, part + (nbar & 1u) * 2u * nb, S, nbar * nb, z.tot, (typename AC::T(*)[1])sh, &z.ok,
                         NoHook(), rank, (int)nb))
@@ -440,7 +440,7 @@ __global__ void __launch_bounds__(pers_threads(U, false), kPersMinBlocks) kb_cg_
     if (z.flag) break;
     typename AC::T v3[3] = {AC::zero(), AC::zero(), AC::zero()};
     bool proj = false;
-    update_rows<R>(Q, z.coef[0], z.coef[1], pid, stride, v3, proj, n1);
+    update_rows<R>(Q, z.coef[0], z.coef[1], pid, stride, v3, proj, n1, (z.iters & 1) != 0);
     typename AC::T v2[2] = {v3[0], v3[1]};
     ++nbar;
     if (!grid_sum<R, 2>(v2, part + (nbar & 1u) * 2u * nb, S, nbar * nb, z.tot, sh, &z.ok, NoHook(), rank,

@@ -1646,12 +1646,13 @@ __device__ __forceinline__ void nb_load6(const Params<float> &P, int i, NbRow6 &
 // pipelined: the next row's records load while this row's neighbour values
 // are gathered; cur holds row i0's records.  Same arithmetic as erec_row.
 __device__ __forceinline__ void nb_rows6(const Params<float> &P, float beta, int i0, int stride, DF &acc,
-                                         NbRow6 cur, int n) {
+                                         NbRow6 cur, int n, int ifirst, bool rev) {
   typedef Acc<float> AC;
-  for (int i = i0; i < n; i += stride) {
+  const int step = rev ? -stride : stride;
+  for (int i = ifirst; rev ? i >= i0 : i < n; i += step) {
     NbRow6 nxt;
-    const int in = i + stride;
-    if (in < n) nb_load6(P, in, nxt);
+    const int in = i + step;
+    if (rev ? in >= i0 : in < n) nb_load6(P, in, nxt);
     float q = 0.f;
     if (!((cur.fl & kNotch) || (P.freef && !P.freef[i]))) {
       const float pc = pnew(P, i, beta);
@@ -1686,7 +1687,8 @@ __device__ __forceinline__ void matvec_rows(const Params<R> &P, R beta, int i0, 
   const int ilast = i0 < n ? i0 + (n - 1 - i0) / stride * stride : i0 - stride;
   if constexpr (sizeof(R) == 8) {
     if (P.nbc || P.ecfd) {  // FP64 merged rows or entry records
-      for (int i = i0; i < n; i += stride) {
+      const int istep = rev ? -stride : stride;
+      for (int i = rev ? ilast : i0; rev ? i >= i0 : i < n; i += istep) {
         R q = 0;
         if (!is_fixed(P, i)) {
           const R pc = pnew(P, i, beta);
@@ -1702,8 +1704,9 @@ __device__ __forceinline__ void matvec_rows(const Params<R> &P, R beta, int i0, 
   if constexpr (sizeof(R) == 4) {
     if (U >= 2 && P.nbc && P.Dn <= 6) {
       NbRow6 first;
-      if (i0 < n) nb_load6(P, i0, first);
-      nb_rows6(P, beta, i0, stride, acc, first, n);
+      const int ifirst = rev ? ilast : i0;
+      if (i0 < n) nb_load6(P, ifirst, first);
+      nb_rows6(P, beta, i0, stride, acc, first, n, ifirst, rev);
       return;
     }
     if (has_erec(P)) {
@@ -1856,7 +1859,9 @@ __device__ __forceinline__ void update_rows(const Params<R> &P, R alpha, R beta,
       pz4[j] = make_float4(pz0.x, pz0.y, pz1.x, pz1.y);
     }
   } else {
-    for (int i = j0; i < n; i += stride) {
+    const int ilast = j0 < n ? j0 + (n - 1 - j0) / stride * stride : j0 - stride;
+    const int istep = rev ? -stride : stride;
+    for (int i = rev ? ilast : j0; rev ? i >= j0 : i < n; i += istep) {
       if (is_fixed(P, i)) continue;
       R2 pz = P.pz[i];
       R x = P.x[i], r = P.r[i];
@@ -2268,14 +2273,16 @@ __device__ __forceinline__ float cg_unew(const float4 v, float al, float be) {
 // gathered); the arithmetic of fused_rows.
 __device__ __forceinline__ void fused_rows6(const Params<float> &P, float al, float be,
                                             const float4 *__restrict__ vin, float4 *__restrict__ vout, int i0,
-                                            int stride, DF (&acc)[3]) {
+                                            int stride, DF (&acc)[3], bool rev) {
   typedef Acc<float> AC;
+  const int jlast = i0 < P.N ? i0 + (P.N - 1 - i0) / stride * stride : i0 - stride;
+  const int step = rev ? -stride : stride;
   NbRow6 cur;
-  if (i0 < P.N) nb_load6(P, i0, cur);
-  for (int j = i0; j < P.N; j += stride) {
+  if (i0 < P.N) nb_load6(P, rev ? jlast : i0, cur);
+  for (int j = rev ? jlast : i0; rev ? j >= i0 : j < P.N; j += step) {
     NbRow6 nxt;
-    const int jn = j + stride;
-    if (jn < P.N) nb_load6(P, jn, nxt);
+    const int jn = j + step;
+    if (rev ? jn >= i0 : jn < P.N) nb_load6(P, jn, nxt);
     const float4 v = vin[j];
     if ((cur.fl & kNotch) || (P.freef && !P.freef[j])) {  // eliminated row: everything stays zero
       vout[j] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -2314,9 +2321,11 @@ __device__ __forceinline__ void fused_rows6(const Params<float> &P, float al, fl
 // (el_rows6's operator, fused_rows6's recurrences).
 __device__ __forceinline__ void fused_el_rows6(const Params<float> &P, float al, float be,
                                                const float4 *__restrict__ vin, float4 *__restrict__ vout, int i0,
-                                               int stride, DF (&acc)[3]) {
+                                               int stride, DF (&acc)[3], bool rev) {
   typedef Acc<float> AC;
-  for (int j = i0; j < P.N; j += stride) {
+  const int jlast = i0 < P.N ? i0 + (P.N - 1 - i0) / stride * stride : i0 - stride;
+  const int step = rev ? -stride : stride;
+  for (int j = rev ? jlast : i0; rev ? j >= i0 : j < P.N; j += step) {
     ElRow6 cur;
     el_load6(P, j, cur);
     const float4 v = vin[j];
@@ -2343,17 +2352,20 @@ __device__ __forceinline__ void fused_el_rows6(const Params<float> &P, float al,
 
 template <int U>
 __device__ __forceinline__ void fused_rows(const Params<float> &P, float al, float be, const float4 *__restrict__ vin,
-                                           float4 *__restrict__ vout, int i0, int stride, DF (&acc)[3]) {
+                                           float4 *__restrict__ vout, int i0, int stride, DF (&acc)[3],
+                                           bool rev = false) {
   typedef Acc<float> AC;
   if (U >= 2 && P.nbc && P.Dn <= 6) {
-    fused_rows6(P, al, be, vin, vout, i0, stride, acc);
+    fused_rows6(P, al, be, vin, vout, i0, stride, acc, rev);
     return;
   }
   if (U >= 2 && P.gnbo) {
-    fused_el_rows6(P, al, be, vin, vout, i0, stride, acc);
+    fused_el_rows6(P, al, be, vin, vout, i0, stride, acc, rev);
     return;
   }
-  for (int j = i0; j < P.N; j += stride) {
+  const int jlast = i0 < P.N ? i0 + (P.N - 1 - i0) / stride * stride : i0 - stride;
+  const int jstep = rev ? -stride : stride;
+  for (int j = rev ? jlast : i0; rev ? j >= i0 : j < P.N; j += jstep) {
     const float4 v = vin[j];
     if (is_fixed(P, j)) {  // eliminated row: everything stays zero
       vout[j] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -2633,7 +2645,7 @@ __global__ void __launch_bounds__(fused_threads(U, ST), fused_minb(U, ST)) k_cg_
                     reinterpret_cast<const uint16_t *>(stage_smem + L.slot), L.mc,
                     reinterpret_cast<const float4 *>(stage_smem), vout, acc);
     } else {
-      fused_rows<U>(P, z.al, z.be, vin, vout, tid, stride, acc);
+      fused_rows<U>(P, z.al, z.be, vin, vout, tid, stride, acc, (pass & 1) != 0);  // alternate directions
     }
     ++nbar;
     ++pass;
