@@ -69,6 +69,8 @@ def parse():
                     help="skip the 1M-node volumetric-deviatoric and AT1 configurations")
     ap.add_argument("--no-inversion", action="store_true",
                     help="skip the gradient checks and L-BFGS recovery on the 500x500 plate")
+    ap.add_argument("--fuse", choices=["auto", "separate", "fused"], default="auto",
+                    help="force and damage right-hand side: autotuned, two kernels, or one (pff_options.fuse)")
     ap.add_argument("--nvtx-range", action="store_true",
                     help="wrap the timed steps in the NVTX range 'timed' (for ncu --nvtx-include timed/)")
     ap.add_argument("--loop", choices=["graph", "host"], default="graph",
@@ -410,8 +412,11 @@ def cpu_baseline(args, budget_s=20.0):
 def batched(pff, dev, steps=500, warmup=5):
     """The batched workload: 64 independent plates drawn from SplitMix64
     seed 1 (200..700 x 80..280 cells, Gc in [1, 5] J/m^2, traction in
-    [0.5, 2] MPa), FP32 with FP64-class reductions, all plates advanced by
-    one CUDA graph launch per step with per-plate CG convergence."""
+    [0.5, 2] MPa), FP32 with FP64-class reductions, 500 steps, all plates
+    advanced by one CUDA graph launch per step, the damage solves of all
+    plates in the CG loop form and with the gathers in flight the batch's
+    autotuner picked (per-plate persistent launch or kernels per phase;
+    `tuning`), each plate to its own stop."""
     import torch
     plates = []
     for dr in S.batch_draws(64, seed=1):
@@ -435,7 +440,8 @@ def batched(pff, dev, steps=500, warmup=5):
     it = log.cpu().numpy()
     return dict(workload="64 plates, seed 1", plates=b.nplates, nodes=nodes, steps=steps, warmup=warmup,
                 value=nodes * steps / (ms / 1e3), unit="node-updates/s", ms_per_step=ms / steps,
-                cg_iters_mean=float(it.mean()), cg_iters_max=int(it.max()))
+                cg_iters_mean=float(it.mean()), cg_iters_max=int(it.max()), cg_iters_min=int(it.min()),
+                tuning=b.tuning())
 
 
 def fwd_adjoint(pff, dev, steps=300, policies=((0, "recompute"), (25, "recompute"), (25, "damage_tape"))):
@@ -847,7 +853,8 @@ def run_ours(args):
     opts = pff.options(cg_tol=c["cg_tol"], t_ramp=c["t_ramp"],
                        loop_mode=pff.PFF_LOOP_HOST if args.loop == "host" else pff.PFF_LOOP_GRAPH,
                        variant=args.variant,
-                       cg_kernel={v: k for k, v in pff.CG_KINDS.items()}[args.cg_kernel])
+                       cg_kernel={v: k for k, v in pff.CG_KINDS.items()}[args.cg_kernel],
+                       fuse={"auto": 0, "separate": 1, "fused": 2}[args.fuse])
     st = mesh.new_state(device=dev)
     total = args.warmup + args.steps
     log = torch.zeros(total + args.e2e_steps, 2, dtype=torch.int32, device=dev)

@@ -656,11 +656,16 @@ __global__ void __launch_bounds__(kQsPersThreads, 2) k_qs_cg_rows(QkParams<float
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
   unsigned int nbar = 0;
   bool done = false;
+  // rows last first on odd iterations: each pass starts on the blocks and
+  // vectors the previous one touched last (the working set exceeds L2)
+  const int ilast = tid < I.N ? tid + (I.N - 1 - tid) / stride * stride : tid - stride;
   for (;;) {
     const float beta = (float)beta_d;
+    const bool rev = (iters & 1) != 0;
+    const int istep = rev ? -stride : stride;
     // rows: q = K_T p_new on the free dofs, p_new . q
     typename AC::T v1[1] = {AC::zero()};
-    for (int i = tid; i < I.N; i += stride) {
+    for (int i = rev ? ilast : tid; rev ? i >= tid : i < I.N; i += istep) {
       const K2 pc = qs_pnew(I, i, beta);
       float qx = 0.f, qy = 0.f;
       if (I.nbk) {
@@ -724,7 +729,7 @@ __global__ void __launch_bounds__(kQsPersThreads, 2) k_qs_cg_rows(QkParams<float
     __syncthreads();
     const float alpha = (float)alpha_d;
     typename AC::T v2[2] = {AC::zero(), AC::zero()};
-    for (int i = tid; i < I.N; i += stride) {
+    for (int i = rev ? ilast : tid; rev ? i >= tid : i < I.N; i += istep) {
       const K2 pn = qs_pnew(I, i, beta), q = I.q[i], dg = I.dg[i];
       K2 x = I.x[i], r = I.r[i];
       x.x = fmaf(alpha, pn.x, x.x);
