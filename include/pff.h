@@ -224,13 +224,17 @@ pff_status pff_mesh_set_gc_field(pff_mesh *mesh, const double *gc);
  *    and applies that element's own coefficients; no two elements'
  *    coupling coefficients are ever added together.  The coefficients of
  *    an element (they depend on H, which is fixed while a solve runs) are
- *    evaluated once per solve by the right-hand-side pass: FP32 meshes keep
- *    them per incidence entry (row a of element e: the coefficients of p_b
- *    and p_c with 16-bit neighbour offsets, 12 bytes; the row's own terms
- *    sum_e A^e_aa p_a are applied as diag_a p_a through the Jacobi diagonal
- *    the preconditioner needs anyway), FP64 meshes one 64-byte record per
- *    element (ids, three stiffness weights, mass) from which every product
- *    evaluates whole element rows.
+ *    evaluated once per solve by the right-hand-side pass and kept per
+ *    incidence entry (row a of element e: the coefficients of p_b and p_c,
+ *    FP32 or FP64 with the mesh; the row's own terms sum_e A^e_aa p_a are
+ *    applied as diag_a p_a through the Jacobi diagonal the preconditioner
+ *    needs anyway).  On conforming meshes whose vertex fans have at most six
+ *    triangles the entries are stored in fan order (triangle k of a vertex
+ *    couples its neighbours v_k and v_{k+1}), so a row gathers each
+ *    distinct neighbour once; other meshes keep incidence order with 16-bit
+ *    neighbour offsets, and FP64 meshes too wide for those one 64-byte
+ *    record per element from which every product evaluates whole element
+ *    rows.
  *  PFF_OP_MERGED: the two elements' coefficients of each mesh edge summed
  *    once per solve into one coefficient per distinct neighbour -- the
  *    solve's sparse operator assembled in an ELL layout and thrown away
@@ -241,9 +245,11 @@ pff_status pff_mesh_set_gc_field(pff_mesh *mesh, const double *gc);
  * (re-timed on the next solve).  Host-only; no device work. */
 enum { PFF_OP_ELEMENT = 0, PFF_OP_MERGED = 1 };
 pff_status pff_mesh_set_operator(pff_mesh *mesh, int32_t form);
-/* The form in use and whether PFF_OP_MERGED is available (host outputs,
- * each nullable). */
-pff_status pff_mesh_get_operator(const pff_mesh *mesh, int32_t *form, int32_t *merged_available);
+/* The form in use, whether PFF_OP_MERGED is available, and whether the
+ * element-wise entries are stored in fan order (1) or incidence order (0)
+ * (host outputs, each nullable). */
+pff_status pff_mesh_get_operator(const pff_mesh *mesh, int32_t *form, int32_t *merged_available,
+                                 int32_t *fan_order);
 
 /* Sets the material: the plane model's Lame constants (Sec. 2.1), lumped mass
  * m_i = rho sum A_e / 3 and the stable step dt = cfl * h_min / c_p with

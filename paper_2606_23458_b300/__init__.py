@@ -121,7 +121,7 @@ _sig = {
                              C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_double)],
     "pff_batch_run": [_P, C.POINTER(pff_state), C.c_int64, C.c_int64, C.POINTER(pff_options), _P, _P],
     "pff_mesh_set_operator": [_P, C.c_int32],
-    "pff_mesh_get_operator": [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int32)],
+    "pff_mesh_get_operator": [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)],
     "pff_batch_set_operator": [_P, C.c_int32],
     "pff_batch_tuning": [_P, _P, _P],
     "pff_damage_solve_noalloc": [_P, _P, _P, _P, C.POINTER(pff_options), C.POINTER(C.c_int32),
@@ -500,8 +500,14 @@ class Mesh:
     def operator(self):
         """(form name, whether "merged" is available on this mesh)."""
         f = C.c_int32(); a = C.c_int32()
-        _check(_lib.pff_mesh_get_operator(self._h, C.byref(f), C.byref(a)))
+        _check(_lib.pff_mesh_get_operator(self._h, C.byref(f), C.byref(a), None))
         return {v: k for k, v in OPERATORS.items()}[f.value], bool(a.value)
+
+    def fan_order(self):
+        """Whether the element-wise entries are stored in fan order."""
+        v = C.c_int32()
+        _check(_lib.pff_mesh_get_operator(self._h, None, None, C.byref(v)))
+        return bool(v.value)
 
     def set_gc_field(self, gc):
         """Per-element toughness Gc_e (array of Ne, host), or None for the

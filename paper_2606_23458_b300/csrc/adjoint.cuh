@@ -168,7 +168,7 @@ __device__ __forceinline__ void split_tangent(const Params<R> &P, R exx, R eyy, 
 // entry record.
 template <typename R>
 __device__ __forceinline__ void adj_rhs_entry(const AdjParams<R> &A, const Slot<R> &S, int en, int k, int i,
-                                              R &dgc, R &axc, typename Params<R>::R2 *cf) {
+                                              R &dgc, R &axc, typename Params<R>::R2 *cf, uint32_t fm) {
   typedef typename Params<R>::R4 R4;
   const Params<R> &P = A.P;
   const int e = en >> 2, a = en & 3;
@@ -185,7 +185,7 @@ __device__ __forceinline__ void adj_rhs_entry(const AdjParams<R> &A, const Slot<
   if (cf)
     *cf = erec_coef<R>(G, a, kA, mA);
   else if (has_erec(P))
-    put_erec(P, k, i, G, a, kA, mA);
+    put_erec(P, k, i, G, a, kA, mA, fm);
   const R l0 = (P.flags[t.x] & kNotch) ? R(0) : P.x[t.x];
   const R l1 = (P.flags[t.y] & kNotch) ? R(0) : P.x[t.y];
   const R l2 = (P.flags[t.z] & kNotch) ? R(0) : P.x[t.z];
@@ -229,6 +229,7 @@ __global__ void __launch_bounds__(256) k_adj_rhs(AdjParams<R> A) {
     NbAcc<R> nacc;
     nacc.zero();
     if (merge) nacc.load_map(P, i);
+    const uint32_t fm = fan_word(P, i);
     // two incidence entries in flight, summed in slot order
     for (int k = 0; k < P.D; k += 2) {
       int en[2];
@@ -238,7 +239,7 @@ __global__ void __launch_bounds__(256) k_adj_rhs(AdjParams<R> A) {
       typename Params<R>::R2 cf[2];
 #pragma unroll
       for (int u = 0; u < 2; ++u)
-        if (en[u] >= 0) adj_rhs_entry(A, S, en[u], k + u, i, cd[u], ca[u], merge ? &cf[u] : nullptr);
+        if (en[u] >= 0) adj_rhs_entry(A, S, en[u], k + u, i, cd[u], ca[u], merge ? &cf[u] : nullptr, fm);
 #pragma unroll
       for (int u = 0; u < 2; ++u)
         if (en[u] >= 0) {

@@ -205,6 +205,7 @@ __global__ void __launch_bounds__(256) kb_rhs(Params<R> P, Batch B) {
       NbAcc<R> nacc;
       nacc.zero();
       if (merge) nacc.load_map(Q, i);
+      const uint32_t fm = fan_word(Q, i);
       for (int k = 0; k < P.D; k += U) {
         R4 o[U];
         typename Params<R>::R2 cf[U];
@@ -213,7 +214,7 @@ __global__ void __launch_bounds__(256) kb_rhs(Params<R> P, Batch B) {
         for (int u = 0; u < U; ++u) en[u] = k + u < P.D ? __ldg(&P.ell[(size_t)(k + u) * P.N + i]) : -1;
 #pragma unroll
         for (int u = 0; u < U; ++u)
-          if (en[u] >= 0) o[u] = rhs_entry(Q, en[u], k + u, i, -1, merge ? &cf[u] : nullptr);
+          if (en[u] >= 0) o[u] = rhs_entry(Q, en[u], k + u, i, -1, merge ? &cf[u] : nullptr, fm);
 #pragma unroll
         for (int u = 0; u < U; ++u)
           if (en[u] >= 0) {

@@ -152,6 +152,16 @@ template <typename R> struct Params {
                   // coefficients; an empty slot is offsets 0, coefficients 0.
                   // Nullable; at most one of erec and ecmp is set.
   double2 *ecfd;  // FP64 meshes: the entry coefficients in FP64 (with ecmp)
+  // Fan order (compact meshes whose every vertex fan fits six positions):
+  // fno packs the row's distinct neighbours v_0..v_{m-1} as 16-bit offsets
+  // in counter-clockwise order around the vertex (three words, layout
+  // w N + i, zero padded); fmap[i] holds m in its top byte and, in 4-bit
+  // fields, the fan position of each incidence slot.  With them the entry
+  // records are stored in fan position (the fan's k-th triangle couples
+  // v_k and v_{k+1 mod m}, its two coefficients in that order) and a row
+  // gathers each distinct neighbour once.  Nullable.
+  const uint32_t *__restrict__ fno;
+  const uint32_t *__restrict__ fmap;
   // Compact meshes (both precisions) whose rows have at most kNbMax distinct
   // neighbours:
   // the same rows with each neighbour's coefficients merged (rows sum the
@@ -755,22 +765,41 @@ __device__ __forceinline__ bool has_erec(const Params<R> &P) {
 // (slot k, node i); the neighbour ids or offsets depend on the mesh alone
 // and are written once (k_erec_ids).
 template <typename R>
-__device__ __forceinline__ typename Params<R>::R2 erec_coef(const typename Params<R>::R4 &G, int a, R kA, R mA) {
+__device__ __forceinline__ typename Params<R>::R2 erec_coef(const typename Params<R>::R4 &G, int a, R kA, R mA,
+                                                            bool ccw = false) {
   R gx, gy, gbx, gby, gcx, gcy;
   slot_grad<R>(G, a, gx, gy);
-  slot_grad<R>(G, a == 0 ? 1 : 0, gbx, gby);
-  slot_grad<R>(G, a == 2 ? 1 : 2, gcx, gcy);
+  // (b, c): the element's other slots in increasing order, or
+  // counter-clockwise from a ((a+1, a+2) mod 3)
+  const int sb = ccw ? (a == 2 ? 0 : a + 1) : (a == 0 ? 1 : 0);
+  const int sc = ccw ? (a == 0 ? 2 : a - 1) : (a == 2 ? 1 : 2);
+  slot_grad<R>(G, sb, gbx, gby);
+  slot_grad<R>(G, sc, gcx, gcy);
   typename Params<R>::R2 c;  // roundings spelled out: every schedule gets the same bits
   c.x = rfma(kA, rfma(gx, gbx, rmul(gy, gby)), mA);
   c.y = rfma(kA, rfma(gx, gcx, rmul(gy, gcy)), mA);
   return c;
 }
 
+// Fan word of row i for put_erec (kFanLoad: put_erec reads it itself).
+constexpr uint32_t kFanLoad = 0xffffffffu;
+template <typename R>
+__device__ __forceinline__ uint32_t fan_word(const Params<R> &P, int i) {
+  return P.fmap ? __ldg(&P.fmap[i]) : 0u;
+}
+
 template <typename R>
 __device__ __forceinline__ void put_erec(const Params<R> &P, int k, int i, const typename Params<R>::R4 &G, int a,
-                                         R kA, R mA) {
-  const typename Params<R>::R2 cr = erec_coef<R>(G, a, kA, mA);
-  const size_t q = (size_t)k * P.N + i;
+                                         R kA, R mA, uint32_t fm = kFanLoad) {
+  // fan order: at the fan position of incidence slot k, the pair ordered
+  // (v_k, v_{k+1}), counter-clockwise from the vertex
+  const bool fan = P.fmap != nullptr;
+  const typename Params<R>::R2 cr = erec_coef<R>(G, a, kA, mA, fan);
+  size_t q = (size_t)k * P.N + i;
+  if (fan) {
+    if (fm == kFanLoad) fm = __ldg(&P.fmap[i]);
+    q = (size_t)((fm >> (4 * k)) & 15u) * P.N + i;
+  }
   if constexpr (sizeof(R) == 8) {
     if (P.ecfd) P.ecfd[q] = make_double2((double)cr.x, (double)cr.y);
     return;
@@ -1038,7 +1067,7 @@ template <typename R>
 __device__ __forceinline__ typename Params<R>::R4 rhs_entry_core(const Params<R> &P, int e, int a, const int4 &t,
                                                                  R A, const typename Params<R>::R4 &G, R h, R sg,
                                                                  int slot, int node, int csr,
-                                                                 typename Params<R>::R2 *cf) {
+                                                                 typename Params<R>::R2 *cf, uint32_t fm = kFanLoad) {
   typedef typename Params<R>::R4 R4;
   const R w = P.wbase * sg + R(2) * h;
   const bool n0 = P.flags[t.x] & kNotch, n1 = P.flags[t.y] & kNotch, n2 = P.flags[t.z] & kNotch;
@@ -1058,7 +1087,7 @@ __device__ __forceinline__ typename Params<R>::R4 rhs_entry_core(const Params<R>
       node = a == 0 ? t.x : (a == 1 ? t.y : t.z);
       slot = csr - __ldg(&P.ptr[node]);
     }
-    if (slot >= 0) put_erec(P, slot, node, G, a, kA, mA);
+    if (slot >= 0) put_erec(P, slot, node, G, a, kA, mA, fm);
   }
   R4 o;
   o.x = w * A * (R(1) / R(3));
@@ -1072,14 +1101,15 @@ __device__ __forceinline__ typename Params<R>::R4 rhs_entry_core(const Params<R>
 template <typename R>
 __device__ __forceinline__ typename Params<R>::R4 rhs_entry(const Params<R> &P, int en, int slot = -1,
                                                             int node = -1, int csr = -1,
-                                                            typename Params<R>::R2 *cf = nullptr) {
+                                                            typename Params<R>::R2 *cf = nullptr,
+                                                            uint32_t fm = kFanLoad) {
   typedef typename Params<R>::R4 R4;
   const int e = en >> 2, a = en & 3;
   int4 t;
   R A;
   R4 G;
   load_elem(P, e, t, A, G);
-  return rhs_entry_core<R>(P, e, a, t, A, G, P.Hr[e], gc_scale(P, e), slot, node, csr, cf);
+  return rhs_entry_core<R>(P, e, a, t, A, G, P.Hr[e], gc_scale(P, e), slot, node, csr, cf, fm);
 }
 
 // Node i of the right-hand side: r = b - A x0, b_eff = b - A 1_D, the
@@ -1203,6 +1233,7 @@ __global__ void __launch_bounds__(256) k_dmg_rhs_nc(Params<R> P) {
     NbAcc<R> nacc;
     nacc.zero();
     if (merge) nacc.load_map(P, i);
+    const uint32_t fm = fan_word(P, i);
     for (int k = 0; k < P.D; k += U) {
       R4 o[U];
       typename Params<R>::R2 cf[U];
@@ -1211,7 +1242,7 @@ __global__ void __launch_bounds__(256) k_dmg_rhs_nc(Params<R> P) {
       for (int u = 0; u < U; ++u) en[u] = k + u < P.D ? __ldg(&P.ell[(size_t)(k + u) * P.N + i]) : -1;
 #pragma unroll
       for (int u = 0; u < U; ++u)
-        if (en[u] >= 0) o[u] = rhs_entry(P, en[u], k + u, i, -1, merge ? &cf[u] : nullptr);
+        if (en[u] >= 0) o[u] = rhs_entry(P, en[u], k + u, i, -1, merge ? &cf[u] : nullptr, fm);
 #pragma unroll
       for (int u = 0; u < U; ++u)
         if (en[u] >= 0) {
@@ -1242,7 +1273,7 @@ __global__ void __launch_bounds__(256) k_dmg_rhs_nc(Params<R> P) {
 // idempotent), so no thread depends on another's write.
 template <typename R>
 __device__ __forceinline__ void force_rhs_entry(const Params<R> &P, int en, int slot, int node, R &fx, R &fy, R &psip,
-                                                typename Params<R>::R4 &o, typename Params<R>::R2 *cf) {
+                                                typename Params<R>::R4 &o, typename Params<R>::R2 *cf, uint32_t fm) {
   typedef typename Params<R>::R4 R4;
   const int e = en >> 2, a = en & 3;
   int4 t;
@@ -1267,7 +1298,7 @@ __device__ __forceinline__ void force_rhs_entry(const Params<R> &P, int en, int 
     const long long hb = __double_as_longlong(P.H[e]);
     h = pb > hb ? (float)psip : (float)__longlong_as_double(hb);
   }
-  o = rhs_entry_core<R>(P, e, a, t, A, G, h, gc_scale(P, e), slot, node, -1, cf);
+  o = rhs_entry_core<R>(P, e, a, t, A, G, h, gc_scale(P, e), slot, node, -1, cf, fm);
 }
 
 template <typename R, int U>
@@ -1283,6 +1314,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 1) k_force_rhs_nc(Pa
     NbAcc<R> nacc;
     nacc.zero();
     if (merge) nacc.load_map(P, i);
+    const uint32_t fm = fan_word(P, i);
     for (int k = 0; k < P.D; k += U) {
       int en[U];
       R cx[U], cy[U], pp[U];
@@ -1293,7 +1325,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 1) k_force_rhs_nc(Pa
 #pragma unroll
       for (int u = 0; u < U; ++u)
         if (en[u] >= 0)  // a notch row has no damage row: only the element records are written
-          force_rhs_entry(P, en[u], notch ? -1 : k + u, i, cx[u], cy[u], pp[u], o[u], merge ? &cf[u] : nullptr);
+          force_rhs_entry(P, en[u], notch ? -1 : k + u, i, cx[u], cy[u], pp[u], o[u], merge ? &cf[u] : nullptr, fm);
 #pragma unroll
       for (int u = 0; u < U; ++u)
         if (en[u] >= 0) {
@@ -1328,6 +1360,43 @@ __device__ __forceinline__ R pnew(const Params<R> &P, int j, R beta) {
   return fma(beta, v.x, v.y);
 }
 
+// Fan rows: the row's six distinct-neighbour values val(i + o) gathered
+// once, then per fan position k the triangle's two coefficients applied to
+// v_k and v_{k+1 mod m} (explicit fma and non-contracted adds, positions in
+// order; positions past the fan have zero coefficients and add an exact 0).
+template <typename R, typename C2, typename F>
+__device__ __forceinline__ R fan_row(const Params<R> &P, const C2 *cfs, int i, R q, F val) {
+  uint32_t w[3];
+  C2 cf[6];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) w[j] = __ldg(&P.fno[(size_t)j * P.N + i]);
+  const int m = (int)(__ldg(&P.fmap[i]) >> 24);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    if (k < P.D) {
+      cf[k] = __ldg(&cfs[(size_t)k * P.N + i]);
+    } else {
+      cf[k].x = 0;
+      cf[k].y = 0;
+    }
+  }
+  R v[6];
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    const uint32_t x = w[j >> 1];
+    v[j] = val(i + ((j & 1) ? (int)x >> 16 : (int)(int16_t)(x & 0xffffu)));
+  }
+  R c[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const R vc = (k + 1 == m) ? v[0] : v[k < 5 ? k + 1 : 0];
+    c[k] = rfma(cf[k].x, v[k], rmul(cf[k].y, vc));
+  }
+#pragma unroll
+  for (int k = 0; k < 6; ++k) q = radd(q, c[k]);
+  return q;
+}
+
 // Row i of q = A p_new from the FP32 entry records: diag_i p_i, then per
 // incidence slot in order (U records in flight) c_b p_b + c_c p_c, rounded
 // the same way in every schedule (explicit fma and non-contracted adds).
@@ -1336,6 +1405,7 @@ template <int U>
 __device__ __forceinline__ float erec_row(const Params<float> &P, int i, float beta, float pc) {
   float q = P.diag[i] * pc;
   if (P.nbc) return nb_row_any(P, i, q, [&](int j) { return pnew(P, j, beta); });
+  if (P.fno) return fan_row(P, P.ecf, i, q, [&](int j) { return pnew(P, j, beta); });
   if (P.ecmp) {
     if (U >= 3 && P.D <= 6) {
       // the whole row at once: six slots' records, then their twelve
@@ -1462,6 +1532,7 @@ __device__ __forceinline__ void el_gather6(const ElRow6 &r, int i, float (&v)[6]
 template <int U>
 __device__ __forceinline__ double erec_row_d(const Params<double> &P, int i, double beta, double pc) {
   double q = P.diag[i] * pc;
+  if (P.fno) return fan_row(P, P.ecfd, i, q, [&](int j) { return pnew(P, j, beta); });
   for (int k = 0; k < P.D; k += U) {
     uint32_t w[U];
     double2 cf[U];
@@ -2384,6 +2455,8 @@ __device__ __forceinline__ void fused_rows(const Params<float> &P, float al, flo
     float wq = P.diag[j] * un;
     if (P.nbc) {
       wq = nb_row_any(P, j, wq, [&](int n) { return cg_unew(vin[n], al, be); });
+    } else if (P.fno) {
+      wq = fan_row(P, P.ecf, j, wq, [&](int n) { return cg_unew(vin[n], al, be); });
     } else if (P.ecmp) {
       for (int k = 0; k < P.D; k += U) {
         uint32_t w[U];

@@ -269,6 +269,8 @@ struct pff_mesh {
   uint32_t *ecmp = nullptr;  // FP32, compact entry records: packed 16-bit neighbour offsets (D x N)
   float2 *ecf = nullptr;     // FP32, compact entry records: coefficients (D x N)
   double2 *ecfd = nullptr;   // FP64, compact entry records: coefficients (D x N)
+  uint32_t *fno = nullptr;   // fan order: distinct neighbour offsets (3 x N)
+  uint32_t *fmap = nullptr;  // fan order: neighbour count and slot positions (N)
   int64_t span = 0;          // largest node-id difference within an element
   uint32_t *nbo = nullptr;   // merged rows: neighbour offsets (Dn / 2 x N)
   void *nbc = nullptr;       // merged rows: coefficients (Dn x N, kernel precision)
@@ -348,7 +350,8 @@ static void mesh_free(pff_mesh *m) {
   free_graph(m->step_g);
   free_graph(m->mech_g);
   void *ptrs[] = {m->gcs, m->st_cta, m->st_rng, m->st_nrng, m->st_lrec, m->st_slot, m->cgv, m->cgp,
-                  m->ptr, m->ent, m->ell, m->rec, m->drec, m->erec, m->ecmp, m->ecf, m->ecfd, m->nbo, m->nbc, m->nmap,
+                  m->ptr, m->ent, m->ell, m->rec, m->drec, m->erec, m->ecmp, m->ecf, m->ecfd, m->fno, m->fmap,
+                  m->nbo, m->nbc, m->nmap,
                   m->diagf, m->diagd, m->fe, m->fext, m->minv,
                   m->area_d,
                   m->flags,
@@ -823,12 +826,80 @@ static pff_status build_merged(pff_mesh *m, const uint32_t *ofs) {
   return PFF_OK;
 }
 
+// Fan order of every row (host, once per mesh).  Around vertex i the
+// counter-clockwise pair (b, c) of each incident triangle (for local slot a
+// of (t0, t1, t2): (t1, t2), (t2, t0), (t0, t1)) links b to c; in a
+// conforming triangulation the triangles chain into a fan, closed around an
+// interior vertex (m = d neighbours) or open at the boundary (m = d + 1,
+// starting at the b that is no triangle's c).  Position k of the fan is the
+// triangle from v_k to v_{k+1 mod m}.  Rows without triangles stay empty.
+// Tables are built only if every row's fan has at most six positions and
+// six neighbours within 2^15 node ids (else the records stay in incidence
+// order).
+static pff_status build_fan(pff_mesh *m, const std::vector<int32_t> &ptr, const int32_t *tri) {
+  const int64_t N = m->N;
+  if (!tri || m->D > 6 || m->span >= 32768 || !m->ecmp) return PFF_OK;
+  std::vector<int32_t> ent(ptr[N]);
+  CUDA_TRY(cudaMemcpy(ent.data(), m->ent, ent.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+  std::vector<uint32_t> fno(3 * (size_t)N, 0u), fmap((size_t)N, 0u);
+  for (int64_t i = 0; i < N; ++i) {
+    const int d = ptr[i + 1] - ptr[i];
+    if (d == 0) continue;
+    int b[6], c[6], pos[6], v[7];
+    for (int j = 0; j < d; ++j) {
+      const int en = ent[ptr[i] + j], e = en >> 2, a = en & 3;
+      const int32_t t0 = tri[3 * (int64_t)e], t1 = tri[3 * (int64_t)e + 1], t2 = tri[3 * (int64_t)e + 2];
+      b[j] = a == 0 ? t1 : (a == 1 ? t2 : t0);
+      c[j] = a == 0 ? t2 : (a == 1 ? t0 : t1);
+      pos[j] = -1;
+    }
+    int start = -1, starts = 0;
+    for (int j = 0; j < d; ++j) {
+      bool inner = false;
+      for (int k = 0; k < d; ++k) inner = inner || c[k] == b[j];
+      if (!inner) {
+        start = j;
+        ++starts;
+      }
+    }
+    if (starts > 1) return PFF_OK;  // not a single fan (non-manifold vertex)
+    const bool closed = start < 0;
+    int cur = closed ? 0 : start;
+    v[0] = b[cur];
+    for (int k = 0; k < d; ++k) {
+      if (cur < 0 || pos[cur] >= 0) return PFF_OK;
+      pos[cur] = k;
+      v[k + 1] = c[cur];
+      int nxt = -1;
+      for (int j = 0; j < d; ++j)
+        if (pos[j] < 0 && b[j] == c[cur]) nxt = j;
+      cur = nxt;
+    }
+    const int mcount = closed ? d : d + 1;
+    if (closed && v[d] != v[0]) return PFF_OK;
+    if (mcount > 6) return PFF_OK;
+    uint32_t f = (uint32_t)mcount << 24;
+    for (int j = 0; j < d; ++j) f |= (uint32_t)pos[j] << (4 * j);
+    fmap[i] = f;
+    for (int k = 0; k < mcount; ++k) {
+      const int64_t o = (int64_t)v[k] - i;
+      if (o < -32768 || o > 32767 || o == 0) return PFF_OK;
+      fno[(size_t)(k >> 1) * N + i] |= (uint32_t)(uint16_t)(int16_t)o << (16 * (k & 1));
+    }
+  }
+  PFF_TRY(dalloc(&m->fno, 3 * (size_t)N));
+  PFF_TRY(dalloc(&m->fmap, (size_t)N));
+  CUDA_TRY(cudaMemcpy(m->fno, fno.data(), fno.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(m->fmap, fmap.data(), fmap.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
+  return PFF_OK;
+}
+
 // Launch geometry.  Node-block kernels stage one value set per incidence
 // entry of a block of NB nodes in shared memory; NB is halved until the
 // largest block's entries fit in 40 KB.  Grids are the smaller of the
 // work and one full wave (SMs x resident blocks), with grid-stride loops.
 template <typename R>
-static pff_status configure(pff_mesh *m) {
+static pff_status configure(pff_mesh *m, const int32_t *tri_host) {
   std::vector<int32_t> ptr(m->N + 1);
   CUDA_TRY(cudaMemcpy(ptr.data(), m->ptr, (m->N + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
   const size_t per_entry = sizeof(typename V<R>::T4);  // the widest staged record (rhs)
@@ -890,6 +961,7 @@ static pff_status configure(pff_mesh *m) {
     if (m->drec) CUDA_TRY(cudaFree(m->drec));
     m->drec = nullptr;
   }
+  if (!m->fno) PFF_TRY(build_fan(m, ptr, tri_host));
   m->nblk = (int32_t)((m->N + NB - 1) / NB);
   if (!m->fe) PFF_TRY(dalloc((typename V<R>::T2 **)&m->fe, 3 * (size_t)m->Ne));
   const size_t sm_ep[KP_COUNT] = {0, 0, maxE * sizeof(typename V<R>::T4),
@@ -1008,7 +1080,13 @@ static Params<R> base_params(pff_mesh *m, const pff_options &o) {
   P.Dn = merged ? m->Dn : 0;
   // element-wise form on rows with at most six slots and six distinct
   // neighbours: gather each distinct neighbour once (FP32 compact records)
-  const bool shared = !merged && sizeof(R) == 4 && m->ecmp && m->nbo && m->Dn == 6 && m->D <= 6;
+  // element-wise form in fan order (each distinct neighbour gathered once,
+  // a fixed pattern); else, FP32 rows with at most six slots and six
+  // distinct neighbours gather through the merged rows' slot maps in the
+  // single-reduction loop
+  P.fno = merged ? nullptr : m->fno;
+  P.fmap = merged ? nullptr : m->fmap;
+  const bool shared = !merged && !m->fno && sizeof(R) == 4 && m->ecmp && m->nbo && m->Dn == 6 && m->D <= 6;
   P.gnbo = shared ? m->nbo : nullptr;
   P.gmap = shared ? m->nmap : nullptr;
   P.diag = sizeof(R) == 4 ? (R *)m->diagf : (R *)m->diagd;  // FP64: nullable (wide meshes)
@@ -2052,6 +2130,9 @@ static pff_status qs_run_t(pff_mesh *m, const pff_state *st, const uint8_t *bc_h
   I.nbo = qnbo;
   I.nmap = qnmap;
   I.nbk = nbk;
+  // the element-wise tangent in fan order where the mesh has fan tables
+  I.fno = rows && !nbk ? m->fno : nullptr;
+  I.fmap = rows && !nbk ? m->fmap : nullptr;
   I.qs = qs;
   I.part = Q.P.part;
   I.ticket = Q.P.ticket;
@@ -2336,9 +2417,9 @@ pff_status pff_mesh_create(int64_t N, const double *xy, int64_t Ne, const int32_
   CSTEP(cudaGetLastError());
   CSTEP(cudaDeviceSynchronize());
   if (precision == PFF_FP64)
-    STEP(configure<double>(m));
+    STEP(configure<double>(m, tri));
   else
-    STEP(configure<float>(m));
+    STEP(configure<float>(m, tri));
   // workspaces
   const int64_t maxblocks = (N + 31) / 32;
   STEP(dalloc(&m->x, N + 2));
@@ -3258,10 +3339,12 @@ pff_status pff_mesh_set_operator(pff_mesh *m, int32_t form) {
   return PFF_OK;
 }
 
-pff_status pff_mesh_get_operator(const pff_mesh *m, int32_t *form, int32_t *merged_available) {
+pff_status pff_mesh_get_operator(const pff_mesh *m, int32_t *form, int32_t *merged_available,
+                                 int32_t *fan_order) {
   if (!m) return fail(PFF_ERR_ARG, "null mesh");
   if (form) *form = m->dop;
   if (merged_available) *merged_available = m->nbc ? 1 : 0;
+  if (fan_order) *fan_order = m->fno ? 1 : 0;
   return PFF_OK;
 }
 
@@ -3825,7 +3908,7 @@ pff_status pff_batch_tuning(const pff_batch *b, int32_t *choice, float *ms) {
 pff_status pff_batch_set_operator(pff_batch *b, int32_t form) {
   if (!b) return fail(PFF_ERR_ARG, "null batch");
   int32_t cur = 0;
-  PFF_TRY(pff_mesh_get_operator(b->m, &cur, nullptr));
+  PFF_TRY(pff_mesh_get_operator(b->m, &cur, nullptr, nullptr));
   if (cur == form) return PFF_OK;
   PFF_TRY(pff_mesh_set_operator(b->m, form));
   free_graph(b->g);

@@ -73,6 +73,11 @@ template <typename K> struct QkParams {
   const uint32_t *nbo;
   const uint2 *nmap;
   float4 *nbk;
+  // fan order of the entry records (nullable; the mesh's fan tables, see
+  // Params::fno): with them kb and kc are stored by fan position, the
+  // fan's k-th triangle coupling v_k and v_{k+1 mod m}, and a row gathers
+  // each distinct neighbour once
+  const uint32_t *fno, *fmap;
   QsScalars *qs;
   double *part;       // per-block partial sums and the ticket of reduce_last
   unsigned int *ticket;
@@ -575,6 +580,7 @@ __global__ void __launch_bounds__(256) k_qs_entry_build(QkParams<float> I) {
       for (int j = 0; j < 6; ++j) acc[j] = make_float4(0.f, 0.f, 0.f, 0.f);
       map = __ldg(&I.nmap[i]);
     }
+    const uint32_t fm = I.fmap ? __ldg(&I.fmap[i]) : 0u;
     for (int k = 0; k < I.D; ++k) {
       const size_t q = (size_t)k * I.N + i;
       const int en = __ldg(&I.ell[q]);
@@ -611,6 +617,14 @@ __global__ void __launch_bounds__(256) k_qs_entry_build(QkParams<float> I) {
             acc[j].w = __fadd_rn(acc[j].w, kc.w);
           }
         }
+        continue;
+      }
+      if (I.fmap) {
+        // fan position; (K_ab, K_ac) ordered counter-clockwise from the
+        // vertex, which (b, c) is for slots 0 and 2 and reverses for slot 1
+        const size_t qf = (size_t)((fm >> (4 * k)) & 15u) * I.N + i;
+        I.kb[qf] = a == 1 ? kc : kb;
+        I.kc[qf] = a == 1 ? kb : kc;
         continue;
       }
       const int nb = b == 0 ? n0 : n1, nc = c == 1 ? n1 : n2;
@@ -691,7 +705,38 @@ __global__ void __launch_bounds__(kQsPersThreads, 2) k_qs_cg_rows(QkParams<float
           qy = __fadd_rn(qy, fmaf(kk[j].z, dx, __fmul_rn(kk[j].w, dy)));
         }
       }
-      for (int k = 0; k < I.D && !I.nbk; k += U) {
+      if (!I.nbk && I.fno) {
+        // fan order: the six distinct neighbours gathered once, then per
+        // fan position K_b (p_{v_k} - p_i) + K_c (p_{v_{k+1}} - p_i) in
+        // position order (positions past the fan hold zero blocks)
+        uint32_t w[3];
+        float4 bb[6], cc[6];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) w[j] = __ldg(&I.fno[(size_t)j * I.N + i]);
+        const int m = (int)(__ldg(&I.fmap[i]) >> 24);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+          const bool in = k < I.D;
+          bb[k] = in ? __ldg(&I.kb[(size_t)k * I.N + i]) : make_float4(0.f, 0.f, 0.f, 0.f);
+          cc[k] = in ? __ldg(&I.kc[(size_t)k * I.N + i]) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        K2 pv[6];
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+          const uint32_t x = w[j >> 1];
+          pv[j] = qs_pnew(I, i + ((j & 1) ? (int)x >> 16 : (int)(int16_t)(x & 0xffffu)), beta);
+        }
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+          const K2 pb = pv[k], pcc = (k + 1 == m) ? pv[0] : pv[k < 5 ? k + 1 : 0];
+          const float bx = pb.x - pc.x, by = pb.y - pc.y, cx = pcc.x - pc.x, cy = pcc.y - pc.y;
+          const float fx = fmaf(bb[k].x, bx, fmaf(bb[k].y, by, fmaf(cc[k].x, cx, __fmul_rn(cc[k].y, cy))));
+          const float fy = fmaf(bb[k].z, bx, fmaf(bb[k].w, by, fmaf(cc[k].z, cx, __fmul_rn(cc[k].w, cy))));
+          qx = __fadd_rn(qx, fx);
+          qy = __fadd_rn(qy, fy);
+        }
+      }
+      for (int k = 0; k < I.D && !I.nbk && !I.fno; k += U) {
         uint32_t w[U];
         float4 bb[U], cc[U];
 #pragma unroll

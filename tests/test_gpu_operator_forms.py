@@ -148,3 +148,13 @@ def test_merged_unavailable_on_wide_mesh(pff):
         with pytest.raises(pff.PffError) as e:
             m.set_operator("merged")
         assert e.value.status == pff.PFF_ERR_ARG
+
+
+def test_fan_order_where_the_fans_fit(pff):
+    """Plates (every vertex fan at most six triangles) store the element-wise
+    entries in fan order; a vertex with twelve triangles keeps incidence
+    order.  Both are checked against the oracle by the other tests."""
+    from test_gpu_wide_incidence import _plate
+    for prec in ("fp32", "fp64"):
+        assert pff.Mesh.from_plate(S.plate(40, 16, jitter=0.1, seed=1), precision=prec).fan_order()
+        assert not pff.Mesh.from_plate(_plate(), precision=prec).fan_order()
