@@ -55,7 +55,7 @@ def parse():
                     help="skip the forward+adjoint measurement on the 500x500 plate")
     ap.add_argument("--variant", type=int, default=0,
                     help="gather schedule (0 = autotuned; 1..5 fixed, see pff_options.variant)")
-    ap.add_argument("--cg-kernel", choices=["auto", "phases", "persistent", "staged", "fused", "fused_staged"],
+    ap.add_argument("--cg-kernel", choices=["auto", "phases", "persistent", "staged", "fused", "fused_staged", "resident"],
                     default="auto", help="AT2 CG loop (pff_options.cg_kernel; auto = autotuned)")
     ap.add_argument("--no-precision", action="store_true",
                     help="skip the FP64 run and the FP32-vs-FP64 error of the benchmark plate")
@@ -223,6 +223,32 @@ def peaks():
     return 6400.0, "fallback"
 
 
+def l2_copy_gbs(dev, sizes_mb=(8, 16, 24), reps=50, rounds=5):
+    """Copy bandwidth of an L2-resident working set, measured here: b.copy_(a)
+    on FP32 buffers of each size (source and destination together 16 to 48
+    MB, well inside the 126 MB L2), `reps` copies back to back between CUDA
+    events, best round, read + write bytes.  The denominator of the CG
+    loop's roofline, whose working set stays in L2 across iterations."""
+    import torch
+    best = 0.0
+    for mb in sizes_mb:
+        n = mb * 2 ** 20 // 4
+        a = torch.ones(n, device=dev)
+        b = torch.empty_like(a)
+        for _ in range(3):
+            b.copy_(a)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for _ in range(rounds):
+            e0.record()
+            for _ in range(reps):
+                b.copy_(a)
+            e1.record()
+            e1.synchronize()
+            best = max(best, 2 * n * 4 * reps / (e0.elapsed_time(e1) * 1e-3) / 1e9)
+        del a, b
+    return best
+
+
 def ncu_traffic(kernel_prefix, summary="ncu_streaming_plate_1000x1000_fp32.md"):
     """DRAM bytes (read + write) from the committed ncu summary: the column of
     the first table whose header names the kernel (per launch, or per CG
@@ -323,18 +349,27 @@ def merged_row_width(tri, N):
     return 6 if deg <= 6 else 8 if deg <= 8 else None
 
 
-def format_bytes_cg_iteration(N, form, width, family):
+def format_bytes_cg_iteration(N, form, width, family, fan=False):
     """Bytes one FP32 CG iteration reads and writes in the stored form of the
     damage operator, per row (neighbour values are L2 hits):
     element-wise (entry records): flags, diagonal and per incidence slot a
     16-bit offset pair and two element coefficients (12 B, width = slots);
+    element-wise in fan order: flags, diagonal, six 16-bit neighbour offsets
+    (12 B), the fan word (4 B) and per fan position two coefficients (8 B);
     merged rows: flags, diagonal, width/2 offset words and width merged
     coefficients.  Two-pass families (persistent, phases): matvec (the row's
     own (p, z) pair read, q written) and vector update (x, r, (p, z) read
     and written; q and 1/diag read, flags again).  Single-reduction family:
     one pass reading the row's (r, w, s, 1/diag) record, p and x, writing
-    the new record, p and x."""
-    rec = 1 + 4 + (12 * width if form == "element" else 2 * width + 4 * width)
+    the new record, p and x.  Resident family: x, p, flags, diagonal and
+    the fan tables stay in shared memory for the whole solve, so a pass
+    moves the coefficients and the row's record (read and write)."""
+    if form == "element" and fan:
+        rec = 1 + 4 + 12 + 4 + 8 * width
+    else:
+        rec = 1 + 4 + (12 * width if form == "element" else 2 * width + 4 * width)
+    if family == "resident":
+        return N * (8 * width + 16 + 16)
     if family == "fused":
         return N * (rec + 16 + 8 + 8 + 16)
     return N * ((rec + 8 + 4) + (1 + 8 + 8 + 16 + 4 + 4))
@@ -757,7 +792,7 @@ def inversion(pff, dev, steps=300, gcs=(2.0, 2.5, 3.5), gc_star=3.0, max_states=
                            final_rel_err=abs(gc - gc_star) / gc_star, wall_s=el, checkpoint_every=25))
 
 
-def kernel_rooflines(prof, iters_mean, N, Ne, prec, form, width, peak, peak_kind):
+def kernel_rooflines(prof, iters_mean, N, Ne, prec, form, width, peak, peak_kind, fan=False, l2_peak=None):
     """Roofline of the dominant kernel of a step and the HBM fractions of the
     streaming kernels, from pff_profile_kernels' live launch times (CUDA
     events on the launching stream, L2 flushed before every launch).
@@ -769,8 +804,10 @@ def kernel_rooflines(prof, iters_mean, N, Ne, prec, form, width, peak, peak_kind
     and vectors, about 100 MB on the 1M-node plate) stays in the 126 MB L2
     across iterations, so `traffic` (ncu DRAM bytes) sits far below those
     bytes and `dram_frac` is the fraction of HBM bandwidth the loop really
-    draws: the loop is bound by L2 latency and grid synchronisation, not by
-    HBM.  The streaming kernels (force with history and corrector, damage
+    draws.  Its bound is then the L2: with l2_peak (l2_copy_gbs) the CG
+    loop's roofline is labelled "l2", its fraction taken against that
+    measured L2-resident copy bandwidth, and the HBM figures (peak, DRAM
+    traffic, dram_frac) move to roofline["hbm"].  The streaming kernels (force with history and corrector, damage
     right-hand side, predictor, clamp) read and write each element and node
     once from HBM; their fractions are the HBM roofline figures proper."""
     ab = algorithmic_bytes(N, Ne, prec)
@@ -804,16 +841,26 @@ def kernel_rooflines(prof, iters_mean, N, Ne, prec, form, width, peak, peak_kind
                     cg_iterations_per_launch=prof["cg_loop_iters"] if dom == "cg_loop" else None)
     if traffic:
         roofline["dram_frac"] = traffic / (ms_launch[dom] * 1e-3) / 1e9 / peak
-    if dom == "cg_loop" and width and prec == "fp32" and prof["cg_loop_family"] in ("persistent", "phases", "fused"):
-        fb = format_bytes_cg_iteration(N, form, width, prof["cg_loop_family"]) * prof["cg_loop_iters"]
-        roofline["format"] = dict(name=("element-wise entry records" if form == "element" else "merged rows")
+    den = peak
+    if dom == "cg_loop" and l2_peak:
+        hbm = dict(peak=peak, peak_kind=peak_kind, traffic=traffic, dram_frac=roofline.pop("dram_frac", None),
+                   method_bytes_over_hbm_peak=achieved / peak)
+        roofline.update(bound="l2", peak=l2_peak, frac=achieved / l2_peak,
+                        peak_kind="measured here: L2-resident copy bandwidth (l2_copy_gbs)", hbm=hbm)
+        den = l2_peak
+    if dom == "cg_loop" and width and prec == "fp32" and prof["cg_loop_family"] in (
+            "persistent", "phases", "fused", "resident"):
+        fb = format_bytes_cg_iteration(N, form, width, prof["cg_loop_family"], fan) * prof["cg_loop_iters"]
+        roofline["format"] = dict(name=("element-wise entry records" + (" in fan order" if fan else "")
+                                        if form == "element" else "merged rows")
                                   + f", width {width}", bytes_per_launch=fb,
                                   achieved=fb / (ms_launch[dom] * 1e-3) / 1e9,
-                                  frac=fb / (ms_launch[dom] * 1e-3) / 1e9 / peak)
+                                  frac=fb / (ms_launch[dom] * 1e-3) / 1e9 / den)
         roofline["note"] = ("bytes_per_launch: the method's matrix-free count; format: the bytes the stored "
-                            "operator records and vectors move; the loop's working set stays in L2, so its "
-                            "DRAM traffic (traffic, dram_frac) is a small share of either: L2-latency and "
-                            "grid-synchronisation bound; the HBM roofline figures are the streaming kernels'")
+                            "operator records and vectors move; the loop's working set stays in L2 across "
+                            "iterations, so its DRAM traffic (hbm.traffic, hbm.dram_frac) is a small share of "
+                            "either and its roofline is the L2's; the HBM roofline figures are the streaming "
+                            "kernels'")
     streaming = {}
     for k, kn in (("predict", "k_predict"), ("force", "k_force_nc"), ("rhs", "k_dmg_rhs_nc"),
                   ("finish", "k_dmg_finish")):
@@ -924,10 +971,12 @@ def run_ours(args):
             torch.distributed.destroy_process_group()
         return
     peak, peak_kind = peaks()
+    l2_peak = l2_copy_gbs(dev)
     roofline, streaming = kernel_rooflines(prof, iters.mean(), N, Ne, args.prec, args.operator,
                                            incidence_width(c["mesh"]["tri"], N)
                                            if args.operator == "element" else
-                                           merged_row_width(c["mesh"]["tri"], N), peak, peak_kind)
+                                           merged_row_width(c["mesh"]["tri"], N), peak, peak_kind,
+                                           fan=args.operator == "element" and mesh.fan_order(), l2_peak=l2_peak)
     ab = algorithmic_bytes(N, Ne, args.prec)
     step_bytes = sum(ab[k] for k in ("predict", "force", "rhs", "finish")) + iters.mean() * ab["cg_iteration"]
     line = dict(
@@ -974,7 +1023,7 @@ def run_ours(args):
             line["operator_forms"][other].pop("kernel_ms"), line["operator_forms"][other]["cg_iters_mean"],
             N, Ne, args.prec, other,
             merged_row_width(c["mesh"]["tri"], N) if other == "merged" else incidence_width(c["mesh"]["tri"], N),
-            pk, pk_kind)[0]
+            pk, pk_kind, l2_peak=l2_peak)[0]
     if args.model == "AT2" and args.split == "spectral" and not args.no_variants:
         line["variants_1m"] = variants_1m(pff, dev, args.config)
     if args.model == "AT2":

@@ -54,7 +54,7 @@ enum { PFF_PLANE_STRAIN = 0, PFF_PLANE_STRESS = 1 };
 enum { PFF_FP64 = 0, PFF_FP32_MIXED = 1 };
 enum { PFF_LOOP_GRAPH = 0, PFF_LOOP_HOST = 1 };
 enum { PFF_CG_AUTO = 0, PFF_CG_PHASES = 1, PFF_CG_PERSISTENT = 2, PFF_CG_TEST_TIMEOUT = 3,
-       PFF_CG_STAGED = 4, PFF_CG_FUSED = 5, PFF_CG_FUSED_STAGED = 6 };
+       PFF_CG_STAGED = 4, PFF_CG_FUSED = 5, PFF_CG_FUSED_STAGED = 6, PFF_CG_RESIDENT = 7 };
 
 typedef struct pff_mesh pff_mesh; /* opaque; owns geometry, CSR, workspaces */
 
@@ -109,9 +109,15 @@ typedef struct {
                            the kernel-per-phase loop);
                            PFF_CG_FUSED_STAGED = that with the operator
                            staged in shared memory;
+                           PFF_CG_RESIDENT = the single-reduction CG with
+                           each CTA owning a contiguous range of rows whose
+                           x, p, diagonal and fan tables stay in shared
+                           memory for the whole solve (FP32 element-wise
+                           operator in fan order, rows fitting 28 B each;
+                           else as PFF_CG_FUSED);
                            PFF_CG_AUTO = the fastest on this mesh, timed on
                            first use [0].
-                           Same iteration arithmetic; the two group the
+                           Same iteration arithmetic; the forms group the
                            partial sums of the dot products differently.
                            AT1 always uses the kernel-per-phase loop.
                            PFF_CG_TEST_TIMEOUT: the persistent loop awaits
@@ -438,9 +444,10 @@ pff_status pff_profile_kernels(pff_mesh *mesh, const pff_state *state, double dt
 pff_status pff_mesh_schedule(const pff_mesh *mesh, int32_t *variant, float *tune_ms);
 
 /* The AT2 CG loop the autotuner chose on this mesh: *cg_kernel =
- * PFF_CG_PHASES, _PERSISTENT, _STAGED, _FUSED or _FUSED_STAGED (PFF_CG_AUTO
- * while not yet timed), the chosen persistent kernel's gathers in flight
- * (1..4, 0 for phases), and ms[5]: 30 iterations of the kernel-per-phase
+ * PFF_CG_PHASES, _PERSISTENT, _STAGED, _FUSED, _FUSED_STAGED or _RESIDENT
+ * (PFF_CG_AUTO while not yet timed), the chosen persistent kernel's variant
+ * (1..4: gathers in flight, or the resident kernel's CTA shape; 0 for
+ * phases), and ms[6]: 30 iterations of the kernel-per-phase
  * loop and of the best variant of each persistent kernel in that order (0
  * if not timed or not available).  Host outputs; each pointer nullable. */
 pff_status pff_mesh_cg_choice(const pff_mesh *mesh, int32_t *cg_kernel, int32_t *gathers, float *ms);

@@ -28,9 +28,11 @@ PFF_SPLIT_SPECTRAL, PFF_SPLIT_AMOR, PFF_SPLIT_ISO = 0, 1, 2
 PFF_FP64, PFF_FP32_MIXED = 0, 1
 PFF_LOOP_GRAPH, PFF_LOOP_HOST = 0, 1
 PFF_CG_AUTO, PFF_CG_PHASES, PFF_CG_PERSISTENT, PFF_CG_TEST_TIMEOUT = 0, 1, 2, 3
-PFF_CG_STAGED, PFF_CG_FUSED, PFF_CG_FUSED_STAGED = 4, 5, 6
+PFF_CG_STAGED, PFF_CG_FUSED, PFF_CG_FUSED_STAGED, PFF_CG_RESIDENT = 4, 5, 6, 7
 CG_KINDS = {PFF_CG_AUTO: "auto", PFF_CG_PHASES: "phases", PFF_CG_PERSISTENT: "persistent",
-            PFF_CG_STAGED: "staged", PFF_CG_FUSED: "fused", PFF_CG_FUSED_STAGED: "fused_staged"}
+            PFF_CG_STAGED: "staged", PFF_CG_FUSED: "fused", PFF_CG_FUSED_STAGED: "fused_staged",
+            PFF_CG_RESIDENT: "resident"}
+CG_FAMILIES = ("phases", "persistent", "staged", "fused", "fused_staged", "resident")
 
 MODELS = {"AT1": PFF_AT1, "AT2": PFF_AT2}
 SPLITS = {"spectral": PFF_SPLIT_SPECTRAL, "amor": PFF_SPLIT_AMOR, "iso": PFF_SPLIT_ISO}
@@ -533,14 +535,14 @@ class Mesh:
 
     def cg_choice(self):
         """(AT2 CG loop in use: "auto" (not timed yet) / "phases" /
-        "persistent" / "staged" / "fused" / "fused_staged", its gathers in
-        flight, and {loop: ms of 30 iterations of its best variant})."""
+        "persistent" / "staged" / "fused" / "fused_staged" / "resident", its
+        variant (gathers in flight, or the resident kernel's CTA shape), and
+        {loop: ms of 30 iterations of its best variant})."""
         k = C.c_int32()
         u = C.c_int32()
-        ms = np.zeros(5, np.float32)
+        ms = np.zeros(len(CG_FAMILIES), np.float32)
         _check(_lib.pff_mesh_cg_choice(self._h, C.byref(k), C.byref(u), _hp(ms)))
-        names = ("phases", "persistent", "staged", "fused", "fused_staged")
-        return CG_KINDS[k.value], u.value, {n: float(x) for n, x in zip(names, ms)}
+        return CG_KINDS[k.value], u.value, {n: float(x) for n, x in zip(CG_FAMILIES, ms)}
 
     KERNELS = ("predict", "force", "rhs", "matvec", "update", "finish", "energies")
 
@@ -555,7 +557,7 @@ class Mesh:
         d = dict(zip(self.KERNELS, out[:7].tolist()))
         d["cg_loop"] = float(out[7])          # one persistent CG launch (0: kernel per phase)
         d["cg_loop_iters"] = int(out[8])
-        d["cg_loop_family"] = ("phases", "persistent", "staged", "fused", "fused_staged")[int(out[9])]
+        d["cg_loop_family"] = CG_FAMILIES[int(out[9])]
         d["force_rhs"] = float(out[10])        # the fused force and right-hand-side kernel
         d["force_rhs_used"] = bool(out[11])
         return d

@@ -133,6 +133,7 @@ template <typename R> struct Params {
   // (read one, write the other each pass) and the search direction p
   float4 *cgv0, *cgv1;
   float *cgp;
+  int32_t res_rows;  // resident single-reduction CG: rows per CTA
   // material (lam: the plane model's first Lame parameter; K: 3-D bulk
   // modulus; cz = nu / (1 - nu) under plane stress, 0 under plane strain)
   R lam, mu, K, eta, cz;
@@ -1364,13 +1365,11 @@ __device__ __forceinline__ R pnew(const Params<R> &P, int j, R beta) {
 // once, then per fan position k the triangle's two coefficients applied to
 // v_k and v_{k+1 mod m} (explicit fma and non-contracted adds, positions in
 // order; positions past the fan have zero coefficients and add an exact 0).
+// fan_row_w takes the row's fan words w and fan length m already loaded.
 template <typename R, typename C2, typename F>
-__device__ __forceinline__ R fan_row(const Params<R> &P, const C2 *cfs, int i, R q, F val) {
-  uint32_t w[3];
+__device__ __forceinline__ R fan_row_w(const Params<R> &P, const C2 *cfs, int i, R q, const uint32_t (&w)[3], int m,
+                                       F val) {
   C2 cf[6];
-#pragma unroll
-  for (int j = 0; j < 3; ++j) w[j] = __ldg(&P.fno[(size_t)j * P.N + i]);
-  const int m = (int)(__ldg(&P.fmap[i]) >> 24);
 #pragma unroll
   for (int k = 0; k < 6; ++k) {
     if (k < P.D) {
@@ -1395,6 +1394,14 @@ __device__ __forceinline__ R fan_row(const Params<R> &P, const C2 *cfs, int i, R
 #pragma unroll
   for (int k = 0; k < 6; ++k) q = radd(q, c[k]);
   return q;
+}
+
+template <typename R, typename C2, typename F>
+__device__ __forceinline__ R fan_row(const Params<R> &P, const C2 *cfs, int i, R q, F val) {
+  uint32_t w[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) w[j] = __ldg(&P.fno[(size_t)j * P.N + i]);
+  return fan_row_w(P, cfs, i, q, w, (int)(__ldg(&P.fmap[i]) >> 24), val);
 }
 
 // Row i of q = A p_new from the FP32 entry records: diag_i p_i, then per
@@ -2582,6 +2589,78 @@ struct FusedShared {
   float al, be;
 };
 
+// Thread 0 of every CTA: the solve's scalars at the start of the loop.
+__device__ __forceinline__ void fused_load(FusedShared &z, const SolveScalars *S) {
+  z.bn = S->bn;
+  z.gamma = S->rho;
+  z.rr = S->rr;
+  z.iters = S->iters;
+  z.status = kStOk;
+  z.done = 0;
+  z.al = 0.f;
+  z.be = 0.f;
+  z.alpha = 0.0;
+}
+
+// Thread 0 of every CTA after the all-reduce of pass `pass` (gamma, delta,
+// |r|^2 in z.tot): the stop tests and the next alpha and beta of the
+// single-reduction recurrences; z.flag = 1 ends the loop.
+__device__ __forceinline__ void fused_scalars(FusedShared &z, const Params<float> &P, int pass) {
+  const double g1 = z.tot[0], d1 = z.tot[1], t0 = z.tot[2];
+  bool stop = false;
+  if (pass > 1) {  // pass 1 was the set-up pass (w0 = A u0): no iterate yet
+    z.iters += 1;
+    z.rr = t0;
+  }
+  if (!(t0 == t0) || isinf(t0) || !(d1 == d1) || isinf(d1)) {
+    z.status = kStNonfinite;
+    z.done = 1;
+    stop = true;
+  } else if (pass > 1 && sqrt(t0) <= P.tol * z.bn) {
+    z.done = 1;
+    stop = true;
+  } else if (g1 == 0.0) {  // u = 0: the iterate is exact
+    z.done = 1;
+    stop = true;
+  }
+  if (!stop && z.iters >= P.max_it) {
+    stop = true;
+    z.status = kStNotConverged;
+    z.done = 1;
+  }
+  if (!stop) {
+    const double beta = pass > 1 ? g1 / z.gamma : 0.0;
+    const double den = pass > 1 ? d1 - beta * g1 / z.alpha : d1;
+    if (den == 0.0 || !(den == den)) {  // breakdown: A is SPD, so only through rounding
+      z.status = kStNonfinite;
+      z.done = 1;
+      stop = true;
+    } else {
+      z.alpha = g1 / den;
+      z.gamma = g1;
+      z.al = (float)z.alpha;
+      z.be = (float)beta;
+    }
+  }
+  z.flag = stop ? 1 : 0;
+}
+
+// CTA 0's thread 0 at the end: the scalars as the kernel-per-phase loop
+// leaves them.
+__device__ __forceinline__ void fused_store(FusedShared &z, SolveScalars *S) {
+  if (!z.ok) {
+    z.status = kStTimeout;
+    z.done = 1;
+  }
+  S->iters = z.iters;
+  S->rr = z.rr;
+  S->rho = z.gamma;
+  S->alpha = z.alpha;
+  S->status = z.status;
+  S->done = z.done;
+  S->inner_done = 1;
+}
+
 // Shared-memory layout of the local (ST) kernel for one CTA: element
 // records (32 B), row entries (D rows of mc = row count rounded up to 8),
 // then a region that first receives the elements' history (4 B each) and,
@@ -2652,17 +2731,7 @@ __global__ void __launch_bounds__(fused_threads(U, ST), fused_minb(U, ST)) k_cg_
     P.cgv0[j] = make_float4(P.r[j], 0.f, 0.f, P.dinv[j]);
     P.cgp[j] = 0.f;
   }
-  if (threadIdx.x == 0) {
-    z.bn = S->bn;
-    z.gamma = S->rho;
-    z.rr = S->rr;
-    z.iters = S->iters;
-    z.status = kStOk;
-    z.done = 0;
-    z.al = 0.f;
-    z.be = 0.f;
-    z.alpha = 0.0;
-  }
+  if (threadIdx.x == 0) fused_load(z, S);
   if constexpr (ST) {
     __syncthreads();  // the mbarriers are initialised before anyone polls them
     if (!mbar_wait_bounded(&bar_static, 0u)) *(volatile int32_t *)&S->abort = 1;  // all leave at the next barrier
@@ -2727,45 +2796,7 @@ __global__ void __launch_bounds__(fused_threads(U, ST), fused_minb(U, ST)) k_cg_
                             [&]() { issue_vec(vout); }))
       break;
     if (ST) copies = pass + 1;
-    if (threadIdx.x == 0) {
-      const double g1 = z.tot[0], d1 = z.tot[1], t0 = z.tot[2];
-      bool stop = false;
-      if (pass > 1) {  // pass 1 was the set-up pass (w0 = A u0): no iterate yet
-        z.iters += 1;
-        z.rr = t0;
-      }
-      if (!(t0 == t0) || isinf(t0) || !(d1 == d1) || isinf(d1)) {
-        z.status = kStNonfinite;
-        z.done = 1;
-        stop = true;
-      } else if (pass > 1 && sqrt(t0) <= P.tol * z.bn) {
-        z.done = 1;
-        stop = true;
-      } else if (g1 == 0.0) {  // u = 0: the iterate is exact
-        z.done = 1;
-        stop = true;
-      }
-      if (!stop && z.iters >= P.max_it) {
-        stop = true;
-        z.status = kStNotConverged;
-        z.done = 1;
-      }
-      if (!stop) {
-        const double beta = pass > 1 ? g1 / z.gamma : 0.0;
-        const double den = pass > 1 ? d1 - beta * g1 / z.alpha : d1;
-        if (den == 0.0 || !(den == den)) {  // breakdown: A is SPD, so only through rounding
-          z.status = kStNonfinite;
-          z.done = 1;
-          stop = true;
-        } else {
-          z.alpha = g1 / den;
-          z.gamma = g1;
-          z.al = (float)z.alpha;
-          z.be = (float)beta;
-        }
-      }
-      z.flag = stop ? 1 : 0;
-    }
+    if (threadIdx.x == 0) fused_scalars(z, P, pass);
     __syncthreads();
     if (z.flag) break;
   }
@@ -2774,19 +2805,109 @@ __global__ void __launch_bounds__(fused_threads(U, ST), fused_minb(U, ST)) k_cg_
     // the CTA (and its shared memory) goes away
     if (copies > pass && !mbar_wait_bounded(&bar_vec, (unsigned)pass & 1u)) *(volatile int32_t *)&S->abort = 1;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    if (!z.ok) {
-      z.status = kStTimeout;
-      z.done = 1;
+  if (blockIdx.x == 0 && threadIdx.x == 0) fused_store(z, S);
+}
+
+// ------------------------------------------- resident single-reduction CG
+//
+// The recurrences of k_cg_fused on fan-order element-wise rows (FP32), with
+// CTA b owning rows [b R, (b+1) R) for the whole solve (R = P.res_rows).
+// Per row, x, p, the operator diagonal, the three fan words and the fan
+// length (with the row's fixed flag) stay in the CTA's shared memory from
+// the set-up to the end of the loop, so a pass reads from global memory
+// only the row's entry coefficients and the (r, w, s, 1/diag) records of
+// the row and its neighbours, and writes only the row's record; x is
+// written back when the loop ends.  kResWords 4-byte words a row bound R,
+// which decides on which meshes the family exists.  U picks the CTA shape:
+// 1024 threads (one CTA per SM), 512 (two), 384 (two, up to 85 registers)
+// or 256 (three).  Per row the arithmetic of fused_rows; the dot products'
+// partial sums are grouped by CTA range instead of grid stride.
+__host__ __device__ constexpr int res_threads(int U) {
+  return U == 1 ? 1024 : (U == 2 ? 512 : (U == 3 ? 384 : 256));
+}
+__host__ __device__ constexpr int res_minb(int U) { return U == 1 ? 1 : (U == 4 ? 3 : 2); }
+constexpr int kResWords = 7;  // x, p, diagonal, fan words 0..2, fan length | fixed << 8
+
+__device__ __forceinline__ void resident_rows(const Params<float> &P, float al, float be,
+                                              const float4 *__restrict__ vin, float4 *__restrict__ vout, int row0,
+                                              int nr, int R, uint32_t *rs, DF (&acc)[3], bool rev) {
+  typedef Acc<float> AC;
+  float *xs = reinterpret_cast<float *>(rs);
+  float *ps = xs + R;
+  const float *ds = ps + R;
+  const uint32_t *fw = rs + 3 * R, *meta = rs + 6 * R;
+  const int T = (int)blockDim.x, t = (int)threadIdx.x;
+  const int llast = t < nr ? t + (nr - 1 - t) / T * T : t - T;
+  const int lstep = rev ? -T : T;
+  for (int l = rev ? llast : t; rev ? l >= t : l < nr; l += lstep) {
+    const int j = row0 + l;
+    const float4 v = vin[j];
+    const uint32_t mt = meta[l];
+    if (mt & 0x100u) {  // eliminated row: everything stays zero
+      vout[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+      continue;
     }
-    S->iters = z.iters;
-    S->rr = z.rr;
-    S->rho = z.gamma;
-    S->alpha = z.alpha;
-    S->status = z.status;
-    S->done = z.done;
-    S->inner_done = 1;
+    const float p = fmaf(be, ps[l], v.w * v.x);
+    const float sn = fmaf(be, v.z, v.y);
+    const float rn = fmaf(-al, sn, v.x);
+    const float un = v.w * rn;
+    xs[l] = fmaf(al, p, xs[l]);
+    ps[l] = p;
+    const uint32_t w[3] = {fw[l], fw[R + l], fw[2 * R + l]};
+    const float wq = fan_row_w(P, P.ecf, j, ds[l] * un, w, (int)(mt & 0xffu),
+                               [&](int n) { return cg_unew(vin[n], al, be); });
+    vout[j] = make_float4(rn, wq, sn, v.w);
+    const float sr = P.rscale * rn;
+    acc[0] = AC::add(acc[0], AC::prod(sr, un));             // gamma
+    acc[1] = AC::add(acc[1], AC::prod(P.rscale * wq, un));  // delta
+    acc[2] = AC::add(acc[2], AC::prod(sr, sr));             // |r|^2
   }
+}
+
+template <int U>
+__global__ void __launch_bounds__(res_threads(U), res_minb(U)) k_cg_resident(Params<float> P) {
+  typedef Acc<float> AC;
+  SolveScalars *S = P.sc;
+  __shared__ DF sh[32][3];
+  __shared__ FusedShared z;
+  extern __shared__ __align__(16) uint32_t res_smem[];
+  if (S->done) return;  // set-up found b_eff = 0 or r_0 already small
+  const int R = P.res_rows;
+  const int row0 = (int)blockIdx.x * R;
+  const int nr = max(0, min(R, P.N - row0));
+  float *xs = reinterpret_cast<float *>(res_smem);
+  // set-up: the rows' resident words, p = 0 and (r0, 0, 0, 1/diag)
+  for (int l = threadIdx.x; l < nr; l += blockDim.x) {
+    const int j = row0 + l;
+    xs[l] = P.x[j];
+    xs[R + l] = 0.f;
+    xs[2 * R + l] = P.diag[j];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) res_smem[(3 + k) * R + l] = __ldg(&P.fno[(size_t)k * P.N + j]);
+    res_smem[6 * R + l] = (__ldg(&P.fmap[j]) >> 24) | (is_fixed(P, j) ? 0x100u : 0u);
+    P.cgv0[j] = make_float4(P.r[j], 0.f, 0.f, P.dinv[j]);
+  }
+  if (threadIdx.x == 0) fused_load(z, S);
+  const unsigned int nb = gridDim.x;
+  unsigned int nbar = 1;
+  DF v3[3] = {AC::zero(), AC::zero(), AC::zero()};
+  bool fine = grid_sum<float, 3>(v3, P.part + 3u * nb, S, nb + P.bar_extra, z.tot, sh, &z.ok);
+  int pass = 0;  // passes read cgv[pass & 1] and write the other buffer
+  while (fine) {
+    const float4 *vin = (pass & 1) ? P.cgv1 : P.cgv0;
+    float4 *vout = (pass & 1) ? P.cgv0 : P.cgv1;
+    DF acc[3] = {AC::zero(), AC::zero(), AC::zero()};
+    resident_rows(P, z.al, z.be, vin, vout, row0, nr, R, res_smem, acc, (pass & 1) != 0);  // alternate directions
+    ++nbar;
+    ++pass;
+    if (!grid_sum<float, 3>(acc, P.part + (nbar & 1u) * 3u * nb, S, nbar * nb + P.bar_extra, z.tot, sh, &z.ok))
+      break;
+    if (threadIdx.x == 0) fused_scalars(z, P, pass);
+    __syncthreads();
+    if (z.flag) break;
+  }
+  for (int l = threadIdx.x; l < nr; l += blockDim.x) P.x[row0 + l] = xs[l];
+  if (blockIdx.x == 0 && threadIdx.x == 0) fused_store(z, S);
 }
 
 // AT1 restart (projected CG, Sec. 2.4): r = b - A x, active set

@@ -317,6 +317,9 @@ struct pff_mesh {
   // kernel-per-phase loop and both timings (kTuneCgIters iterations, ms)
   unsigned pgrid[5] = {0};
   unsigned fgrid[5] = {0};   // single-reduction CG grid per U (FP32)
+  unsigned rgrid[5] = {0};   // resident single-reduction CG: grid, rows per CTA and
+  int32_t rrows[5] = {0};    // dynamic shared memory per U (0: no fan order, or the
+  size_t rsmem[5] = {0};     // rows do not fit)
   bool st_fused = false;     // the staged tables also fit the single-reduction kernel
   int fam_U[8] = {0};        // tuned gathers in flight per CG-loop family
   int best_fam = 0;          // fastest family (kFamPhases when untuned)
@@ -452,11 +455,14 @@ static const void *pers_fun(int U, bool st = false) {
 //   kFamStaged       the same with each CTA's operator in shared memory;
 //   kFamFused        one cooperative launch of the single-reduction CG
 //                    (one pass and one all-reduce per iteration; FP32);
-//   kFamFusedStaged  the same with the operator in shared memory.
+//   kFamFusedStaged  the same with the operator in shared memory;
+//   kFamResident     the single-reduction CG on fan-order element-wise rows
+//                    with each CTA's rows (x, p, diagonal, fan tables) kept
+//                    in shared memory for the whole solve.
 // Forced by opt->cg_kernel, else the autotuner's fastest.  The barrier
 // count (at most 2 per iteration per CTA) must stay below 2^31; a plan that
 // cannot run falls back to the kernel-per-phase loop.
-enum { kFamPhases = 0, kFamPersistent, kFamStaged, kFamFused, kFamFusedStaged, kFamCount };
+enum { kFamPhases = 0, kFamPersistent, kFamStaged, kFamFused, kFamFusedStaged, kFamResident, kFamCount };
 constexpr int kTuneCgIters = 30;  // CG iterations per timed solve of the family autotuner
 constexpr int kTuneCgRounds = 8;  // timed rounds (the first warms up; the best of the rest counts)
 
@@ -467,6 +473,7 @@ struct CgPlan {
   bool pers() const { return fam != kFamPhases; }
   bool st() const { return fam == kFamStaged || fam == kFamFusedStaged; }
   bool fused() const { return fam == kFamFused || fam == kFamFusedStaged; }
+  bool res() const { return fam == kFamResident; }
 };
 
 static inline int matvec_u(const pff_mesh *m) {
@@ -482,6 +489,7 @@ static inline unsigned fam_grid(const pff_mesh *m, int fam, int U, bool fp32) {
     case kFamStaged: return stage ? m->st_grid : 0u;
     case kFamFused: return fp32 && (m->erec || m->ecmp) ? m->fgrid[U] : 0u;  // reads the entry records
     case kFamFusedStaged: return stage && m->st_fused ? m->st_grid : 0u;
+    case kFamResident: return fp32 && m->dop == PFF_OP_ELEMENT ? m->rgrid[U] : 0u;  // fan-order records
     default: return 0u;
   }
 }
@@ -496,6 +504,7 @@ static CgPlan cg_plan(const pff_mesh *m, const pff_options &o, int model, bool f
     case PFF_CG_STAGED: p.fam = kFamStaged; break;
     case PFF_CG_FUSED: p.fam = kFamFused; break;
     case PFF_CG_FUSED_STAGED: p.fam = kFamFusedStaged; break;
+    case PFF_CG_RESIDENT: p.fam = kFamResident; break;
     default:
       if (!m->pers_tuned) return p;
       p.fam = m->best_fam;
@@ -503,7 +512,8 @@ static CgPlan cg_plan(const pff_mesh *m, const pff_options &o, int model, bool f
   if (p.fam == kFamPhases) return p;
   p.U = m->fam_U[p.fam] ? m->fam_U[p.fam] : matvec_u(m);
   p.grid = fam_grid(m, p.fam, p.U, fp32);
-  if (p.grid == 0 && (p.fam == kFamStaged || p.fam == kFamFusedStaged)) {  // not stageable: unstaged
+  if (p.grid == 0 && (p.fam == kFamStaged || p.fam == kFamFusedStaged || p.fam == kFamResident)) {
+    // not stageable, or the rows do not fit shared memory: global memory
     p.fam = p.fam == kFamStaged ? kFamPersistent : kFamFused;
     p.U = m->fam_U[p.fam] ? m->fam_U[p.fam] : matvec_u(m);
     p.grid = fam_grid(m, p.fam, p.U, fp32);
@@ -525,6 +535,14 @@ static inline bool use_fused(const pff_mesh *m, const pff_options &o, const CgPl
 template <typename R>
 static const void *plan_fun(const CgPlan &c) {
   if constexpr (sizeof(R) == 4) {
+    if (c.res()) {
+      switch (c.U) {
+        case 1: return (const void *)k_cg_resident<1>;
+        case 3: return (const void *)k_cg_resident<3>;
+        case 4: return (const void *)k_cg_resident<4>;
+        default: return (const void *)k_cg_resident<2>;
+      }
+    }
     if (c.fused()) {
       const bool st = c.st();
       switch (c.U) {
@@ -539,15 +557,18 @@ static const void *plan_fun(const CgPlan &c) {
 }
 
 static inline unsigned plan_threads(const CgPlan &c) {
+  if (c.res()) return res_threads(c.U);
   return c.fam == kFamFusedStaged ? FusedCfg<true>::threads : (c.fam == kFamFused ? fused_threads(c.U, false) : pers_threads(c.U, c.st()));
 }
 
 static inline size_t plan_smem(const pff_mesh *m, const CgPlan &c) {
+  if (c.res()) return m->rsmem[c.U];
   return c.fam == kFamStaged ? m->st_smem : (c.fam == kFamFusedStaged ? m->st_smem_local : 0);
 }
 
 template <typename R>
 static pff_status launch_pers(const pff_mesh *m, const CgPlan &c, Params<R> &P, cudaStream_t s) {
+  P.res_rows = c.res() ? m->rrows[c.U] : 0;
   void *args[] = {(void *)&P};
   CUDA_TRY(cudaLaunchCooperativeKernel(plan_fun<R>(c), dim3(c.grid), dim3(plan_threads(c)), args,
                                        plan_smem(m, c), s));
@@ -559,6 +580,7 @@ static pff_status add_pers(const pff_mesh *m, const CgPlan &c, cudaGraph_t g,
                            const std::vector<cudaGraphNode_t> &deps, Params<R> &P, cudaGraphNode_t *out) {
   cudaKernelNodeParams kp;
   std::memset(&kp, 0, sizeof(kp));
+  P.res_rows = c.res() ? m->rrows[c.U] : 0;
   void *args[] = {(void *)&P};
   kp.func = const_cast<void *>(plan_fun<R>(c));
   kp.gridDim = dim3(c.grid);
@@ -1015,6 +1037,37 @@ static pff_status configure(pff_mesh *m, const int32_t *tri_host) {
       const int64_t wave = (int64_t)nsm * occ;  // a full wave, as for the persistent loop
       const int64_t ctas = std::max<int64_t>(1, (m->N + T - 1) / T);
       m->fgrid[U] = coop && occ > 0 ? (unsigned)std::min<int64_t>(ctas, wave) : 0u;
+    }
+    // resident single-reduction CG (fan-order rows): a full wave of
+    // res_minb(U) CTAs per SM (fewer CTAs on a small mesh), available if
+    // every CTA's rows fit its shared memory and all CTAs are co-resident
+    int smem_optin = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    for (int U = 1; U <= 4; ++U) {
+      m->rgrid[U] = 0u;
+      m->rrows[U] = 0;
+      m->rsmem[U] = 0;
+      if (!coop || !m->fno) continue;
+      CgPlan c;
+      c.fam = kFamResident;
+      c.U = U;
+      const int T = res_threads(U);
+      const int64_t ctas = std::min<int64_t>((int64_t)nsm * res_minb(U), (m->N + T - 1) / T);
+      const int64_t rows = (m->N + ctas - 1) / ctas;
+      const size_t smem = (size_t)kResWords * sizeof(uint32_t) * (size_t)rows;
+      const void *f = plan_fun<float>(c);
+      cudaFuncAttributes fa;
+      CUDA_TRY(cudaFuncGetAttributes(&fa, f));
+      const int dyn_max = smem_optin - (int)fa.sharedSizeBytes;
+      if (smem > (size_t)std::max(dyn_max, 0)) continue;
+      // the opt-in maximum, so that every mesh's launch stays within it
+      CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max));
+      int occ = 0;
+      CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f, T, smem));
+      if ((int64_t)occ * nsm < ctas) continue;
+      m->rgrid[U] = (unsigned)ctas;
+      m->rrows[U] = (int32_t)rows;
+      m->rsmem[U] = smem;
     }
     if (!m->cgv) {
       PFF_TRY(dalloc((float4 **)&m->cgv, 2 * (size_t)(m->N + 2)));
@@ -2609,7 +2662,7 @@ pff_status pff_mesh_schedule(const pff_mesh *m, int32_t *variant, float *tune_ms
 pff_status pff_mesh_cg_choice(const pff_mesh *m, int32_t *cg_kernel, int32_t *gathers, float *ms) {
   if (!m) return fail(PFF_ERR_ARG, "null mesh");
   static const int32_t kinds[kFamCount] = {PFF_CG_PHASES, PFF_CG_PERSISTENT, PFF_CG_STAGED, PFF_CG_FUSED,
-                                           PFF_CG_FUSED_STAGED};
+                                           PFF_CG_FUSED_STAGED, PFF_CG_RESIDENT};
   if (cg_kernel) *cg_kernel = !m->pers_tuned ? PFF_CG_AUTO : kinds[m->best_fam];
   if (gathers) *gathers = m->best_fam == kFamPhases ? 0 : m->fam_U[m->best_fam];
   if (ms)

@@ -2,9 +2,9 @@
 solve in one persistent cooperative kernel with grid barriers; the same
 with each CTA's operator staged in shared memory by bulk copies; the
 single-reduction form of the same PCG, one pass and one barrier per
-iteration, unstaged and staged) against the oracle and against each other,
-on meshes from one CTA to a full wave; the bounded barrier wait; the
-autotuner's report."""
+iteration, unstaged, staged, and with each CTA's rows resident in shared
+memory) against the oracle and against each other, on meshes from one CTA
+to a full wave; the bounded barrier wait; the autotuner's report."""
 import numpy as np
 import pytest
 
@@ -37,7 +37,7 @@ def _solve(pff, mesh, H, dprev, cgk, tol=1e-8):
     return out.double().cpu().numpy(), info
 
 
-FP32_LOOPS = [2, 4, 5, 6]  # persistent, staged, fused, fused staged (pff.PFF_CG_*)
+FP32_LOOPS = [2, 4, 5, 6, 7]  # persistent, staged, fused, fused staged, resident (pff.PFF_CG_*)
 
 # 20 x 8: 189 nodes, one CTA; 300 x 120: 36,421 nodes, 36 CTAs;
 # 520 x 300 jittered: 156,821 nodes, one CTA per SM
@@ -136,6 +136,21 @@ def test_persistent_backward_matches_phases(pff, prec):
     tol = 1e-9 if prec == "fp64" else 2e-3
     for g in grads[1:]:
         assert abs(g - grads[0]) <= tol * abs(grads[0]), grads
+
+
+def test_resident_without_fan_order_runs_unstaged(pff):
+    """A mesh whose fans do not fit the fan tables (a vertex with twelve
+    triangles) has no resident loop: asking for it runs the global-memory
+    single-reduction loop, with the same result."""
+    from test_gpu_wide_incidence import _plate
+    q = _plate()
+    mesh = pff.Mesh.from_plate(q, precision="fp32")
+    mesh.set_material(S.material(2 * q["h"]), 0.5)
+    assert not mesh.fan_order()
+    H, dprev = _inputs(q, 4)
+    d_re, i_re = _solve(pff, mesh, H, dprev, pff.PFF_CG_RESIDENT)
+    d_fu, i_fu = _solve(pff, mesh, H, dprev, pff.PFF_CG_FUSED)
+    assert i_re["iters"] == i_fu["iters"] and np.array_equal(d_re, d_fu)
 
 
 def test_bounded_barrier_wait_reports_timeout(pff):
