@@ -253,6 +253,35 @@ __device__ __forceinline__ DF df_add(DF a, DF b) {
   return DF{hi, e - (hi - s)};
 }
 
+// Double-word arithmetic for the single-reduction loops' scalar step, in
+// FP32 instructions only (an FP64 warp instruction costs ~17 SM cycles on
+// this GPU, and the step is on every iteration's critical path).  Products
+// and quotients of (hi, lo) pairs after Dekker (1971), in the forms whose
+// errors Joldes, Muller and Popescu (2017) bound by a few units of 2^-44
+// relative: ample for alpha and beta, which the rows use rounded to FP32.
+__device__ __forceinline__ DF df_fast(float a, float b) {  // |a| >= |b| or a = 0
+  const float s = a + b;
+  return DF{s, b - (s - a)};
+}
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+  const DF p = two_prod(a.hi, b.hi);
+  return df_fast(p.hi, p.lo + fmaf(a.hi, b.lo, a.lo * b.hi));
+}
+__device__ __forceinline__ DF df_div(DF a, DF b) {
+  const float q1 = a.hi / b.hi;
+  const DF qb = df_mul(DF{q1, 0.f}, b);
+  const DF r = df_add(a, DF{-qb.hi, -qb.lo});
+  return df_fast(q1, r.hi / b.hi);
+}
+__device__ __forceinline__ DF df_sub(DF a, DF b) { return df_add(a, DF{-b.hi, -b.lo}); }
+__device__ __forceinline__ bool df_le(DF a, DF b) { return a.hi < b.hi || (a.hi == b.hi && a.lo <= b.lo); }
+__device__ __forceinline__ bool df_finite(DF a) { return isfinite(a.hi) && isfinite(a.lo); }
+__device__ __forceinline__ DF df_from(double d) {
+  const float hi = (float)d;
+  return DF{hi, (float)(d - (double)hi)};
+}
+__device__ __forceinline__ double df_to(DF a) { return (double)a.hi + (double)a.lo; }
+
 template <typename R> struct Acc;
 template <> struct Acc<double> {
   typedef double T;
@@ -1365,7 +1394,27 @@ __device__ __forceinline__ R pnew(const Params<R> &P, int j, R beta) {
 // once, then per fan position k the triangle's two coefficients applied to
 // v_k and v_{k+1 mod m} (explicit fma and non-contracted adds, positions in
 // order; positions past the fan have zero coefficients and add an exact 0).
-// fan_row_w takes the row's fan words w and fan length m already loaded.
+// fan_row_w takes the row's fan words w and fan length m already loaded;
+// fan_sum is the row's sum once coefficients and neighbour values are in
+// registers.
+__device__ __forceinline__ int fan_offset(const uint32_t (&w)[3], int j) {
+  const uint32_t x = w[j >> 1];
+  return (j & 1) ? (int)x >> 16 : (int)(int16_t)(x & 0xffffu);
+}
+
+template <typename R, typename C2>
+__device__ __forceinline__ R fan_sum(R q, const C2 (&cf)[6], const R (&v)[6], int m) {
+  R c[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const R vc = (k + 1 == m) ? v[0] : v[k < 5 ? k + 1 : 0];
+    c[k] = rfma(cf[k].x, v[k], rmul(cf[k].y, vc));
+  }
+#pragma unroll
+  for (int k = 0; k < 6; ++k) q = radd(q, c[k]);
+  return q;
+}
+
 template <typename R, typename C2, typename F>
 __device__ __forceinline__ R fan_row_w(const Params<R> &P, const C2 *cfs, int i, R q, const uint32_t (&w)[3], int m,
                                        F val) {
@@ -1381,19 +1430,8 @@ __device__ __forceinline__ R fan_row_w(const Params<R> &P, const C2 *cfs, int i,
   }
   R v[6];
 #pragma unroll
-  for (int j = 0; j < 6; ++j) {
-    const uint32_t x = w[j >> 1];
-    v[j] = val(i + ((j & 1) ? (int)x >> 16 : (int)(int16_t)(x & 0xffffu)));
-  }
-  R c[6];
-#pragma unroll
-  for (int k = 0; k < 6; ++k) {
-    const R vc = (k + 1 == m) ? v[0] : v[k < 5 ? k + 1 : 0];
-    c[k] = rfma(cf[k].x, v[k], rmul(cf[k].y, vc));
-  }
-#pragma unroll
-  for (int k = 0; k < 6; ++k) q = radd(q, c[k]);
-  return q;
+  for (int j = 0; j < 6; ++j) v[j] = val(i + fan_offset(w, j));
+  return fan_sum(q, cf, v, m);
 }
 
 template <typename R, typename C2, typename F>
@@ -2069,8 +2107,13 @@ __device__ __forceinline__ void cta_sum(typename Acc<R>::T (&v)[NV], typename Ac
 // 32 kPartWarps); sh is a free [>= kPartWarps][NV] scratch, free again on
 // return.
 constexpr int kPartWarps = 8;
-template <typename R, int NV>
-__device__ __forceinline__ void grid_partials(const double *part, double *tot, typename Acc<R>::T (*sh)[NV],
+__device__ __forceinline__ void put_tot(double &d, double v) { d = v; }
+__device__ __forceinline__ void put_tot(double &d, DF v) { d = Acc<float>::to_d(v); }
+__device__ __forceinline__ void put_tot(DF &d, DF v) { d = v; }
+
+// tot: double, or DF to keep FP32-mode totals double-word (no FP64).
+template <typename R, int NV, typename TOT>
+__device__ __forceinline__ void grid_partials(const double *part, TOT *tot, typename Acc<R>::T (*sh)[NV],
                                               int nbg = -1) {
   typedef Acc<R> A;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -2105,7 +2148,7 @@ __device__ __forceinline__ void grid_partials(const double *part, double *tot, t
       typename A::T s = lane < kPartWarps ? sh[lane][k] : A::zero();
 #pragma unroll
       for (int o = kPartWarps / 2; o > 0; o >>= 1) s = A::add(s, A::shfl(s, o));
-      if (lane == 0) tot[k] = A::to_d(s);
+      if (lane == 0) put_tot(tot[k], s);
     }
   }
   __syncthreads();  // sh is free again, tot is visible to every thread
@@ -2122,9 +2165,9 @@ struct NoHook {
 // has completed, before the partials are summed.  A group of CTAs (the
 // CTAs of one plate of a batch) reduces among itself with cta = the CTA's
 // rank in the group and nb = the group's size (defaults: the whole grid).
-template <typename R, int NV, typename Hook = NoHook>
+template <typename R, int NV, typename TOT, typename Hook = NoHook>
 __device__ __forceinline__ bool grid_sum(typename Acc<R>::T (&v)[NV], double *part, SolveScalars *S,
-                                         unsigned int target, double *tot, typename Acc<R>::T (*sh)[NV],
+                                         unsigned int target, TOT *tot, typename Acc<R>::T (*sh)[NV],
                                          int *ok_sh, const Hook &hook = Hook(), int cta = -1, int nb = -1) {
   typedef Acc<R> A;
   cta_sum<R, NV>(v, sh);  // its barriers order every thread's row writes before thread 0's release
@@ -2583,43 +2626,46 @@ __host__ __device__ constexpr int fused_minb(int U, bool ST) {
 }
 
 struct FusedShared {
-  double gamma, alpha, bn, rr;
-  double tot[3];
+  DF gamma, alpha, rr, thr2;  // double-word: no FP64 instruction in the loop
+  DF tot[3];
   int iters, status, done, flag, ok;
   float al, be;
 };
 
-// Thread 0 of every CTA: the solve's scalars at the start of the loop.
-__device__ __forceinline__ void fused_load(FusedShared &z, const SolveScalars *S) {
-  z.bn = S->bn;
-  z.gamma = S->rho;
-  z.rr = S->rr;
+// Thread 0 of every CTA: the solve's scalars at the start of the loop; the
+// stop test ||r|| <= tol ||b_eff|| is taken as |r|^2 <= (tol ||b_eff||)^2.
+__device__ __forceinline__ void fused_load(FusedShared &z, const SolveScalars *S, double tol) {
+  const double t = tol * S->bn;
+  z.thr2 = df_from(t * t);
+  z.gamma = df_from(S->rho);
+  z.rr = df_from(S->rr);
   z.iters = S->iters;
   z.status = kStOk;
   z.done = 0;
   z.al = 0.f;
   z.be = 0.f;
-  z.alpha = 0.0;
+  z.alpha = DF{0.f, 0.f};
 }
 
 // Thread 0 of every CTA after the all-reduce of pass `pass` (gamma, delta,
 // |r|^2 in z.tot): the stop tests and the next alpha and beta of the
-// single-reduction recurrences; z.flag = 1 ends the loop.
+// single-reduction recurrences, in double-word arithmetic; z.flag = 1 ends
+// the loop.
 __device__ __forceinline__ void fused_scalars(FusedShared &z, const Params<float> &P, int pass) {
-  const double g1 = z.tot[0], d1 = z.tot[1], t0 = z.tot[2];
+  const DF g1 = z.tot[0], d1 = z.tot[1], t0 = z.tot[2];
   bool stop = false;
   if (pass > 1) {  // pass 1 was the set-up pass (w0 = A u0): no iterate yet
     z.iters += 1;
     z.rr = t0;
   }
-  if (!(t0 == t0) || isinf(t0) || !(d1 == d1) || isinf(d1)) {
+  if (!df_finite(t0) || !df_finite(d1)) {
     z.status = kStNonfinite;
     z.done = 1;
     stop = true;
-  } else if (pass > 1 && sqrt(t0) <= P.tol * z.bn) {
+  } else if (pass > 1 && df_le(t0, z.thr2)) {
     z.done = 1;
     stop = true;
-  } else if (g1 == 0.0) {  // u = 0: the iterate is exact
+  } else if (g1.hi == 0.f) {  // u = 0: the iterate is exact
     z.done = 1;
     stop = true;
   }
@@ -2629,17 +2675,18 @@ __device__ __forceinline__ void fused_scalars(FusedShared &z, const Params<float
     z.done = 1;
   }
   if (!stop) {
-    const double beta = pass > 1 ? g1 / z.gamma : 0.0;
-    const double den = pass > 1 ? d1 - beta * g1 / z.alpha : d1;
-    if (den == 0.0 || !(den == den)) {  // breakdown: A is SPD, so only through rounding
+    const DF beta = pass > 1 ? df_div(g1, z.gamma) : DF{0.f, 0.f};
+    const DF den = pass > 1 ? df_sub(d1, df_mul(beta, df_div(g1, z.alpha))) : d1;
+    const DF alpha = df_div(g1, den);
+    if (den.hi == 0.f || !df_finite(den) || !df_finite(alpha)) {  // breakdown: A is SPD, so only through rounding
       z.status = kStNonfinite;
       z.done = 1;
       stop = true;
     } else {
-      z.alpha = g1 / den;
+      z.alpha = alpha;
       z.gamma = g1;
-      z.al = (float)z.alpha;
-      z.be = (float)beta;
+      z.al = alpha.hi;
+      z.be = beta.hi;
     }
   }
   z.flag = stop ? 1 : 0;
@@ -2653,9 +2700,9 @@ __device__ __forceinline__ void fused_store(FusedShared &z, SolveScalars *S) {
     z.done = 1;
   }
   S->iters = z.iters;
-  S->rr = z.rr;
-  S->rho = z.gamma;
-  S->alpha = z.alpha;
+  S->rr = df_to(z.rr);
+  S->rho = df_to(z.gamma);
+  S->alpha = df_to(z.alpha);
   S->status = z.status;
   S->done = z.done;
   S->inner_done = 1;
@@ -2731,7 +2778,7 @@ __global__ void __launch_bounds__(fused_threads(U, ST), fused_minb(U, ST)) k_cg_
     P.cgv0[j] = make_float4(P.r[j], 0.f, 0.f, P.dinv[j]);
     P.cgp[j] = 0.f;
   }
-  if (threadIdx.x == 0) fused_load(z, S);
+  if (threadIdx.x == 0) fused_load(z, S, P.tol);
   if constexpr (ST) {
     __syncthreads();  // the mbarriers are initialised before anyone polls them
     if (!mbar_wait_bounded(&bar_static, 0u)) *(volatile int32_t *)&S->abort = 1;  // all leave at the next barrier
@@ -2822,11 +2869,21 @@ __global__ void __launch_bounds__(fused_threads(U, ST), fused_minb(U, ST)) k_cg_
 // 1024 threads (one CTA per SM), 512 (two), 384 (two, up to 85 registers)
 // or 256 (three).  Per row the arithmetic of fused_rows; the dot products'
 // partial sums are grouped by CTA range instead of grid stride.
+// FULL (meshes small enough, e.g. a quarter-million rows on 148 SMs): the
+// rows' coefficient pairs and their (r, w, s, 1/diag) records (both
+// buffers) live in shared memory as well, kResWordsFull words a row; a
+// pass then reads global memory only for neighbours owned by another CTA,
+// and writes every new record to global memory too (for those CTAs).
+// Shared-memory layout (words, R a multiple of 4): [0, 7R) the base words
+// (x, p, diagonal, fan words 0..2, fan length | fixed << 8, each R long);
+// FULL adds [7R, 19R) the coefficient pairs of fan positions 0..5 (R
+// float2 each) and [19R, 27R) the two record buffers (R float4 each).
 __host__ __device__ constexpr int res_threads(int U) {
   return U == 1 ? 1024 : (U == 2 ? 512 : (U == 3 ? 384 : 256));
 }
 __host__ __device__ constexpr int res_minb(int U) { return U == 1 ? 1 : (U == 4 ? 3 : 2); }
 constexpr int kResWords = 7;  // x, p, diagonal, fan words 0..2, fan length | fixed << 8
+constexpr int kResWordsFull = 27;  // + 6 coefficient pairs + 2 records
 
 __device__ __forceinline__ void resident_rows(const Params<float> &P, float al, float be,
                                               const float4 *__restrict__ vin, float4 *__restrict__ vout, int row0,
@@ -2864,7 +2921,57 @@ __device__ __forceinline__ void resident_rows(const Params<float> &P, float al, 
   }
 }
 
-template <int U>
+// FULL: the rows of a pass with everything of the CTA's own rows in
+// shared memory; rin / rout the shared record buffers (old, new).
+__device__ __forceinline__ void resident_rows_full(const Params<float> &P, float al, float be,
+                                                   const float4 *__restrict__ vin, float4 *__restrict__ vout,
+                                                   int row0, int nr, int R, uint32_t *rs, const float4 *rin,
+                                                   float4 *rout, DF (&acc)[3], bool rev) {
+  typedef Acc<float> AC;
+  float *xs = reinterpret_cast<float *>(rs);
+  float *ps = xs + R;
+  const float *ds = ps + R;
+  const uint32_t *fw = rs + 3 * R, *meta = rs + 6 * R;
+  const float2 *cfs = reinterpret_cast<const float2 *>(rs + 7 * R);
+  const int T = (int)blockDim.x, t = (int)threadIdx.x;
+  const int llast = t < nr ? t + (nr - 1 - t) / T * T : t - T;
+  const int lstep = rev ? -T : T;
+  for (int l = rev ? llast : t; rev ? l >= t : l < nr; l += lstep) {
+    const int j = row0 + l;
+    const float4 v = rin[l];
+    const uint32_t mt = meta[l];
+    if (mt & 0x100u) {  // eliminated row: everything stays zero
+      rout[l] = make_float4(0.f, 0.f, 0.f, 0.f);
+      vout[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+      continue;
+    }
+    const float p = fmaf(be, ps[l], v.w * v.x);
+    const float sn = fmaf(be, v.z, v.y);
+    const float rn = fmaf(-al, sn, v.x);
+    const float un = v.w * rn;
+    xs[l] = fmaf(al, p, xs[l]);
+    ps[l] = p;
+    const uint32_t w[3] = {fw[l], fw[R + l], fw[2 * R + l]};
+    float2 cf[6];
+    float nv[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      cf[k] = k < P.D ? cfs[k * R + l] : make_float2(0.f, 0.f);
+      const int ln = l + fan_offset(w, k);
+      nv[k] = cg_unew((unsigned)ln < (unsigned)nr ? rin[ln] : vin[row0 + ln], al, be);
+    }
+    const float wq = fan_sum(ds[l] * un, cf, nv, (int)(mt & 0xffu));
+    const float4 rec = make_float4(rn, wq, sn, v.w);
+    rout[l] = rec;
+    vout[j] = rec;
+    const float sr = P.rscale * rn;
+    acc[0] = AC::add(acc[0], AC::prod(sr, un));             // gamma
+    acc[1] = AC::add(acc[1], AC::prod(P.rscale * wq, un));  // delta
+    acc[2] = AC::add(acc[2], AC::prod(sr, sr));             // |r|^2
+  }
+}
+
+template <int U, bool FULL>
 __global__ void __launch_bounds__(res_threads(U), res_minb(U)) k_cg_resident(Params<float> P) {
   typedef Acc<float> AC;
   SolveScalars *S = P.sc;
@@ -2876,6 +2983,7 @@ __global__ void __launch_bounds__(res_threads(U), res_minb(U)) k_cg_resident(Par
   const int row0 = (int)blockIdx.x * R;
   const int nr = max(0, min(R, P.N - row0));
   float *xs = reinterpret_cast<float *>(res_smem);
+  float4 *recs = reinterpret_cast<float4 *>(res_smem + 19 * R);  // FULL: two buffers of R
   // set-up: the rows' resident words, p = 0 and (r0, 0, 0, 1/diag)
   for (int l = threadIdx.x; l < nr; l += blockDim.x) {
     const int j = row0 + l;
@@ -2885,9 +2993,16 @@ __global__ void __launch_bounds__(res_threads(U), res_minb(U)) k_cg_resident(Par
 #pragma unroll
     for (int k = 0; k < 3; ++k) res_smem[(3 + k) * R + l] = __ldg(&P.fno[(size_t)k * P.N + j]);
     res_smem[6 * R + l] = (__ldg(&P.fmap[j]) >> 24) | (is_fixed(P, j) ? 0x100u : 0u);
-    P.cgv0[j] = make_float4(P.r[j], 0.f, 0.f, P.dinv[j]);
+    const float4 rec = make_float4(P.r[j], 0.f, 0.f, P.dinv[j]);
+    P.cgv0[j] = rec;
+    if constexpr (FULL) {
+      float2 *cfs = reinterpret_cast<float2 *>(res_smem + 7 * R);
+#pragma unroll
+      for (int k = 0; k < 6; ++k) cfs[k * R + l] = k < P.D ? __ldg(&P.ecf[(size_t)k * P.N + j]) : make_float2(0.f, 0.f);
+      recs[l] = rec;
+    }
   }
-  if (threadIdx.x == 0) fused_load(z, S);
+  if (threadIdx.x == 0) fused_load(z, S, P.tol);
   const unsigned int nb = gridDim.x;
   unsigned int nbar = 1;
   DF v3[3] = {AC::zero(), AC::zero(), AC::zero()};
@@ -2897,7 +3012,11 @@ __global__ void __launch_bounds__(res_threads(U), res_minb(U)) k_cg_resident(Par
     const float4 *vin = (pass & 1) ? P.cgv1 : P.cgv0;
     float4 *vout = (pass & 1) ? P.cgv0 : P.cgv1;
     DF acc[3] = {AC::zero(), AC::zero(), AC::zero()};
-    resident_rows(P, z.al, z.be, vin, vout, row0, nr, R, res_smem, acc, (pass & 1) != 0);  // alternate directions
+    if constexpr (FULL)
+      resident_rows_full(P, z.al, z.be, vin, vout, row0, nr, R, res_smem, recs + (pass & 1) * R,
+                         recs + ((pass + 1) & 1) * R, acc, (pass & 1) != 0);
+    else
+      resident_rows(P, z.al, z.be, vin, vout, row0, nr, R, res_smem, acc, (pass & 1) != 0);  // alternate directions
     ++nbar;
     ++pass;
     if (!grid_sum<float, 3>(acc, P.part + (nbar & 1u) * 3u * nb, S, nbar * nb + P.bar_extra, z.tot, sh, &z.ok))

@@ -320,6 +320,7 @@ struct pff_mesh {
   unsigned rgrid[5] = {0};   // resident single-reduction CG: grid, rows per CTA and
   int32_t rrows[5] = {0};    // dynamic shared memory per U (0: no fan order, or the
   size_t rsmem[5] = {0};     // rows do not fit)
+  bool rfull[5] = {false};   // the resident CG's FULL form (coefficients and records too)
   bool st_fused = false;     // the staged tables also fit the single-reduction kernel
   int fam_U[8] = {0};        // tuned gathers in flight per CG-loop family
   int best_fam = 0;          // fastest family (kFamPhases when untuned)
@@ -470,6 +471,7 @@ struct CgPlan {
   int fam = kFamPhases;
   int U = 2;
   unsigned grid = 0;
+  bool full = false;  // resident family: its FULL form
   bool pers() const { return fam != kFamPhases; }
   bool st() const { return fam == kFamStaged || fam == kFamFusedStaged; }
   bool fused() const { return fam == kFamFused || fam == kFamFusedStaged; }
@@ -512,6 +514,7 @@ static CgPlan cg_plan(const pff_mesh *m, const pff_options &o, int model, bool f
   if (p.fam == kFamPhases) return p;
   p.U = m->fam_U[p.fam] ? m->fam_U[p.fam] : matvec_u(m);
   p.grid = fam_grid(m, p.fam, p.U, fp32);
+  p.full = p.fam == kFamResident && m->rfull[p.U];
   if (p.grid == 0 && (p.fam == kFamStaged || p.fam == kFamFusedStaged || p.fam == kFamResident)) {
     // not stageable, or the rows do not fit shared memory: global memory
     p.fam = p.fam == kFamStaged ? kFamPersistent : kFamFused;
@@ -536,11 +539,17 @@ template <typename R>
 static const void *plan_fun(const CgPlan &c) {
   if constexpr (sizeof(R) == 4) {
     if (c.res()) {
+      if (c.full) switch (c.U) {
+          case 1: return (const void *)k_cg_resident<1, true>;
+          case 3: return (const void *)k_cg_resident<3, true>;
+          case 4: return (const void *)k_cg_resident<4, true>;
+          default: return (const void *)k_cg_resident<2, true>;
+        }
       switch (c.U) {
-        case 1: return (const void *)k_cg_resident<1>;
-        case 3: return (const void *)k_cg_resident<3>;
-        case 4: return (const void *)k_cg_resident<4>;
-        default: return (const void *)k_cg_resident<2>;
+        case 1: return (const void *)k_cg_resident<1, false>;
+        case 3: return (const void *)k_cg_resident<3, false>;
+        case 4: return (const void *)k_cg_resident<4, false>;
+        default: return (const void *)k_cg_resident<2, false>;
       }
     }
     if (c.fused()) {
@@ -1047,27 +1056,33 @@ static pff_status configure(pff_mesh *m, const int32_t *tri_host) {
       m->rgrid[U] = 0u;
       m->rrows[U] = 0;
       m->rsmem[U] = 0;
+      m->rfull[U] = false;
       if (!coop || !m->fno) continue;
-      CgPlan c;
-      c.fam = kFamResident;
-      c.U = U;
       const int T = res_threads(U);
       const int64_t ctas = std::min<int64_t>((int64_t)nsm * res_minb(U), (m->N + T - 1) / T);
-      const int64_t rows = (m->N + ctas - 1) / ctas;
-      const size_t smem = (size_t)kResWords * sizeof(uint32_t) * (size_t)rows;
-      const void *f = plan_fun<float>(c);
-      cudaFuncAttributes fa;
-      CUDA_TRY(cudaFuncGetAttributes(&fa, f));
-      const int dyn_max = smem_optin - (int)fa.sharedSizeBytes;
-      if (smem > (size_t)std::max(dyn_max, 0)) continue;
-      // the opt-in maximum, so that every mesh's launch stays within it
-      CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max));
-      int occ = 0;
-      CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f, T, smem));
-      if ((int64_t)occ * nsm < ctas) continue;
-      m->rgrid[U] = (unsigned)ctas;
-      m->rrows[U] = (int32_t)rows;
-      m->rsmem[U] = smem;
+      const int64_t rows = ((m->N + ctas - 1) / ctas + 3) / 4 * 4;  // a multiple of 4 (16-byte arrays)
+      for (int full = 1; full >= 0; --full) {  // the FULL form where it fits
+        CgPlan c;
+        c.fam = kFamResident;
+        c.U = U;
+        c.full = full != 0;
+        const size_t smem = (size_t)(full ? kResWordsFull : kResWords) * sizeof(uint32_t) * (size_t)rows;
+        const void *f = plan_fun<float>(c);
+        cudaFuncAttributes fa;
+        CUDA_TRY(cudaFuncGetAttributes(&fa, f));
+        const int dyn_max = smem_optin - (int)fa.sharedSizeBytes;
+        if (smem > (size_t)std::max(dyn_max, 0)) continue;
+        // the opt-in maximum, so that every mesh's launch stays within it
+        CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max));
+        int occ = 0;
+        CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f, T, smem));
+        if ((int64_t)occ * nsm < ctas) continue;
+        m->rgrid[U] = (unsigned)ctas;
+        m->rrows[U] = (int32_t)rows;
+        m->rsmem[U] = smem;
+        m->rfull[U] = full != 0;
+        break;
+      }
     }
     if (!m->cgv) {
       PFF_TRY(dalloc((float4 **)&m->cgv, 2 * (size_t)(m->N + 2)));
@@ -1467,6 +1482,7 @@ static pff_status autotune(pff_mesh *m, const pff_options &o, Params<R> P, bool 
       c.fam = 1 + (kind - 1) / 4;
       c.U = 1 + (kind - 1) % 4;
       c.grid = fam_grid(m, c.fam, c.U, sizeof(R) == 4);
+      c.full = c.fam == kFamResident && m->rfull[c.U];
       return c;
     };
     for (int kind = 0; kind < NK && !skip && st == PFF_OK; ++kind) {
