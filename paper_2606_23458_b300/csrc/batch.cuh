@@ -397,17 +397,8 @@ __global__ void __launch_bounds__(pers_threads(U, false), kPersMinBlocks) kb_cg_
   __shared__ PersShared<R> z;
   if (S->done) return;  // set-up found b_eff = 0 or r_0 already small
   if (threadIdx.x == 0) {
-    z.rho = S->rho;
-    z.beta = S->beta;
-    z.alpha = S->alpha;
-    z.rr = S->rr;
-    z.pq = S->pq;
-    z.bn = S->bn;
-    z.iters = S->iters;
-    z.status = kStOk;
-    z.done = 0;
+    pers_load(z, S, Q.tol);
     z.ok = 1;
-    z.coef[1] = sizeof(R) == 4 ? (R)S->beta_f : (R)S->beta;
   }
   __syncthreads();
   const unsigned int nb = (unsigned)c.ncta;
@@ -427,15 +418,9 @@ __global__ void __launch_bounds__(pers_threads(U, false), kPersMinBlocks) kb_cg_
                         NoHook(), rank, (int)nb))
       break;
     if (threadIdx.x == 0) {
-      z.pq = z.tot[0];
-      if (z.pq == 0.0) {
-        z.done = 1;
-        z.flag = 1;
-      } else {
-        z.alpha = z.rho / z.pq;
-        z.coef[0] = sizeof(R) == 4 ? (R)(float)z.alpha : (R)z.alpha;
-        z.flag = 0;
-      }
+      const bool moved = pers_alpha(z);  // p = 0: nothing moved, the iterate is exact
+      z.done = moved ? z.done : 1;
+      z.flag = moved ? 0 : 1;
     }
     __syncthreads();
     if (z.flag) break;
@@ -447,48 +432,13 @@ __global__ void __launch_bounds__(pers_threads(U, false), kPersMinBlocks) kb_cg_
     if (!grid_sum<R, 2>(v2, part + (nbar & 1u) * 2u * nb, S, nbar * nb, z.tot, sh, &z.ok, NoHook(), rank,
                         (int)nb))
       break;
-    if (threadIdx.x == 0) {
-      bool stop = false;
-      const double t0 = z.tot[0], t1 = z.tot[1];
-      z.iters += 1;
-      z.rr = t0;
-      if (!(t0 == t0) || isinf(t0)) {
-        z.status = kStNonfinite;
-        z.done = 1;
-        stop = true;
-      } else if (sqrt(t0) <= Q.tol * z.bn) {
-        z.done = 1;
-        stop = true;
-      }
-      if (!stop && z.iters >= P.max_it) {
-        stop = true;
-        z.status = kStNotConverged;
-        z.done = 1;
-      }
-      z.beta = z.rho != 0.0 ? t1 / z.rho : 0.0;
-      z.rho = t1;
-      z.coef[1] = sizeof(R) == 4 ? (R)(float)z.beta : (R)z.beta;
-      z.flag = stop ? 1 : 0;
-    }
+    if (threadIdx.x == 0) z.flag = pers_beta(z, Q.tol, P.max_it) ? 1 : 0;
     __syncthreads();
     if (z.flag) break;
   }
   // the group's first CTA leaves the plate's scalars as the phases loop would
   if (rank == 0 && threadIdx.x == 0) {
-    if (!z.ok) {
-      z.status = kStTimeout;
-      z.done = 1;
-    }
-    S->iters = z.iters;
-    S->rr = z.rr;
-    S->pq = z.pq;
-    S->alpha = z.alpha;
-    S->alpha_f = (float)z.alpha;
-    S->beta = z.beta;
-    S->beta_f = (float)z.beta;
-    S->rho = z.rho;
-    S->status = z.status;
-    S->done = z.done;
+    pers_store(z, S);
     S->inner_done = 1;
   }
 }

@@ -2202,12 +2202,115 @@ __device__ __forceinline__ bool grid_sum(typename Acc<R>::T (&v)[NV], double *pa
 // The solve's scalars, kept in shared memory by thread 0 of every CTA
 // (identical in all CTAs); coef holds alpha and beta in the kernel
 // precision for every thread.
+// The two-all-reduce loops' scalar type: FP64 for FP64 meshes, double-word
+// FP32 for FP32 meshes (no FP64 instruction in the loop; see fused_scalars).
+template <typename R> struct Sc;
+template <> struct Sc<double> {
+  typedef double T;
+  static __device__ __forceinline__ T from(double d) { return d; }
+  static __device__ __forceinline__ double to(T v) { return v; }
+  static __device__ __forceinline__ T div(T a, T b) { return a / b; }
+  static __device__ __forceinline__ bool zero(T a) { return a == 0.0; }
+  static __device__ __forceinline__ bool finite(T a) { return !isnan(a) && !isinf(a); }
+  static __device__ __forceinline__ double coef(T a) { return a; }
+  // ||r|| <= tol ||b_eff||, as the kernel-per-phase loop takes it
+  static __device__ __forceinline__ bool stop(T t0, double tol, double bn, T) { return sqrt(t0) <= tol * bn; }
+};
+template <> struct Sc<float> {
+  typedef DF T;
+  static __device__ __forceinline__ T from(double d) { return df_from(d); }
+  static __device__ __forceinline__ double to(T v) { return df_to(v); }
+  static __device__ __forceinline__ T div(T a, T b) { return df_div(a, b); }
+  static __device__ __forceinline__ bool zero(T a) { return a.hi == 0.f; }
+  static __device__ __forceinline__ bool finite(T a) { return df_finite(a); }
+  static __device__ __forceinline__ float coef(T a) { return a.hi; }
+  // |r|^2 <= (tol ||b_eff||)^2 (thr2)
+  static __device__ __forceinline__ bool stop(T t0, double, double, T thr2) { return df_le(t0, thr2); }
+};
+
 template <typename R> struct PersShared {
-  double rho, beta, alpha, rr, pq, bn;
-  double tot[2];
+  typedef typename Sc<R>::T T;
+  T rho, beta, alpha, rr, pq, thr2;
+  double bn;
+  T tot[2];
   int iters, status, done, flag, ok;
   R coef[2];
 };
+
+// Thread 0: the two-all-reduce loops' scalars at the start, alpha after the
+// p.q all-reduce (false: p = 0, the iterate is exact), the stop test and
+// beta after the (|r|^2, r.z) all-reduce (true: stop), and the scalars left
+// for the kernel-per-phase loop at the end.
+template <typename R>
+__device__ __forceinline__ void pers_load(PersShared<R> &z, const SolveScalars *S, double tol) {
+  typedef Sc<R> C;
+  z.rho = C::from(S->rho);
+  z.beta = C::from(S->beta);
+  z.alpha = C::from(S->alpha);
+  z.rr = C::from(S->rr);
+  z.pq = C::from(S->pq);
+  z.bn = S->bn;
+  z.thr2 = C::from(tol * S->bn * (tol * S->bn));
+  z.iters = S->iters;
+  z.status = kStOk;
+  z.done = 0;
+  z.coef[1] = sizeof(R) == 4 ? (R)S->beta_f : (R)S->beta;
+}
+
+template <typename R>
+__device__ __forceinline__ bool pers_alpha(PersShared<R> &z) {
+  typedef Sc<R> C;
+  z.pq = z.tot[0];
+  if (C::zero(z.pq)) return false;
+  z.alpha = C::div(z.rho, z.pq);
+  z.coef[0] = (R)C::coef(z.alpha);
+  return true;
+}
+
+template <typename R>
+__device__ __forceinline__ bool pers_beta(PersShared<R> &z, double tol, int max_it) {
+  typedef Sc<R> C;
+  bool stop = false;
+  const typename C::T t0 = z.tot[0], t1 = z.tot[1];
+  z.iters += 1;
+  z.rr = t0;
+  if (!C::finite(t0)) {
+    z.status = kStNonfinite;
+    z.done = 1;
+    stop = true;
+  } else if (C::stop(t0, tol, z.bn, z.thr2)) {
+    z.done = 1;
+    stop = true;
+  }
+  if (!stop && z.iters >= max_it) {
+    stop = true;
+    z.status = kStNotConverged;
+    z.done = 1;
+  }
+  z.beta = !C::zero(z.rho) ? C::div(t1, z.rho) : C::from(0.0);
+  z.rho = t1;
+  z.coef[1] = (R)C::coef(z.beta);
+  return stop;
+}
+
+template <typename R>
+__device__ __forceinline__ void pers_store(PersShared<R> &z, SolveScalars *S) {
+  typedef Sc<R> C;
+  if (!z.ok) {
+    z.status = kStTimeout;
+    z.done = 1;
+  }
+  S->iters = z.iters;
+  S->rr = C::to(z.rr);
+  S->pq = C::to(z.pq);
+  S->alpha = C::to(z.alpha);
+  S->alpha_f = (float)C::coef(z.alpha);
+  S->beta = C::to(z.beta);
+  S->beta_f = (float)C::coef(z.beta);
+  S->rho = C::to(z.rho);
+  S->status = z.status;
+  S->done = z.done;
+}
 
 // Partials: P.part holds two buffers of 2 * gridDim.x slots, used by
 // alternate barriers (a CTA can only refill a buffer after every CTA has
@@ -2272,18 +2375,7 @@ __global__ void __launch_bounds__(pers_threads(U, ST), kPersMinBlocks) k_cg_pers
       return;
     }
   }
-  if (threadIdx.x == 0) {
-    z.rho = S->rho;
-    z.beta = S->beta;
-    z.alpha = S->alpha;
-    z.rr = S->rr;
-    z.pq = S->pq;
-    z.bn = S->bn;
-    z.iters = S->iters;
-    z.status = kStOk;
-    z.done = 0;
-    z.coef[1] = sizeof(R) == 4 ? (R)S->beta_f : (R)S->beta;
-  }
+  if (threadIdx.x == 0) pers_load(z, S, P.tol);
   __syncthreads();
   const unsigned int nb = gridDim.x;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
@@ -2300,15 +2392,9 @@ __global__ void __launch_bounds__(pers_threads(U, ST), kPersMinBlocks) k_cg_pers
                         (typename AC::T(*)[1])sh, &z.ok))
       break;
     if (threadIdx.x == 0) {
-      z.pq = z.tot[0];
-      if (z.pq == 0.0) {  // p = 0: nothing moved, the iterate is exact
-        z.done = 1;
-        z.flag = 1;
-      } else {
-        z.alpha = z.rho / z.pq;
-        z.coef[0] = sizeof(R) == 4 ? (R)(float)z.alpha : (R)z.alpha;
-        z.flag = 0;
-      }
+      const bool moved = pers_alpha(z);  // p = 0: nothing moved, the iterate is exact
+      z.done = moved ? z.done : 1;
+      z.flag = moved ? 0 : 1;
     }
     __syncthreads();
     if (z.flag) break;
@@ -2320,48 +2406,13 @@ __global__ void __launch_bounds__(pers_threads(U, ST), kPersMinBlocks) k_cg_pers
     ++nbar;
     if (!grid_sum<R, 2>(v2, P.part + (nbar & 1u) * 2u * nb, S, nbar * nb + P.bar_extra, z.tot, sh, &z.ok))
       break;
-    if (threadIdx.x == 0) {
-      bool stop = false;
-      const double t0 = z.tot[0], t1 = z.tot[1];
-      z.iters += 1;
-      z.rr = t0;
-      if (!(t0 == t0) || isinf(t0)) {
-        z.status = kStNonfinite;
-        z.done = 1;
-        stop = true;
-      } else if (sqrt(t0) <= P.tol * z.bn) {
-        z.done = 1;
-        stop = true;
-      }
-      if (!stop && z.iters >= P.max_it) {
-        stop = true;
-        z.status = kStNotConverged;
-        z.done = 1;
-      }
-      z.beta = z.rho != 0.0 ? t1 / z.rho : 0.0;
-      z.rho = t1;
-      z.coef[1] = sizeof(R) == 4 ? (R)(float)z.beta : (R)z.beta;
-      z.flag = stop ? 1 : 0;
-    }
+    if (threadIdx.x == 0) z.flag = pers_beta(z, P.tol, P.max_it) ? 1 : 0;
     __syncthreads();
     if (z.flag) break;
   }
   // CTA 0 leaves the scalars as the kernel-per-phase loop would
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    if (!z.ok) {
-      z.status = kStTimeout;
-      z.done = 1;
-    }
-    S->iters = z.iters;
-    S->rr = z.rr;
-    S->pq = z.pq;
-    S->alpha = z.alpha;
-    S->alpha_f = (float)z.alpha;
-    S->beta = z.beta;
-    S->beta_f = (float)z.beta;
-    S->rho = z.rho;
-    S->status = z.status;
-    S->done = z.done;
+    pers_store(z, S);
     S->inner_done = 1;
   }
 }

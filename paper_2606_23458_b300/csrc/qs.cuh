@@ -644,24 +644,27 @@ __global__ void __launch_bounds__(256) k_qs_entry_build(QkParams<float> I) {
 // K_ac (p_c - p_i)) with a grid all-reduce of p.q, then the update with a grid
 // all-reduce of (|r|^2, r.z) -- two grid barriers per iteration instead of
 // the element pass's three.  Decisions and bounded waits as in
-// k_qs_cg_persistent.
+// k_qs_cg_persistent; the totals and the scalar step (alpha, beta, the stop
+// test |r|^2 <= tol^2 |r_0|^2) in double-word FP32, as in the damage
+// solve's single-reduction loops (no FP64 instruction in the loop).
 template <int U>
 __global__ void __launch_bounds__(kQsPersThreads, 2) k_qs_cg_rows(QkParams<float> I, SolveScalars *B) {
   typedef Acc<float> AC;
   typedef float2 K2;
   __shared__ typename AC::T sh[kQsPersThreads / 32][2];
-  __shared__ double tot[2];
+  __shared__ DF tot[2];
   __shared__ int ok_sh, flag;
-  __shared__ double rho, rr, pq, alpha_d, beta_d;
+  __shared__ DF rho, rr, pq, alpha_d, beta_d, thr2;
   __shared__ int iters, status;
   QsScalars *S = I.qs;
   if (S->done) return;
   if (threadIdx.x == 0) {
-    rho = S->rho;
-    rr = 0.0;
-    pq = 0.0;
-    alpha_d = 0.0;
-    beta_d = 0.0;
+    rho = df_from(S->rho);
+    rr = DF{0.f, 0.f};
+    pq = DF{0.f, 0.f};
+    alpha_d = DF{0.f, 0.f};
+    beta_d = DF{0.f, 0.f};
+    thr2 = df_from(I.tol * I.tol * S->rr0);
     iters = 0;
     status = 0;
   }
@@ -674,7 +677,7 @@ __global__ void __launch_bounds__(kQsPersThreads, 2) k_qs_cg_rows(QkParams<float
   // vectors the previous one touched last (the working set exceeds L2)
   const int ilast = tid < I.N ? tid + (I.N - 1 - tid) / stride * stride : tid - stride;
   for (;;) {
-    const float beta = (float)beta_d;
+    const float beta = beta_d.hi;
     const bool rev = (iters & 1) != 0;
     const int istep = rev ? -stride : stride;
     // rows: q = K_T p_new on the free dofs, p_new . q
@@ -769,10 +772,10 @@ __global__ void __launch_bounds__(kQsPersThreads, 2) k_qs_cg_rows(QkParams<float
       break;
     if (threadIdx.x == 0) {
       pq = tot[0];
-      alpha_d = pq != 0.0 ? rho / pq : 0.0;
+      alpha_d = pq.hi != 0.f ? df_div(rho, pq) : DF{0.f, 0.f};
     }
     __syncthreads();
-    const float alpha = (float)alpha_d;
+    const float alpha = alpha_d.hi;
     typename AC::T v2[2] = {AC::zero(), AC::zero()};
     for (int i = rev ? ilast : tid; rev ? i >= tid : i < I.N; i += istep) {
       const K2 pn = qs_pnew(I, i, beta), q = I.q[i], dg = I.dg[i];
@@ -796,16 +799,16 @@ __global__ void __launch_bounds__(kQsPersThreads, 2) k_qs_cg_rows(QkParams<float
       iters += 1;
       rr = tot[0];
       flag = 0;
-      if (!(tot[0] == tot[0]) || isinf(tot[0])) {
+      if (!df_finite(tot[0])) {
         status = kStNonfinite;
         flag = 1;
-      } else if (pq == 0.0 || sqrt(tot[0]) <= I.tol * sqrt(S->rr0)) {
+      } else if (pq.hi == 0.f || df_le(tot[0], thr2)) {
         flag = 1;
       } else if (iters >= I.max_it) {
         status = kStNotConverged;
         flag = 1;
       }
-      beta_d = rho != 0.0 ? tot[1] / rho : 0.0;
+      beta_d = rho.hi != 0.f ? df_div(tot[1], rho) : DF{0.f, 0.f};
       rho = tot[1];
     }
     __syncthreads();
@@ -816,11 +819,11 @@ __global__ void __launch_bounds__(kQsPersThreads, 2) k_qs_cg_rows(QkParams<float
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     S->iters = iters;
-    S->rr = rr;
-    S->pq = pq;
-    S->rho = rho;
-    S->alpha = alpha_d;
-    S->beta = beta_d;
+    S->rr = df_to(rr);
+    S->pq = df_to(pq);
+    S->rho = df_to(rho);
+    S->alpha = df_to(alpha_d);
+    S->beta = df_to(beta_d);
     S->status = done ? status : kStTimeout;
     S->done = 1;
   }
