@@ -2180,14 +2180,16 @@ __device__ __forceinline__ bool grid_sum(typename Acc<R>::T (&v)[NV], double *pa
     const unsigned long long t0 = global_ns();
     unsigned int spins = 0;
     while (ld_acquire_u32(&S->bar) < target) {
-      if (*(volatile int32_t *)&S->abort) {
-        ok = 0;
-        break;
-      }
-      if ((++spins & 31u) == 0u && global_ns() - t0 > kSpinTimeoutNs) {
-        *(volatile int32_t *)&S->abort = 1;
-        ok = 0;
-        break;
+      if ((++spins & 31u) == 0u) {  // another CTA gave up, or this wait is too long
+        if (*(volatile int32_t *)&S->abort) {
+          ok = 0;
+          break;
+        }
+        if (global_ns() - t0 > kSpinTimeoutNs) {
+          *(volatile int32_t *)&S->abort = 1;
+          ok = 0;
+          break;
+        }
       }
     }
     if (ok) hook();

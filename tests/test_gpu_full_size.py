@@ -18,7 +18,7 @@ import numpy as np
 import pytest
 
 import pff_synth as S
-from gpu_common import FIELD_FLOOR, merge_worst, rel_l2, state_errs, to_np
+from gpu_common import FIELD_FLOOR, field_err, merge_worst, rel_l2, state_errs, to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -160,6 +160,39 @@ def test_sent_full_size_increment(pff):
         out.append((r["reaction"][0], to_np(st["d"])))
     assert abs(out[0][0] - out[1][0]) <= 1e-7 * abs(out[1][0]), (out[0][0], out[1][0])
     assert np.abs(out[0][1] - out[1][1]).max() <= 1e-6
+
+
+def test_sent_full_size_increment_vs_oracle(orc, pff):
+    """The 700 x 700 SENT's first increment (FP64 state, FP32 tangent CG)
+    checked by the oracle where it can be checked at this size: the
+    mechanics' equilibrium (the oracle's f_int at the GPU's u and the
+    increment's starting damage meets the Newton stop test on the free dofs,
+    and gives the GPU's reaction), the history (the oracle's psi+ at that u,
+    element by element), and the damage (the oracle's own solve with the
+    GPU's history from the same starting damage, entry by entry)."""
+    import torch
+    c = S.sent(700)
+    mat = c["material"]
+    m = pff.Mesh.from_plate(c["mesh"], precision="fp64")
+    m.set_material(mat, 0.5)
+    st = m.new_state()
+    d0, H0 = to_np(st["d"]).copy(), to_np(st["H"]).copy()
+    r = m.qs_run(st, c["bc"], 1, c["du"], newton_tol=c["newton_tol"], krylov="fp32",
+                 opts=pff.options(cg_tol=c["cg_tol"], cg_max_it=100000))
+    torch.cuda.synchronize()
+    u, d, H = to_np(st["u"]).reshape(-1, 2), to_np(st["d"]), to_np(st["H"])
+    om = orc.Mesh.from_plate(c["mesh"])
+    f, psip = om.internal_force(mat, u, d0)
+    bc = c["bc"]
+    free = np.stack([(bc & 1) == 0, (bc & 6) == 0], axis=1)
+    rfree = np.linalg.norm(f[free])
+    assert rfree <= 1.01 * c["newton_tol"] * np.linalg.norm(f), (rfree, np.linalg.norm(f))
+    reac = f[(bc & 4) != 0, 1].sum()
+    assert abs(r["reaction"][0] - reac) <= 1e-9 * abs(reac), (r["reaction"][0], reac)
+    Hor = np.maximum(H0, psip)
+    assert field_err(H, Hor) <= 1e-10, field_err(H, Hor)
+    dor, info, rel, status, _ = om.damage_solve(mat, H, d0, tol=c["cg_tol"], max_it=100000)
+    assert status == 0 and np.abs(d - dor).max() <= 1e-6, np.abs(d - dor).max()
 
 
 @pytest.fixture(scope="module")
