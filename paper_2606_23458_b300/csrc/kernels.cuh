@@ -1247,8 +1247,10 @@ __device__ __forceinline__ void drec_notch_node(const Params<R> &P, int i) {
   }
 }
 
+// FP32: four CTAs per SM (at most 64 registers; the U > 1 variants spill a
+// little, measured faster than three CTAs without spills).
 template <typename R, int U>
-__global__ void __launch_bounds__(256) k_dmg_rhs_nc(Params<R> P) {
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 1) k_dmg_rhs_nc(Params<R> P) {
   typedef typename Params<R>::R4 R4;
   typedef Acc<R> AC;
   typename AC::T vals[3] = {AC::zero(), AC::zero(), AC::zero()};
@@ -1300,7 +1302,9 @@ __global__ void __launch_bounds__(256) k_dmg_rhs_nc(Params<R> P) {
 // of the force kernel followed by the right-hand-side kernel: the history
 // each thread uses is max(H_n, psi+) taken the way history_update takes it,
 // whether or not the element's owner entry has already stored it (max is
-// idempotent), so no thread depends on another's write.
+// idempotent), so no thread depends on another's write.  FP32: four CTAs
+// per SM (64 registers: U = 1 fits without spills; 109 against 124 us for
+// three CTAs on the 1M-node plate).
 template <typename R>
 __device__ __forceinline__ void force_rhs_entry(const Params<R> &P, int en, int slot, int node, R &fx, R &fy, R &psip,
                                                 typename Params<R>::R4 &o, typename Params<R>::R2 *cf, uint32_t fm) {
@@ -1332,7 +1336,7 @@ __device__ __forceinline__ void force_rhs_entry(const Params<R> &P, int en, int 
 }
 
 template <typename R, int U>
-__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 1) k_force_rhs_nc(Params<R> P) {
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 1) k_force_rhs_nc(Params<R> P) {
   typedef typename Params<R>::R4 R4;
   typedef Acc<R> AC;
   typename AC::T vals[3] = {AC::zero(), AC::zero(), AC::zero()};
