@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(256) kb_force(Params<R> P, Batch B) {
 }
 
 template <typename R, int U>
-__global__ void __launch_bounds__(256) kb_rhs(Params<R> P, Batch B) {
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 1) kb_rhs(Params<R> P, Batch B) {
   typedef typename Params<R>::R4 R4;
   typedef Acc<R> AC;
   const int p = B.blk_plate[blockIdx.x];
