@@ -112,9 +112,11 @@ typedef struct {
                            PFF_CG_RESIDENT = the single-reduction CG with
                            each CTA owning a contiguous range of rows whose
                            x, p, diagonal and fan tables stay in shared
-                           memory for the whole solve (FP32 element-wise
-                           operator in fan order, rows fitting 28 B each;
-                           else as PFF_CG_FUSED);
+                           memory for the whole solve, and where the rows
+                           fit 108 B each their coefficients and records
+                           too (FP32 element-wise operator in fan order,
+                           rows fitting at least 28 B each; else as
+                           PFF_CG_FUSED);
                            PFF_CG_AUTO = the fastest on this mesh, timed on
                            first use [0].
                            Same iteration arithmetic; the forms group the

@@ -104,17 +104,21 @@ def test_fp64_1m_plate_at1_amor_matches_oracle(orc, pff):
     assert np.all(g["d"] >= -1e-15) and np.all(g["d"] <= 1.0)
 
 
-def test_fp32_1m_plate_bench_configuration(pff, plate_1m):
-    """FP32 with the bench's options (graph loop, autotuned CG family, the
-    default element-wise damage operator) against the FP64 oracle state at
-    the end of the window: u relative L2 <= 1e-4, max |d - d_oracle| <=
-    1e-3."""
+@pytest.mark.parametrize("cgk", ["auto", "resident", "fused"])
+def test_fp32_1m_plate_bench_configuration(pff, plate_1m, cgk):
+    """FP32 with the bench's options (graph loop, the default element-wise
+    damage operator; the autotuned CG family, or the resident loop, whose
+    rows at this size keep only x, p, the diagonal and the fan tables in
+    shared memory, or the global-memory single-reduction loop) against the
+    FP64 oracle state at the end of the window: u relative L2 <= 1e-4, max
+    |d - d_oracle| <= 1e-3."""
     import torch
     c = plate_1m["c"]
     gm = pff.Mesh.from_plate(c["mesh"], precision="fp32")
     gm.set_material(c["material"], c["cfl"])
     gst = gm.new_state()
-    gm.run(gst, plate_1m["nsteps"], opts=pff.options(cg_tol=c["cg_tol"], t_ramp=c["t_ramp"]))
+    kind = {v: k for k, v in pff.CG_KINDS.items()}[cgk]
+    gm.run(gst, plate_1m["nsteps"], opts=pff.options(cg_tol=c["cg_tol"], t_ramp=c["t_ramp"], cg_kernel=kind))
     torch.cuda.synchronize()
     assert gm.sync_status() == 0
     o = plate_1m["ost"]
