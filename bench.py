@@ -950,22 +950,23 @@ def run_ours(args):
     per_solve = 1 if cg_kind_run not in ("phases", "auto") else None
     launches = int(1 + 4 * args.steps + (args.steps * per_solve if per_solve else 2 * iters.sum()))
 
-    # end-to-end through the public API with host-resident state: every step
-    # copies the state in from pinned host memory, runs, and copies it back.
+    # end-to-end through the public API with host-resident state
+    # (pff_run_host): every step copies the state in from pinned host memory,
+    # runs, and copies it back (the copies of u, v, a and H back overlap the
+    # damage solve); one call per step.
     hs = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in st.items()}
     for k in hs:
         hs[k].copy_(st[k])
     bytes_state = sum(v.numel() * v.element_size() for v in st.values())
+    mesh.run_host(hs, st, 1, step0=total, opts=opts)  # its graph, once
+    for k in hs:
+        hs[k].copy_(st[k])
     torch.cuda.synchronize()
     ee0 = torch.cuda.Event(enable_timing=True)
     ee1 = torch.cuda.Event(enable_timing=True)
     ee0.record(stream)
     for n in range(args.e2e_steps):
-        for k in st:
-            st[k].copy_(hs[k], non_blocking=True)
-        mesh.run(st, 1, step0=total + n, opts=opts, iters_log=log[total + n:total + n + 1])
-        for k in st:
-            hs[k].copy_(st[k], non_blocking=True)
+        mesh.run_host(hs, st, 1, step0=total + 1 + n, opts=opts, iters_log=log[total + n:total + n + 1])
     ee1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = ee0.elapsed_time(ee1)

@@ -309,6 +309,20 @@ pff_status pff_run(pff_mesh *mesh, const pff_state *state, int64_t step0,
                    int64_t nsteps, double dt, const pff_options *opt,
                    int32_t *iters_log, double *energy_log, pff_stream stream);
 
+/* pff_run with the state resident in host memory: host holds u, v, a, d, H
+ * in pinned host memory (the device layout and precision), dev the same
+ * fields as device workspace (caller-owned, mesh precision).  Every step
+ * copies the state in, runs the step of pff_run on dev, and copies it back
+ * out; the copies of u, v, a and H back to the host start as soon as the
+ * step's mechanics are done, overlapping the damage solve, and d follows
+ * the clamp.  The paper has no counterpart: this is the call for callers
+ * whose state lives on the host between steps.  damage_every > 1 is
+ * PFF_ERR_ARG.  iters_log as pff_run (device).  Asynchronous: host is
+ * complete after the stream synchronises. */
+pff_status pff_run_host(pff_mesh *mesh, const pff_state *host, const pff_state *dev,
+                        int64_t step0, int64_t nsteps, double dt, const pff_options *opt,
+                        int32_t *iters_log, pff_stream stream);
+
 /* Checkpointed run and its adjoint (Sec. 4: implicit differentiation of the
  * damage solve, Eqs. implicit_forward_linear_system /
  * implicit_adjoint_linear_system / implicit_gc_l0_element_term, with

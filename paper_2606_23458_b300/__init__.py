@@ -96,6 +96,8 @@ _sig = {
                           C.POINTER(pff_options), _P],
     "pff_damage_solve": [_P, _P, _P, _P, C.POINTER(pff_options), C.POINTER(C.c_int32),
                          C.POINTER(C.c_double), C.POINTER(C.c_int32), _P],
+    "pff_run_host": [_P, C.POINTER(pff_state), C.POINTER(pff_state), C.c_int64, C.c_int64, C.c_double,
+                     C.POINTER(pff_options), _P, _P],
     "pff_run": [_P, C.POINTER(pff_state), C.c_int64, C.c_int64, C.c_double,
                 C.POINTER(pff_options), _P, _P, _P],
     "pff_sync_status": [_P, _P],
@@ -417,6 +419,22 @@ class Mesh:
         assert st["H"].dtype.is_floating_point and st["H"].element_size() == 8
         return pff_state(st["u"].data_ptr(), st["v"].data_ptr(), st["a"].data_ptr(),
                          st["d"].data_ptr(), st["H"].data_ptr())
+
+    def run_host(self, host, st, nsteps, step0=0, dt=None, opts=None, iters_log=None, stream=None):
+        """pff_run_host: nsteps steps of the state held in `host` (pinned CPU
+        tensors u, v, a, d, H in the mesh precision), with `st` (device
+        tensors of the same shapes) as the device workspace; each step copies
+        the state in and back out."""
+        for k in ("u", "v", "a", "d", "H"):
+            t = host[k]
+            assert not t.is_cuda and t.is_pinned() and t.is_contiguous(), k
+            assert t.shape == st[k].shape and t.dtype == st[k].dtype, k
+        h = pff_state(host["u"].data_ptr(), host["v"].data_ptr(), host["a"].data_ptr(),
+                      host["d"].data_ptr(), host["H"].data_ptr())
+        s = self._state(st)
+        o = opts or options()
+        _check(_lib.pff_run_host(self._h, C.byref(h), C.byref(s), int(step0), int(nsteps),
+                                 float(dt or self.dt), C.byref(o), _dptr(iters_log), _stream(stream)))
 
     def step_explicit(self, st, t_next, dt=None, opts=None, stream=None):
         s = self._state(st)

@@ -302,6 +302,7 @@ struct pff_mesh {
   double *stab = nullptr;        // S(t) per step of the current run
   int64_t stab_cap = 0;
   GraphCache solve_g, step_g, mech_g;  // mech_g: a step without the damage solve
+  GraphCache host_g;                   // a step with its host copies (pff_run_host)
   int block = 256;
   // launch configuration (kernel id -> grid, dynamic shared memory)
   int32_t NB = 256, nblk = 0, maxE = 0;
@@ -352,6 +353,7 @@ static void mesh_free(pff_mesh *m) {
   if (!m) return;
   free_graph(m->solve_g);
   free_graph(m->step_g);
+  free_graph(m->host_g);
   free_graph(m->mech_g);
   void *ptrs[] = {m->gcs, m->st_cta, m->st_rng, m->st_nrng, m->st_lrec, m->st_slot, m->cgv, m->cgp,
                   m->ptr, m->ent, m->ell, m->rec, m->drec, m->erec, m->ecmp, m->ecf, m->ecfd, m->fno, m->fmap,
@@ -1744,8 +1746,8 @@ __global__ void k_set_i64(int64_t *p, int64_t v) {
 template <typename R>
 static pff_status run_t(pff_mesh *m, const pff_state *st, int64_t step0, int64_t nsteps, double dt,
                         const pff_options &o, int32_t *iters_log, double *energy_log, cudaStream_t s,
-                        GraphCache *gcache = nullptr, const Tape *tape = nullptr) {
-  GraphCache &gc = gcache ? *gcache : m->step_g;
+                        GraphCache *gcache = nullptr, const Tape *tape = nullptr, const pff_state *host = nullptr) {
+  GraphCache &gc = gcache ? *gcache : (host ? m->host_g : m->step_g);
   Params<R> P = base_params<R>(m, o);
   P.u = (typename V<R>::T2 *)st->u;
   P.v = (typename V<R>::T2 *)st->v;
@@ -1762,6 +1764,7 @@ static pff_status run_t(pff_mesh *m, const pff_state *st, int64_t step0, int64_t
     PFF_TRY(dalloc(&m->stab, nsteps + 1));
     m->stab_cap = nsteps + 1;
     free_graph(m->step_g);
+    free_graph(m->host_g);
     free_graph(m->mech_g);
     if (gcache) free_graph(*gcache);
   }
@@ -1789,8 +1792,19 @@ static pff_status run_t(pff_mesh *m, const pff_state *st, int64_t step0, int64_t
   // (n + 1) % n_sub == 0 only; H is updated every step by the force kernel
   const int64_t n_sub = std::max<int32_t>(1, o.damage_every);
   auto solves = [&](int64_t n) { return (step0 + n + 1) % n_sub == 0; };
+  // host-resident state (pff_run_host): every step copies the state in and
+  // out (bytes of u, v, a; d; H)
+  const size_t bn2 = (size_t)m->N * 2 * sizeof(R), bn1 = (size_t)m->N * sizeof(R), bne = (size_t)m->Ne * sizeof(double);
+  void *const hp[5] = {host ? host->u : nullptr, host ? host->v : nullptr, host ? host->a : nullptr,
+                       host ? host->d : nullptr, host ? (void *)host->H : nullptr};
+  void *const dp[5] = {st->u, st->v, st->a, st->d, (void *)st->H};
+  const size_t nb[5] = {bn2, bn2, bn2, bn1, bne};
   if (o.loop_mode == PFF_LOOP_HOST) {
     for (int64_t n = 0; n < nsteps; ++n) {
+      if (host) {
+        for (int k = 0; k < 5; ++k) CUDA_TRY(cudaMemcpyAsync(dp[k], hp[k], nb[k], cudaMemcpyHostToDevice, s));
+        if (sizeof(R) == 4) PFF_TRY(bind_history<R>(m, P, st->H, s));
+      }
       PFF_TRY(launch<R>(m, KP_PREDICT, P, s));
       if (solves(n) && fused) {
         PFF_TRY(launch<R>(m, KP_FRHS, P, s));
@@ -1808,6 +1822,8 @@ static pff_status run_t(pff_mesh *m, const pff_state *st, int64_t step0, int64_t
         E.energy_out = energy_log + 4 * n;
         PFF_TRY(launch<R>(m, KP_ENERGIES, E, s));
       }
+      if (host)
+        for (int k = 0; k < 5; ++k) CUDA_TRY(cudaMemcpyAsync(hp[k], dp[k], nb[k], cudaMemcpyDeviceToHost, s));
     }
     CUDA_TRY(cudaGetLastError());
     return PFF_OK;
@@ -1821,6 +1837,7 @@ static pff_status run_t(pff_mesh *m, const pff_state *st, int64_t step0, int64_t
                                (uint64_t)plan.fam,
                                (uint64_t)plan.U, (uint64_t)o.cg_kernel, (uint64_t)fused,
                                (uint64_t)m->var[KP_FRHS]};
+  for (int k = 0; k < 5; ++k) key.push_back((uint64_t)hp[k]);
   uint64_t b1, b2;
   std::memcpy(&b1, &o.cg_tol, 8);
   std::memcpy(&b2, &dt, 8);
@@ -1837,9 +1854,42 @@ static pff_status run_t(pff_mesh *m, const pff_state *st, int64_t step0, int64_t
     }
     P.use_cond = pers ? 0 : 1;
     cudaGraphNode_t n_pr, n_f, last;
-    pff_status stt = add_kernel<R>(m, g, {}, KP_PREDICT, P, &n_pr);
-    if (stt == PFF_OK) stt = add_kernel<R>(m, g, {n_pr}, fused ? KP_FRHS : KP_FORCE, P, &n_f);
+    pff_status stt = PFF_OK;
+    std::vector<cudaGraphNode_t> dep_pr, dep_f;
+    cudaGraphNode_t cin[5];
+    if (host) {
+      // the state in (the predictor needs u, v, a; the force kernel d and H,
+      // FP32 through the history mirror)
+      for (int k = 0; k < 5 && stt == PFF_OK; ++k)
+        if (cudaGraphAddMemcpyNode1D(&cin[k], g, nullptr, 0, dp[k], hp[k], nb[k], cudaMemcpyHostToDevice) !=
+            cudaSuccess)
+          stt = fail(PFF_ERR_CUDA, "host step: copy-in node");
+      dep_pr = {cin[0], cin[1], cin[2]};
+      dep_f = {cin[3], cin[4]};
+      if (stt == PFF_OK && sizeof(R) == 4) {
+        const double *Hd = st->H;
+        float *Hf = (float *)m->Hf;
+        int ne = (int)m->Ne;
+        void *margs[] = {(void *)&Hd, (void *)&Hf, (void *)&ne};
+        cudaGraphNode_t n_mir;
+        stt = add_generic(g, {cin[4]}, (const void *)k_h_mirror,
+                          std::min<unsigned>(grid_for(m->Ne, 256), stride_cap()), 256, 0, margs, &n_mir);
+        dep_f = {cin[3], n_mir};
+      }
+    }
+    if (stt == PFF_OK) stt = add_kernel<R>(m, g, dep_pr, KP_PREDICT, P, &n_pr);
+    dep_f.push_back(n_pr);
+    if (stt == PFF_OK) stt = add_kernel<R>(m, g, dep_f, fused ? KP_FRHS : KP_FORCE, P, &n_f);
     if (stt == PFF_OK) stt = append_solve<R>(m, g, n_f, P, plan, &last, fused);
+    if (stt == PFF_OK && host) {
+      // the state out: u, v, a and H are final after the force kernel, so
+      // their copies overlap the damage solve; d follows the clamp
+      cudaGraphNode_t n_out;
+      for (int k = 0; k < 5 && stt == PFF_OK; ++k)
+        if (cudaGraphAddMemcpyNode1D(&n_out, g, k == 3 ? &last : &n_f, 1, hp[k], dp[k], nb[k],
+                                     cudaMemcpyDeviceToHost) != cudaSuccess)
+          stt = fail(PFF_ERR_CUDA, "host step: copy-out node");
+    }
     if (stt == PFF_OK && tape) {
       cudaKernelNodeParams kp;
       std::memset(&kp, 0, sizeof(kp));
@@ -2547,6 +2597,7 @@ pff_status pff_mesh_set_material(pff_mesh *m, const pff_material *mat, double cf
   CUDA_TRY(cudaDeviceSynchronize());
   free_graph(m->solve_g);
   free_graph(m->step_g);
+  free_graph(m->host_g);
   m->has_mat = true;
   if (!m->gc_field.empty()) PFF_TRY(upload_gc_field(m));  // relative to the new Gc
   const double cp = std::sqrt((m->lam + 2.0 * m->mu) / mat->rho);
@@ -2630,6 +2681,21 @@ pff_status pff_run(pff_mesh *m, const pff_state *st, int64_t step0, int64_t nste
   cudaStream_t s = (cudaStream_t)stream;
   return m->prec == PFF_FP64 ? run_t<double>(m, st, step0, nsteps, dt, o, iters_log, energy_log, s)
                              : run_t<float>(m, st, step0, nsteps, dt, o, iters_log, energy_log, s);
+}
+
+pff_status pff_run_host(pff_mesh *m, const pff_state *host, const pff_state *dev, int64_t step0, int64_t nsteps,
+                        double dt, const pff_options *opt, int32_t *iters_log, pff_stream stream) {
+  if (!m || !host || !dev || !host->u || !host->v || !host->a || !host->d || !host->H || !dev->u || !dev->v ||
+      !dev->a || !dev->d || !dev->H)
+    return fail(PFF_ERR_ARG, "null argument");
+  if (!m->has_mat) return fail(PFF_ERR_ARG, "material not set");
+  if (!(dt > 0) || nsteps < 0 || step0 < 0) return fail(PFF_ERR_ARG, "bad dt / step range");
+  const pff_options o = defaults(opt);
+  if (o.damage_every > 1) return fail(PFF_ERR_ARG, "damage subcycling is not supported with host-resident state");
+  cudaStream_t s = (cudaStream_t)stream;
+  return m->prec == PFF_FP64
+             ? run_t<double>(m, dev, step0, nsteps, dt, o, iters_log, nullptr, s, nullptr, nullptr, host)
+             : run_t<float>(m, dev, step0, nsteps, dt, o, iters_log, nullptr, s, nullptr, nullptr, host);
 }
 
 pff_status pff_sync_status(pff_mesh *m, pff_stream stream) {
@@ -3075,6 +3141,7 @@ static pff_status recompute_mech_t(pff_mesh *m, pff_ckpt *c, const pff_state *st
     PFF_TRY(dalloc(&m->stab, nsteps + 1));
     m->stab_cap = nsteps + 1;
     free_graph(m->step_g);
+    free_graph(m->host_g);
     free_graph(m->mech_g);
   }
   {
@@ -3382,6 +3449,7 @@ pff_status pff_mesh_set_gc_field(pff_mesh *m, const double *gc) {
   }
   free_graph(m->solve_g);
   free_graph(m->step_g);
+  free_graph(m->host_g);
   free_graph(m->mech_g);
   return PFF_OK;
 }
@@ -3397,6 +3465,7 @@ pff_status pff_mesh_set_operator(pff_mesh *m, int32_t form) {
   // the step graphs and the CG timings belong to the previous form
   free_graph(m->solve_g);
   free_graph(m->step_g);
+  free_graph(m->host_g);
   free_graph(m->mech_g);
   m->tuned[KP_RHS] = m->tuned[KP_MATVEC] = false;
   m->pers_tuned = false;

@@ -153,6 +153,20 @@ def test_resident_without_fan_order_runs_unstaged(pff):
     assert i_re["iters"] == i_fu["iters"] and np.array_equal(d_re, d_fu)
 
 
+def test_resident_beyond_shared_memory_runs_unstaged(pff):
+    """A plate whose rows do not fit the SMs' shared memory at 28 B each
+    (1,324,601 nodes) has no resident loop: asking for it runs the
+    global-memory single-reduction loop, with the same result."""
+    p = S.plate(1200, 1100, jitter=0.1, seed=3)
+    mesh = pff.Mesh.from_plate(p, precision="fp32")
+    mesh.set_material(S.material(2 * p["h"]), 0.5)
+    assert mesh.fan_order()
+    H, dprev = _inputs(p, 6)
+    d_re, i_re = _solve(pff, mesh, H, dprev, pff.PFF_CG_RESIDENT)
+    d_fu, i_fu = _solve(pff, mesh, H, dprev, pff.PFF_CG_FUSED)
+    assert i_re["iters"] == i_fu["iters"] > 0 and np.array_equal(d_re, d_fu)
+
+
 def test_bounded_barrier_wait_reports_timeout(pff):
     """A barrier that awaits one CTA more than the grid gives up after its
     wait limit: the call returns PFF_ERR_TIMEOUT, the context stays usable

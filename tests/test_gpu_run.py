@@ -307,3 +307,31 @@ def test_fused_force_rhs_fp64_per_step_parity(orc, pff):
         merge_worst(worst, state_errs(gst, ost))
         assert max(worst.values()) <= 1e-10, (n, worst)
     assert gm.sync_status() == 0
+
+
+@pytest.mark.parametrize("prec,loop", [("fp32", "graph"), ("fp64", "graph"), ("fp32", "host")])
+def test_run_host_matches_device_run(orc, pff, prec, loop):
+    """pff_run_host (the state in pinned host memory, copied in and out every
+    step, the copies back overlapping the damage solve) gives the bits of
+    pff_run on the device state, step by step."""
+    import torch
+    c, om, gm, dt = _setup(pff, orc, prec=prec)
+    opts = pff.options(cg_tol=c["cg_tol"], t_ramp=c["t_ramp"],
+                       loop_mode=pff.PFF_LOOP_HOST if loop == "host" else pff.PFF_LOOP_GRAPH)
+    ref = gm.new_state()
+    work = gm.new_state()
+    host = {k: torch.zeros(v.shape, dtype=v.dtype, pin_memory=True) for k, v in ref.items()}
+    nsteps = 12
+    for n in range(nsteps):
+        gm.run(ref, 1, step0=n, opts=opts)
+        gm.run_host(host, work, 1, step0=n, opts=opts)
+        torch.cuda.synchronize()
+        for k in ("u", "v", "a", "d", "H"):
+            assert torch.equal(host[k], ref[k].cpu()), (n, k)
+    # several steps in one call
+    gm.run(ref, 5, step0=nsteps, opts=opts)
+    gm.run_host(host, work, 5, step0=nsteps, opts=opts)
+    torch.cuda.synchronize()
+    for k in ("u", "v", "a", "d", "H"):
+        assert torch.equal(host[k], ref[k].cpu()), k
+    assert gm.sync_status() == 0
