@@ -315,7 +315,8 @@ pff_status pff_run(pff_mesh *mesh, const pff_state *state, int64_t step0,
  * copies the state in, runs the step of pff_run on dev, and copies it back
  * out; the copies of u, v, a and H back to the host start as soon as the
  * step's mechanics are done, overlapping the damage solve, and d follows
- * the clamp.  The paper has no counterpart: this is the call for callers
+ * the clamp.  With a persistent CG loop the steps run in pipelined chunks
+ * of eight (a step's copies in overlapping the previous step's solve).  The paper has no counterpart: this is the call for callers
  * whose state lives on the host between steps.  damage_every > 1 is
  * PFF_ERR_ARG.  iters_log as pff_run (device).  Asynchronous: host is
  * complete after the stream synchronises. */

@@ -303,6 +303,7 @@ struct pff_mesh {
   int64_t stab_cap = 0;
   GraphCache solve_g, step_g, mech_g;  // mech_g: a step without the damage solve
   GraphCache host_g;                   // a step with its host copies (pff_run_host)
+  GraphCache hostc_g;                  // kHostChunk such steps, pipelined
   int block = 256;
   // launch configuration (kernel id -> grid, dynamic shared memory)
   int32_t NB = 256, nblk = 0, maxE = 0;
@@ -354,6 +355,7 @@ static void mesh_free(pff_mesh *m) {
   free_graph(m->solve_g);
   free_graph(m->step_g);
   free_graph(m->host_g);
+  free_graph(m->hostc_g);
   free_graph(m->mech_g);
   void *ptrs[] = {m->gcs, m->st_cta, m->st_rng, m->st_nrng, m->st_lrec, m->st_slot, m->cgv, m->cgp,
                   m->ptr, m->ent, m->ell, m->rec, m->drec, m->erec, m->ecmp, m->ecf, m->ecfd, m->fno, m->fmap,
@@ -1743,6 +1745,10 @@ __global__ void k_set_i64(int64_t *p, int64_t v) {
   if (threadIdx.x == 0 && blockIdx.x == 0) *p = v;
 }
 
+// pff_run_host: steps per pipelined graph (a step's copies in overlap the
+// previous step's damage solve within a graph, not across graphs).
+constexpr int kHostChunk = 8;
+
 template <typename R>
 static pff_status run_t(pff_mesh *m, const pff_state *st, int64_t step0, int64_t nsteps, double dt,
                         const pff_options &o, int32_t *iters_log, double *energy_log, cudaStream_t s,
@@ -1765,6 +1771,7 @@ static pff_status run_t(pff_mesh *m, const pff_state *st, int64_t step0, int64_t
     m->stab_cap = nsteps + 1;
     free_graph(m->step_g);
     free_graph(m->host_g);
+    free_graph(m->hostc_g);
     free_graph(m->mech_g);
     if (gcache) free_graph(*gcache);
   }
@@ -1843,8 +1850,12 @@ static pff_status run_t(pff_mesh *m, const pff_state *st, int64_t step0, int64_t
   std::memcpy(&b2, &dt, 8);
   key.push_back(b1);
   key.push_back(b2);
-  if (!gc.exec || gc.key != key) {
-    free_graph(gc);
+  // pff_run_host with a persistent CG loop: chunks of kHostChunk steps in
+  // one graph, so that a step's copies in (after the previous step's copies
+  // out of the same fields) overlap the previous step's damage solve
+  const int chunk = host && pers && !tape && nsteps >= kHostChunk ? kHostChunk : 0;
+  auto build = [&](GraphCache &cache, int C) -> pff_status {
+    free_graph(cache);
     cudaGraph_t g;
     CUDA_TRY(cudaGraphCreate(&g, 0));
     if (!pers) {  // an unused handle makes instantiation fail
@@ -1855,40 +1866,61 @@ static pff_status run_t(pff_mesh *m, const pff_state *st, int64_t step0, int64_t
     P.use_cond = pers ? 0 : 1;
     cudaGraphNode_t n_pr, n_f, last;
     pff_status stt = PFF_OK;
-    std::vector<cudaGraphNode_t> dep_pr, dep_f;
-    cudaGraphNode_t cin[5];
-    if (host) {
-      // the state in (the predictor needs u, v, a; the force kernel d and H,
-      // FP32 through the history mirror)
-      for (int k = 0; k < 5 && stt == PFF_OK; ++k)
-        if (cudaGraphAddMemcpyNode1D(&cin[k], g, nullptr, 0, dp[k], hp[k], nb[k], cudaMemcpyHostToDevice) !=
-            cudaSuccess)
-          stt = fail(PFF_ERR_CUDA, "host step: copy-in node");
-      dep_pr = {cin[0], cin[1], cin[2]};
-      dep_f = {cin[3], cin[4]};
-      if (stt == PFF_OK && sizeof(R) == 4) {
-        const double *Hd = st->H;
-        float *Hf = (float *)m->Hf;
-        int ne = (int)m->Ne;
-        void *margs[] = {(void *)&Hd, (void *)&Hf, (void *)&ne};
-        cudaGraphNode_t n_mir;
-        stt = add_generic(g, {cin[4]}, (const void *)k_h_mirror,
-                          std::min<unsigned>(grid_for(m->Ne, 256), stride_cap()), 256, 0, margs, &n_mir);
-        dep_f = {cin[3], n_mir};
+    cudaGraphNode_t cpout[5], plast = nullptr, prhs = nullptr;  // the previous step's (C > 1)
+    for (int q = 0; q < C && stt == PFF_OK; ++q) {
+      std::vector<cudaGraphNode_t> dep_pr, dep_f;
+      if (q > 0) dep_pr = {plast};
+      cudaGraphNode_t cin[5];
+      if (host) {
+        // the state in (the predictor needs u, v, a; the force kernel d and
+        // H, FP32 through the history mirror); in a chunk, each field after
+        // the previous step's copy of it out, and H also after the previous
+        // step's last reader of H (its right-hand side)
+        for (int k = 0; k < 5 && stt == PFF_OK; ++k) {
+          cudaGraphNode_t dk[2] = {q > 0 ? cpout[k] : nullptr, prhs};
+          const size_t ndk = q == 0 ? 0 : (k == 4 ? 2 : 1);
+          if (cudaGraphAddMemcpyNode1D(&cin[k], g, dk, ndk, dp[k], hp[k], nb[k], cudaMemcpyHostToDevice) !=
+              cudaSuccess)
+            stt = fail(PFF_ERR_CUDA, "host step: copy-in node");
+        }
+        dep_pr.insert(dep_pr.end(), {cin[0], cin[1], cin[2]});
+        dep_f = {cin[3], cin[4]};
+        if (stt == PFF_OK && sizeof(R) == 4) {
+          const double *Hd = st->H;
+          float *Hf = (float *)m->Hf;
+          int ne = (int)m->Ne;
+          void *margs[] = {(void *)&Hd, (void *)&Hf, (void *)&ne};
+          cudaGraphNode_t n_mir;
+          std::vector<cudaGraphNode_t> dm = {cin[4]};
+          if (q > 0) dm.push_back(plast);
+          stt = add_generic(g, dm, (const void *)k_h_mirror,
+                            std::min<unsigned>(grid_for(m->Ne, 256), stride_cap()), 256, 0, margs, &n_mir);
+          dep_f = {cin[3], n_mir};
+        }
       }
-    }
-    if (stt == PFF_OK) stt = add_kernel<R>(m, g, dep_pr, KP_PREDICT, P, &n_pr);
-    dep_f.push_back(n_pr);
-    if (stt == PFF_OK) stt = add_kernel<R>(m, g, dep_f, fused ? KP_FRHS : KP_FORCE, P, &n_f);
-    if (stt == PFF_OK) stt = append_solve<R>(m, g, n_f, P, plan, &last, fused);
-    if (stt == PFF_OK && host) {
-      // the state out: u, v, a and H are final after the force kernel, so
-      // their copies overlap the damage solve; d follows the clamp
-      cudaGraphNode_t n_out;
-      for (int k = 0; k < 5 && stt == PFF_OK; ++k)
-        if (cudaGraphAddMemcpyNode1D(&n_out, g, k == 3 ? &last : &n_f, 1, hp[k], dp[k], nb[k],
-                                     cudaMemcpyDeviceToHost) != cudaSuccess)
-          stt = fail(PFF_ERR_CUDA, "host step: copy-out node");
+      if (stt == PFF_OK) stt = add_kernel<R>(m, g, dep_pr, KP_PREDICT, P, &n_pr);
+      dep_f.push_back(n_pr);
+      if (stt == PFF_OK) stt = add_kernel<R>(m, g, dep_f, fused ? KP_FRHS : KP_FORCE, P, &n_f);
+      if (stt == PFF_OK) stt = append_solve<R>(m, g, n_f, P, plan, &last, fused);
+      if (stt == PFF_OK && host) {
+        // the state out: u, v, a and H are final after the force kernel, so
+        // their copies overlap the damage solve; d follows the clamp.  One
+        // after another (u, v, a, H, d), so that each field is back early
+        // and, in a chunk, its copy in for the next step can start while
+        // the later fields are still coming out.
+        const int order[5] = {0, 1, 2, 4, 3};
+        cudaGraphNode_t prev = n_f;
+        for (int j = 0; j < 5 && stt == PFF_OK; ++j) {
+          const int k = order[j];
+          cudaGraphNode_t dk[2] = {prev, last};
+          if (cudaGraphAddMemcpyNode1D(&cpout[k], g, dk, k == 3 ? 2 : 1, hp[k], dp[k], nb[k],
+                                       cudaMemcpyDeviceToHost) != cudaSuccess)
+            stt = fail(PFF_ERR_CUDA, "host step: copy-out node");
+          prev = cpout[k];
+        }
+      }
+      plast = last;
+      prhs = fused ? n_f : last;
     }
     if (stt == PFF_OK && tape) {
       cudaKernelNodeParams kp;
@@ -1906,14 +1938,17 @@ static pff_status run_t(pff_mesh *m, const pff_state *st, int64_t step0, int64_t
       cudaGraphDestroy(g);
       return stt;
     }
-    cudaError_t e = cudaGraphInstantiate(&gc.exec, g, 0);
+    cudaError_t e = cudaGraphInstantiate(&cache.exec, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
-      gc.exec = nullptr;
+      cache.exec = nullptr;
       return fail(PFF_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
     }
-    gc.key = key;
-  }
+    cache.key = key;
+    return PFF_OK;
+  };
+  if (!gc.exec || gc.key != key) PFF_TRY(build(gc, 1));
+  if (chunk && (!m->hostc_g.exec || m->hostc_g.key != key)) PFF_TRY(build(m->hostc_g, chunk));
   if (n_sub > 1 && (!m->mech_g.exec || m->mech_g.key != key)) {
     // the step without the damage solve: predictor, force, step bookkeeping
     free_graph(m->mech_g);
@@ -1940,7 +1975,9 @@ static pff_status run_t(pff_mesh *m, const pff_state *st, int64_t step0, int64_t
     }
     m->mech_g.key = key;
   }
-  for (int64_t n = 0; n < nsteps; ++n) {
+  int64_t n0 = 0;
+  for (; chunk && n0 + chunk <= nsteps; n0 += chunk) CUDA_TRY(cudaGraphLaunch(m->hostc_g.exec, s));
+  for (int64_t n = n0; n < nsteps; ++n) {
     CUDA_TRY(cudaGraphLaunch(solves(n) ? gc.exec : m->mech_g.exec, s));
     if (energy_log && o.energy_every > 0 && (n + 1) % o.energy_every == 0) {
       Params<R> E = P;
@@ -2598,6 +2635,7 @@ pff_status pff_mesh_set_material(pff_mesh *m, const pff_material *mat, double cf
   free_graph(m->solve_g);
   free_graph(m->step_g);
   free_graph(m->host_g);
+  free_graph(m->hostc_g);
   m->has_mat = true;
   if (!m->gc_field.empty()) PFF_TRY(upload_gc_field(m));  // relative to the new Gc
   const double cp = std::sqrt((m->lam + 2.0 * m->mu) / mat->rho);
@@ -3142,6 +3180,7 @@ static pff_status recompute_mech_t(pff_mesh *m, pff_ckpt *c, const pff_state *st
     m->stab_cap = nsteps + 1;
     free_graph(m->step_g);
     free_graph(m->host_g);
+    free_graph(m->hostc_g);
     free_graph(m->mech_g);
   }
   {
@@ -3450,6 +3489,7 @@ pff_status pff_mesh_set_gc_field(pff_mesh *m, const double *gc) {
   free_graph(m->solve_g);
   free_graph(m->step_g);
   free_graph(m->host_g);
+  free_graph(m->hostc_g);
   free_graph(m->mech_g);
   return PFF_OK;
 }
@@ -3466,6 +3506,7 @@ pff_status pff_mesh_set_operator(pff_mesh *m, int32_t form) {
   free_graph(m->solve_g);
   free_graph(m->step_g);
   free_graph(m->host_g);
+  free_graph(m->hostc_g);
   free_graph(m->mech_g);
   m->tuned[KP_RHS] = m->tuned[KP_MATVEC] = false;
   m->pers_tuned = false;

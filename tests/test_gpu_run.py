@@ -328,10 +328,14 @@ def test_run_host_matches_device_run(orc, pff, prec, loop):
         torch.cuda.synchronize()
         for k in ("u", "v", "a", "d", "H"):
             assert torch.equal(host[k], ref[k].cpu()), (n, k)
-    # several steps in one call
-    gm.run(ref, 5, step0=nsteps, opts=opts)
-    gm.run_host(host, work, 5, step0=nsteps, opts=opts)
-    torch.cuda.synchronize()
-    for k in ("u", "v", "a", "d", "H"):
-        assert torch.equal(host[k], ref[k].cpu()), k
+    # several steps in one call: 5 (one graph per step) and 21 (two
+    # pipelined chunks of 8 steps in one graph each, then single steps)
+    n0 = nsteps
+    for k_steps in (5, 21):
+        gm.run(ref, k_steps, step0=n0, opts=opts)
+        gm.run_host(host, work, k_steps, step0=n0, opts=opts)
+        torch.cuda.synchronize()
+        for k in ("u", "v", "a", "d", "H"):
+            assert torch.equal(host[k], ref[k].cpu()), (k_steps, k)
+        n0 += k_steps
     assert gm.sync_status() == 0
