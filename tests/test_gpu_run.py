@@ -309,13 +309,15 @@ def test_fused_force_rhs_fp64_per_step_parity(orc, pff):
     assert gm.sync_status() == 0
 
 
-@pytest.mark.parametrize("prec,loop", [("fp32", "graph"), ("fp64", "graph"), ("fp32", "host")])
-def test_run_host_matches_device_run(orc, pff, prec, loop):
+@pytest.mark.parametrize("prec,loop,model", [("fp32", "graph", "AT2"), ("fp64", "graph", "AT2"),
+                                              ("fp32", "host", "AT2"), ("fp32", "graph", "AT1")])
+def test_run_host_matches_device_run(orc, pff, prec, loop, model):
     """pff_run_host (the state in pinned host memory, copied in and out every
     step, the copies back overlapping the damage solve) gives the bits of
-    pff_run on the device state, step by step."""
+    pff_run on the device state, step by step (AT1: its kernel-per-phase
+    loop, one graph per step)."""
     import torch
-    c, om, gm, dt = _setup(pff, orc, prec=prec)
+    c, om, gm, dt = _setup(pff, orc, prec=prec, model=model, split="amor" if model == "AT1" else "spectral")
     opts = pff.options(cg_tol=c["cg_tol"], t_ramp=c["t_ramp"],
                        loop_mode=pff.PFF_LOOP_HOST if loop == "host" else pff.PFF_LOOP_GRAPH)
     ref = gm.new_state()
