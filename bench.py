@@ -999,10 +999,11 @@ def run_ours(args):
         scaling="weak", vs_baseline=None, dtype="f32" if args.prec == "fp32" else "f64",
         data="synthetic",
         config=dict(workload=args.config, nodes=N, elements=Ne, split=args.split, model=args.model,
-                    precision="FP32 kernels, FP64 reductions/history" if args.prec == "fp32" else "FP64",
+                    precision=("FP32 kernels and vectors, double-word FP32 dot products and CG scalars, FP64 history"
+                               if args.prec == "fp32" else "FP64"),
                     cg_tol=c["cg_tol"], cg_tol_fp32_floor=2.0 ** -22 if args.prec == "fp32" else None,
                     dt=dt, parallelism=f"replicas x{ws}", loop=args.loop,
-                    l2=("no flush between steps: a step streams about 0.4 GB of element and node data "
+                    l2=("no flush between steps: a step streams about 0.3 GB of element and node data "
                         "through HBM (inputs larger than the 126 MB L2); the damage solve's ~100 MB "
                         "working set stays L2-resident within a step"),
                     operator=args.operator),
