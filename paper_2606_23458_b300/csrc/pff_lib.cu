@@ -2298,7 +2298,9 @@ static pff_status qs_run_t(pff_mesh *m, const pff_state *st, const uint8_t *bc_h
   const unsigned Gf = grid_for(m->Ne, kThreads);  // element pass: one element per thread, no reduction
   // the tangent CG as one cooperative launch per Newton step: a full wave
   // of co-resident CTAs (0: not available, the kernel-per-phase loop runs)
-  unsigned Gp = 0;
+  unsigned Gp = 0, Gres = 0;  // Gres: the resident form's grid (0: not used)
+  int Rres = 0;
+  size_t smres = 0;
   {
     int dev = 0, coop = 0, nsm = 0, occ = 0;
     CUDA_TRY(cudaGetDevice(&dev));
@@ -2310,6 +2312,32 @@ static pff_status qs_run_t(pff_mesh *m, const pff_state *st, const uint8_t *bc_h
     const int64_t work =
         std::max<int64_t>(1, ((rows ? N : std::max(N, m->Ne)) + kQsPersThreads - 1) / kQsPersThreads);
     if (coop && occ > 0) Gp = (unsigned)std::min<int64_t>(work, (int64_t)nsm * occ);
+    // the resident form on fan-order rows: one CTA per SM, each owning a
+    // contiguous range of rows whose vectors fit its shared memory
+    if constexpr (sizeof(K) == 4) {
+      if (Gp && rows && I.fno && !I.nbk) {
+        int optin = 0;
+        CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        cudaFuncAttributes fa;
+        CUDA_TRY(cudaFuncGetAttributes(&fa, (const void *)k_qs_cg_res));
+        const int dyn_max = optin - (int)fa.sharedSizeBytes;
+        const int64_t ctas = std::min<int64_t>((int64_t)nsm, (N + kQsResThreads - 1) / kQsResThreads);
+        const int64_t rws = ((N + ctas - 1) / ctas + 3) / 4 * 4;
+        const size_t sm = (size_t)kQsResWords * sizeof(uint32_t) * (size_t)rws;
+        if (dyn_max > 0 && sm <= (size_t)dyn_max) {
+          CUDA_TRY(cudaFuncSetAttribute((const void *)k_qs_cg_res, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        dyn_max));
+          int ro = 0;
+          CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ro, (const void *)k_qs_cg_res, kQsResThreads, sm));
+          const int64_t grid = (N + rws - 1) / rws;
+          if ((int64_t)ro * nsm >= grid) {
+            Gres = (unsigned)grid;
+            Rres = (int)rws;
+            smres = sm;
+          }
+        }
+      }
+    }
   }
   QsScalars hs;
   auto read = [&]() -> pff_status {
@@ -2345,7 +2373,13 @@ static pff_status qs_run_t(pff_mesh *m, const pff_state *st, const uint8_t *bc_h
         int ne = (int)m->Ne;
         cudaError_t le;
         if constexpr (sizeof(K) == 4) {
-          if (rows) {
+          if (rows && Gres) {
+            k_qs_entry_build<<<Gn, kThreads, 0, s>>>(I);
+            int H = (int)m->span;
+            void *args[] = {(void *)&I, (void *)&bsc, (void *)&Rres, (void *)&H};
+            le = cudaLaunchCooperativeKernel((const void *)k_qs_cg_res, dim3(Gres), dim3(kQsResThreads), args, smres,
+                                             s);
+          } else if (rows) {
             k_qs_entry_build<<<Gn, kThreads, 0, s>>>(I);
             void *args[] = {(void *)&I, (void *)&bsc};
             le = cudaLaunchCooperativeKernel((const void *)k_qs_cg_rows<kQsRowGathers>, dim3(Gp),

@@ -829,6 +829,193 @@ __global__ void __launch_bounds__(kQsPersThreads, 2) k_qs_cg_rows(QkParams<float
   }
 }
 
+// ------------------------------------------- resident tangent CG (fan rows)
+//
+// k_qs_cg_rows on fan-order rows with CTA b owning the rows [b R, (b+1) R)
+// for the whole solve (R rows, a multiple of 4): per row x, r, (p, z), q,
+// the Jacobi diagonal, the fan words and the fan length with the row's
+// boundary flags stay in shared memory (kQsResWords words a row), so a
+// pass reads from global memory only the rows' pair blocks and the (p, z)
+// of neighbours another CTA owns, and the update pass works in shared
+// memory alone; a row writes its (p, z) to global memory only if it lies
+// within H (the mesh's element span, which bounds every neighbour offset)
+// of either end of the range, where another CTA may read it.  Per row the
+// arithmetic of k_qs_cg_rows' fan branch and update; the dot products'
+// partial sums are grouped by CTA range.  x goes back to global memory at
+// the end.  Layout (words): x [0, 2R), r [2R, 4R), (p, z) [4R, 8R), q
+// [8R, 10R), diagonal [10R, 12R), fan words [12R, 15R), fan length | bc
+// << 8 [15R, 16R).
+constexpr int kQsResThreads = 1024;
+constexpr int kQsResWords = 16;
+
+__device__ __forceinline__ float2 qs_pnew_v(const float4 v, float beta) {
+  return make_float2(fmaf(beta, v.x, v.y), fmaf(beta, v.z, v.w));
+}
+
+// Row l's q = K_T p_new (fan branch of k_qs_cg_rows) and its p_new . q.
+__device__ __forceinline__ void qs_res_row(const QkParams<float> &I, int row0, int nr, int R, uint32_t *rs,
+                                           int l, float beta, DF &v1) {
+  typedef Acc<float> AC;
+  const float4 *pzs = reinterpret_cast<const float4 *>(rs + 4 * R);
+  float2 *qsm = reinterpret_cast<float2 *>(rs + 8 * R);
+  const int i = row0 + l;
+  const uint32_t mt = rs[15 * R + l];
+  const float2 pc = qs_pnew_v(pzs[l], beta);
+  const uint32_t w[3] = {rs[12 * R + l], rs[13 * R + l], rs[14 * R + l]};
+  const int m = (int)(mt & 0xffu);
+  float4 bb[6], cc[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const bool in = k < I.D;
+    bb[k] = in ? __ldg(&I.kb[(size_t)k * I.N + i]) : make_float4(0.f, 0.f, 0.f, 0.f);
+    cc[k] = in ? __ldg(&I.kc[(size_t)k * I.N + i]) : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  float2 pv[6];
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    const int ln = l + fan_offset(w, j);
+    pv[j] = qs_pnew_v((unsigned)ln < (unsigned)nr ? pzs[ln] : I.pz[row0 + ln], beta);
+  }
+  float qx = 0.f, qy = 0.f;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const float2 pb = pv[k], pcc = (k + 1 == m) ? pv[0] : pv[k < 5 ? k + 1 : 0];
+    const float bx = pb.x - pc.x, by = pb.y - pc.y, cx = pcc.x - pc.x, cy = pcc.y - pc.y;
+    const float fx = fmaf(bb[k].x, bx, fmaf(bb[k].y, by, fmaf(cc[k].x, cx, __fmul_rn(cc[k].y, cy))));
+    const float fy = fmaf(bb[k].z, bx, fmaf(bb[k].w, by, fmaf(cc[k].z, cx, __fmul_rn(cc[k].w, cy))));
+    qx = __fadd_rn(qx, fx);
+    qy = __fadd_rn(qy, fy);
+  }
+  const uint32_t bcf = mt >> 8;
+  if (bcf & kQsFixX) qx = 0.f;
+  if (bcf & (kQsFixY | kQsLoaded)) qy = 0.f;
+  qsm[l] = make_float2(qx, qy);
+  v1 = AC::add(v1, AC::add(AC::prod(pc.x, qx), AC::prod(pc.y, qy)));
+}
+
+// Row l's update (k_qs_cg_rows' second phase) in shared memory; |r|^2 and
+// r.z.
+__device__ __forceinline__ void qs_res_update(const QkParams<float> &I, int row0, int nr, int R, int H,
+                                              uint32_t *rs, int l, float alpha, float beta, DF (&v2)[2]) {
+  typedef Acc<float> AC;
+  float2 *xs = reinterpret_cast<float2 *>(rs);
+  float2 *rsv = reinterpret_cast<float2 *>(rs + 2 * R);
+  float4 *pzs = reinterpret_cast<float4 *>(rs + 4 * R);
+  const float2 *qsm = reinterpret_cast<const float2 *>(rs + 8 * R);
+  const float2 *dgs = reinterpret_cast<const float2 *>(rs + 10 * R);
+  const uint32_t bcf = rs[15 * R + l] >> 8;
+  const float2 pn = qs_pnew_v(pzs[l], beta), q = qsm[l], dg = dgs[l];
+  float2 x = xs[l], r = rsv[l];
+  x.x = fmaf(alpha, pn.x, x.x);
+  x.y = fmaf(alpha, pn.y, x.y);
+  r.x = fmaf(-alpha, q.x, r.x);
+  r.y = fmaf(-alpha, q.y, r.y);
+  if (bcf & kQsFixX) r.x = 0.f;
+  if (bcf & (kQsFixY | kQsLoaded)) r.y = 0.f;
+  xs[l] = x;
+  rsv[l] = r;
+  const float4 pz = make_float4(pn.x, r.x / dg.x, pn.y, r.y / dg.y);
+  pzs[l] = pz;
+  if (l < H || l >= nr - H) I.pz[row0 + l] = pz;  // another CTA's neighbour
+  v2[0] = AC::add(v2[0], AC::add(AC::prod(r.x, r.x), AC::prod(r.y, r.y)));
+  v2[1] = AC::add(v2[1], AC::add(AC::prod(r.x, pz.y), AC::prod(r.y, pz.w)));
+}
+
+__global__ void __launch_bounds__(kQsResThreads, 1) k_qs_cg_res(QkParams<float> I, SolveScalars *B, int R, int H) {
+  typedef Acc<float> AC;
+  __shared__ typename AC::T sh[kQsResThreads / 32][2];
+  __shared__ DF tot[2];
+  __shared__ int ok_sh, flag;
+  __shared__ DF rho, rr, pq, alpha_d, beta_d, thr2;
+  __shared__ int iters, status;
+  extern __shared__ __align__(16) uint32_t qres_smem[];
+  uint32_t *rs = qres_smem;
+  QsScalars *S = I.qs;
+  if (S->done) return;
+  const int row0 = (int)blockIdx.x * R;
+  const int nr = max(0, min(R, I.N - row0));
+  for (int l = threadIdx.x; l < nr; l += blockDim.x) {
+    const int i = row0 + l;
+    reinterpret_cast<float2 *>(rs)[l] = I.x[i];
+    reinterpret_cast<float2 *>(rs + 2 * R)[l] = I.r[i];
+    reinterpret_cast<float4 *>(rs + 4 * R)[l] = I.pz[i];
+    reinterpret_cast<float2 *>(rs + 10 * R)[l] = I.dg[i];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) rs[(12 + k) * R + l] = __ldg(&I.fno[(size_t)k * I.N + i]);
+    rs[15 * R + l] = (__ldg(&I.fmap[i]) >> 24) | ((uint32_t)I.bc[i] << 8);
+  }
+  if (threadIdx.x == 0) {
+    rho = df_from(S->rho);
+    rr = DF{0.f, 0.f};
+    pq = DF{0.f, 0.f};
+    alpha_d = DF{0.f, 0.f};
+    beta_d = DF{0.f, 0.f};
+    thr2 = df_from(I.tol * I.tol * S->rr0);
+    iters = 0;
+    status = 0;
+  }
+  __syncthreads();
+  const unsigned int nb = gridDim.x;
+  const int T = (int)blockDim.x, t = (int)threadIdx.x;
+  const int llast = t < nr ? t + (nr - 1 - t) / T * T : t - T;
+  unsigned int nbar = 0;
+  bool done = false;
+  for (;;) {
+    const float beta = beta_d.hi;
+    const bool rev = (iters & 1) != 0;  // rows last first on odd iterations
+    const int lstep = rev ? -T : T;
+    typename AC::T v1[1] = {AC::zero()};
+    for (int l = rev ? llast : t; rev ? l >= t : l < nr; l += lstep) qs_res_row(I, row0, nr, R, rs, l, beta, v1[0]);
+    ++nbar;
+    if (!grid_sum<float, 1>(v1, I.part + (nbar & 1u) * 2u * nb, B, nbar * nb, tot, (typename AC::T(*)[1])sh,
+                            &ok_sh))
+      break;
+    if (threadIdx.x == 0) {
+      pq = tot[0];
+      alpha_d = pq.hi != 0.f ? df_div(rho, pq) : DF{0.f, 0.f};
+    }
+    __syncthreads();
+    const float alpha = alpha_d.hi;
+    typename AC::T v2[2] = {AC::zero(), AC::zero()};
+    for (int l = rev ? llast : t; rev ? l >= t : l < nr; l += lstep)
+      qs_res_update(I, row0, nr, R, H, rs, l, alpha, beta, v2);
+    ++nbar;
+    if (!grid_sum<float, 2>(v2, I.part + (nbar & 1u) * 2u * nb, B, nbar * nb, tot, sh, &ok_sh)) break;
+    if (threadIdx.x == 0) {
+      iters += 1;
+      rr = tot[0];
+      flag = 0;
+      if (!df_finite(tot[0])) {
+        status = kStNonfinite;
+        flag = 1;
+      } else if (pq.hi == 0.f || df_le(tot[0], thr2)) {
+        flag = 1;
+      } else if (iters >= I.max_it) {
+        status = kStNotConverged;
+        flag = 1;
+      }
+      beta_d = rho.hi != 0.f ? df_div(tot[1], rho) : DF{0.f, 0.f};
+      rho = tot[1];
+    }
+    __syncthreads();
+    if (flag) {
+      done = true;
+      break;
+    }
+  }
+  for (int l = threadIdx.x; l < nr; l += blockDim.x) I.x[row0 + l] = reinterpret_cast<const float2 *>(rs)[l];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    S->iters = iters;
+    S->rr = df_to(rr);
+    S->pq = df_to(pq);
+    S->rho = df_to(rho);
+    S->alpha = df_to(alpha_d);
+    S->beta = df_to(beta_d);
+    S->status = done ? status : kStTimeout;
+    S->done = 1;
+  }
+}
+
 // u += x on the free dofs.
 template <typename R, typename K>
 __global__ void __launch_bounds__(256) k_qs_apply(QsParams<R, K> Q) {
