@@ -134,6 +134,7 @@ template <typename R> struct Params {
   float4 *cgv0, *cgv1;
   float *cgp;
   int32_t res_rows;  // resident single-reduction CG: rows per CTA
+  int32_t res_halo;  // its FULL form: the mesh's element span (bounds every neighbour offset)
   // material (lam: the plane model's first Lame parameter; K: 3-D bulk
   // modulus; cz = nu / (1 - nu) under plane stress, 0 under plane strain)
   R lam, mu, K, eta, cz;
@@ -2930,7 +2931,8 @@ __global__ void __launch_bounds__(fused_threads(U, ST), fused_minb(U, ST)) k_cg_
 // rows' coefficient pairs and their (r, w, s, 1/diag) records (both
 // buffers) live in shared memory as well, kResWordsFull words a row; a
 // pass then reads global memory only for neighbours owned by another CTA,
-// and writes every new record to global memory too (for those CTAs).
+// and writes a new record to global memory only for the rows within the
+// mesh's element span (P.res_halo) of either end of its range.
 // Shared-memory layout (words, R a multiple of 4): [0, 7R) the base words
 // (x, p, diagonal, fan words 0..2, fan length | fixed << 8, each R long);
 // FULL adds [7R, 19R) the coefficient pairs of fan positions 0..5 (R
@@ -2997,9 +2999,12 @@ __device__ __forceinline__ void resident_rows_full(const Params<float> &P, float
     const int j = row0 + l;
     const float4 v = rin[l];
     const uint32_t mt = meta[l];
+    // only rows within the span of either end of the range are read by
+    // another CTA, from global memory
+    const bool edge = l < P.res_halo || l >= nr - P.res_halo;
     if (mt & 0x100u) {  // eliminated row: everything stays zero
       rout[l] = make_float4(0.f, 0.f, 0.f, 0.f);
-      vout[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (edge) vout[j] = make_float4(0.f, 0.f, 0.f, 0.f);
       continue;
     }
     const float p = fmaf(be, ps[l], v.w * v.x);
@@ -3020,7 +3025,7 @@ __device__ __forceinline__ void resident_rows_full(const Params<float> &P, float
     const float wq = fan_sum(ds[l] * un, cf, nv, (int)(mt & 0xffu));
     const float4 rec = make_float4(rn, wq, sn, v.w);
     rout[l] = rec;
-    vout[j] = rec;
+    if (edge) vout[j] = rec;
     const float sr = P.rscale * rn;
     acc[0] = AC::add(acc[0], AC::prod(sr, un));             // gamma
     acc[1] = AC::add(acc[1], AC::prod(P.rscale * wq, un));  // delta

@@ -582,6 +582,7 @@ static inline size_t plan_smem(const pff_mesh *m, const CgPlan &c) {
 template <typename R>
 static pff_status launch_pers(const pff_mesh *m, const CgPlan &c, Params<R> &P, cudaStream_t s) {
   P.res_rows = c.res() ? m->rrows[c.U] : 0;
+  P.res_halo = c.res() && c.full ? (int32_t)m->span : 0;
   void *args[] = {(void *)&P};
   CUDA_TRY(cudaLaunchCooperativeKernel(plan_fun<R>(c), dim3(c.grid), dim3(plan_threads(c)), args,
                                        plan_smem(m, c), s));
@@ -594,6 +595,7 @@ static pff_status add_pers(const pff_mesh *m, const CgPlan &c, cudaGraph_t g,
   cudaKernelNodeParams kp;
   std::memset(&kp, 0, sizeof(kp));
   P.res_rows = c.res() ? m->rrows[c.U] : 0;
+  P.res_halo = c.res() && c.full ? (int32_t)m->span : 0;
   void *args[] = {(void *)&P};
   kp.func = const_cast<void *>(plan_fun<R>(c));
   kp.gridDim = dim3(c.grid);
