@@ -469,6 +469,14 @@ pff_status pff_mesh_schedule(const pff_mesh *mesh, int32_t *variant, float *tune
  * if not timed or not available).  Host outputs; each pointer nullable. */
 pff_status pff_mesh_cg_choice(const pff_mesh *mesh, int32_t *cg_kernel, int32_t *gathers, float *ms);
 
+/* Which form of the resident loop (PFF_CG_RESIDENT) each of its CTA shapes
+ * U = 1..4 runs on this mesh: forms[U - 1] = -1 unavailable (no fan order,
+ * FP64, or the rows do not fit shared memory), 0 partial (x, p, the
+ * diagonal and the fan words resident), 1 full (the coefficients and both
+ * CG record buffers resident as well).  Fixed at mesh creation and by
+ * pff_mesh_set_operator.  forms is host, 4 entries. */
+pff_status pff_mesh_resident_forms(const pff_mesh *mesh, int32_t *forms);
+
 /* The damage solve of pff_damage_solve, for callers that must not allocate
  * device memory during the call.  The paper has no counterpart of this entry
  * point.  Who needs it: cudaFree synchronises the whole device and the

@@ -106,6 +106,7 @@ _sig = {
                             C.c_int32, _P, _P],
     "pff_mesh_schedule": [_P, _P, _P],
     "pff_mesh_cg_choice": [_P, _P, _P, _P],
+    "pff_mesh_resident_forms": [_P, _P],
     "pff_subcycling_limit": [C.POINTER(pff_material), C.POINTER(C.c_double), C.POINTER(C.c_int32)],
     "pff_ckpt_create": [_P, C.c_int64, C.c_int32, C.POINTER(C.c_void_p)],
     "pff_ckpt_create_policy": [_P, C.c_int64, C.c_int32, C.c_int32, C.POINTER(C.c_void_p)],
@@ -561,6 +562,15 @@ class Mesh:
         ms = np.zeros(len(CG_FAMILIES), np.float32)
         _check(_lib.pff_mesh_cg_choice(self._h, C.byref(k), C.byref(u), _hp(ms)))
         return CG_KINDS[k.value], u.value, {n: float(x) for n, x in zip(CG_FAMILIES, ms)}
+
+    RESIDENT_FORMS = {-1: None, 0: "partial", 1: "full"}
+
+    def resident_forms(self):
+        """Form of the resident CG loop per CTA shape U = 1..4: None
+        (unavailable), "partial" or "full"."""
+        f = np.zeros(4, np.int32)
+        _check(_lib.pff_mesh_resident_forms(self._h, _hp(f)))
+        return [self.RESIDENT_FORMS[int(v)] for v in f]
 
     KERNELS = ("predict", "force", "rhs", "matvec", "update", "finish", "energies")
 

@@ -2815,6 +2815,13 @@ pff_status pff_mesh_schedule(const pff_mesh *m, int32_t *variant, float *tune_ms
   return PFF_OK;
 }
 
+pff_status pff_mesh_resident_forms(const pff_mesh *m, int32_t *forms) {
+  if (!m || !forms) return fail(PFF_ERR_ARG, "null argument");
+  for (int U = 1; U <= 4; ++U)
+    forms[U - 1] = fam_grid(m, kFamResident, U, m->prec != PFF_FP64) ? (m->rfull[U] ? 1 : 0) : -1;
+  return PFF_OK;
+}
+
 pff_status pff_mesh_cg_choice(const pff_mesh *m, int32_t *cg_kernel, int32_t *gathers, float *ms) {
   if (!m) return fail(PFF_ERR_ARG, "null mesh");
   static const int32_t kinds[kFamCount] = {PFF_CG_PHASES, PFF_CG_PERSISTENT, PFF_CG_STAGED, PFF_CG_FUSED,

@@ -167,6 +167,57 @@ def test_resident_beyond_shared_memory_runs_unstaged(pff):
     assert i_re["iters"] == i_fu["iters"] > 0 and np.array_equal(d_re, d_fu)
 
 
+def _shuffled(p, block, seed):
+    """The plate with its node ids permuted within consecutive blocks of
+    `block` ids: the same mesh, fan offsets still within 16 bits, but
+    thousands of distinct fan-word triples."""
+    rng = np.random.default_rng(seed)
+    N = p["xy"].shape[0]
+    new = np.arange(N)
+    for b0 in range(0, N, block):
+        new[b0:b0 + block] = b0 + rng.permutation(min(block, N - b0))
+    q = dict(p)
+    q["xy"] = np.empty_like(p["xy"])
+    q["xy"][new] = p["xy"]
+    q["notch"] = np.empty_like(p["notch"])
+    q["notch"][new] = p["notch"]
+    q["tri"] = new[p["tri"]].astype(np.int32)
+    q["tedges"] = new[p["tedges"]].astype(np.int32)
+    return q, new
+
+
+def test_resident_forms_follow_the_mesh(pff):
+    """The resident loop keeps as much of each CTA's rows in shared memory
+    as fits: everything on 36,421 nodes (full form), x, p, the diagonal and
+    the fan words on 359,601 nodes (partial), with the same result when the
+    node ids are shuffled within blocks of 64 (other fan words on every row,
+    other CTA ranges).  Each against the kernel-per-phase loop."""
+    p = S.plate(640, 560, jitter=0.1, seed=2)
+    ps, new = _shuffled(p, 64, 7)
+    H, dprev = _inputs(p, 3)
+    dprev_s = np.empty_like(dprev)
+    dprev_s[new] = dprev
+    small = S.plate(300, 120, jitter=0.1, seed=2)
+    cases = [(small, "full", _inputs(small, 3)), (p, "partial", (H, dprev)), (ps, "shuffled", (H, dprev_s))]
+    out = {}
+    for q, form, (H, dprev) in cases:
+        mesh = pff.Mesh.from_plate(q, precision="fp32")
+        mesh.set_material(S.material(2 * q["h"]), 0.5)
+        assert mesh.fan_order()
+        want = "partial" if form == "shuffled" else form
+        assert mesh.resident_forms() == [want] * 4, (form, mesh.resident_forms())
+        d_ph, i_ph = _solve(pff, mesh, H, dprev, pff.PFF_CG_PHASES)
+        d_re, i_re = _solve(pff, mesh, H, dprev, pff.PFF_CG_RESIDENT)
+        assert abs(i_re["iters"] - i_ph["iters"]) <= 2, form
+        assert np.max(np.abs(d_re - d_ph) / np.maximum(np.abs(d_ph), 1e-3)) <= 1e-4, form
+        assert i_re["relres"] <= 2.0 ** -22 * 1.0001, form
+        out[form] = d_re
+    # the shuffled plate is the same problem (element order kept, node
+    # values permuted): plain node k is shuffled node new[k]
+    dc, dp = out["partial"], out["shuffled"][new]
+    assert np.max(np.abs(dp - dc) / np.maximum(np.abs(dc), 1e-3)) <= 1e-4
+
+
 def test_bounded_barrier_wait_reports_timeout(pff):
     """A barrier that awaits one CTA more than the grid gives up after its
     wait limit: the call returns PFF_ERR_TIMEOUT, the context stays usable
