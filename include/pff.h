@@ -381,8 +381,9 @@ pff_status pff_backward_field(pff_mesh *mesh, pff_ckpt *ckpt, const void *dL_dd,
  * steps) advanced together, one CUDA graph launch per step for all plates,
  * with per-plate CG reductions and convergence (the CG loop of all plates
  * either as kernels per phase, a converged plate's blocks skipping the
- * remaining iterations, or as one cooperative launch with a group of CTAs
- * per plate; see pff_batch_tuning).  Plates share E, nu, rho, eta, the split
+ * remaining iterations, as one cooperative launch with a group of CTAs
+ * per plate, or as a few such launches (waves of plates) with each CTA's
+ * rows resident in shared memory; see pff_batch_tuning).  Plates share E, nu, rho, eta, the split
  * and the AT2 model.  The caller owns the concatenated state of
  * pff_batch_size's N nodes / Ne elements: plate p's nodes start at node0
  * (pff_batch_plate_info; a multiple of 256, padding nodes between plates
@@ -411,14 +412,21 @@ void pff_batch_destroy(pff_batch *batch);
  * the CG loop form (PFF_CG_PHASES: a matvec and an update kernel per
  * iteration for all plates in a device loop; PFF_CG_PERSISTENT: one
  * cooperative launch in which each plate's group of CTAs iterates its own
- * plate to its own stop), that loop's gathers in flight, 1 once the
- * autotuner has run, and the persistent launch's CTAs (0: unavailable).
- * ms[3 x 8]: the autotuner's timings -- force U = 1..4, right-hand side
+ * plate to its own stop; PFF_CG_RESIDENT: the same single-reduction loop
+ * as the one-mesh resident family, on FP32 batches with fan-order rows, in
+ * waves of consecutive plates whose rows fit the SMs' shared memory
+ * together, one cooperative launch per wave, each plate's CTAs owning
+ * contiguous row ranges), that loop's gathers in flight (the resident
+ * loop's CTA shape), 1 once the autotuner has run, and the persistent
+ * launch's CTAs (0: unavailable).
+ * ms[3 x 12]: the autotuner's timings -- force U = 1..4, right-hand side
  * U = 1..4, a right-hand side plus a whole solve for the phases loop with
- * U = 1..4 and the persistent loop with U = 2..4 (0 where not timed).  The
- * autotuner runs at the first pff_batch_run unless pff_options.variant
- * fixes the gathers; pff_options.cg_kernel PFF_CG_PHASES or
- * PFF_CG_PERSISTENT forces the loop form. */
+ * U = 1..4, the persistent loop with U = 2..4 and the resident loop with
+ * U = 1..4 (0 where not timed).  The autotuner runs at the first
+ * pff_batch_run unless pff_options.variant fixes the gathers;
+ * pff_options.cg_kernel PFF_CG_PHASES, PFF_CG_PERSISTENT or
+ * PFF_CG_RESIDENT forces the loop form (the resident loop falls back to
+ * the persistent one where it is unavailable). */
 pff_status pff_batch_tuning(const pff_batch *batch, int32_t *choice, float *ms);
 /* pff_mesh_set_operator for every plate of the batch (the same forms and
  * conditions; PFF_OP_ELEMENT by default); the batch is re-tuned. */

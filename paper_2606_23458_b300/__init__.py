@@ -274,16 +274,17 @@ class Batch:
 
     def tuning(self):
         """The loop configuration (pff_batch_tuning): gathers in flight of the
-        force, right-hand side and CG kernels, the CG loop form ("phases" or
-        "persistent"), whether the autotuner has run, the persistent launch's
-        CTAs, and the autotuner's timings in ms."""
+        force, right-hand side and CG kernels, the CG loop form ("phases",
+        "persistent" or "resident"), whether the autotuner has run, the
+        persistent launch's CTAs, and the autotuner's timings in ms."""
         ch = np.zeros(6, np.int32)
-        ms = np.zeros((3, 8), np.float32)
+        ms = np.zeros((3, 12), np.float32)
         _check(_lib.pff_batch_tuning(self._h, _hp(ch), _hp(ms)))
         return dict(force_U=int(ch[0]), rhs_U=int(ch[1]), cg=CG_KINDS.get(int(ch[2]), str(int(ch[2]))),
                     cg_U=int(ch[3]), tuned=bool(ch[4]), persistent_ctas=int(ch[5]),
                     ms=dict(force=[float(x) for x in ms[0, :4]], rhs=[float(x) for x in ms[1, :4]],
-                            cg_phases=[float(x) for x in ms[2, :4]], cg_persistent=[float(x) for x in ms[2, 4:7]]))
+                            cg_phases=[float(x) for x in ms[2, :4]], cg_persistent=[float(x) for x in ms[2, 4:7]],
+                            cg_resident=[float(x) for x in ms[2, 7:11]]))
 
     def set_operator(self, form):
         """Damage operator form of every plate: "element" (matrix-free, the

@@ -443,6 +443,76 @@ __global__ void __launch_bounds__(pers_threads(U, false), kPersMinBlocks) kb_cg_
   }
 }
 
+// ------------------------------------------------ per-plate resident CG
+//
+// k_cg_resident's single-reduction loop (FP32, fan-order rows, the partial
+// form: x, p, the diagonal and the fan words of a CTA's rows in its shared
+// memory) for many plates at once.  The plates are solved in waves, one
+// cooperative launch each: a wave's plates together fit the SMs' shared
+// memory, and their operator records and CG records (about 80 B a row)
+// stay in L2 across the wave's iterations, where all plates at once would
+// stream them from HBM every iteration.  Within a wave each plate has a
+// group of CTAs, each owning a contiguous range of the plate's rows
+// (ResCta); a group's all-reduces are among its own CTAs (the plate's
+// barrier counter, its slice of the partials at the group's first CTA of
+// the wave), it takes its plate's stop decision and leaves when its plate
+// has converged.  Same arithmetic per row as k_cg_resident; the dot
+// products' partial sums are grouped by CTA range.
+struct ResCta {
+  int32_t plate, rank;  // the plate, and the CTA's rank in the plate's group
+  int32_t row0, nr;     // the CTA's rows [row0, row0 + nr)
+  int32_t g0, ncta;     // the group's first CTA within the wave, and its size
+};
+
+template <int U>
+__global__ void __launch_bounds__(res_threads(U), res_minb(U)) kb_cg_resident(Params<float> P, Batch B,
+                                                                                const ResCta *map) {
+  typedef Acc<float> AC;
+  const ResCta c = map[blockIdx.x];
+  Params<float> Q = P;
+  plate_apply(Q, B, c.plate);
+  SolveScalars *S = Q.sc;
+  __shared__ DF sh[32][3];
+  __shared__ FusedShared z;
+  extern __shared__ __align__(16) uint32_t res_smem[];
+  if (S->done) return;  // set-up found b_eff = 0 or r_0 already small
+  const int R = P.res_rows, row0 = c.row0, nr = c.nr;
+  float *xs = reinterpret_cast<float *>(res_smem);
+  for (int l = threadIdx.x; l < nr; l += blockDim.x) {
+    const int j = row0 + l;
+    xs[l] = Q.x[j];
+    xs[R + l] = 0.f;
+    xs[2 * R + l] = Q.diag[j];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) res_smem[(3 + k) * R + l] = __ldg(&Q.fno[(size_t)k * Q.N + j]);
+    res_smem[6 * R + l] = (__ldg(&Q.fmap[j]) >> 24) | (is_fixed(Q, j) ? 0x100u : 0u);
+    Q.cgv0[j] = make_float4(Q.r[j], 0.f, 0.f, Q.dinv[j]);
+  }
+  if (threadIdx.x == 0) fused_load(z, S, Q.tol);
+  const unsigned int nb = (unsigned)c.ncta;
+  double *part = P.part + 6u * (unsigned)c.g0;
+  unsigned int nbar = 1;
+  DF v3[3] = {AC::zero(), AC::zero(), AC::zero()};
+  bool fine = grid_sum<float, 3>(v3, part + 3u * nb, S, nb, z.tot, sh, &z.ok, NoHook(), c.rank, (int)nb);
+  int pass = 0;  // passes read cgv[pass & 1] and write the other buffer
+  while (fine) {
+    const float4 *vin = (pass & 1) ? Q.cgv1 : Q.cgv0;
+    float4 *vout = (pass & 1) ? Q.cgv0 : Q.cgv1;
+    DF acc[3] = {AC::zero(), AC::zero(), AC::zero()};
+    resident_rows(Q, z.al, z.be, vin, vout, row0, nr, R, res_smem, acc, (pass & 1) != 0);
+    ++nbar;
+    ++pass;
+    if (!grid_sum<float, 3>(acc, part + (nbar & 1u) * 3u * nb, S, nbar * nb, z.tot, sh, &z.ok, NoHook(), c.rank,
+                            (int)nb))
+      break;
+    if (threadIdx.x == 0) fused_scalars(z, Q, pass);
+    __syncthreads();
+    if (z.flag) break;
+  }
+  for (int l = threadIdx.x; l < nr; l += blockDim.x) Q.x[row0 + l] = xs[l];
+  if (c.rank == 0 && threadIdx.x == 0) fused_store(z, S);
+}
+
 // Advances the step counter after all kernels of the step read it.
 __global__ void kb_step_done(int64_t *step_ctr) {
   if (threadIdx.x == 0 && blockIdx.x == 0) *step_ctr += 1;

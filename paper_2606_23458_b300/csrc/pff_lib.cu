@@ -3595,13 +3595,21 @@ struct pff_batch {
   int32_t U = 3;         // gathers in flight of the kernel-per-phase matvec
   // the autotuner's choice (gathers in flight per kernel, CG loop form) and
   // its timings: force U = 1..4, right-hand side U = 1..4, CG loop
-  // candidates (phases U = 1..4, persistent U = 2..4), ms
+  // candidates (phases U = 1..4, persistent U = 2..4, resident U = 1..4), ms
   int32_t Uf = 3, Ur = 3, cgU = 3, cg_mode = PFF_CG_PHASES;
   bool tuned = false;
-  float tune_ms[3][8] = {{0.f}};
+  float tune_ms[3][12] = {{0.f}};
   // per-plate persistent CG: CTA -> (plate, rank), grid (0: unavailable)
   int2 *cta_plate = nullptr;
   unsigned pgrid = 0;
+  // per-plate resident CG, per CTA shape U = 1..4: the CTAs of all waves,
+  // each wave's (first CTA, CTAs) (none: unavailable), the rows bound
+  // (shared-memory stride) and the dynamic shared memory
+  ResCta *rmap[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  double *rpart = nullptr;  // the waves' partial sums (6 per CTA of the largest wave)
+  std::vector<std::pair<int32_t, int32_t>> rwaves[5];
+  int32_t rrows[5] = {0};
+  size_t rsmem[5] = {0};
 };
 
 namespace pff {
@@ -3609,7 +3617,8 @@ namespace pff {
 static void batch_free(pff_batch *b) {
   if (!b) return;
   free_graph(b->g);
-  void *p[] = {b->blk_plate, b->pc, b->stab, b->sc, b->tick, b->gtick, b->nactive, b->cta_plate};
+  void *p[] = {b->blk_plate, b->pc, b->stab, b->sc, b->tick, b->gtick, b->nactive, b->cta_plate,
+               b->rmap[1], b->rmap[2], b->rmap[3], b->rmap[4], b->rpart};
   for (void *q : p)
     if (q) cudaFree(q);
   if (b->m) mesh_free(b->m);
@@ -3694,9 +3703,138 @@ static pff_status batch_groups(pff_batch *b, std::vector<PlateC> &pc) {
   return PFF_OK;
 }
 
+static const void *kb_res_fun(int U) {
+  return U == 1 ? (const void *)kb_cg_resident<1> : U == 2 ? (const void *)kb_cg_resident<2>
+       : U == 3 ? (const void *)kb_cg_resident<3> : (const void *)kb_cg_resident<4>;
+}
+
+// Waves of the per-plate resident CG (FP32 batches with fan-order rows),
+// per CTA shape U: the rows bound Rmax (the largest multiple of 4 with
+// res_minb(U) CTAs of Rmax rows per SM in shared memory) and G = SMs x
+// res_minb(U) CTAs per wave.  Consecutive plates fill a wave while their
+// CTAs (ceil(rows / Rmax) each) fit G; the wave's spare CTAs go one at a
+// time to the plate with the most rows per CTA while that is above the
+// CTA's threads (ties to the lower plate), and a plate's rows are split
+// evenly over its CTAs.  No waves if a plate alone needs more than G CTAs.
+static pff_status batch_res_plan(pff_batch *b, const std::vector<PlateC> &pc) {
+  pff_mesh *m = b->m;
+  int dev = 0, nsm = 0, coop = 0, optin = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  if (!coop || !m->fno || m->prec == PFF_FP64) return PFF_OK;
+  const int np = b->np;
+  std::vector<int64_t> rows(np), n0(np);
+  for (int p = 0; p < np; ++p) {
+    n0[p] = (int64_t)pc[p].blk0 * kThreads;
+    rows[p] = std::min<int64_t>(m->N, (int64_t)(pc[p].blk0 + pc[p].nblk) * kThreads) - n0[p];
+  }
+  if (!m->cgv) {
+    PFF_TRY(dalloc((float4 **)&m->cgv, 2 * (size_t)(m->N + 2)));
+    PFF_TRY(dalloc(&m->cgp, (size_t)(m->N + 2)));
+    CUDA_TRY(cudaMemset(m->cgv, 0, 2 * (size_t)(m->N + 2) * sizeof(float4)));
+    CUDA_TRY(cudaMemset(m->cgp, 0, (size_t)(m->N + 2) * sizeof(float)));
+  }
+  int64_t nparts = 0;  // CTAs the partials buffer holds
+  for (int U = 1; U <= 4; ++U) {
+    const void *f = kb_res_fun(U);
+    cudaFuncAttributes fa;
+    CUDA_TRY(cudaFuncGetAttributes(&fa, f));
+    const int dyn_max = optin - (int)fa.sharedSizeBytes;
+    if (dyn_max < kResWords * 4 * 4) continue;
+    CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max));
+    const int T = res_threads(U), minb = res_minb(U);
+    // the largest multiple of 4 with minb CTAs per SM (occupancy falls with the rows)
+    int64_t lo = 0, hi = (int64_t)dyn_max / (kResWords * 4) / 4;  // in units of 4 rows
+    while (lo < hi) {
+      const int64_t mid = (lo + hi + 1) / 2;
+      int occ = 0;
+      CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f, T, (size_t)mid * 4 * kResWords * 4));
+      if (occ >= minb) lo = mid;
+      else hi = mid - 1;
+    }
+    const int64_t Rmax = 4 * lo, G = (int64_t)nsm * minb;
+    if (Rmax == 0) continue;
+    std::vector<std::vector<int>> waves;
+    std::vector<int> cur;
+    int64_t ccta = 0;
+    bool ok = true;
+    for (int p = 0; p < np; ++p) {
+      const int64_t need = std::max<int64_t>(1, (rows[p] + Rmax - 1) / Rmax);
+      if (need > G) {
+        ok = false;
+        break;
+      }
+      if (ccta + need > G) {
+        waves.push_back(cur);
+        cur.clear();
+        ccta = 0;
+      }
+      cur.push_back(p);
+      ccta += need;
+    }
+    if (!ok) continue;
+    if (!cur.empty()) waves.push_back(cur);
+    std::vector<ResCta> map;
+    std::vector<std::pair<int32_t, int32_t>> wl;
+    int64_t Rb = 4;
+    for (const auto &wv : waves) {
+      std::vector<int64_t> n(wv.size());
+      int64_t used = 0;
+      for (size_t k = 0; k < wv.size(); ++k) {
+        n[k] = std::max<int64_t>(1, (rows[wv[k]] + Rmax - 1) / Rmax);
+        used += n[k];
+      }
+      for (; used < G; ++used) {
+        size_t best = wv.size();
+        for (size_t k = 0; k < wv.size(); ++k)
+          if (n[k] * T < rows[wv[k]] && (best == wv.size() || rows[wv[k]] * n[best] > rows[wv[best]] * n[k]))
+            best = k;
+        if (best == wv.size()) break;
+        n[best] += 1;
+      }
+      const int32_t c0 = (int32_t)map.size();
+      for (size_t k = 0; k < wv.size(); ++k) {
+        const int p = wv[k];
+        const int32_t g0 = (int32_t)map.size() - c0;
+        for (int64_t r = 0; r < n[k]; ++r) {
+          const int64_t a = n0[p] + r * rows[p] / n[k], e = n0[p] + (r + 1) * rows[p] / n[k];
+          ResCta c;
+          c.plate = p;
+          c.rank = (int32_t)r;
+          c.row0 = (int32_t)a;
+          c.nr = (int32_t)(e - a);
+          c.g0 = g0;
+          c.ncta = (int32_t)n[k];
+          map.push_back(c);
+          Rb = std::max(Rb, e - a);
+        }
+      }
+      wl.push_back(std::make_pair(c0, (int32_t)map.size() - c0));
+    }
+    const int64_t R = (Rb + 3) / 4 * 4;  // <= Rmax: every plate has ceil(rows / Rmax) CTAs or more
+    int64_t wmax = 0;
+    for (const auto &w : wl) wmax = std::max<int64_t>(wmax, w.second);
+    if (wmax > nparts) {
+      if (b->rpart) cudaFree(b->rpart);
+      b->rpart = nullptr;
+      PFF_TRY(dalloc(&b->rpart, 6 * (size_t)wmax));
+      CUDA_TRY(cudaMemset(b->rpart, 0, 6 * (size_t)wmax * sizeof(double)));
+      nparts = wmax;
+    }
+    PFF_TRY(dalloc(&b->rmap[U], map.size()));
+    CUDA_TRY(cudaMemcpy(b->rmap[U], map.data(), map.size() * sizeof(ResCta), cudaMemcpyHostToDevice));
+    b->rwaves[U] = wl;
+    b->rrows[U] = (int32_t)R;
+    b->rsmem[U] = (size_t)R * kResWords * 4;
+  }
+  return PFF_OK;
+}
+
 static pff_status add_coop(cudaGraph_t g, const std::vector<cudaGraphNode_t> &deps, const void *fn, unsigned grid,
-                           unsigned block, void **args, cudaGraphNode_t *out) {
-  PFF_TRY(add_generic(g, deps, fn, grid, block, 0, args, out));
+                           unsigned block, void **args, cudaGraphNode_t *out, size_t smem = 0) {
+  PFF_TRY(add_generic(g, deps, fn, grid, block, smem, args, out));
   cudaLaunchAttributeValue av;
   std::memset(&av, 0, sizeof(av));
   av.cooperative = 1;
@@ -3709,16 +3847,24 @@ static pff_status add_coop(cudaGraph_t g, const std::vector<cudaGraphNode_t> &de
 // the per-plate persistent launch), clamp and step counter.  With
 // solve_only: the right-hand side and the CG loop alone (the autotuner's
 // timed unit; it leaves the state untouched).
+// The resident loop with CTA shape U runs on this batch: FP32, the
+// element-wise operator in fan order, and waves planned.
+template <typename R>
+static bool batch_res_ok(const pff_batch *b, int U) {
+  return sizeof(R) == 4 && U >= 1 && U <= 4 && !b->rwaves[U].empty() && b->m->dop == PFF_OP_ELEMENT && b->m->fno;
+}
+
 template <typename R>
 static pff_status batch_graph(pff_batch *b, Params<R> P, Batch &B, int Uf, int Ur, int mode, int cgU,
                               bool solve_only, cudaGraphExec_t *exec) {
   pff_mesh *m = b->m;
   const int64_t nblk = (m->N + kThreads - 1) / kThreads;
   const bool pers = mode == PFF_CG_PERSISTENT && b->pgrid > 0;
+  const bool res = mode == PFF_CG_RESIDENT && batch_res_ok<R>(b, cgU);
   cudaGraph_t g;
   CUDA_TRY(cudaGraphCreate(&g, 0));
   P.use_cond = 0;
-  if (!pers) {
+  if (!pers && !res) {
     if (cudaGraphConditionalHandleCreate(&P.cond_inner, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
       cudaGraphDestroy(g);
       return fail(PFF_ERR_CUDA, "batch graph: conditional handle");
@@ -3740,6 +3886,20 @@ static pff_status batch_graph(pff_batch *b, Params<R> P, Batch &B, int Uf, int U
   if (st == PFF_OK) st = add_generic(g, dep, kb_fun<R>(KP_RHS, Ur), G, kThreads, 0, args, &n_rhs);
   if (st == PFF_OK && pers) {
     st = add_coop(g, {n_rhs}, kb_pers_fun<R>(cgU), b->pgrid, kBatchPersThreads, args, &n_loop);
+  } else if (st == PFF_OK && res) {
+    // one cooperative launch per wave, in order
+    Params<R> Pr = P;
+    Pr.res_rows = b->rrows[cgU];
+    Pr.part = b->rpart;
+    n_loop = n_rhs;
+    for (const auto &w : b->rwaves[cgU]) {
+      const ResCta *mp = b->rmap[cgU] + w.first;
+      void *rargs[] = {(void *)&Pr, (void *)&B, (void *)&mp};
+      const cudaGraphNode_t prev = n_loop;
+      st = add_coop(g, {prev}, kb_res_fun(cgU), (unsigned)w.second, res_threads(cgU), rargs, &n_loop,
+                    b->rsmem[cgU]);
+      if (st != PFF_OK) break;
+    }
   } else if (st == PFF_OK) {
     st = add_while(g, {n_rhs}, P.cond_inner, &body, &n_loop);
     if (st == PFF_OK) st = add_generic(body, {}, kb_fun<R>(KP_MATVEC, cgU), G, kThreads, 0, args, &n_mv);
@@ -3861,10 +4021,11 @@ static pff_status batch_tune(pff_batch *b, Params<R> P, Batch B, cudaStream_t s)
   }
   if (res == PFF_OK) {
     float best = 1e30f;
-    for (int k = 0; k < 7 && res == PFF_OK; ++k) {
-      const int mode = k < 4 ? PFF_CG_PHASES : PFF_CG_PERSISTENT;
-      const int U = k < 4 ? k + 1 : k - 2;
+    for (int k = 0; k < 11 && res == PFF_OK; ++k) {
+      const int mode = k < 4 ? PFF_CG_PHASES : (k < 7 ? PFF_CG_PERSISTENT : PFF_CG_RESIDENT);
+      const int U = k < 4 ? k + 1 : (k < 7 ? k - 2 : k - 6);
       if (mode == PFF_CG_PERSISTENT && b->pgrid == 0) continue;
+      if (mode == PFF_CG_RESIDENT && !batch_res_ok<R>(b, U)) continue;
       cudaGraphExec_t ex = nullptr;
       res = batch_graph<R>(b, P, B, b->Uf, b->Ur, mode, U, true, &ex);
       if (res != PFF_OK) break;
@@ -3959,6 +4120,14 @@ static pff_status batch_run_t(pff_batch *b, const pff_state *st, int64_t step0, 
   int mode = b->cg_mode, cgU = b->cgU;
   if (o.cg_kernel == PFF_CG_PHASES) mode = PFF_CG_PHASES;
   if (o.cg_kernel == PFF_CG_PERSISTENT) mode = PFF_CG_PERSISTENT;
+  if (o.cg_kernel == PFF_CG_RESIDENT) mode = PFF_CG_RESIDENT;
+  if (mode == PFF_CG_RESIDENT && !batch_res_ok<R>(b, cgU)) {  // another CTA shape, else the persistent loop
+    int u = 0;
+    for (int k = 4; k >= 1 && u == 0; --k)
+      if (batch_res_ok<R>(b, k)) u = k;
+    if (u) cgU = u;
+    else mode = PFF_CG_PERSISTENT;
+  }
   if (mode == PFF_CG_PERSISTENT && b->pgrid == 0) mode = PFF_CG_PHASES;
   if (mode == PFF_CG_PERSISTENT) cgU = std::max(cgU, 2);
   std::vector<uint64_t> key = {(uint64_t)nsteps, (uint64_t)iters_log, (uint64_t)b->Uf, (uint64_t)b->Ur,
@@ -4081,6 +4250,7 @@ pff_status pff_batch_create(int32_t nplates, const pff_plate *plates, int32_t pr
     for (int32_t k = 0; k < c.nblk; ++k) bp[c.blk0 + k] = p;
   }
   st = precision == PFF_FP64 ? batch_groups<double>(b, pc) : batch_groups<float>(b, pc);
+  if (st == PFF_OK) st = batch_res_plan(b, pc);
   if (st != PFF_OK) {
     batch_free(b);
     return st;

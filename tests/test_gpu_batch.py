@@ -81,27 +81,32 @@ def test_batch_fp32_vs_oracle(orc, pff):
         assert np.abs(to_np(v["d"]) - ost["d"]).max() <= 1e-3, k
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_batch_persistent_loop_matches_phases(pff, prec):
+@pytest.mark.parametrize("prec,loop", [("fp64", "persistent"), ("fp32", "persistent"), ("fp32", "resident")])
+def test_batch_persistent_loop_matches_phases(pff, prec, loop):
     """The per-plate persistent CG (one cooperative launch, a CTA group per
-    plate iterating to its own stop) against the kernel-per-phase batch
-    loop: the same Jacobi PCG per plate, the dot products' partial sums
-    grouped differently, so iteration counts within one and fields within
-    the rounding of the solve."""
+    plate iterating to its own stop), and the per-plate resident CG (the
+    single-reduction loop with each CTA's rows in shared memory, in waves
+    of plates), against the kernel-per-phase batch loop: the same Jacobi
+    PCG per plate, the dot products' partial sums grouped differently (and
+    for the resident loop the single-reduction recurrences), so iteration
+    counts within one (two) and fields within the rounding of the solve."""
     import torch
     plates = _plates()
     nsteps = 40
     out = {}
-    for kind in (pff.PFF_CG_PHASES, pff.PFF_CG_PERSISTENT):
+    kind = pff.PFF_CG_PERSISTENT if loop == "persistent" else pff.PFF_CG_RESIDENT
+    for k in (pff.PFF_CG_PHASES, kind):
         b = pff.Batch(plates, precision=prec)
         st = b.new_state()
         log = torch.zeros(nsteps, len(plates), dtype=torch.int32, device="cuda")
-        b.run(st, nsteps, opts=pff.options(cg_kernel=kind), iters_log=log)
+        b.run(st, nsteps, opts=pff.options(cg_kernel=k), iters_log=log)
         torch.cuda.synchronize()
         assert b.tuning()["persistent_ctas"] >= len(plates)
-        out[kind] = ({k: to_np(v) for k, v in st.items()}, log.cpu().numpy())
-    (a, la), (c, lc) = out[pff.PFF_CG_PHASES], out[pff.PFF_CG_PERSISTENT]
-    assert np.abs(la - lc).max() <= 1
+        if loop == "resident":  # the autotuner timed the resident loop: it is available
+            assert max(b.tuning()["ms"]["cg_resident"]) > 0
+        out[k] = ({n: to_np(v) for n, v in st.items()}, log.cpu().numpy())
+    (a, la), (c, lc) = out[pff.PFF_CG_PHASES], out[kind]
+    assert np.abs(la - lc).max() <= (1 if loop == "persistent" else 2)
     tol = 1e-9 if prec == "fp64" else 2e-5
     assert rel_l2(c["u"], a["u"]) <= tol
     assert np.abs(c["d"] - a["d"]).max() <= (1e-9 if prec == "fp64" else 1e-4)
@@ -116,12 +121,14 @@ def test_batch_autotuner_report(pff):
     b.run(st, 3)
     torch.cuda.synchronize()
     t = b.tuning()
-    assert t["tuned"] and t["cg"] in ("phases", "persistent")
+    assert t["tuned"] and t["cg"] in ("phases", "persistent", "resident")
     assert 1 <= t["force_U"] <= 4 and 1 <= t["rhs_U"] <= 4 and 1 <= t["cg_U"] <= 4
     assert min(t["ms"]["force"]) > 0 and min(t["ms"]["rhs"]) > 0 and min(t["ms"]["cg_phases"]) > 0
     if t["persistent_ctas"]:
         assert min(t["ms"]["cg_persistent"]) > 0
-    best = min(t["ms"]["cg_phases"] + [x for x in t["ms"]["cg_persistent"] if x > 0])
+    assert max(t["ms"]["cg_resident"]) > 0
+    best = min(t["ms"]["cg_phases"] + [x for x in t["ms"]["cg_persistent"] + t["ms"]["cg_resident"] if x > 0])
     chosen = (t["ms"]["cg_phases"][t["cg_U"] - 1] if t["cg"] == "phases"
-              else t["ms"]["cg_persistent"][t["cg_U"] - 2])
+              else t["ms"]["cg_persistent"][t["cg_U"] - 2] if t["cg"] == "persistent"
+              else t["ms"]["cg_resident"][t["cg_U"] - 1])
     assert chosen == best

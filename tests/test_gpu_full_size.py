@@ -199,9 +199,11 @@ def test_sent_full_size_increment_vs_oracle(orc, pff):
     assert status == 0 and np.abs(d - dor).max() <= 1e-6, np.abs(d - dor).max()
 
 
-@pytest.fixture(scope="module")
-def batch64(pff):
-    """The bench's 64-plate batch (5.24M nodes, FP32) after 6 steps."""
+@pytest.fixture(scope="module", params=["auto", "resident"])
+def batch64(pff, request):
+    """The bench's 64-plate batch (5.24M nodes, FP32) after 6 steps, with
+    the autotuned CG loop and with the per-plate resident loop (in waves of
+    plates that fit the SMs' shared memory together)."""
     import torch
     plates = []
     for dr in S.batch_draws(64, seed=1):
@@ -211,8 +213,10 @@ def batch64(pff):
     b = pff.Batch(plates, precision="fp32")
     st = b.new_state()
     log = torch.zeros(nsteps, b.nplates, dtype=torch.int32, device="cuda")
-    b.run(st, nsteps, iters_log=log)
+    cgk = pff.PFF_CG_RESIDENT if request.param == "resident" else pff.PFF_CG_AUTO
+    b.run(st, nsteps, opts=pff.options(cg_kernel=cgk), iters_log=log)
     torch.cuda.synchronize()
+    assert max(b.tuning()["ms"]["cg_resident"]) > 0  # available on this batch
     sizes = [p["xy"].shape[0] for p, _ in plates]
     picks = sorted({0, int(np.argmin(sizes)), int(np.argmax(sizes))})
     return dict(plates=plates, b=b, st=st, log=log.cpu().numpy(), nsteps=nsteps, picks=picks)
