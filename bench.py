@@ -975,6 +975,7 @@ def run_ours(args):
 
     # per-kernel device times on this data (overwrites the state)
     sched_var, sched_ms = mesh.schedule()
+    frhs_var, frhs_ms = mesh.fused_schedule()
     cg_kind, cg_U, cg_ms = mesh.cg_choice()
     prof = mesh.profile_kernels(st, reps=5, opts=opts)
 
@@ -1021,6 +1022,7 @@ def run_ours(args):
                       per_step=[int(v) for v in iters] if args.steps <= 64 else None),
         kernel_ms=prof,
         schedule=dict(variant=sched_var, tune_ms=sched_ms,
+                      force_rhs=dict(variant=frhs_var, tune_ms=frhs_ms),
                       cg_loop=dict(kind=cg_kind, gathers=cg_U, ms_30_iterations=cg_ms)),
     )
     other = "merged" if args.operator == "element" else "element"

@@ -468,6 +468,16 @@ pff_status pff_profile_kernels(pff_mesh *mesh, const pff_state *state, double dt
  * (3 x 5, 0 where not measured).  Host outputs, each nullable. */
 pff_status pff_mesh_schedule(const pff_mesh *mesh, int32_t *variant, float *tune_ms);
 
+/* The fused internal force and damage right-hand side (Sec. 2.2-2.4: one
+ * node-centric pass computing the force of Eq. vv_a with the history update
+ * and the set-up of the damage solve of Eq. damage_pde_at2/at1): *variant =
+ * the pff_options.variant code in use (1..5: U = 2, 1, 2, 3, 4 entries in
+ * flight; every variant gives the same bits), tune_ms[5] = the autotuner's
+ * time per variant (0 where not measured).  Whether a step uses the fused
+ * kernel at all is ms_out[11] of pff_profile_kernels.  Host outputs, each
+ * nullable. */
+pff_status pff_mesh_fused_schedule(const pff_mesh *mesh, int32_t *variant, float *tune_ms);
+
 /* The AT2 CG loop the autotuner chose on this mesh: *cg_kernel =
  * PFF_CG_PHASES, _PERSISTENT, _STAGED, _FUSED, _FUSED_STAGED or _RESIDENT
  * (PFF_CG_AUTO while not yet timed), the chosen persistent kernel's variant

@@ -105,6 +105,7 @@ _sig = {
     "pff_profile_kernels": [_P, C.POINTER(pff_state), C.c_double, C.POINTER(pff_options),
                             C.c_int32, _P, _P],
     "pff_mesh_schedule": [_P, _P, _P],
+    "pff_mesh_fused_schedule": [_P, _P, _P],
     "pff_mesh_cg_choice": [_P, _P, _P, _P],
     "pff_mesh_resident_forms": [_P, _P],
     "pff_subcycling_limit": [C.POINTER(pff_material), C.POINTER(C.c_double), C.POINTER(C.c_int32)],
@@ -552,6 +553,14 @@ class Mesh:
         names = ("force", "rhs", "matvec")
         return ({n: int(v) for n, v in zip(names, var)},
                 {n: [round(float(x), 4) for x in row] for n, row in zip(names, ms)})
+
+    def fused_schedule(self):
+        """(variant code of the fused force and right-hand side in use,
+        autotuner ms per variant)."""
+        var = C.c_int32()
+        ms = np.zeros(5, np.float32)
+        _check(_lib.pff_mesh_fused_schedule(self._h, C.byref(var), _hp(ms)))
+        return var.value, [round(float(x), 4) for x in ms]
 
     def cg_choice(self):
         """(AT2 CG loop in use: "auto" (not timed yet) / "phases" /

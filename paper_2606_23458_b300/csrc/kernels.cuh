@@ -439,48 +439,54 @@ __device__ __forceinline__ long long f2d_bits(float f) {
 // strain with e_zz = -cz tr (0 in plane strain; plane stress: the
 // out-of-plane strain of Sec. 2.1, whose dependence on the in-plane strain
 // enters the stress).  sigma = g sigma+ + sigma-.
+// Every multiply-add is written out (rfma / rmul / radd): which products
+// the compiler would fuse otherwise depends on the code around the call
+// (how often each product is used there), and the kernels that evaluate an
+// element once per incidence entry and those that evaluate it once per
+// element must round alike.
 template <typename R>
 __device__ __forceinline__ void stress(const Params<R> &P, R exx, R eyy, R exy, R g,
                                        R &sxx, R &syy, R &sxy, R &psip) {
-  const R tr = exx + eyy;
+  const R tr = radd(exx, eyy);
   const R trp = rpos(tr), trm = rneg(tr);
+  // exx^2 + eyy^2 + 2 exy^2
+  const R sq = rfma(rmul(R(2), exy), exy, rfma(exx, exx, rmul(eyy, eyy)));
   if (P.split == kSpectral) {
-    const R half = R(0.5) * (exx - eyy);
-    const R rad = sqrt(half * half + exy * exy);
-    const R e1 = R(0.5) * tr + rad, e2 = R(0.5) * tr - rad;
+    const R half = rmul(R(0.5), exx - eyy);
+    const R rad = sqrt(rfma(half, half, rmul(exy, exy)));
+    const R e1 = rfma(R(0.5), tr, rad), e2 = rfma(R(0.5), tr, -rad);
     const R e1p = rpos(e1), e2p = rpos(e2);
-    const R s = rad > R(0) ? (e1p - e2p) / (R(2) * rad) : R(0);
-    const R m = R(0.5) * (e1p + e2p);
-    const R pxx = m + s * half, pyy = m - s * half, pxy = s * exy;
-    const R tm = P.lam * trm, tp = P.lam * trp, mu2 = R(2) * P.mu;
-    sxx = g * (tp + mu2 * pxx) + tm + mu2 * (exx - pxx);
-    syy = g * (tp + mu2 * pyy) + tm + mu2 * (eyy - pyy);
-    sxy = g * (mu2 * pxy) + mu2 * (exy - pxy);
-    psip = R(0.5) * P.lam * trp * trp + P.mu * (e1p * e1p + e2p * e2p);
+    const R s = rad > R(0) ? (e1p - e2p) / rmul(R(2), rad) : R(0);
+    const R m = rmul(R(0.5), radd(e1p, e2p));
+    const R pxx = rfma(s, half, m), pyy = rfma(-s, half, m), pxy = rmul(s, exy);
+    const R tm = rmul(P.lam, trm), tp = rmul(P.lam, trp), mu2 = rmul(R(2), P.mu);
+    sxx = rfma(mu2, exx - pxx, rfma(g, rfma(mu2, pxx, tp), tm));
+    syy = rfma(mu2, eyy - pyy, rfma(g, rfma(mu2, pyy, tp), tm));
+    sxy = rfma(g, rmul(mu2, pxy), rmul(mu2, exy - pxy));
+    psip = rfma(P.mu, rfma(e1p, e1p, rmul(e2p, e2p)), rmul(rmul(rmul(R(0.5), P.lam), trp), trp));
   } else if (P.split == kAmor && P.cz == R(0)) {
-    const R t3 = tr * (R(1) / R(3)), mu2 = R(2) * P.mu;
-    sxx = g * (P.K * trp + mu2 * (exx - t3)) + P.K * trm;
-    syy = g * (P.K * trp + mu2 * (eyy - t3)) + P.K * trm;
-    sxy = g * (mu2 * exy);
-    psip = R(0.5) * P.K * trp * trp +
-           P.mu * (exx * exx + eyy * eyy + R(2) * exy * exy - tr * t3);
+    const R t3 = rmul(tr, R(1) / R(3)), mu2 = rmul(R(2), P.mu), km = rmul(P.K, trm);
+    sxx = rfma(g, rfma(P.K, trp, rmul(mu2, exx - t3)), km);
+    syy = rfma(g, rfma(P.K, trp, rmul(mu2, eyy - t3)), km);
+    sxy = rmul(g, rmul(mu2, exy));
+    psip = rfma(P.mu, rfma(-tr, t3, sq), rmul(rmul(rmul(R(0.5), P.K), trp), trp));
   } else if (P.split == kAmor) {
     // plane stress: e_zz = -cz tr, tr3 = f tr with f = 1 - cz; the in-plane
     // stresses carry d e_zz / d e_ii = -cz
-    const R f = R(1) - P.cz, ez = -P.cz * tr, tr3 = f * tr;
-    const R t3p = rpos(tr3), t3m = rneg(tr3), mu2 = R(2) * P.mu;
-    const R lin = P.cz * P.cz * tr - f * tr3 * (R(1) / R(3));
-    sxx = g * (P.K * f * t3p + mu2 * (exx + lin)) + P.K * f * t3m;
-    syy = g * (P.K * f * t3p + mu2 * (eyy + lin)) + P.K * f * t3m;
-    sxy = g * (mu2 * exy);
-    psip = R(0.5) * P.K * t3p * t3p +
-           P.mu * (exx * exx + eyy * eyy + R(2) * exy * exy + ez * ez - tr3 * tr3 * (R(1) / R(3)));
+    const R f = R(1) - P.cz, ez = rmul(-P.cz, tr), tr3 = rmul(f, tr);
+    const R t3p = rpos(tr3), t3m = rneg(tr3), mu2 = rmul(R(2), P.mu), kf = rmul(P.K, f);
+    const R lin = rfma(rmul(P.cz, P.cz), tr, -rmul(rmul(f, tr3), R(1) / R(3)));
+    sxx = rfma(g, rfma(kf, t3p, rmul(mu2, radd(exx, lin))), rmul(kf, t3m));
+    syy = rfma(g, rfma(kf, t3p, rmul(mu2, radd(eyy, lin))), rmul(kf, t3m));
+    sxy = rmul(g, rmul(mu2, exy));
+    psip = rfma(P.mu, rfma(-rmul(tr3, tr3), R(1) / R(3), rfma(ez, ez, sq)),
+                rmul(rmul(rmul(R(0.5), P.K), t3p), t3p));
   } else {
-    const R mu2 = R(2) * P.mu;
-    sxx = g * (P.lam * tr + mu2 * exx);
-    syy = g * (P.lam * tr + mu2 * eyy);
-    sxy = g * (mu2 * exy);
-    psip = R(0.5) * P.lam * tr * tr + P.mu * (exx * exx + eyy * eyy + R(2) * exy * exy);
+    const R mu2 = rmul(R(2), P.mu);
+    sxx = rmul(g, rfma(P.lam, tr, rmul(mu2, exx)));
+    syy = rmul(g, rfma(P.lam, tr, rmul(mu2, eyy)));
+    sxy = rmul(g, rmul(mu2, exy));
+    psip = rfma(P.mu, sq, rmul(rmul(rmul(R(0.5), P.lam), tr), tr));
   }
 }
 
@@ -538,16 +544,23 @@ __device__ __forceinline__ void load_elem(const Params<R> &P, int e, int4 &t, R 
   }
 }
 
+// Strain (tensor components) of an element from its three nodes' u.
+template <typename R, typename R2, typename R4>
+__device__ __forceinline__ void elem_strain_u(const R4 &G, const R2 &u0, const R2 &u1, const R2 &u2,
+                                              R &exx, R &eyy, R &exy) {
+  const R ax0 = u0.x - u2.x, ax1 = u1.x - u2.x, ay0 = u0.y - u2.y, ay1 = u1.y - u2.y;
+  exx = rfma(G.x, ax0, rmul(G.z, ax1));
+  eyy = rfma(G.y, ay0, rmul(G.w, ay1));
+  exy = rmul(R(0.5), rfma(G.z, ay1, rfma(G.x, ay0, rfma(G.y, ax0, rmul(G.w, ax1)))));
+}
+
 // Strain (tensor components) of element e from nodal u.
 template <typename R>
 __device__ __forceinline__ void elem_strain(const Params<R> &P, const typename Params<R>::R4 &G, const int4 &t,
                                             R &exx, R &eyy, R &exy) {
   typedef typename Params<R>::R2 R2;
   const R2 u0 = P.u[t.x], u1 = P.u[t.y], u2 = P.u[t.z];
-  const R ax0 = u0.x - u2.x, ax1 = u1.x - u2.x, ay0 = u0.y - u2.y, ay1 = u1.y - u2.y;
-  exx = G.x * ax0 + G.z * ax1;
-  eyy = G.y * ay0 + G.w * ay1;
-  exy = R(0.5) * (G.y * ax0 + G.w * ax1 + G.x * ay0 + G.z * ay1);
+  elem_strain_u<R>(G, u0, u1, u2, exx, eyy, exy);
 }
 
 // Predictor, Eq. (vv_u): u += dt v + dt^2/2 a.  With track_work the
@@ -615,8 +628,8 @@ __device__ __forceinline__ void force_entry(const Params<R> &P, int en, R &fx, R
   load_elem(P, e, t, A, G);
   R exx, eyy, exy;
   elem_strain(P, G, t, exx, eyy, exy);
-  const R db = (P.d[t.x] + P.d[t.y] + P.d[t.z]) * (R(1) / R(3));
-  const R g = (R(1) - db) * (R(1) - db) + P.eta;
+  const R db = rmul(radd(radd(P.d[t.x], P.d[t.y]), P.d[t.z]), R(1) / R(3));
+  const R g = rfma(R(1) - db, R(1) - db, P.eta);
   R sxx, syy, sxy;
   stress(P, exx, eyy, exy, g, sxx, syy, sxy, psip);
   R gx, gy;
@@ -657,11 +670,11 @@ __device__ __forceinline__ void corrector(const Params<R> &P, int i, R fx, R fy,
     fey = fe.y;
   }
   const R mi = P.minv[i];
-  const R anx = mi * (Sf * fex - fx), any = mi * (Sf * fey - fy);
+  const R anx = rmul(mi, rfma(Sf, fex, -fx)), any = rmul(mi, rfma(Sf, fey, -fy));
   R2 v = P.v[i], ao = P.a[i];
-  const R hd = R(0.5) * (R)P.dt;
-  v.x += hd * (ao.x + anx);
-  v.y += hd * (ao.y + any);
+  const R hd = rmul(R(0.5), (R)P.dt);
+  v.x = rfma(hd, radd(ao.x, anx), v.x);
+  v.y = rfma(hd, radd(ao.y, any), v.y);
   P.v[i] = v;
   R2 an;
   an.x = anx;
@@ -689,8 +702,8 @@ __global__ void __launch_bounds__(256) k_force_elem(Params<R> P) {
     load_elem(P, e, t, A, G);
     R exx, eyy, exy;
     elem_strain(P, G, t, exx, eyy, exy);
-    const R db = (P.d[t.x] + P.d[t.y] + P.d[t.z]) * (R(1) / R(3));
-    const R g = (R(1) - db) * (R(1) - db) + P.eta;
+    const R db = rmul(radd(radd(P.d[t.x], P.d[t.y]), P.d[t.z]), R(1) / R(3));
+    const R g = rfma(R(1) - db, R(1) - db, P.eta);
     R sxx, syy, sxy, psip;
     stress(P, exx, eyy, exy, g, sxx, syy, sxy, psip);
     history_update(P, e << 2, psip);
@@ -773,12 +786,12 @@ __global__ void k_h_mirror(const double *H, float *Hf, int n) {
 //   kA grad(phi_a) . grad(x_e) + mA (x_a + x_0 + x_1 + x_2).
 template <typename R, typename R4>
 __device__ __forceinline__ R elem_row(const R4 &G, int a, R kA, R mA, R x0, R x1, R x2) {
-  const R dx = G.x * (x0 - x2) + G.z * (x1 - x2);
-  const R dy = G.y * (x0 - x2) + G.w * (x1 - x2);
+  const R dx = rfma(G.x, x0 - x2, rmul(G.z, x1 - x2));
+  const R dy = rfma(G.y, x0 - x2, rmul(G.w, x1 - x2));
   R gx, gy;
   slot_grad<R>(G, a, gx, gy);
   const R xa = a == 0 ? x0 : (a == 1 ? x1 : x2);
-  return kA * (gx * dx + gy * dy) + mA * (xa + x0 + x1 + x2);
+  return rfma(kA, rfma(gx, dx, rmul(gy, dy)), rmul(mA, radd(radd(radd(xa, x0), x1), x2)));
 }
 
 // Entry record of slot a of an element (FP32 entry records): the other two
@@ -1094,21 +1107,37 @@ __global__ void __launch_bounds__(256) k_drec_build(Params<R> P) {
 // rhs_entry's arithmetic on an element already loaded (t, A, G), its
 // history h in the kernel precision and toughness scale sg (the fused
 // force and right-hand-side kernel calls this directly).
+// The entry's four terms from its element's load density w, coefficients
+// kA, mA, the notch flags n0..n2 and x0 = d_prev of its three nodes.
+template <typename R>
+__device__ __forceinline__ typename Params<R>::R4 rhs_entry_terms(int a, R A, const typename Params<R>::R4 &G, R w,
+                                                                  R kA, R mA, bool n0, bool n1, bool n2, R x0, R x1,
+                                                                  R x2) {
+  typedef typename Params<R>::R4 R4;
+  R gx, gy;
+  slot_grad<R>(G, a, gx, gy);
+  R4 o;
+  o.x = rmul(rmul(w, A), R(1) / R(3));
+  o.y = rfma(kA, rfma(gx, gx, rmul(gy, gy)), rmul(R(2), mA));
+  o.z = elem_row<R>(G, a, kA, mA, x0, x1, x2);
+  o.w = (n0 || n1 || n2) ? elem_row<R>(G, a, kA, mA, n0 ? R(1) : R(0), n1 ? R(1) : R(0), n2 ? R(1) : R(0))
+                         : R(0);
+  return o;
+}
+
 template <typename R>
 __device__ __forceinline__ typename Params<R>::R4 rhs_entry_core(const Params<R> &P, int e, int a, const int4 &t,
                                                                  R A, const typename Params<R>::R4 &G, R h, R sg,
                                                                  int slot, int node, int csr,
                                                                  typename Params<R>::R2 *cf, uint32_t fm = kFanLoad) {
   typedef typename Params<R>::R4 R4;
-  const R w = P.wbase * sg + R(2) * h;
+  const R w = rfma(P.wbase, sg, rmul(R(2), h));
   const bool n0 = P.flags[t.x] & kNotch, n1 = P.flags[t.y] & kNotch, n2 = P.flags[t.z] & kNotch;
   const R x0 = n0 ? R(1) : P.dprev[t.x];
   const R x1 = n1 ? R(1) : P.dprev[t.y];
   const R x2 = n2 ? R(1) : P.dprev[t.z];
   R kA, mA;
   dmg_coefs(P, e, A, h, sg, kA, mA);
-  R gx, gy;
-  slot_grad<R>(G, a, gx, gy);
   if (a == 0 && P.drec) P.drec[e] = make_drec<R>(t, G, kA, mA);
   if (cf) {
     *cf = erec_coef<R>(G, a, kA, mA);
@@ -1120,13 +1149,7 @@ __device__ __forceinline__ typename Params<R>::R4 rhs_entry_core(const Params<R>
     }
     if (slot >= 0) put_erec(P, slot, node, G, a, kA, mA, fm);
   }
-  R4 o;
-  o.x = w * A * (R(1) / R(3));
-  o.y = kA * (gx * gx + gy * gy) + R(2) * mA;
-  o.z = elem_row<R>(G, a, kA, mA, x0, x1, x2);
-  o.w = (n0 || n1 || n2) ? elem_row<R>(G, a, kA, mA, n0 ? R(1) : R(0), n1 ? R(1) : R(0), n2 ? R(1) : R(0))
-                         : R(0);
-  return o;
+  return rhs_entry_terms<R>(a, A, G, w, kA, mA, n0, n1, n2, x0, x1, x2);
 }
 
 template <typename R>
@@ -1317,8 +1340,8 @@ __device__ __forceinline__ void force_rhs_entry(const Params<R> &P, int en, int 
   load_elem(P, e, t, A, G);
   R exx, eyy, exy;
   elem_strain(P, G, t, exx, eyy, exy);
-  const R db = (P.d[t.x] + P.d[t.y] + P.d[t.z]) * (R(1) / R(3));
-  const R g = (R(1) - db) * (R(1) - db) + P.eta;
+  const R db = rmul(radd(radd(P.d[t.x], P.d[t.y]), P.d[t.z]), R(1) / R(3));
+  const R g = rfma(R(1) - db, R(1) - db, P.eta);
   R sxx, syy, sxy;
   stress(P, exx, eyy, exy, g, sxx, syy, sxy, psip);
   R gx, gy;

@@ -2815,6 +2815,14 @@ pff_status pff_mesh_schedule(const pff_mesh *m, int32_t *variant, float *tune_ms
   return PFF_OK;
 }
 
+pff_status pff_mesh_fused_schedule(const pff_mesh *m, int32_t *variant, float *tune_ms) {
+  if (!m) return fail(PFF_ERR_ARG, "null mesh");
+  if (variant) *variant = m->var[KP_FRHS] + 1;
+  if (tune_ms)
+    for (int v = 0; v < kNumVariants; ++v) tune_ms[v] = m->tune_ms[KP_FRHS][v];
+  return PFF_OK;
+}
+
 pff_status pff_mesh_resident_forms(const pff_mesh *m, int32_t *forms) {
   if (!m || !forms) return fail(PFF_ERR_ARG, "null argument");
   for (int U = 1; U <= 4; ++U)

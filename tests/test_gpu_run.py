@@ -341,3 +341,40 @@ def test_run_host_matches_device_run(orc, pff, prec, loop, model):
             assert torch.equal(host[k], ref[k].cpu()), (k_steps, k)
         n0 += k_steps
     assert gm.sync_status() == 0
+
+
+@pytest.mark.parametrize("name,split,model,field", [("plate_100x40", "spectral", "AT2", False),
+                                                     ("plate_100x40", "amor", "AT1", False),
+                                                     ("plate_100x40", "spectral", "AT2", True),
+                                                     ("plate_500x500", "spectral", "AT2", False)])
+def test_fused_variants_bit_identical(orc, pff, name, split, model, field):
+    """Every variant of the fused force and right-hand side (1..5: one to
+    four entries in flight) against the two separate kernels: identical bits
+    in every field and the same CG counts after FP32 steps.  The element
+    arithmetic spells out every multiply-add, so kernels of different shape
+    round alike; the 251k-node plate has more rows than the grid has
+    threads (grid-stride rows), and the toughness field varies from element
+    to element."""
+    import torch
+    c = S.config(name, split=split, model=model)
+    gm = pff.Mesh.from_plate(c["mesh"], precision="fp32")
+    gm.set_material(c["material"], c["cfl"])
+    if field:
+        cx = c["mesh"]["xy"][c["mesh"]["tri"]].mean(axis=1)[:, 0]
+        gm.set_gc_field(c["material"]["Gc"] * (1.0 + 0.3 * np.sin(60.0 * cx)))
+    nsteps = 30 if name == "plate_100x40" else 8
+    out = []
+    for var, fuse in [(0, 1), (1, 2), (2, 2), (3, 2), (4, 2), (5, 2)]:
+        st = gm.new_state()
+        log = torch.zeros(nsteps, 2, dtype=torch.int32, device="cuda")
+        gm.run(st, nsteps, opts=pff.options(variant=var, fuse=fuse), iters_log=log)
+        torch.cuda.synchronize()
+        assert gm.sync_status() == 0
+        if var > 0:
+            assert gm.fused_schedule()[0] == var
+        out.append((st, log.cpu().numpy()))
+    assert float(out[0][0]["d"].max()) > 0.5
+    for st, lg in out[1:]:
+        for k in ("u", "v", "a", "d", "H"):
+            assert torch.equal(st[k], out[0][0][k]), k
+        assert np.array_equal(lg, out[0][1])
