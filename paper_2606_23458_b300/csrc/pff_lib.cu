@@ -1722,13 +1722,24 @@ __global__ void __launch_bounds__(256) k_tape_store(Params<R> P, Tape T) {
 }
 
 // The clamp of Sec. 2.4 (k_dmg_finish's arithmetic, AT2) applied to the
-// unclamped solution taped by the forward run instead of a fresh solve:
-// the mechanics-only recompute of the damage-tape checkpoint policy.
-// Slot *base + step of the run's tape; advances the step counter.
+// unclamped solution taped by the forward run instead of a fresh solve, and
+// the tape store of the recomputed step (u, d and H into slot k of the
+// segment's tape T): the mechanics-only recompute of the damage-tape
+// checkpoint policy.  k is the step counter, which every thread reads (x
+// from slot *base + k of the run's tape); the last block to finish, counted
+// on *ticket (0 on entry, left 0), advances it, so no block can see it
+// advanced while it still has to read it.
 template <typename R>
-__global__ void __launch_bounds__(256) k_finish_tape(Params<R> P, const R *tx, int64_t stride, const int64_t *base) {
-  const R *x = tx + (*P.step_ctr + *base) * stride;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.N; i += gridDim.x * blockDim.x) {
+__global__ void __launch_bounds__(256) k_finish_tape(Params<R> P, Tape T, const R *tx, int64_t stride,
+                                                    const int64_t *base, unsigned int *ticket) {
+  typedef typename V<R>::T2 R2;
+  const int64_t k = *P.step_ctr;
+  const R *x = tx + (k + *base) * stride;
+  R2 *tu = (R2 *)T.u + k * T.stride_n;
+  R *td = (R *)T.d + k * T.stride_n;
+  double *tH = T.H + k * T.stride_e;
+  const int gs = gridDim.x * blockDim.x;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.N; i += gs) {
     R v;
     if (P.flags[i] & kNotch) {
       v = R(1);
@@ -1739,8 +1750,18 @@ __global__ void __launch_bounds__(256) k_finish_tape(Params<R> P, const R *tx, i
       v = v < R(1) ? v : R(1);
     }
     P.dout[i] = v;
+    td[i] = v;
+    tu[i] = P.u[i];
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0 && P.step_inc) *P.step_inc += 1;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < P.Ne; e += gs) tH[e] = P.H[e];
+  __syncthreads();  // every thread of the block has read the counter
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(ticket, 1u) == gridDim.x - 1) {
+      *ticket = 0u;
+      if (P.step_inc) *P.step_inc += 1;
+    }
+  }
 }
 
 __global__ void k_set_i64(int64_t *p, int64_t v) {
@@ -3270,15 +3291,13 @@ static pff_status recompute_mech_t(pff_mesh *m, pff_ckpt *c, const pff_state *st
     const R *tx = (const R *)c->tX;
     int64_t stride = (int64_t)Np;
     const int64_t *base = c->xbase;
-    void *fargs[] = {(void *)&P, (void *)&tx, (void *)&stride, (void *)&base};
-    void *targs[] = {(void *)&P, (void *)&T};
-    const unsigned Gn = std::min<unsigned>(grid_for(m->N, kThreads), m->grid[KP_UPDATE][0]);
+    unsigned int *ticket = reinterpret_cast<unsigned int *>(c->kctr + 3);  // zeroed by backward_t
+    void *fargs[] = {(void *)&P, (void *)&T, (void *)&tx, (void *)&stride, (void *)&base, (void *)&ticket};
     const unsigned Gt = std::min<unsigned>(grid_for(std::max(m->N, m->Ne), kThreads), m->grid[KP_UPDATE][0]);
-    cudaGraphNode_t n_pr, n_f, n_fin, n_t;
+    cudaGraphNode_t n_pr, n_f, n_fin;
     pff_status stt = add_kernel<R>(m, g, {}, KP_PREDICT, P, &n_pr);
     if (stt == PFF_OK) stt = add_kernel<R>(m, g, {n_pr}, KP_FORCE, P, &n_f);
-    if (stt == PFF_OK) stt = add_generic(g, {n_f}, (const void *)k_finish_tape<R>, Gn, kThreads, 0, fargs, &n_fin);
-    if (stt == PFF_OK) stt = add_generic(g, {n_fin}, (const void *)k_tape_store<R>, Gt, kThreads, 0, targs, &n_t);
+    if (stt == PFF_OK) stt = add_generic(g, {n_f}, (const void *)k_finish_tape<R>, Gt, kThreads, 0, fargs, &n_fin);
     if (stt != PFF_OK) {
       cudaGraphDestroy(g);
       return stt;
