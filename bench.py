@@ -63,6 +63,10 @@ def parse():
                     help="skip the quasi-static single-edge-notched tension measurement")
     ap.add_argument("--qs-only", action="store_true",
                     help="run only the quasi-static measurement and print its line")
+    ap.add_argument("--batch-only", action="store_true",
+                    help="run only the 64-plate batch measurement and print its line")
+    ap.add_argument("--batch-steps", type=int, default=500,
+                    help="timed steps of the 64-plate batch (500 by default)")
     ap.add_argument("--qs-increments", type=int, default=100,
                     help="timed load increments of the quasi-static run (all 100 by default)")
     ap.add_argument("--no-variants", action="store_true",
@@ -455,14 +459,15 @@ def cpu_baseline(args, budget_s=20.0):
                        f"({n} steps, {el:.1f} s, single thread of {host_cores()} host threads, FP64)")
 
 
-def batched(pff, dev, steps=500, warmup=5):
+def batched(pff, dev, steps=500, warmup=5, nvtx=False):
     """The batched workload: 64 independent plates drawn from SplitMix64
     seed 1 (200..700 x 80..280 cells, Gc in [1, 5] J/m^2, traction in
     [0.5, 2] MPa), FP32 with FP64-class reductions, 500 steps, all plates
     advanced by one CUDA graph launch per step, the damage solves of all
     plates in the CG loop form and with the gathers in flight the batch's
-    autotuner picked (per-plate persistent launch or kernels per phase;
-    `tuning`), each plate to its own stop."""
+    autotuner picked (per-plate persistent launch, the per-plate resident
+    loop in waves of plates, or kernels per phase; `tuning`), each plate to
+    its own stop."""
     import torch
     plates = []
     for dr in S.batch_draws(64, seed=1):
@@ -478,9 +483,13 @@ def batched(pff, dev, steps=500, warmup=5):
     stream = torch.cuda.current_stream()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    if nvtx:
+        torch.cuda.nvtx.range_push("timed")
     e0.record(stream)
     b.run(st, steps, step0=warmup, opts=opts, iters_log=log)
     e1.record(stream)
+    if nvtx:
+        torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     it = log.cpu().numpy()
@@ -896,6 +905,13 @@ def run_ours(args):
     torch.cuda.set_device(dev)
     import paper_2606_23458_b300 as pff
 
+    if args.batch_only:
+        if rank == 0:
+            print(json.dumps(dict(batched=batched(pff, dev, steps=args.batch_steps, nvtx=args.nvtx_range))),
+                  flush=True)
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
     if args.qs_only:
         if rank == 0:
             print(json.dumps(dict(quasistatic=quasistatic(pff, dev, args.qs_increments, compare_increments=0))),
