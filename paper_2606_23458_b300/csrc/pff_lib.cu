@@ -3046,6 +3046,9 @@ struct pff_ckpt {
   void *db = nullptr, *dbn = nullptr, *g = nullptr, *lam = nullptr, *Hcur = nullptr;
   void *fe = nullptr, *fd = nullptr;  // element shares of the reverse mechanics
   double *gc = nullptr;
+  // device counters, zeroed by each pff_backward: [0] the reverse sweep's
+  // tape slot, [1] worst adjoint-solve status, [2] adjoint CG iterations,
+  // [3] the damage-tape recompute's block ticket (k_finish_tape)
   int *kctr = nullptr;
   int64_t adj_iters = 0;  // adjoint CG iterations of the last pff_backward
   GraphCache rec_g;     // taping step graph of the recompute

@@ -56,6 +56,7 @@ def test_host_side_argument_checks(lib):
     assert lib.pff_last_error().decode()
     assert lib.pff_mesh_set_material(None, None, C.c_double(0.5), None) == 1
     assert lib.pff_mesh_cg_choice(None, None, None, None) == 1
+    assert lib.pff_mesh_fused_schedule(None, None, None) == 1
     assert lib.pff_ckpt_create(None, C.c_int64(10), C.c_int32(0), C.byref(out)) == 1
     assert lib.pff_backward(None, None, None, None, None, None) == 1
     lib.pff_mesh_destroy(None)  # a no-op
