@@ -3,7 +3,9 @@
 * The 1M-node plate (1000 x 1000 cells, jittered): the first 8 steps in FP64
   against the oracle with the oracle forced to the GPU's CG iteration
   counts, every entry of every field within 1e-10 (spectral and
-  volumetric-deviatoric AT2); 3 steps of AT1 with the volumetric-deviatoric
+  volumetric-deviatoric AT2), 6 steps with plane stress (spectral and
+  isotropic splits), 8 steps with the damage solved every 2nd step; 3
+  steps of AT1 with the volumetric-deviatoric
   split and the projected CG at natural stops; FP32_MIXED with the bench's
   options against the same oracle state (u relative L2 <= 1e-4, max |d -
   d_oracle| <= 1e-3).
@@ -29,17 +31,18 @@ def pff():
     return pff
 
 
-def _fp64_window(orc, pff, c, nsteps, forced_counts=True):
+def _fp64_window(orc, pff, c, nsteps, forced_counts=True, mat=None, n_sub=1):
     """GPU FP64 and the oracle over the first nsteps steps of a plate, step
     by step: with forced_counts the oracle runs each step's CG for the GPU's
-    iteration count (AT2), else to its own stop.  Returns the worst
-    element-wise error per field over the window, the last states and the
-    GPU's iteration counts."""
+    iteration count (AT2), else to its own stop; mat replaces the plate's
+    material, n_sub > 1 solves damage every n_sub-th step on both sides.
+    Returns the worst element-wise error per field over the window, the
+    last states and the GPU's iteration counts."""
     import torch
-    mat = c["material"]
+    mat = c["material"] if mat is None else mat
     gm = pff.Mesh.from_plate(c["mesh"], precision="fp64")
     dt = gm.set_material(mat, c["cfl"])
-    opts = pff.options(cg_tol=c["cg_tol"], t_ramp=c["t_ramp"])
+    opts = pff.options(cg_tol=c["cg_tol"], t_ramp=c["t_ramp"], damage_every=n_sub)
     gst = gm.new_state()
     om = orc.Mesh.from_plate(c["mesh"])
     ost = om.new_state()
@@ -49,7 +52,7 @@ def _fp64_window(orc, pff, c, nsteps, forced_counts=True):
         gm.run(gst, 1, step0=n, opts=opts, iters_log=log[n:n + 1])
         torch.cuda.synchronize()
         forced = [int(log[n, 0])] if forced_counts else None
-        r = om.run(mat, ost, 1, dt, n0=n, t_ramp=c["t_ramp"], forced=forced)
+        r = om.run(mat, ost, 1, dt, n0=n, t_ramp=c["t_ramp"], forced=forced, n_sub=n_sub)
         oiters.append(int(r["iters"][0, 0]))
         merge_worst(worst, state_errs(gst, ost, floors=FIELD_FLOOR))  # 1e-6 on every field
     assert gm.sync_status() == 0
@@ -81,6 +84,29 @@ def test_fp64_1m_plate_amor_matches_oracle(orc, pff):
     print(f"1M plate, Amor FP64, 8 steps: element-wise worst {r['worst']}, CG iterations {r['iters']}")
     assert max(r["worst"].values()) <= 1e-10, r["worst"]
     assert np.abs(r["g64"]["H"]).max() > 0
+
+
+@pytest.mark.parametrize("split", ["spectral", "iso"])
+def test_fp64_1m_plate_plane_stress_matches_oracle(orc, pff, split):
+    """Plane stress (Sec. 2.1 plane assumptions) on the 1M-node plate with
+    the spectral and the isotropic split: 6 steps in FP64, every entry
+    within 1e-10 of the oracle per step."""
+    c = S.config("plate_1000x1000", split=split)
+    r = _fp64_window(orc, pff, c, 6, mat=dict(c["material"], plane="stress"))
+    print(f"1M plate, plane stress {split} FP64, 6 steps: element-wise worst {r['worst']}, CG iterations {r['iters']}")
+    assert max(r["worst"].values()) <= 1e-10, r["worst"]
+    assert np.abs(r["g64"]["H"]).max() > 0 and max(r["iters"]) > 0
+
+
+def test_fp64_1m_plate_subcycled_matches_oracle(orc, pff):
+    """Damage subcycling (Sec. 2.4) on the 1M-node plate: the damage solved
+    every 2nd step (the glass plate's limit), H every step; 8 steps in FP64,
+    every entry within 1e-10 of the oracle per step, and no solve on the
+    skipped steps."""
+    r = _fp64_window(orc, pff, S.config("plate_1000x1000"), 8, n_sub=2)
+    print(f"1M plate, subcycled FP64, 8 steps: element-wise worst {r['worst']}, CG iterations {r['iters']}")
+    assert max(r["worst"].values()) <= 1e-10, r["worst"]
+    assert all(r["iters"][n] == 0 for n in range(0, 8, 2)) and max(r["iters"]) > 0
 
 
 def test_fp64_1m_plate_at1_amor_matches_oracle(orc, pff):
