@@ -4,7 +4,8 @@
   against the oracle with the oracle forced to the GPU's CG iteration
   counts, every entry of every field within 1e-10 (spectral and
   volumetric-deviatoric AT2), 6 steps with plane stress (spectral and
-  isotropic splits), 8 steps with the damage solved every 2nd step; 3
+  isotropic splits), 8 steps with the damage solved every 2nd step, 6
+  steps with a per-element toughness field; 3
   steps of AT1 with the volumetric-deviatoric
   split and the projected CG at natural stops; FP32_MIXED with the bench's
   options against the same oracle state (u relative L2 <= 1e-4, max |d -
@@ -31,11 +32,12 @@ def pff():
     return pff
 
 
-def _fp64_window(orc, pff, c, nsteps, forced_counts=True, mat=None, n_sub=1):
+def _fp64_window(orc, pff, c, nsteps, forced_counts=True, mat=None, n_sub=1, gc=None):
     """GPU FP64 and the oracle over the first nsteps steps of a plate, step
     by step: with forced_counts the oracle runs each step's CG for the GPU's
     iteration count (AT2), else to its own stop; mat replaces the plate's
-    material, n_sub > 1 solves damage every n_sub-th step on both sides.
+    material, n_sub > 1 solves damage every n_sub-th step on both sides, gc
+    (per element) is a toughness field set on both sides.
     Returns the worst element-wise error per field over the window, the
     last states and the GPU's iteration counts."""
     import torch
@@ -43,8 +45,12 @@ def _fp64_window(orc, pff, c, nsteps, forced_counts=True, mat=None, n_sub=1):
     gm = pff.Mesh.from_plate(c["mesh"], precision="fp64")
     dt = gm.set_material(mat, c["cfl"])
     opts = pff.options(cg_tol=c["cg_tol"], t_ramp=c["t_ramp"], damage_every=n_sub)
+    if gc is not None:
+        gm.set_gc_field(gc)
     gst = gm.new_state()
     om = orc.Mesh.from_plate(c["mesh"])
+    if gc is not None:
+        om.set_gc_field(gc)
     ost = om.new_state()
     log = torch.zeros(nsteps, 2, dtype=torch.int32, device="cuda")
     worst, oiters = {}, []
@@ -107,6 +113,20 @@ def test_fp64_1m_plate_subcycled_matches_oracle(orc, pff):
     print(f"1M plate, subcycled FP64, 8 steps: element-wise worst {r['worst']}, CG iterations {r['iters']}")
     assert max(r["worst"].values()) <= 1e-10, r["worst"]
     assert all(r["iters"][n] == 0 for n in range(0, 8, 2)) and max(r["iters"]) > 0
+
+
+def test_fp64_1m_plate_toughness_field_matches_oracle(orc, pff):
+    """A per-element toughness field Gc_e = Gc (1 + 0.3 sin(60 x_e / m))
+    (Sec. 4.2's field-valued parameter) on the 1M-node plate: 6 steps in
+    FP64, every entry within 1e-10 of the oracle per step."""
+    c = S.config("plate_1000x1000")
+    m = c["mesh"]
+    cx = np.asarray(m["xy"])[np.asarray(m["tri"])].mean(axis=1)[:, 0]
+    gc = c["material"]["Gc"] * (1.0 + 0.3 * np.sin(60.0 * cx))
+    r = _fp64_window(orc, pff, c, 6, gc=gc)
+    print(f"1M plate, toughness field FP64, 6 steps: element-wise worst {r['worst']}, CG iterations {r['iters']}")
+    assert max(r["worst"].values()) <= 1e-10, r["worst"]
+    assert max(r["iters"]) > 0
 
 
 def test_fp64_1m_plate_at1_amor_matches_oracle(orc, pff):
