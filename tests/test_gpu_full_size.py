@@ -9,7 +9,8 @@
   steps of AT1 with the volumetric-deviatoric
   split and the projected CG at natural stops; FP32_MIXED with the bench's
   options against the same oracle state (u relative L2 <= 1e-4, max |d -
-  d_oracle| <= 1e-3).
+  d_oracle| <= 1e-3), and so for the volumetric-deviatoric split and AT1
+  with it against the oracle at natural stops.
 * The differentiation plate (500 x 500 cells): dL/dGc of a short window in
   FP32 against the oracle's discrete adjoint.
 * The 700 x 700 SENT: one load increment with the tangent CG in FP32 against
@@ -170,6 +171,31 @@ def test_fp32_1m_plate_bench_configuration(pff, plate_1m, cgk):
     o = plate_1m["ost"]
     assert rel_l2(to_np(gst["u"]), o["u"]) <= 1e-4
     assert np.abs(to_np(gst["d"]) - o["d"]).max() <= 1e-3
+
+
+@pytest.mark.parametrize("split,model,nsteps", [("amor", "AT2", 8), ("amor", "AT1", 3)])
+def test_fp32_1m_plate_variants_vs_oracle(orc, pff, split, model, nsteps):
+    """FP32_MIXED with the bench's options for the volumetric-deviatoric
+    split (AT2) and for AT1 with it (bound-projected CG) on the 1M-node
+    plate, against the FP64 oracle at its natural stops: u relative L2
+    <= 1e-4 and max |d - d_oracle| <= 1e-3, the FP32 bounds."""
+    import torch
+    c = S.config("plate_1000x1000", split=split, model=model)
+    gm = pff.Mesh.from_plate(c["mesh"], precision="fp32")
+    dt = gm.set_material(c["material"], c["cfl"])
+    gst = gm.new_state()
+    gm.run(gst, nsteps, opts=pff.options(cg_tol=c["cg_tol"], t_ramp=c["t_ramp"]))
+    torch.cuda.synchronize()
+    assert gm.sync_status() == 0
+    om = orc.Mesh.from_plate(c["mesh"])
+    ost = om.new_state()
+    om.run(c["material"], ost, nsteps, dt, t_ramp=c["t_ramp"])
+    eu = rel_l2(to_np(gst["u"]), ost["u"])
+    ed = float(np.abs(to_np(gst["d"]) - ost["d"]).max())
+    print(f"1M plate, {model} {split} FP32 vs FP64 oracle, {nsteps} steps: u rel L2 {eu:.2e}, max |dd| {ed:.2e}")
+    assert eu <= 1e-4 and ed <= 1e-3, (eu, ed)
+    band = (ost["d"] > 0) & (np.asarray(c["mesh"]["notch"]) == 0)
+    assert np.abs(ost["u"]).max() > 0 and band.sum() > 0  # the window loaded the plate and grew damage
 
 
 def test_differentiation_plate_gradient(orc, pff):
