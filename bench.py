@@ -977,12 +977,6 @@ def run_ours(args):
     ms = e0.elapsed_time(e1)
     status = mesh.sync_status()
     iters = log[args.warmup:total, 0].cpu().numpy()
-    # our kernels in the timed region: the history mirror once per run call,
-    # then per step predictor, force, right-hand side, finish and the CG loop
-    # (one persistent launch, or a matvec and an update per iteration)
-    cg_kind_run = mesh.cg_choice()[0]
-    per_solve = 1 if cg_kind_run not in ("phases", "auto") else None
-    launches = int(1 + 4 * args.steps + (args.steps * per_solve if per_solve else 2 * iters.sum()))
 
     # end-to-end through the public API with host-resident state
     # (pff_run_host, one call for the e2e steps): every step copies the state
@@ -1012,6 +1006,13 @@ def run_ours(args):
     frhs_var, frhs_ms = mesh.fused_schedule()
     cg_kind, cg_U, cg_ms = mesh.cg_choice()
     prof = mesh.profile_kernels(st, reps=5, opts=opts)
+    # our kernels in the timed region: the history mirror once per run call,
+    # then per step the predictor, the force and right-hand side (one fused
+    # kernel, or two), the clamp and the CG loop (one persistent launch, or
+    # a matvec and an update per iteration)
+    per_solve = 1 if cg_kind not in ("phases", "auto") else None
+    per_step = 3 if prof.get("force_rhs_used") else 4
+    launches = int(1 + per_step * args.steps + (args.steps * per_solve if per_solve else 2 * iters.sum()))
 
     # aggregate over ranks
     value, t_max = job_throughput(ms, N, args.steps, device=dev)
