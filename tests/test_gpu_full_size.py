@@ -173,26 +173,38 @@ def test_fp32_1m_plate_bench_configuration(pff, plate_1m, cgk):
     assert np.abs(to_np(gst["d"]) - o["d"]).max() <= 1e-3
 
 
-@pytest.mark.parametrize("split,model,nsteps", [("amor", "AT2", 8), ("amor", "AT1", 3)])
-def test_fp32_1m_plate_variants_vs_oracle(orc, pff, split, model, nsteps):
-    """FP32_MIXED with the bench's options for the volumetric-deviatoric
-    split (AT2) and for AT1 with it (bound-projected CG) on the 1M-node
-    plate, against the FP64 oracle at its natural stops: u relative L2
+@pytest.mark.parametrize("split,model,nsteps,plane,field", [("amor", "AT2", 8, "strain", False),
+                                                            ("amor", "AT1", 3, "strain", False),
+                                                            ("iso", "AT2", 6, "stress", False),
+                                                            ("spectral", "AT2", 6, "strain", True)])
+def test_fp32_1m_plate_variants_vs_oracle(orc, pff, split, model, nsteps, plane, field):
+    """FP32_MIXED with the bench's options on the 1M-node plate for the
+    volumetric-deviatoric split (AT2), AT1 with it (bound-projected CG),
+    plane stress with the isotropic split, and a per-element toughness
+    field, against the FP64 oracle at its natural stops: u relative L2
     <= 1e-4 and max |d - d_oracle| <= 1e-3, the FP32 bounds."""
     import torch
     c = S.config("plate_1000x1000", split=split, model=model)
+    mat = dict(c["material"], plane=plane)
     gm = pff.Mesh.from_plate(c["mesh"], precision="fp32")
-    dt = gm.set_material(c["material"], c["cfl"])
+    dt = gm.set_material(mat, c["cfl"])
+    om = orc.Mesh.from_plate(c["mesh"])
+    if field:
+        m = c["mesh"]
+        cx = np.asarray(m["xy"])[np.asarray(m["tri"])].mean(axis=1)[:, 0]
+        gc = mat["Gc"] * (1.0 + 0.3 * np.sin(60.0 * cx))
+        gm.set_gc_field(gc)
+        om.set_gc_field(gc)
     gst = gm.new_state()
     gm.run(gst, nsteps, opts=pff.options(cg_tol=c["cg_tol"], t_ramp=c["t_ramp"]))
     torch.cuda.synchronize()
     assert gm.sync_status() == 0
-    om = orc.Mesh.from_plate(c["mesh"])
     ost = om.new_state()
-    om.run(c["material"], ost, nsteps, dt, t_ramp=c["t_ramp"])
+    om.run(mat, ost, nsteps, dt, t_ramp=c["t_ramp"])
     eu = rel_l2(to_np(gst["u"]), ost["u"])
     ed = float(np.abs(to_np(gst["d"]) - ost["d"]).max())
-    print(f"1M plate, {model} {split} FP32 vs FP64 oracle, {nsteps} steps: u rel L2 {eu:.2e}, max |dd| {ed:.2e}")
+    print(f"1M plate, {model} {split} plane {plane}{' field' if field else ''} FP32 vs FP64 oracle, {nsteps} steps: "
+          f"u rel L2 {eu:.2e}, max |dd| {ed:.2e}")
     assert eu <= 1e-4 and ed <= 1e-3, (eu, ed)
     band = (ost["d"] > 0) & (np.asarray(c["mesh"]["notch"]) == 0)
     assert np.abs(ost["u"]).max() > 0 and band.sum() > 0  # the window loaded the plate and grew damage
