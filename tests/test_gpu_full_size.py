@@ -173,15 +173,17 @@ def test_fp32_1m_plate_bench_configuration(pff, plate_1m, cgk):
     assert np.abs(to_np(gst["d"]) - o["d"]).max() <= 1e-3
 
 
-@pytest.mark.parametrize("split,model,nsteps,plane,field", [("amor", "AT2", 8, "strain", False),
-                                                            ("amor", "AT1", 3, "strain", False),
-                                                            ("iso", "AT2", 6, "stress", False),
-                                                            ("spectral", "AT2", 6, "strain", True)])
-def test_fp32_1m_plate_variants_vs_oracle(orc, pff, split, model, nsteps, plane, field):
+@pytest.mark.parametrize("split,model,nsteps,plane,field,n_sub", [("amor", "AT2", 8, "strain", False, 1),
+                                                                  ("amor", "AT1", 3, "strain", False, 1),
+                                                                  ("iso", "AT2", 6, "stress", False, 1),
+                                                                  ("spectral", "AT2", 6, "strain", True, 1),
+                                                                  ("spectral", "AT2", 8, "strain", False, 2)])
+def test_fp32_1m_plate_variants_vs_oracle(orc, pff, split, model, nsteps, plane, field, n_sub):
     """FP32_MIXED with the bench's options on the 1M-node plate for the
     volumetric-deviatoric split (AT2), AT1 with it (bound-projected CG),
-    plane stress with the isotropic split, and a per-element toughness
-    field, against the FP64 oracle at its natural stops: u relative L2
+    plane stress with the isotropic split, a per-element toughness field,
+    and the damage solved every 2nd step (both sides), against the FP64
+    oracle at its natural stops: u relative L2
     <= 1e-4 and max |d - d_oracle| <= 1e-3, the FP32 bounds."""
     import torch
     c = S.config("plate_1000x1000", split=split, model=model)
@@ -196,14 +198,14 @@ def test_fp32_1m_plate_variants_vs_oracle(orc, pff, split, model, nsteps, plane,
         gm.set_gc_field(gc)
         om.set_gc_field(gc)
     gst = gm.new_state()
-    gm.run(gst, nsteps, opts=pff.options(cg_tol=c["cg_tol"], t_ramp=c["t_ramp"]))
+    gm.run(gst, nsteps, opts=pff.options(cg_tol=c["cg_tol"], t_ramp=c["t_ramp"], damage_every=n_sub))
     torch.cuda.synchronize()
     assert gm.sync_status() == 0
     ost = om.new_state()
-    om.run(mat, ost, nsteps, dt, t_ramp=c["t_ramp"])
+    om.run(mat, ost, nsteps, dt, t_ramp=c["t_ramp"], n_sub=n_sub)
     eu = rel_l2(to_np(gst["u"]), ost["u"])
     ed = float(np.abs(to_np(gst["d"]) - ost["d"]).max())
-    print(f"1M plate, {model} {split} plane {plane}{' field' if field else ''} FP32 vs FP64 oracle, {nsteps} steps: "
+    print(f"1M plate, {model} {split} plane {plane}{' field' if field else ''} n_sub {n_sub} FP32 vs FP64 oracle, {nsteps} steps: "
           f"u rel L2 {eu:.2e}, max |dd| {ed:.2e}")
     assert eu <= 1e-4 and ed <= 1e-3, (eu, ed)
     band = (ost["d"] > 0) & (np.asarray(c["mesh"]["notch"]) == 0)
